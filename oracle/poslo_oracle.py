@@ -1,0 +1,481 @@
+"""CPU oracle for POSLO batch verification (test infrastructure only).
+
+This is the plain, slow, obviously-correct statement of what the GPU path computes.  It
+is imported by the tests, by the package smoke check and by the benchmark's CPU-baseline
+leg, and by nothing else: the product path never calls it.  It shares no code with the
+CUDA library; the two meet only through the seeded inputs of ``synth``.
+
+Everything is exact integer arithmetic with Python ints.  SHA-256 is hashlib (a library
+primitive used as one step).  Section, figure and equation numbers refer to Nouma and
+Yavuz, "Lightweight and High-Throughput Secure Logging for Internet of Things and Cold
+Cloud Continuum" (arXiv 2506.08781).
+
+Readings of points the paper leaves open:
+  * group: the prime-order subgroup of edwards25519 (the paper names FourQ with
+    |q| = 256, which is self-inconsistent; no FourQ constants are given);
+  * PRF_b(z) = SHA-256(z || byte b)[:16] for the seed tree; the per-entry seed is
+    x_i^j = PRF_0(x_0[i] || j) = SHA-256(x_0[i] || le32(j) || 0x00)[:16], j 0-based;
+  * e = SHA-256(m || x) read little-endian, reduced mod q;
+  * POSLO-C nonces r_i^j = SHA-256(r || le32(i) || le32(j) || 0x00) mod q;
+  * points are 32-byte compressed edwards25519 encodings, decoded strictly; scalars are
+    32-byte little-endian and must be canonical (< q);
+  * every group equation is checked with the cofactor: [8](R - eY - sG) = O.
+
+Parity pins: see tests/test_oracle_pins.py (hashlib KATs, libsodium group operations,
+the seed-tree worked example of Sec. 4.1, closed forms and brute force).
+"""
+from __future__ import annotations
+
+import hashlib
+import struct
+from dataclasses import dataclass
+
+# ----------------------------------------------------------------------------------
+# edwards25519 (RFC 8032 Sec. 5.1 parameters)
+# ----------------------------------------------------------------------------------
+P = 2 ** 255 - 19
+Q = 2 ** 252 + 27742317777372353535851937790883648493
+D = (-121665 * pow(121666, P - 2, P)) % P
+SQRT_M1 = pow(2, (P - 1) // 4, P)
+COFACTOR = 8
+
+IDENTITY = (0, 1, 1, 0)          # extended coordinates (X:Y:Z:T), x = X/Z, y = Y/Z, xy = T/Z
+
+
+def _recover_x(y: int, sign: int):
+    """x with x^2 = (y^2 - 1) / (d y^2 + 1) and parity `sign`, or None (RFC 8032 5.1.3)."""
+    if y >= P:
+        return None
+    u = (y * y - 1) % P
+    v = (D * y * y + 1) % P
+    x2 = u * pow(v, P - 2, P) % P
+    if x2 == 0:
+        return None if sign else 0
+    x = pow(x2, (P + 3) // 8, P)
+    if (x * x - x2) % P != 0:
+        x = x * SQRT_M1 % P
+    if (x * x - x2) % P != 0:
+        return None
+    if x & 1 != sign:
+        x = P - x
+    return x
+
+
+def point_from_affine(x: int, y: int):
+    return (x % P, y % P, 1, x * y % P)
+
+
+def to_affine(pt):
+    X, Y, Z, _ = pt
+    zi = pow(Z, P - 2, P)
+    return X * zi % P, Y * zi % P
+
+
+def on_curve(pt) -> bool:
+    x, y = to_affine(pt)
+    return (-x * x + y * y - 1 - D * x * x * y * y) % P == 0
+
+
+def decode_point(b: bytes):
+    """Strict decoding of a 32-byte compressed point; None if not a curve point."""
+    if len(b) != 32:
+        return None
+    v = int.from_bytes(b, "little")
+    sign = v >> 255
+    y = v & ((1 << 255) - 1)
+    x = _recover_x(y, sign)
+    if x is None:
+        return None
+    return point_from_affine(x, y)
+
+
+def encode_point(pt) -> bytes:
+    x, y = to_affine(pt)
+    return (y | ((x & 1) << 255)).to_bytes(32, "little")
+
+
+def point_add(p1, p2):
+    """Unified addition in extended coordinates for a = -1 (Hisil, Wong, Carter, Dawson,
+    "Twisted Edwards curves revisited", 2008); complete on edwards25519 since d is a
+    non-square."""
+    X1, Y1, Z1, T1 = p1
+    X2, Y2, Z2, T2 = p2
+    A = (Y1 - X1) * (Y2 - X2) % P
+    B = (Y1 + X1) * (Y2 + X2) % P
+    C = T1 * 2 * D * T2 % P
+    Dd = Z1 * 2 * Z2 % P
+    E, F, G_, H = B - A, Dd - C, Dd + C, B + A
+    return (E * F % P, G_ * H % P, F * G_ % P, E * H % P)
+
+
+def point_neg(pt):
+    X, Y, Z, T = pt
+    return ((-X) % P, Y, Z, (-T) % P)
+
+
+def point_sub(p1, p2):
+    return point_add(p1, point_neg(p2))
+
+
+def is_identity(pt) -> bool:
+    X, Y, Z, _ = pt
+    return X % P == 0 and (Y - Z) % P == 0
+
+
+def point_eq(p1, p2) -> bool:
+    X1, Y1, Z1, _ = p1
+    X2, Y2, Z2, _ = p2
+    return (X1 * Z2 - X2 * Z1) % P == 0 and (Y1 * Z2 - Y2 * Z1) % P == 0
+
+
+def scalar_mult(k: int, pt):
+    """Textbook left-to-right double-and-add, k >= 0."""
+    acc = IDENTITY
+    for bit in bin(k)[2:] if k else "":
+        acc = point_add(acc, acc)
+        if bit == "1":
+            acc = point_add(acc, pt)
+    return acc
+
+
+def _base_point():
+    y = 4 * pow(5, P - 2, P) % P
+    return point_from_affine(_recover_x(y, 0), y)
+
+
+G = _base_point()
+
+
+def mul_by_cofactor(pt):
+    return scalar_mult(COFACTOR, pt)
+
+
+# ----------------------------------------------------------------------------------
+# scalars mod q
+# ----------------------------------------------------------------------------------
+
+def scalar_to_bytes(k: int) -> bytes:
+    return (k % Q).to_bytes(32, "little")
+
+
+def scalar_from_bytes(b: bytes):
+    """Canonical 32-byte little-endian scalar, or None if >= q."""
+    k = int.from_bytes(b, "little")
+    return k if k < Q else None
+
+
+# ----------------------------------------------------------------------------------
+# H and PRF (Sec. 7.2 instantiation "POSLO": SHA-256 for both)
+# ----------------------------------------------------------------------------------
+
+def sha256(data: bytes) -> bytes:
+    return hashlib.sha256(data).digest()
+
+
+def prf(bit: int, z: bytes) -> bytes:
+    """PRF_bit(z) = F(z || bit) with F = SHA-256 truncated to kappa = 128 bits."""
+    return sha256(z + bytes([bit]))[:16]
+
+
+def entry_seed(x0: bytes, j: int) -> bytes:
+    """x_i^j = PRF_0(x_0[i] || j) (Fig. 3a AVer, Fig. 6 Agg-eKeys)."""
+    return sha256(x0 + struct.pack("<I", j) + b"\x00")[:16]
+
+
+def hash_to_scalar(m: bytes, x: bytes) -> int:
+    """e = H(m || x) mod q."""
+    return int.from_bytes(sha256(m + x), "little") % Q
+
+
+def nonce_c(r: bytes, i: int, j: int) -> int:
+    """POSLO-C one-time nonce r_i^j = PRF_0(r || i || j) mod q (Fig. 3a Kg)."""
+    return int.from_bytes(sha256(r + struct.pack("<II", i, j) + b"\x00"), "little") % Q
+
+
+# ----------------------------------------------------------------------------------
+# POSLOT seed tree and seed management functions (Sec. 4.1, Eq. 1, Fig. 2a)
+# ----------------------------------------------------------------------------------
+
+def tree_node(root: bytes, D_: int, d: int, i: int) -> bytes:
+    """x_d[i] by the recursive definition of Eq. 1: even children take PRF_0 of the
+    parent, odd children PRF_1; x_D[0] is the root."""
+    if not (0 <= d <= D_ and 0 <= i < (1 << (D_ - d))):
+        raise ValueError("node out of range")
+    if d == D_:
+        return root
+    parent = tree_node(root, D_, d + 1, i // 2)
+    return prf(i % 2, parent)
+
+
+def SC(x_src: bytes, d0: int, i0: int, d1: int, i1: int) -> bytes:
+    """Seed computation: walk from x_{d0}[i0] down to its descendant x_{d1}[i1]; bit j of
+    the relative offset (most significant first) chooses PRF_0 or PRF_1 (Fig. 2a)."""
+    if not (d1 <= d0 and i0 * (1 << (d0 - d1)) <= i1 < (i0 + 1) * (1 << (d0 - d1))):
+        raise ValueError("SC: target is not a descendant")
+    x = x_src
+    off = i1 - i0 * (1 << (d0 - d1))
+    for j in range(d0 - d1 - 1, -1, -1):
+        x = prf((off >> j) & 1, x)
+    return x
+
+
+@dataclass(frozen=True)
+class Node:
+    d: int
+    i: int
+    seed: bytes
+
+
+def SSO(ds: list, root: bytes, D_: int, i: int):
+    """Seed storage optimiser (Fig. 2a): returns (ds_i, x_0[i]) from ds_{i-1}.  While the
+    top of the stack sits at the current depth it is merged away and we move one level
+    up; then the node reached is pushed."""
+    if not 0 <= i < (1 << D_):
+        raise ValueError("SSO: epoch out of range")
+    ds = list(ds)
+    d1, i1 = 0, i
+    while ds and ds[-1].d == d1:
+        ds.pop()
+        d1 += 1
+        i1 //= 2
+    node = Node(d1, i1, SC(root, D_, 0, d1, i1))
+    ds.append(node)
+    return ds, SC(node.seed, d1, i1, 0, i)
+
+
+def SRet(ds: list, i_target: int) -> bytes:
+    """Seed retrieval (Fig. 2a): pop nodes until one covers leaf i_target, then walk down
+    to it.  Raises ValueError for the paper's bottom symbol."""
+    stack = list(ds)
+    if not stack:
+        raise ValueError("SRet: empty ds")
+    n = stack.pop()
+    if i_target >= (n.i + 1) << n.d:
+        raise ValueError("SRet: leaf not yet disclosed")
+    while i_target < n.i << n.d:
+        if not stack:
+            raise ValueError("SRet: no ancestor in ds")
+        n = stack.pop()
+    return SC(n.seed, n.d, n.i, 0, i_target)
+
+
+def ds_after(root: bytes, D_: int, i: int) -> list:
+    """ds_i obtained by running SSO for epochs 0..i from an empty stack."""
+    ds = []
+    for k in range(i + 1):
+        ds, _ = SSO(ds, root, D_, k)
+    return ds
+
+
+def ds_root(root: bytes, D_: int) -> list:
+    """The final disclosure: the root alone (Sec. 4.1)."""
+    return [Node(D_, 0, root)]
+
+
+def ds_serialize(ds: list) -> bytes:
+    """Wire form: 24 bytes per node, bottom of the stack first: le32 depth, le32 index,
+    16-byte seed."""
+    return b"".join(struct.pack("<II", n.d, n.i) + n.seed for n in ds)
+
+
+# ----------------------------------------------------------------------------------
+# POSLO-C (Fig. 3a)
+# ----------------------------------------------------------------------------------
+
+@dataclass
+class SecretKeyC:
+    y: int
+    r: bytes
+    root: bytes
+    D: int
+    n2: int
+
+
+def kg_c(y_bytes: bytes, r: bytes, root: bytes, D_: int, n2: int):
+    """POSLO-C.Kg: Y = yG and, per epoch i, R~_i = (sum_j r_i^j mod q) G."""
+    y = int.from_bytes(y_bytes, "little") % Q
+    if y == 0:
+        raise ValueError("y must be non-zero")
+    Y = scalar_mult(y, G)
+    epoch_R = []
+    for i in range(1 << D_):
+        ri = sum(nonce_c(r, i, j) for j in range(n2)) % Q
+        epoch_R.append(encode_point(scalar_mult(ri, G)))
+    return SecretKeyC(y, r, root, D_, n2), encode_point(Y), epoch_R
+
+
+def sig_c(sk: SecretKeyC, i: int, msgs_i: list) -> bytes:
+    """POSLO-C.Sig for epoch i: s~_i = sum_j (r_i^j - e_i^j y) mod q.  The disclosed
+    seeds ds_i that go with it come from SSO (ds_after)."""
+    if len(msgs_i) != sk.n2:
+        raise ValueError("epoch must hold n2 entries")
+    x0 = SC(sk.root, sk.D, 0, 0, i)
+    s = 0
+    for j, m in enumerate(msgs_i):
+        e = hash_to_scalar(m, entry_seed(x0, j))
+        s = (s + nonce_c(sk.r, i, j) - e * sk.y) % Q
+    return scalar_to_bytes(s)
+
+
+def agg_scalars(scalars: list) -> bytes:
+    """POSLO-C.Agg on scalar components: sum mod q."""
+    return scalar_to_bytes(sum(int.from_bytes(s, "little") for s in scalars) % Q)
+
+
+def agg_points(points: list) -> bytes:
+    """POSLO-C.Agg on commitments: the group operation over all of them."""
+    acc = IDENTITY
+    for b in points:
+        pt = decode_point(b)
+        if pt is None:
+            raise ValueError("undecodable point")
+        acc = point_add(acc, pt)
+    return encode_point(acc)
+
+
+def cofactored_check(R, e: int, Y, s: int) -> bool:
+    """[8](R - eY - sG) = O."""
+    diff = point_sub(point_sub(R, scalar_mult(e % Q, Y)), scalar_mult(s % Q, G))
+    return is_identity(mul_by_cofactor(diff))
+
+
+def aver_c(Y_bytes: bytes, epochs: list, msgs: list, n2: int, s_agg: bytes, R_agg, ds: list):
+    """POSLO-C.AVer (Fig. 3a): `epochs` lists the epoch indices I; msgs[k] holds the n2
+    entries of epoch epochs[k]; R_agg is either the aggregate R~ (bytes) or the list of
+    per-epoch R~_i from pk.  Returns True/False; raises ValueError for bottom."""
+    if any(len(mk) != n2 for mk in msgs) or len(msgs) != len(epochs):
+        raise ValueError("epoch sizes must equal n2")
+    Y = decode_point(Y_bytes)
+    if Y is None:
+        raise ValueError("bad public key")
+    if isinstance(R_agg, (bytes, bytearray)):
+        R = decode_point(bytes(R_agg))
+    else:
+        R = IDENTITY
+        for b in R_agg:
+            pt = decode_point(b)
+            if pt is None:
+                return False
+            R = point_add(R, pt)
+    s = scalar_from_bytes(s_agg)
+    if R is None or s is None:
+        return False
+    e = 0
+    for i, mk in zip(epochs, msgs):
+        x0 = SRet(ds, i)
+        for j, m in enumerate(mk):
+            e = (e + hash_to_scalar(m, entry_seed(x0, j))) % Q
+    return cofactored_check(R, e, Y, s)
+
+
+# ----------------------------------------------------------------------------------
+# POSLO-F (Fig. 4) with the BPV generator (Definition 3)
+# ----------------------------------------------------------------------------------
+
+@dataclass
+class SecretKeyF:
+    y: int
+    root: bytes
+    D: int
+    n2: int
+    bpv_r: list
+    bpv_R: list        # extended points
+
+
+def kg_f(y_bytes: bytes, root: bytes, D_: int, n2: int, bpv_r_bytes: bytes):
+    """POSLO-F.Kg: Y = yG and the BPV table {r_k, R_k = r_k G}."""
+    y = int.from_bytes(y_bytes, "little") % Q
+    if y == 0:
+        raise ValueError("y must be non-zero")
+    v = len(bpv_r_bytes) // 32
+    rs = [int.from_bytes(bpv_r_bytes[32 * k:32 * k + 32], "little") % Q for k in range(v)]
+    Rs = [scalar_mult(r, G) for r in rs]
+    return SecretKeyF(y, root, D_, n2, rs, Rs), encode_point(scalar_mult(y, G))
+
+
+def bpv_table_encoded(sk: SecretKeyF) -> list:
+    return [encode_point(R) for R in sk.bpv_R]
+
+
+def sig_f(sk: SecretKeyF, t: int, m: bytes, subset):
+    """POSLO-F.Sig for entry t: (r_t, R_t) = BPV.Online over `subset`, e_t = H(m || x_t)
+    with x_t = PRF_0(x_0[i] || j), s_t = r_t - e_t y.  Returns (s, R, x) as bytes."""
+    i, j = divmod(t, sk.n2)
+    x0 = SC(sk.root, sk.D, 0, 0, i)
+    r = sum(sk.bpv_r[k] for k in subset) % Q
+    R = IDENTITY
+    for k in subset:
+        R = point_add(R, sk.bpv_R[k])
+    x = entry_seed(x0, j)
+    e = hash_to_scalar(m, x)
+    s = (r - e * sk.y) % Q
+    return scalar_to_bytes(s), encode_point(R), x
+
+
+def entry_scalar(ds: list, n2: int, t: int, m: bytes) -> int:
+    """e_t of entry t under the disclosed seeds ds."""
+    i, j = divmod(t, n2)
+    return hash_to_scalar(m, entry_seed(SRet(ds, i), j))
+
+
+def verify_entry_f(Y, e: int, s_bytes: bytes, R_bytes: bytes) -> bool:
+    """Single-entry POSLO-F check (Fig. 4 AVer, |m| = 1): s canonical, R decodable and
+    [8](R - eY - sG) = O."""
+    s = scalar_from_bytes(s_bytes)
+    R = decode_point(R_bytes)
+    if s is None or R is None:
+        return False
+    return cofactored_check(R, e, Y, s)
+
+
+def aver_f(Y_bytes: bytes, msgs: list, first_index: int, n2: int, s_list: list, R_list: list,
+           ds: list) -> bool:
+    """POSLO-F.AVer over a batch (Fig. 4: C.AVer steps 2-8 with R~ = sum R_t): all s_t
+    canonical, all R_t decodable, and [8](sum R_t - (sum e_t) Y - (sum s_t) G) = O."""
+    Y = decode_point(Y_bytes)
+    if Y is None:
+        raise ValueError("bad public key")
+    R = IDENTITY
+    s = 0
+    e = 0
+    for k, m in enumerate(msgs):
+        sk = scalar_from_bytes(s_list[k])
+        Rk = decode_point(R_list[k])
+        if sk is None or Rk is None:
+            return False
+        R = point_add(R, Rk)
+        s = (s + sk) % Q
+        e = (e + entry_scalar(ds, n2, first_index + k, m)) % Q
+    return cofactored_check(R, e, Y, s)
+
+
+def distill_f(Y_bytes: bytes, msgs: list, first_index: int, n2: int, s_list: list, R_list: list,
+              ds: list):
+    """POSLO-F Distill (Sec. 4.3 prose, Fig. 3b semantics at entry granularity): the
+    invalid set is exactly the entries that fail their own check; ccd^v aggregates the
+    rest.  Returns (sorted global indices, ccd_s bytes, ccd_R bytes)."""
+    Y = decode_point(Y_bytes)
+    if Y is None:
+        raise ValueError("bad public key")
+    invalid = []
+    s_v, R_v = 0, IDENTITY
+    for k, m in enumerate(msgs):
+        t = first_index + k
+        e = entry_scalar(ds, n2, t, m)
+        if verify_entry_f(Y, e, s_list[k], R_list[k]):
+            s_v = (s_v + int.from_bytes(s_list[k], "little")) % Q
+            R_v = point_add(R_v, decode_point(R_list[k]))
+        else:
+            invalid.append(t)
+    return invalid, scalar_to_bytes(s_v), encode_point(R_v)
+
+
+def msm(scalars: list, points: list):
+    """sum_t k_t P_t by the definition (one scalar multiplication per term)."""
+    acc = IDENTITY
+    for k, b in zip(scalars, points):
+        pt = decode_point(b)
+        if pt is None:
+            raise ValueError("undecodable point")
+        acc = point_add(acc, scalar_mult(k, pt))
+    return encode_point(acc)

@@ -1,0 +1,369 @@
+"""Pins of the CPU oracle against things other than itself.
+
+Each test ties one part of oracle/poslo_oracle.py to an external fact: published
+known-answer values (FIPS 180-2, RFC 8032), libsodium's edwards25519 routines (through
+PyNaCl), the paper's worked seed-tree example (Sec. 4.1), closed forms from the scheme's
+algebra (Fig. 3a / Fig. 4, Appendix A extraction identity r = s + e y), group invariants,
+and brute force on tiny inputs.  A plausible slip in the oracle (dropped term, wrong
+sign, swapped PRF bit, wrong byte order, missing cofactor) fails at least one of them.
+"""
+import hashlib
+import struct
+
+import pytest
+
+from oracle import poslo_oracle as O
+from paper_2506_08781_gb300 import synth
+from tests.conftest import golden_lines
+
+nb = pytest.importorskip("nacl.bindings")
+
+
+# ---------------------------------------------------------------- SHA-256 / H / PRF
+
+def test_sha256_fips_kat():
+    for msg_hex, digest in golden_lines("sha256_kat.txt"):
+        msg = b"" if msg_hex == "-" else bytes.fromhex(msg_hex)
+        assert O.sha256(msg).hex() == digest
+
+
+def test_prf_and_entry_seed_layout():
+    # PRF_b(z) keeps the first kappa = 128 bits of SHA-256(z || b); the entry seed puts the
+    # 0-based index j as 4 little-endian bytes before the PRF_0 bit.
+    z = bytes(range(16))
+    assert O.prf(0, z) == hashlib.sha256(z + b"\x00").digest()[:16]
+    assert O.prf(1, z) == hashlib.sha256(z + b"\x01").digest()[:16]
+    assert O.prf(0, z) != O.prf(1, z)
+    assert O.entry_seed(z, 0x01020304) == hashlib.sha256(z + b"\x04\x03\x02\x01\x00").digest()[:16]
+
+
+def test_hash_to_scalar_little_endian_and_reduced():
+    m, x = b"log entry", bytes(16)
+    d = hashlib.sha256(m + x).digest()
+    e = O.hash_to_scalar(m, x)
+    assert 0 <= e < O.Q
+    assert e == int.from_bytes(d, "little") % O.Q
+    assert e != int.from_bytes(d, "big") % O.Q
+    # libsodium's scalar_reduce of the 64-byte zero-extended digest gives the same value
+    assert nb.crypto_core_ed25519_scalar_reduce(d + bytes(32)) == O.scalar_to_bytes(e)
+
+
+# ---------------------------------------------------------------- edwards25519
+
+def test_rfc8032_base_point_and_public_key():
+    vals = dict(golden_lines("ed25519_rfc8032.txt"))
+    x, y = O.to_affine(O.G)
+    assert x == int(vals["base_x"]) and y == int(vals["base_y"])
+    assert O.encode_point(O.G).hex() == vals["base_enc"]
+    h = hashlib.sha512(bytes.fromhex(vals["test1_secret"])).digest()
+    a = bytearray(h[:32])
+    a[0] &= 248
+    a[31] &= 127
+    a[31] |= 64
+    s = int.from_bytes(a, "little")
+    assert O.encode_point(O.scalar_mult(s, O.G)).hex() == vals["test1_public"]
+
+
+def test_group_order_and_on_curve():
+    assert O.is_identity(O.scalar_mult(O.Q, O.G))
+    assert not O.is_identity(O.scalar_mult(O.Q - 1, O.G))
+    assert O.on_curve(O.G)
+    assert O.on_curve(O.scalar_mult(123456789, O.G))
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 8, 255, 2 ** 128 + 1, O.Q - 1, 0xDEADBEEF * 2 ** 200 + 77])
+def test_base_mult_matches_libsodium(k):
+    want = nb.crypto_scalarmult_ed25519_base_noclamp(O.scalar_to_bytes(k))
+    assert O.encode_point(O.scalar_mult(k, O.G)) == want
+
+
+def test_point_add_and_variable_base_match_libsodium():
+    ks = [int.from_bytes(synth.random_bytes(7, f"k{i}", 32).tobytes(), "little") % O.Q for i in range(6)]
+    pts = [O.scalar_mult(k, O.G) for k in ks]
+    enc = [O.encode_point(p) for p in pts]
+    for a, b, pa, pb in zip(enc, enc[1:], pts, pts[1:]):
+        assert O.encode_point(O.point_add(pa, pb)) == nb.crypto_core_ed25519_add(a, b)
+        assert O.encode_point(O.point_sub(pa, pb)) == nb.crypto_core_ed25519_sub(a, b)
+        assert O.encode_point(O.point_add(pa, pa)) == nb.crypto_core_ed25519_add(a, a)
+    k = ks[0]
+    assert O.encode_point(O.scalar_mult(k, pts[1])) == nb.crypto_scalarmult_ed25519_noclamp(
+        O.scalar_to_bytes(k), enc[1])
+
+
+def test_decode_roundtrip_and_strictness():
+    for i in range(20):
+        p = O.scalar_mult(1000003 * i + 5, O.G)
+        b = O.encode_point(p)
+        assert O.point_eq(O.decode_point(b), p)
+        assert nb.crypto_core_ed25519_is_valid_point(b)
+    # y >= p is rejected (non-canonical encoding of y = 1 - p... here y = p + 1)
+    assert O.decode_point((O.P + 1).to_bytes(32, "little")) is None
+    # x = 0 with the sign bit set is rejected (y = 1 is the identity)
+    assert O.decode_point(((1 << 255) | 1).to_bytes(32, "little")) is None
+    assert O.is_identity(O.decode_point((1).to_bytes(32, "little")))
+    # about half of all y values have no x: find one and check libsodium agrees
+    y = 2
+    while O.decode_point(y.to_bytes(32, "little")) is not None:
+        y += 1
+    assert not nb.crypto_core_ed25519_is_valid_point(y.to_bytes(32, "little"))
+
+
+def test_torsion_killed_by_cofactor():
+    # [q]P of an arbitrary curve point lies in the 8-torsion; [8] kills it.
+    y = 3
+    while O.decode_point(y.to_bytes(32, "little")) is None:
+        y += 1
+    P = O.decode_point(y.to_bytes(32, "little"))
+    T = O.scalar_mult(O.Q, P)
+    assert not O.is_identity(T)          # this P has a torsion component
+    assert O.is_identity(O.mul_by_cofactor(T))
+    # the point (0, -1) has order 2
+    T2 = O.decode_point((O.P - 1).to_bytes(32, "little"))
+    assert not O.is_identity(T2) and O.is_identity(O.point_add(T2, T2))
+
+
+def test_scalar_reduce_matches_libsodium():
+    for i in range(10):
+        b = synth.random_bytes(11, f"red{i}", 64).tobytes()
+        assert O.scalar_to_bytes(int.from_bytes(b, "little")) == nb.crypto_core_ed25519_scalar_reduce(b)
+
+
+def test_msm_matches_libsodium():
+    ks = [int.from_bytes(synth.random_bytes(3, f"m{i}", 16).tobytes(), "little") for i in range(5)]
+    pts = [O.encode_point(O.scalar_mult(1 + 17 * i, O.G)) for i in range(5)]
+    acc = None
+    for k, p in zip(ks, pts):
+        term = nb.crypto_scalarmult_ed25519_noclamp(O.scalar_to_bytes(k), p)
+        acc = term if acc is None else nb.crypto_core_ed25519_add(acc, term)
+    assert O.msm(ks, pts) == acc
+
+
+# ---------------------------------------------------------------- seed tree (Sec. 4.1)
+
+def _pos(ds):
+    return [f"{n.d}:{n.i}" for n in ds]
+
+
+def test_worked_example_sso_sret():
+    ex = {l[0]: l[1:] for l in golden_lines("seed_tree_example.txt")}
+    D_ = int(ex["D"][0])
+    root = bytes(range(16))
+    ds5 = O.ds_after(root, D_, 5)
+    assert _pos(ds5) == ex["ds5"]
+    ds6, x06 = O.SSO(ds5, root, D_, 6)
+    assert _pos(ds6) == ex["ds6"]
+    assert x06 == O.tree_node(root, D_, 0, 6)
+    # SRet(ds_6, 3): pops x_0[6] and x_1[2], then walks down from x_2[0]
+    _, target, _, via = ex["sret"][0], int(ex["sret"][1]), ex["sret"][2], ex["sret"][3]
+    d, i = map(int, via.split(":"))
+    stack = list(ds6)
+    while not (stack[-1].i << stack[-1].d) <= target < ((stack[-1].i + 1) << stack[-1].d):
+        stack.pop()
+    assert (stack[-1].d, stack[-1].i) == (d, i)
+    assert O.SRet(ds6, target) == O.tree_node(root, D_, 0, target)
+
+
+@pytest.mark.parametrize("D_", [3, 4, 6])
+def test_sc_equals_recursive_definition(D_):
+    root = synth.random_bytes(5, "root", 16).tobytes()
+    for d in range(D_ + 1):
+        for i in range(1 << (D_ - d)):
+            node = O.tree_node(root, D_, d, i)
+            assert O.SC(root, D_, 0, d, i) == node
+            if d > 0:   # children: even -> PRF_0, odd -> PRF_1 (Eq. 1)
+                assert O.tree_node(root, D_, d - 1, 2 * i) == O.prf(0, node)
+                assert O.tree_node(root, D_, d - 1, 2 * i + 1) == O.prf(1, node)
+
+
+@pytest.mark.parametrize("D_", [3, 4, 5])
+def test_sso_sret_all_epochs(D_):
+    root = synth.random_bytes(6, "root", 16).tobytes()
+    leaves = [O.tree_node(root, D_, 0, i) for i in range(1 << D_)]
+    ds = []
+    for i in range(1 << D_):
+        ds, x0 = O.SSO(ds, root, D_, i)
+        assert x0 == leaves[i]
+        # closed form: ds_i holds one node per set bit of i+1, largest subtree first
+        bits = [b for b in range(D_, -1, -1) if (i + 1) >> b & 1]
+        assert [n.d for n in ds] == bits
+        for ip in range(i + 1):
+            assert O.SRet(ds, ip) == leaves[ip]
+        if i + 1 < (1 << D_):
+            with pytest.raises(ValueError):
+                O.SRet(ds, i + 1)
+    assert O.SRet(O.ds_root(root, D_), (1 << D_) - 1) == leaves[-1]
+
+
+def test_ds_serialize_layout():
+    ds = [O.Node(2, 0, bytes(16)), O.Node(0, 6, bytes(range(16)))]
+    b = O.ds_serialize(ds)
+    assert len(b) == 48 and b[:8] == struct.pack("<II", 2, 0) and b[32:48] == bytes(range(16))
+
+
+# ---------------------------------------------------------------- signatures
+
+def _c_instance(seed, D_=2, n2=8, lmin=16, lmax=40):
+    km = synth.key_material(seed)
+    sk, Y, epoch_R = O.kg_c(km.y, km.r, km.root, D_, n2)
+    n1 = 1 << D_
+    msgs = synth.messages(seed, n1 * n2, lmin, lmax).as_list()
+    per_epoch = [msgs[i * n2:(i + 1) * n2] for i in range(n1)]
+    sigs = [O.sig_c(sk, i, per_epoch[i]) for i in range(n1)]
+    return km, sk, Y, epoch_R, per_epoch, sigs
+
+
+def test_c_extraction_identity_and_accept():
+    km, sk, Y, epoch_R, per_epoch, sigs = _c_instance(21)
+    y = int.from_bytes(km.y, "little")
+    for i, (mi, si) in enumerate(zip(per_epoch, sigs)):
+        r_i = sum(O.nonce_c(km.r, i, j) for j in range(sk.n2)) % O.Q
+        x0 = O.tree_node(km.root, sk.D, 0, i)
+        e_i = sum(O.hash_to_scalar(m, O.entry_seed(x0, j)) for j, m in enumerate(mi)) % O.Q
+        # Appendix A: r~_i = s~_i + e~_i y (mod q); and R~_i = r~_i G via libsodium
+        assert (int.from_bytes(si, "little") + e_i * y) % O.Q == r_i
+        assert nb.crypto_scalarmult_ed25519_base_noclamp(O.scalar_to_bytes(r_i)) == epoch_R[i]
+    assert nb.crypto_scalarmult_ed25519_base_noclamp(km.y) == Y
+    ds = O.ds_after(km.root, sk.D, len(sigs) - 1)
+    s_all = O.agg_scalars(sigs)
+    epochs = list(range(len(sigs)))
+    assert O.aver_c(Y, epochs, per_epoch, sk.n2, s_all, epoch_R, ds)
+    assert O.aver_c(Y, epochs, per_epoch, sk.n2, s_all, O.agg_points(epoch_R), ds)
+    # a subset of epochs with its own aggregate
+    sub = [1, 3]
+    assert O.aver_c(Y, sub, [per_epoch[i] for i in sub], sk.n2, O.agg_scalars([sigs[i] for i in sub]),
+                    [epoch_R[i] for i in sub], ds)
+    # wrong epoch size is the paper's bottom
+    with pytest.raises(ValueError):
+        O.aver_c(Y, epochs, [mi[:-1] for mi in per_epoch], sk.n2, s_all, epoch_R, ds)
+
+
+def test_c_rejects_tamper_and_wrong_key():
+    km, sk, Y, epoch_R, per_epoch, sigs = _c_instance(22)
+    ds = O.ds_root(km.root, sk.D)
+    s_all = O.agg_scalars(sigs)
+    epochs = list(range(len(sigs)))
+    bad = [list(mi) for mi in per_epoch]
+    bad[2][5] = bytes([bad[2][5][0] ^ 1]) + bad[2][5][1:]
+    assert not O.aver_c(Y, epochs, bad, sk.n2, s_all, epoch_R, ds)
+    Y2 = O.encode_point(O.scalar_mult(5, O.G))
+    assert not O.aver_c(Y2, epochs, per_epoch, sk.n2, s_all, epoch_R, ds)
+    s_bad = O.scalar_to_bytes(int.from_bytes(s_all, "little") + 1)
+    assert not O.aver_c(Y, epochs, per_epoch, sk.n2, s_bad, epoch_R, ds)
+
+
+def _f_instance(seed, n, D_=3, n2=4, lmin=0, lmax=48, v=32, k=4):
+    km = synth.key_material(seed, v=v)
+    sk, Y = O.kg_f(km.y, km.root, D_, n2, km.bpv_r.tobytes())
+    msgs = synth.messages(seed, n, lmin, lmax).as_list()
+    subsets = synth.bpv_subsets(seed, n, v=v, k=k)
+    sig = [O.sig_f(sk, t, msgs[t], subsets[t]) for t in range(n)]
+    return km, sk, Y, msgs, [s for s, _, _ in sig], [R for _, R, _ in sig], [x for _, _, x in sig], subsets
+
+
+def test_f_signatures_closed_form_and_accept():
+    km, sk, Y, msgs, s, R, x, subsets = _f_instance(31, 12)
+    y = int.from_bytes(km.y, "little")
+    ds = O.ds_root(km.root, sk.D)
+    for t in range(len(msgs)):
+        e = O.entry_scalar(ds, sk.n2, t, msgs[t])
+        assert x[t] == O.entry_seed(O.tree_node(km.root, sk.D, 0, t // sk.n2), t % sk.n2)
+        # R_t = (s_t + e_t y) G, computed independently by libsodium
+        r_t = (int.from_bytes(s[t], "little") + e * y) % O.Q
+        assert nb.crypto_scalarmult_ed25519_base_noclamp(O.scalar_to_bytes(r_t)) == R[t]
+        # and r_t is the BPV subset sum of the table scalars
+        assert r_t == sum(int.from_bytes(km.bpv_r[32 * kk:32 * kk + 32].tobytes(), "little")
+                          for kk in subsets[t]) % O.Q
+    assert O.aver_f(Y, msgs, 0, sk.n2, s, R, ds)
+    inv, cs, cR = O.distill_f(Y, msgs, 0, sk.n2, s, R, ds)
+    assert inv == [] and cs == O.agg_scalars(s) and cR == O.agg_points(R)
+
+
+def test_f_subrange_with_first_index():
+    km, sk, Y, msgs, s, R, x, _ = _f_instance(32, 16)
+    ds = O.ds_after(km.root, sk.D, 3)      # epochs 0..3 disclosed = entries 0..15
+    assert O.aver_f(Y, msgs[5:13], 5, sk.n2, s[5:13], R[5:13], ds)
+    assert not O.aver_f(Y, msgs[5:13], 6, sk.n2, s[5:13], R[5:13], ds)
+
+
+def test_f_bruteforce_single_byte_tamper():
+    """Every single-byte flip of every entry of a 3-entry batch (2-byte messages, all 255
+    masks) is rejected by AVer and localised exactly by Distill."""
+    km, sk, Y, msgs, s, R, _, _ = _f_instance(33, 3, lmin=2, lmax=2)
+    ds = O.ds_root(km.root, sk.D)
+    Yp = O.decode_point(Y)
+    base_e = [O.entry_scalar(ds, sk.n2, t, msgs[t]) for t in range(3)]
+    for t in range(3):
+        for pos in range(2):
+            for mask in range(1, 256):
+                mt = bytearray(msgs[t])
+                mt[pos] ^= mask
+                e = O.entry_scalar(ds, sk.n2, t, bytes(mt))
+                assert e != base_e[t]
+                assert not O.verify_entry_f(Yp, e, s[t], R[t])
+    # full AVer / Distill on a sample of the flips
+    for t, pos, mask in [(0, 0, 1), (1, 1, 0x80), (2, 0, 0xFF), (2, 1, 0x5A)]:
+        bad = list(msgs)
+        mt = bytearray(bad[t]); mt[pos] ^= mask; bad[t] = bytes(mt)
+        assert not O.aver_f(Y, bad, 0, sk.n2, s, R, ds)
+        inv, _, _ = O.distill_f(Y, bad, 0, sk.n2, s, R, ds)
+        assert inv == [t]
+
+
+def test_f_distill_random_patterns():
+    km, sk, Y, msgs, s, R, _, _ = _f_instance(34, 12, lmin=4, lmax=12)
+    ds = O.ds_root(km.root, sk.D)
+    for trial in range(6):
+        pattern = [t for t in range(12) if (synth.words(34, f"pat{trial}", 12)[t] >> 62) == 0]
+        bad = list(msgs)
+        for t in pattern:
+            mt = bytearray(bad[t]); mt[0] ^= 1; bad[t] = bytes(mt)
+        inv, cs, cR = O.distill_f(Y, bad, 0, sk.n2, s, R, ds)
+        assert inv == pattern
+        keep = [t for t in range(12) if t not in pattern]
+        assert cs == O.agg_scalars([s[t] for t in keep])
+        assert O.aver_f(Y, bad, 0, sk.n2, s, R, ds) == (not pattern)
+
+
+def test_s_shift_fools_unit_aggregate_but_not_distill():
+    """Moving delta from s_a to s_b keeps every unit aggregate containing both entries
+    valid, while both entries fail their own check: the aggregate (AVer) and per-entry
+    (Distill) definitions differ exactly here."""
+    km, sk, Y, msgs, s, R, _, _ = _f_instance(35, 8)
+    ds = O.ds_root(km.root, sk.D)
+    delta = 12345
+    s2 = list(s)
+    s2[2] = O.scalar_to_bytes(int.from_bytes(s[2], "little") + delta)
+    s2[5] = O.scalar_to_bytes(int.from_bytes(s[5], "little") - delta)
+    assert O.aver_f(Y, msgs, 0, sk.n2, s2, R, ds)
+    inv, _, _ = O.distill_f(Y, msgs, 0, sk.n2, s2, R, ds)
+    assert inv == [2, 5]
+
+
+def test_malformed_entries_are_invalid():
+    km, sk, Y, msgs, s, R, _, _ = _f_instance(36, 6)
+    ds = O.ds_root(km.root, sk.D)
+    s2, R2 = list(s), list(R)
+    s2[1] = (int.from_bytes(s[1], "little") + O.Q).to_bytes(32, "little")    # s >= q
+    y = 2
+    while O.decode_point(y.to_bytes(32, "little")) is not None:
+        y += 1
+    R2[4] = y.to_bytes(32, "little")                                          # not on the curve
+    assert not O.aver_f(Y, msgs, 0, sk.n2, s2, R, ds)
+    assert not O.aver_f(Y, msgs, 0, sk.n2, s, R2, ds)
+    inv, _, _ = O.distill_f(Y, msgs, 0, sk.n2, s2, R2, ds)
+    assert inv == [1, 4]
+
+
+def test_cofactor_matters_for_torsion():
+    """R_t + T8 (T8 in the 8-torsion) passes the cofactored check; without the cofactor
+    it would fail.  Pins the [8] in the verification equation."""
+    km, sk, Y, msgs, s, R, _, _ = _f_instance(37, 1)
+    ds = O.ds_root(km.root, sk.D)
+    T2 = O.decode_point((O.P - 1).to_bytes(32, "little"))     # order 2
+    Rt = O.point_add(O.decode_point(R[0]), T2)
+    R2 = [O.encode_point(Rt)]
+    e = O.entry_scalar(ds, sk.n2, 0, msgs[0])
+    Yp = O.decode_point(Y)
+    assert O.verify_entry_f(Yp, e, s[0], R2[0])
+    diff = O.point_sub(O.point_sub(Rt, O.scalar_mult(e, Yp)), O.scalar_mult(int.from_bytes(s[0], "little"), O.G))
+    assert not O.is_identity(diff)
