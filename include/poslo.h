@@ -1,0 +1,182 @@
+/*
+ * libposlo — GB300 (sm_103a) batch verification of POSLO signed logs.
+ *
+ * C ABI over the cold-storage verification path of POSLO (Nouma and Yavuz, "Lightweight and
+ * High-Throughput Secure Logging for Internet of Things and Cold Cloud Continuum",
+ * arXiv 2506.08781).  Section, figure and equation numbers below refer to that paper.
+ *
+ * Instantiation: "POSLO" of Sec. 7.2 (Table 2): SHA-256 for both PRF and H; the group is the
+ * prime-order subgroup of edwards25519 (the paper names FourQ with |q| = 256, which is not
+ * self-consistent; edwards25519 is the reading used throughout).
+ *
+ * Encodings (all little-endian):
+ *   scalar  32 bytes, canonical (< q = 2^252 + 27742317777372353535851937790883648493);
+ *   point   32 bytes, edwards25519 compressed encoding (y with the parity of x in bit 255);
+ *   seed    16 bytes (kappa = 128);
+ *   ds node 24 bytes: le32 depth d, le32 index i, 16-byte seed x_d[i]; a disclosed-seed stack
+ *           (ds, Sec. 4.1) is an array of nodes with the bottom of the stack first.
+ *   messages: one byte buffer plus n+1 uint64 offsets; entry t is msgs[offs[t] .. offs[t+1]).
+ *
+ * Derivations (Sec. 4.1 and Fig. 3a, with the readings of the design notes):
+ *   PRF_b(z)      = SHA-256(z || byte b)[0..16)            seed-tree children (Eq. 1)
+ *   x_i^j         = SHA-256(x_0[i] || le32(j) || 0x00)[0..16)  one-time seed, j = t mod n2
+ *   e_t           = SHA-256(m_t || x_t) as a little-endian integer, mod q
+ *   verification  [8](R - e Y - s G) = O  (cofactored)
+ *
+ * Ownership and errors.  The caller owns every buffer it passes.  Unless a call says
+ * otherwise, pointers are host pointers; batch pointers marked "device-capable" may be
+ * device pointers when poslo_batch.on_device = 1 (they must then stay valid and unmodified
+ * until the call returns).  Every call is synchronous: it returns when its outputs are in
+ * the caller's buffers.  Calls on one context must not overlap (they share its streams and
+ * workspace); different contexts are independent.  A call returns POSLO_OK or a negative
+ * poslo_status; poslo_last_error() then describes the failure.  "Signature invalid" is not
+ * an error: it is an output bit or index.
+ */
+#ifndef POSLO_H_
+#define POSLO_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define POSLO_ABI_VERSION 1
+
+typedef enum {
+  POSLO_OK = 0,
+  POSLO_EINVAL = -1,    /* malformed argument: sizes, bad public key, seed not disclosed (SRet bottom) */
+  POSLO_ENOMEM = -2,    /* device memory could not be allocated or the context budget is exceeded */
+  POSLO_EDEVICE = -3,   /* CUDA error (no device, launch failure) */
+  POSLO_ETIMEOUT = -4,  /* a bounded device-side wait expired */
+  POSLO_EBUFSMALL = -5, /* an output buffer is too small; the needed count is still reported */
+  POSLO_EBUSY = -6,     /* serving: admission refused by the memory budget */
+  POSLO_ENOTFOUND = -7  /* serving: unknown key id or ticket */
+} poslo_status;
+
+enum { POSLO_VARIANT_C = 0, POSLO_VARIANT_F = 1 };
+enum { POSLO_AGG_UNIT = 0, POSLO_AGG_WEIGHTED = 1 };
+
+typedef struct poslo_ctx poslo_ctx;
+
+typedef struct {
+  int device;                 /* CUDA device ordinal */
+  uint32_t msm_window;        /* Pippenger window in bits, 8..16; 0 = autotune */
+  uint64_t mem_budget;        /* bytes of device memory the context may hold; 0 = no limit */
+  uint8_t verifier_seed[32];  /* secret randomness of the verifier for the weights z_t */
+} poslo_params;
+
+/*
+ * One batch of signed log entries of a single signer.
+ *   POSLO-F (Fig. 4): entry t (global index first_index + t) carries (s_t, R_t); s and R
+ *     hold n scalars and n points.  R_count must equal n.
+ *   POSLO-C (Fig. 3a): the batch is whole epochs: first_index and n are multiples of n2.
+ *     s is the aggregate s~ (one scalar); R is either the aggregate R~ (R_count = 1) or the
+ *     per-epoch commitments R~_i of pk for the batch's epochs (R_count = n / n2).
+ * msgs, offs, s and R are device-capable; Y and ds are always host memory.
+ */
+typedef struct {
+  uint32_t variant;      /* POSLO_VARIANT_C or POSLO_VARIANT_F */
+  uint32_t n2;           /* entries per epoch, >= 1 */
+  const uint8_t* Y;      /* 32-byte public key */
+  const uint8_t* msgs;   /* message bytes */
+  const uint64_t* offs;  /* n+1 non-decreasing offsets into msgs */
+  uint64_t n;            /* number of entries */
+  uint64_t first_index;  /* global index of entry 0 */
+  const uint8_t* s;      /* F: n*32; C: 32 */
+  const uint8_t* R;      /* F: n*32; C: R_count*32 */
+  uint64_t R_count;
+  const uint8_t* ds;     /* disclosed seeds (24 bytes per node), or the root as one node at depth D */
+  uint32_t ds_nodes;
+  uint32_t on_device;    /* 1: msgs, offs, s, R are device pointers */
+} poslo_batch;
+
+/* Context: device memory, streams, the fixed-base table of G and the Pippenger settings.
+ * Returns POSLO_EDEVICE when the device is missing or not an sm_103 part. */
+int poslo_create(const poslo_params* params, poslo_ctx** out);
+void poslo_destroy(poslo_ctx* ctx);
+const char* poslo_last_error(const poslo_ctx* ctx);
+/* The CUDA stream (cudaStream_t) the context launches its hot kernels on. */
+void* poslo_stream(poslo_ctx* ctx);
+
+/* ---- test-data side (signer): deterministic from the caller's secret bytes ---------- */
+
+/* POSLO-C.Kg (Fig. 3a) for n1 = 2^D epochs: Y = [y]G and R~_i = [sum_j r_i^j]G with
+ * r_i^j = SHA-256(r || le32(i) || le32(j) || 0x00) mod q.  y: 32-byte scalar, 0 < y < q.
+ * epoch_R_out: n1*32 bytes. */
+int poslo_keygen_c(poslo_ctx* ctx, const uint8_t y[32], const uint8_t r[32], uint32_t D, uint32_t n2,
+                   uint8_t Y_out[32], uint8_t* epoch_R_out);
+
+/* POSLO-F.Kg (Fig. 4) with the BPV table of Definition 3: Y = [y]G, R_k = [r_k]G for the
+ * v table scalars bpv_r (v*32 bytes, canonical).  bpv_R_out: v*32 bytes. */
+int poslo_keygen_f(poslo_ctx* ctx, const uint8_t y[32], const uint8_t* bpv_r, uint32_t v, uint8_t Y_out[32],
+                   uint8_t* bpv_R_out);
+
+/* POSLO-C.Sig (Fig. 3a) for n_epochs whole epochs starting at first_epoch: msgs/offs hold
+ * n_epochs*n2 entries; s_out receives one aggregate scalar s~_i per epoch (n_epochs*32). */
+int poslo_sign_c(poslo_ctx* ctx, const uint8_t y[32], const uint8_t r[32], const uint8_t root[16], uint32_t D,
+                 uint32_t n2, const uint8_t* msgs, const uint64_t* offs, uint64_t first_epoch,
+                 uint64_t n_epochs, uint8_t* s_out);
+
+/* POSLO-F.Sig (Fig. 4) for entries first_index .. first_index+n-1.  subsets: n*k uint16
+ * indices into the BPV table (the online step's random choice, supplied by the caller);
+ * outputs s_t (n*32), R_t (n*32, compressed) and optionally x_t (n*16, may be NULL). */
+int poslo_sign_f(poslo_ctx* ctx, const uint8_t y[32], const uint8_t root[16], uint32_t D, uint32_t n2,
+                 const uint8_t* bpv_r, const uint8_t* bpv_R, uint32_t v, uint32_t k, const uint16_t* subsets,
+                 const uint8_t* msgs, const uint64_t* offs, uint64_t n, uint64_t first_index, uint8_t* s_out,
+                 uint8_t* R_out, uint8_t* x_out);
+
+/* SSO (Fig. 2a) run for epochs 0..i from an empty stack: writes ds_i (24 bytes per node,
+ * bottom first) to ds_out (capacity cap_nodes) and its node count to *nodes. */
+int poslo_disclose(poslo_ctx* ctx, const uint8_t root[16], uint32_t D, uint64_t i, uint8_t* ds_out,
+                   uint32_t cap_nodes, uint32_t* nodes);
+
+/* ---- verifier side (device) ----------------------------------------------------------- */
+
+/* POSLO.AVer / PAVer (Fig. 3a, Fig. 4, Fig. 6): one accept bit for the whole batch.
+ *   agg_mode = POSLO_AGG_UNIT: the paper's equation with unit coefficients,
+ *     [8](sum R - (sum e) Y - (sum s) G) = O, plus "every s_t canonical, every R_t decodable".
+ *   agg_mode = POSLO_AGG_WEIGHTED (POSLO-F only): each entry weighted by a secret 128-bit z_t,
+ *     accepts iff every entry passes its own check, except with probability <= 2^-128.
+ * Errors: EINVAL for malformed sizes, an undecodable Y, or a seed the ds does not disclose. */
+int poslo_aver(poslo_ctx* ctx, const poslo_batch* batch, uint32_t agg_mode, uint8_t* accept);
+
+/* POSLO-F Distill / SeBVer at entry granularity (Fig. 3b semantics, Sec. 4.3): the sorted
+ * global indices of every entry that fails its own check (malformed s_t or R_t included),
+ * and ccd^v = (sum of valid s_t, sum of valid R_t).  invalid_idx has room for cap indices;
+ * *n_invalid is the full count (EBUFSMALL if it exceeds cap). */
+int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_idx, uint64_t cap,
+                  uint64_t* n_invalid, uint8_t ccd_s[32], uint8_t ccd_R[32]);
+
+/* ---- inspection entry points (single steps of the path, for parity tests) ---------------- */
+
+/* SRet (Fig. 2a) for epochs first_epoch .. first_epoch+n_epochs-1: x_0[i] (16 bytes each). */
+int poslo_epoch_seeds(poslo_ctx* ctx, const uint8_t* ds, uint32_t ds_nodes, uint64_t first_epoch,
+                      uint64_t n_epochs, uint8_t* x0_out);
+
+/* e_t = H(m_t || x_t) mod q for every entry of the batch (Fig. 6 Agg-eKeys, per entry);
+ * e_out: n*32 bytes, host or device memory as batch->on_device says. */
+int poslo_hash_entries(poslo_ctx* ctx, const poslo_batch* batch, uint8_t* e_out);
+
+/* sum_t [k_t]P_t for n compressed points and n 32-byte scalars (any value below 2^256 is
+ * taken as the integer it encodes).  Host or device memory per on_device.  EINVAL if a
+ * point does not decode. */
+int poslo_msm(poslo_ctx* ctx, const uint8_t* points, const uint8_t* scalars, uint64_t n, uint32_t on_device,
+              uint8_t out[32]);
+
+/* ---- profiling -------------------------------------------------------------------------- */
+
+/* When enabled, the context brackets each hot kernel with CUDA events on its own stream and
+ * accumulates the durations: poslo_kernel_time() returns total milliseconds and launch count
+ * for kernel `name` ("hash", "points", "msm", "finalize", ...); poslo_reset_kernel_times()
+ * clears them. */
+int poslo_set_profiling(poslo_ctx* ctx, int enabled);
+int poslo_kernel_time(poslo_ctx* ctx, const char* name, double* total_ms, uint64_t* launches);
+void poslo_reset_kernel_times(poslo_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POSLO_H_ */

@@ -1,0 +1,434 @@
+// Shared device code of the POSLO verification path (sm_103a): argument structs, per-entry
+// helpers and the declarations of every kernel (defined in k_verify.cu, k_check.cu,
+// k_signer.cu).
+//
+//   k_epoch_seeds   A1  x_0[i] = SRet(ds, i), hoisted once per epoch (Fig. 2a; the paper's
+//                       Agg-eKeys recomputes it in every thread, Fig. 6)
+//   k_hash          A2-A4  x_t = PRF_0(x_0[i] || j), e_t = H(m_t || x_t) mod q, and the
+//                       scalar aggregates sum e_t, sum s_t (or their weighted forms)
+//   k_points        A5  strict decoding of R_t and the unit aggregate sum R_t
+//   k_table         fixed-window tables {d 16^w P : d = 1..8, w = 0..63} for the check
+//   k_finalize      A4/A6  reduce the partial aggregates and evaluate [8](R - eY - sG) = O
+#pragma once
+#include <cstdint>
+
+#include "ge25519.cuh"
+#include "sc25519.cuh"
+#include "sha256.cuh"
+
+namespace poslo {
+
+
+constexpr int kHashThreads = 128;
+constexpr int kPointThreads = 128;
+constexpr int kTableWindows = 64;   // 4-bit windows over 256 bits
+constexpr int kTableDigits = 8;     // signed digits |d| in 1..8
+
+// Device-side error codes written to the context's status word.
+enum : uint32_t { kErrNone = 0, kErrSeed = 1, kErrKey = 2, kErrPoint = 4, kErrTimeout = 8 };
+
+struct DsNode { uint32_t d, i; uint32_t seed[4]; };   // seed as 4 big-endian words
+
+// ----------------------------------------------------------------------------------------
+// A1: SRet per epoch.
+// ----------------------------------------------------------------------------------------
+
+
+// ----------------------------------------------------------------------------------------
+// A2-A4: per-entry hashing and scalar aggregation.
+// ----------------------------------------------------------------------------------------
+struct HashArgs {
+  const uint8_t* msgs;
+  const uint64_t* offs;        // n+1
+  uint64_t base_off;           // offs[] value that corresponds to msgs[0]
+  uint64_t n;
+  uint64_t first_index;        // global index of entry 0
+  uint64_t e0;                 // epoch of seeds[0]
+  uint32_t n2;
+  uint32_t n2_log2;            // log2(n2) if n2 is a power of two, else 0xffffffff
+  const uint32_t* seeds;       // x_0 per epoch, 4 BE words each
+  uint8_t* e_out;              // optional: n*32 bytes
+  const uint8_t* s;            // optional (F): n*32 scalars to check and aggregate
+  uint32_t weighted;           // 1: aggregate z_t e_t and z_t s_t
+  uint32_t zpre[10];           // weighted: BE words of "POSLO-Z" || verifier_seed || (byte 39 = 0)
+  uint32_t* z_out;             // optional (weighted): n*4 words of z_t
+  unsigned long long* partial; // per block: 13 u64 limb sums of e, 13 of s, 1 bad count (27 u64)
+};
+
+constexpr int kPartialWords = 27;
+
+// Big-endian word at byte offset o (a multiple of 4) of the padded SHA-256 input
+// m || x || 0x80 || 0.. || bitlen, for the blocks that are not wholly message bytes.
+struct EntryStream {
+  const uint32_t* base;   // 4-byte aligned pointer at or before the first message byte
+  uint32_t sel;           // PRMT selector realigning two loaded words to the message
+  uint32_t sh_nz;         // 1 if the message is not 4-byte aligned
+  uint32_t L;             // message length in bytes
+  int32_t kmax;           // last loadable word index (the word holding the last byte)
+  uint32_t a;             // L rounded down to a multiple of 4
+  uint32_t S[5];          // x || 0x80 shifted by L mod 4 bytes, as the words at a, a+4, ...
+};
+
+__device__ __forceinline__ uint32_t load_msg_word(const EntryStream& es, uint32_t k) {
+  const uint32_t lo = __ldg(es.base + k);
+  const uint32_t hi = __ldg(es.base + k + es.sh_nz);
+  return __byte_perm(lo, hi, es.sel);
+}
+
+__device__ __forceinline__ uint32_t stream_word(const EntryStream& es, uint32_t o) {
+  uint32_t mw = 0;
+  if (es.L > 0) {
+    const int32_t k = (int32_t)(o >> 2);
+    const uint32_t k0 = (uint32_t)min(k, es.kmax);
+    const uint32_t k1 = (uint32_t)min(k + (int32_t)es.sh_nz, es.kmax);
+    mw = __byte_perm(__ldg(es.base + k0), __ldg(es.base + k1), es.sel);
+    // keep the leading min(4, max(0, L - o)) bytes
+    const int32_t keep = min(4, max(0, (int32_t)es.L - (int32_t)o));
+    mw &= __funnelshift_lc(0u, 0xffffffffu, 8u * (uint32_t)(4 - keep));
+  }
+  const int32_t kk = ((int32_t)o - (int32_t)es.a) >> 2;
+  uint32_t tw = 0;
+  tw = kk == 0 ? es.S[0] : tw;
+  tw = kk == 1 ? es.S[1] : tw;
+  tw = kk == 2 ? es.S[2] : tw;
+  tw = kk == 3 ? es.S[3] : tw;
+  tw = kk == 4 ? es.S[4] : tw;
+  return mw | tw;
+}
+
+// SHA-256(m || x) for one entry; returns the 8 state words.
+__device__ __forceinline__ void hash_entry(const uint8_t* m, uint32_t L, const uint32_t x[4], uint32_t st[8]) {
+  EntryStream es;
+  const uintptr_t p = reinterpret_cast<uintptr_t>(m);
+  const uint32_t sh = (uint32_t)(p & 3u);
+  es.base = reinterpret_cast<const uint32_t*>(p - sh);
+  es.sel = (sh + 3) | ((sh + 2) << 4) | ((sh + 1) << 8) | (sh << 12);
+  es.sh_nz = sh != 0;
+  es.L = L;
+  es.kmax = L > 0 ? (int32_t)((L + sh - 1) >> 2) : 0;
+  const uint32_t r = L & 3u;
+  es.a = L - r;
+  const uint32_t sr = 8u * r;
+  es.S[0] = __funnelshift_r(x[0], 0u, sr);
+  es.S[1] = __funnelshift_r(x[1], x[0], sr);
+  es.S[2] = __funnelshift_r(x[2], x[1], sr);
+  es.S[3] = __funnelshift_r(x[3], x[2], sr);
+  es.S[4] = __funnelshift_r(0x80000000u, x[3], sr);
+  const uint32_t total = L + 16;
+  const uint32_t nb = (total + 9 + 63) >> 6;
+  sha256_init(st);
+  for (uint32_t b = 0; b < nb; ++b) {
+    uint32_t w[16];
+    const uint32_t o0 = b << 6;
+    if (o0 + 64 <= L) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) w[i] = load_msg_word(es, (o0 >> 2) + i);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) w[i] = stream_word(es, o0 + 4 * i);
+      if (b == nb - 1) {
+        w[14] |= total >> 29;
+        w[15] |= total << 3;
+      }
+    }
+    sha256_compress(st, w);
+  }
+}
+
+// z_t = SHA-256("POSLO-Z" || verifier_seed || le64(t))[0..16) as a 128-bit little-endian integer.
+__device__ __forceinline__ void weight_of(const uint32_t zpre[10], uint64_t t, uint32_t z[4]) {
+  uint32_t w[16];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) w[i] = zpre[i];
+  const uint32_t lo = (uint32_t)t, hi = (uint32_t)(t >> 32);
+  w[9] = zpre[9] | (lo & 0xffu);
+  w[10] = ((lo >> 8) & 0xffu) << 24 | ((lo >> 16) & 0xffu) << 16 | ((lo >> 24) & 0xffu) << 8 | (hi & 0xffu);
+  w[11] = ((hi >> 8) & 0xffu) << 24 | ((hi >> 16) & 0xffu) << 16 | ((hi >> 24) & 0xffu) << 8 | 0x80u;
+  w[12] = 0; w[13] = 0; w[14] = 0; w[15] = 47 * 8;
+  uint32_t st[8];
+  sha256_init(st);
+  sha256_compress(st, w);
+  z[0] = bswap32(st[0]); z[1] = bswap32(st[1]); z[2] = bswap32(st[2]); z[3] = bswap32(st[3]);
+}
+
+__device__ __forceinline__ void warp_sum_u64(unsigned long long& v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+}
+
+
+
+// ----------------------------------------------------------------------------------------
+// A5 (unit): decode R_t, flag malformed ones, sum the rest.
+// ----------------------------------------------------------------------------------------
+struct PointArgs {
+  const uint8_t* R;       // count*32
+  uint64_t count;
+  uint32_t* partial;      // per block: ge (32 words) + bad count (1 word), 33 words
+  uint32_t* affine_out;   // optional: count*16 words (x, y) of decoded points
+  uint8_t* bad_out;       // optional: count bytes, 1 = undecodable
+  const uint8_t* skip;    // optional: count bytes, 1 = leave the point out of the sum
+};
+
+constexpr int kPointPartialWords = 33;
+
+__device__ __forceinline__ void ge_store(uint32_t* dst, const ge& p) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    dst[i] = p.X.v[i]; dst[8 + i] = p.Y.v[i]; dst[16 + i] = p.Z.v[i]; dst[24 + i] = p.T.v[i];
+  }
+}
+
+__device__ __forceinline__ ge ge_load(const uint32_t* src) {
+  ge p;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    p.X.v[i] = src[i]; p.Y.v[i] = src[8 + i]; p.Z.v[i] = src[16 + i]; p.T.v[i] = src[24 + i];
+  }
+  return p;
+}
+
+
+
+// ----------------------------------------------------------------------------------------
+// Fixed-window tables: table[w][d-1] = d * 16^w * P for w = 0..63, d = 1..8.  Thread w
+// reaches 16^w P by 4w doublings, so the whole table costs the latency of 252 doublings.
+// ----------------------------------------------------------------------------------------
+
+
+// Recode k (< 2^253) into 64 signed digits in [-8, 8).
+__device__ __forceinline__ void recode4(const uint32_t k[8], int8_t dig[64]) {
+  int carry = 0;
+  for (int w = 0; w < 64; ++w) dig[w] = (int8_t)sc_digit4(k, w, carry);
+}
+
+__device__ __forceinline__ ge table_pick(const uint32_t* table, int w, int d) {
+  if (d == 0) return ge_identity();
+  const ge p = ge_load(table + ((size_t)w * kTableDigits + (abs(d) - 1)) * 32);
+  return d < 0 ? ge_neg(p) : p;
+}
+
+// ----------------------------------------------------------------------------------------
+// A4 + A6: combine the partial aggregates and evaluate the cofactored check.
+// ----------------------------------------------------------------------------------------
+struct FinalArgs {
+  const unsigned long long* hash_partial;   // nhash blocks * kPartialWords
+  uint32_t nhash;
+  const uint32_t* point_partial;            // npoint blocks * kPointPartialWords (unit R sum)
+  uint32_t npoint;
+  const uint32_t* R_given;                  // optional: an extended point (32 words) used as R
+  const uint8_t* s_given;                   // optional: aggregate s (C), 32 bytes
+  const uint32_t* tableY;
+  const uint32_t* tableG;
+  uint8_t* accept;                          // 1 byte
+  uint32_t* out_words;                      // optional: e~ (8), s~ (8), R (32) for inspection
+  uint32_t* status;
+};
+
+constexpr int kFinalThreads = 256;
+
+__device__ __forceinline__ sc limb_sums_to_scalar(const unsigned long long* sums13) {
+  // value = sum_k sums13[k] * 2^(32k); propagate carries into 16 limbs and reduce mod q
+  uint32_t x[16];
+  unsigned long long carry = 0;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const unsigned long long v = (k < 13 ? sums13[k] : 0ull) + carry;
+    x[k] = (uint32_t)v;
+    carry = v >> 32;
+  }
+  return sc_reduce512(x);
+}
+
+
+
+
+// ---- per-entry checks and reference MSM (see k_check.cu) ----
+// Per-entry verification and a reference multi-scalar multiplication.
+//
+//   k_entry_check  the single-entry POSLO-F check of Fig. 4 (|m| = 1) for every entry:
+//                  s_t canonical, R_t decodable, [8](R_t - e_t Y - s_t G) = O, with
+//                  [e]Y + [s]G taken from the two fixed-window tables (128 additions)
+//   k_msm_direct   sum_t [k_t]P_t with one double-and-add per term, for short MSMs and as
+//                  the definition the bucket method is checked against
+
+
+__device__ __forceinline__ ge double_scalar_tables(const uint32_t e[8], const uint32_t s[8],
+                                                   const uint32_t* tableY, const uint32_t* tableG) {
+  int8_t de[64], ds_[64];
+  recode4(e, de);
+  recode4(s, ds_);
+  ge acc = ge_identity();
+  for (int w = 0; w < 64; ++w) {
+    acc = ge_add(acc, table_pick(tableY, w, de[w]));
+    acc = ge_add(acc, table_pick(tableG, w, ds_[w]));
+  }
+  return acc;
+}
+
+struct CheckArgs {
+  const uint8_t* e;          // n*32 (from k_hash)
+  const uint8_t* s;          // n*32
+  const uint8_t* R;          // n*32 compressed
+  uint64_t n;
+  const uint32_t* tableY;
+  const uint32_t* tableG;
+  uint8_t* invalid;          // n bytes: 1 = entry fails its own check
+};
+
+
+
+struct MsmArgs {
+  const uint8_t* points;     // n*32 compressed (or NULL when affine is given)
+  const uint32_t* affine;    // n*16 words (x, y) already decoded (or NULL)
+  const uint8_t* scalars;    // n*scalar_bytes little-endian
+  uint32_t scalar_bytes;     // 16 or 32
+  uint64_t n;
+  const uint8_t* skip;       // optional: n bytes, 1 = leave the term out
+  uint32_t* partial;         // per block: kPointPartialWords words
+};
+
+
+
+// Masked scalar sum: per block, 13 u64 limb sums of the s_t whose skip byte is 0.
+
+
+// Reduce scalar partials (13 u64 limb sums per block) to one canonical scalar.
+
+
+// Ordered compaction of flagged entries: one block walks the flags in chunks of its size,
+// each chunk scanned with warp ballots, and writes first_index + t for every flag in
+// ascending order (up to cap; the total count goes to *count).
+constexpr int kCompactThreads = 1024;
+
+
+// Sum point partials (one block) and encode the result.
+
+
+
+// ---- signer helpers (see k_signer.cu) ----
+// Signer-side kernels: key generation and signing of synthetic logs (POSLO-C.Kg/Sig of
+// Fig. 3a, POSLO-F.Kg/Sig of Fig. 4 with the BPV generator of Definition 3).  They produce
+// workloads for the verifier; they are not on the verification path.
+
+
+__device__ __forceinline__ void load_sc_bytes(const uint8_t* b, uint32_t v[8]) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    v[k] = b[4 * k] | (b[4 * k + 1] << 8) | (b[4 * k + 2] << 16) | ((uint32_t)b[4 * k + 3] << 24);
+}
+
+__device__ __forceinline__ void store_words_bytes(uint8_t* b, const uint32_t v[8]) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    b[4 * k] = (uint8_t)v[k]; b[4 * k + 1] = (uint8_t)(v[k] >> 8);
+    b[4 * k + 2] = (uint8_t)(v[k] >> 16); b[4 * k + 3] = (uint8_t)(v[k] >> 24);
+  }
+}
+
+// r_i^j = SHA-256(r || le32(i) || le32(j) || 0x00) mod q: one block of 41 bytes.
+__device__ __forceinline__ sc nonce_c(const uint32_t rw[8], uint32_t i, uint32_t j) {
+  uint32_t w[16];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) w[k] = rw[k];
+  w[8] = bswap32(i);
+  w[9] = bswap32(j);
+  w[10] = 0x00800000u;   // byte 40 = 0x00, byte 41 = 0x80
+#pragma unroll
+  for (int k = 11; k < 15; ++k) w[k] = 0;
+  w[15] = 41 * 8;
+  uint32_t st[8];
+  sha256_init(st);
+  sha256_compress(st, w);
+  uint32_t d[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) d[k] = bswap32(st[k]);
+  return sc_reduce256(d);
+}
+
+// [k]G for a scalar below 2^256 via the fixed-window table of G (64 table additions).
+__device__ __forceinline__ ge base_mult_table(const uint32_t k[8], const uint32_t* tableG) {
+  int8_t dig[64];
+  recode4(k, dig);
+  ge acc = ge_identity();
+  for (int w = 0; w < 64; ++w) acc = ge_add(acc, table_pick(tableG, w, dig[w]));
+  return acc;
+}
+
+// Y = [y]G (one thread).
+
+
+// POSLO-C.Kg steps 5-7: R~_i = [sum_j r_i^j mod q]G, one thread per epoch.
+
+
+// BPV.Offline: R_k = [r_k]G, one thread per table entry.
+
+
+// Decode the BPV commitment table once into extended points.
+
+
+struct SignFArgs {
+  const uint8_t* msgs;
+  const uint64_t* offs;
+  uint64_t base_off;
+  uint64_t n;
+  uint64_t first_index;
+  uint64_t e0;
+  uint32_t n2;
+  const uint32_t* seeds;     // x_0 per epoch (BE words)
+  const uint8_t* y;          // 32 bytes
+  const uint8_t* bpv_r;      // v*32
+  const uint32_t* bpv_pts;   // v decoded points (32 words each)
+  uint32_t v, k;
+  const uint16_t* subsets;   // n*k
+  uint8_t* s_out;
+  uint8_t* R_out;
+  uint8_t* x_out;            // optional
+};
+
+// POSLO-F.Sig: (r_t, R_t) = BPV.Online, e_t = H(m_t || x_t), s_t = r_t - e_t y.
+
+
+struct SignCArgs {
+  const uint8_t* msgs;
+  const uint64_t* offs;
+  uint64_t base_off;
+  uint64_t n_epochs;
+  uint64_t first_epoch;
+  uint32_t n2;
+  const uint32_t* seeds;     // x_0 per epoch of the range (BE words)
+  const uint8_t* y;
+  const uint8_t* r;
+  uint8_t* s_out;            // n_epochs*32
+};
+
+// POSLO-C.Sig: s~_i = sum_j (r_i^j - e_i^j y) mod q, one thread per epoch.
+
+
+
+// ---- kernel declarations ----
+__global__ void k_epoch_seeds(const DsNode* __restrict__ ds, int nds, uint64_t e0, uint64_t ne,
+                              uint32_t* __restrict__ x0_out, uint32_t* __restrict__ status);
+__global__ void __launch_bounds__(kHashThreads) k_hash(const HashArgs a);
+__global__ void __launch_bounds__(kPointThreads) k_points(const PointArgs a);
+__global__ void k_table(const uint32_t* __restrict__ enc, uint32_t* __restrict__ table,
+                        uint32_t* __restrict__ status, int use_base);
+__global__ void __launch_bounds__(kFinalThreads) k_finalize(const FinalArgs a);
+__global__ void __launch_bounds__(128) k_entry_check(const CheckArgs a);
+__global__ void __launch_bounds__(kPointThreads) k_msm_direct(const MsmArgs a);
+__global__ void __launch_bounds__(kHashThreads) k_sum_scalars(const uint8_t* s, uint64_t n, const uint8_t* skip,
+                                                             unsigned long long* partial);
+__global__ void k_reduce_scalars(const unsigned long long* partial, uint32_t nparts, uint8_t* out);
+__global__ void __launch_bounds__(kCompactThreads) k_compact(const uint8_t* flags, uint64_t n, uint64_t first_index,
+                                                             uint64_t* out, uint64_t cap, uint64_t* count);
+__global__ void k_sum_encode(const uint32_t* partial, uint32_t nparts, uint32_t* point_out, uint8_t* enc_out,
+                             uint32_t* bad_out);
+__global__ void k_keygen_y(const uint8_t* y, const uint32_t* tableG, uint8_t* Y_out);
+__global__ void k_keygen_c_epochs(const uint8_t* r, uint32_t n1, uint32_t n2, const uint32_t* tableG,
+                                  uint8_t* epoch_R);
+__global__ void k_keygen_bpv(const uint8_t* bpv_r, uint32_t v, const uint32_t* tableG, uint8_t* bpv_R);
+__global__ void k_decode_table(const uint8_t* enc, uint32_t v, uint32_t* out, uint32_t* status);
+__global__ void k_sign_f(const SignFArgs a);
+__global__ void k_sign_c(const SignCArgs a);
+
+}  // namespace poslo

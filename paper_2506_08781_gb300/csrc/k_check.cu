@@ -1,0 +1,176 @@
+// Per-entry checks, the reference multi-scalar multiplication, masked sums and ordered compaction used by Distill.
+#include "common.cuh"
+
+namespace poslo {
+
+__global__ void __launch_bounds__(128) k_entry_check(const CheckArgs a) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.n; t += stride) {
+    const uint4* ep = reinterpret_cast<const uint4*>(a.e + 32 * t);
+    const uint4* sp = reinterpret_cast<const uint4*>(a.s + 32 * t);
+    const uint4* rp = reinterpret_cast<const uint4*>(a.R + 32 * t);
+    const uint4 e0 = ep[0], e1 = ep[1], s0 = __ldg(sp), s1 = __ldg(sp + 1), r0 = __ldg(rp), r1 = __ldg(rp + 1);
+    const uint32_t e[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
+    const uint32_t s[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+    const uint32_t rb[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+    ge R;
+    bool ok = ge_decode(rb, R);
+    ok &= sc_is_canonical(s);
+    if (ok) {
+      const ge d = ge_sub(R, double_scalar_tables(e, s, a.tableY, a.tableG));
+      ok = ge_is_identity(ge_mul_cofactor(d));
+    }
+    a.invalid[t] = ok ? 0 : 1;
+  }
+}
+
+__global__ void __launch_bounds__(kPointThreads) k_msm_direct(const MsmArgs a) {
+  ge acc = ge_identity();
+  uint32_t bad = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.n; t += stride) {
+    if (a.skip && a.skip[t]) continue;
+    ge P;
+    if (a.affine) {
+      const uint32_t* src = a.affine + 16 * t;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) { P.X.v[i] = src[i]; P.Y.v[i] = src[8 + i]; }
+      P.Z = fe_one();
+      P.T = fe_mul(P.X, P.Y);
+    } else {
+      const uint4* rp = reinterpret_cast<const uint4*>(a.points + 32 * t);
+      const uint4 r0 = __ldg(rp), r1 = __ldg(rp + 1);
+      const uint32_t b[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+      if (!ge_decode(b, P)) { ++bad; continue; }
+    }
+    uint32_t k[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const uint8_t* kb = a.scalars + (size_t)a.scalar_bytes * t;
+    for (uint32_t q = 0; q < a.scalar_bytes / 4; ++q)
+      k[q] = kb[4 * q] | (kb[4 * q + 1] << 8) | (kb[4 * q + 2] << 16) | ((uint32_t)kb[4 * q + 3] << 24);
+    acc = ge_add(acc, ge_scalarmult(k, P, 8 * (int)a.scalar_bytes));
+  }
+  __shared__ uint32_t sp[kPointThreads][32];
+  __shared__ uint32_t sbad[kPointThreads];
+  ge_store(sp[threadIdx.x], acc);
+  sbad[threadIdx.x] = bad;
+  __syncthreads();
+  for (int h = kPointThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+      ge_store(sp[threadIdx.x], ge_add(ge_load(sp[threadIdx.x]), ge_load(sp[threadIdx.x + h])));
+      sbad[threadIdx.x] += sbad[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 32) a.partial[(uint64_t)blockIdx.x * kPointPartialWords + threadIdx.x] = sp[0][threadIdx.x];
+  if (threadIdx.x == 0) a.partial[(uint64_t)blockIdx.x * kPointPartialWords + 32] = sbad[0];
+}
+
+__global__ void __launch_bounds__(kHashThreads) k_sum_scalars(const uint8_t* s, uint64_t n, const uint8_t* skip,
+                                                             unsigned long long* partial) {
+  acc13 acc;
+  acc_zero(acc);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
+    if (skip && skip[t]) continue;
+    const uint4* sp = reinterpret_cast<const uint4*>(s + 32 * t);
+    const uint4 s0 = __ldg(sp), s1 = __ldg(sp + 1);
+    const uint32_t v[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+    acc_add<8>(acc, v);
+  }
+  __shared__ unsigned long long red[kHashThreads / 32][13];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 13; ++k) {
+    unsigned long long v = acc.v[k];
+    warp_sum_u64(v);
+    if (lane == 0) red[warp][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 13) {
+    unsigned long long v = 0;
+    for (int w = 0; w < kHashThreads / 32; ++w) v += red[w][threadIdx.x];
+    partial[(uint64_t)blockIdx.x * 13 + threadIdx.x] = v;
+  }
+}
+
+__global__ void k_reduce_scalars(const unsigned long long* partial, uint32_t nparts, uint8_t* out) {
+  __shared__ unsigned long long sums[13];
+  if (threadIdx.x < 13) {
+    unsigned long long v = 0;
+    for (uint32_t b = 0; b < nparts; ++b) v += partial[(size_t)b * 13 + threadIdx.x];
+    sums[threadIdx.x] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const sc r = limb_sums_to_scalar(sums);
+    for (int k = 0; k < 8; ++k) {
+      out[4 * k] = (uint8_t)r.v[k]; out[4 * k + 1] = (uint8_t)(r.v[k] >> 8);
+      out[4 * k + 2] = (uint8_t)(r.v[k] >> 16); out[4 * k + 3] = (uint8_t)(r.v[k] >> 24);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kCompactThreads) k_compact(const uint8_t* flags, uint64_t n, uint64_t first_index,
+                                                             uint64_t* out, uint64_t cap, uint64_t* count) {
+  __shared__ uint32_t warp_tot[kCompactThreads / 32];
+  __shared__ uint64_t base;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  for (uint64_t c0 = 0; c0 < n; c0 += kCompactThreads) {
+    const uint64_t t = c0 + threadIdx.x;
+    const bool f = t < n && flags[t] != 0;
+    const uint32_t m = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) warp_tot[warp] = __popc(m);
+    __syncthreads();
+    uint64_t off = base;
+    for (int w = 0; w < warp; ++w) off += warp_tot[w];
+    off += __popc(m & ((1u << lane) - 1u));
+    if (f && off < cap) out[off] = first_index + t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint64_t tot = 0;
+      for (int w = 0; w < kCompactThreads / 32; ++w) tot += warp_tot[w];
+      base += tot;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *count = base;
+}
+
+__global__ void k_sum_encode(const uint32_t* partial, uint32_t nparts, uint32_t* point_out, uint8_t* enc_out,
+                             uint32_t* bad_out) {
+  __shared__ uint32_t sp[kFinalThreads][32];
+  __shared__ uint32_t sbad;
+  const int tid = threadIdx.x;
+  if (tid == 0) sbad = 0;
+  __syncthreads();
+  ge acc = ge_identity();
+  uint32_t bad = 0;
+  for (uint32_t b = tid; b < nparts; b += kFinalThreads) {
+    acc = ge_add(acc, ge_load(partial + (size_t)b * kPointPartialWords));
+    bad += partial[(size_t)b * kPointPartialWords + 32];
+  }
+  ge_store(sp[tid], acc);
+  atomicAdd(&sbad, bad);
+  __syncthreads();
+  for (int h = kFinalThreads / 2; h > 0; h >>= 1) {
+    if (tid < h) ge_store(sp[tid], ge_add(ge_load(sp[tid]), ge_load(sp[tid + h])));
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const ge r = ge_load(sp[0]);
+    if (point_out) ge_store(point_out, r);
+    if (enc_out) {
+      uint32_t w[8];
+      ge_encode(r, w);
+      for (int k = 0; k < 8; ++k) {
+        enc_out[4 * k] = (uint8_t)w[k]; enc_out[4 * k + 1] = (uint8_t)(w[k] >> 8);
+        enc_out[4 * k + 2] = (uint8_t)(w[k] >> 16); enc_out[4 * k + 3] = (uint8_t)(w[k] >> 24);
+      }
+    }
+    if (bad_out) *bad_out = sbad;
+  }
+}
+
+}  // namespace poslo

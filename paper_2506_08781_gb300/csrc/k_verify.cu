@@ -1,0 +1,254 @@
+// Verification kernels: epoch seeds (A1), hashing and scalar aggregation (A2-A4), point decoding and sums (A5), window tables and the final cofactored check (A6).
+#include "common.cuh"
+
+namespace poslo {
+
+__global__ void k_epoch_seeds(const DsNode* __restrict__ ds, int nds, uint64_t e0, uint64_t ne,
+                              uint32_t* __restrict__ x0_out, uint32_t* __restrict__ status) {
+  const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= ne) return;
+  const uint64_t target = e0 + k;
+  // pop from the top of the stack until a node covers leaf `target`
+  int top = nds - 1;
+  bool ok = top >= 0;
+  if (ok) {
+    const DsNode& n = ds[top];
+    ok = target < (((uint64_t)n.i + 1) << n.d);
+  }
+  while (ok && target < ((uint64_t)ds[top].i << ds[top].d)) {
+    --top;
+    ok = top >= 0;
+  }
+  uint32_t x[4] = {0, 0, 0, 0};
+  if (ok) {
+    const DsNode n = ds[top];
+    x[0] = n.seed[0]; x[1] = n.seed[1]; x[2] = n.seed[2]; x[3] = n.seed[3];
+    const uint64_t off = target - ((uint64_t)n.i << n.d);
+    for (int j = (int)n.d - 1; j >= 0; --j) {
+      uint32_t y[4];
+      prf_node(x, (uint32_t)(off >> j) & 1u, y);
+      x[0] = y[0]; x[1] = y[1]; x[2] = y[2]; x[3] = y[3];
+    }
+  } else {
+    atomicOr(status, kErrSeed);
+  }
+  uint4* o = reinterpret_cast<uint4*>(x0_out) + k;
+  *o = make_uint4(x[0], x[1], x[2], x[3]);
+}
+
+__global__ void __launch_bounds__(kHashThreads) k_hash(const HashArgs a) {
+  acc13 acc_e, acc_s;
+  acc_zero(acc_e);
+  acc_zero(acc_s);
+  uint32_t bad = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.n; t += stride) {
+    const uint64_t gi = a.first_index + t;
+    uint64_t i, j;
+    if (a.n2_log2 != 0xffffffffu) {
+      i = gi >> a.n2_log2;
+      j = gi & ((1ull << a.n2_log2) - 1);
+    } else {
+      i = gi / a.n2;
+      j = gi - i * a.n2;
+    }
+    const uint4 xs = __ldg(reinterpret_cast<const uint4*>(a.seeds) + (i - a.e0));
+    const uint32_t x0[4] = {xs.x, xs.y, xs.z, xs.w};
+    uint32_t x[4];
+    prf_entry(x0, (uint32_t)j, x);
+    const uint64_t o0 = a.offs[t] - a.base_off, o1 = a.offs[t + 1] - a.base_off;
+    uint32_t st[8];
+    hash_entry(a.msgs + o0, (uint32_t)(o1 - o0), x, st);
+    uint32_t d[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) d[k] = bswap32(st[k]);
+    const sc e = sc_reduce256(d);
+    if (a.e_out) {
+      uint4* eo = reinterpret_cast<uint4*>(a.e_out + 32 * t);
+      eo[0] = make_uint4(e.v[0], e.v[1], e.v[2], e.v[3]);
+      eo[1] = make_uint4(e.v[4], e.v[5], e.v[6], e.v[7]);
+    }
+    uint32_t s[8];
+    if (a.s) {
+      const uint4* sp = reinterpret_cast<const uint4*>(a.s + 32 * t);
+      const uint4 s0 = __ldg(sp), s1 = __ldg(sp + 1);
+      s[0] = s0.x; s[1] = s0.y; s[2] = s0.z; s[3] = s0.w; s[4] = s1.x; s[5] = s1.y; s[6] = s1.z; s[7] = s1.w;
+      bad += sc_is_canonical(s) ? 0u : 1u;
+    }
+    if (a.weighted) {
+      uint32_t z[4];
+      weight_of(a.zpre, gi, z);
+      if (a.z_out) reinterpret_cast<uint4*>(a.z_out)[t] = make_uint4(z[0], z[1], z[2], z[3]);
+      uint32_t p[12];
+      mul_4x8(p, z, e.v);
+      acc_add<12>(acc_e, p);
+      if (a.s) {
+        mul_4x8(p, z, s);
+        acc_add<12>(acc_s, p);
+      }
+    } else {
+      acc_add<8>(acc_e, e.v);
+      if (a.s) acc_add<8>(acc_s, s);
+    }
+  }
+  // block reduction of the limb values as 64-bit sums
+  __shared__ unsigned long long red[kHashThreads / 32][kPartialWords];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < kPartialWords; ++k) {
+    unsigned long long v = k < 13 ? acc_e.v[k] : (k < 26 ? acc_s.v[k - 13] : bad);
+    warp_sum_u64(v);
+    if (lane == 0) red[warp][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kPartialWords) {
+    unsigned long long v = 0;
+    for (int w = 0; w < kHashThreads / 32; ++w) v += red[w][threadIdx.x];
+    a.partial[(uint64_t)blockIdx.x * kPartialWords + threadIdx.x] = v;
+  }
+}
+
+__global__ void __launch_bounds__(kPointThreads) k_points(const PointArgs a) {
+  ge acc = ge_identity();
+  uint32_t bad = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.count; t += stride) {
+    const uint4* rp = reinterpret_cast<const uint4*>(a.R + 32 * t);
+    const uint4 r0 = __ldg(rp), r1 = __ldg(rp + 1);
+    const uint32_t b[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+    ge P;
+    const bool ok = ge_decode(b, P);
+    bad += ok ? 0u : 1u;
+    if (a.bad_out) a.bad_out[t] = ok ? 0 : 1;
+    if (a.affine_out) {
+      uint32_t* dst = a.affine_out + 16 * t;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) { dst[i] = P.X.v[i]; dst[8 + i] = P.Y.v[i]; }
+    } else if (ok && !(a.skip && a.skip[t])) {
+      acc = ge_add(acc, P);
+    }
+  }
+  // tree reduction in shared memory
+  __shared__ uint32_t sp[kPointThreads][32];
+  __shared__ uint32_t sbad[kPointThreads];
+  ge_store(sp[threadIdx.x], acc);
+  sbad[threadIdx.x] = bad;
+  __syncthreads();
+  for (int h = kPointThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+      const ge o = ge_load(sp[threadIdx.x + h]);
+      const ge m = ge_load(sp[threadIdx.x]);
+      ge_store(sp[threadIdx.x], ge_add(m, o));
+      sbad[threadIdx.x] += sbad[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 32) a.partial[(uint64_t)blockIdx.x * kPointPartialWords + threadIdx.x] = sp[0][threadIdx.x];
+  if (threadIdx.x == 0) a.partial[(uint64_t)blockIdx.x * kPointPartialWords + 32] = sbad[0];
+}
+
+__global__ void k_table(const uint32_t* __restrict__ enc, uint32_t* __restrict__ table,
+                        uint32_t* __restrict__ status, int use_base) {
+  const int w = threadIdx.x;
+  if (w >= kTableWindows) return;
+  ge P;
+  if (use_base) {
+    P = ge_base();
+  } else {
+    uint32_t b[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) b[i] = enc[i];
+    if (!ge_decode(b, P)) {
+      if (w == 0) atomicOr(status, kErrKey);
+      P = ge_identity();
+    }
+  }
+  for (int k = 0; k < 4 * w; ++k) P = ge_dbl(P);
+  ge acc = P;
+  uint32_t* row = table + (size_t)w * kTableDigits * 32;
+  ge_store(row, acc);
+  for (int d = 2; d <= kTableDigits; ++d) {
+    acc = ge_add(acc, P);
+    ge_store(row + (d - 1) * 32, acc);
+  }
+}
+
+__global__ void __launch_bounds__(kFinalThreads) k_finalize(const FinalArgs a) {
+  __shared__ unsigned long long sums[kPartialWords];
+  __shared__ uint32_t pts[kFinalThreads][32];
+  __shared__ uint32_t pbad;
+  __shared__ int8_t dig_e[64], dig_s[64];
+  __shared__ uint32_t sh_e[8], sh_s[8];
+  __shared__ uint32_t bad_flag;
+  const int tid = threadIdx.x;
+  if (tid < kPartialWords) sums[tid] = 0;
+  if (tid == 0) { pbad = 0; bad_flag = 0; }
+  __syncthreads();
+  // scalar partial sums
+  if (tid < kPartialWords) {
+    unsigned long long v = 0;
+    for (uint32_t b = 0; b < a.nhash; ++b) v += a.hash_partial[(size_t)b * kPartialWords + tid];
+    sums[tid] = v;
+  }
+  // point partials
+  ge acc = ge_identity();
+  uint32_t bad = 0;
+  for (uint32_t b = tid; b < a.npoint; b += kFinalThreads) {
+    acc = ge_add(acc, ge_load(a.point_partial + (size_t)b * kPointPartialWords));
+    bad += a.point_partial[(size_t)b * kPointPartialWords + 32];
+  }
+  ge_store(pts[tid], acc);
+  atomicAdd(&pbad, bad);
+  __syncthreads();
+  for (int h = kFinalThreads / 2; h > 0; h >>= 1) {
+    if (tid < h) ge_store(pts[tid], ge_add(ge_load(pts[tid]), ge_load(pts[tid + h])));
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const sc e = limb_sums_to_scalar(sums);
+    sc s;
+    uint32_t bf = (sums[26] != 0 || pbad != 0) ? 1u : 0u;
+    if (a.s_given) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        s.v[k] = a.s_given[4 * k] | (a.s_given[4 * k + 1] << 8) | (a.s_given[4 * k + 2] << 16) |
+                 ((uint32_t)a.s_given[4 * k + 3] << 24);
+      if (!sc_is_canonical(s.v)) bf = 1;
+    } else {
+      s = limb_sums_to_scalar(sums + 13);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) { sh_e[k] = e.v[k]; sh_s[k] = s.v[k]; }
+    recode4(e.v, dig_e);
+    recode4(s.v, dig_s);
+    bad_flag = bf;
+  }
+  __syncthreads();
+  // R is the reduced point sum unless given
+  ge R = a.R_given ? ge_load(a.R_given) : ge_load(pts[0]);
+  __syncthreads();
+  // window terms: thread w adds dig_e[w] 16^w Y + dig_s[w] 16^w G
+  ge term = ge_identity();
+  if (tid < kTableWindows) {
+    term = ge_add(table_pick(a.tableY, tid, dig_e[tid]), table_pick(a.tableG, tid, dig_s[tid]));
+  }
+  ge_store(pts[tid], term);
+  __syncthreads();
+  for (int h = kTableWindows / 2; h > 0; h >>= 1) {
+    if (tid < h) ge_store(pts[tid], ge_add(ge_load(pts[tid]), ge_load(pts[tid + h])));
+    __syncthreads();
+  }
+  if (tid == 0) {
+    const ge eYsG = ge_load(pts[0]);
+    const ge diff = ge_sub(R, eYsG);
+    const bool ok = ge_is_identity(ge_mul_cofactor(diff)) && !bad_flag;
+    const bool key_bad = (*a.status & kErrKey) != 0;
+    a.accept[0] = (ok && !key_bad) ? 1 : 0;
+    if (a.out_words) {
+      for (int k = 0; k < 8; ++k) { a.out_words[k] = sh_e[k]; a.out_words[8 + k] = sh_s[k]; }
+      ge_store(a.out_words + 16, R);
+    }
+  }
+}
+
+}  // namespace poslo

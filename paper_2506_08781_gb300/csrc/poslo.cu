@@ -1,0 +1,929 @@
+// libposlo: host orchestration and the C ABI declared in include/poslo.h.
+//
+// One context owns three CUDA streams: the main stream runs the hashing (A1-A4) and the
+// final check; a side stream builds the window table of the public key Y while hashing
+// runs; a third stream decodes and sums the commitments R_t (A5).  The hash kernel is
+// bound by the integer ALU pipe (SHA-256) and the point kernel by the IMAD pipe (field
+// multiplication), so running them concurrently lets both pipes issue on every SM.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/poslo.h"
+#include "common.cuh"
+
+using namespace poslo;
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+struct KernelTimer {
+  double total_ms = 0;
+  uint64_t launches = 0;
+};
+
+}  // namespace
+
+struct poslo_ctx {
+  int device = 0;
+  int sm_count = 0;
+  uint32_t msm_window = 0;
+  uint64_t mem_budget = 0;
+  uint64_t mem_used = 0;
+  uint8_t vseed[32] = {0};
+  cudaStream_t s_main = nullptr, s_table = nullptr, s_points = nullptr;
+  cudaEvent_t ev_table = nullptr, ev_points = nullptr, ev_main = nullptr;
+  std::map<std::string, DevBuf> bufs;
+  uint32_t* tableG = nullptr;     // fixed-window table of G (64 KiB)
+  uint32_t* status = nullptr;     // device status word
+  uint32_t* h_status = nullptr;   // pinned mirror
+  std::string err;
+  bool profiling = false;
+  std::map<std::string, KernelTimer> timers;
+  std::vector<std::pair<std::string, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+  std::vector<cudaEvent_t> event_pool;
+};
+
+namespace {
+
+int fail(poslo_ctx* c, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return code;
+}
+
+#define CU(call)                                                                           \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) return fail(ctx, POSLO_EDEVICE, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+// Grow-only named workspace buffers.
+int ensure(poslo_ctx* ctx, const char* name, size_t bytes, void** out) {
+  DevBuf& b = ctx->bufs[name];
+  if (bytes == 0) bytes = 16;
+  if (b.cap < bytes) {
+    size_t want = std::max(bytes, b.cap + b.cap / 2);
+    want = (want + 255) & ~size_t(255);
+    if (ctx->mem_budget && ctx->mem_used - b.cap + want > ctx->mem_budget)
+      return fail(ctx, POSLO_ENOMEM, "workspace '%s' of %zu bytes exceeds the memory budget", name, want);
+    if (b.p) {
+      cudaStreamSynchronize(ctx->s_main);
+      cudaStreamSynchronize(ctx->s_table);
+      cudaStreamSynchronize(ctx->s_points);
+      cudaFree(b.p);
+      ctx->mem_used -= b.cap;
+      b.p = nullptr;
+      b.cap = 0;
+    }
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) return fail(ctx, POSLO_ENOMEM, "cudaMalloc(%zu) for '%s': %s", want, name, cudaGetErrorString(e));
+    b.cap = want;
+    ctx->mem_used += want;
+  }
+  *out = b.p;
+  return POSLO_OK;
+}
+
+template <class T>
+int ensure_t(poslo_ctx* ctx, const char* name, size_t bytes, T** out) {
+  void* p;
+  int rc = ensure(ctx, name, bytes, &p);
+  *out = static_cast<T*>(p);
+  return rc;
+}
+
+// Device view of a caller buffer: either the caller's device pointer or a copy.
+int stage(poslo_ctx* ctx, const char* name, const void* src, size_t bytes, bool on_device, cudaStream_t st,
+          const void** out) {
+  if (on_device || bytes == 0) {
+    *out = src;
+    if (bytes == 0 && !src) {
+      void* p;
+      int rc = ensure(ctx, name, 16, &p);
+      if (rc) return rc;
+      *out = p;
+    }
+    return POSLO_OK;
+  }
+  void* p;
+  int rc = ensure(ctx, name, bytes, &p);
+  if (rc) return rc;
+  CU(cudaMemcpyAsync(p, src, bytes, cudaMemcpyHostToDevice, st));
+  *out = p;
+  return POSLO_OK;
+}
+
+void timer_begin(poslo_ctx* ctx, const char* name, cudaStream_t st, cudaEvent_t* b, cudaEvent_t* e) {
+  *b = *e = nullptr;
+  if (!ctx->profiling) return;
+  auto take = [&]() {
+    cudaEvent_t ev;
+    if (!ctx->event_pool.empty()) {
+      ev = ctx->event_pool.back();
+      ctx->event_pool.pop_back();
+    } else {
+      cudaEventCreate(&ev);
+    }
+    return ev;
+  };
+  *b = take();
+  *e = take();
+  cudaEventRecord(*b, st);
+  (void)name;
+}
+
+void timer_end(poslo_ctx* ctx, const char* name, cudaStream_t st, cudaEvent_t b, cudaEvent_t e) {
+  if (!ctx->profiling || !b) return;
+  cudaEventRecord(e, st);
+  ctx->pending.push_back({name, {b, e}});
+}
+
+void timers_collect(poslo_ctx* ctx) {
+  for (auto& p : ctx->pending) {
+    cudaEventSynchronize(p.second.second);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, p.second.first, p.second.second);
+    KernelTimer& t = ctx->timers[p.first];
+    t.total_ms += ms;
+    t.launches += 1;
+    ctx->event_pool.push_back(p.second.first);
+    ctx->event_pool.push_back(p.second.second);
+  }
+  ctx->pending.clear();
+}
+
+uint32_t load_be32(const uint8_t* b) {
+  return ((uint32_t)b[0] << 24) | ((uint32_t)b[1] << 16) | ((uint32_t)b[2] << 8) | b[3];
+}
+
+int parse_ds(poslo_ctx* ctx, const uint8_t* ds, uint32_t nodes, std::vector<DsNode>& out) {
+  if (nodes == 0 || !ds) return fail(ctx, POSLO_EINVAL, "empty disclosed-seed stack");
+  out.resize(nodes);
+  for (uint32_t k = 0; k < nodes; ++k) {
+    const uint8_t* b = ds + 24 * (size_t)k;
+    DsNode n;
+    n.d = b[0] | (b[1] << 8) | (b[2] << 16) | ((uint32_t)b[3] << 24);
+    n.i = b[4] | (b[5] << 8) | (b[6] << 16) | ((uint32_t)b[7] << 24);
+    if (n.d > 40) return fail(ctx, POSLO_EINVAL, "ds node %u: depth %u too large", k, n.d);
+    for (int w = 0; w < 4; ++w) n.seed[w] = load_be32(b + 8 + 4 * w);
+    out[k] = n;
+  }
+  return POSLO_OK;
+}
+
+int grid_for(const poslo_ctx* ctx, uint64_t n, int threads, int per_sm) {
+  const uint64_t need = (n + threads - 1) / threads;
+  const uint64_t cap = (uint64_t)ctx->sm_count * per_sm;
+  return (int)std::max<uint64_t>(1, std::min(need, cap));
+}
+
+int check_status(poslo_ctx* ctx) {
+  CU(cudaMemcpyAsync(ctx->h_status, ctx->status, 4, cudaMemcpyDeviceToHost, ctx->s_main));
+  CU(cudaStreamSynchronize(ctx->s_main));
+  const uint32_t st = *ctx->h_status;
+  if (st & kErrSeed) return fail(ctx, POSLO_EINVAL, "a requested epoch seed is not disclosed by ds (SRet bottom)");
+  if (st & kErrKey) return fail(ctx, POSLO_EINVAL, "public key Y does not decode");
+  if (st & kErrTimeout) return fail(ctx, POSLO_ETIMEOUT, "device-side wait expired");
+  return POSLO_OK;
+}
+
+int reset_status(poslo_ctx* ctx) {
+  CU(cudaMemsetAsync(ctx->status, 0, 4, ctx->s_main));
+  return POSLO_OK;
+}
+
+uint32_t log2_exact(uint32_t n) {
+  if (n == 0 || (n & (n - 1))) return 0xffffffffu;
+  uint32_t l = 0;
+  while ((1u << l) < n) ++l;
+  return l;
+}
+
+// Epoch seeds for global entries [first, first+n) into buffer "seeds"; returns e0.
+int run_epoch_seeds(poslo_ctx* ctx, const uint8_t* ds, uint32_t nodes, uint64_t first_epoch, uint64_t n_epochs,
+                    uint32_t** seeds_out) {
+  std::vector<DsNode> h;
+  int rc = parse_ds(ctx, ds, nodes, h);
+  if (rc) return rc;
+  DsNode* d_ds;
+  if ((rc = ensure_t(ctx, "ds", h.size() * sizeof(DsNode), &d_ds))) return rc;
+  CU(cudaMemcpyAsync(d_ds, h.data(), h.size() * sizeof(DsNode), cudaMemcpyHostToDevice, ctx->s_main));
+  uint32_t* seeds;
+  if ((rc = ensure_t(ctx, "seeds", std::max<uint64_t>(1, n_epochs) * 16, &seeds))) return rc;
+  if (n_epochs) {
+    const int threads = 128;
+    const uint64_t blocks = (n_epochs + threads - 1) / threads;
+    cudaEvent_t b, e;
+    timer_begin(ctx, "seeds", ctx->s_main, &b, &e);
+    k_epoch_seeds<<<(unsigned)blocks, threads, 0, ctx->s_main>>>(d_ds, (int)h.size(), first_epoch, n_epochs, seeds,
+                                                                ctx->status);
+    CU(cudaGetLastError());
+    timer_end(ctx, "seeds", ctx->s_main, b, e);
+  }
+  *seeds_out = seeds;
+  return POSLO_OK;
+}
+
+struct Staged {
+  const uint8_t* msgs = nullptr;
+  const uint64_t* offs = nullptr;
+  uint64_t base_off = 0;
+  const uint8_t* s = nullptr;
+  const uint8_t* R = nullptr;
+};
+
+int validate_batch(poslo_ctx* ctx, const poslo_batch* b) {
+  if (!b) return fail(ctx, POSLO_EINVAL, "null batch");
+  if (b->variant != POSLO_VARIANT_C && b->variant != POSLO_VARIANT_F) return fail(ctx, POSLO_EINVAL, "bad variant");
+  if (b->n2 == 0) return fail(ctx, POSLO_EINVAL, "n2 must be >= 1");
+  if (!b->Y) return fail(ctx, POSLO_EINVAL, "missing public key");
+  if (b->n && (!b->offs || !b->s || !b->R)) return fail(ctx, POSLO_EINVAL, "missing batch arrays");
+  if (b->variant == POSLO_VARIANT_C) {
+    if (b->n % b->n2 || b->first_index % b->n2)
+      return fail(ctx, POSLO_EINVAL, "POSLO-C batches hold whole epochs of n2 entries");
+    if (!b->s || !b->R) return fail(ctx, POSLO_EINVAL, "POSLO-C needs s~ and R");
+    if (b->R_count != 1 && b->R_count != b->n / b->n2)
+      return fail(ctx, POSLO_EINVAL, "POSLO-C R_count must be 1 or n/n2");
+  } else {
+    if (b->R_count != b->n) return fail(ctx, POSLO_EINVAL, "POSLO-F R_count must equal n");
+  }
+  return POSLO_OK;
+}
+
+int stage_batch(poslo_ctx* ctx, const poslo_batch* b, Staged& sb) {
+  int rc;
+  const bool dev = b->on_device != 0;
+  const void* p;
+  if (b->n == 0) {
+    uint64_t* z;
+    if ((rc = ensure_t(ctx, "offs", 16, &z))) return rc;
+    CU(cudaMemsetAsync(z, 0, 16, ctx->s_main));
+    sb.offs = z;
+    sb.msgs = reinterpret_cast<const uint8_t*>(z);
+  } else {
+    if ((rc = stage(ctx, "offs", b->offs, (b->n + 1) * 8, dev, ctx->s_main, &p))) return rc;
+    sb.offs = static_cast<const uint64_t*>(p);
+    if (dev) {
+      sb.msgs = b->msgs;
+      sb.base_off = 0;
+    } else {
+      const uint64_t lo = b->offs[0], hi = b->offs[b->n];
+      if (hi < lo) return fail(ctx, POSLO_EINVAL, "offsets decrease");
+      for (uint64_t t = 0; t < b->n; ++t)
+        if (b->offs[t + 1] < b->offs[t]) return fail(ctx, POSLO_EINVAL, "offsets decrease at entry %llu", (unsigned long long)t);
+      if ((rc = stage(ctx, "msgs", b->msgs + lo, hi - lo, false, ctx->s_main, &p))) return rc;
+      sb.msgs = static_cast<const uint8_t*>(p);
+      sb.base_off = lo;
+    }
+  }
+  const size_t s_bytes = b->variant == POSLO_VARIANT_F ? 32 * b->n : 32;
+  const size_t R_bytes = 32 * (b->variant == POSLO_VARIANT_F ? b->n : b->R_count);
+  if ((rc = stage(ctx, "s_in", b->s, s_bytes, dev, ctx->s_main, &p))) return rc;
+  sb.s = static_cast<const uint8_t*>(p);
+  if ((rc = stage(ctx, "R_in", b->R, R_bytes, dev, ctx->s_main, &p))) return rc;
+  sb.R = static_cast<const uint8_t*>(p);
+  return POSLO_OK;
+}
+
+void make_zpre(const uint8_t vseed[32], uint32_t zpre[10]) {
+  uint8_t buf[40] = {'P', 'O', 'S', 'L', 'O', '-', 'Z'};
+  memcpy(buf + 7, vseed, 32);
+  buf[39] = 0;
+  for (int i = 0; i < 10; ++i) zpre[i] = load_be32(buf + 4 * i);
+}
+
+// Hash stage shared by AVer, Distill and the inspection call.
+int run_hash(poslo_ctx* ctx, const poslo_batch* b, const Staged& sb, uint8_t* e_out, bool weighted, bool with_s,
+             uint32_t* z_out, unsigned long long** partial_out, uint32_t* nblocks_out) {
+  int rc;
+  uint64_t e_first = 0, ne = 0;
+  if (b->n) {
+    e_first = b->first_index / b->n2;
+    ne = (b->first_index + b->n - 1) / b->n2 - e_first + 1;
+  }
+  uint32_t* seeds;
+  if ((rc = run_epoch_seeds(ctx, b->ds, b->ds_nodes, e_first, ne, &seeds))) return rc;
+  const int blocks = grid_for(ctx, b->n, kHashThreads, 8);
+  unsigned long long* partial;
+  if ((rc = ensure_t(ctx, "hash_partial", (size_t)blocks * kPartialWords * 8, &partial))) return rc;
+  HashArgs a{};
+  a.msgs = sb.msgs;
+  a.offs = sb.offs;
+  a.base_off = sb.base_off;
+  a.n = b->n;
+  a.first_index = b->first_index;
+  a.e0 = e_first;
+  a.n2 = b->n2;
+  a.n2_log2 = log2_exact(b->n2);
+  a.seeds = seeds;
+  a.e_out = e_out;
+  a.s = with_s ? sb.s : nullptr;
+  a.weighted = weighted ? 1u : 0u;
+  make_zpre(ctx->vseed, a.zpre);
+  a.z_out = z_out;
+  a.partial = partial;
+  cudaEvent_t tb, te;
+  timer_begin(ctx, "hash", ctx->s_main, &tb, &te);
+  k_hash<<<blocks, kHashThreads, 0, ctx->s_main>>>(a);
+  CU(cudaGetLastError());
+  timer_end(ctx, "hash", ctx->s_main, tb, te);
+  *partial_out = partial;
+  *nblocks_out = (uint32_t)blocks;
+  return POSLO_OK;
+}
+
+// Window table of Y on the side stream (ordered after the main stream's uploads).
+int run_ytable(poslo_ctx* ctx, const uint8_t* Y, uint32_t** table_out) {
+  int rc;
+  uint32_t* d_Y;
+  if ((rc = ensure_t(ctx, "Y", 32, &d_Y))) return rc;
+  uint32_t* tableY;
+  if ((rc = ensure_t(ctx, "tableY", kTableWindows * kTableDigits * 128, &tableY))) return rc;
+  CU(cudaMemcpyAsync(d_Y, Y, 32, cudaMemcpyHostToDevice, ctx->s_main));
+  CU(cudaEventRecord(ctx->ev_main, ctx->s_main));
+  CU(cudaStreamWaitEvent(ctx->s_table, ctx->ev_main, 0));
+  cudaEvent_t tb, te;
+  timer_begin(ctx, "table", ctx->s_table, &tb, &te);
+  k_table<<<1, kTableWindows, 0, ctx->s_table>>>(d_Y, tableY, ctx->status, 0);
+  CU(cudaGetLastError());
+  timer_end(ctx, "table", ctx->s_table, tb, te);
+  CU(cudaEventRecord(ctx->ev_table, ctx->s_table));
+  *table_out = tableY;
+  return POSLO_OK;
+}
+
+int run_points(poslo_ctx* ctx, const uint8_t* R, uint64_t count, uint32_t* affine_out, uint8_t* bad_out,
+               uint32_t** partial_out, uint32_t* nblocks_out) {
+  int rc;
+  const int blocks = grid_for(ctx, count, kPointThreads, 8);
+  uint32_t* partial;
+  if ((rc = ensure_t(ctx, "point_partial", (size_t)blocks * kPointPartialWords * 4, &partial))) return rc;
+  CU(cudaEventRecord(ctx->ev_main, ctx->s_main));
+  CU(cudaStreamWaitEvent(ctx->s_points, ctx->ev_main, 0));
+  PointArgs a{};
+  a.R = R;
+  a.count = count;
+  a.partial = partial;
+  a.affine_out = affine_out;
+  a.bad_out = bad_out;
+  cudaEvent_t tb, te;
+  timer_begin(ctx, "points", ctx->s_points, &tb, &te);
+  k_points<<<blocks, kPointThreads, 0, ctx->s_points>>>(a);
+  CU(cudaGetLastError());
+  timer_end(ctx, "points", ctx->s_points, tb, te);
+  CU(cudaEventRecord(ctx->ev_points, ctx->s_points));
+  *partial_out = partial;
+  *nblocks_out = (uint32_t)blocks;
+  return POSLO_OK;
+}
+
+int run_msm_direct(poslo_ctx* ctx, cudaStream_t st, const uint8_t* points, const uint32_t* affine,
+                   const uint8_t* scalars, uint32_t scalar_bytes, uint64_t n, const uint8_t* skip,
+                   uint32_t* point_out, uint8_t* enc_out, uint32_t* bad_out) {
+  int rc;
+  const int blocks = grid_for(ctx, n, kPointThreads, 8);
+  uint32_t* partial;
+  if ((rc = ensure_t(ctx, "msm_partial", (size_t)blocks * kPointPartialWords * 4, &partial))) return rc;
+  MsmArgs a{};
+  a.points = points;
+  a.affine = affine;
+  a.scalars = scalars;
+  a.scalar_bytes = scalar_bytes;
+  a.n = n;
+  a.skip = skip;
+  a.partial = partial;
+  cudaEvent_t tb, te;
+  timer_begin(ctx, "msm", st, &tb, &te);
+  k_msm_direct<<<blocks, kPointThreads, 0, st>>>(a);
+  CU(cudaGetLastError());
+  k_sum_encode<<<1, kFinalThreads, 0, st>>>(partial, blocks, point_out, enc_out, bad_out);
+  CU(cudaGetLastError());
+  timer_end(ctx, "msm", st, tb, te);
+  return POSLO_OK;
+}
+
+}  // namespace
+
+// ==========================================================================================
+// C ABI
+// ==========================================================================================
+extern "C" {
+
+int poslo_create(const poslo_params* params, poslo_ctx** out) {
+  poslo_ctx* ctx = nullptr;
+  if (!out) return POSLO_EINVAL;
+  *out = nullptr;
+  const int device = params ? params->device : 0;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= device || device < 0) return POSLO_EDEVICE;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return POSLO_EDEVICE;
+  if (prop.major != 10 || prop.minor != 3) return POSLO_EDEVICE;   // built for sm_103a only
+  ctx = new poslo_ctx();
+  ctx->device = device;
+  ctx->sm_count = prop.multiProcessorCount;
+  if (params) {
+    ctx->msm_window = params->msm_window;
+    ctx->mem_budget = params->mem_budget;
+    memcpy(ctx->vseed, params->verifier_seed, 32);
+  }
+  auto bail = [&](int code) {
+    poslo_destroy(ctx);
+    return code;
+  };
+  if (cudaSetDevice(device) != cudaSuccess) return bail(POSLO_EDEVICE);
+  if (cudaStreamCreateWithFlags(&ctx->s_main, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->s_table, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->s_points, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_table, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_points, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_main, cudaEventDisableTiming) != cudaSuccess)
+    return bail(POSLO_EDEVICE);
+  if (cudaMalloc(&ctx->status, 4) != cudaSuccess) return bail(POSLO_ENOMEM);
+  if (cudaMallocHost(&ctx->h_status, 4) != cudaSuccess) return bail(POSLO_ENOMEM);
+  if (cudaMalloc(&ctx->tableG, kTableWindows * kTableDigits * 128) != cudaSuccess) return bail(POSLO_ENOMEM);
+  cudaMemsetAsync(ctx->status, 0, 4, ctx->s_main);
+  k_table<<<1, kTableWindows, 0, ctx->s_main>>>(nullptr, ctx->tableG, ctx->status, 1);
+  if (cudaStreamSynchronize(ctx->s_main) != cudaSuccess) return bail(POSLO_EDEVICE);
+  *out = ctx;
+  return POSLO_OK;
+}
+
+void poslo_destroy(poslo_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->s_main) cudaStreamSynchronize(ctx->s_main);
+  if (ctx->s_table) cudaStreamSynchronize(ctx->s_table);
+  if (ctx->s_points) cudaStreamSynchronize(ctx->s_points);
+  for (auto& kv : ctx->bufs)
+    if (kv.second.p) cudaFree(kv.second.p);
+  for (auto& p : ctx->pending) {
+    cudaEventDestroy(p.second.first);
+    cudaEventDestroy(p.second.second);
+  }
+  for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+  if (ctx->tableG) cudaFree(ctx->tableG);
+  if (ctx->status) cudaFree(ctx->status);
+  if (ctx->h_status) cudaFreeHost(ctx->h_status);
+  if (ctx->ev_table) cudaEventDestroy(ctx->ev_table);
+  if (ctx->ev_points) cudaEventDestroy(ctx->ev_points);
+  if (ctx->ev_main) cudaEventDestroy(ctx->ev_main);
+  if (ctx->s_main) cudaStreamDestroy(ctx->s_main);
+  if (ctx->s_table) cudaStreamDestroy(ctx->s_table);
+  if (ctx->s_points) cudaStreamDestroy(ctx->s_points);
+  delete ctx;
+}
+
+const char* poslo_last_error(const poslo_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+void* poslo_stream(poslo_ctx* ctx) { return ctx ? (void*)ctx->s_main : nullptr; }
+
+int poslo_set_profiling(poslo_ctx* ctx, int enabled) {
+  if (!ctx) return POSLO_EINVAL;
+  ctx->profiling = enabled != 0;
+  return POSLO_OK;
+}
+
+int poslo_kernel_time(poslo_ctx* ctx, const char* name, double* total_ms, uint64_t* launches) {
+  if (!ctx || !name) return POSLO_EINVAL;
+  timers_collect(ctx);
+  auto it = ctx->timers.find(name);
+  if (it == ctx->timers.end()) {
+    if (total_ms) *total_ms = 0;
+    if (launches) *launches = 0;
+    return POSLO_ENOTFOUND;
+  }
+  if (total_ms) *total_ms = it->second.total_ms;
+  if (launches) *launches = it->second.launches;
+  return POSLO_OK;
+}
+
+void poslo_reset_kernel_times(poslo_ctx* ctx) {
+  if (!ctx) return;
+  timers_collect(ctx);
+  ctx->timers.clear();
+}
+
+// ---------------------------------------------------------------------------- signer side
+
+int poslo_keygen_c(poslo_ctx* ctx, const uint8_t y[32], const uint8_t r[32], uint32_t D, uint32_t n2,
+                   uint8_t Y_out[32], uint8_t* epoch_R_out) {
+  if (!ctx || !y || !r || !Y_out || D > 24 || n2 == 0) return fail(ctx, POSLO_EINVAL, "bad keygen_c arguments");
+  int rc;
+  const uint64_t n1 = 1ull << D;
+  uint8_t *d_in, *d_out;
+  if ((rc = ensure_t(ctx, "kg_in", 64, &d_in))) return rc;
+  if ((rc = ensure_t(ctx, "kg_out", 32 + 32 * n1, &d_out))) return rc;
+  CU(cudaMemcpyAsync(d_in, y, 32, cudaMemcpyHostToDevice, ctx->s_main));
+  CU(cudaMemcpyAsync(d_in + 32, r, 32, cudaMemcpyHostToDevice, ctx->s_main));
+  k_keygen_y<<<1, 1, 0, ctx->s_main>>>(d_in, ctx->tableG, d_out);
+  k_keygen_c_epochs<<<(unsigned)((n1 + 63) / 64), 64, 0, ctx->s_main>>>(d_in + 32, (uint32_t)n1, n2, ctx->tableG,
+                                                                         d_out + 32);
+  CU(cudaGetLastError());
+  CU(cudaMemcpyAsync(Y_out, d_out, 32, cudaMemcpyDeviceToHost, ctx->s_main));
+  if (epoch_R_out) CU(cudaMemcpyAsync(epoch_R_out, d_out + 32, 32 * n1, cudaMemcpyDeviceToHost, ctx->s_main));
+  CU(cudaStreamSynchronize(ctx->s_main));
+  return POSLO_OK;
+}
+
+int poslo_keygen_f(poslo_ctx* ctx, const uint8_t y[32], const uint8_t* bpv_r, uint32_t v, uint8_t Y_out[32],
+                   uint8_t* bpv_R_out) {
+  if (!ctx || !y || !Y_out || (v && (!bpv_r || !bpv_R_out))) return fail(ctx, POSLO_EINVAL, "bad keygen_f arguments");
+  int rc;
+  uint8_t *d_y, *d_r, *d_out;
+  if ((rc = ensure_t(ctx, "kg_in", 32, &d_y))) return rc;
+  if ((rc = ensure_t(ctx, "kg_bpv", 32 * (size_t)std::max(v, 1u), &d_r))) return rc;
+  if ((rc = ensure_t(ctx, "kg_out", 32 + 32 * (size_t)v, &d_out))) return rc;
+  CU(cudaMemcpyAsync(d_y, y, 32, cudaMemcpyHostToDevice, ctx->s_main));
+  if (v) CU(cudaMemcpyAsync(d_r, bpv_r, 32 * (size_t)v, cudaMemcpyHostToDevice, ctx->s_main));
+  k_keygen_y<<<1, 1, 0, ctx->s_main>>>(d_y, ctx->tableG, d_out);
+  if (v) k_keygen_bpv<<<(v + 63) / 64, 64, 0, ctx->s_main>>>(d_r, v, ctx->tableG, d_out + 32);
+  CU(cudaGetLastError());
+  CU(cudaMemcpyAsync(Y_out, d_out, 32, cudaMemcpyDeviceToHost, ctx->s_main));
+  if (v) CU(cudaMemcpyAsync(bpv_R_out, d_out + 32, 32 * (size_t)v, cudaMemcpyDeviceToHost, ctx->s_main));
+  CU(cudaStreamSynchronize(ctx->s_main));
+  return POSLO_OK;
+}
+
+static int root_ds(const uint8_t root[16], uint32_t D, uint8_t out[24]) {
+  memset(out, 0, 24);
+  out[0] = (uint8_t)D; out[1] = (uint8_t)(D >> 8); out[2] = (uint8_t)(D >> 16); out[3] = (uint8_t)(D >> 24);
+  memcpy(out + 8, root, 16);
+  return 0;
+}
+
+int poslo_sign_f(poslo_ctx* ctx, const uint8_t y[32], const uint8_t root[16], uint32_t D, uint32_t n2,
+                 const uint8_t* bpv_r, const uint8_t* bpv_R, uint32_t v, uint32_t k, const uint16_t* subsets,
+                 const uint8_t* msgs, const uint64_t* offs, uint64_t n, uint64_t first_index, uint8_t* s_out,
+                 uint8_t* R_out, uint8_t* x_out) {
+  if (!ctx || !y || !root || !bpv_r || !bpv_R || !subsets || !offs || !s_out || !R_out || n2 == 0 || v == 0 || D > 40)
+    return fail(ctx, POSLO_EINVAL, "bad sign_f arguments");
+  if (n == 0) return POSLO_OK;
+  if ((first_index + n - 1) / n2 >= (1ull << D)) return fail(ctx, POSLO_EINVAL, "entry index beyond n1*n2");
+  for (uint64_t t = 0; t < n * k; ++t)
+    if (subsets[t] >= v) return fail(ctx, POSLO_EINVAL, "BPV subset index out of range");
+  int rc;
+  uint8_t ds[24];
+  root_ds(root, D, ds);
+  const uint64_t e0 = first_index / n2, ne = (first_index + n - 1) / n2 - e0 + 1;
+  CU(cudaMemsetAsync(ctx->status, 0, 4, ctx->s_main));
+  uint32_t* seeds;
+  if ((rc = run_epoch_seeds(ctx, ds, 1, e0, ne, &seeds))) return rc;
+  const void* p;
+  SignFArgs a{};
+  if ((rc = stage(ctx, "offs", offs, (n + 1) * 8, false, ctx->s_main, &p))) return rc;
+  a.offs = static_cast<const uint64_t*>(p);
+  a.base_off = offs[0];
+  if ((rc = stage(ctx, "msgs", msgs + offs[0], offs[n] - offs[0], false, ctx->s_main, &p))) return rc;
+  a.msgs = static_cast<const uint8_t*>(p);
+  uint8_t* d_y;
+  if ((rc = ensure_t(ctx, "sig_y", 32, &d_y))) return rc;
+  CU(cudaMemcpyAsync(d_y, y, 32, cudaMemcpyHostToDevice, ctx->s_main));
+  if ((rc = stage(ctx, "sig_bpv_r", bpv_r, 32 * (size_t)v, false, ctx->s_main, &p))) return rc;
+  a.bpv_r = static_cast<const uint8_t*>(p);
+  const uint8_t* d_bpvR;
+  if ((rc = stage(ctx, "sig_bpv_R", bpv_R, 32 * (size_t)v, false, ctx->s_main, &p))) return rc;
+  d_bpvR = static_cast<const uint8_t*>(p);
+  uint32_t* pts;
+  if ((rc = ensure_t(ctx, "sig_bpv_pts", 128 * (size_t)v, &pts))) return rc;
+  k_decode_table<<<(v + 63) / 64, 64, 0, ctx->s_main>>>(d_bpvR, v, pts, ctx->status);
+  if ((rc = stage(ctx, "sig_subsets", subsets, 2 * n * k, false, ctx->s_main, &p))) return rc;
+  a.subsets = static_cast<const uint16_t*>(p);
+  uint8_t *d_s, *d_R, *d_x = nullptr;
+  if ((rc = ensure_t(ctx, "sig_s", 32 * n, &d_s))) return rc;
+  if ((rc = ensure_t(ctx, "sig_R", 32 * n, &d_R))) return rc;
+  if (x_out && (rc = ensure_t(ctx, "sig_x", 16 * n, &d_x))) return rc;
+  a.n = n;
+  a.first_index = first_index;
+  a.e0 = e0;
+  a.n2 = n2;
+  a.seeds = seeds;
+  a.y = d_y;
+  a.bpv_pts = pts;
+  a.v = v;
+  a.k = k;
+  a.s_out = d_s;
+  a.R_out = d_R;
+  a.x_out = d_x;
+  k_sign_f<<<(unsigned)((n + 127) / 128), 128, 0, ctx->s_main>>>(a);
+  CU(cudaGetLastError());
+  CU(cudaMemcpyAsync(s_out, d_s, 32 * n, cudaMemcpyDeviceToHost, ctx->s_main));
+  CU(cudaMemcpyAsync(R_out, d_R, 32 * n, cudaMemcpyDeviceToHost, ctx->s_main));
+  if (x_out) CU(cudaMemcpyAsync(x_out, d_x, 16 * n, cudaMemcpyDeviceToHost, ctx->s_main));
+  int st = check_status(ctx);
+  if (st == POSLO_OK && (*ctx->h_status & kErrPoint)) return fail(ctx, POSLO_EINVAL, "BPV table point does not decode");
+  return st;
+}
+
+int poslo_sign_c(poslo_ctx* ctx, const uint8_t y[32], const uint8_t r[32], const uint8_t root[16], uint32_t D,
+                 uint32_t n2, const uint8_t* msgs, const uint64_t* offs, uint64_t first_epoch, uint64_t n_epochs,
+                 uint8_t* s_out) {
+  if (!ctx || !y || !r || !root || !offs || !s_out || n2 == 0 || D > 40)
+    return fail(ctx, POSLO_EINVAL, "bad sign_c arguments");
+  if (n_epochs == 0) return POSLO_OK;
+  if (first_epoch + n_epochs > (1ull << D)) return fail(ctx, POSLO_EINVAL, "epoch beyond n1");
+  int rc;
+  uint8_t ds[24];
+  root_ds(root, D, ds);
+  CU(cudaMemsetAsync(ctx->status, 0, 4, ctx->s_main));
+  uint32_t* seeds;
+  if ((rc = run_epoch_seeds(ctx, ds, 1, first_epoch, n_epochs, &seeds))) return rc;
+  const uint64_t n = n_epochs * n2;
+  const void* p;
+  SignCArgs a{};
+  if ((rc = stage(ctx, "offs", offs, (n + 1) * 8, false, ctx->s_main, &p))) return rc;
+  a.offs = static_cast<const uint64_t*>(p);
+  a.base_off = offs[0];
+  if ((rc = stage(ctx, "msgs", msgs + offs[0], offs[n] - offs[0], false, ctx->s_main, &p))) return rc;
+  a.msgs = static_cast<const uint8_t*>(p);
+  uint8_t* d_yr;
+  if ((rc = ensure_t(ctx, "sig_yr", 64, &d_yr))) return rc;
+  CU(cudaMemcpyAsync(d_yr, y, 32, cudaMemcpyHostToDevice, ctx->s_main));
+  CU(cudaMemcpyAsync(d_yr + 32, r, 32, cudaMemcpyHostToDevice, ctx->s_main));
+  uint8_t* d_s;
+  if ((rc = ensure_t(ctx, "sig_s", 32 * n_epochs, &d_s))) return rc;
+  a.n_epochs = n_epochs;
+  a.first_epoch = first_epoch;
+  a.n2 = n2;
+  a.seeds = seeds;
+  a.y = d_yr;
+  a.r = d_yr + 32;
+  a.s_out = d_s;
+  k_sign_c<<<(unsigned)((n_epochs + 63) / 64), 64, 0, ctx->s_main>>>(a);
+  CU(cudaGetLastError());
+  CU(cudaMemcpyAsync(s_out, d_s, 32 * n_epochs, cudaMemcpyDeviceToHost, ctx->s_main));
+  return check_status(ctx);
+}
+
+int poslo_disclose(poslo_ctx* ctx, const uint8_t root[16], uint32_t D, uint64_t i, uint8_t* ds_out, uint32_t cap_nodes,
+                   uint32_t* nodes) {
+  if (!ctx || !root || !nodes || D > 40 || i >= (1ull << D)) return fail(ctx, POSLO_EINVAL, "bad disclose arguments");
+  // SSO (Fig. 2a) over node positions: merge the top while it sits at the current depth.
+  std::vector<std::pair<uint32_t, uint64_t>> stack;
+  for (uint64_t k = 0; k <= i; ++k) {
+    uint32_t d1 = 0;
+    uint64_t i1 = k;
+    while (!stack.empty() && stack.back().first == d1) {
+      stack.pop_back();
+      ++d1;
+      i1 >>= 1;
+    }
+    stack.push_back({d1, i1});
+  }
+  *nodes = (uint32_t)stack.size();
+  if (stack.size() > cap_nodes || !ds_out) return fail(ctx, POSLO_EBUFSMALL, "ds needs %zu nodes", stack.size());
+  // seeds: SC(root, D, 0, d, i) on the device, walking from the root
+  int rc;
+  uint8_t rds[24];
+  root_ds(root, D, rds);
+  std::vector<DsNode> hroot;
+  if ((rc = parse_ds(ctx, rds, 1, hroot))) return rc;
+  // node x_d[i] is the ancestor at depth d: compute it as the seed of the leaf range start
+  // walked only D-d levels, i.e. an SRet over a shortened tree rooted at the same seed.
+  std::vector<uint8_t> out(24 * stack.size());
+  for (size_t k = 0; k < stack.size(); ++k) {
+    const uint32_t d = stack[k].first;
+    const uint64_t idx = stack[k].second;
+    DsNode top = hroot[0];
+    top.d = D - d;          // a tree of height D-d whose leaves are the depth-d nodes
+    uint8_t tmp[24];
+    memcpy(tmp, &top.d, 4);
+    uint32_t zero = 0;
+    memcpy(tmp + 4, &zero, 4);
+    memcpy(tmp + 8, root, 16);
+    uint32_t* seeds;
+    CU(cudaMemsetAsync(ctx->status, 0, 4, ctx->s_main));
+    if ((rc = run_epoch_seeds(ctx, tmp, 1, idx, 1, &seeds))) return rc;
+    uint32_t w[4];
+    CU(cudaMemcpyAsync(w, seeds, 16, cudaMemcpyDeviceToHost, ctx->s_main));
+    if ((rc = check_status(ctx))) return rc;
+    uint8_t* o = out.data() + 24 * k;
+    memcpy(o, &d, 4);
+    const uint32_t i32 = (uint32_t)idx;
+    memcpy(o + 4, &i32, 4);
+    for (int q = 0; q < 4; ++q) {
+      o[8 + 4 * q] = (uint8_t)(w[q] >> 24); o[9 + 4 * q] = (uint8_t)(w[q] >> 16);
+      o[10 + 4 * q] = (uint8_t)(w[q] >> 8); o[11 + 4 * q] = (uint8_t)w[q];
+    }
+  }
+  memcpy(ds_out, out.data(), out.size());
+  return POSLO_OK;
+}
+
+// ---------------------------------------------------------------------------- verifier side
+
+int poslo_epoch_seeds(poslo_ctx* ctx, const uint8_t* ds, uint32_t ds_nodes, uint64_t first_epoch, uint64_t n_epochs,
+                      uint8_t* x0_out) {
+  if (!ctx || !x0_out) return fail(ctx, POSLO_EINVAL, "bad epoch_seeds arguments");
+  int rc;
+  if ((rc = reset_status(ctx))) return rc;
+  uint32_t* seeds;
+  if ((rc = run_epoch_seeds(ctx, ds, ds_nodes, first_epoch, n_epochs, &seeds))) return rc;
+  std::vector<uint32_t> h(4 * n_epochs);
+  if (n_epochs) CU(cudaMemcpyAsync(h.data(), seeds, 16 * n_epochs, cudaMemcpyDeviceToHost, ctx->s_main));
+  if ((rc = check_status(ctx))) return rc;
+  for (uint64_t k = 0; k < 4 * n_epochs; ++k) {
+    x0_out[4 * k] = (uint8_t)(h[k] >> 24); x0_out[4 * k + 1] = (uint8_t)(h[k] >> 16);
+    x0_out[4 * k + 2] = (uint8_t)(h[k] >> 8); x0_out[4 * k + 3] = (uint8_t)h[k];
+  }
+  return POSLO_OK;
+}
+
+int poslo_hash_entries(poslo_ctx* ctx, const poslo_batch* batch, uint8_t* e_out) {
+  if (!ctx || !e_out) return fail(ctx, POSLO_EINVAL, "bad hash_entries arguments");
+  int rc;
+  if ((rc = validate_batch(ctx, batch))) return rc;
+  if ((rc = reset_status(ctx))) return rc;
+  Staged sb;
+  if ((rc = stage_batch(ctx, batch, sb))) return rc;
+  uint8_t* d_e = e_out;
+  if (!batch->on_device && (rc = ensure_t(ctx, "e_out", 32 * batch->n, &d_e))) return rc;
+  unsigned long long* partial;
+  uint32_t nb;
+  if ((rc = run_hash(ctx, batch, sb, d_e, false, false, nullptr, &partial, &nb))) return rc;
+  if (!batch->on_device && batch->n)
+    CU(cudaMemcpyAsync(e_out, d_e, 32 * batch->n, cudaMemcpyDeviceToHost, ctx->s_main));
+  return check_status(ctx);
+}
+
+int poslo_aver(poslo_ctx* ctx, const poslo_batch* batch, uint32_t agg_mode, uint8_t* accept) {
+  if (!ctx || !accept) return fail(ctx, POSLO_EINVAL, "bad aver arguments");
+  int rc;
+  if ((rc = validate_batch(ctx, batch))) return rc;
+  const bool F = batch->variant == POSLO_VARIANT_F;
+  if (agg_mode == POSLO_AGG_WEIGHTED && !F) return fail(ctx, POSLO_EINVAL, "weighted aggregation needs POSLO-F");
+  if (agg_mode > POSLO_AGG_WEIGHTED) return fail(ctx, POSLO_EINVAL, "bad aggregation mode");
+  const bool weighted = agg_mode == POSLO_AGG_WEIGHTED;
+  if ((rc = reset_status(ctx))) return rc;
+  Staged sb;
+  if ((rc = stage_batch(ctx, batch, sb))) return rc;
+  uint32_t* tableY;
+  if ((rc = run_ytable(ctx, batch->Y, &tableY))) return rc;
+  const uint64_t npts = F ? batch->n : batch->R_count;
+  uint32_t* affine = nullptr;
+  if (weighted && (rc = ensure_t(ctx, "affine", 64 * std::max<uint64_t>(npts, 1), &affine))) return rc;
+  uint32_t *ppart, npb;
+  if ((rc = run_points(ctx, sb.R, npts, affine, nullptr, &ppart, &npb))) return rc;
+  uint32_t* z = nullptr;
+  if (weighted && (rc = ensure_t(ctx, "z", 16 * std::max<uint64_t>(batch->n, 1), &z))) return rc;
+  unsigned long long* hpart;
+  uint32_t nhb;
+  if ((rc = run_hash(ctx, batch, sb, nullptr, weighted, F, z, &hpart, &nhb))) return rc;
+  CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_table, 0));
+  CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_points, 0));
+  uint32_t* Rw = nullptr;
+  if (weighted) {
+    if ((rc = ensure_t(ctx, "R_weighted", 128, &Rw))) return rc;
+    if ((rc = run_msm_direct(ctx, ctx->s_main, nullptr, affine, reinterpret_cast<const uint8_t*>(z), 16, batch->n,
+                             nullptr, Rw, nullptr, nullptr)))
+      return rc;
+  }
+  uint8_t* d_acc;
+  if ((rc = ensure_t(ctx, "accept", 16, &d_acc))) return rc;
+  FinalArgs f{};
+  f.hash_partial = hpart;
+  f.nhash = nhb;
+  f.point_partial = ppart;
+  f.npoint = npb;
+  f.R_given = Rw;
+  f.s_given = F ? nullptr : sb.s;
+  f.tableY = tableY;
+  f.tableG = ctx->tableG;
+  f.accept = d_acc;
+  f.status = ctx->status;
+  cudaEvent_t tb, te;
+  timer_begin(ctx, "finalize", ctx->s_main, &tb, &te);
+  k_finalize<<<1, kFinalThreads, 0, ctx->s_main>>>(f);
+  CU(cudaGetLastError());
+  timer_end(ctx, "finalize", ctx->s_main, tb, te);
+  uint8_t h_acc = 0;
+  CU(cudaMemcpyAsync(&h_acc, d_acc, 1, cudaMemcpyDeviceToHost, ctx->s_main));
+  if ((rc = check_status(ctx))) return rc;
+  *accept = h_acc;
+  return POSLO_OK;
+}
+
+int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_idx, uint64_t cap, uint64_t* n_invalid,
+                  uint8_t ccd_s[32], uint8_t ccd_R[32]) {
+  if (!ctx || !n_invalid) return fail(ctx, POSLO_EINVAL, "bad distill arguments");
+  int rc;
+  if ((rc = validate_batch(ctx, batch))) return rc;
+  if (batch->variant != POSLO_VARIANT_F) return fail(ctx, POSLO_EINVAL, "distill is entry-granular: POSLO-F batches");
+  const uint64_t n = batch->n;
+  if ((rc = reset_status(ctx))) return rc;
+  Staged sb;
+  if ((rc = stage_batch(ctx, batch, sb))) return rc;
+  uint32_t* tableY;
+  if ((rc = run_ytable(ctx, batch->Y, &tableY))) return rc;
+  uint8_t* d_e;
+  if ((rc = ensure_t(ctx, "e_all", 32 * std::max<uint64_t>(n, 1), &d_e))) return rc;
+  unsigned long long* hpart;
+  uint32_t nhb;
+  if ((rc = run_hash(ctx, batch, sb, d_e, false, true, nullptr, &hpart, &nhb))) return rc;
+  CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_table, 0));
+  uint8_t* d_inv;
+  if ((rc = ensure_t(ctx, "invalid", std::max<uint64_t>(n, 1), &d_inv))) return rc;
+  CheckArgs a{};
+  a.e = d_e;
+  a.s = sb.s;
+  a.R = sb.R;
+  a.n = n;
+  a.tableY = tableY;
+  a.tableG = ctx->tableG;
+  a.invalid = d_inv;
+  if (n) {
+    cudaEvent_t tb, te;
+    timer_begin(ctx, "check", ctx->s_main, &tb, &te);
+    k_entry_check<<<grid_for(ctx, n, 128, 8), 128, 0, ctx->s_main>>>(a);
+    CU(cudaGetLastError());
+    timer_end(ctx, "check", ctx->s_main, tb, te);
+  }
+  // ordered list of flagged entries
+  uint64_t* d_idx;
+  if ((rc = ensure_t(ctx, "invalid_idx", 8 * std::max<uint64_t>(std::min(cap, n), 1) + 8, &d_idx))) return rc;
+  uint64_t* d_cnt = d_idx + std::max<uint64_t>(std::min(cap, n), 1);
+  k_compact<<<1, kCompactThreads, 0, ctx->s_main>>>(d_inv, n, batch->first_index, d_idx, std::min(cap, n), d_cnt);
+  CU(cudaGetLastError());
+  // ccd^v = (sum of valid s_t mod q, sum of valid R_t)
+  uint8_t* d_ccd;
+  if ((rc = ensure_t(ctx, "ccd", 64, &d_ccd))) return rc;
+  {
+    const int blocks = grid_for(ctx, n, kHashThreads, 8);
+    unsigned long long* sp;
+    if ((rc = ensure_t(ctx, "ccd_spart", (size_t)blocks * 13 * 8, &sp))) return rc;
+    k_sum_scalars<<<blocks, kHashThreads, 0, ctx->s_main>>>(sb.s, n, d_inv, sp);
+    k_reduce_scalars<<<1, 32, 0, ctx->s_main>>>(sp, blocks, d_ccd);
+    CU(cudaGetLastError());
+    const int pblocks = grid_for(ctx, n, kPointThreads, 8);
+    uint32_t* pp;
+    if ((rc = ensure_t(ctx, "ccd_ppart", (size_t)pblocks * kPointPartialWords * 4, &pp))) return rc;
+    PointArgs pa{};
+    pa.R = sb.R;
+    pa.count = n;
+    pa.partial = pp;
+    pa.skip = d_inv;
+    k_points<<<pblocks, kPointThreads, 0, ctx->s_main>>>(pa);
+    k_sum_encode<<<1, kFinalThreads, 0, ctx->s_main>>>(pp, pblocks, nullptr, d_ccd + 32, nullptr);
+    CU(cudaGetLastError());
+  }
+  uint64_t cnt = 0;
+  uint8_t hccd[64];
+  CU(cudaMemcpyAsync(&cnt, d_cnt, 8, cudaMemcpyDeviceToHost, ctx->s_main));
+  CU(cudaMemcpyAsync(hccd, d_ccd, 64, cudaMemcpyDeviceToHost, ctx->s_main));
+  if ((rc = check_status(ctx))) return rc;
+  const uint64_t got = std::min(cnt, cap);
+  if (got && invalid_idx) CU(cudaMemcpy(invalid_idx, d_idx, 8 * got, cudaMemcpyDeviceToHost));
+  *n_invalid = cnt;
+  if (ccd_s) memcpy(ccd_s, hccd, 32);
+  if (ccd_R) memcpy(ccd_R, hccd + 32, 32);
+  if (cnt > cap) return fail(ctx, POSLO_EBUFSMALL, "%llu invalid entries, room for %llu", (unsigned long long)cnt,
+                             (unsigned long long)cap);
+  return POSLO_OK;
+}
+
+int poslo_msm(poslo_ctx* ctx, const uint8_t* points, const uint8_t* scalars, uint64_t n, uint32_t on_device,
+              uint8_t out[32]) {
+  if (!ctx || !out || (n && (!points || !scalars))) return fail(ctx, POSLO_EINVAL, "bad msm arguments");
+  int rc;
+  if ((rc = reset_status(ctx))) return rc;
+  const void *dp, *ds;
+  if ((rc = stage(ctx, "msm_pts", points, 32 * n, on_device, ctx->s_main, &dp))) return rc;
+  if ((rc = stage(ctx, "msm_sc", scalars, 32 * n, on_device, ctx->s_main, &ds))) return rc;
+  uint8_t* d_out;
+  uint32_t* d_bad;
+  if ((rc = ensure_t(ctx, "msm_out", 64, &d_out))) return rc;
+  d_bad = reinterpret_cast<uint32_t*>(d_out + 32);
+  if (n == 0) {
+    out[0] = 1;
+    memset(out + 1, 0, 31);
+    return POSLO_OK;
+  }
+  if ((rc = run_msm_direct(ctx, ctx->s_main, static_cast<const uint8_t*>(dp), nullptr,
+                           static_cast<const uint8_t*>(ds), 32, n, nullptr, nullptr, d_out, d_bad)))
+    return rc;
+  uint8_t h[36];
+  CU(cudaMemcpyAsync(h, d_out, 36, cudaMemcpyDeviceToHost, ctx->s_main));
+  if ((rc = check_status(ctx))) return rc;
+  uint32_t bad;
+  memcpy(&bad, h + 32, 4);
+  if (bad) return fail(ctx, POSLO_EINVAL, "%u points do not decode", bad);
+  memcpy(out, h, 32);
+  return POSLO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,300 @@
+"""ctypes binding of libposlo (include/poslo.h): argument marshalling only.
+
+Every computation of the verification path runs in the CUDA library.  Arrays may be numpy
+arrays (host memory) or torch CUDA tensors (device memory; the call then passes
+on_device = 1).  Loading fails loudly when the library has not been built: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libposlo.so")
+
+POSLO_OK = 0
+STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "EDEVICE", -4: "ETIMEOUT", -5: "EBUFSMALL", -6: "EBUSY",
+          -7: "ENOTFOUND"}
+VARIANT_C, VARIANT_F = 0, 1
+AGG_UNIT, AGG_WEIGHTED = 0, 1
+
+# Every entry point declared in include/poslo.h.
+EXPORTS = [
+    "poslo_create", "poslo_destroy", "poslo_last_error", "poslo_stream",
+    "poslo_keygen_c", "poslo_keygen_f", "poslo_sign_c", "poslo_sign_f", "poslo_disclose",
+    "poslo_aver", "poslo_distill", "poslo_epoch_seeds", "poslo_hash_entries", "poslo_msm",
+    "poslo_set_profiling", "poslo_kernel_time", "poslo_reset_kernel_times",
+]
+
+
+class PosloError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(C.Structure):
+    _fields_ = [("device", C.c_int), ("msm_window", C.c_uint32), ("mem_budget", C.c_uint64),
+                ("verifier_seed", C.c_uint8 * 32)]
+
+
+class Batch(C.Structure):
+    _fields_ = [("variant", C.c_uint32), ("n2", C.c_uint32), ("Y", C.c_void_p), ("msgs", C.c_void_p),
+                ("offs", C.c_void_p), ("n", C.c_uint64), ("first_index", C.c_uint64), ("s", C.c_void_p),
+                ("R", C.c_void_p), ("R_count", C.c_uint64), ("ds", C.c_void_p), ("ds_nodes", C.c_uint32),
+                ("on_device", C.c_uint32)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> C.CDLL:
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libposlo.so is not built ({path}); run __graft_entry__.build() "
+                          "or python -m paper_2506_08781_gb300.build — there is no CPU fallback")
+    lib = C.CDLL(path)
+    vp, u8p, u64, u32 = C.c_void_p, C.c_void_p, C.c_uint64, C.c_uint32
+    sig = {
+        "poslo_create": ([C.POINTER(Params), C.POINTER(vp)], C.c_int),
+        "poslo_destroy": ([vp], None),
+        "poslo_last_error": ([vp], C.c_char_p),
+        "poslo_stream": ([vp], vp),
+        "poslo_keygen_c": ([vp, u8p, u8p, u32, u32, u8p, u8p], C.c_int),
+        "poslo_keygen_f": ([vp, u8p, u8p, u32, u8p, u8p], C.c_int),
+        "poslo_sign_c": ([vp, u8p, u8p, u8p, u32, u32, u8p, vp, u64, u64, u8p], C.c_int),
+        "poslo_sign_f": ([vp, u8p, u8p, u32, u32, u8p, u8p, u32, u32, vp, u8p, vp, u64, u64, u8p, u8p, u8p],
+                         C.c_int),
+        "poslo_disclose": ([vp, u8p, u32, u64, u8p, u32, C.POINTER(u32)], C.c_int),
+        "poslo_aver": ([vp, C.POINTER(Batch), u32, u8p], C.c_int),
+        "poslo_distill": ([vp, C.POINTER(Batch), vp, u64, C.POINTER(u64), u8p, u8p], C.c_int),
+        "poslo_epoch_seeds": ([vp, u8p, u32, u64, u64, u8p], C.c_int),
+        "poslo_hash_entries": ([vp, C.POINTER(Batch), u8p], C.c_int),
+        "poslo_msm": ([vp, u8p, u8p, u64, u32, u8p], C.c_int),
+        "poslo_set_profiling": ([vp, C.c_int], C.c_int),
+        "poslo_kernel_time": ([vp, C.c_char_p, C.POINTER(C.c_double), C.POINTER(u64)], C.c_int),
+        "poslo_reset_kernel_times": ([vp], None),
+    }
+    for name in EXPORTS:
+        f = getattr(lib, name)
+        f.argtypes, f.restype = sig[name]
+    _lib = lib
+    return lib
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    """Host or device address of a numpy array, bytes, or torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if _is_torch(x):
+        return x.data_ptr()
+    if isinstance(x, (bytes, bytearray)):
+        buf = (C.c_uint8 * len(x)).from_buffer_copy(x)
+        _keep.append(buf)
+        return C.addressof(buf)
+    arr = np.ascontiguousarray(x)
+    if arr is not x:
+        _keep.append(arr)
+    return arr.ctypes.data
+
+
+_keep: list = []
+
+
+def _u8(x) -> np.ndarray:
+    if isinstance(x, (bytes, bytearray)):
+        return np.frombuffer(bytes(x), dtype=np.uint8).copy()
+    return np.ascontiguousarray(x, dtype=np.uint8).reshape(-1)
+
+
+@dataclass
+class BatchData:
+    """A batch as the caller holds it (numpy arrays or torch CUDA tensors)."""
+    variant: int
+    n2: int
+    Y: bytes
+    msgs: object
+    offs: object
+    n: int
+    first_index: int
+    s: object
+    R: object
+    R_count: int
+    ds: bytes
+    ds_nodes: int
+
+
+class Context:
+    """A libposlo context on one device."""
+
+    def __init__(self, device: int = 0, msm_window: int = 0, mem_budget: int = 0,
+                 verifier_seed: bytes = bytes(32)):
+        self.lib = load_library()
+        p = Params()
+        p.device = device
+        p.msm_window = msm_window
+        p.mem_budget = mem_budget
+        for i, b in enumerate(verifier_seed[:32]):
+            p.verifier_seed[i] = b
+        h = C.c_void_p()
+        rc = self.lib.poslo_create(C.byref(p), C.byref(h))
+        if rc != POSLO_OK:
+            raise PosloError(rc, "poslo_create failed (needs an sm_103 GPU)")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.poslo_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, rc: int):
+        _keep.clear()
+        if rc != POSLO_OK:
+            raise PosloError(rc, self.lib.poslo_last_error(self.h).decode())
+
+    @property
+    def stream(self) -> int:
+        return self.lib.poslo_stream(self.h) or 0
+
+    # ------------------------------------------------------------------ signer side
+    def keygen_c(self, y: bytes, r: bytes, D: int, n2: int):
+        Y = np.zeros(32, np.uint8)
+        R = np.zeros(32 << D, np.uint8)
+        self._check(self.lib.poslo_keygen_c(self.h, _ptr(y), _ptr(r), D, n2, _ptr(Y), _ptr(R)))
+        return Y.tobytes(), R
+
+    def keygen_f(self, y: bytes, bpv_r):
+        bpv_r = _u8(bpv_r)
+        v = len(bpv_r) // 32
+        Y = np.zeros(32, np.uint8)
+        R = np.zeros(32 * v, np.uint8)
+        self._check(self.lib.poslo_keygen_f(self.h, _ptr(y), _ptr(bpv_r), v, _ptr(Y), _ptr(R)))
+        return Y.tobytes(), R
+
+    def sign_c(self, y: bytes, r: bytes, root: bytes, D: int, n2: int, msgs, offs, first_epoch: int,
+               n_epochs: int):
+        s = np.zeros(32 * n_epochs, np.uint8)
+        offs = np.ascontiguousarray(offs, dtype=np.uint64)
+        self._check(self.lib.poslo_sign_c(self.h, _ptr(y), _ptr(r), _ptr(root), D, n2, _ptr(_u8(msgs)),
+                                          _ptr(offs), first_epoch, n_epochs, _ptr(s)))
+        return s
+
+    def sign_f(self, y: bytes, root: bytes, D: int, n2: int, bpv_r, bpv_R, subsets, msgs, offs,
+               first_index: int = 0, want_x: bool = False):
+        offs = np.ascontiguousarray(offs, dtype=np.uint64)
+        n = len(offs) - 1
+        subsets = np.ascontiguousarray(subsets, dtype=np.uint16)
+        k = subsets.shape[1] if subsets.ndim == 2 else 0
+        bpv_r, bpv_R = _u8(bpv_r), _u8(bpv_R)
+        s = np.zeros(32 * n, np.uint8)
+        R = np.zeros(32 * n, np.uint8)
+        x = np.zeros(16 * n, np.uint8) if want_x else None
+        self._check(self.lib.poslo_sign_f(self.h, _ptr(y), _ptr(root), D, n2, _ptr(bpv_r), _ptr(bpv_R),
+                                          len(bpv_r) // 32, k, _ptr(subsets), _ptr(_u8(msgs)), _ptr(offs), n,
+                                          first_index, _ptr(s), _ptr(R), _ptr(x)))
+        return (s, R, x) if want_x else (s, R)
+
+    def disclose(self, root: bytes, D: int, i: int) -> bytes:
+        cap = D + 2
+        out = np.zeros(24 * cap, np.uint8)
+        nodes = C.c_uint32()
+        self._check(self.lib.poslo_disclose(self.h, _ptr(root), D, i, _ptr(out), cap, C.byref(nodes)))
+        return out[:24 * nodes.value].tobytes()
+
+    # ------------------------------------------------------------------ verifier side
+    @staticmethod
+    def make_batch(variant: int, n2: int, Y: bytes, msgs, offs, s, R, ds: bytes, first_index: int = 0,
+                   R_count: int | None = None) -> BatchData:
+        if _is_torch(offs):
+            n = offs.numel() - 1
+        else:
+            offs = np.ascontiguousarray(offs, dtype=np.uint64)
+            n = len(offs) - 1
+            msgs, s, R = _u8(msgs), _u8(s), _u8(R)
+        if R_count is None:
+            R_count = n if variant == VARIANT_F else (len(R) // 32 if not _is_torch(R) else R.numel() // 32)
+        return BatchData(variant, n2, bytes(Y), msgs, offs, n, first_index, s, R, R_count, bytes(ds), len(ds) // 24)
+
+    def _cbatch(self, b: BatchData) -> Batch:
+        cb = Batch()
+        cb.variant, cb.n2 = b.variant, b.n2
+        cb.Y = _ptr(b.Y)
+        on_dev = _is_torch(b.offs)
+        cb.msgs, cb.offs, cb.s, cb.R = _ptr(b.msgs), _ptr(b.offs), _ptr(b.s), _ptr(b.R)
+        cb.n, cb.first_index, cb.R_count = b.n, b.first_index, b.R_count
+        cb.ds, cb.ds_nodes = _ptr(b.ds), b.ds_nodes
+        cb.on_device = 1 if on_dev else 0
+        return cb
+
+    def aver(self, b: BatchData, agg_mode: int = AGG_UNIT) -> bool:
+        acc = np.zeros(1, np.uint8)
+        cb = self._cbatch(b)
+        self._check(self.lib.poslo_aver(self.h, C.byref(cb), agg_mode, _ptr(acc)))
+        return bool(acc[0])
+
+    def distill(self, b: BatchData, cap: int | None = None):
+        cap = b.n if cap is None else cap
+        idx = np.zeros(max(cap, 1), np.uint64)
+        cnt = C.c_uint64()
+        cs = np.zeros(32, np.uint8)
+        cR = np.zeros(32, np.uint8)
+        cb = self._cbatch(b)
+        self._check(self.lib.poslo_distill(self.h, C.byref(cb), _ptr(idx), cap, C.byref(cnt), _ptr(cs), _ptr(cR)))
+        return idx[:cnt.value].copy(), cs.tobytes(), cR.tobytes()
+
+    def epoch_seeds(self, ds: bytes, first_epoch: int, n_epochs: int) -> np.ndarray:
+        out = np.zeros(16 * max(n_epochs, 1), np.uint8)
+        self._check(self.lib.poslo_epoch_seeds(self.h, _ptr(ds), len(ds) // 24, first_epoch, n_epochs, _ptr(out)))
+        return out[:16 * n_epochs].reshape(n_epochs, 16)
+
+    def hash_entries(self, b: BatchData, out=None):
+        cb = self._cbatch(b)
+        if out is None:
+            out = np.zeros(32 * max(b.n, 1), np.uint8)
+        self._check(self.lib.poslo_hash_entries(self.h, C.byref(cb), _ptr(out)))
+        return out
+
+    def msm(self, points, scalars, on_device: bool = False) -> bytes:
+        out = np.zeros(32, np.uint8)
+        if on_device:
+            n = points.numel() // 32
+        else:
+            points, scalars = _u8(points), _u8(scalars)
+            n = len(points) // 32
+        self._check(self.lib.poslo_msm(self.h, _ptr(points), _ptr(scalars), n, 1 if on_device else 0, _ptr(out)))
+        return out.tobytes()
+
+    # ------------------------------------------------------------------ profiling
+    def set_profiling(self, on: bool):
+        self._check(self.lib.poslo_set_profiling(self.h, 1 if on else 0))
+
+    def kernel_time(self, name: str):
+        ms = C.c_double()
+        n = C.c_uint64()
+        self.lib.poslo_kernel_time(self.h, name.encode(), C.byref(ms), C.byref(n))
+        return ms.value, n.value
+
+    def reset_kernel_times(self):
+        self.lib.poslo_reset_kernel_times(self.h)

@@ -1,0 +1,287 @@
+"""GPU parity: every step of the CUDA path against the CPU oracle, through the C ABI.
+
+Inputs come from the seeded generators (synth); signatures used as oracle inputs are made
+by the oracle's own signer.  All results are integers, points or bits, so every comparison
+is bit-exact.
+"""
+import numpy as np
+import pytest
+
+from oracle import poslo_oracle as O
+from paper_2506_08781_gb300 import poslo, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import __graft_entry__
+    __graft_entry__.build()
+    c = poslo.Context(device=0, verifier_seed=synth.verifier_seed(99))
+    yield c
+    c.close()
+
+
+def _f_data(seed, n, D, n2, lmin, lmax, v=32, k=4, first_index=0, msgs=None):
+    km = synth.key_material(seed, v=v)
+    sk, Y = O.kg_f(km.y, km.root, D, n2, km.bpv_r.tobytes())
+    if msgs is None:
+        msgs = synth.messages(seed, n, lmin, lmax)
+    subsets = synth.bpv_subsets(seed, n, first_index=first_index, v=v, k=k)
+    sig = [O.sig_f(sk, first_index + t, msgs.entry(t), subsets[t]) for t in range(n)]
+    return km, sk, Y, msgs, subsets, [x[0] for x in sig], [x[1] for x in sig], [x[2] for x in sig]
+
+
+# ------------------------------------------------------------------------------ A1 seeds
+
+@pytest.mark.parametrize("D", [3, 5])
+def test_epoch_seeds_every_ds(ctx, D):
+    root = synth.random_bytes(D, "root", 16).tobytes()
+    leaves = [O.tree_node(root, D, 0, i) for i in range(1 << D)]
+    for i in range(1 << D):
+        ds = O.ds_after(root, D, i)
+        got = ctx.epoch_seeds(O.ds_serialize(ds), 0, i + 1)
+        assert [bytes(r) for r in got] == leaves[:i + 1]
+
+
+def test_epoch_seeds_root_large_tree(ctx):
+    D = 12
+    root = synth.random_bytes(12, "root", 16).tobytes()
+    got = ctx.epoch_seeds(O.ds_serialize(O.ds_root(root, D)), 0, 1 << D)
+    for i in [0, 1, 2, 777, 2048, 4095]:
+        assert bytes(got[i]) == O.tree_node(root, D, 0, i)
+
+
+def test_epoch_seeds_not_disclosed_is_einval(ctx):
+    root = bytes(16)
+    ds = O.ds_serialize(O.ds_after(root, 4, 5))
+    with pytest.raises(poslo.PosloError) as e:
+        ctx.epoch_seeds(ds, 5, 2)          # epoch 6 is not disclosed yet
+    assert e.value.code == -1
+
+
+def test_disclose_matches_sso(ctx):
+    root = synth.random_bytes(3, "root", 16).tobytes()
+    for D, i in [(3, 0), (3, 5), (3, 6), (3, 7), (6, 37), (10, 1000)]:
+        assert ctx.disclose(root, D, i) == O.ds_serialize(O.ds_after(root, D, i))
+
+
+# ------------------------------------------------------------------------------ A2-A3 hashing
+
+def test_hash_every_length_and_alignment(ctx):
+    """Message lengths 0..300 (all SHA-256 padding boundaries) at every byte alignment."""
+    D, n2 = 6, 8
+    root = synth.random_bytes(4, "root", 16).tobytes()
+    ds = O.ds_root(root, D)
+    lens = list(range(0, 301))
+    entries = [synth.random_bytes(4, f"m{L}", L).tobytes() for L in lens]
+    for pad in range(4):
+        buf = bytes(pad) + b"".join(entries)
+        offs = np.zeros(len(entries) + 1, np.uint64)
+        offs[0] = pad
+        offs[1:] = pad + np.cumsum([len(m) for m in entries])
+        b = ctx.make_batch(poslo.VARIANT_F, n2, O.encode_point(O.G), np.frombuffer(buf, np.uint8), offs,
+                           bytes(32 * len(entries)), bytes(32 * len(entries)), O.ds_serialize(ds), first_index=3)
+        e = ctx.hash_entries(b).reshape(-1, 32)
+        for t, m in enumerate(entries):
+            want = O.entry_scalar(ds, n2, 3 + t, m)
+            assert int.from_bytes(bytes(e[t]), "little") == want, (pad, t)
+
+
+def test_hash_non_power_of_two_epoch(ctx):
+    D, n2 = 6, 5
+    root = synth.random_bytes(5, "root", 16).tobytes()
+    msgs = synth.messages(5, 200, 0, 130)
+    ds = O.ds_after(root, D, 45)
+    b = ctx.make_batch(poslo.VARIANT_F, n2, O.encode_point(O.G), msgs.data, msgs.offs, bytes(32 * 200),
+                       bytes(32 * 200), O.ds_serialize(ds), first_index=17)
+    e = ctx.hash_entries(b).reshape(-1, 32)
+    for t in range(200):
+        assert int.from_bytes(bytes(e[t]), "little") == O.entry_scalar(ds, n2, 17 + t, msgs.entry(t))
+
+
+# ------------------------------------------------------------------------------ signer parity
+
+def test_keygen_and_sign_f_match_oracle(ctx):
+    D, n2, n = 3, 8, 40
+    km, sk, Y, msgs, subsets, s, R, x = _f_data(7, n, D, n2, 0, 200, v=32, k=16)
+    gY, gR = ctx.keygen_f(km.y, km.bpv_r)
+    assert gY == Y
+    assert gR.tobytes() == b"".join(O.bpv_table_encoded(sk))
+    gs, gRt, gx = ctx.sign_f(km.y, km.root, D, n2, km.bpv_r, gR, subsets, msgs.data, msgs.offs, want_x=True)
+    assert gs.tobytes() == b"".join(s)
+    assert gRt.tobytes() == b"".join(R)
+    assert gx.tobytes() == b"".join(x)
+
+
+def test_keygen_and_sign_c_match_oracle(ctx):
+    D, n2 = 2, 16
+    km = synth.key_material(8)
+    sk, Y, epoch_R = O.kg_c(km.y, km.r, km.root, D, n2)
+    gY, gR = ctx.keygen_c(km.y, km.r, D, n2)
+    assert gY == Y and gR.tobytes() == b"".join(epoch_R)
+    msgs = synth.messages(8, n2 << D, 10, 90)
+    gs = ctx.sign_c(km.y, km.r, km.root, D, n2, msgs.data, msgs.offs, 0, 1 << D)
+    for i in range(1 << D):
+        assert gs[32 * i:32 * i + 32].tobytes() == O.sig_c(sk, i, [msgs.entry(i * n2 + j) for j in range(n2)])
+
+
+# ------------------------------------------------------------------------------ A4-A6 AVer
+
+@pytest.mark.parametrize("mode", [poslo.AGG_UNIT, poslo.AGG_WEIGHTED])
+def test_aver_f_config1_shape(ctx, mode):
+    """POSLO-F, 1,024 entries of 64 bytes: the valid copy accepts, a one-byte flip rejects."""
+    D, n2, n = 2, 256, 1024
+    km, sk, Y, msgs, subsets, s, R, _ = _f_data(1, n, D, n2, 64, 64)
+    ds = O.ds_serialize(O.ds_root(km.root, D))
+    b = ctx.make_batch(poslo.VARIANT_F, n2, Y, msgs.data, msgs.offs, b"".join(s), b"".join(R), ds)
+    assert ctx.aver(b, mode) is True
+    bad = synth.apply_tamper(msgs, synth.tamper_plan(1, msgs, 1))
+    tb = ctx.make_batch(poslo.VARIANT_F, n2, Y, bad.data, bad.offs, b"".join(s), b"".join(R), ds)
+    assert ctx.aver(tb, mode) is False
+    assert O.aver_f(Y, bad.as_list(), 0, n2, s, R, O.ds_root(km.root, D)) is False
+
+
+def test_aver_c_config1_shape(ctx):
+    """POSLO-C, n1 = 4 epochs of 256 entries of 64 bytes, both R~ forms of AVer step 2."""
+    D, n2 = 2, 256
+    km = synth.key_material(11)
+    sk, Y, epoch_R = O.kg_c(km.y, km.r, km.root, D, n2)
+    msgs = synth.messages(11, n2 << D, 64, 64)
+    s_ep = [O.sig_c(sk, i, [msgs.entry(i * n2 + j) for j in range(n2)]) for i in range(1 << D)]
+    s_all = O.agg_scalars(s_ep)
+    ds = O.ds_serialize(O.ds_root(km.root, D))
+    for R in (b"".join(epoch_R), O.agg_points(epoch_R)):
+        b = ctx.make_batch(poslo.VARIANT_C, n2, Y, msgs.data, msgs.offs, s_all, R, ds)
+        assert ctx.aver(b) is True
+        bad = synth.apply_tamper(msgs, synth.tamper_plan(11, msgs, 1))
+        tb = ctx.make_batch(poslo.VARIANT_C, n2, Y, bad.data, bad.offs, s_all, R, ds)
+        assert ctx.aver(tb) is False
+    # a subrange of epochs 1..2 under ds_2 with the per-epoch R~_i of those epochs
+    ds2 = O.ds_after(km.root, D, 2)
+    sub = synth.pack([msgs.entry(t) for t in range(n2, 3 * n2)])
+    b = ctx.make_batch(poslo.VARIANT_C, n2, Y, sub.data, sub.offs, O.agg_scalars(s_ep[1:3]),
+                       b"".join(epoch_R[1:3]), O.ds_serialize(ds2), first_index=n2)
+    assert ctx.aver(b) is True
+    assert O.aver_c(Y, [1, 2], [[msgs.entry(i * n2 + j) for j in range(n2)] for i in (1, 2)], n2,
+                    O.agg_scalars(s_ep[1:3]), epoch_R[1:3], ds2)
+
+
+def test_aver_s_shift_unit_accepts_weighted_rejects(ctx):
+    D, n2, n = 3, 4, 24
+    km, sk, Y, msgs, subsets, s, R, _ = _f_data(12, n, D, n2, 5, 50)
+    s2 = list(s)
+    s2[3] = O.scalar_to_bytes(int.from_bytes(s[3], "little") + 999)
+    s2[17] = O.scalar_to_bytes(int.from_bytes(s[17], "little") - 999)
+    ds = O.ds_serialize(O.ds_root(km.root, D))
+    b = ctx.make_batch(poslo.VARIANT_F, n2, Y, msgs.data, msgs.offs, b"".join(s2), b"".join(R), ds)
+    assert O.aver_f(Y, msgs.as_list(), 0, n2, s2, R, O.ds_root(km.root, D)) is True
+    assert ctx.aver(b, poslo.AGG_UNIT) is True          # the paper's unit aggregate
+    assert ctx.aver(b, poslo.AGG_WEIGHTED) is False     # = per-entry definition
+    idx, _, _ = ctx.distill(b)
+    assert list(idx) == [3, 17]
+
+
+def test_aver_malformed_and_errors(ctx):
+    D, n2, n = 2, 4, 10
+    km, sk, Y, msgs, subsets, s, R, _ = _f_data(13, n, D, n2, 1, 40)
+    ds = O.ds_serialize(O.ds_root(km.root, D))
+    s_bad = list(s)
+    s_bad[2] = (int.from_bytes(s[2], "little") + O.Q).to_bytes(32, "little")
+    y = 2
+    while O.decode_point(y.to_bytes(32, "little")) is not None:
+        y += 1
+    R_bad = list(R)
+    R_bad[7] = y.to_bytes(32, "little")
+    for ss, RR, want in [(s_bad, R, [2]), (s, R_bad, [7]), (s_bad, R_bad, [2, 7])]:
+        b = ctx.make_batch(poslo.VARIANT_F, n2, Y, msgs.data, msgs.offs, b"".join(ss), b"".join(RR), ds)
+        for mode in (poslo.AGG_UNIT, poslo.AGG_WEIGHTED):
+            assert ctx.aver(b, mode) is False
+        idx, cs, cR = ctx.distill(b)
+        wi, ws, wR = O.distill_f(Y, msgs.as_list(), 0, n2, ss, RR, O.ds_root(km.root, D))
+        assert list(idx) == wi == want and cs == ws and cR == wR
+    # undecodable public key, undisclosed seed, wrong R_count: errors, not reject bits
+    b = ctx.make_batch(poslo.VARIANT_F, n2, y.to_bytes(32, "little"), msgs.data, msgs.offs, b"".join(s),
+                       b"".join(R), ds)
+    with pytest.raises(poslo.PosloError):
+        ctx.aver(b)
+    b = ctx.make_batch(poslo.VARIANT_F, n2, Y, msgs.data, msgs.offs, b"".join(s), b"".join(R),
+                       O.ds_serialize(O.ds_after(km.root, D, 1)))
+    with pytest.raises(poslo.PosloError):
+        ctx.aver(b)
+
+
+def test_aver_empty_and_single(ctx):
+    D, n2 = 2, 4
+    km, sk, Y, msgs, subsets, s, R, _ = _f_data(14, 1, D, n2, 0, 0)
+    ds = O.ds_serialize(O.ds_root(km.root, D))
+    e = synth.pack([])
+    b = ctx.make_batch(poslo.VARIANT_F, n2, Y, e.data, e.offs, b"", b"", ds)
+    assert ctx.aver(b) is O.aver_f(Y, [], 0, n2, [], [], O.ds_root(km.root, D)) is True
+    idx, cs, cR = ctx.distill(b)
+    assert len(idx) == 0 and cs == bytes(32) and cR == O.encode_point(O.IDENTITY)
+    b = ctx.make_batch(poslo.VARIANT_F, n2, Y, msgs.data, msgs.offs, s[0], R[0], ds)
+    assert ctx.aver(b) is True and ctx.aver(b, poslo.AGG_WEIGHTED) is True
+
+
+# ------------------------------------------------------------------------------ A7 Distill
+
+def test_distill_random_patterns_ragged(ctx):
+    D, n2, n = 4, 16, 150
+    km, sk, Y, msgs, subsets, s, R, _ = _f_data(15, n, D, n2, 0, 260)
+    ds_l = O.ds_root(km.root, D)
+    ds = O.ds_serialize(ds_l)
+    for trial, count in enumerate([0, 1, 5, 40]):
+        nz = synth.pack([m for m in msgs.as_list()])
+        if count:
+            # only non-empty entries can be flipped
+            cand = [t for t in range(n) if len(msgs.entry(t))]
+            pick = synth.choose_without_replacement(15 + trial, "pick", len(cand), count)
+            data = nz.data.copy()
+            for q in pick:
+                t = cand[q]
+                data[int(nz.offs[t])] ^= 0x5A
+            nz = synth.Messages(data, nz.offs)
+        b = ctx.make_batch(poslo.VARIANT_F, n2, Y, nz.data, nz.offs, b"".join(s), b"".join(R), ds)
+        idx, cs, cR = ctx.distill(b)
+        wi, ws, wR = O.distill_f(Y, nz.as_list(), 0, n2, s, R, ds_l)
+        assert list(idx) == wi and cs == ws and cR == wR
+
+
+def test_distill_capacity(ctx):
+    D, n2, n = 2, 8, 16
+    km, sk, Y, msgs, subsets, s, R, _ = _f_data(16, n, D, n2, 8, 8)
+    ds = O.ds_serialize(O.ds_root(km.root, D))
+    bad = synth.apply_tamper(msgs, synth.tamper_plan(16, msgs, 5))
+    b = ctx.make_batch(poslo.VARIANT_F, n2, Y, bad.data, bad.offs, b"".join(s), b"".join(R), ds)
+    with pytest.raises(poslo.PosloError) as e:
+        ctx.distill(b, cap=3)
+    assert e.value.code == -5
+
+
+# ------------------------------------------------------------------------------ MSM
+
+def test_msm_matches_oracle(ctx):
+    n = 37
+    pts = [O.encode_point(O.scalar_mult(3 + 11 * i, O.G)) for i in range(n)]
+    ks = [int.from_bytes(synth.random_bytes(17, f"k{i}", 32).tobytes(), "little") for i in range(n)]
+    got = ctx.msm(b"".join(pts), b"".join(k.to_bytes(32, "little") for k in ks))
+    assert got == O.msm(ks, pts)
+
+
+# ------------------------------------------------------------------------------ device inputs
+
+def test_device_inputs_same_as_host(ctx):
+    import torch
+    D, n2, n = 3, 8, 64
+    km, sk, Y, msgs, subsets, s, R, _ = _f_data(18, n, D, n2, 20, 200)
+    ds = O.ds_serialize(O.ds_root(km.root, D))
+    bad = synth.apply_tamper(msgs, synth.tamper_plan(18, msgs, 3))
+    hb = ctx.make_batch(poslo.VARIANT_F, n2, Y, bad.data, bad.offs, b"".join(s), b"".join(R), ds)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    db = ctx.make_batch(poslo.VARIANT_F, n2, Y, dev(bad.data), dev(bad.offs.astype(np.int64)),
+                        dev(np.frombuffer(b"".join(s), np.uint8)), dev(np.frombuffer(b"".join(R), np.uint8)), ds)
+    torch.cuda.synchronize()
+    assert ctx.aver(hb) is ctx.aver(db) is False
+    assert [list(x) if i == 0 else x for i, x in enumerate(ctx.distill(hb))] == \
+           [list(x) if i == 0 else x for i, x in enumerate(ctx.distill(db))]
