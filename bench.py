@@ -1,0 +1,402 @@
+"""Benchmark: verified POSLO log entries per second on one GB300 (AVer + Distill).
+
+One step = one poslo_distill call over the large single-signer workload: 2^20 POSLO-F
+entries, message lengths uniform in [32, 256] bytes, epochs of n2 = 256 (n1 = 4096, the
+seed tree's root disclosed), all entries valid.  The call runs every stage of the hot path:
+epoch seeds (SRet), per-entry PRF and H (SHA-256), scalar aggregation mod q, decoding of
+the 2^20 commitments R_t, their aggregation, the cofactored group check, and the
+localisation of invalid entries with the ccd^v aggregate of the valid ones.
+
+Inputs are resident in HBM when the timed region starts (value); the e2e figure repeats the
+step through the same C-ABI call with pinned host buffers, so the host-to-device copies of
+the inputs and the device-to-host copy of the results are inside its timed region.  The
+inputs (151 MB of messages + 64 MB of signatures) exceed the 129 MB L2 between steps.
+
+--impl reference times the CPU oracle (the plain per-entry definition) on a bounded sample
+of the same workload on this machine's host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import json
+import multiprocessing as mp
+import os
+import statistics
+import struct
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_ENTRIES = 1 << 20
+N2 = 256
+D = 12
+LMIN, LMAX = 32, 256
+SEED = 2
+
+WORKLOAD = ("POSLO-F AVer+Distill, single signer: N=2^20 entries, |m|~U[32,256] B, n2=256, "
+            "n1=4096 (root disclosed), all valid, edwards25519 + SHA-256")
+
+
+# ------------------------------------------------------------------------------ helpers
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def probe_int_peaks(device: int) -> dict:
+    from paper_2506_08781_gb300 import build
+    lib = C.CDLL(build.PROBE_LIB)
+    out = (C.c_double * 5)()
+    rc = lib.poslo_probe_int_peaks(device, out)
+    if rc != 0:
+        return {}
+    return {"imad_lo_ops": out[0], "imad_hi_ops": out[1], "lop3_ops": out[2], "iadd_ops": out[3],
+            "shf_ops": out[4]}
+
+
+# Algorithmic integer work per entry for the roofline (counted from the algorithms, not
+# from the compiled code):
+#   decoding R_t: 255 squarings + 20 multiplications in F_p; a schoolbook 8x8-limb product
+#     is 64 low + 64 high 32-bit multiply-adds, a squaring 36 + 36, each followed by a
+#     16 multiply-add fold by 38  -> 255*(72+18) + 20*(128+18) = 25,870 IMAD per entry
+#   SHA-256: 1,384 ALU instructions per compression with 3-input LOP3/IADD3 and funnel
+#     shifts (64 rounds x 14 + 48 schedule words x 10 + 8); compressions per entry =
+#     1 (PRF) + ceil((L + 25) / 64) (H)
+IMAD_PER_DECODE = 255 * (72 + 18) + 20 * (128 + 18)
+ALU_PER_COMPRESSION = 64 * 14 + 48 * 10 + 8
+
+
+def make_workload(n=N_ENTRIES, seed=SEED, tamper=0):
+    from paper_2506_08781_gb300 import synth
+    km = synth.key_material(seed)
+    msgs = synth.messages(seed, n, LMIN, LMAX)
+    subsets = synth.bpv_subsets(seed, n)
+    plan = synth.tamper_plan(seed, msgs, tamper) if tamper else None
+    return km, msgs, subsets, plan
+
+
+def sign_workload(ctx, km, msgs, subsets):
+    Y, bpv_R = ctx.keygen_f(km.y, km.bpv_r)
+    s, R = ctx.sign_f(km.y, km.root, D, N2, km.bpv_r, bpv_R, subsets, msgs.data, msgs.offs)
+    return Y, s, R
+
+
+def compressions(msgs) -> int:
+    L = (msgs.offs[1:] - msgs.offs[:-1]).astype(np.int64)
+    return int(np.sum(1 + (L + 16 + 9 + 63) // 64))
+
+
+# ------------------------------------------------------------------------------ CPU oracle arm
+
+def _oracle_worker(args):
+    Y, entries, first, s, R, ds_ser = args
+    from oracle import poslo_oracle as O
+    ds = [O.Node(*struct.unpack("<II", ds_ser[24 * k:24 * k + 8]), ds_ser[24 * k + 8:24 * k + 24])
+          for k in range(len(ds_ser) // 24)]
+    t0 = time.perf_counter()
+    inv, _, _ = O.distill_f(Y, entries, first, N2, s, R, ds)
+    return time.perf_counter() - t0, len(entries), len(inv)
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+class OracleSample:
+    """A bounded sample of the workload signed by the oracle's own signer, verified by the
+    oracle's per-entry Distill (which also decides AVer) in one spawned process per core."""
+
+    def __init__(self, n: int, cores: int):
+        from oracle import poslo_oracle as O
+        from paper_2506_08781_gb300 import synth
+        self.cores = cores
+        km = synth.key_material(SEED, v=64)
+        sk, self.Y = O.kg_f(km.y, km.root, D, N2, km.bpv_r.tobytes())
+        msgs = synth.messages(SEED, n, LMIN, LMAX)
+        subsets = synth.bpv_subsets(SEED, n, v=64)
+        self.entries = msgs.as_list()
+        sig = [O.sig_f(sk, t, self.entries[t], subsets[t]) for t in range(n)]
+        self.s = [x[0] for x in sig]
+        self.R = [x[1] for x in sig]
+        self.ds = O.ds_serialize(O.ds_root(km.root, D))
+        self.pool = mp.get_context("spawn").Pool(cores)
+
+    def run(self, lo: int, per_core: int):
+        jobs = []
+        for c in range(self.cores):
+            a, b = lo + c * per_core, lo + (c + 1) * per_core
+            jobs.append((self.Y, self.entries[a:b], a, self.s[a:b], self.R[a:b], self.ds))
+        t0 = time.perf_counter()
+        res = self.pool.map(_oracle_worker, jobs)
+        wall = time.perf_counter() - t0
+        return self.cores * per_core, max(r[0] for r in res), wall
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_oracle_baseline(per_core: int = 256):
+    cores = host_cores()
+    smp = OracleSample(cores * per_core, cores)
+    try:
+        n, busy, wall = smp.run(0, per_core)
+    finally:
+        smp.close()
+    return {"value": n / busy, "unit": "entries/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} entries of the same workload ({per_core} per core, one spawned process per core); "
+                      f"per-entry Distill (the definition); slowest core {busy:.1f} s, pool wall {wall:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    cores = host_cores()
+    per_step = max(4, args.cpu_per_core // 8)
+    smp = OracleSample(cores * per_step * (args.steps + args.warmup), cores)
+    try:
+        for w in range(args.warmup):
+            smp.run(w * cores * per_step, per_step)
+        tot_n, tot_t = 0, 0.0
+        for k in range(args.steps):
+            n, busy, wall = smp.run((args.warmup + k) * cores * per_step, per_step)
+            tot_n += n
+            tot_t += wall
+    finally:
+        smp.close()
+    value = tot_n / tot_t
+    sample = (f"{cores * per_step} entries per step ({per_step} per core, one spawned process per core), "
+              f"per-entry Distill (the definition)")
+    line = {"impl": "reference", "metric": "verified log entries/sec at 1 GB300 (AVer+Distill)",
+            "value": value, "unit": "entries/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot_t / max(args.steps, 1), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": value, "unit": "entries/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "entries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------ GPU arm
+
+def run_ours(args):
+    import torch
+    import __graft_entry__
+    from paper_2506_08781_gb300 import poslo, synth
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    device = local
+    torch.cuda.set_device(device)
+    __graft_entry__.build()
+    ctx = poslo.Context(device=device, verifier_seed=synth.verifier_seed(1000 + rank))
+    km, msgs, subsets, _ = make_workload(seed=SEED + rank)
+    Y, s, R = sign_workload(ctx, km, msgs, subsets)
+    ds = struct.pack("<II", D, 0) + km.root      # final disclosure: the root x_D[0] alone
+    n = msgs.n
+
+    # device-resident inputs
+    d_msgs = torch.from_numpy(msgs.data).cuda()
+    d_offs = torch.from_numpy(msgs.offs.view(np.int64)).cuda()
+    d_s = torch.from_numpy(s).cuda()
+    d_R = torch.from_numpy(R).cuda()
+    torch.cuda.synchronize()
+    batch = ctx.make_batch(poslo.VARIANT_F, N2, Y, d_msgs, d_offs, d_s, d_R, ds)
+
+    def step(b):
+        idx, cs, cR = ctx.distill(b)
+        return idx
+
+    for _ in range(args.warmup):
+        idx = step(batch)
+    assert len(idx) == 0, "all-valid workload reported invalid entries"
+
+    stream = torch.cuda.ExternalStream(ctx.stream)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ctx.set_profiling(True)
+    ctx.reset_kernel_times()
+    launches0 = ctx.kernel_time("*")[1]
+    with ClockSampler(device) as clk:
+        ev0.record(stream)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step(batch)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    ms = ev0.elapsed_time(ev1) / args.steps
+    gpu_launches = ctx.kernel_time("*")[1] - launches0
+    kernels = {}
+    for name in ("seeds", "hash", "points", "table", "msm", "check", "finalize", "compact"):
+        tot, cnt = ctx.kernel_time(name)
+        if cnt:
+            kernels[name] = {"ms_per_launch": tot / cnt, "launches": cnt}
+    ctx.set_profiling(False)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n / (ms * 1e-3)
+
+    # unit AVer (the paper's equation) on the same resident inputs, for context
+    for _ in range(2):
+        ctx.aver(batch, poslo.AGG_UNIT)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.aver(batch, poslo.AGG_UNIT)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    aver_ms = e0.elapsed_time(e1) / args.steps
+
+    # end to end through the C ABI from pinned host memory
+    p_msgs = torch.from_numpy(msgs.data).pin_memory()
+    p_offs = torch.from_numpy(msgs.offs.view(np.int64)).pin_memory()
+    p_s = torch.from_numpy(s).pin_memory()
+    p_R = torch.from_numpy(R).pin_memory()
+    hbatch = ctx.make_batch(poslo.VARIANT_F, N2, Y, p_msgs, p_offs, p_s, p_R, ds)
+    for _ in range(2):
+        step(hbatch)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        idx = step(hbatch)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    h2d = msgs.data.nbytes + msgs.offs.nbytes + s.nbytes + R.nbytes + 32 + len(ds)
+    d2h = 8 * len(idx) + 64 + 8
+
+    # roofline of the dominant kernel
+    peaks = probe_int_peaks(device)
+    dom = max(kernels, key=lambda k: kernels[k]["ms_per_launch"]) if kernels else None
+    roof = None
+    if dom in ("points", "check") and peaks:
+        work = n * IMAD_PER_DECODE
+        ach = work / (kernels[dom]["ms_per_launch"] * 1e-3) / 1e9
+        pk = peaks["imad_lo_ops"] / 1e9
+        roof = {"bound": "alu", "pipe": "IMAD", "kernel": dom, "achieved": ach, "peak": pk, "unit": "Gop/s",
+                "frac": ach / pk, "traffic": None,
+                "peak_source": "probed mad.lo.u32 issue rate on this GPU (probe/peaks.cu)",
+                "work": "25,870 IMAD per R_t decode (schoolbook count)"}
+    elif dom == "hash" and peaks:
+        work = compressions(msgs) * ALU_PER_COMPRESSION
+        ach = work / (kernels[dom]["ms_per_launch"] * 1e-3) / 1e9
+        pk = peaks["lop3_ops"] / 1e9
+        roof = {"bound": "alu", "pipe": "ALU", "kernel": dom, "achieved": ach, "peak": pk, "unit": "Gop/s",
+                "frac": ach / pk, "traffic": None, "peak_source": "probed lop3 issue rate on this GPU",
+                "work": "1,384 ALU ops per SHA-256 compression"}
+    clocks = clk.summary()
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            cpu = cpu_oracle_baseline(per_core=args.cpu_per_core)
+        line = {
+            "metric": "verified log entries/sec at 1 GB300 (AVer+Distill)",
+            "value": value, "unit": "entries/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic (seeded SplitMix64 messages; keys and signatures made by "
+                                    "poslo_keygen_f/poslo_sign_f)",
+            "config": {"workload": WORKLOAD, "entries_per_gpu": n, "message_bytes": int(msgs.data.nbytes),
+                       "l2": "inputs (215 MB) larger than the 129 MB L2; no flush", "parallelism": f"dp{world}"},
+            "clocks": clocks,
+            "gpu_launches": gpu_launches,
+            "kernels": kernels,
+            "aver_unit": {"value": n / (aver_ms * 1e-3), "ms_per_step": aver_ms},
+            "e2e": {"value": world * n / e2e_s, "unit": "entries/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "roofline": roof,
+            "int_peaks": peaks,
+            "cpu_baseline": cpu,
+            "wall_s_timed": wall,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-per-core", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -49,6 +49,7 @@ struct poslo_ctx {
   uint32_t* h_status = nullptr;   // pinned mirror
   std::string err;
   bool profiling = false;
+  uint64_t launch_count = 0;   // kernels launched by this context
   std::map<std::string, KernelTimer> timers;
   std::vector<std::pair<std::string, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
   std::vector<cudaEvent_t> event_pool;
@@ -232,6 +233,7 @@ int run_epoch_seeds(poslo_ctx* ctx, const uint8_t* ds, uint32_t nodes, uint64_t 
     timer_begin(ctx, "seeds", ctx->s_main, &b, &e);
     k_epoch_seeds<<<(unsigned)blocks, threads, 0, ctx->s_main>>>(d_ds, (int)h.size(), first_epoch, n_epochs, seeds,
                                                                 ctx->status);
+                                                                ++ctx->launch_count;
     CU(cudaGetLastError());
     timer_end(ctx, "seeds", ctx->s_main, b, e);
   }
@@ -340,6 +342,7 @@ int run_hash(poslo_ctx* ctx, const poslo_batch* b, const Staged& sb, uint8_t* e_
   cudaEvent_t tb, te;
   timer_begin(ctx, "hash", ctx->s_main, &tb, &te);
   k_hash<<<blocks, kHashThreads, 0, ctx->s_main>>>(a);
+  ++ctx->launch_count;
   CU(cudaGetLastError());
   timer_end(ctx, "hash", ctx->s_main, tb, te);
   *partial_out = partial;
@@ -360,6 +363,7 @@ int run_ytable(poslo_ctx* ctx, const uint8_t* Y, uint32_t** table_out) {
   cudaEvent_t tb, te;
   timer_begin(ctx, "table", ctx->s_table, &tb, &te);
   k_table<<<1, kTableWindows, 0, ctx->s_table>>>(d_Y, tableY, ctx->status, 0);
+  ++ctx->launch_count;
   CU(cudaGetLastError());
   timer_end(ctx, "table", ctx->s_table, tb, te);
   CU(cudaEventRecord(ctx->ev_table, ctx->s_table));
@@ -384,6 +388,7 @@ int run_points(poslo_ctx* ctx, const uint8_t* R, uint64_t count, uint32_t* affin
   cudaEvent_t tb, te;
   timer_begin(ctx, "points", ctx->s_points, &tb, &te);
   k_points<<<blocks, kPointThreads, 0, ctx->s_points>>>(a);
+  ++ctx->launch_count;
   CU(cudaGetLastError());
   timer_end(ctx, "points", ctx->s_points, tb, te);
   CU(cudaEventRecord(ctx->ev_points, ctx->s_points));
@@ -410,8 +415,10 @@ int run_msm_direct(poslo_ctx* ctx, cudaStream_t st, const uint8_t* points, const
   cudaEvent_t tb, te;
   timer_begin(ctx, "msm", st, &tb, &te);
   k_msm_direct<<<blocks, kPointThreads, 0, st>>>(a);
+  ++ctx->launch_count;
   CU(cudaGetLastError());
   k_sum_encode<<<1, kFinalThreads, 0, st>>>(partial, blocks, point_out, enc_out, bad_out);
+  ++ctx->launch_count;
   CU(cudaGetLastError());
   timer_end(ctx, "msm", st, tb, te);
   return POSLO_OK;
@@ -459,6 +466,7 @@ int poslo_create(const poslo_params* params, poslo_ctx** out) {
   if (cudaMalloc(&ctx->tableG, kTableWindows * kTableDigits * 128) != cudaSuccess) return bail(POSLO_ENOMEM);
   cudaMemsetAsync(ctx->status, 0, 4, ctx->s_main);
   k_table<<<1, kTableWindows, 0, ctx->s_main>>>(nullptr, ctx->tableG, ctx->status, 1);
+  ++ctx->launch_count;
   if (cudaStreamSynchronize(ctx->s_main) != cudaSuccess) return bail(POSLO_EDEVICE);
   *out = ctx;
   return POSLO_OK;
@@ -502,6 +510,11 @@ int poslo_set_profiling(poslo_ctx* ctx, int enabled) {
 int poslo_kernel_time(poslo_ctx* ctx, const char* name, double* total_ms, uint64_t* launches) {
   if (!ctx || !name) return POSLO_EINVAL;
   timers_collect(ctx);
+  if (strcmp(name, "*") == 0) {   // every kernel this context launched, untimed
+    if (total_ms) *total_ms = 0;
+    if (launches) *launches = ctx->launch_count;
+    return POSLO_OK;
+  }
   auto it = ctx->timers.find(name);
   if (it == ctx->timers.end()) {
     if (total_ms) *total_ms = 0;
@@ -532,8 +545,10 @@ int poslo_keygen_c(poslo_ctx* ctx, const uint8_t y[32], const uint8_t r[32], uin
   CU(cudaMemcpyAsync(d_in, y, 32, cudaMemcpyHostToDevice, ctx->s_main));
   CU(cudaMemcpyAsync(d_in + 32, r, 32, cudaMemcpyHostToDevice, ctx->s_main));
   k_keygen_y<<<1, 1, 0, ctx->s_main>>>(d_in, ctx->tableG, d_out);
+  ++ctx->launch_count;
   k_keygen_c_epochs<<<(unsigned)((n1 + 63) / 64), 64, 0, ctx->s_main>>>(d_in + 32, (uint32_t)n1, n2, ctx->tableG,
                                                                          d_out + 32);
+                                                                         ++ctx->launch_count;
   CU(cudaGetLastError());
   CU(cudaMemcpyAsync(Y_out, d_out, 32, cudaMemcpyDeviceToHost, ctx->s_main));
   if (epoch_R_out) CU(cudaMemcpyAsync(epoch_R_out, d_out + 32, 32 * n1, cudaMemcpyDeviceToHost, ctx->s_main));
@@ -552,7 +567,9 @@ int poslo_keygen_f(poslo_ctx* ctx, const uint8_t y[32], const uint8_t* bpv_r, ui
   CU(cudaMemcpyAsync(d_y, y, 32, cudaMemcpyHostToDevice, ctx->s_main));
   if (v) CU(cudaMemcpyAsync(d_r, bpv_r, 32 * (size_t)v, cudaMemcpyHostToDevice, ctx->s_main));
   k_keygen_y<<<1, 1, 0, ctx->s_main>>>(d_y, ctx->tableG, d_out);
+  ++ctx->launch_count;
   if (v) k_keygen_bpv<<<(v + 63) / 64, 64, 0, ctx->s_main>>>(d_r, v, ctx->tableG, d_out + 32);
+  ++ctx->launch_count;
   CU(cudaGetLastError());
   CU(cudaMemcpyAsync(Y_out, d_out, 32, cudaMemcpyDeviceToHost, ctx->s_main));
   if (v) CU(cudaMemcpyAsync(bpv_R_out, d_out + 32, 32 * (size_t)v, cudaMemcpyDeviceToHost, ctx->s_main));
@@ -602,6 +619,7 @@ int poslo_sign_f(poslo_ctx* ctx, const uint8_t y[32], const uint8_t root[16], ui
   uint32_t* pts;
   if ((rc = ensure_t(ctx, "sig_bpv_pts", 128 * (size_t)v, &pts))) return rc;
   k_decode_table<<<(v + 63) / 64, 64, 0, ctx->s_main>>>(d_bpvR, v, pts, ctx->status);
+  ++ctx->launch_count;
   if ((rc = stage(ctx, "sig_subsets", subsets, 2 * n * k, false, ctx->s_main, &p))) return rc;
   a.subsets = static_cast<const uint16_t*>(p);
   uint8_t *d_s, *d_R, *d_x = nullptr;
@@ -621,6 +639,7 @@ int poslo_sign_f(poslo_ctx* ctx, const uint8_t y[32], const uint8_t root[16], ui
   a.R_out = d_R;
   a.x_out = d_x;
   k_sign_f<<<(unsigned)((n + 127) / 128), 128, 0, ctx->s_main>>>(a);
+  ++ctx->launch_count;
   CU(cudaGetLastError());
   CU(cudaMemcpyAsync(s_out, d_s, 32 * n, cudaMemcpyDeviceToHost, ctx->s_main));
   CU(cudaMemcpyAsync(R_out, d_R, 32 * n, cudaMemcpyDeviceToHost, ctx->s_main));
@@ -665,6 +684,7 @@ int poslo_sign_c(poslo_ctx* ctx, const uint8_t y[32], const uint8_t r[32], const
   a.r = d_yr + 32;
   a.s_out = d_s;
   k_sign_c<<<(unsigned)((n_epochs + 63) / 64), 64, 0, ctx->s_main>>>(a);
+  ++ctx->launch_count;
   CU(cudaGetLastError());
   CU(cudaMemcpyAsync(s_out, d_s, 32 * n_epochs, cudaMemcpyDeviceToHost, ctx->s_main));
   return check_status(ctx);
@@ -809,6 +829,7 @@ int poslo_aver(poslo_ctx* ctx, const poslo_batch* batch, uint32_t agg_mode, uint
   cudaEvent_t tb, te;
   timer_begin(ctx, "finalize", ctx->s_main, &tb, &te);
   k_finalize<<<1, kFinalThreads, 0, ctx->s_main>>>(f);
+  ++ctx->launch_count;
   CU(cudaGetLastError());
   timer_end(ctx, "finalize", ctx->s_main, tb, te);
   uint8_t h_acc = 0;
@@ -850,6 +871,7 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
     cudaEvent_t tb, te;
     timer_begin(ctx, "check", ctx->s_main, &tb, &te);
     k_entry_check<<<grid_for(ctx, n, 128, 8), 128, 0, ctx->s_main>>>(a);
+    ++ctx->launch_count;
     CU(cudaGetLastError());
     timer_end(ctx, "check", ctx->s_main, tb, te);
   }
@@ -858,6 +880,7 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
   if ((rc = ensure_t(ctx, "invalid_idx", 8 * std::max<uint64_t>(std::min(cap, n), 1) + 8, &d_idx))) return rc;
   uint64_t* d_cnt = d_idx + std::max<uint64_t>(std::min(cap, n), 1);
   k_compact<<<1, kCompactThreads, 0, ctx->s_main>>>(d_inv, n, batch->first_index, d_idx, std::min(cap, n), d_cnt);
+  ++ctx->launch_count;
   CU(cudaGetLastError());
   // ccd^v = (sum of valid s_t mod q, sum of valid R_t)
   uint8_t* d_ccd;
@@ -867,7 +890,9 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
     unsigned long long* sp;
     if ((rc = ensure_t(ctx, "ccd_spart", (size_t)blocks * 13 * 8, &sp))) return rc;
     k_sum_scalars<<<blocks, kHashThreads, 0, ctx->s_main>>>(sb.s, n, d_inv, sp);
+    ++ctx->launch_count;
     k_reduce_scalars<<<1, 32, 0, ctx->s_main>>>(sp, blocks, d_ccd);
+    ++ctx->launch_count;
     CU(cudaGetLastError());
     const int pblocks = grid_for(ctx, n, kPointThreads, 8);
     uint32_t* pp;
@@ -878,7 +903,9 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
     pa.partial = pp;
     pa.skip = d_inv;
     k_points<<<pblocks, kPointThreads, 0, ctx->s_main>>>(pa);
+    ++ctx->launch_count;
     k_sum_encode<<<1, kFinalThreads, 0, ctx->s_main>>>(pp, pblocks, nullptr, d_ccd + 32, nullptr);
+    ++ctx->launch_count;
     CU(cudaGetLastError());
   }
   uint64_t cnt = 0;

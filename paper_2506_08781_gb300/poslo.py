@@ -241,7 +241,7 @@ class Context:
         cb = Batch()
         cb.variant, cb.n2 = b.variant, b.n2
         cb.Y = _ptr(b.Y)
-        on_dev = _is_torch(b.offs)
+        on_dev = _is_torch(b.offs) and b.offs.is_cuda
         cb.msgs, cb.offs, cb.s, cb.R = _ptr(b.msgs), _ptr(b.offs), _ptr(b.s), _ptr(b.R)
         cb.n, cb.first_index, cb.R_count = b.n, b.first_index, b.R_count
         cb.ds, cb.ds_nodes = _ptr(b.ds), b.ds_nodes
