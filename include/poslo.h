@@ -17,7 +17,7 @@
  *           (ds, Sec. 4.1) is an array of nodes with the bottom of the stack first.
  *   messages: one byte buffer plus n+1 uint64 offsets; entry t is msgs[offs[t] .. offs[t+1]).
  *
- * Derivations (Sec. 4.1 and Fig. 3a, with the readings of the design notes):
+ * Derivations (Sec. 4.1 and Fig. 3a; byte layouts are this library's reading of the paper):
  *   PRF_b(z)      = SHA-256(z || byte b)[0..16)            seed-tree children (Eq. 1)
  *   x_i^j         = SHA-256(x_0[i] || le32(j) || 0x00)[0..16)  one-time seed, j = t mod n2
  *   e_t           = SHA-256(m_t || x_t) as a little-endian integer, mod q
@@ -164,6 +164,31 @@ int poslo_hash_entries(poslo_ctx* ctx, const poslo_batch* batch, uint8_t* e_out)
  * point does not decode. */
 int poslo_msm(poslo_ctx* ctx, const uint8_t* points, const uint8_t* scalars, uint64_t n, uint32_t on_device,
               uint8_t out[32]);
+
+/* ---- allocation-free variant ---------------------------------------------------------- */
+
+/* The paper has no counterpart to this entry point: it exists for callers that cannot
+ * allocate device memory, such as a process whose device memory is owned by another
+ * allocator that has reserved all of it (a framework's caching allocator, a fixed pool
+ * sized at start-up) or a service that forbids allocation after its initialisation.
+ *
+ * It computes exactly what poslo_hash_entries computes (e_t = H(m_t || x_t) mod q for every
+ * entry, n*32 bytes to e_out) without a context and without allocating: no cudaMalloc,
+ * no cudaFree, no allocating library routine.  Its scratch memory is one file-scope device
+ * array of about 1.3 MiB that every GPU loading the library keeps until the process exits.
+ *   - batch->on_device must be 1: msgs, offs (and e_out) are device pointers; Y, s and R are
+ *     not read; batch->ds is host memory with at most 64 nodes.
+ *   - Limits: the batch may span at most 65,536 epochs; larger batches return POSLO_EINVAL
+ *     before any work is queued.  A seed that ds does not disclose returns POSLO_EINVAL.
+ *   - stream: the cudaStream_t to run on (NULL = the legacy default stream); the call returns
+ *     after that stream has finished its work.
+ *   - The first call on each device looks up the scratch array's device address (with that
+ *     device current); make that first call before any stream capture.
+ *   - Every call on a device shares the one scratch array.  Calls that overlap on the GPU
+ *     (from several host threads or streams at once) race on it and must be serialised by
+ *     the caller.
+ * Returns POSLO_OK, POSLO_EINVAL or POSLO_EDEVICE. */
+int poslo_hash_entries_noalloc(const poslo_batch* batch, uint8_t* e_out, void* stream);
 
 /* ---- profiling -------------------------------------------------------------------------- */
 

@@ -28,6 +28,7 @@ EXPORTS = [
     "poslo_keygen_c", "poslo_keygen_f", "poslo_sign_c", "poslo_sign_f", "poslo_disclose",
     "poslo_aver", "poslo_distill", "poslo_epoch_seeds", "poslo_hash_entries", "poslo_msm",
     "poslo_set_profiling", "poslo_kernel_time", "poslo_reset_kernel_times",
+    "poslo_hash_entries_noalloc",
 ]
 
 
@@ -80,6 +81,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "poslo_set_profiling": ([vp, C.c_int], C.c_int),
         "poslo_kernel_time": ([vp, C.c_char_p, C.POINTER(C.c_double), C.POINTER(u64)], C.c_int),
         "poslo_reset_kernel_times": ([vp], None),
+        "poslo_hash_entries_noalloc": ([C.POINTER(Batch), u8p, vp], C.c_int),
     }
     for name in EXPORTS:
         f = getattr(lib, name)
@@ -132,6 +134,19 @@ class BatchData:
     R_count: int
     ds: bytes
     ds_nodes: int
+
+
+def hash_entries_noalloc(b: BatchData, e_out, stream: int = 0) -> None:
+    """poslo_hash_entries_noalloc: e_t for every entry of a device-resident batch into the
+    device tensor e_out (n*32 bytes), without a context and without device allocation."""
+    lib = load_library()
+    if not (_is_torch(b.offs) and b.offs.is_cuda and _is_torch(e_out) and e_out.is_cuda):
+        raise ValueError("hash_entries_noalloc takes device tensors only")
+    cb = Context._cbatch(None, b)
+    rc = lib.poslo_hash_entries_noalloc(C.byref(cb), _ptr(e_out), stream or None)
+    _keep.clear()
+    if rc != POSLO_OK:
+        raise PosloError(rc, "poslo_hash_entries_noalloc failed")
 
 
 class Context:
