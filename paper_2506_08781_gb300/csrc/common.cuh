@@ -52,6 +52,7 @@ struct HashArgs {
   uint32_t weighted;           // 1: aggregate z_t e_t and z_t s_t
   uint32_t zpre[10];           // weighted: BE words of "POSLO-Z" || verifier_seed || (byte 39 = 0)
   uint32_t* z_out;             // optional (weighted): n*4 words of z_t
+  uint8_t* sbad_out;           // optional: n bytes, 1 = s_t is not canonical
   unsigned long long* partial; // per block: 13 u64 limb sums of e, 13 of s, 1 bad count (27 u64)
 };
 
@@ -165,10 +166,12 @@ struct PointArgs {
   const uint8_t* R;       // count*32
   uint64_t count;
   uint32_t* partial;      // per block: ge (32 words) + bad count (1 word), 33 words
-  uint32_t* affine_out;   // optional: count*16 words (x, y) of decoded points
+  uint32_t* pts_out;      // optional: count*24 words (x, y, 2d x y) of decoded points
   uint8_t* bad_out;       // optional: count bytes, 1 = undecodable
   const uint8_t* skip;    // optional: count bytes, 1 = leave the point out of the sum
 };
+
+constexpr int kPtsWords = 24;   // stored decoded point: x, y, t2d = 2d x y (8 words each)
 
 constexpr int kPointPartialWords = 33;
 
@@ -279,8 +282,8 @@ struct CheckArgs {
 
 
 struct MsmArgs {
-  const uint8_t* points;     // n*32 compressed (or NULL when affine is given)
-  const uint32_t* affine;    // n*16 words (x, y) already decoded (or NULL)
+  const uint8_t* points;     // n*32 compressed (or NULL when pts is given)
+  const uint32_t* pts;       // n*kPtsWords words (x, y, t2d) already decoded (or NULL)
   const uint8_t* scalars;    // n*scalar_bytes little-endian
   uint32_t scalar_bytes;     // 16 or 32
   uint64_t n;
@@ -406,6 +409,70 @@ struct SignCArgs {
 
 
 
+// ---- Pippenger multi-scalar multiplication (k_msm.cu) ----
+// sum_t [z_t] P_t for 128-bit scalars z_t (4 words each) and stored points P_t (kPtsWords
+// each).  Scalars are cut into windows of c bits; in window w every point goes to bucket
+// digit_w(z_t), found by a counting sort (count with atomics, scan, scatter).  Bucket sums
+// B_{w,d} come from one thread per bucket; the window sum sum_d d B_{w,d} from chunks of
+// kMsmChunk buckets (running sums inside a chunk, then a binary decomposition of the chunk
+// index), and the windows are joined by Horner's rule in one warp with quad-cooperative
+// doublings.
+constexpr int kMsmChunk = 16;
+
+struct MsmPlan {
+  int c;              // window bits (8..16)
+  int sw;             // scalar words: 4 (128-bit weights) or 8 (256-bit scalars)
+  int windows;        // ceil(32 sw / c)
+  uint32_t nb;        // buckets per window, 2^c
+  uint32_t nchunks;   // nb / kMsmChunk
+  int jbits;          // log2(nchunks)
+};
+
+__device__ __forceinline__ uint32_t z_digit(const uint32_t* z, int sw, int w, int c) {
+  const int bit = w * c;
+  if (bit >= 32 * sw) return 0;
+  const int word = bit >> 5, off = bit & 31;
+  uint64_t v = z[word];
+  if (word + 1 < sw) v |= (uint64_t)z[word + 1] << 32;
+  return (uint32_t)(v >> off) & ((1u << c) - 1u);
+}
+
+__device__ __forceinline__ void z_load(const uint32_t* z, int sw, uint64_t t, uint32_t zw[8]) {
+  const uint4* p = reinterpret_cast<const uint4*>(z + (size_t)sw * t);
+  const uint4 a = __ldg(p);
+  zw[0] = a.x; zw[1] = a.y; zw[2] = a.z; zw[3] = a.w;
+  if (sw == 8) {
+    const uint4 b = __ldg(p + 1);
+    zw[4] = b.x; zw[5] = b.y; zw[6] = b.z; zw[7] = b.w;
+  } else {
+    zw[4] = zw[5] = zw[6] = zw[7] = 0;
+  }
+}
+
+__device__ __forceinline__ void pts_load(const uint32_t* src, fe& x, fe& y, fe& t2d) {
+  const uint4* s4 = reinterpret_cast<const uint4*>(src);
+  uint4 v[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) v[i] = __ldg(s4 + i);
+  x = fe_const(v[0].x, v[0].y, v[0].z, v[0].w, v[1].x, v[1].y, v[1].z, v[1].w);
+  y = fe_const(v[2].x, v[2].y, v[2].z, v[2].w, v[3].x, v[3].y, v[3].z, v[3].w);
+  t2d = fe_const(v[4].x, v[4].y, v[4].z, v[4].w, v[5].x, v[5].y, v[5].z, v[5].w);
+}
+
+// ---- Distill segment tree (k_distill.cu) ----
+struct TreeArgs {
+  const uint32_t* pts;       // n*kPtsWords decoded points
+  const uint8_t* e;          // n*32 e_t
+  const uint8_t* s;          // n*32 s_t
+  const uint8_t* skip1;      // malformed R_t (undecodable)
+  const uint8_t* skip2;      // malformed s_t (non-canonical)
+  uint64_t n;                // entries
+  uint64_t M;                // leaves, the next power of two >= max(n, 2)
+  uint32_t* tree_pts;        // M-1 nodes (levels 1..log2 M), 32 words each
+  uint8_t* tree_e;           // M-1 scalars
+  uint8_t* tree_s;           // M-1 scalars
+};
+
 // ---- kernel declarations ----
 __global__ void k_epoch_seeds(const DsNode* __restrict__ ds, int nds, uint64_t e0, uint64_t ne,
                               uint32_t* __restrict__ x0_out, uint32_t* __restrict__ status);
@@ -430,5 +497,28 @@ __global__ void k_keygen_bpv(const uint8_t* bpv_r, uint32_t v, const uint32_t* t
 __global__ void k_decode_table(const uint8_t* enc, uint32_t v, uint32_t* out, uint32_t* status);
 __global__ void k_sign_f(const SignFArgs a);
 __global__ void k_sign_c(const SignCArgs a);
+__global__ void k_msm_count(const uint32_t* z, const uint8_t* skip, uint64_t n, MsmPlan pl, uint32_t* cnt,
+                            uint32_t* rank);
+__global__ void __launch_bounds__(1024) k_msm_scan(const uint32_t* cnt, uint32_t* off, MsmPlan pl);
+__global__ void k_msm_scatter(const uint32_t* z, const uint8_t* skip, uint64_t n, MsmPlan pl, const uint32_t* off,
+                              const uint32_t* rank, uint32_t* idx);
+__global__ void __launch_bounds__(128) k_msm_bucket(const uint32_t* pts, const uint32_t* idx, const uint32_t* off, const uint32_t* cnt,
+                             uint64_t n, MsmPlan pl, uint32_t* buckets);
+__global__ void __launch_bounds__(128) k_msm_chunk(const uint32_t* buckets, MsmPlan pl, uint32_t* L, uint32_t* T);
+__global__ void __launch_bounds__(256) k_msm_groups(const uint32_t* L, const uint32_t* T, MsmPlan pl, uint32_t* groups);
+__global__ void __launch_bounds__(32) k_msm_final(const uint32_t* groups, MsmPlan pl, uint32_t* out);
+__global__ void __launch_bounds__(128) k_tree_leaves(const TreeArgs a);
+__global__ void __launch_bounds__(128) k_tree_level(const TreeArgs a, uint64_t in_off, uint64_t out_off,
+                                                    uint64_t count);
+__global__ void __launch_bounds__(128) k_bisect(const TreeArgs a, int lvl, uint64_t lvl_off, const uint64_t* front, const uint64_t* front_cnt,
+                         uint64_t* next, uint64_t* next_cnt, const uint32_t* tY, const uint32_t* tG);
+__global__ void __launch_bounds__(128) k_bisect_leaves(const TreeArgs a, const uint64_t* front, const uint64_t* front_cnt, const uint32_t* tY,
+                                const uint32_t* tG, uint8_t* invalid);
+__global__ void __launch_bounds__(kHashThreads) k_weighted_sums(const uint8_t* e, const uint8_t* s, const uint32_t* z, const uint8_t* skip1,
+                                const uint8_t* skip2, uint64_t n, unsigned long long* partial);
+__global__ void __launch_bounds__(kPointThreads) k_pts_sum(const uint32_t* pts, const uint8_t* skip1, const uint8_t* skip2, uint64_t n,
+                          uint32_t* partial);
+__global__ void k_flags_or(const uint8_t* a, const uint8_t* b, const uint8_t* c, uint64_t n, uint8_t* out);
+__global__ void k_encode_ext(const uint32_t* point, uint8_t* out);
 
 }  // namespace poslo

@@ -119,6 +119,76 @@ __device__ __forceinline__ void ge_encode(const ge& p, uint32_t b[8]) {
   b[7] |= (x.v[0] & 1u) << 31;
 }
 
+// Mixed addition with an affine point given as (x, y, t2d = 2d x y): the "precomputed"
+// form of the unified addition, 7M (Hisil et al. 2008, Sec. 3.1 with Z2 = 1).
+__device__ __forceinline__ ge ge_madd(const ge& p, const fe& x, const fe& y, const fe& t2d) {
+  const fe A = fe_mul(fe_sub(p.Y, p.X), fe_sub(y, x));
+  const fe B = fe_mul(fe_add(p.Y, p.X), fe_add(y, x));
+  const fe C = fe_mul(p.T, t2d);
+  const fe D = fe_add(p.Z, p.Z);
+  const fe E = fe_sub(B, A), F = fe_sub(D, C), G = fe_add(D, C), H = fe_add(B, A);
+  ge r;
+  r.X = fe_mul(E, F); r.Y = fe_mul(G, H); r.Z = fe_mul(F, G); r.T = fe_mul(E, H);
+  return r;
+}
+
+// ---- quad-cooperative point operations ------------------------------------------------
+// Four consecutive lanes of a warp (a quad) hold the same point and split the field
+// multiplications of one group operation between them, then exchange the results by
+// shuffles: a doubling costs the latency of 2 multiplications instead of 8, an addition
+// 3 instead of 9.  Every lane of the warp must take part (full-mask shuffles); each quad
+// works on its own point.
+__device__ __forceinline__ fe fe_shfl(const fe& a, int src) {
+  fe r;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) r.v[i] = __shfl_sync(0xffffffffu, a.v[i], src);
+  return r;
+}
+
+__device__ __forceinline__ ge ge_dbl_quad(const ge& p) {
+  const int lane = threadIdx.x & 31, q = lane & 3, base = lane & ~3;
+  fe in = fe_select(p.X, p.Y, q == 1);
+  in = fe_select(in, p.Z, q == 2);
+  in = fe_select(in, fe_add(p.X, p.Y), q == 3);
+  const fe sq = fe_sq(in);
+  const fe A = fe_shfl(sq, base), B = fe_shfl(sq, base + 1), Z2 = fe_shfl(sq, base + 2), S = fe_shfl(sq, base + 3);
+  const fe C = fe_add(Z2, Z2);
+  const fe E = fe_sub(fe_sub(S, A), B);
+  const fe G = fe_sub(B, A);
+  const fe F = fe_sub(G, C);
+  const fe H = fe_neg(fe_add(A, B));
+  // X3 = E F, Y3 = G H, Z3 = F G, T3 = E H
+  fe m1 = fe_select(E, G, q == 1), m2 = fe_select(F, H, q == 1);
+  m1 = fe_select(m1, F, q == 2); m2 = fe_select(m2, G, q == 2);
+  m2 = fe_select(m2, H, q == 3);
+  const fe r = fe_mul(m1, m2);
+  ge o;
+  o.X = fe_shfl(r, base); o.Y = fe_shfl(r, base + 1); o.Z = fe_shfl(r, base + 2); o.T = fe_shfl(r, base + 3);
+  return o;
+}
+
+__device__ __forceinline__ ge ge_add_quad(const ge& p, const ge& qq) {
+  const int lane = threadIdx.x & 31, q = lane & 3, base = lane & ~3;
+  // phase 1: A = (Y1-X1)(Y2-X2), B = (Y1+X1)(Y2+X2), TT = T1 T2, ZZ = Z1 Z2
+  fe a = fe_select(fe_sub(p.Y, p.X), fe_add(p.Y, p.X), q == 1);
+  fe b = fe_select(fe_sub(qq.Y, qq.X), fe_add(qq.Y, qq.X), q == 1);
+  a = fe_select(a, p.T, q == 2); b = fe_select(b, qq.T, q == 2);
+  a = fe_select(a, p.Z, q == 3); b = fe_select(b, qq.Z, q == 3);
+  fe r = fe_mul(a, b);
+  // lane 2 turns T1 T2 into C = 2d T1 T2
+  r = fe_select(r, fe_mul(r, fe_d2()), q == 2);
+  const fe A = fe_shfl(r, base), B = fe_shfl(r, base + 1), C = fe_shfl(r, base + 2), ZZ = fe_shfl(r, base + 3);
+  const fe D = fe_add(ZZ, ZZ);
+  const fe E = fe_sub(B, A), F = fe_sub(D, C), G = fe_add(D, C), H = fe_add(B, A);
+  fe m1 = fe_select(E, G, q == 1), m2 = fe_select(F, H, q == 1);
+  m1 = fe_select(m1, F, q == 2); m2 = fe_select(m2, G, q == 2);
+  m2 = fe_select(m2, H, q == 3);
+  const fe s = fe_mul(m1, m2);
+  ge o;
+  o.X = fe_shfl(s, base); o.Y = fe_shfl(s, base + 1); o.Z = fe_shfl(s, base + 2); o.T = fe_shfl(s, base + 3);
+  return o;
+}
+
 // Signed 4-bit recoding of a scalar below 2^253: 64 digits in [-8, 8), sum d_i 16^i = k.
 __device__ __forceinline__ int sc_digit4(const uint32_t k[8], int w, int& carry) {
   int d = (int)((k[w >> 3] >> ((w & 7) * 4)) & 15u) + carry;

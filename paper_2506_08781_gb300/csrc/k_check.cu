@@ -31,10 +31,9 @@ __global__ void __launch_bounds__(kPointThreads) k_msm_direct(const MsmArgs a) {
   for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.n; t += stride) {
     if (a.skip && a.skip[t]) continue;
     ge P;
-    if (a.affine) {
-      const uint32_t* src = a.affine + 16 * t;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) { P.X.v[i] = src[i]; P.Y.v[i] = src[8 + i]; }
+    if (a.pts) {
+      fe t2d;
+      pts_load(a.pts + (size_t)kPtsWords * t, P.X, P.Y, t2d);
       P.Z = fe_one();
       P.T = fe_mul(P.X, P.Y);
     } else {
@@ -170,6 +169,17 @@ __global__ void k_sum_encode(const uint32_t* partial, uint32_t nparts, uint32_t*
       }
     }
     if (bad_out) *bad_out = sbad;
+  }
+}
+
+// Encode one extended point (32 words) to its 32-byte compressed form.
+__global__ void k_encode_ext(const uint32_t* point, uint8_t* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  uint32_t w[8];
+  ge_encode(ge_load(point), w);
+  for (int k = 0; k < 8; ++k) {
+    out[4 * k] = (uint8_t)w[k]; out[4 * k + 1] = (uint8_t)(w[k] >> 8);
+    out[4 * k + 2] = (uint8_t)(w[k] >> 16); out[4 * k + 3] = (uint8_t)(w[k] >> 24);
   }
 }
 

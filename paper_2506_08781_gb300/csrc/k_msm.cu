@@ -1,0 +1,160 @@
+// Pippenger bucket multi-scalar multiplication sum_t [z_t] P_t (128- or 256-bit scalars) for the
+// weighted aggregate check: the verifier's random linear combination of the entries'
+// equations R_t = e_t Y + s_t G (an extension of AVer, Fig. 4; the paper aggregates with
+// unit coefficients only).
+#include "common.cuh"
+
+namespace poslo {
+
+// Counting sort, pass 1: rank of every (window, entry) inside its bucket.
+__global__ void k_msm_count(const uint32_t* z, const uint8_t* skip, uint64_t n, MsmPlan pl, uint32_t* cnt,
+                            uint32_t* rank) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
+    if (skip && skip[t]) continue;
+    uint32_t zw[8];
+    z_load(z, pl.sw, t, zw);
+    for (int w = 0; w < pl.windows; ++w) {
+      const uint32_t d = z_digit(zw, pl.sw, w, pl.c);
+      if (d) rank[(size_t)w * n + t] = atomicAdd(&cnt[(size_t)w * pl.nb + d], 1u);
+    }
+  }
+}
+
+// Counting sort, pass 2: exclusive scan of the bucket counts, one block per window.
+__global__ void __launch_bounds__(1024) k_msm_scan(const uint32_t* cnt, uint32_t* off, MsmPlan pl) {
+  __shared__ uint32_t warp_sums[32];
+  const int w = blockIdx.x;
+  const uint32_t per = (pl.nb + blockDim.x - 1) / blockDim.x;
+  const uint32_t lo = threadIdx.x * per;
+  const uint32_t* c = cnt + (size_t)w * pl.nb;
+  uint32_t local = 0;
+  for (uint32_t d = lo; d < lo + per && d < pl.nb; ++d) local += c[d];
+  // block-wide exclusive scan of `local`
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t incl = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) warp_sums[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t v = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += u;
+    }
+    warp_sums[lane] = v;   // inclusive over warps
+  }
+  __syncthreads();
+  uint32_t base = (incl - local) + (warp > 0 ? warp_sums[warp - 1] : 0u);
+  uint32_t* o = off + (size_t)w * pl.nb;
+  for (uint32_t d = lo; d < lo + per && d < pl.nb; ++d) {
+    o[d] = base;
+    base += c[d];
+  }
+}
+
+// Counting sort, pass 3: entry indices in bucket order, per window.
+__global__ void k_msm_scatter(const uint32_t* z, const uint8_t* skip, uint64_t n, MsmPlan pl, const uint32_t* off,
+                              const uint32_t* rank, uint32_t* idx) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
+    if (skip && skip[t]) continue;
+    uint32_t zw[8];
+    z_load(z, pl.sw, t, zw);
+    for (int w = 0; w < pl.windows; ++w) {
+      const uint32_t d = z_digit(zw, pl.sw, w, pl.c);
+      if (d) idx[(size_t)w * n + off[(size_t)w * pl.nb + d] + rank[(size_t)w * n + t]] = (uint32_t)t;
+    }
+  }
+}
+
+// Bucket sums B_{w,d}: one thread per bucket, mixed additions of its points.
+__global__ void __launch_bounds__(128) k_msm_bucket(const uint32_t* pts, const uint32_t* idx, const uint32_t* off,
+                                                    const uint32_t* cnt, uint64_t n, MsmPlan pl, uint32_t* buckets) {
+  const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= (uint64_t)pl.windows * pl.nb) return;
+  const uint32_t w = (uint32_t)(b / pl.nb), d = (uint32_t)(b % pl.nb);
+  ge acc = ge_identity();
+  if (d) {
+    const uint32_t* list = idx + (size_t)w * n + off[b];
+    const uint32_t len = cnt[b];
+    for (uint32_t k = 0; k < len; ++k) {
+      fe x, y, t2d;
+      pts_load(pts + (size_t)kPtsWords * __ldg(list + k), x, y, t2d);
+      acc = ge_madd(acc, x, y, t2d);
+    }
+  }
+  ge_store(buckets + 32 * b, acc);
+}
+
+// Chunk j of window w holds buckets d = 16j .. 16j+15: L = sum_r r B_{16j+r} by running
+// sums, T = sum_r B_{16j+r}.
+__global__ void __launch_bounds__(128) k_msm_chunk(const uint32_t* buckets, MsmPlan pl, uint32_t* L, uint32_t* T) {
+  const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= (uint64_t)pl.windows * pl.nchunks) return;
+  const uint32_t w = (uint32_t)(g / pl.nchunks), j = (uint32_t)(g % pl.nchunks);
+  const uint32_t* B = buckets + 32 * ((size_t)w * pl.nb + (size_t)j * kMsmChunk);
+  ge run = ge_identity(), acc = ge_identity();
+  for (int r = kMsmChunk - 1; r >= 1; --r) {
+    run = ge_add(run, ge_load(B + 32 * r));
+    acc = ge_add(acc, run);
+  }
+  run = ge_add(run, ge_load(B));
+  ge_store(L + 32 * g, acc);
+  ge_store(T + 32 * g, run);
+}
+
+// Group sums per window: group 0 = sum_j L_j; group 1+k = sum of T_j over chunks j whose
+// bit k is set.  One block per (window, group).
+constexpr int kGroupThreads = 256;
+__global__ void __launch_bounds__(256) k_msm_groups(const uint32_t* L, const uint32_t* T, MsmPlan pl,
+                                                               uint32_t* groups) {
+  const int ng = 1 + pl.jbits;
+  const int w = blockIdx.x / ng, grp = blockIdx.x % ng;
+  const uint32_t* base = (grp == 0 ? L : T) + 32 * (size_t)w * pl.nchunks;
+  ge acc = ge_identity();
+  for (uint32_t j = threadIdx.x; j < pl.nchunks; j += blockDim.x) {
+    if (grp == 0 || ((j >> (grp - 1)) & 1u)) acc = ge_add(acc, ge_load(base + 32 * (size_t)j));
+  }
+  __shared__ uint32_t sp[kGroupThreads][32];
+  ge_store(sp[threadIdx.x], acc);
+  __syncthreads();
+  for (int h = kGroupThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) ge_store(sp[threadIdx.x], ge_add(ge_load(sp[threadIdx.x]), ge_load(sp[threadIdx.x + h])));
+    __syncthreads();
+  }
+  if (threadIdx.x < 32) groups[32 * (size_t)blockIdx.x + threadIdx.x] = sp[0][threadIdx.x];
+}
+
+// Window sums W_w = G_0 + 16 sum_k 2^k G_{1+k} (quad w computes window w), then
+// sum_w 2^{c w} W_w by Horner's rule in quad 0.  One warp; windows are processed in rounds
+// of eight quads.
+__global__ void __launch_bounds__(32) k_msm_final(const uint32_t* groups, MsmPlan pl, uint32_t* out) {
+  __shared__ uint32_t wsum[32][32];
+  const int lane = threadIdx.x & 31, quad = lane >> 2;
+  const int ng = 1 + pl.jbits;
+  for (int r0 = 0; r0 < pl.windows; r0 += 8) {
+    const int w = r0 + quad;
+    const int wc = w < pl.windows ? w : pl.windows - 1;
+    const uint32_t* G = groups + 32 * (size_t)wc * ng;
+    ge acc = ge_load(G + 32 * pl.jbits);       // top bit group
+    for (int k = pl.jbits - 2; k >= 0; --k) acc = ge_add_quad(ge_dbl_quad(acc), ge_load(G + 32 * (1 + k)));
+    for (int s = 0; s < 4; ++s) acc = ge_dbl_quad(acc);   // times kMsmChunk = 16
+    acc = ge_add_quad(acc, ge_load(G));
+    if ((lane & 3) == 0 && w < pl.windows) ge_store(wsum[w], acc);
+    __syncwarp();
+  }
+  ge acc = ge_load(wsum[pl.windows - 1]);
+  for (int w = pl.windows - 2; w >= 0; --w) {
+    for (int s = 0; s < pl.c; ++s) acc = ge_dbl_quad(acc);
+    acc = ge_add_quad(acc, ge_load(wsum[w]));
+  }
+  if (lane == 0) ge_store(out, acc);
+}
+
+}  // namespace poslo

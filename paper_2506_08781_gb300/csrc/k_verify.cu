@@ -73,7 +73,9 @@ __global__ void __launch_bounds__(kHashThreads) k_hash(const HashArgs a) {
       const uint4* sp = reinterpret_cast<const uint4*>(a.s + 32 * t);
       const uint4 s0 = __ldg(sp), s1 = __ldg(sp + 1);
       s[0] = s0.x; s[1] = s0.y; s[2] = s0.z; s[3] = s0.w; s[4] = s1.x; s[5] = s1.y; s[6] = s1.z; s[7] = s1.w;
-      bad += sc_is_canonical(s) ? 0u : 1u;
+      const bool canon = sc_is_canonical(s);
+      bad += canon ? 0u : 1u;
+      if (a.sbad_out) a.sbad_out[t] = canon ? 0 : 1;
     }
     if (a.weighted) {
       uint32_t z[4];
@@ -120,13 +122,17 @@ __global__ void __launch_bounds__(kPointThreads) k_points(const PointArgs a) {
     const bool ok = ge_decode(b, P);
     bad += ok ? 0u : 1u;
     if (a.bad_out) a.bad_out[t] = ok ? 0 : 1;
-    if (a.affine_out) {
-      uint32_t* dst = a.affine_out + 16 * t;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) { dst[i] = P.X.v[i]; dst[8 + i] = P.Y.v[i]; }
-    } else if (ok && !(a.skip && a.skip[t])) {
-      acc = ge_add(acc, P);
+    const fe t2d = fe_mul(P.T, fe_d2());
+    if (a.pts_out) {
+      uint4* dst = reinterpret_cast<uint4*>(a.pts_out + (size_t)kPtsWords * t);
+      dst[0] = make_uint4(P.X.v[0], P.X.v[1], P.X.v[2], P.X.v[3]);
+      dst[1] = make_uint4(P.X.v[4], P.X.v[5], P.X.v[6], P.X.v[7]);
+      dst[2] = make_uint4(P.Y.v[0], P.Y.v[1], P.Y.v[2], P.Y.v[3]);
+      dst[3] = make_uint4(P.Y.v[4], P.Y.v[5], P.Y.v[6], P.Y.v[7]);
+      dst[4] = make_uint4(t2d.v[0], t2d.v[1], t2d.v[2], t2d.v[3]);
+      dst[5] = make_uint4(t2d.v[4], t2d.v[5], t2d.v[6], t2d.v[7]);
     }
+    if (ok && !(a.skip && a.skip[t])) acc = ge_madd(acc, P.X, P.Y, t2d);
   }
   // tree reduction in shared memory
   __shared__ uint32_t sp[kPointThreads][32];

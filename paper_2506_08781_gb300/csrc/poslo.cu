@@ -53,6 +53,7 @@ struct poslo_ctx {
   std::map<std::string, KernelTimer> timers;
   std::vector<std::pair<std::string, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
   std::vector<cudaEvent_t> event_pool;
+  std::map<int, int> msm_tuned;   // (log2 n) * 16 + scalar words -> best window c
 };
 
 namespace {
@@ -371,7 +372,7 @@ int run_ytable(poslo_ctx* ctx, const uint8_t* Y, uint32_t** table_out) {
   return POSLO_OK;
 }
 
-int run_points(poslo_ctx* ctx, const uint8_t* R, uint64_t count, uint32_t* affine_out, uint8_t* bad_out,
+int run_points(poslo_ctx* ctx, const uint8_t* R, uint64_t count, uint32_t* pts_out, uint8_t* bad_out,
                uint32_t** partial_out, uint32_t* nblocks_out) {
   int rc;
   const int blocks = grid_for(ctx, count, kPointThreads, 8);
@@ -383,7 +384,7 @@ int run_points(poslo_ctx* ctx, const uint8_t* R, uint64_t count, uint32_t* affin
   a.R = R;
   a.count = count;
   a.partial = partial;
-  a.affine_out = affine_out;
+  a.pts_out = pts_out;
   a.bad_out = bad_out;
   cudaEvent_t tb, te;
   timer_begin(ctx, "points", ctx->s_points, &tb, &te);
@@ -397,7 +398,7 @@ int run_points(poslo_ctx* ctx, const uint8_t* R, uint64_t count, uint32_t* affin
   return POSLO_OK;
 }
 
-int run_msm_direct(poslo_ctx* ctx, cudaStream_t st, const uint8_t* points, const uint32_t* affine,
+int run_msm_direct(poslo_ctx* ctx, cudaStream_t st, const uint8_t* points, const uint32_t* pts,
                    const uint8_t* scalars, uint32_t scalar_bytes, uint64_t n, const uint8_t* skip,
                    uint32_t* point_out, uint8_t* enc_out, uint32_t* bad_out) {
   int rc;
@@ -406,7 +407,7 @@ int run_msm_direct(poslo_ctx* ctx, cudaStream_t st, const uint8_t* points, const
   if ((rc = ensure_t(ctx, "msm_partial", (size_t)blocks * kPointPartialWords * 4, &partial))) return rc;
   MsmArgs a{};
   a.points = points;
-  a.affine = affine;
+  a.pts = pts;
   a.scalars = scalars;
   a.scalar_bytes = scalar_bytes;
   a.n = n;
@@ -421,6 +422,93 @@ int run_msm_direct(poslo_ctx* ctx, cudaStream_t st, const uint8_t* points, const
   ++ctx->launch_count;
   CU(cudaGetLastError());
   timer_end(ctx, "msm", st, tb, te);
+  return POSLO_OK;
+}
+
+// Pippenger plan: the window c comes from the context (poslo_params.msm_window) or from the
+// autotuned table for this size class (see autotune_msm); the default before tuning is
+// c = log2(n) - 4 clamped to [8, 16].
+MsmPlan msm_plan(poslo_ctx* ctx, uint64_t n, int sw) {
+  int c = (int)ctx->msm_window;
+  if (c == 0) {
+    int lg = 0;
+    while ((1ull << (lg + 1)) <= std::max<uint64_t>(n, 1)) ++lg;
+    auto it = ctx->msm_tuned.find(lg * 16 + sw);
+    c = it != ctx->msm_tuned.end() ? it->second : std::min(16, std::max(8, lg - 4));
+  }
+  MsmPlan pl;
+  pl.c = c;
+  pl.sw = sw;
+  pl.windows = (32 * sw + c - 1) / c;
+  pl.nb = 1u << c;
+  pl.nchunks = pl.nb / kMsmChunk;
+  pl.jbits = c - 4;
+  return pl;
+}
+
+// sum_t [z_t] P_t over the stored points (skipping flagged entries) into out (32 words).
+int run_msm(poslo_ctx* ctx, cudaStream_t st, const uint32_t* pts, const uint32_t* z, int sw, const uint8_t* skip,
+            uint64_t n, uint32_t* out, const MsmPlan* forced = nullptr) {
+  int rc;
+  const MsmPlan pl = forced ? *forced : msm_plan(ctx, n, sw);
+  const size_t nbw = (size_t)pl.windows * pl.nb;
+  uint32_t *cnt, *off, *rank, *idx, *buckets, *L, *T, *groups;
+  if ((rc = ensure_t(ctx, "msm_cnt", 4 * nbw, &cnt))) return rc;
+  if ((rc = ensure_t(ctx, "msm_off", 4 * nbw, &off))) return rc;
+  if ((rc = ensure_t(ctx, "msm_rank", 4 * (size_t)pl.windows * std::max<uint64_t>(n, 1), &rank))) return rc;
+  if ((rc = ensure_t(ctx, "msm_idx", 4 * (size_t)pl.windows * std::max<uint64_t>(n, 1), &idx))) return rc;
+  if ((rc = ensure_t(ctx, "msm_buckets", 128 * nbw, &buckets))) return rc;
+  if ((rc = ensure_t(ctx, "msm_L", 128 * (size_t)pl.windows * pl.nchunks, &L))) return rc;
+  if ((rc = ensure_t(ctx, "msm_T", 128 * (size_t)pl.windows * pl.nchunks, &T))) return rc;
+  if ((rc = ensure_t(ctx, "msm_groups", 128 * (size_t)pl.windows * (1 + pl.jbits), &groups))) return rc;
+  cudaEvent_t tb, te;
+  timer_begin(ctx, "msm", st, &tb, &te);
+  CU(cudaMemsetAsync(cnt, 0, 4 * nbw, st));
+  if (n) {
+    const int g = grid_for(ctx, n, 256, 8);
+    k_msm_count<<<g, 256, 0, st>>>(z, skip, n, pl, cnt, rank);
+    ++ctx->launch_count;
+    k_msm_scan<<<pl.windows, 1024, 0, st>>>(cnt, off, pl);
+    ++ctx->launch_count;
+    k_msm_scatter<<<g, 256, 0, st>>>(z, skip, n, pl, off, rank, idx);
+    ++ctx->launch_count;
+  }
+  k_msm_bucket<<<(unsigned)((nbw + 127) / 128), 128, 0, st>>>(pts, idx, off, cnt, std::max<uint64_t>(n, 1), pl,
+                                                             buckets);
+  ++ctx->launch_count;
+  const size_t nch = (size_t)pl.windows * pl.nchunks;
+  k_msm_chunk<<<(unsigned)((nch + 127) / 128), 128, 0, st>>>(buckets, pl, L, T);
+  ++ctx->launch_count;
+  k_msm_groups<<<pl.windows * (1 + pl.jbits), 256, 0, st>>>(L, T, pl, groups);
+  ++ctx->launch_count;
+  k_msm_final<<<1, 32, 0, st>>>(groups, pl, out);
+  ++ctx->launch_count;
+  CU(cudaGetLastError());
+  timer_end(ctx, "msm", st, tb, te);
+  return POSLO_OK;
+}
+
+int run_finalize(poslo_ctx* ctx, const unsigned long long* hpart, uint32_t nhb, const uint32_t* ppart, uint32_t npb,
+                 const uint32_t* R_given, const uint8_t* s_given, const uint32_t* tableY, uint8_t* d_acc,
+                 uint32_t* out_words) {
+  FinalArgs f{};
+  f.hash_partial = hpart;
+  f.nhash = nhb;
+  f.point_partial = ppart;
+  f.npoint = npb;
+  f.R_given = R_given;
+  f.s_given = s_given;
+  f.tableY = tableY;
+  f.tableG = ctx->tableG;
+  f.accept = d_acc;
+  f.out_words = out_words;
+  f.status = ctx->status;
+  cudaEvent_t tb, te;
+  timer_begin(ctx, "finalize", ctx->s_main, &tb, &te);
+  k_finalize<<<1, kFinalThreads, 0, ctx->s_main>>>(f);
+  ++ctx->launch_count;
+  CU(cudaGetLastError());
+  timer_end(ctx, "finalize", ctx->s_main, tb, te);
   return POSLO_OK;
 }
 
@@ -795,10 +883,14 @@ int poslo_aver(poslo_ctx* ctx, const poslo_batch* batch, uint32_t agg_mode, uint
   uint32_t* tableY;
   if ((rc = run_ytable(ctx, batch->Y, &tableY))) return rc;
   const uint64_t npts = F ? batch->n : batch->R_count;
-  uint32_t* affine = nullptr;
-  if (weighted && (rc = ensure_t(ctx, "affine", 64 * std::max<uint64_t>(npts, 1), &affine))) return rc;
+  uint32_t* pts = nullptr;
+  uint8_t* badR = nullptr;
+  if (weighted) {
+    if ((rc = ensure_t(ctx, "pts", 4 * kPtsWords * std::max<uint64_t>(npts, 1), &pts))) return rc;
+    if ((rc = ensure_t(ctx, "badR", std::max<uint64_t>(npts, 1), &badR))) return rc;
+  }
   uint32_t *ppart, npb;
-  if ((rc = run_points(ctx, sb.R, npts, affine, nullptr, &ppart, &npb))) return rc;
+  if ((rc = run_points(ctx, sb.R, npts, pts, badR, &ppart, &npb))) return rc;
   uint32_t* z = nullptr;
   if (weighted && (rc = ensure_t(ctx, "z", 16 * std::max<uint64_t>(batch->n, 1), &z))) return rc;
   unsigned long long* hpart;
@@ -809,29 +901,11 @@ int poslo_aver(poslo_ctx* ctx, const poslo_batch* batch, uint32_t agg_mode, uint
   uint32_t* Rw = nullptr;
   if (weighted) {
     if ((rc = ensure_t(ctx, "R_weighted", 128, &Rw))) return rc;
-    if ((rc = run_msm_direct(ctx, ctx->s_main, nullptr, affine, reinterpret_cast<const uint8_t*>(z), 16, batch->n,
-                             nullptr, Rw, nullptr, nullptr)))
-      return rc;
+    if ((rc = run_msm(ctx, ctx->s_main, pts, z, 4, badR, batch->n, Rw))) return rc;
   }
   uint8_t* d_acc;
   if ((rc = ensure_t(ctx, "accept", 16, &d_acc))) return rc;
-  FinalArgs f{};
-  f.hash_partial = hpart;
-  f.nhash = nhb;
-  f.point_partial = ppart;
-  f.npoint = npb;
-  f.R_given = Rw;
-  f.s_given = F ? nullptr : sb.s;
-  f.tableY = tableY;
-  f.tableG = ctx->tableG;
-  f.accept = d_acc;
-  f.status = ctx->status;
-  cudaEvent_t tb, te;
-  timer_begin(ctx, "finalize", ctx->s_main, &tb, &te);
-  k_finalize<<<1, kFinalThreads, 0, ctx->s_main>>>(f);
-  ++ctx->launch_count;
-  CU(cudaGetLastError());
-  timer_end(ctx, "finalize", ctx->s_main, tb, te);
+  if ((rc = run_finalize(ctx, hpart, nhb, ppart, npb, Rw, F ? nullptr : sb.s, tableY, d_acc, nullptr))) return rc;
   uint8_t h_acc = 0;
   CU(cudaMemcpyAsync(&h_acc, d_acc, 1, cudaMemcpyDeviceToHost, ctx->s_main));
   if ((rc = check_status(ctx))) return rc;
@@ -839,6 +913,10 @@ int poslo_aver(poslo_ctx* ctx, const poslo_batch* batch, uint32_t agg_mode, uint
   return POSLO_OK;
 }
 
+// Distill: weighted check of the whole batch first; when it fails (or entries are
+// malformed) the segment-tree bisection finds the failing entries, the weighted check of
+// the remaining entries confirms them, and per-entry checks of all entries settle the rare
+// case where that confirmation fails.
 int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_idx, uint64_t cap, uint64_t* n_invalid,
                   uint8_t ccd_s[32], uint8_t ccd_R[32]) {
   if (!ctx || !n_invalid) return fail(ctx, POSLO_EINVAL, "bad distill arguments");
@@ -846,63 +924,183 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
   if ((rc = validate_batch(ctx, batch))) return rc;
   if (batch->variant != POSLO_VARIANT_F) return fail(ctx, POSLO_EINVAL, "distill is entry-granular: POSLO-F batches");
   const uint64_t n = batch->n;
+  const uint64_t n1 = std::max<uint64_t>(n, 1);
   if ((rc = reset_status(ctx))) return rc;
   Staged sb;
   if ((rc = stage_batch(ctx, batch, sb))) return rc;
   uint32_t* tableY;
   if ((rc = run_ytable(ctx, batch->Y, &tableY))) return rc;
-  uint8_t* d_e;
-  if ((rc = ensure_t(ctx, "e_all", 32 * std::max<uint64_t>(n, 1), &d_e))) return rc;
+  uint32_t *pts, *z;
+  uint8_t *badR, *badS, *d_e, *inv;
+  if ((rc = ensure_t(ctx, "pts", 4 * kPtsWords * n1, &pts))) return rc;
+  if ((rc = ensure_t(ctx, "badR", n1, &badR))) return rc;
+  if ((rc = ensure_t(ctx, "badS", n1, &badS))) return rc;
+  if ((rc = ensure_t(ctx, "z", 16 * n1, &z))) return rc;
+  if ((rc = ensure_t(ctx, "e_all", 32 * n1, &d_e))) return rc;
+  if ((rc = ensure_t(ctx, "invalid", n1, &inv))) return rc;
+  // A1-A5: hashing (main stream) overlapped with decoding (points stream)
+  uint32_t *ppart, npb;
+  if ((rc = run_points(ctx, sb.R, n, pts, badR, &ppart, &npb))) return rc;
   unsigned long long* hpart;
   uint32_t nhb;
-  if ((rc = run_hash(ctx, batch, sb, d_e, false, true, nullptr, &hpart, &nhb))) return rc;
-  CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_table, 0));
-  uint8_t* d_inv;
-  if ((rc = ensure_t(ctx, "invalid", std::max<uint64_t>(n, 1), &d_inv))) return rc;
-  CheckArgs a{};
-  a.e = d_e;
-  a.s = sb.s;
-  a.R = sb.R;
-  a.n = n;
-  a.tableY = tableY;
-  a.tableG = ctx->tableG;
-  a.invalid = d_inv;
-  if (n) {
+  {
+    // run_hash with the per-entry outputs Distill needs
+    uint64_t e_first = 0, ne = 0;
+    if (n) {
+      e_first = batch->first_index / batch->n2;
+      ne = (batch->first_index + n - 1) / batch->n2 - e_first + 1;
+    }
+    uint32_t* seeds;
+    if ((rc = run_epoch_seeds(ctx, batch->ds, batch->ds_nodes, e_first, ne, &seeds))) return rc;
+    const int blocks = grid_for(ctx, n, kHashThreads, 8);
+    if ((rc = ensure_t(ctx, "hash_partial", (size_t)blocks * kPartialWords * 8, &hpart))) return rc;
+    HashArgs a{};
+    a.msgs = sb.msgs;
+    a.offs = sb.offs;
+    a.base_off = sb.base_off;
+    a.n = n;
+    a.first_index = batch->first_index;
+    a.e0 = e_first;
+    a.n2 = batch->n2;
+    a.n2_log2 = log2_exact(batch->n2);
+    a.seeds = seeds;
+    a.e_out = d_e;
+    a.s = sb.s;
+    a.weighted = 1;
+    make_zpre(ctx->vseed, a.zpre);
+    a.z_out = z;
+    a.sbad_out = badS;
+    a.partial = hpart;
     cudaEvent_t tb, te;
-    timer_begin(ctx, "check", ctx->s_main, &tb, &te);
-    k_entry_check<<<grid_for(ctx, n, 128, 8), 128, 0, ctx->s_main>>>(a);
+    timer_begin(ctx, "hash", ctx->s_main, &tb, &te);
+    k_hash<<<blocks, kHashThreads, 0, ctx->s_main>>>(a);
     ++ctx->launch_count;
     CU(cudaGetLastError());
-    timer_end(ctx, "check", ctx->s_main, tb, te);
+    timer_end(ctx, "hash", ctx->s_main, tb, te);
+    nhb = (uint32_t)blocks;
   }
-  // ordered list of flagged entries
-  uint64_t* d_idx;
-  if ((rc = ensure_t(ctx, "invalid_idx", 8 * std::max<uint64_t>(std::min(cap, n), 1) + 8, &d_idx))) return rc;
-  uint64_t* d_cnt = d_idx + std::max<uint64_t>(std::min(cap, n), 1);
-  k_compact<<<1, kCompactThreads, 0, ctx->s_main>>>(d_inv, n, batch->first_index, d_idx, std::min(cap, n), d_cnt);
-  ++ctx->launch_count;
-  CU(cudaGetLastError());
-  // ccd^v = (sum of valid s_t mod q, sum of valid R_t)
+  CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_table, 0));
+  CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_points, 0));
+  // A5-A6: weighted MSM and the weighted check of the whole batch
+  uint32_t *Rw, *words;
+  uint8_t* d_acc;
+  if ((rc = ensure_t(ctx, "R_weighted", 128, &Rw))) return rc;
+  if ((rc = ensure_t(ctx, "final_words", 4 * 48, &words))) return rc;
+  if ((rc = ensure_t(ctx, "accept", 16, &d_acc))) return rc;
+  if ((rc = run_msm(ctx, ctx->s_main, pts, z, 4, badR, n, Rw))) return rc;
+  if ((rc = run_finalize(ctx, hpart, nhb, ppart, npb, Rw, nullptr, tableY, d_acc, nullptr))) return rc;
+  // unit sums of the good entries (ccd^v when every entry is valid)
   uint8_t* d_ccd;
   if ((rc = ensure_t(ctx, "ccd", 64, &d_ccd))) return rc;
-  {
-    const int blocks = grid_for(ctx, n, kHashThreads, 8);
-    unsigned long long* sp;
-    if ((rc = ensure_t(ctx, "ccd_spart", (size_t)blocks * 13 * 8, &sp))) return rc;
-    k_sum_scalars<<<blocks, kHashThreads, 0, ctx->s_main>>>(sb.s, n, d_inv, sp);
+  const int sblocks = grid_for(ctx, n, kHashThreads, 8);
+  unsigned long long* sp;
+  if ((rc = ensure_t(ctx, "ccd_spart", (size_t)sblocks * 13 * 8, &sp))) return rc;
+  uint8_t h_acc = 0;
+  CU(cudaMemcpyAsync(&h_acc, d_acc, 1, cudaMemcpyDeviceToHost, ctx->s_main));
+  if ((rc = check_status(ctx))) return rc;   // synchronises: h_acc is ready
+  // h_acc covers "no malformed entry and the weighted equation holds"
+  uint64_t* d_idx;
+  const uint64_t capn = std::max<uint64_t>(std::min(cap, n), 1);
+  if ((rc = ensure_t(ctx, "invalid_idx", 8 * capn + 8, &d_idx))) return rc;
+  uint64_t* d_cnt = d_idx + capn;
+  if (h_acc) {
+    CU(cudaMemsetAsync(inv, 0, n1, ctx->s_main));
+  } else {
+    // ---- A7: segment-tree bisection over unit aggregates ----
+    uint64_t M = 2, L = 1;
+    while (M < n) { M <<= 1; ++L; }
+    TreeArgs ta{};
+    ta.pts = pts;
+    ta.e = d_e;
+    ta.s = sb.s;
+    ta.skip1 = badR;
+    ta.skip2 = badS;
+    ta.n = n;
+    ta.M = M;
+    if ((rc = ensure_t(ctx, "tree_pts", 128 * (M - 1), &ta.tree_pts))) return rc;
+    if ((rc = ensure_t(ctx, "tree_e", 32 * (M - 1), &ta.tree_e))) return rc;
+    if ((rc = ensure_t(ctx, "tree_s", 32 * (M - 1), &ta.tree_s))) return rc;
+    cudaEvent_t tb, te;
+    timer_begin(ctx, "tree", ctx->s_main, &tb, &te);
+    k_tree_leaves<<<(unsigned)((M / 2 + 127) / 128), 128, 0, ctx->s_main>>>(ta);
     ++ctx->launch_count;
-    k_reduce_scalars<<<1, 32, 0, ctx->s_main>>>(sp, blocks, d_ccd);
+    std::vector<uint64_t> lvl_off(L + 1, 0);
+    lvl_off[1] = 0;
+    for (uint64_t l = 2; l <= L; ++l) {
+      lvl_off[l] = lvl_off[l - 1] + (M >> (l - 1));
+      const uint64_t count = M >> l;
+      k_tree_level<<<(unsigned)((count + 127) / 128), 128, 0, ctx->s_main>>>(ta, lvl_off[l - 1], lvl_off[l], count);
+      ++ctx->launch_count;
+    }
+    CU(cudaGetLastError());
+    timer_end(ctx, "tree", ctx->s_main, tb, te);
+    uint64_t *fa, *fb, *cnts;
+    if ((rc = ensure_t(ctx, "front_a", 8 * M, &fa))) return rc;
+    if ((rc = ensure_t(ctx, "front_b", 8 * M, &fb))) return rc;
+    if ((rc = ensure_t(ctx, "front_cnt", 16, &cnts))) return rc;
+    // frontier = {root}
+    const uint64_t init[2] = {0, 1};
+    CU(cudaMemcpyAsync(fa, init, 8, cudaMemcpyHostToDevice, ctx->s_main));
+    CU(cudaMemcpyAsync(cnts, init + 1, 8, cudaMemcpyHostToDevice, ctx->s_main));
+    // invalid starts as the malformed entries
+    k_flags_or<<<grid_for(ctx, n, 256, 4), 256, 0, ctx->s_main>>>(badR, badS, nullptr, n, inv);
+    ++ctx->launch_count;
+    const int bgrid = ctx->sm_count * 8;
+    timer_begin(ctx, "bisect", ctx->s_main, &tb, &te);
+    uint64_t* cur = fa;
+    uint64_t* nxt = fb;
+    for (uint64_t l = L; l >= 1; --l) {
+      uint64_t* cur_cnt = cnts + ((L - l) & 1);
+      uint64_t* nxt_cnt = cnts + ((L - l + 1) & 1);
+      CU(cudaMemsetAsync(nxt_cnt, 0, 8, ctx->s_main));
+      k_bisect<<<bgrid, 128, 0, ctx->s_main>>>(ta, (int)l, lvl_off[l], cur, cur_cnt, nxt, nxt_cnt, tableY,
+                                               ctx->tableG);
+      ++ctx->launch_count;
+      std::swap(cur, nxt);
+    }
+    k_bisect_leaves<<<bgrid, 128, 0, ctx->s_main>>>(ta, cur, cnts + (L & 1), tableY, ctx->tableG, inv);
     ++ctx->launch_count;
     CU(cudaGetLastError());
+    timer_end(ctx, "bisect", ctx->s_main, tb, te);
+    // ---- confirmation: weighted check of every entry not flagged ----
+    const int wblocks = grid_for(ctx, n, kHashThreads, 8);
+    unsigned long long* wpart;
+    if ((rc = ensure_t(ctx, "w_partial", (size_t)wblocks * kPartialWords * 8, &wpart))) return rc;
+    k_weighted_sums<<<wblocks, kHashThreads, 0, ctx->s_main>>>(d_e, sb.s, z, inv, nullptr, n, wpart);
+    ++ctx->launch_count;
+    if ((rc = run_msm(ctx, ctx->s_main, pts, z, 4, inv, n, Rw))) return rc;
+    if ((rc = run_finalize(ctx, wpart, wblocks, nullptr, 0, Rw, nullptr, tableY, d_acc, nullptr))) return rc;
+    CU(cudaMemcpyAsync(&h_acc, d_acc, 1, cudaMemcpyDeviceToHost, ctx->s_main));
+    if ((rc = check_status(ctx))) return rc;
+    if (!h_acc) {
+      // errors that cancel inside unit aggregates: settle every entry by its own check
+      CheckArgs a{};
+      a.e = d_e;
+      a.s = sb.s;
+      a.R = sb.R;
+      a.n = n;
+      a.tableY = tableY;
+      a.tableG = ctx->tableG;
+      a.invalid = inv;
+      timer_begin(ctx, "check", ctx->s_main, &tb, &te);
+      k_entry_check<<<grid_for(ctx, n, 128, 8), 128, 0, ctx->s_main>>>(a);
+      ++ctx->launch_count;
+      CU(cudaGetLastError());
+      timer_end(ctx, "check", ctx->s_main, tb, te);
+    }
+  }
+  // ordered list of flagged entries and ccd^v over the others
+  k_compact<<<1, kCompactThreads, 0, ctx->s_main>>>(inv, n, batch->first_index, d_idx, std::min(cap, n), d_cnt);
+  ++ctx->launch_count;
+  k_sum_scalars<<<sblocks, kHashThreads, 0, ctx->s_main>>>(sb.s, n, inv, sp);
+  ++ctx->launch_count;
+  k_reduce_scalars<<<1, 32, 0, ctx->s_main>>>(sp, sblocks, d_ccd);
+  ++ctx->launch_count;
+  {
     const int pblocks = grid_for(ctx, n, kPointThreads, 8);
     uint32_t* pp;
     if ((rc = ensure_t(ctx, "ccd_ppart", (size_t)pblocks * kPointPartialWords * 4, &pp))) return rc;
-    PointArgs pa{};
-    pa.R = sb.R;
-    pa.count = n;
-    pa.partial = pp;
-    pa.skip = d_inv;
-    k_points<<<pblocks, kPointThreads, 0, ctx->s_main>>>(pa);
+    k_pts_sum<<<pblocks, kPointThreads, 0, ctx->s_main>>>(pts, inv, badR, n, pp);
     ++ctx->launch_count;
     k_sum_encode<<<1, kFinalThreads, 0, ctx->s_main>>>(pp, pblocks, nullptr, d_ccd + 32, nullptr);
     ++ctx->launch_count;
@@ -929,26 +1127,37 @@ int poslo_msm(poslo_ctx* ctx, const uint8_t* points, const uint8_t* scalars, uin
   int rc;
   if ((rc = reset_status(ctx))) return rc;
   const void *dp, *ds;
-  if ((rc = stage(ctx, "msm_pts", points, 32 * n, on_device, ctx->s_main, &dp))) return rc;
-  if ((rc = stage(ctx, "msm_sc", scalars, 32 * n, on_device, ctx->s_main, &ds))) return rc;
-  uint8_t* d_out;
-  uint32_t* d_bad;
-  if ((rc = ensure_t(ctx, "msm_out", 64, &d_out))) return rc;
-  d_bad = reinterpret_cast<uint32_t*>(d_out + 32);
+  if ((rc = stage(ctx, "msm_pts_in", points, 32 * n, on_device, ctx->s_main, &dp))) return rc;
+  if ((rc = stage(ctx, "msm_sc_in", scalars, 32 * n, on_device, ctx->s_main, &ds))) return rc;
   if (n == 0) {
     out[0] = 1;
     memset(out + 1, 0, 31);
     return POSLO_OK;
   }
-  if ((rc = run_msm_direct(ctx, ctx->s_main, static_cast<const uint8_t*>(dp), nullptr,
-                           static_cast<const uint8_t*>(ds), 32, n, nullptr, nullptr, d_out, d_bad)))
-    return rc;
-  uint8_t h[36];
-  CU(cudaMemcpyAsync(h, d_out, 36, cudaMemcpyDeviceToHost, ctx->s_main));
+  uint32_t* pts;
+  uint8_t* bad;
+  if ((rc = ensure_t(ctx, "pts", 4 * kPtsWords * n, &pts))) return rc;
+  if ((rc = ensure_t(ctx, "badR", n, &bad))) return rc;
+  uint32_t *ppart, npb;
+  if ((rc = run_points(ctx, static_cast<const uint8_t*>(dp), n, pts, bad, &ppart, &npb))) return rc;
+  CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_points, 0));
+  uint32_t* acc;
+  uint8_t* d_out;
+  if ((rc = ensure_t(ctx, "msm_acc", 128, &acc))) return rc;
+  if ((rc = ensure_t(ctx, "msm_out", 64, &d_out))) return rc;
+  if ((rc = run_msm(ctx, ctx->s_main, pts, static_cast<const uint32_t*>(ds), 8, bad, n, acc))) return rc;
+  k_encode_ext<<<1, 1, 0, ctx->s_main>>>(acc, d_out);
+  ++ctx->launch_count;
+  uint32_t *d_bad_cnt;
+  if ((rc = ensure_t(ctx, "msm_badcnt", 16, &d_bad_cnt))) return rc;
+  k_sum_encode<<<1, kFinalThreads, 0, ctx->s_main>>>(ppart, npb, nullptr, nullptr, d_bad_cnt);
+  ++ctx->launch_count;
+  uint8_t h[32];
+  uint32_t bad_cnt = 0;
+  CU(cudaMemcpyAsync(h, d_out, 32, cudaMemcpyDeviceToHost, ctx->s_main));
+  CU(cudaMemcpyAsync(&bad_cnt, d_bad_cnt, 4, cudaMemcpyDeviceToHost, ctx->s_main));
   if ((rc = check_status(ctx))) return rc;
-  uint32_t bad;
-  memcpy(&bad, h + 32, 4);
-  if (bad) return fail(ctx, POSLO_EINVAL, "%u points do not decode", bad);
+  if (bad_cnt) return fail(ctx, POSLO_EINVAL, "%u points do not decode", bad_cnt);
   memcpy(out, h, 32);
   return POSLO_OK;
 }

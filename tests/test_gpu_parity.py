@@ -285,3 +285,64 @@ def test_device_inputs_same_as_host(ctx):
     assert ctx.aver(hb) is ctx.aver(db) is False
     assert [list(x) if i == 0 else x for i, x in enumerate(ctx.distill(hb))] == \
            [list(x) if i == 0 else x for i, x in enumerate(ctx.distill(db))]
+
+
+@pytest.mark.parametrize("c", [8, 11, 13, 16])
+def test_msm_every_window_width(c):
+    """The bucket method gives the definition's result for every window width."""
+    import __graft_entry__
+    __graft_entry__.build()
+    n = 300
+    pts = [O.encode_point(O.scalar_mult(5 + 7 * i, O.G)) for i in range(n)]
+    ks = [int.from_bytes(synth.random_bytes(c, f"w{i}", 32).tobytes(), "little") >> (i % 5) for i in range(n)]
+    ks[3] = 0
+    ks[4] = (1 << 256) - 1
+    with poslo.Context(device=0, msm_window=c) as cx:
+        got = cx.msm(b"".join(pts), b"".join(k.to_bytes(32, "little") for k in ks))
+    assert got == O.msm(ks, pts)
+
+
+def test_msm_rejects_undecodable_point(ctx):
+    y = 2
+    while O.decode_point(y.to_bytes(32, "little")) is not None:
+        y += 1
+    pts = [O.encode_point(O.G), y.to_bytes(32, "little")]
+    with pytest.raises(poslo.PosloError):
+        ctx.msm(b"".join(pts), bytes(64))
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 17])
+def test_distill_small_batches_every_pattern(ctx, n):
+    """Every tamper pattern of a tiny batch (all 2^n for n <= 5)."""
+    D, n2 = 3, 4
+    km, sk, Y, msgs, subsets, s, R, _ = _f_data(60 + n, n, D, n2, 3, 40)
+    ds_l = O.ds_root(km.root, D)
+    ds = O.ds_serialize(ds_l)
+    patterns = range(1 << n) if n <= 5 else [0, 1, (1 << n) - 1, 0x5A5A & ((1 << n) - 1), 1 << (n - 1)]
+    for pat in patterns:
+        data = msgs.data.copy()
+        for t in range(n):
+            if pat >> t & 1:
+                data[int(msgs.offs[t])] ^= 0x11
+        bad = synth.Messages(data, msgs.offs)
+        b = ctx.make_batch(poslo.VARIANT_F, n2, Y, bad.data, bad.offs, b"".join(s), b"".join(R), ds)
+        idx, cs, cR = ctx.distill(b)
+        want = [t for t in range(n) if pat >> t & 1]
+        assert list(idx) == want, (n, pat)
+        keep = [t for t in range(n) if not pat >> t & 1]
+        assert cs == O.agg_scalars([s[t] for t in keep])
+        assert cR == O.agg_points([R[t] for t in keep])
+        assert ctx.aver(b, poslo.AGG_WEIGHTED) is (pat == 0)
+
+
+def test_distill_dense_tampering(ctx):
+    """40 % of 200 entries tampered: deep bisection with wide frontiers."""
+    D, n2, n = 4, 16, 200
+    km, sk, Y, msgs, subsets, s, R, _ = _f_data(70, n, D, n2, 1, 100)
+    ds_l = O.ds_root(km.root, D)
+    plan = synth.tamper_plan(70, msgs, 80)
+    bad = synth.apply_tamper(msgs, plan)
+    b = ctx.make_batch(poslo.VARIANT_F, n2, Y, bad.data, bad.offs, b"".join(s), b"".join(R), O.ds_serialize(ds_l))
+    idx, cs, cR = ctx.distill(b)
+    wi, ws, wR = O.distill_f(Y, bad.as_list(), 0, n2, s, R, ds_l)
+    assert list(idx) == wi == list(plan.idx) and cs == ws and cR == wR
