@@ -461,8 +461,9 @@ int run_msm(poslo_ctx* ctx, cudaStream_t st, const uint32_t* pts, const uint32_t
   if ((rc = ensure_t(ctx, "msm_L", 128 * (size_t)pl.windows * pl.nchunks, &L))) return rc;
   if ((rc = ensure_t(ctx, "msm_T", 128 * (size_t)pl.windows * pl.nchunks, &T))) return rc;
   if ((rc = ensure_t(ctx, "msm_groups", 128 * (size_t)pl.windows * (1 + pl.jbits), &groups))) return rc;
-  cudaEvent_t tb, te;
+  cudaEvent_t tb, te, sb_, se_;
   timer_begin(ctx, "msm", st, &tb, &te);
+  timer_begin(ctx, "msm_sort", st, &sb_, &se_);
   CU(cudaMemsetAsync(cnt, 0, 4 * nbw, st));
   if (n) {
     const int g = grid_for(ctx, n, 256, 8);
@@ -473,17 +474,24 @@ int run_msm(poslo_ctx* ctx, cudaStream_t st, const uint32_t* pts, const uint32_t
     k_msm_scatter<<<g, 256, 0, st>>>(z, skip, n, pl, off, rank, idx);
     ++ctx->launch_count;
   }
+  timer_end(ctx, "msm_sort", st, sb_, se_);
+  timer_begin(ctx, "msm_bucket", st, &sb_, &se_);
   k_msm_bucket<<<(unsigned)((nbw + 127) / 128), 128, 0, st>>>(pts, idx, off, cnt, std::max<uint64_t>(n, 1), pl,
                                                              buckets);
   ++ctx->launch_count;
+  timer_end(ctx, "msm_bucket", st, sb_, se_);
+  timer_begin(ctx, "msm_reduce", st, &sb_, &se_);
   const size_t nch = (size_t)pl.windows * pl.nchunks;
   k_msm_chunk<<<(unsigned)((nch + 127) / 128), 128, 0, st>>>(buckets, pl, L, T);
   ++ctx->launch_count;
   k_msm_groups<<<pl.windows * (1 + pl.jbits), 256, 0, st>>>(L, T, pl, groups);
   ++ctx->launch_count;
+  timer_end(ctx, "msm_reduce", st, sb_, se_);
+  timer_begin(ctx, "msm_final", st, &sb_, &se_);
   k_msm_final<<<1, 32, 0, st>>>(groups, pl, out);
   ++ctx->launch_count;
   CU(cudaGetLastError());
+  timer_end(ctx, "msm_final", st, sb_, se_);
   timer_end(ctx, "msm", st, tb, te);
   return POSLO_OK;
 }
