@@ -413,11 +413,12 @@ struct SignCArgs {
 // sum_t [z_t] P_t for 128-bit scalars z_t (4 words each) and stored points P_t (kPtsWords
 // each).  Scalars are cut into windows of c bits; in window w every point goes to bucket
 // digit_w(z_t), found by a counting sort (count with atomics, scan, scatter).  Bucket sums
-// B_{w,d} come from one thread per bucket; the window sum sum_d d B_{w,d} from chunks of
+// B_{w,d} come from a load-balanced pass over the sorted entries; the window sum sum_d d B_{w,d} from chunks of
 // kMsmChunk buckets (running sums inside a chunk, then a binary decomposition of the chunk
 // index), and the windows are joined by Horner's rule in one warp with quad-cooperative
 // doublings.
 constexpr int kMsmChunk = 16;
+constexpr int kMsmSeg = 16;     // sorted entries per thread in the bucket accumulation
 
 struct MsmPlan {
   int c;              // window bits (8..16)
@@ -476,7 +477,7 @@ struct TreeArgs {
 // ---- kernel declarations ----
 __global__ void k_epoch_seeds(const DsNode* __restrict__ ds, int nds, uint64_t e0, uint64_t ne,
                               uint32_t* __restrict__ x0_out, uint32_t* __restrict__ status);
-__global__ void __launch_bounds__(kHashThreads) k_hash(const HashArgs a);
+__global__ void __launch_bounds__(kHashThreads, 5) k_hash(const HashArgs a);
 __global__ void __launch_bounds__(kPointThreads) k_points(const PointArgs a);
 __global__ void k_table(const uint32_t* __restrict__ enc, uint32_t* __restrict__ table,
                         uint32_t* __restrict__ status, int use_base);
@@ -501,9 +502,12 @@ __global__ void k_msm_count(const uint32_t* z, const uint8_t* skip, uint64_t n, 
                             uint32_t* rank);
 __global__ void __launch_bounds__(1024) k_msm_scan(const uint32_t* cnt, uint32_t* off, MsmPlan pl);
 __global__ void k_msm_scatter(const uint32_t* z, const uint8_t* skip, uint64_t n, MsmPlan pl, const uint32_t* off,
-                              const uint32_t* rank, uint32_t* idx);
-__global__ void __launch_bounds__(128) k_msm_bucket(const uint32_t* pts, const uint32_t* idx, const uint32_t* off, const uint32_t* cnt,
-                             uint64_t n, MsmPlan pl, uint32_t* buckets);
+                              const uint32_t* rank, uint32_t* idx, uint16_t* bkt);
+__global__ void __launch_bounds__(128) k_msm_accum(const uint32_t* pts, const uint32_t* idx, const uint16_t* bkt,
+                                                   const uint32_t* off, const uint32_t* cnt, uint64_t n, MsmPlan pl,
+                                                   uint32_t* buckets, uint32_t* A, uint32_t* B);
+__global__ void __launch_bounds__(128) k_msm_combine(const uint32_t* off, const uint32_t* cnt, uint64_t n, MsmPlan pl,
+                                                     const uint32_t* A, const uint32_t* B, uint32_t* buckets);
 __global__ void __launch_bounds__(128) k_msm_chunk(const uint32_t* buckets, MsmPlan pl, uint32_t* L, uint32_t* T);
 __global__ void __launch_bounds__(256) k_msm_groups(const uint32_t* L, const uint32_t* T, MsmPlan pl, uint32_t* groups);
 __global__ void __launch_bounds__(32) k_msm_final(const uint32_t* groups, MsmPlan pl, uint32_t* out);
@@ -520,5 +524,11 @@ __global__ void __launch_bounds__(kPointThreads) k_pts_sum(const uint32_t* pts, 
                           uint32_t* partial);
 __global__ void k_flags_or(const uint8_t* a, const uint8_t* b, const uint8_t* c, uint64_t n, uint8_t* out);
 __global__ void k_encode_ext(const uint32_t* point, uint8_t* out);
+constexpr uint32_t kFlagChunk = 8192;
+__global__ void __launch_bounds__(1024) k_flag_count(const uint8_t* flags, uint64_t n, uint32_t* blockcnt);
+__global__ void __launch_bounds__(1024) k_flag_scan(const uint32_t* blockcnt, uint32_t nblocks, uint64_t* blockoff,
+                                                   uint64_t* total);
+__global__ void __launch_bounds__(1024) k_flag_scatter(const uint8_t* flags, uint64_t n, uint64_t first_index,
+                                                      const uint64_t* blockoff, uint64_t* out, uint64_t cap);
 
 }  // namespace poslo

@@ -217,61 +217,171 @@ __device__ __forceinline__ fe fe_mul(const fe& a, const fe& b) {
   return fe_fold512(t);
 }
 
-// Squaring: the 28 cross products a_i a_j (i < j) once (operand scanning with 64-bit
-// partial sums, each row ending in a fresh limb), doubled by a one-bit shift, plus the 8
-// diagonal squares a_i^2 at limb 2i in one carry chain.
+// Squaring: the 28 cross products a_i a_j (i < j) once, as row carry chains like mul_8x8
+// (row i covers columns 2i+1 .. i+8), doubled by a funnel shift, plus the 8 diagonal
+// squares a_i^2 at limb 2i in one multiply-add chain: 36 low + 36 high products instead of
+// 64 + 64.
 __device__ __forceinline__ fe fe_sq(const fe& a) {
   uint32_t t[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) t[k] = 0;
+  uint32_t unused;
+  // row 0: low halves of a_0 a_j, j = 1..7
+  asm("mad.lo.cc.u32 %0, %9, %10, %0;\n\t"
+      "madc.lo.cc.u32 %1, %9, %11, %1;\n\t"
+      "madc.lo.cc.u32 %2, %9, %12, %2;\n\t"
+      "madc.lo.cc.u32 %3, %9, %13, %3;\n\t"
+      "madc.lo.cc.u32 %4, %9, %14, %4;\n\t"
+      "madc.lo.cc.u32 %5, %9, %15, %5;\n\t"
+      "madc.lo.cc.u32 %6, %9, %16, %6;\n\t"
+      "addc.u32 %7, 0, 0;"
+      : "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]), "=r"(t[8]), "=r"(unused)
+      : "r"(a.v[0]), "r"(a.v[1]), "r"(a.v[2]), "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]), "r"(a.v[6]), "r"(a.v[7]));
+  // row 0: high halves
+  asm("mad.hi.cc.u32 %0, %8, %9, %0;\n\t"
+      "madc.hi.cc.u32 %1, %8, %10, %1;\n\t"
+      "madc.hi.cc.u32 %2, %8, %11, %2;\n\t"
+      "madc.hi.cc.u32 %3, %8, %12, %3;\n\t"
+      "madc.hi.cc.u32 %4, %8, %13, %4;\n\t"
+      "madc.hi.cc.u32 %5, %8, %14, %5;\n\t"
+      "madc.hi.cc.u32 %6, %8, %15, %6;\n\t"
+      "addc.u32 %7, %7, 0;"
+      : "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]), "+r"(t[8]), "+r"(t[9])
+      : "r"(a.v[0]), "r"(a.v[1]), "r"(a.v[2]), "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]), "r"(a.v[6]), "r"(a.v[7]));
+  // row 1: low halves of a_1 a_j, j = 2..7
+  asm("mad.lo.cc.u32 %0, %8, %9, %0;\n\t"
+      "madc.lo.cc.u32 %1, %8, %10, %1;\n\t"
+      "madc.lo.cc.u32 %2, %8, %11, %2;\n\t"
+      "madc.lo.cc.u32 %3, %8, %12, %3;\n\t"
+      "madc.lo.cc.u32 %4, %8, %13, %4;\n\t"
+      "madc.lo.cc.u32 %5, %8, %14, %5;\n\t"
+      "addc.cc.u32 %6, %6, 0;\n\t"
+      "addc.u32 %7, 0, 0;"
+      : "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]), "+r"(t[8]), "+r"(t[9]), "=r"(t[10])
+      : "r"(a.v[1]), "r"(a.v[2]), "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]), "r"(a.v[6]), "r"(a.v[7]));
+  // row 1: high halves
+  asm("mad.hi.cc.u32 %0, %7, %8, %0;\n\t"
+      "madc.hi.cc.u32 %1, %7, %9, %1;\n\t"
+      "madc.hi.cc.u32 %2, %7, %10, %2;\n\t"
+      "madc.hi.cc.u32 %3, %7, %11, %3;\n\t"
+      "madc.hi.cc.u32 %4, %7, %12, %4;\n\t"
+      "madc.hi.cc.u32 %5, %7, %13, %5;\n\t"
+      "addc.u32 %6, %6, 0;"
+      : "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]), "+r"(t[8]), "+r"(t[9]), "+r"(t[10])
+      : "r"(a.v[1]), "r"(a.v[2]), "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]), "r"(a.v[6]), "r"(a.v[7]));
+  // row 2: low halves of a_2 a_j, j = 3..7
+  asm("mad.lo.cc.u32 %0, %7, %8, %0;\n\t"
+      "madc.lo.cc.u32 %1, %7, %9, %1;\n\t"
+      "madc.lo.cc.u32 %2, %7, %10, %2;\n\t"
+      "madc.lo.cc.u32 %3, %7, %11, %3;\n\t"
+      "madc.lo.cc.u32 %4, %7, %12, %4;\n\t"
+      "addc.cc.u32 %5, %5, 0;\n\t"
+      "addc.u32 %6, 0, 0;"
+      : "+r"(t[5]), "+r"(t[6]), "+r"(t[7]), "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "=r"(t[11])
+      : "r"(a.v[2]), "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]), "r"(a.v[6]), "r"(a.v[7]));
+  // row 2: high halves
+  asm("mad.hi.cc.u32 %0, %6, %7, %0;\n\t"
+      "madc.hi.cc.u32 %1, %6, %8, %1;\n\t"
+      "madc.hi.cc.u32 %2, %6, %9, %2;\n\t"
+      "madc.hi.cc.u32 %3, %6, %10, %3;\n\t"
+      "madc.hi.cc.u32 %4, %6, %11, %4;\n\t"
+      "addc.u32 %5, %5, 0;"
+      : "+r"(t[6]), "+r"(t[7]), "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "+r"(t[11])
+      : "r"(a.v[2]), "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]), "r"(a.v[6]), "r"(a.v[7]));
+  // row 3: low halves of a_3 a_j, j = 4..7
+  asm("mad.lo.cc.u32 %0, %6, %7, %0;\n\t"
+      "madc.lo.cc.u32 %1, %6, %8, %1;\n\t"
+      "madc.lo.cc.u32 %2, %6, %9, %2;\n\t"
+      "madc.lo.cc.u32 %3, %6, %10, %3;\n\t"
+      "addc.cc.u32 %4, %4, 0;\n\t"
+      "addc.u32 %5, 0, 0;"
+      : "+r"(t[7]), "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "+r"(t[11]), "=r"(t[12])
+      : "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]), "r"(a.v[6]), "r"(a.v[7]));
+  // row 3: high halves
+  asm("mad.hi.cc.u32 %0, %5, %6, %0;\n\t"
+      "madc.hi.cc.u32 %1, %5, %7, %1;\n\t"
+      "madc.hi.cc.u32 %2, %5, %8, %2;\n\t"
+      "madc.hi.cc.u32 %3, %5, %9, %3;\n\t"
+      "addc.u32 %4, %4, 0;"
+      : "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "+r"(t[11]), "+r"(t[12])
+      : "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]), "r"(a.v[6]), "r"(a.v[7]));
+  // row 4: low halves of a_4 a_j, j = 5..7
+  asm("mad.lo.cc.u32 %0, %5, %6, %0;\n\t"
+      "madc.lo.cc.u32 %1, %5, %7, %1;\n\t"
+      "madc.lo.cc.u32 %2, %5, %8, %2;\n\t"
+      "addc.cc.u32 %3, %3, 0;\n\t"
+      "addc.u32 %4, 0, 0;"
+      : "+r"(t[9]), "+r"(t[10]), "+r"(t[11]), "+r"(t[12]), "=r"(t[13])
+      : "r"(a.v[4]), "r"(a.v[5]), "r"(a.v[6]), "r"(a.v[7]));
+  // row 4: high halves
+  asm("mad.hi.cc.u32 %0, %4, %5, %0;\n\t"
+      "madc.hi.cc.u32 %1, %4, %6, %1;\n\t"
+      "madc.hi.cc.u32 %2, %4, %7, %2;\n\t"
+      "addc.u32 %3, %3, 0;"
+      : "+r"(t[10]), "+r"(t[11]), "+r"(t[12]), "+r"(t[13])
+      : "r"(a.v[4]), "r"(a.v[5]), "r"(a.v[6]), "r"(a.v[7]));
+  // row 5: low halves of a_5 a_j, j = 6..7
+  asm("mad.lo.cc.u32 %0, %4, %5, %0;\n\t"
+      "madc.lo.cc.u32 %1, %4, %6, %1;\n\t"
+      "addc.cc.u32 %2, %2, 0;\n\t"
+      "addc.u32 %3, 0, 0;"
+      : "+r"(t[11]), "+r"(t[12]), "+r"(t[13]), "=r"(t[14])
+      : "r"(a.v[5]), "r"(a.v[6]), "r"(a.v[7]));
+  // row 5: high halves
+  asm("mad.hi.cc.u32 %0, %3, %4, %0;\n\t"
+      "madc.hi.cc.u32 %1, %3, %5, %1;\n\t"
+      "addc.u32 %2, %2, 0;"
+      : "+r"(t[12]), "+r"(t[13]), "+r"(t[14])
+      : "r"(a.v[5]), "r"(a.v[6]), "r"(a.v[7]));
+  // row 6: low halves of a_6 a_j, j = 7..7
+  asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\t"
+      "addc.cc.u32 %1, %1, 0;\n\t"
+      "addc.u32 %2, 0, 0;"
+      : "+r"(t[13]), "+r"(t[14]), "=r"(t[15])
+      : "r"(a.v[6]), "r"(a.v[7]));
+  // row 6: high halves
+  asm("mad.hi.cc.u32 %0, %2, %3, %0;\n\t"
+      "addc.u32 %1, %1, 0;"
+      : "+r"(t[14]), "+r"(t[15])
+      : "r"(a.v[6]), "r"(a.v[7]));
+  // double the cross products (their sum is below 2^511)
+#pragma unroll
+  for (int k = 15; k > 0; --k) t[k] = __funnelshift_l(t[k - 1], t[k], 1);
   t[0] = 0;
-#pragma unroll
-  for (int k = 1; k < 16; ++k) t[k] = 0;
-#pragma unroll
-  for (int i = 0; i < 7; ++i) {
-    uint64_t carry = 0;
-#pragma unroll
-    for (int j = i + 1; j < 8; ++j) {
-      const uint64_t p = (uint64_t)a.v[i] * a.v[j] + t[i + j] + carry;
-      t[i + j] = (uint32_t)p;
-      carry = p >> 32;
-    }
-    t[i + 8] = (uint32_t)carry;
-  }
-#pragma unroll
-  for (int k = 15; k > 0; --k) t[k] = (t[k] << 1) | (t[k - 1] >> 31);
-  t[0] <<= 1;
-  uint32_t s[16];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    s[2 * i] = a.v[i] * a.v[i];
-    s[2 * i + 1] = __umulhi(a.v[i], a.v[i]);
-  }
-  asm("add.cc.u32 %0, %0, %16;\n\t"
-      "addc.cc.u32 %1, %1, %17;\n\t"
-      "addc.cc.u32 %2, %2, %18;\n\t"
-      "addc.cc.u32 %3, %3, %19;\n\t"
-      "addc.cc.u32 %4, %4, %20;\n\t"
-      "addc.cc.u32 %5, %5, %21;\n\t"
-      "addc.cc.u32 %6, %6, %22;\n\t"
-      "addc.cc.u32 %7, %7, %23;\n\t"
-      "addc.cc.u32 %8, %8, %24;\n\t"
-      "addc.cc.u32 %9, %9, %25;\n\t"
-      "addc.cc.u32 %10, %10, %26;\n\t"
-      "addc.cc.u32 %11, %11, %27;\n\t"
-      "addc.cc.u32 %12, %12, %28;\n\t"
-      "addc.cc.u32 %13, %13, %29;\n\t"
-      "addc.cc.u32 %14, %14, %30;\n\t"
-      "addc.u32 %15, %15, %31;"
+  asm("mad.lo.cc.u32 %0, %16, %16, %0;\n\t"
+      "madc.hi.cc.u32 %1, %16, %16, %1;\n\t"
+      "madc.lo.cc.u32 %2, %17, %17, %2;\n\t"
+      "madc.hi.cc.u32 %3, %17, %17, %3;\n\t"
+      "madc.lo.cc.u32 %4, %18, %18, %4;\n\t"
+      "madc.hi.cc.u32 %5, %18, %18, %5;\n\t"
+      "madc.lo.cc.u32 %6, %19, %19, %6;\n\t"
+      "madc.hi.cc.u32 %7, %19, %19, %7;\n\t"
+      "madc.lo.cc.u32 %8, %20, %20, %8;\n\t"
+      "madc.hi.cc.u32 %9, %20, %20, %9;\n\t"
+      "madc.lo.cc.u32 %10, %21, %21, %10;\n\t"
+      "madc.hi.cc.u32 %11, %21, %21, %11;\n\t"
+      "madc.lo.cc.u32 %12, %22, %22, %12;\n\t"
+      "madc.hi.cc.u32 %13, %22, %22, %13;\n\t"
+      "madc.lo.cc.u32 %14, %23, %23, %14;\n\t"
+      "madc.hi.u32 %15, %23, %23, %15;"
       : "+r"(t[0]), "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]),
         "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "+r"(t[11]), "+r"(t[12]), "+r"(t[13]), "+r"(t[14]), "+r"(t[15])
-      : "r"(s[0]), "r"(s[1]), "r"(s[2]), "r"(s[3]), "r"(s[4]), "r"(s[5]), "r"(s[6]), "r"(s[7]), "r"(s[8]),
-        "r"(s[9]), "r"(s[10]), "r"(s[11]), "r"(s[12]), "r"(s[13]), "r"(s[14]), "r"(s[15]));
+      : "r"(a.v[0]), "r"(a.v[1]), "r"(a.v[2]), "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]), "r"(a.v[6]), "r"(a.v[7]));
+  (void)unused;
   return fe_fold512(t);
 }
 
+// n successive squarings; the loop is kept rolled so the exponentiation chains of the
+// inversion and square root stay small in the instruction cache.
 __device__ __forceinline__ fe fe_sqn(fe a, int n) {
+#pragma unroll 1
   for (int i = 0; i < n; ++i) a = fe_sq(a);
   return a;
 }
+
+// Out-of-line copies for loops whose bodies would otherwise hold many inlined products
+// (a mixed addition is seven): one shared body keeps the loop inside the instruction cache.
+static __device__ __noinline__ fe fe_mul_nl(const fe a, const fe b) { return fe_mul(a, b); }
 
 // Multiply by a small constant k < 2^26 and fold.
 __device__ __forceinline__ fe fe_mul_small(const fe& a, uint32_t k) {

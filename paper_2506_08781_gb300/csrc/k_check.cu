@@ -183,4 +183,85 @@ __global__ void k_encode_ext(const uint32_t* point, uint8_t* out) {
   }
 }
 
+// Ordered compaction across many blocks: block b owns flags [b*kFlagChunk, (b+1)*kFlagChunk).
+// Pass 1 counts, pass 2 scans the counts (one block), pass 3 writes first_index + t of
+// every flagged t in ascending order.
+__global__ void __launch_bounds__(1024) k_flag_count(const uint8_t* flags, uint64_t n, uint32_t* blockcnt) {
+  __shared__ uint32_t tot;
+  if (threadIdx.x == 0) tot = 0;
+  __syncthreads();
+  const uint64_t lo = (uint64_t)blockIdx.x * kFlagChunk;
+  uint32_t c = 0;
+  for (uint64_t t = lo + threadIdx.x; t < lo + kFlagChunk && t < n; t += blockDim.x) c += flags[t] ? 1u : 0u;
+  c = __reduce_add_sync(0xffffffffu, c);
+  if ((threadIdx.x & 31) == 0) atomicAdd(&tot, c);
+  __syncthreads();
+  if (threadIdx.x == 0) blockcnt[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_flag_scan(const uint32_t* blockcnt, uint32_t nblocks, uint64_t* blockoff,
+                                                   uint64_t* total) {
+  __shared__ uint64_t warp_sums[32];
+  __shared__ uint64_t base;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint32_t c0 = 0; c0 < nblocks; c0 += blockDim.x) {
+    const uint32_t b = c0 + threadIdx.x;
+    const uint64_t v = b < nblocks ? blockcnt[b] : 0;
+    uint64_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      uint64_t w = warp_sums[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t u = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += u;
+      }
+      warp_sums[lane] = w;
+    }
+    __syncthreads();
+    const uint64_t excl = base + (warp ? warp_sums[warp - 1] : 0) + incl - v;
+    if (b < nblocks) blockoff[b] = excl;
+    __syncthreads();
+    if (threadIdx.x == 0) base += warp_sums[31];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = base;
+}
+
+__global__ void __launch_bounds__(1024) k_flag_scatter(const uint8_t* flags, uint64_t n, uint64_t first_index,
+                                                      const uint64_t* blockoff, uint64_t* out, uint64_t cap) {
+  __shared__ uint32_t warp_tot[32];
+  __shared__ uint64_t base;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) base = blockoff[blockIdx.x];
+  __syncthreads();
+  const uint64_t lo = (uint64_t)blockIdx.x * kFlagChunk;
+  for (uint64_t c0 = lo; c0 < lo + kFlagChunk && c0 < n; c0 += blockDim.x) {
+    const uint64_t t = c0 + threadIdx.x;
+    const bool f = t < n && t < lo + kFlagChunk && flags[t] != 0;
+    const uint32_t m = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) warp_tot[warp] = __popc(m);
+    __syncthreads();
+    uint64_t off = base;
+    for (int w = 0; w < warp; ++w) off += warp_tot[w];
+    off += __popc(m & ((1u << lane) - 1u));
+    if (f && off < cap) out[off] = first_index + t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint64_t tot = 0;
+      for (int w = 0; w < 32; ++w) tot += warp_tot[w];
+      base += tot;
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace poslo

@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(1024) k_msm_scan(const uint32_t* cnt, uint32_t
 
 // Counting sort, pass 3: entry indices in bucket order, per window.
 __global__ void k_msm_scatter(const uint32_t* z, const uint8_t* skip, uint64_t n, MsmPlan pl, const uint32_t* off,
-                              const uint32_t* rank, uint32_t* idx) {
+                              const uint32_t* rank, uint32_t* idx, uint16_t* bkt) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
     if (skip && skip[t]) continue;
@@ -68,27 +68,80 @@ __global__ void k_msm_scatter(const uint32_t* z, const uint8_t* skip, uint64_t n
     z_load(z, pl.sw, t, zw);
     for (int w = 0; w < pl.windows; ++w) {
       const uint32_t d = z_digit(zw, pl.sw, w, pl.c);
-      if (d) idx[(size_t)w * n + off[(size_t)w * pl.nb + d] + rank[(size_t)w * n + t]] = (uint32_t)t;
+      if (d) {
+        const size_t pos = (size_t)w * n + off[(size_t)w * pl.nb + d] + rank[(size_t)w * n + t];
+        idx[pos] = (uint32_t)t;
+        bkt[pos] = (uint16_t)d;
+      }
     }
   }
 }
 
-// Bucket sums B_{w,d}: one thread per bucket, mixed additions of its points.
-__global__ void __launch_bounds__(128) k_msm_bucket(const uint32_t* pts, const uint32_t* idx, const uint32_t* off,
-                                                    const uint32_t* cnt, uint64_t n, MsmPlan pl, uint32_t* buckets) {
+// Bucket sums B_{w,d}, load-balanced: thread (w, tau) adds exactly the kMsmSeg sorted entries
+// at positions [tau kMsmSeg, (tau+1) kMsmSeg) of window w, cutting its run wherever the
+// bucket changes.  A bucket lying strictly inside the range is written directly; the first
+// run goes to A[w][tau], the last (when different) to B[w][tau], and k_msm_combine joins
+// the pieces of buckets that cross range boundaries.
+__global__ void __launch_bounds__(128) k_msm_accum(const uint32_t* pts, const uint32_t* idx, const uint16_t* bkt,
+                                                   const uint32_t* off, const uint32_t* cnt, uint64_t n, MsmPlan pl,
+                                                   uint32_t* buckets, uint32_t* A, uint32_t* B) {
+  const uint64_t nseg = (n + kMsmSeg - 1) / kMsmSeg;
+  const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= (uint64_t)pl.windows * nseg) return;
+  const uint32_t w = (uint32_t)(g / nseg);
+  const uint64_t tau = g % nseg;
+  const size_t last = (size_t)w * pl.nb + pl.nb - 1;
+  const uint64_t nnz = (uint64_t)off[last] + cnt[last];
+  const uint64_t p0 = tau * kMsmSeg;
+  if (p0 >= nnz) return;
+  const uint64_t p1 = min(p0 + kMsmSeg, nnz);
+  const uint32_t* li = idx + (size_t)w * n;
+  const uint16_t* lb = bkt + (size_t)w * n;
+  uint32_t cur = lb[p0];
+  bool first = true;
+  ge acc = ge_identity();
+  fe x, y, t2d;
+  pts_load(pts + (size_t)kPtsWords * __ldg(li + p0), x, y, t2d);
+  for (uint64_t p = p0; p < p1; ++p) {
+    const uint32_t d = lb[p];
+    if (d != cur) {
+      uint32_t* dst = first ? A + 32 * g : buckets + 32 * ((size_t)w * pl.nb + cur);
+      ge_store(dst, acc);
+      first = false;
+      acc = ge_identity();
+      cur = d;
+    }
+    fe nx = x, ny = y, nt = t2d;
+    if (p + 1 < p1) pts_load(pts + (size_t)kPtsWords * __ldg(li + p + 1), nx, ny, nt);
+    acc = ge_madd_nl(acc, x, y, t2d);
+    x = nx; y = ny; t2d = nt;
+  }
+  ge_store(first ? A + 32 * g : B + 32 * g, acc);
+}
+
+// Buckets that were not written whole by k_msm_accum: the run in the range holding the
+// bucket's first entry (A or B of that range) plus the first runs of the following ranges.
+__global__ void __launch_bounds__(128) k_msm_combine(const uint32_t* off, const uint32_t* cnt, uint64_t n, MsmPlan pl,
+                                                     const uint32_t* A, const uint32_t* B, uint32_t* buckets) {
   const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= (uint64_t)pl.windows * pl.nb) return;
   const uint32_t w = (uint32_t)(b / pl.nb), d = (uint32_t)(b % pl.nb);
-  ge acc = ge_identity();
-  if (d) {
-    const uint32_t* list = idx + (size_t)w * n + off[b];
-    const uint32_t len = cnt[b];
-    for (uint32_t k = 0; k < len; ++k) {
-      fe x, y, t2d;
-      pts_load(pts + (size_t)kPtsWords * __ldg(list + k), x, y, t2d);
-      acc = ge_madd(acc, x, y, t2d);
-    }
+  const uint32_t len = d ? cnt[b] : 0u;
+  if (len == 0) {
+    ge_store(buckets + 32 * b, ge_identity());
+    return;
   }
+  const uint64_t nseg = (n + kMsmSeg - 1) / kMsmSeg;
+  const size_t last = (size_t)w * pl.nb + pl.nb - 1;
+  const uint64_t nnz = (uint64_t)off[last] + cnt[last];
+  const uint64_t s = off[b], e = s + len - 1;
+  const uint64_t ts = s / kMsmSeg, te = e / kMsmSeg;
+  const uint64_t r_end = min((ts + 1) * kMsmSeg, nnz) - 1;   // last position of range ts
+  const bool starts_range = s == ts * kMsmSeg;
+  if (!starts_range && e < r_end) return;                    // strictly inside: written whole
+  const uint64_t g0 = (uint64_t)w * nseg;
+  ge acc = ge_load((starts_range ? A : B) + 32 * (g0 + ts));
+  for (uint64_t t = ts + 1; t <= te; ++t) acc = ge_add(acc, ge_load(A + 32 * (g0 + t)));
   ge_store(buckets + 32 * b, acc);
 }
 

@@ -36,62 +36,167 @@ __global__ void k_epoch_seeds(const DsNode* __restrict__ ds, int nds, uint64_t e
   *o = make_uint4(x[0], x[1], x[2], x[3]);
 }
 
-__global__ void __launch_bounds__(kHashThreads) k_hash(const HashArgs a) {
+// Entries are processed in tiles of kHashTile; inside a tile they are reordered by the
+// number of SHA-256 blocks of m_t || x_t (a counting sort in shared memory), so the lanes of
+// a warp run the same number of compressions.  Per entry, one loop drives every
+// compression (the PRF block, the message blocks, and the weight block in weighted mode)
+// through a single inlined copy of the compression function.
+constexpr int kHashTile = 256;
+constexpr int kHashClasses = 8;
+
+__global__ void __launch_bounds__(kHashThreads, 5) k_hash(const HashArgs a) {
   acc13 acc_e, acc_s;
   acc_zero(acc_e);
   acc_zero(acc_s);
   uint32_t bad = 0;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.n; t += stride) {
-    const uint64_t gi = a.first_index + t;
-    uint64_t i, j;
-    if (a.n2_log2 != 0xffffffffu) {
-      i = gi >> a.n2_log2;
-      j = gi & ((1ull << a.n2_log2) - 1);
-    } else {
-      i = gi / a.n2;
-      j = gi - i * a.n2;
-    }
-    const uint4 xs = __ldg(reinterpret_cast<const uint4*>(a.seeds) + (i - a.e0));
-    const uint32_t x0[4] = {xs.x, xs.y, xs.z, xs.w};
-    uint32_t x[4];
-    prf_entry(x0, (uint32_t)j, x);
-    const uint64_t o0 = a.offs[t] - a.base_off, o1 = a.offs[t + 1] - a.base_off;
-    uint32_t st[8];
-    hash_entry(a.msgs + o0, (uint32_t)(o1 - o0), x, st);
-    uint32_t d[8];
+  __shared__ uint16_t s_order[kHashTile];
+  __shared__ uint32_t s_cnt[kHashClasses], s_off[kHashClasses];
+  constexpr int kPer = kHashTile / kHashThreads;
+  const uint64_t ntiles = (a.n + kHashTile - 1) / kHashTile;
+  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const uint64_t base = tile * kHashTile;
+    const uint64_t rem = a.n - base;
+    const uint32_t m = rem < (uint64_t)kHashTile ? (uint32_t)rem : (uint32_t)kHashTile;
+    if (threadIdx.x < kHashClasses) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    uint32_t cls[kPer], pos[kPer];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) d[k] = bswap32(st[k]);
-    const sc e = sc_reduce256(d);
-    if (a.e_out) {
-      uint4* eo = reinterpret_cast<uint4*>(a.e_out + 32 * t);
-      eo[0] = make_uint4(e.v[0], e.v[1], e.v[2], e.v[3]);
-      eo[1] = make_uint4(e.v[4], e.v[5], e.v[6], e.v[7]);
-    }
-    uint32_t s[8];
-    if (a.s) {
-      const uint4* sp = reinterpret_cast<const uint4*>(a.s + 32 * t);
-      const uint4 s0 = __ldg(sp), s1 = __ldg(sp + 1);
-      s[0] = s0.x; s[1] = s0.y; s[2] = s0.z; s[3] = s0.w; s[4] = s1.x; s[5] = s1.y; s[6] = s1.z; s[7] = s1.w;
-      const bool canon = sc_is_canonical(s);
-      bad += canon ? 0u : 1u;
-      if (a.sbad_out) a.sbad_out[t] = canon ? 0 : 1;
-    }
-    if (a.weighted) {
-      uint32_t z[4];
-      weight_of(a.zpre, gi, z);
-      if (a.z_out) reinterpret_cast<uint4*>(a.z_out)[t] = make_uint4(z[0], z[1], z[2], z[3]);
-      uint32_t p[12];
-      mul_4x8(p, z, e.v);
-      acc_add<12>(acc_e, p);
-      if (a.s) {
-        mul_4x8(p, z, s);
-        acc_add<12>(acc_s, p);
+    for (int r = 0; r < kPer; ++r) {
+      const uint32_t k = threadIdx.x + r * kHashThreads;
+      if (k < m) {
+        const uint64_t L = a.offs[base + k + 1] - a.offs[base + k];
+        const uint64_t c = (L + 88) >> 6;
+        cls[r] = c < (uint64_t)(kHashClasses - 1) ? (uint32_t)c : (uint32_t)(kHashClasses - 1);
+        pos[r] = atomicAdd(&s_cnt[cls[r]], 1u);
       }
-    } else {
-      acc_add<8>(acc_e, e.v);
-      if (a.s) acc_add<8>(acc_s, s);
     }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t acc = 0;
+      for (int c = 0; c < kHashClasses; ++c) { s_off[c] = acc; acc += s_cnt[c]; }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+      const uint32_t k = threadIdx.x + r * kHashThreads;
+      if (k < m) s_order[s_off[cls[r]] + pos[r]] = (uint16_t)k;
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int r = 0; r < kPer; ++r) {
+      const uint32_t k = threadIdx.x + r * kHashThreads;
+      if (k >= m) continue;
+      const uint64_t t = base + s_order[k];
+      const uint64_t gi = a.first_index + t;
+      uint64_t i, j;
+      if (a.n2_log2 != 0xffffffffu) {
+        i = gi >> a.n2_log2;
+        j = gi & ((1ull << a.n2_log2) - 1);
+      } else {
+        i = gi / a.n2;
+        j = gi - i * a.n2;
+      }
+      const uint4 xs = __ldg(reinterpret_cast<const uint4*>(a.seeds) + (i - a.e0));
+      const uint64_t o0 = a.offs[t] - a.base_off, o1 = a.offs[t + 1] - a.base_off;
+      const uint32_t L = (uint32_t)(o1 - o0);
+      // padded stream of m || x (x is known after the PRF block)
+      EntryStream es;
+      {
+        const uintptr_t p = reinterpret_cast<uintptr_t>(a.msgs + o0);
+        const uint32_t sh = (uint32_t)(p & 3u);
+        es.base = reinterpret_cast<const uint32_t*>(p - sh);
+        es.sel = (sh + 3) | ((sh + 2) << 4) | ((sh + 1) << 8) | (sh << 12);
+        es.sh_nz = sh != 0;
+        es.L = L;
+        es.kmax = L > 0 ? (int32_t)((L + sh - 1) >> 2) : 0;
+        es.a = L & ~3u;
+      }
+      const uint32_t total = L + 16;
+      const uint32_t nb = (total + 9 + 63) >> 6;
+      const uint32_t iters = 1 + nb + (a.weighted ? 1u : 0u);
+      uint32_t st[8], dig[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      sha256_init(st);
+#pragma unroll 1
+      for (uint32_t it = 0; it < iters; ++it) {
+        uint32_t w[16];
+        if (it == 0) {
+          // PRF_0(x_0[i] || le32(j)): x0 || le32(j) || 0x00 || 0x80 ... || bitlen(21 bytes)
+          w[0] = xs.x; w[1] = xs.y; w[2] = xs.z; w[3] = xs.w;
+          w[4] = bswap32((uint32_t)j);
+          w[5] = 0x00800000u;
+#pragma unroll
+          for (int q = 6; q < 15; ++q) w[q] = 0;
+          w[15] = 21 * 8;
+        } else if (it <= nb) {
+          const uint32_t o = (it - 1) << 6;
+          if (o + 64 <= L) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) w[q] = load_msg_word(es, (o >> 2) + q);
+          } else {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) w[q] = stream_word(es, o + 4 * q);
+            if (it == nb) {
+              w[14] |= total >> 29;
+              w[15] |= total << 3;
+            }
+          }
+        } else {
+          // z_t = SHA-256("POSLO-Z" || verifier_seed || le64(t))[0..16)
+          const uint32_t lo = (uint32_t)gi, hi = (uint32_t)(gi >> 32);
+#pragma unroll
+          for (int q = 0; q < 9; ++q) w[q] = a.zpre[q];
+          w[9] = a.zpre[9] | (lo & 0xffu);
+          w[10] = ((lo >> 8) & 0xffu) << 24 | ((lo >> 16) & 0xffu) << 16 | ((lo >> 24) & 0xffu) << 8 | (hi & 0xffu);
+          w[11] = ((hi >> 8) & 0xffu) << 24 | ((hi >> 16) & 0xffu) << 16 | ((hi >> 24) & 0xffu) << 8 | 0x80u;
+          w[12] = 0; w[13] = 0; w[14] = 0; w[15] = 47 * 8;
+        }
+        sha256_compress(st, w);
+        if (it == 0) {
+          // x = first 16 bytes of the PRF digest, shifted into the stream after m
+          const uint32_t sr = 8u * (L & 3u);
+          es.S[0] = __funnelshift_r(st[0], 0u, sr);
+          es.S[1] = __funnelshift_r(st[1], st[0], sr);
+          es.S[2] = __funnelshift_r(st[2], st[1], sr);
+          es.S[3] = __funnelshift_r(st[3], st[2], sr);
+          es.S[4] = __funnelshift_r(0x80000000u, st[3], sr);
+          sha256_init(st);
+        } else if (it == nb) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) dig[q] = bswap32(st[q]);
+          sha256_init(st);
+        }
+      }
+      const sc e = sc_reduce256(dig);
+      if (a.e_out) {
+        uint4* eo = reinterpret_cast<uint4*>(a.e_out + 32 * t);
+        eo[0] = make_uint4(e.v[0], e.v[1], e.v[2], e.v[3]);
+        eo[1] = make_uint4(e.v[4], e.v[5], e.v[6], e.v[7]);
+      }
+      uint32_t s[8];
+      if (a.s) {
+        const uint4* sp = reinterpret_cast<const uint4*>(a.s + 32 * t);
+        const uint4 s0 = __ldg(sp), s1 = __ldg(sp + 1);
+        s[0] = s0.x; s[1] = s0.y; s[2] = s0.z; s[3] = s0.w; s[4] = s1.x; s[5] = s1.y; s[6] = s1.z; s[7] = s1.w;
+        const bool canon = sc_is_canonical(s);
+        bad += canon ? 0u : 1u;
+        if (a.sbad_out) a.sbad_out[t] = canon ? 0 : 1;
+      }
+      if (a.weighted) {
+        const uint32_t z[4] = {bswap32(st[0]), bswap32(st[1]), bswap32(st[2]), bswap32(st[3])};
+        if (a.z_out) reinterpret_cast<uint4*>(a.z_out)[t] = make_uint4(z[0], z[1], z[2], z[3]);
+        uint32_t pr[12];
+        mul_4x8(pr, z, e.v);
+        acc_add<12>(acc_e, pr);
+        if (a.s) {
+          mul_4x8(pr, z, s);
+          acc_add<12>(acc_s, pr);
+        }
+      } else {
+        acc_add<8>(acc_e, e.v);
+        if (a.s) acc_add<8>(acc_s, s);
+      }
+    }
+    __syncthreads();
   }
   // block reduction of the limb values as 64-bit sums
   __shared__ unsigned long long red[kHashThreads / 32][kPartialWords];

@@ -452,11 +452,16 @@ int run_msm(poslo_ctx* ctx, cudaStream_t st, const uint32_t* pts, const uint32_t
   int rc;
   const MsmPlan pl = forced ? *forced : msm_plan(ctx, n, sw);
   const size_t nbw = (size_t)pl.windows * pl.nb;
-  uint32_t *cnt, *off, *rank, *idx, *buckets, *L, *T, *groups;
+  uint32_t *cnt, *off, *rank, *idx, *buckets, *L, *T, *groups, *segA, *segB;
+  uint16_t* bkt;
+  const uint64_t nseg = (std::max<uint64_t>(n, 1) + kMsmSeg - 1) / kMsmSeg;
   if ((rc = ensure_t(ctx, "msm_cnt", 4 * nbw, &cnt))) return rc;
   if ((rc = ensure_t(ctx, "msm_off", 4 * nbw, &off))) return rc;
   if ((rc = ensure_t(ctx, "msm_rank", 4 * (size_t)pl.windows * std::max<uint64_t>(n, 1), &rank))) return rc;
   if ((rc = ensure_t(ctx, "msm_idx", 4 * (size_t)pl.windows * std::max<uint64_t>(n, 1), &idx))) return rc;
+  if ((rc = ensure_t(ctx, "msm_bkt", 2 * (size_t)pl.windows * std::max<uint64_t>(n, 1), &bkt))) return rc;
+  if ((rc = ensure_t(ctx, "msm_segA", 128 * (size_t)pl.windows * nseg, &segA))) return rc;
+  if ((rc = ensure_t(ctx, "msm_segB", 128 * (size_t)pl.windows * nseg, &segB))) return rc;
   if ((rc = ensure_t(ctx, "msm_buckets", 128 * nbw, &buckets))) return rc;
   if ((rc = ensure_t(ctx, "msm_L", 128 * (size_t)pl.windows * pl.nchunks, &L))) return rc;
   if ((rc = ensure_t(ctx, "msm_T", 128 * (size_t)pl.windows * pl.nchunks, &T))) return rc;
@@ -471,13 +476,18 @@ int run_msm(poslo_ctx* ctx, cudaStream_t st, const uint32_t* pts, const uint32_t
     ++ctx->launch_count;
     k_msm_scan<<<pl.windows, 1024, 0, st>>>(cnt, off, pl);
     ++ctx->launch_count;
-    k_msm_scatter<<<g, 256, 0, st>>>(z, skip, n, pl, off, rank, idx);
+    k_msm_scatter<<<g, 256, 0, st>>>(z, skip, n, pl, off, rank, idx, bkt);
     ++ctx->launch_count;
   }
   timer_end(ctx, "msm_sort", st, sb_, se_);
   timer_begin(ctx, "msm_bucket", st, &sb_, &se_);
-  k_msm_bucket<<<(unsigned)((nbw + 127) / 128), 128, 0, st>>>(pts, idx, off, cnt, std::max<uint64_t>(n, 1), pl,
-                                                             buckets);
+  if (n) {
+    const size_t nth = (size_t)pl.windows * nseg;
+    k_msm_accum<<<(unsigned)((nth + 127) / 128), 128, 0, st>>>(pts, idx, bkt, off, cnt, n, pl, buckets, segA, segB);
+    ++ctx->launch_count;
+  }
+  k_msm_combine<<<(unsigned)((nbw + 127) / 128), 128, 0, st>>>(off, cnt, std::max<uint64_t>(n, 1), pl, segA, segB,
+                                                              buckets);
   ++ctx->launch_count;
   timer_end(ctx, "msm_bucket", st, sb_, se_);
   timer_begin(ctx, "msm_reduce", st, &sb_, &se_);
@@ -517,6 +527,24 @@ int run_finalize(poslo_ctx* ctx, const unsigned long long* hpart, uint32_t nhb, 
   ++ctx->launch_count;
   CU(cudaGetLastError());
   timer_end(ctx, "finalize", ctx->s_main, tb, te);
+  return POSLO_OK;
+}
+
+// Ordered list of flagged entries (first_index + t, ascending) into out (room for cap);
+// the full count goes to *d_count (device).
+int run_compact(poslo_ctx* ctx, const uint8_t* flags, uint64_t n, uint64_t first_index, uint64_t* out, uint64_t cap,
+                uint64_t* d_count) {
+  int rc;
+  const uint32_t nb = (uint32_t)std::max<uint64_t>(1, (n + kFlagChunk - 1) / kFlagChunk);
+  uint32_t* bc;
+  uint64_t* bo;
+  if ((rc = ensure_t(ctx, "flag_cnt", 4 * (size_t)nb, &bc))) return rc;
+  if ((rc = ensure_t(ctx, "flag_off", 8 * (size_t)nb, &bo))) return rc;
+  k_flag_count<<<nb, 1024, 0, ctx->s_main>>>(flags, n, bc);
+  k_flag_scan<<<1, 1024, 0, ctx->s_main>>>(bc, nb, bo, d_count);
+  k_flag_scatter<<<nb, 1024, 0, ctx->s_main>>>(flags, n, first_index, bo, out, cap);
+  ctx->launch_count += 3;
+  CU(cudaGetLastError());
   return POSLO_OK;
 }
 
@@ -1098,20 +1126,24 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
     }
   }
   // ordered list of flagged entries and ccd^v over the others
-  k_compact<<<1, kCompactThreads, 0, ctx->s_main>>>(inv, n, batch->first_index, d_idx, std::min(cap, n), d_cnt);
-  ++ctx->launch_count;
-  k_sum_scalars<<<sblocks, kHashThreads, 0, ctx->s_main>>>(sb.s, n, inv, sp);
-  ++ctx->launch_count;
-  k_reduce_scalars<<<1, 32, 0, ctx->s_main>>>(sp, sblocks, d_ccd);
-  ++ctx->launch_count;
-  {
-    const int pblocks = grid_for(ctx, n, kPointThreads, 8);
-    uint32_t* pp;
-    if ((rc = ensure_t(ctx, "ccd_ppart", (size_t)pblocks * kPointPartialWords * 4, &pp))) return rc;
+  const int pblocks = grid_for(ctx, n, kPointThreads, 8);
+  uint32_t* pp;
+  if ((rc = ensure_t(ctx, "ccd_ppart", (size_t)pblocks * kPointPartialWords * 4, &pp))) return rc;
+  if (h_acc) {
+    // every entry valid: no list; ccd^v = the unit sums of the whole batch
+    CU(cudaMemsetAsync(d_cnt, 0, 8, ctx->s_main));
+    k_sum_scalars<<<sblocks, kHashThreads, 0, ctx->s_main>>>(sb.s, n, nullptr, sp);
+    k_reduce_scalars<<<1, 32, 0, ctx->s_main>>>(sp, sblocks, d_ccd);
+    k_sum_encode<<<1, kFinalThreads, 0, ctx->s_main>>>(ppart, npb, nullptr, d_ccd + 32, nullptr);
+    ctx->launch_count += 3;
+    CU(cudaGetLastError());
+  } else {
+    if ((rc = run_compact(ctx, inv, n, batch->first_index, d_idx, std::min(cap, n), d_cnt))) return rc;
+    k_sum_scalars<<<sblocks, kHashThreads, 0, ctx->s_main>>>(sb.s, n, inv, sp);
+    k_reduce_scalars<<<1, 32, 0, ctx->s_main>>>(sp, sblocks, d_ccd);
     k_pts_sum<<<pblocks, kPointThreads, 0, ctx->s_main>>>(pts, inv, badR, n, pp);
-    ++ctx->launch_count;
     k_sum_encode<<<1, kFinalThreads, 0, ctx->s_main>>>(pp, pblocks, nullptr, d_ccd + 32, nullptr);
-    ++ctx->launch_count;
+    ctx->launch_count += 4;
     CU(cudaGetLastError());
   }
   uint64_t cnt = 0;
