@@ -20,12 +20,15 @@ namespace poslo {
 
 
 constexpr int kHashThreads = 128;
+#ifndef POSLO_HASH_MIN_BLOCKS
+#define POSLO_HASH_MIN_BLOCKS 3   // resident blocks per SM the hash kernel is compiled for
+#endif
 constexpr int kPointThreads = 128;
 constexpr int kTableWindows = 64;   // 4-bit windows over 256 bits
 constexpr int kTableDigits = 8;     // signed digits |d| in 1..8
 
 // Device-side error codes written to the context's status word.
-enum : uint32_t { kErrNone = 0, kErrSeed = 1, kErrKey = 2, kErrPoint = 4, kErrTimeout = 8 };
+enum : uint32_t { kErrNone = 0, kErrSeed = 1, kErrKey = 2, kErrPoint = 4, kErrTimeout = 8, kErrInput = 16 };
 
 struct DsNode { uint32_t d, i; uint32_t seed[4]; };   // seed as 4 big-endian words
 
@@ -54,6 +57,7 @@ struct HashArgs {
   uint32_t* z_out;             // optional (weighted): n*4 words of z_t
   uint8_t* sbad_out;           // optional: n bytes, 1 = s_t is not canonical
   unsigned long long* partial; // per block: 13 u64 limb sums of e, 13 of s, 1 bad count (27 u64)
+  uint32_t* status;            // device status word (kErrInput for decreasing offsets)
 };
 
 constexpr int kPartialWords = 27;
@@ -477,7 +481,7 @@ struct TreeArgs {
 // ---- kernel declarations ----
 __global__ void k_epoch_seeds(const DsNode* __restrict__ ds, int nds, uint64_t e0, uint64_t ne,
                               uint32_t* __restrict__ x0_out, uint32_t* __restrict__ status);
-__global__ void __launch_bounds__(kHashThreads, 5) k_hash(const HashArgs a);
+__global__ void __launch_bounds__(kHashThreads, POSLO_HASH_MIN_BLOCKS) k_hash(const HashArgs a);
 __global__ void __launch_bounds__(kPointThreads) k_points(const PointArgs a);
 __global__ void k_table(const uint32_t* __restrict__ enc, uint32_t* __restrict__ table,
                         uint32_t* __restrict__ status, int use_base);
@@ -505,7 +509,7 @@ __global__ void k_msm_scatter(const uint32_t* z, const uint8_t* skip, uint64_t n
                               const uint32_t* rank, uint32_t* idx, uint16_t* bkt);
 __global__ void __launch_bounds__(128) k_msm_accum(const uint32_t* pts, const uint32_t* idx, const uint16_t* bkt,
                                                    const uint32_t* off, const uint32_t* cnt, uint64_t n, MsmPlan pl,
-                                                   uint32_t* buckets, uint32_t* A, uint32_t* B);
+                                                   const uint8_t* skip, uint32_t* buckets, uint32_t* A, uint32_t* B);
 __global__ void __launch_bounds__(128) k_msm_combine(const uint32_t* off, const uint32_t* cnt, uint64_t n, MsmPlan pl,
                                                      const uint32_t* A, const uint32_t* B, uint32_t* buckets);
 __global__ void __launch_bounds__(128) k_msm_chunk(const uint32_t* buckets, MsmPlan pl, uint32_t* L, uint32_t* T);

@@ -10,6 +10,23 @@
 #pragma once
 #include <cstdint>
 
+// Implementation switches (build flags): squaring, multiplication, the 512-to-256-bit fold
+// and addition/subtraction either as PTX carry chains or as 64-bit partial sums.  Measured on
+// GB300: the 64-bit partial sums (independent wide products the scheduler overlaps) are
+// faster than carry-flag chains for squaring and multiplication.
+#ifndef POSLO_SQ_CHAINS
+#define POSLO_SQ_CHAINS 0
+#endif
+#ifndef POSLO_MUL_WIDE
+#define POSLO_MUL_WIDE 1
+#endif
+#ifndef POSLO_FOLD_WIDE
+#define POSLO_FOLD_WIDE 0
+#endif
+#ifndef POSLO_ADD_WIDE
+#define POSLO_ADD_WIDE 0
+#endif
+
 namespace poslo {
 
 struct fe { uint32_t v[8]; };
@@ -34,6 +51,61 @@ __device__ __forceinline__ fe fe_sqrtm1() {
   return fe_const(0x4a0ea0b0u, 0xc4ee1b27u, 0xad2fe478u, 0x2f431806u, 0x3dfbd7a7u, 0x2b4d0099u, 0x4fc1df0bu, 0x2b832480u);
 }
 
+#if POSLO_ADD_WIDE
+// r = a + b, folding the carry out of bit 256 (2^256 = 38) until none is left.
+__device__ __forceinline__ fe fe_add(const fe& a, const fe& b) {
+  fe r;
+  uint64_t c = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    c += (uint64_t)a.v[k] + b.v[k];
+    r.v[k] = (uint32_t)c;
+    c >>= 32;
+  }
+#pragma unroll
+  for (int pass = 0; pass < 2; ++pass) {
+    uint64_t d = (uint64_t)r.v[0] + c * 38u;
+    r.v[0] = (uint32_t)d;
+    d >>= 32;
+#pragma unroll
+    for (int k = 1; k < 8; ++k) {
+      d += r.v[k];
+      r.v[k] = (uint32_t)d;
+      d >>= 32;
+    }
+    c = d;
+  }
+  return r;
+}
+
+// r = a - b: a borrow out of bit 256 means the wrapped value is 38 too large mod p, so 38 is
+// subtracted (twice at most).
+__device__ __forceinline__ fe fe_sub(const fe& a, const fe& b) {
+  fe r;
+  int64_t c = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    c += (int64_t)a.v[k] - (int64_t)b.v[k];
+    r.v[k] = (uint32_t)c;
+    c >>= 32;   // 0 or -1
+  }
+#pragma unroll
+  for (int pass = 0; pass < 2; ++pass) {
+    int64_t d = (int64_t)r.v[0] + c * 38;
+    r.v[0] = (uint32_t)d;
+    d >>= 32;
+#pragma unroll
+    for (int k = 1; k < 8; ++k) {
+      d += r.v[k];
+      r.v[k] = (uint32_t)d;
+      d >>= 32;
+    }
+    c = d;
+  }
+  return r;
+}
+
+#else
 // r = a + b, folding the carry out of bit 256 twice (2^256 = 38).
 __device__ __forceinline__ fe fe_add(const fe& a, const fe& b) {
   fe r;
@@ -107,8 +179,34 @@ __device__ __forceinline__ fe fe_sub(const fe& a, const fe& b) {
   return r;
 }
 
+#endif
+
 // Fold a 512-bit product t[0..15] to 256 bits: r = t_lo + 38 * t_hi, then fold the
 // small top limb (and a possible last carry) the same way.
+#if POSLO_FOLD_WIDE
+__device__ __forceinline__ fe fe_fold512(const uint32_t t[16]) {
+  fe r;
+  uint64_t c = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    c += (uint64_t)t[8 + k] * 38u + t[k];
+    r.v[k] = (uint32_t)c;
+    c >>= 32;
+  }
+  // c < 38 + 1: fold again, then a possible last carry (at most 1) as 38
+  uint64_t d = (uint64_t)r.v[0] + c * 38u;
+  r.v[0] = (uint32_t)d;
+  d >>= 32;
+#pragma unroll
+  for (int k = 1; k < 8; ++k) {
+    d += r.v[k];
+    r.v[k] = (uint32_t)d;
+    d >>= 32;
+  }
+  r.v[0] += (uint32_t)d * 38u;
+  return r;
+}
+#else
 __device__ __forceinline__ fe fe_fold512(const uint32_t t[16]) {
   fe r;
   uint32_t top;
@@ -156,6 +254,7 @@ __device__ __forceinline__ fe fe_fold512(const uint32_t t[16]) {
   r.v[0] += c * 38u;
   return r;
 }
+#endif
 
 // 8x8-limb schoolbook product.  Row i adds lo(a_i*b_j) into t[i+j] and hi(a_i*b_j) into
 // t[i+j+1], each as one carry chain inside a single asm statement (the carry flag does not
@@ -213,10 +312,28 @@ __device__ __forceinline__ void mul_8x8(uint32_t t[16], const uint32_t a[8], con
 
 __device__ __forceinline__ fe fe_mul(const fe& a, const fe& b) {
   uint32_t t[16];
+#if POSLO_MUL_WIDE
+  // operand scanning with 64-bit partial sums (independent wide products)
+#pragma unroll
+  for (int q = 0; q < 16; ++q) t[q] = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    uint64_t carry = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const uint64_t p = (uint64_t)a.v[i] * b.v[j] + t[i + j] + carry;
+      t[i + j] = (uint32_t)p;
+      carry = p >> 32;
+    }
+    t[i + 8] = (uint32_t)carry;
+  }
+#else
   mul_8x8(t, a.v, b.v);
+#endif
   return fe_fold512(t);
 }
 
+#if POSLO_SQ_CHAINS
 // Squaring: the 28 cross products a_i a_j (i < j) once, as row carry chains like mul_8x8
 // (row i covers columns 2i+1 .. i+8), doubled by a funnel shift, plus the 8 diagonal
 // squares a_i^2 at limb 2i in one multiply-add chain: 36 low + 36 high products instead of
@@ -370,6 +487,52 @@ __device__ __forceinline__ fe fe_sq(const fe& a) {
   (void)unused;
   return fe_fold512(t);
 }
+
+#else
+// Squaring: the 28 cross products a_i a_j (i < j) once (operand scanning with 64-bit
+// partial sums: independent wide products the scheduler can overlap), doubled by a funnel
+// shift, plus the 8 diagonal squares a_i^2 at limb 2i in one carry chain.
+__device__ __forceinline__ fe fe_sq(const fe& a) {
+  uint32_t t[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) t[k] = 0;
+#pragma unroll
+  for (int i = 0; i < 7; ++i) {
+    uint64_t carry = 0;
+#pragma unroll
+    for (int j = i + 1; j < 8; ++j) {
+      const uint64_t p = (uint64_t)a.v[i] * a.v[j] + t[i + j] + carry;
+      t[i + j] = (uint32_t)p;
+      carry = p >> 32;
+    }
+    t[i + 8] = (uint32_t)carry;
+  }
+#pragma unroll
+  for (int k = 15; k > 0; --k) t[k] = __funnelshift_l(t[k - 1], t[k], 1);
+  t[0] = 0;
+  asm("mad.lo.cc.u32 %0, %16, %16, %0;\n\t"
+      "madc.hi.cc.u32 %1, %16, %16, %1;\n\t"
+      "madc.lo.cc.u32 %2, %17, %17, %2;\n\t"
+      "madc.hi.cc.u32 %3, %17, %17, %3;\n\t"
+      "madc.lo.cc.u32 %4, %18, %18, %4;\n\t"
+      "madc.hi.cc.u32 %5, %18, %18, %5;\n\t"
+      "madc.lo.cc.u32 %6, %19, %19, %6;\n\t"
+      "madc.hi.cc.u32 %7, %19, %19, %7;\n\t"
+      "madc.lo.cc.u32 %8, %20, %20, %8;\n\t"
+      "madc.hi.cc.u32 %9, %20, %20, %9;\n\t"
+      "madc.lo.cc.u32 %10, %21, %21, %10;\n\t"
+      "madc.hi.cc.u32 %11, %21, %21, %11;\n\t"
+      "madc.lo.cc.u32 %12, %22, %22, %12;\n\t"
+      "madc.hi.cc.u32 %13, %22, %22, %13;\n\t"
+      "madc.lo.cc.u32 %14, %23, %23, %14;\n\t"
+      "madc.hi.u32 %15, %23, %23, %15;"
+      : "+r"(t[0]), "+r"(t[1]), "+r"(t[2]), "+r"(t[3]), "+r"(t[4]), "+r"(t[5]), "+r"(t[6]), "+r"(t[7]),
+        "+r"(t[8]), "+r"(t[9]), "+r"(t[10]), "+r"(t[11]), "+r"(t[12]), "+r"(t[13]), "+r"(t[14]), "+r"(t[15])
+      : "r"(a.v[0]), "r"(a.v[1]), "r"(a.v[2]), "r"(a.v[3]), "r"(a.v[4]), "r"(a.v[5]), "r"(a.v[6]), "r"(a.v[7]));
+  return fe_fold512(t);
+}
+
+#endif
 
 // n successive squarings; the loop is kept rolled so the exponentiation chains of the
 // inversion and square root stay small in the instruction cache.

@@ -84,7 +84,7 @@ __global__ void k_msm_scatter(const uint32_t* z, const uint8_t* skip, uint64_t n
 // the pieces of buckets that cross range boundaries.
 __global__ void __launch_bounds__(128) k_msm_accum(const uint32_t* pts, const uint32_t* idx, const uint16_t* bkt,
                                                    const uint32_t* off, const uint32_t* cnt, uint64_t n, MsmPlan pl,
-                                                   uint32_t* buckets, uint32_t* A, uint32_t* B) {
+                                                   const uint8_t* skip, uint32_t* buckets, uint32_t* A, uint32_t* B) {
   const uint64_t nseg = (n + kMsmSeg - 1) / kMsmSeg;
   const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= (uint64_t)pl.windows * nseg) return;
@@ -101,7 +101,8 @@ __global__ void __launch_bounds__(128) k_msm_accum(const uint32_t* pts, const ui
   bool first = true;
   ge acc = ge_identity();
   fe x, y, t2d;
-  pts_load(pts + (size_t)kPtsWords * __ldg(li + p0), x, y, t2d);
+  uint32_t tc = __ldg(li + p0);
+  pts_load(pts + (size_t)kPtsWords * tc, x, y, t2d);
   for (uint64_t p = p0; p < p1; ++p) {
     const uint32_t d = lb[p];
     if (d != cur) {
@@ -112,9 +113,15 @@ __global__ void __launch_bounds__(128) k_msm_accum(const uint32_t* pts, const ui
       cur = d;
     }
     fe nx = x, ny = y, nt = t2d;
-    if (p + 1 < p1) pts_load(pts + (size_t)kPtsWords * __ldg(li + p + 1), nx, ny, nt);
-    acc = ge_madd_nl(acc, x, y, t2d);
+    uint32_t tn = tc;
+    if (p + 1 < p1) {
+      tn = __ldg(li + p + 1);
+      pts_load(pts + (size_t)kPtsWords * tn, nx, ny, nt);
+    }
+    // entries whose point did not decode are sorted but never added
+    if (!(skip && skip[tc])) acc = ge_madd_nl(acc, x, y, t2d);
     x = nx; y = ny; t2d = nt;
+    tc = tn;
   }
   ge_store(first ? A + 32 * g : B + 32 * g, acc);
 }

@@ -44,7 +44,7 @@ __global__ void k_epoch_seeds(const DsNode* __restrict__ ds, int nds, uint64_t e
 constexpr int kHashTile = 256;
 constexpr int kHashClasses = 8;
 
-__global__ void __launch_bounds__(kHashThreads, 5) k_hash(const HashArgs a) {
+__global__ void __launch_bounds__(kHashThreads, POSLO_HASH_MIN_BLOCKS) k_hash(const HashArgs a) {
   acc13 acc_e, acc_s;
   acc_zero(acc_e);
   acc_zero(acc_s);
@@ -64,7 +64,9 @@ __global__ void __launch_bounds__(kHashThreads, 5) k_hash(const HashArgs a) {
     for (int r = 0; r < kPer; ++r) {
       const uint32_t k = threadIdx.x + r * kHashThreads;
       if (k < m) {
-        const uint64_t L = a.offs[base + k + 1] - a.offs[base + k];
+        const uint64_t lo = a.offs[base + k], hi = a.offs[base + k + 1];
+        if (hi < lo || lo < a.base_off || hi - lo > 0xffffffffull) atomicOr(a.status, kErrInput);
+        const uint64_t L = hi >= lo ? hi - lo : 0;
         const uint64_t c = (L + 88) >> 6;
         cls[r] = c < (uint64_t)(kHashClasses - 1) ? (uint32_t)c : (uint32_t)(kHashClasses - 1);
         pos[r] = atomicAdd(&s_cnt[cls[r]], 1u);
@@ -98,7 +100,8 @@ __global__ void __launch_bounds__(kHashThreads, 5) k_hash(const HashArgs a) {
       }
       const uint4 xs = __ldg(reinterpret_cast<const uint4*>(a.seeds) + (i - a.e0));
       const uint64_t o0 = a.offs[t] - a.base_off, o1 = a.offs[t + 1] - a.base_off;
-      const uint32_t L = (uint32_t)(o1 - o0);
+      // malformed offsets (flagged above) hash as empty messages and never read memory
+      const uint32_t L = (o1 >= o0 && o1 - o0 <= 0xffffffffull && a.offs[t] >= a.base_off) ? (uint32_t)(o1 - o0) : 0u;
       // padded stream of m || x (x is known after the PRF block)
       EntryStream es;
       {

@@ -121,11 +121,12 @@ extern "C" int poslo_hash_entries_noalloc(const poslo_batch* batch, uint8_t* e_o
   a.seeds = seeds;
   a.e_out = e_out;
   a.partial = partial;
+  a.status = status;
   k_hash<<<blocks, kHashThreads, 0, st>>>(a);
   if (cudaGetLastError() != cudaSuccess) return POSLO_EDEVICE;
   uint32_t h_status = 0;
   if (cudaMemcpyAsync(&h_status, status, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) return POSLO_EDEVICE;
   if (cudaStreamSynchronize(st) != cudaSuccess) return POSLO_EDEVICE;
-  if (h_status & kErrSeed) return POSLO_EINVAL;
+  if (h_status & (kErrSeed | kErrInput)) return POSLO_EINVAL;
   return POSLO_OK;
 }

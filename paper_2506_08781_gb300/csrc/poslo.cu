@@ -201,6 +201,7 @@ int check_status(poslo_ctx* ctx) {
   if (st & kErrSeed) return fail(ctx, POSLO_EINVAL, "a requested epoch seed is not disclosed by ds (SRet bottom)");
   if (st & kErrKey) return fail(ctx, POSLO_EINVAL, "public key Y does not decode");
   if (st & kErrTimeout) return fail(ctx, POSLO_ETIMEOUT, "device-side wait expired");
+  if (st & kErrInput) return fail(ctx, POSLO_EINVAL, "message offsets decrease (or precede msgs)");
   return POSLO_OK;
 }
 
@@ -285,10 +286,9 @@ int stage_batch(poslo_ctx* ctx, const poslo_batch* b, Staged& sb) {
       sb.msgs = b->msgs;
       sb.base_off = 0;
     } else {
+      // monotonicity of every offset is checked on the device (k_hash)
       const uint64_t lo = b->offs[0], hi = b->offs[b->n];
       if (hi < lo) return fail(ctx, POSLO_EINVAL, "offsets decrease");
-      for (uint64_t t = 0; t < b->n; ++t)
-        if (b->offs[t + 1] < b->offs[t]) return fail(ctx, POSLO_EINVAL, "offsets decrease at entry %llu", (unsigned long long)t);
       if ((rc = stage(ctx, "msgs", b->msgs + lo, hi - lo, false, ctx->s_main, &p))) return rc;
       sb.msgs = static_cast<const uint8_t*>(p);
       sb.base_off = lo;
@@ -340,6 +340,7 @@ int run_hash(poslo_ctx* ctx, const poslo_batch* b, const Staged& sb, uint8_t* e_
   make_zpre(ctx->vseed, a.zpre);
   a.z_out = z_out;
   a.partial = partial;
+  a.status = ctx->status;
   cudaEvent_t tb, te;
   timer_begin(ctx, "hash", ctx->s_main, &tb, &te);
   k_hash<<<blocks, kHashThreads, 0, ctx->s_main>>>(a);
@@ -446,62 +447,94 @@ MsmPlan msm_plan(poslo_ctx* ctx, uint64_t n, int sw) {
   return pl;
 }
 
-// sum_t [z_t] P_t over the stored points (skipping flagged entries) into out (32 words).
-int run_msm(poslo_ctx* ctx, cudaStream_t st, const uint32_t* pts, const uint32_t* z, int sw, const uint8_t* skip,
-            uint64_t n, uint32_t* out, const MsmPlan* forced = nullptr) {
+// Pippenger in two halves so the counting sort (which needs only the scalars) can run
+// while the points are still being decoded on the other stream.
+struct MsmState {
+  MsmPlan pl;
+  uint64_t n = 0;
+  uint32_t *cnt = nullptr, *off = nullptr, *idx = nullptr;
+  uint16_t* bkt = nullptr;
+};
+
+// Counting sort of (window, entry) pairs by digit; skip_sort entries take no part at all.
+int run_msm_sort(poslo_ctx* ctx, cudaStream_t st, const uint32_t* z, int sw, const uint8_t* skip_sort, uint64_t n,
+                 MsmState& ms, const MsmPlan* forced = nullptr) {
   int rc;
-  const MsmPlan pl = forced ? *forced : msm_plan(ctx, n, sw);
+  ms.pl = forced ? *forced : msm_plan(ctx, n, sw);
+  ms.n = n;
+  const MsmPlan& pl = ms.pl;
   const size_t nbw = (size_t)pl.windows * pl.nb;
-  uint32_t *cnt, *off, *rank, *idx, *buckets, *L, *T, *groups, *segA, *segB;
-  uint16_t* bkt;
-  const uint64_t nseg = (std::max<uint64_t>(n, 1) + kMsmSeg - 1) / kMsmSeg;
-  if ((rc = ensure_t(ctx, "msm_cnt", 4 * nbw, &cnt))) return rc;
-  if ((rc = ensure_t(ctx, "msm_off", 4 * nbw, &off))) return rc;
+  uint32_t* rank;
+  if ((rc = ensure_t(ctx, "msm_cnt", 4 * nbw, &ms.cnt))) return rc;
+  if ((rc = ensure_t(ctx, "msm_off", 4 * nbw, &ms.off))) return rc;
   if ((rc = ensure_t(ctx, "msm_rank", 4 * (size_t)pl.windows * std::max<uint64_t>(n, 1), &rank))) return rc;
-  if ((rc = ensure_t(ctx, "msm_idx", 4 * (size_t)pl.windows * std::max<uint64_t>(n, 1), &idx))) return rc;
-  if ((rc = ensure_t(ctx, "msm_bkt", 2 * (size_t)pl.windows * std::max<uint64_t>(n, 1), &bkt))) return rc;
+  if ((rc = ensure_t(ctx, "msm_idx", 4 * (size_t)pl.windows * std::max<uint64_t>(n, 1), &ms.idx))) return rc;
+  if ((rc = ensure_t(ctx, "msm_bkt", 2 * (size_t)pl.windows * std::max<uint64_t>(n, 1), &ms.bkt))) return rc;
+  cudaEvent_t sb_, se_;
+  timer_begin(ctx, "msm_sort", st, &sb_, &se_);
+  CU(cudaMemsetAsync(ms.cnt, 0, 4 * nbw, st));
+  if (n) {
+    const int g = grid_for(ctx, n, 256, 8);
+    k_msm_count<<<g, 256, 0, st>>>(z, skip_sort, n, pl, ms.cnt, rank);
+    k_msm_scan<<<pl.windows, 1024, 0, st>>>(ms.cnt, ms.off, pl);
+    k_msm_scatter<<<g, 256, 0, st>>>(z, skip_sort, n, pl, ms.off, rank, ms.idx, ms.bkt);
+    ctx->launch_count += 3;
+  }
+  CU(cudaGetLastError());
+  timer_end(ctx, "msm_sort", st, sb_, se_);
+  return POSLO_OK;
+}
+
+// Bucket sums (entries flagged in skip_add are left out), window sums and Horner's rule.
+int run_msm_finish(poslo_ctx* ctx, cudaStream_t st, const uint32_t* pts, const uint8_t* skip_add, MsmState& ms,
+                   uint32_t* out) {
+  int rc;
+  const MsmPlan& pl = ms.pl;
+  const uint64_t n = ms.n;
+  const size_t nbw = (size_t)pl.windows * pl.nb;
+  const uint64_t nseg = (std::max<uint64_t>(n, 1) + kMsmSeg - 1) / kMsmSeg;
+  uint32_t *buckets, *L, *T, *groups, *segA, *segB;
+  if ((rc = ensure_t(ctx, "msm_buckets", 128 * nbw, &buckets))) return rc;
   if ((rc = ensure_t(ctx, "msm_segA", 128 * (size_t)pl.windows * nseg, &segA))) return rc;
   if ((rc = ensure_t(ctx, "msm_segB", 128 * (size_t)pl.windows * nseg, &segB))) return rc;
-  if ((rc = ensure_t(ctx, "msm_buckets", 128 * nbw, &buckets))) return rc;
   if ((rc = ensure_t(ctx, "msm_L", 128 * (size_t)pl.windows * pl.nchunks, &L))) return rc;
   if ((rc = ensure_t(ctx, "msm_T", 128 * (size_t)pl.windows * pl.nchunks, &T))) return rc;
   if ((rc = ensure_t(ctx, "msm_groups", 128 * (size_t)pl.windows * (1 + pl.jbits), &groups))) return rc;
-  cudaEvent_t tb, te, sb_, se_;
-  timer_begin(ctx, "msm", st, &tb, &te);
-  timer_begin(ctx, "msm_sort", st, &sb_, &se_);
-  CU(cudaMemsetAsync(cnt, 0, 4 * nbw, st));
-  if (n) {
-    const int g = grid_for(ctx, n, 256, 8);
-    k_msm_count<<<g, 256, 0, st>>>(z, skip, n, pl, cnt, rank);
-    ++ctx->launch_count;
-    k_msm_scan<<<pl.windows, 1024, 0, st>>>(cnt, off, pl);
-    ++ctx->launch_count;
-    k_msm_scatter<<<g, 256, 0, st>>>(z, skip, n, pl, off, rank, idx, bkt);
-    ++ctx->launch_count;
-  }
-  timer_end(ctx, "msm_sort", st, sb_, se_);
+  cudaEvent_t sb_, se_;
   timer_begin(ctx, "msm_bucket", st, &sb_, &se_);
   if (n) {
     const size_t nth = (size_t)pl.windows * nseg;
-    k_msm_accum<<<(unsigned)((nth + 127) / 128), 128, 0, st>>>(pts, idx, bkt, off, cnt, n, pl, buckets, segA, segB);
+    k_msm_accum<<<(unsigned)((nth + 127) / 128), 128, 0, st>>>(pts, ms.idx, ms.bkt, ms.off, ms.cnt, n, pl, skip_add,
+                                                               buckets, segA, segB);
     ++ctx->launch_count;
   }
-  k_msm_combine<<<(unsigned)((nbw + 127) / 128), 128, 0, st>>>(off, cnt, std::max<uint64_t>(n, 1), pl, segA, segB,
-                                                              buckets);
+  k_msm_combine<<<(unsigned)((nbw + 127) / 128), 128, 0, st>>>(ms.off, ms.cnt, std::max<uint64_t>(n, 1), pl, segA,
+                                                              segB, buckets);
   ++ctx->launch_count;
   timer_end(ctx, "msm_bucket", st, sb_, se_);
   timer_begin(ctx, "msm_reduce", st, &sb_, &se_);
   const size_t nch = (size_t)pl.windows * pl.nchunks;
   k_msm_chunk<<<(unsigned)((nch + 127) / 128), 128, 0, st>>>(buckets, pl, L, T);
-  ++ctx->launch_count;
   k_msm_groups<<<pl.windows * (1 + pl.jbits), 256, 0, st>>>(L, T, pl, groups);
-  ++ctx->launch_count;
+  ctx->launch_count += 2;
   timer_end(ctx, "msm_reduce", st, sb_, se_);
   timer_begin(ctx, "msm_final", st, &sb_, &se_);
   k_msm_final<<<1, 32, 0, st>>>(groups, pl, out);
   ++ctx->launch_count;
   CU(cudaGetLastError());
   timer_end(ctx, "msm_final", st, sb_, se_);
+  return POSLO_OK;
+}
+
+// sum_t [z_t] P_t over the stored points, leaving out flagged entries, into out (32 words).
+int run_msm(poslo_ctx* ctx, cudaStream_t st, const uint32_t* pts, const uint32_t* z, int sw, const uint8_t* skip,
+            uint64_t n, uint32_t* out, const MsmPlan* forced = nullptr) {
+  MsmState ms;
+  int rc;
+  cudaEvent_t tb, te;
+  timer_begin(ctx, "msm", st, &tb, &te);
+  if ((rc = run_msm_sort(ctx, st, z, sw, skip, n, ms, forced))) return rc;
+  if ((rc = run_msm_finish(ctx, st, pts, skip, ms, out))) return rc;
   timer_end(ctx, "msm", st, tb, te);
   return POSLO_OK;
 }
@@ -716,6 +749,9 @@ int poslo_sign_f(poslo_ctx* ctx, const uint8_t y[32], const uint8_t root[16], ui
     return fail(ctx, POSLO_EINVAL, "bad sign_f arguments");
   if (n == 0) return POSLO_OK;
   if ((first_index + n - 1) / n2 >= (1ull << D)) return fail(ctx, POSLO_EINVAL, "entry index beyond n1*n2");
+  for (uint64_t t = 0; t < n; ++t)
+    if (offs[t + 1] < offs[t] || offs[t + 1] - offs[t] > 0xffffffffull)
+      return fail(ctx, POSLO_EINVAL, "offsets decrease at entry %llu", (unsigned long long)t);
   for (uint64_t t = 0; t < n * k; ++t)
     if (subsets[t] >= v) return fail(ctx, POSLO_EINVAL, "BPV subset index out of range");
   int rc;
@@ -787,6 +823,9 @@ int poslo_sign_c(poslo_ctx* ctx, const uint8_t y[32], const uint8_t r[32], const
   uint32_t* seeds;
   if ((rc = run_epoch_seeds(ctx, ds, 1, first_epoch, n_epochs, &seeds))) return rc;
   const uint64_t n = n_epochs * n2;
+  for (uint64_t t = 0; t < n; ++t)
+    if (offs[t + 1] < offs[t] || offs[t + 1] - offs[t] > 0xffffffffull)
+      return fail(ctx, POSLO_EINVAL, "offsets decrease at entry %llu", (unsigned long long)t);
   const void* p;
   SignCArgs a{};
   if ((rc = stage(ctx, "offs", offs, (n + 1) * 8, false, ctx->s_main, &p))) return rc;
@@ -932,12 +971,14 @@ int poslo_aver(poslo_ctx* ctx, const poslo_batch* batch, uint32_t agg_mode, uint
   unsigned long long* hpart;
   uint32_t nhb;
   if ((rc = run_hash(ctx, batch, sb, nullptr, weighted, F, z, &hpart, &nhb))) return rc;
+  MsmState ms;
+  if (weighted && (rc = run_msm_sort(ctx, ctx->s_main, z, 4, nullptr, batch->n, ms))) return rc;
   CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_table, 0));
   CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_points, 0));
   uint32_t* Rw = nullptr;
   if (weighted) {
     if ((rc = ensure_t(ctx, "R_weighted", 128, &Rw))) return rc;
-    if ((rc = run_msm(ctx, ctx->s_main, pts, z, 4, badR, batch->n, Rw))) return rc;
+    if ((rc = run_msm_finish(ctx, ctx->s_main, pts, badR, ms, Rw))) return rc;
   }
   uint8_t* d_acc;
   if ((rc = ensure_t(ctx, "accept", 16, &d_acc))) return rc;
@@ -1007,6 +1048,7 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
     a.z_out = z;
     a.sbad_out = badS;
     a.partial = hpart;
+    a.status = ctx->status;
     cudaEvent_t tb, te;
     timer_begin(ctx, "hash", ctx->s_main, &tb, &te);
     k_hash<<<blocks, kHashThreads, 0, ctx->s_main>>>(a);
@@ -1015,6 +1057,8 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
     timer_end(ctx, "hash", ctx->s_main, tb, te);
     nhb = (uint32_t)blocks;
   }
+  MsmState ms;
+  if ((rc = run_msm_sort(ctx, ctx->s_main, z, 4, nullptr, n, ms))) return rc;
   CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_table, 0));
   CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_points, 0));
   // A5-A6: weighted MSM and the weighted check of the whole batch
@@ -1023,7 +1067,7 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
   if ((rc = ensure_t(ctx, "R_weighted", 128, &Rw))) return rc;
   if ((rc = ensure_t(ctx, "final_words", 4 * 48, &words))) return rc;
   if ((rc = ensure_t(ctx, "accept", 16, &d_acc))) return rc;
-  if ((rc = run_msm(ctx, ctx->s_main, pts, z, 4, badR, n, Rw))) return rc;
+  if ((rc = run_msm_finish(ctx, ctx->s_main, pts, badR, ms, Rw))) return rc;
   if ((rc = run_finalize(ctx, hpart, nhb, ppart, npb, Rw, nullptr, tableY, d_acc, nullptr))) return rc;
   // unit sums of the good entries (ccd^v when every entry is valid)
   uint8_t* d_ccd;
@@ -1039,7 +1083,8 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
   const uint64_t capn = std::max<uint64_t>(std::min(cap, n), 1);
   if ((rc = ensure_t(ctx, "invalid_idx", 8 * capn + 8, &d_idx))) return rc;
   uint64_t* d_cnt = d_idx + capn;
-  if (h_acc) {
+  const bool all_valid = h_acc != 0;   // the fast path: no malformed entry, weighted check holds
+  if (all_valid) {
     CU(cudaMemsetAsync(inv, 0, n1, ctx->s_main));
   } else {
     // ---- A7: segment-tree bisection over unit aggregates ----
@@ -1106,9 +1151,10 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
     ++ctx->launch_count;
     if ((rc = run_msm(ctx, ctx->s_main, pts, z, 4, inv, n, Rw))) return rc;
     if ((rc = run_finalize(ctx, wpart, wblocks, nullptr, 0, Rw, nullptr, tableY, d_acc, nullptr))) return rc;
-    CU(cudaMemcpyAsync(&h_acc, d_acc, 1, cudaMemcpyDeviceToHost, ctx->s_main));
+    uint8_t confirmed = 0;
+    CU(cudaMemcpyAsync(&confirmed, d_acc, 1, cudaMemcpyDeviceToHost, ctx->s_main));
     if ((rc = check_status(ctx))) return rc;
-    if (!h_acc) {
+    if (!confirmed) {
       // errors that cancel inside unit aggregates: settle every entry by its own check
       CheckArgs a{};
       a.e = d_e;
@@ -1129,7 +1175,7 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
   const int pblocks = grid_for(ctx, n, kPointThreads, 8);
   uint32_t* pp;
   if ((rc = ensure_t(ctx, "ccd_ppart", (size_t)pblocks * kPointPartialWords * 4, &pp))) return rc;
-  if (h_acc) {
+  if (all_valid) {
     // every entry valid: no list; ccd^v = the unit sums of the whole batch
     CU(cudaMemsetAsync(d_cnt, 0, 8, ctx->s_main));
     k_sum_scalars<<<sblocks, kHashThreads, 0, ctx->s_main>>>(sb.s, n, nullptr, sp);

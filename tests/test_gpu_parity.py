@@ -346,3 +346,26 @@ def test_distill_dense_tampering(ctx):
     idx, cs, cR = ctx.distill(b)
     wi, ws, wR = O.distill_f(Y, bad.as_list(), 0, n2, s, R, ds_l)
     assert list(idx) == wi == list(plan.idx) and cs == ws and cR == wR
+
+
+def test_decreasing_offsets_are_einval(ctx):
+    """Offsets that go backwards are rejected (host and device inputs) before any read."""
+    import torch
+    D, n2, n = 2, 4, 8
+    km, sk, Y, msgs, subsets, s, R, _ = _f_data(80, n, D, n2, 10, 20)
+    ds = O.ds_serialize(O.ds_root(km.root, D))
+    offs = msgs.offs.copy()
+    offs[3], offs[4] = offs[4], offs[3]
+    hb = ctx.make_batch(poslo.VARIANT_F, n2, Y, msgs.data, offs, b"".join(s), b"".join(R), ds)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).copy()).cuda()
+    db = ctx.make_batch(poslo.VARIANT_F, n2, Y, dev(msgs.data), dev(offs.view(np.int64)),
+                        dev(np.frombuffer(b"".join(s), np.uint8)), dev(np.frombuffer(b"".join(R), np.uint8)), ds)
+    torch.cuda.synchronize()
+    for b in (hb, db):
+        for call in (lambda: ctx.aver(b), lambda: ctx.distill(b), lambda: ctx.hash_entries(b)):
+            with pytest.raises(poslo.PosloError) as e:
+                call()
+            assert e.value.code == -1
+    # the context stays usable
+    good = ctx.make_batch(poslo.VARIANT_F, n2, Y, msgs.data, msgs.offs, b"".join(s), b"".join(R), ds)
+    assert ctx.aver(good) is True
