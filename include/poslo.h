@@ -149,6 +149,37 @@ int poslo_aver(poslo_ctx* ctx, const poslo_batch* batch, uint32_t agg_mode, uint
 int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_idx, uint64_t cap,
                   uint64_t* n_invalid, uint8_t ccd_s[32], uint8_t ccd_R[32]);
 
+/*
+ * Many signers (IoT devices) verified together.  The entries of all devices are concatenated
+ * (device d owns entries dev_start[d] .. dev_start[d+1]-1); msgs, offs (N+1 offsets into
+ * msgs), s and R (N*32 each) are device-capable; the per-device arrays are host memory.
+ * Each device is a POSLO-F signer with its own key Y_d, epoch size n2[d], disclosed seeds
+ * (ds nodes ds_off[d] .. ds_off[d+1]-1 of ds) and index of its first entry first_index[d].
+ */
+typedef struct {
+  uint32_t n_dev;
+  const uint8_t* Y;             /* n_dev*32 public keys */
+  const uint64_t* dev_start;    /* n_dev+1 entry starts, dev_start[0] = 0 */
+  const uint64_t* first_index;  /* n_dev */
+  const uint32_t* n2;           /* n_dev */
+  const uint8_t* ds;            /* all devices' ds nodes, 24 bytes each */
+  const uint32_t* ds_off;       /* n_dev+1 node offsets, ds_off[0] = 0 */
+  const uint8_t* msgs;
+  const uint64_t* offs;
+  const uint8_t* s;
+  const uint8_t* R;
+  uint32_t on_device;           /* 1: msgs, offs, s, R are device pointers */
+} poslo_multi_batch;
+
+/* Per-device AVer + Distill for a multi-device batch: accept[d] = 1 iff every entry of
+ * device d passes its own check (except with probability <= 2^-128); invalid_pairs receives
+ * (device, global index) pairs of the failing entries, 2 uint64 per pair, sorted by device
+ * then index, room for cap pairs; *n_invalid is the full count (EBUFSMALL if it exceeds cap).
+ * Every stage is one launch over the segment table; one random linear combination checks
+ * all devices at once, and only devices that fail their unit aggregate are localised. */
+int poslo_aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, uint8_t* accept, uint64_t* invalid_pairs,
+                     uint64_t cap, uint64_t* n_invalid);
+
 /* ---- inspection entry points (single steps of the path, for parity tests) ---------------- */
 
 /* SRet (Fig. 2a) for epochs first_epoch .. first_epoch+n_epochs-1: x_0[i] (16 bytes each). */

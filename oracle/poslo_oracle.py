@@ -479,3 +479,15 @@ def msm(scalars: list, points: list):
             raise ValueError("undecodable point")
         acc = point_add(acc, scalar_mult(k, pt))
     return encode_point(acc)
+
+
+def verify_multi(devices: list):
+    """Many single-signer POSLO-F batches, each by its own definition: device d is accepted
+    iff every entry passes its own check; the invalid (device, index) pairs are listed by
+    device, then index.  devices[d] = (Y, msgs, first_index, n2, s_list, R_list, ds)."""
+    accept, pairs = [], []
+    for d, (Y, msgs, first, n2, s_list, R_list, ds) in enumerate(devices):
+        inv, _, _ = distill_f(Y, msgs, first, n2, s_list, R_list, ds)
+        accept.append(not inv)
+        pairs.extend((d, t) for t in inv)
+    return accept, pairs

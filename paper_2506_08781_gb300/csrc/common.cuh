@@ -58,7 +58,27 @@ struct HashArgs {
   uint8_t* sbad_out;           // optional: n bytes, 1 = s_t is not canonical
   unsigned long long* partial; // per block: 13 u64 limb sums of e, 13 of s, 1 bad count (27 u64)
   uint32_t* status;            // device status word (kErrInput for decreasing offsets)
+  // multi-device batches (n_seg > 0): entry t belongs to the device d with
+  // seg_start[d] <= t < seg_start[d+1]; its index in that signer's log is
+  // seg_first[d] + t - seg_start[d], and its epoch seeds start at seeds[seg_seed_off[d]]
+  // (epoch seg_e0[d]).  The weight z_t then uses the batch position t, unique across devices.
+  uint32_t n_seg;
+  const uint64_t* seg_start;
+  const uint64_t* seg_first;
+  const uint64_t* seg_seed_off;
+  const uint64_t* seg_e0;
+  const uint32_t* seg_n2;
 };
+
+// Largest d with start[d] <= t, for start[0] = 0 <= t < start[n].
+__device__ __forceinline__ uint32_t segment_of(const uint64_t* start, uint32_t n, uint64_t t) {
+  uint32_t lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (start[mid] <= t) lo = mid; else hi = mid;
+  }
+  return lo;
+}
 
 constexpr int kPartialWords = 27;
 
@@ -478,6 +498,16 @@ struct TreeArgs {
   uint8_t* tree_s;           // M-1 scalars
 };
 
+// ---- multi-device batches (k_multi.cu) ----
+struct SegSums {
+  uint32_t* Ew;    // n_dev * 8: sum z e mod q
+  uint32_t* Sw;    // n_dev * 8: sum z s mod q
+  uint32_t* Eu;    // n_dev * 8: sum e mod q
+  uint32_t* Su;    // n_dev * 8: sum s mod q
+  uint32_t* Ru;    // n_dev * 32: sum R (extended)
+  uint32_t* bad;   // n_dev: malformed entries
+};
+
 // ---- kernel declarations ----
 __global__ void k_epoch_seeds(const DsNode* __restrict__ ds, int nds, uint64_t e0, uint64_t ne,
                               uint32_t* __restrict__ x0_out, uint32_t* __restrict__ status);
@@ -528,6 +558,21 @@ __global__ void __launch_bounds__(kPointThreads) k_pts_sum(const uint32_t* pts, 
                           uint32_t* partial);
 __global__ void k_flags_or(const uint8_t* a, const uint8_t* b, const uint8_t* c, uint64_t n, uint8_t* out);
 __global__ void k_encode_ext(const uint32_t* point, uint8_t* out);
+__global__ void k_epoch_seeds_multi(const DsNode* ds_all, const uint32_t* ds_off, const uint64_t* seed_off,
+                                    const uint64_t* e0, uint32_t n_dev, uint32_t* seeds, uint32_t* status);
+__global__ void k_rebase_offs(const uint64_t* raw, const uint64_t* slot, const uint64_t* start,
+                              const uint64_t* msg_base, uint32_t n_dev, uint64_t* out, uint32_t* status);
+__global__ void __launch_bounds__(256) k_segment_sums(const uint8_t* e, const uint8_t* s, const uint32_t* z,
+                                                      const uint32_t* pts, const uint8_t* badR, const uint8_t* badS,
+                                                      const uint64_t* start, SegSums out);
+__global__ void __launch_bounds__(kFinalThreads) k_multi_check(const uint32_t* P1, const uint32_t* P2,
+                                                               const uint32_t* Sw, const uint8_t* dev_flag,
+                                                               uint32_t n_dev, const uint32_t* tableG,
+                                                               uint8_t* accept);
+__global__ void __launch_bounds__(128) k_device_unit_check(const uint32_t* Ypts, SegSums ss, uint32_t n_dev,
+                                                           const uint32_t* tableG, uint8_t* dev_flag);
+__global__ void k_device_to_entries(const uint8_t* dev_flag, const uint64_t* start, const uint8_t* badR,
+                                    uint8_t* skip);
 constexpr uint32_t kFlagChunk = 8192;
 __global__ void __launch_bounds__(1024) k_flag_count(const uint8_t* flags, uint64_t n, uint32_t* blockcnt);
 __global__ void __launch_bounds__(1024) k_flag_scan(const uint32_t* blockcnt, uint32_t nblocks, uint64_t* blockoff,

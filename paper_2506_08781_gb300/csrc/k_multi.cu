@@ -1,0 +1,215 @@
+// Multi-device batches: many signers' logs verified in one pass of each stage over a segment
+// table (device d owns entries [seg_start[d], seg_start[d+1]) of the concatenated batch).
+// The paper verifies one signer at a time (single-signer aggregation, Sec. 5); here every
+// stage is one launch for all devices, and one random linear combination checks them all
+// at once: sum_t z_t R_t - sum_d (sum_{t in d} z_t e_t) Y_d - (sum_t z_t s_t) G = O.
+#include "common.cuh"
+
+namespace poslo {
+
+// SRet for every (device, epoch) pair of the batch: seeds[s] for s in
+// [seed_off[d], seed_off[d+1]) is x_0[e0[d] + s - seed_off[d]] under device d's ds.
+__global__ void k_epoch_seeds_multi(const DsNode* ds_all, const uint32_t* ds_off, const uint64_t* seed_off,
+                                    const uint64_t* e0, uint32_t n_dev, uint32_t* seeds, uint32_t* status) {
+  const uint64_t total = seed_off[n_dev];
+  const uint64_t sidx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (sidx >= total) return;
+  const uint32_t d = segment_of(seed_off, n_dev, sidx);
+  const uint64_t target = e0[d] + (sidx - seed_off[d]);
+  const DsNode* ds = ds_all + ds_off[d];
+  int top = (int)(ds_off[d + 1] - ds_off[d]) - 1;
+  bool ok = top >= 0 && target < (((uint64_t)ds[top].i + 1) << ds[top].d);
+  while (ok && target < ((uint64_t)ds[top].i << ds[top].d)) {
+    --top;
+    ok = top >= 0;
+  }
+  uint32_t x[4] = {0, 0, 0, 0};
+  if (ok) {
+    const DsNode n = ds[top];
+    x[0] = n.seed[0]; x[1] = n.seed[1]; x[2] = n.seed[2]; x[3] = n.seed[3];
+    const uint64_t off = target - ((uint64_t)n.i << n.d);
+    for (int j = (int)n.d - 1; j >= 0; --j) {
+      uint32_t y[4];
+      prf_node(x, (uint32_t)(off >> j) & 1u, y);
+      x[0] = y[0]; x[1] = y[1]; x[2] = y[2]; x[3] = y[3];
+    }
+  } else {
+    atomicOr(status, kErrSeed);
+  }
+  reinterpret_cast<uint4*>(seeds)[sidx] = make_uint4(x[0], x[1], x[2], x[3]);
+}
+
+// Concatenated offsets: raw holds each device's n_d + 1 offsets at slot[d]; entry k of
+// device d becomes msg_base[d] + raw[slot[d] + k] - raw[slot[d]] at position start[d] + k.
+__global__ void k_rebase_offs(const uint64_t* raw, const uint64_t* slot, const uint64_t* start,
+                              const uint64_t* msg_base, uint32_t n_dev, uint64_t* out, uint32_t* status) {
+  const uint64_t total = slot[n_dev];
+  const uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= total) return;
+  const uint32_t d = segment_of(slot, n_dev, r);
+  const uint64_t k = r - slot[d];
+  const uint64_t v = raw[r], v0 = raw[slot[d]];
+  if (v < v0) atomicOr(status, kErrInput);
+  out[start[d] + k] = msg_base[d] + (v >= v0 ? v - v0 : 0);
+}
+
+// Per-device sums: weighted E_d = sum z e, S_d = sum z s (mod q), unit Eu_d, Su_d, the unit
+// point sum Ru_d and the count of malformed entries.  One block per device.
+constexpr int kSegThreads = 256;
+__global__ void __launch_bounds__(256) k_segment_sums(const uint8_t* e, const uint8_t* s, const uint32_t* z,
+                                                              const uint32_t* pts, const uint8_t* badR,
+                                                              const uint8_t* badS, const uint64_t* start,
+                                                              SegSums out) {
+  const uint32_t d = blockIdx.x;
+  const uint64_t lo = start[d], hi = start[d + 1];
+  acc13 Ew, Sw, Eu, Su;
+  acc_zero(Ew); acc_zero(Sw); acc_zero(Eu); acc_zero(Su);
+  ge acc = ge_identity();
+  uint32_t bad = 0;
+  for (uint64_t t = lo + threadIdx.x; t < hi; t += blockDim.x) {
+    if (badR[t] || badS[t]) {
+      ++bad;
+      continue;
+    }
+    const uint4* ep = reinterpret_cast<const uint4*>(e + 32 * t);
+    const uint4* sp = reinterpret_cast<const uint4*>(s + 32 * t);
+    const uint4 e0 = ep[0], e1 = ep[1], s0 = __ldg(sp), s1 = __ldg(sp + 1);
+    const uint32_t ev[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
+    const uint32_t sv[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+    const uint4 zz = __ldg(reinterpret_cast<const uint4*>(z) + t);
+    const uint32_t zw[4] = {zz.x, zz.y, zz.z, zz.w};
+    uint32_t pr[12];
+    mul_4x8(pr, zw, ev);
+    acc_add<12>(Ew, pr);
+    mul_4x8(pr, zw, sv);
+    acc_add<12>(Sw, pr);
+    acc_add<8>(Eu, ev);
+    acc_add<8>(Su, sv);
+    fe x, y, t2d;
+    pts_load(pts + (size_t)kPtsWords * t, x, y, t2d);
+    acc = ge_madd(acc, x, y, t2d);
+  }
+  // scalars: 4 x 13 limb sums, warp shuffles then shared memory
+  __shared__ unsigned long long red[kSegThreads / 32][4 * 13 + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = 0; k < 4 * 13 + 1; ++k) {
+    unsigned long long v;
+    if (k < 13) v = Ew.v[k];
+    else if (k < 26) v = Sw.v[k - 13];
+    else if (k < 39) v = Eu.v[k - 26];
+    else if (k < 52) v = Su.v[k - 39];
+    else v = bad;
+    warp_sum_u64(v);
+    if (lane == 0) red[warp][k] = v;
+  }
+  // points: shared-memory tree
+  __shared__ uint32_t sp_[kSegThreads][32];
+  ge_store(sp_[threadIdx.x], acc);
+  __syncthreads();
+  for (int h = kSegThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) ge_store(sp_[threadIdx.x], ge_add(ge_load(sp_[threadIdx.x]), ge_load(sp_[threadIdx.x + h])));
+    __syncthreads();
+  }
+  if (threadIdx.x < 4) {
+    unsigned long long sums[13];
+    for (int k = 0; k < 13; ++k) {
+      unsigned long long v = 0;
+      for (int w = 0; w < kSegThreads / 32; ++w) v += red[w][13 * threadIdx.x + k];
+      sums[k] = v;
+    }
+    const sc r = limb_sums_to_scalar(sums);
+    uint32_t* dst = threadIdx.x == 0 ? out.Ew : threadIdx.x == 1 ? out.Sw : threadIdx.x == 2 ? out.Eu : out.Su;
+    for (int k = 0; k < 8; ++k) dst[8 * (size_t)d + k] = r.v[k];
+  }
+  if (threadIdx.x < 32) out.Ru[32 * (size_t)d + threadIdx.x] = sp_[0][threadIdx.x];
+  if (threadIdx.x == 0) {
+    unsigned long long v = 0;
+    for (int w = 0; w < kSegThreads / 32; ++w) v += red[w][52];
+    out.bad[d] = (uint32_t)v;
+  }
+}
+
+// Combined weighted check over the devices not flagged:
+// [8](P1 - P2 - (sum_d S_d) G) = O, with P1 = sum_t z_t R_t and P2 = sum_d E_d Y_d already
+// restricted to those devices.  One block.
+__global__ void __launch_bounds__(kFinalThreads) k_multi_check(const uint32_t* P1, const uint32_t* P2,
+                                                               const uint32_t* Sw, const uint8_t* dev_flag,
+                                                               uint32_t n_dev, const uint32_t* tableG,
+                                                               uint8_t* accept) {
+  __shared__ unsigned long long red[kFinalThreads / 32][13];
+  __shared__ int8_t dig[64];
+  __shared__ uint32_t pts_[kFinalThreads][32];
+  acc13 a;
+  acc_zero(a);
+  for (uint32_t d = threadIdx.x; d < n_dev; d += blockDim.x)
+    if (!(dev_flag && dev_flag[d])) acc_add<8>(a, Sw + 8 * (size_t)d);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = 0; k < 13; ++k) {
+    unsigned long long v = a.v[k];
+    warp_sum_u64(v);
+    if (lane == 0) red[warp][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long sums[13];
+    for (int k = 0; k < 13; ++k) {
+      unsigned long long v = 0;
+      for (int w = 0; w < kFinalThreads / 32; ++w) v += red[w][k];
+      sums[k] = v;
+    }
+    const sc S = limb_sums_to_scalar(sums);
+    recode4(S.v, dig);
+  }
+  __syncthreads();
+  ge term = threadIdx.x < kTableWindows ? table_pick(tableG, threadIdx.x, dig[threadIdx.x]) : ge_identity();
+  ge_store(pts_[threadIdx.x], term);
+  __syncthreads();
+  for (int h = kTableWindows / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) ge_store(pts_[threadIdx.x], ge_add(ge_load(pts_[threadIdx.x]), ge_load(pts_[threadIdx.x + h])));
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const ge diff = ge_sub(ge_sub(ge_load(P1), ge_load(P2)), ge_load(pts_[0]));
+    accept[0] = ge_is_identity(ge_mul_cofactor(diff)) ? 1 : 0;
+  }
+}
+
+// Per-device unit check [8](Ru - Eu Y_d - Su G) = O, one quad of lanes per device
+// (quad-cooperative double-and-add for Eu Y_d, the window table of G for Su G).  Devices
+// that fail, or hold malformed entries, are flagged.
+__global__ void __launch_bounds__(128) k_device_unit_check(const uint32_t* Ypts, SegSums ss, uint32_t n_dev,
+                                                           const uint32_t* tableG, uint8_t* dev_flag) {
+  const uint32_t quad = ((uint32_t)blockIdx.x * blockDim.x + threadIdx.x) >> 2;
+  const uint32_t d = quad < n_dev ? quad : n_dev - 1;   // surplus quads repeat the last device
+  ge Y;
+  fe t2d;
+  pts_load(Ypts + (size_t)kPtsWords * d, Y.X, Y.Y, t2d);
+  Y.Z = fe_one();
+  Y.T = fe_mul(Y.X, Y.Y);
+  const uint32_t* eu = ss.Eu + 8 * (size_t)d;
+  const uint32_t* su = ss.Su + 8 * (size_t)d;
+  // every lane runs every quad operation (full-mask shuffles): additions are selected, not
+  // branched around
+  ge acc = ge_identity();
+  for (int i = 252; i >= 0; --i) {
+    acc = ge_dbl_quad(acc);
+    const ge sum = ge_add_quad(acc, Y);
+    acc = ge_select(acc, sum, ((eu[i >> 5] >> (i & 31)) & 1u) != 0);
+  }
+  int carry = 0;
+  for (int w = 0; w < 64; ++w) acc = ge_add_quad(acc, table_pick(tableG, w, sc_digit4(su, w, carry)));
+  const ge diff = ge_sub(ge_load(ss.Ru + 32 * (size_t)d), acc);
+  const bool ok = ge_is_identity(ge_mul_cofactor(diff)) && ss.bad[d] == 0;
+  if ((threadIdx.x & 3) == 0 && quad < n_dev) dev_flag[d] = ok ? 0 : 1;
+}
+
+// Entry flags from device flags (entries of flagged devices are left out) or'ed with the
+// malformed-point flags.  One block per device.
+__global__ void k_device_to_entries(const uint8_t* dev_flag, const uint64_t* start, const uint8_t* badR,
+                                    uint8_t* skip) {
+  const uint32_t d = blockIdx.x;
+  const uint8_t f = dev_flag[d];
+  for (uint64_t t = start[d] + threadIdx.x; t < start[d + 1]; t += blockDim.x) skip[t] = (f || badR[t]) ? 1 : 0;
+}
+
+}  // namespace poslo

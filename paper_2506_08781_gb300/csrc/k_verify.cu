@@ -89,16 +89,28 @@ __global__ void __launch_bounds__(kHashThreads, POSLO_HASH_MIN_BLOCKS) k_hash(co
       const uint32_t k = threadIdx.x + r * kHashThreads;
       if (k >= m) continue;
       const uint64_t t = base + s_order[k];
-      const uint64_t gi = a.first_index + t;
-      uint64_t i, j;
-      if (a.n2_log2 != 0xffffffffu) {
-        i = gi >> a.n2_log2;
-        j = gi & ((1ull << a.n2_log2) - 1);
+      uint64_t gi, i, j, seed_idx, zi;
+      if (a.n_seg) {
+        const uint32_t d = segment_of(a.seg_start, a.n_seg, t);
+        gi = a.seg_first[d] + (t - a.seg_start[d]);
+        const uint32_t n2 = a.seg_n2[d];
+        i = gi / n2;
+        j = gi - i * n2;
+        seed_idx = a.seg_seed_off[d] + (i - a.seg_e0[d]);
+        zi = t;
       } else {
-        i = gi / a.n2;
-        j = gi - i * a.n2;
+        gi = a.first_index + t;
+        if (a.n2_log2 != 0xffffffffu) {
+          i = gi >> a.n2_log2;
+          j = gi & ((1ull << a.n2_log2) - 1);
+        } else {
+          i = gi / a.n2;
+          j = gi - i * a.n2;
+        }
+        seed_idx = i - a.e0;
+        zi = gi;
       }
-      const uint4 xs = __ldg(reinterpret_cast<const uint4*>(a.seeds) + (i - a.e0));
+      const uint4 xs = __ldg(reinterpret_cast<const uint4*>(a.seeds) + seed_idx);
       const uint64_t o0 = a.offs[t] - a.base_off, o1 = a.offs[t + 1] - a.base_off;
       // malformed offsets (flagged above) hash as empty messages and never read memory
       const uint32_t L = (o1 >= o0 && o1 - o0 <= 0xffffffffull && a.offs[t] >= a.base_off) ? (uint32_t)(o1 - o0) : 0u;
@@ -145,7 +157,7 @@ __global__ void __launch_bounds__(kHashThreads, POSLO_HASH_MIN_BLOCKS) k_hash(co
           }
         } else {
           // z_t = SHA-256("POSLO-Z" || verifier_seed || le64(t))[0..16)
-          const uint32_t lo = (uint32_t)gi, hi = (uint32_t)(gi >> 32);
+          const uint32_t lo = (uint32_t)zi, hi = (uint32_t)(zi >> 32);
 #pragma unroll
           for (int q = 0; q < 9; ++q) w[q] = a.zpre[q];
           w[9] = a.zpre[9] | (lo & 0xffu);

@@ -1248,4 +1248,227 @@ int poslo_msm(poslo_ctx* ctx, const uint8_t* points, const uint8_t* scalars, uin
   return POSLO_OK;
 }
 
+// ---------------------------------------------------------------------------- multi-device
+
+int poslo_aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, uint8_t* accept, uint64_t* invalid_pairs,
+                     uint64_t cap, uint64_t* n_invalid) {
+  if (!ctx || !mb || !accept || !n_invalid || mb->n_dev == 0 || !mb->Y || !mb->dev_start || !mb->first_index ||
+      !mb->n2 || !mb->ds || !mb->ds_off)
+    return fail(ctx, POSLO_EINVAL, "bad aver_multi arguments");
+  int rc;
+  const uint32_t nd = mb->n_dev;
+  const uint64_t N = mb->dev_start[nd];
+  if (mb->dev_start[0] != 0 || mb->ds_off[0] != 0) return fail(ctx, POSLO_EINVAL, "segment tables must start at 0");
+  std::vector<uint64_t> e0(nd), seed_off(nd + 1, 0);
+  for (uint32_t d = 0; d < nd; ++d) {
+    if (mb->dev_start[d + 1] < mb->dev_start[d]) return fail(ctx, POSLO_EINVAL, "dev_start decreases at %u", d);
+    if (mb->ds_off[d + 1] <= mb->ds_off[d]) return fail(ctx, POSLO_EINVAL, "device %u has no disclosed seed", d);
+    if (mb->n2[d] == 0) return fail(ctx, POSLO_EINVAL, "device %u: n2 = 0", d);
+    const uint64_t nd_ = mb->dev_start[d + 1] - mb->dev_start[d];
+    uint64_t ne = 0;
+    e0[d] = mb->first_index[d] / mb->n2[d];
+    if (nd_) ne = (mb->first_index[d] + nd_ - 1) / mb->n2[d] - e0[d] + 1;
+    seed_off[d + 1] = seed_off[d] + ne;
+  }
+  if (N && (!mb->offs || !mb->s || !mb->R)) return fail(ctx, POSLO_EINVAL, "missing batch arrays");
+  if ((rc = reset_status(ctx))) return rc;
+  // ---- stage the concatenated batch and the segment tables
+  poslo_batch view{};
+  view.variant = POSLO_VARIANT_F;
+  view.n2 = 1;
+  view.Y = mb->Y;
+  view.msgs = mb->msgs;
+  view.offs = mb->offs;
+  view.n = N;
+  view.s = mb->s;
+  view.R = mb->R;
+  view.R_count = N;
+  view.on_device = mb->on_device;
+  Staged sb;
+  if ((rc = stage_batch(ctx, &view, sb))) return rc;
+  std::vector<DsNode> nodes;
+  if ((rc = parse_ds(ctx, mb->ds, mb->ds_off[nd], nodes))) return rc;
+  std::vector<uint64_t> meta;   // start | first | seed_off | e0
+  meta.insert(meta.end(), mb->dev_start, mb->dev_start + nd + 1);
+  meta.insert(meta.end(), mb->first_index, mb->first_index + nd);
+  meta.insert(meta.end(), seed_off.begin(), seed_off.end());
+  meta.insert(meta.end(), e0.begin(), e0.end());
+  uint64_t* d_meta;
+  uint32_t *d_n2, *d_dsoff;
+  DsNode* d_nodes;
+  uint8_t* d_Y;
+  if ((rc = ensure_t(ctx, "m_meta", 8 * meta.size(), &d_meta))) return rc;
+  if ((rc = ensure_t(ctx, "m_n2", 4 * (size_t)nd, &d_n2))) return rc;
+  if ((rc = ensure_t(ctx, "m_dsoff", 4 * (size_t)(nd + 1), &d_dsoff))) return rc;
+  if ((rc = ensure_t(ctx, "m_nodes", sizeof(DsNode) * nodes.size(), &d_nodes))) return rc;
+  if ((rc = ensure_t(ctx, "m_Y", 32 * (size_t)nd, &d_Y))) return rc;
+  CU(cudaMemcpyAsync(d_meta, meta.data(), 8 * meta.size(), cudaMemcpyHostToDevice, ctx->s_main));
+  CU(cudaMemcpyAsync(d_n2, mb->n2, 4 * (size_t)nd, cudaMemcpyHostToDevice, ctx->s_main));
+  CU(cudaMemcpyAsync(d_dsoff, mb->ds_off, 4 * (size_t)(nd + 1), cudaMemcpyHostToDevice, ctx->s_main));
+  CU(cudaMemcpyAsync(d_nodes, nodes.data(), sizeof(DsNode) * nodes.size(), cudaMemcpyHostToDevice, ctx->s_main));
+  CU(cudaMemcpyAsync(d_Y, mb->Y, 32 * (size_t)nd, cudaMemcpyHostToDevice, ctx->s_main));
+  const uint64_t* seg_start = d_meta;
+  const uint64_t* seg_first = d_meta + nd + 1;
+  const uint64_t* seg_seed_off = d_meta + 2 * nd + 1;
+  const uint64_t* seg_e0 = d_meta + 3 * nd + 2;
+  // ---- A1: epoch seeds of every device
+  uint32_t* seeds;
+  if ((rc = ensure_t(ctx, "seeds", 16 * std::max<uint64_t>(seed_off[nd], 1), &seeds))) return rc;
+  if (seed_off[nd]) {
+    k_epoch_seeds_multi<<<(unsigned)((seed_off[nd] + 127) / 128), 128, 0, ctx->s_main>>>(
+        d_nodes, d_dsoff, seg_seed_off, seg_e0, nd, seeds, ctx->status);
+    ++ctx->launch_count;
+  }
+  // ---- A5 (side stream): decode every R_t and every Y_d
+  const uint64_t N1 = std::max<uint64_t>(N, 1);
+  uint32_t *pts, *Ypts, *ppart, npb, *ypart;
+  uint8_t *badR, *badS, *d_e, *badY;
+  if ((rc = ensure_t(ctx, "pts", 4 * kPtsWords * N1, &pts))) return rc;
+  if ((rc = ensure_t(ctx, "badR", N1, &badR))) return rc;
+  if ((rc = ensure_t(ctx, "badS", N1, &badS))) return rc;
+  if ((rc = ensure_t(ctx, "e_all", 32 * N1, &d_e))) return rc;
+  if ((rc = ensure_t(ctx, "m_Ypts", 4 * kPtsWords * (size_t)nd, &Ypts))) return rc;
+  if ((rc = ensure_t(ctx, "m_badY", nd, &badY))) return rc;
+  uint32_t* z;
+  if ((rc = ensure_t(ctx, "z", 16 * N1, &z))) return rc;
+  if ((rc = run_points(ctx, sb.R, N, pts, badR, &ppart, &npb))) return rc;
+  {
+    const int yb = grid_for(ctx, nd, kPointThreads, 8);
+    if ((rc = ensure_t(ctx, "m_ypart", (size_t)yb * kPointPartialWords * 4, &ypart))) return rc;
+    PointArgs pa{};
+    pa.R = d_Y;
+    pa.count = nd;
+    pa.partial = ypart;
+    pa.pts_out = Ypts;
+    pa.bad_out = badY;
+    k_points<<<yb, kPointThreads, 0, ctx->s_points>>>(pa);
+    ++ctx->launch_count;
+    CU(cudaEventRecord(ctx->ev_points, ctx->s_points));
+  }
+  // ---- A2-A4: segmented hashing with per-entry e_t, z_t
+  {
+    const int blocks = grid_for(ctx, N, kHashThreads, 8);
+    unsigned long long* hpart;
+    if ((rc = ensure_t(ctx, "hash_partial", (size_t)blocks * kPartialWords * 8, &hpart))) return rc;
+    HashArgs a{};
+    a.msgs = sb.msgs;
+    a.offs = sb.offs;
+    a.base_off = sb.base_off;
+    a.n = N;
+    a.n2 = 1;
+    a.n2_log2 = 0xffffffffu;
+    a.seeds = seeds;
+    a.e_out = d_e;
+    a.s = sb.s;
+    a.weighted = 1;
+    make_zpre(ctx->vseed, a.zpre);
+    a.z_out = z;
+    a.sbad_out = badS;
+    a.partial = hpart;
+    a.status = ctx->status;
+    a.n_seg = nd;
+    a.seg_start = seg_start;
+    a.seg_first = seg_first;
+    a.seg_seed_off = seg_seed_off;
+    a.seg_e0 = seg_e0;
+    a.seg_n2 = d_n2;
+    cudaEvent_t tb, te;
+    timer_begin(ctx, "hash", ctx->s_main, &tb, &te);
+    k_hash<<<blocks, kHashThreads, 0, ctx->s_main>>>(a);
+    ++ctx->launch_count;
+    CU(cudaGetLastError());
+    timer_end(ctx, "hash", ctx->s_main, tb, te);
+  }
+  MsmState ms;
+  if ((rc = run_msm_sort(ctx, ctx->s_main, z, 4, nullptr, N, ms))) return rc;
+  CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_points, 0));
+  // ---- A5-A6: sum_t z_t R_t, per-device sums, sum_d E_d Y_d, one combined check
+  uint32_t *P1, *P2, *segbuf;
+  uint8_t *d_acc, *dev_flag, *eskip;
+  if ((rc = ensure_t(ctx, "m_P", 256, &P1))) return rc;
+  P2 = P1 + 32;
+  if ((rc = ensure_t(ctx, "accept", 16, &d_acc))) return rc;
+  if ((rc = ensure_t(ctx, "m_devflag", nd, &dev_flag))) return rc;
+  if ((rc = ensure_t(ctx, "m_eskip", N1, &eskip))) return rc;
+  if ((rc = ensure_t(ctx, "m_seg", (size_t)nd * (32 + 32 + 1) * 4, &segbuf))) return rc;
+  SegSums ss;
+  ss.Ew = segbuf;
+  ss.Sw = ss.Ew + 8 * (size_t)nd;
+  ss.Eu = ss.Sw + 8 * (size_t)nd;
+  ss.Su = ss.Eu + 8 * (size_t)nd;
+  ss.Ru = ss.Su + 8 * (size_t)nd;
+  ss.bad = ss.Ru + 32 * (size_t)nd;
+  if ((rc = run_msm_finish(ctx, ctx->s_main, pts, badR, ms, P1))) return rc;
+  k_segment_sums<<<nd, 256, 0, ctx->s_main>>>(d_e, sb.s, z, pts, badR, badS, seg_start, ss);
+  ++ctx->launch_count;
+  if ((rc = run_msm(ctx, ctx->s_main, Ypts, ss.Ew, 8, nullptr, nd, P2))) return rc;
+  k_multi_check<<<1, kFinalThreads, 0, ctx->s_main>>>(P1, P2, ss.Sw, nullptr, nd, ctx->tableG, d_acc);
+  ++ctx->launch_count;
+  CU(cudaGetLastError());
+  uint8_t all_ok = 0;
+  std::vector<uint32_t> bad(nd);
+  std::vector<uint8_t> hbadY(nd);
+  CU(cudaMemcpyAsync(&all_ok, d_acc, 1, cudaMemcpyDeviceToHost, ctx->s_main));
+  CU(cudaMemcpyAsync(bad.data(), ss.bad, 4 * (size_t)nd, cudaMemcpyDeviceToHost, ctx->s_main));
+  CU(cudaMemcpyAsync(hbadY.data(), badY, nd, cudaMemcpyDeviceToHost, ctx->s_main));
+  if ((rc = check_status(ctx))) return rc;
+  for (uint32_t d = 0; d < nd; ++d)
+    if (hbadY[d]) return fail(ctx, POSLO_EINVAL, "public key of device %u does not decode", d);
+  uint64_t total_bad = 0;
+  for (uint32_t d = 0; d < nd; ++d) total_bad += bad[d];
+  std::vector<uint8_t> flag(nd, 0);
+  if (!(all_ok && total_bad == 0)) {
+    // ---- A7 across devices: unit check per device, then confirm the rest together
+    k_device_unit_check<<<(unsigned)((4ull * nd + 127) / 128), 128, 0, ctx->s_main>>>(Ypts, ss, nd, ctx->tableG,
+                                                                                     dev_flag);
+    k_device_to_entries<<<nd, 256, 0, ctx->s_main>>>(dev_flag, seg_start, badR, eskip);
+    ctx->launch_count += 2;
+    if ((rc = run_msm(ctx, ctx->s_main, pts, z, 4, eskip, N, P1))) return rc;
+    if ((rc = run_msm(ctx, ctx->s_main, Ypts, ss.Ew, 8, dev_flag, nd, P2))) return rc;
+    k_multi_check<<<1, kFinalThreads, 0, ctx->s_main>>>(P1, P2, ss.Sw, dev_flag, nd, ctx->tableG, d_acc);
+    ++ctx->launch_count;
+    uint8_t confirmed = 0;
+    CU(cudaMemcpyAsync(&confirmed, d_acc, 1, cudaMemcpyDeviceToHost, ctx->s_main));
+    CU(cudaMemcpyAsync(flag.data(), dev_flag, nd, cudaMemcpyDeviceToHost, ctx->s_main));
+    if ((rc = check_status(ctx))) return rc;
+    if (!confirmed) std::fill(flag.begin(), flag.end(), 1);   // cancelling errors: settle every device
+  }
+  // ---- localise inside the flagged devices (entry-level Distill per device)
+  uint64_t cnt = 0;
+  std::vector<uint64_t> idx;
+  for (uint32_t d = 0; d < nd; ++d) {
+    accept[d] = 1;
+    if (!flag[d]) continue;
+    const uint64_t lo = mb->dev_start[d], nd_ = mb->dev_start[d + 1] - lo;
+    poslo_batch b{};
+    b.variant = POSLO_VARIANT_F;
+    b.n2 = mb->n2[d];
+    b.Y = mb->Y + 32 * (size_t)d;
+    b.msgs = mb->msgs;
+    b.offs = mb->offs + lo;
+    b.n = nd_;
+    b.first_index = mb->first_index[d];
+    b.s = mb->s + 32 * lo;
+    b.R = mb->R + 32 * lo;
+    b.R_count = nd_;
+    b.ds = mb->ds + 24 * (size_t)mb->ds_off[d];
+    b.ds_nodes = mb->ds_off[d + 1] - mb->ds_off[d];
+    b.on_device = mb->on_device;
+    idx.assign(std::max<uint64_t>(nd_, 1), 0);
+    uint64_t k = 0;
+    if ((rc = poslo_distill(ctx, &b, idx.data(), nd_, &k, nullptr, nullptr))) return rc;
+    if (k) accept[d] = 0;
+    for (uint64_t q = 0; q < k; ++q, ++cnt) {
+      if (invalid_pairs && cnt < cap) {
+        invalid_pairs[2 * cnt] = d;
+        invalid_pairs[2 * cnt + 1] = idx[q];
+      }
+    }
+  }
+  *n_invalid = cnt;
+  if (cnt > cap) return fail(ctx, POSLO_EBUFSMALL, "%llu invalid entries, room for %llu", (unsigned long long)cnt,
+                             (unsigned long long)cap);
+  return POSLO_OK;
+}
+
 }  // extern "C"

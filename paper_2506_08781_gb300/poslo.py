@@ -28,7 +28,7 @@ EXPORTS = [
     "poslo_keygen_c", "poslo_keygen_f", "poslo_sign_c", "poslo_sign_f", "poslo_disclose",
     "poslo_aver", "poslo_distill", "poslo_epoch_seeds", "poslo_hash_entries", "poslo_msm",
     "poslo_set_profiling", "poslo_kernel_time", "poslo_reset_kernel_times",
-    "poslo_hash_entries_noalloc",
+    "poslo_hash_entries_noalloc", "poslo_aver_multi",
 ]
 
 
@@ -41,6 +41,12 @@ class PosloError(RuntimeError):
 class Params(C.Structure):
     _fields_ = [("device", C.c_int), ("msm_window", C.c_uint32), ("mem_budget", C.c_uint64),
                 ("verifier_seed", C.c_uint8 * 32)]
+
+
+class MultiBatch(C.Structure):
+    _fields_ = [("n_dev", C.c_uint32), ("Y", C.c_void_p), ("dev_start", C.c_void_p), ("first_index", C.c_void_p),
+                ("n2", C.c_void_p), ("ds", C.c_void_p), ("ds_off", C.c_void_p), ("msgs", C.c_void_p),
+                ("offs", C.c_void_p), ("s", C.c_void_p), ("R", C.c_void_p), ("on_device", C.c_uint32)]
 
 
 class Batch(C.Structure):
@@ -82,6 +88,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "poslo_kernel_time": ([vp, C.c_char_p, C.POINTER(C.c_double), C.POINTER(u64)], C.c_int),
         "poslo_reset_kernel_times": ([vp], None),
         "poslo_hash_entries_noalloc": ([C.POINTER(Batch), u8p, vp], C.c_int),
+        "poslo_aver_multi": ([vp, C.POINTER(MultiBatch), u8p, vp, u64, C.POINTER(u64)], C.c_int),
     }
     for name in EXPORTS:
         f = getattr(lib, name)
@@ -278,6 +285,36 @@ class Context:
         cb = self._cbatch(b)
         self._check(self.lib.poslo_distill(self.h, C.byref(cb), _ptr(idx), cap, C.byref(cnt), _ptr(cs), _ptr(cR)))
         return idx[:cnt.value].copy(), cs.tobytes(), cR.tobytes()
+
+    def aver_multi(self, Ys, dev_sizes, first_index, n2, ds_list, msgs, offs, s, R, cap: int | None = None):
+        """Multi-device AVer + Distill.  Ys: per-device 32-byte keys; dev_sizes: entries per
+        device; msgs/offs/s/R: the concatenated batch (numpy, or torch CUDA tensors)."""
+        nd = len(Ys)
+        dev_start = np.zeros(nd + 1, np.uint64)
+        dev_start[1:] = np.cumsum(np.asarray(dev_sizes, dtype=np.uint64))
+        ds_off = np.zeros(nd + 1, np.uint32)
+        ds_off[1:] = np.cumsum([len(d) // 24 for d in ds_list])
+        Yb = np.frombuffer(b"".join(bytes(y) for y in Ys), np.uint8).copy()
+        dsb = np.frombuffer(b"".join(ds_list), np.uint8).copy()
+        fi = np.ascontiguousarray(first_index, dtype=np.uint64)
+        n2a = np.ascontiguousarray(n2, dtype=np.uint32)
+        on_dev = _is_torch(offs) and offs.is_cuda
+        if not _is_torch(offs):
+            offs = np.ascontiguousarray(offs, dtype=np.uint64)
+            msgs, s, R = _u8(msgs), _u8(s), _u8(R)
+        mb = MultiBatch()
+        mb.n_dev = nd
+        mb.Y, mb.dev_start, mb.first_index, mb.n2 = _ptr(Yb), _ptr(dev_start), _ptr(fi), _ptr(n2a)
+        mb.ds, mb.ds_off = _ptr(dsb), _ptr(ds_off)
+        mb.msgs, mb.offs, mb.s, mb.R = _ptr(msgs), _ptr(offs), _ptr(s), _ptr(R)
+        mb.on_device = 1 if on_dev else 0
+        total = int(dev_start[-1])
+        cap = total if cap is None else cap
+        acc = np.zeros(nd, np.uint8)
+        pairs = np.zeros(2 * max(cap, 1), np.uint64)
+        cnt = C.c_uint64()
+        self._check(self.lib.poslo_aver_multi(self.h, C.byref(mb), _ptr(acc), _ptr(pairs), cap, C.byref(cnt)))
+        return acc.astype(bool), pairs[:2 * cnt.value].reshape(-1, 2).copy()
 
     def epoch_seeds(self, ds: bytes, first_epoch: int, n_epochs: int) -> np.ndarray:
         out = np.zeros(16 * max(n_epochs, 1), np.uint8)

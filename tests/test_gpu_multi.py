@@ -1,0 +1,95 @@
+"""Multi-device AVer + Distill (many signers in one batch) against the oracle's per-device
+definition, through the C ABI."""
+import numpy as np
+import pytest
+
+from oracle import poslo_oracle as O
+from paper_2506_08781_gb300 import poslo, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import __graft_entry__
+    __graft_entry__.build()
+    c = poslo.Context(device=0, verifier_seed=synth.verifier_seed(123))
+    yield c
+    c.close()
+
+
+def _devices(seed, n_dev, lo, hi, tampered, D=4, n2=4, v=16, k=4, empty=()):
+    sizes = synth.device_sizes(seed, n_dev, lo, hi)
+    for d in empty:
+        sizes[d] = 0
+    devs, parts = [], []
+    bad_devs = set(int(d) for d in synth.choose_without_replacement(seed, "baddev", n_dev, tampered))
+    for d in range(n_dev):
+        km = synth.key_material(seed * 1000 + d, v=v)
+        sk, Y = O.kg_f(km.y, km.root, D, n2, km.bpv_r.tobytes())
+        first = int(synth.uniform_int(seed, f"first{d}", 1, 0, 3)[0])
+        msgs = synth.messages(seed * 1000 + d, int(sizes[d]), 0, 60)
+        subsets = synth.bpv_subsets(seed * 1000 + d, msgs.n, first_index=first, v=v, k=k)
+        sig = [O.sig_f(sk, first + t, msgs.entry(t), subsets[t]) for t in range(msgs.n)]
+        s = [x[0] for x in sig]
+        R = [x[1] for x in sig]
+        if d in bad_devs and msgs.n and any(len(m) for m in msgs.as_list()):
+            cand = [t for t in range(msgs.n) if len(msgs.entry(t))]
+            t = cand[int(synth.uniform_int(seed, f"t{d}", 1, 0, len(cand) - 1)[0])]
+            data = msgs.data.copy()
+            data[int(msgs.offs[t])] ^= 0x21
+            msgs = synth.Messages(data, msgs.offs)
+        ds = O.ds_root(km.root, D)
+        devs.append((Y, msgs.as_list(), first, n2, s, R, ds))
+        parts.append((Y, msgs, first, n2, s, R, O.ds_serialize(ds)))
+    return devs, parts
+
+
+def _concat(parts):
+    entries = [m for p in parts for m in p[1].as_list()]
+    cat = synth.pack(entries)
+    s = b"".join(b"".join(p[4]) for p in parts)
+    R = b"".join(b"".join(p[5]) for p in parts)
+    return cat, s, R
+
+
+@pytest.mark.parametrize("seed,n_dev,tampered", [(1, 12, 3), (2, 7, 0), (3, 20, 20)])
+def test_multi_matches_per_device_definition(ctx, seed, n_dev, tampered):
+    devs, parts = _devices(seed, n_dev, 1, 40, tampered)
+    cat, s, R = _concat(parts)
+    acc, pairs = ctx.aver_multi([p[0] for p in parts], [p[1].n for p in parts], [p[2] for p in parts],
+                                [p[3] for p in parts], [p[6] for p in parts], cat.data, cat.offs, s, R)
+    want_acc, want_pairs = O.verify_multi(devs)
+    assert list(acc) == want_acc
+    assert [tuple(int(x) for x in p) for p in pairs] == want_pairs
+
+
+def test_multi_cancelling_errors_fall_back(ctx):
+    """Two devices whose s-shifts cancel inside every unit aggregate are still localised."""
+    devs, parts = _devices(4, 5, 6, 12, 0)
+    Y, msgs, first, n2, s, R, ds = parts[2]
+    s = list(s)
+    s[1] = O.scalar_to_bytes(int.from_bytes(s[1], "little") + 5)
+    s[4] = O.scalar_to_bytes(int.from_bytes(s[4], "little") - 5)
+    parts[2] = (Y, msgs, first, n2, s, R, ds)
+    d = devs[2]
+    devs[2] = (d[0], d[1], d[2], d[3], s, d[5], d[6])
+    cat, sb, Rb = _concat(parts)
+    acc, pairs = ctx.aver_multi([p[0] for p in parts], [p[1].n for p in parts], [p[2] for p in parts],
+                                [p[3] for p in parts], [p[6] for p in parts], cat.data, cat.offs, sb, Rb)
+    want_acc, want_pairs = O.verify_multi(devs)
+    assert list(acc) == want_acc and [tuple(int(x) for x in p) for p in pairs] == want_pairs
+    assert want_pairs == [(2, first + 1), (2, first + 4)]
+
+
+def test_multi_device_inputs_and_empty_device(ctx):
+    import torch
+    devs, parts = _devices(5, 6, 1, 10, 2, empty=(3,))
+    cat, s, R = _concat(parts)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).copy()).cuda()
+    acc, pairs = ctx.aver_multi([p[0] for p in parts], [p[1].n for p in parts], [p[2] for p in parts],
+                                [p[3] for p in parts], [p[6] for p in parts], dev(cat.data),
+                                dev(cat.offs.view(np.int64)), dev(np.frombuffer(s, np.uint8)),
+                                dev(np.frombuffer(R, np.uint8)))
+    want_acc, want_pairs = O.verify_multi(devs)
+    assert list(acc) == want_acc and [tuple(int(x) for x in p) for p in pairs] == want_pairs
