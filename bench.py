@@ -145,6 +145,82 @@ def compressions(msgs) -> int:
     return int(np.sum(1 + (L + 16 + 9 + 63) // 64))
 
 
+# ------------------------------------------------------------------------------ config 4: many devices
+
+MULTI_DEVICES = 4096
+MULTI_LO, MULTI_HI = 16, 65536
+MULTI_TAMPER_FRAC = 0.005
+MULTI_D, MULTI_N2 = 9, 256          # n1 = 512 epochs of 256 entries per device (>= 65,536 entries)
+
+
+def make_multi_workload(ctx, n_dev=MULTI_DEVICES, lo=MULTI_LO, hi=MULTI_HI, seed=4):
+    """4,096 devices, sizes log-uniform in [16, 65536], messages U[32, 256] bytes, 0.5 % of the
+    devices with one entry flipped by one byte.  Keys and signatures come from the library's
+    signer (BPV table of 64 entries, 4 per subset: the verifier does not depend on them)."""
+    from paper_2506_08781_gb300 import synth
+    sizes = synth.device_sizes(seed, n_dev, lo, hi)
+    total = int(sizes.sum())
+    msgs = synth.messages(seed, total, LMIN, LMAX, tag="multi")
+    start = np.zeros(n_dev + 1, np.int64)
+    start[1:] = np.cumsum(sizes)
+    Ys, ss, Rs, dss = [], [], [], []
+    for d in range(n_dev):
+        km = synth.key_material(seed * 100000 + d, v=64)
+        Y, bpv_R = ctx.keygen_f(km.y, km.bpv_r)
+        lo_, hi_ = int(start[d]), int(start[d + 1])
+        offs = msgs.offs[lo_:hi_ + 1]
+        sub = synth.bpv_subsets(seed * 100000 + d, hi_ - lo_, v=64, k=4)
+        s, R = ctx.sign_f(km.y, km.root, MULTI_D, MULTI_N2, km.bpv_r, bpv_R, sub, msgs.data, offs)
+        Ys.append(Y)
+        ss.append(s)
+        Rs.append(R)
+        dss.append(struct.pack("<II", MULTI_D, 0) + km.root)
+    bad_devs = synth.choose_without_replacement(seed, "baddev", n_dev, round(MULTI_TAMPER_FRAC * n_dev))
+    data = msgs.data.copy()
+    pairs = []
+    for d in bad_devs:
+        d = int(d)
+        t = int(start[d]) + int(synth.uniform_int(seed, f"t{d}", 1, 0, int(sizes[d]) - 1)[0])
+        L = int(msgs.offs[t + 1] - msgs.offs[t])
+        pos = int(synth.uniform_int(seed, f"p{d}", 1, 0, L - 1)[0])
+        data[int(msgs.offs[t]) + pos] ^= int(synth.uniform_int(seed, f"m{d}", 1, 1, 255)[0])
+        pairs.append((d, t - int(start[d])))
+    return dict(sizes=sizes, msgs=synth.Messages(data, msgs.offs), Y=Ys, s=np.concatenate(ss),
+                R=np.concatenate(Rs), ds=dss, pairs=sorted(pairs), total=total)
+
+
+def bench_multi(ctx, steps: int, warmup: int) -> dict:
+    import torch
+    from paper_2506_08781_gb300 import poslo
+    t0 = time.perf_counter()
+    w = make_multi_workload(ctx)
+    setup_s = time.perf_counter() - t0
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    d_msgs, d_offs = dev(w["msgs"].data), dev(w["msgs"].offs.view(np.int64))
+    d_s, d_R = dev(w["s"]), dev(w["R"])
+    nd = len(w["Y"])
+    args = (w["Y"], w["sizes"], np.zeros(nd, np.uint64), np.full(nd, MULTI_N2, np.uint32), w["ds"],
+            d_msgs, d_offs, d_s, d_R)
+    torch.cuda.synchronize()
+    for _ in range(warmup):
+        acc, pairs = ctx.aver_multi(*args)
+    got = [(int(a), int(b)) for a, b in pairs]
+    assert got == w["pairs"], "multi-device localisation differs from the tamper plan"
+    assert int((~acc).sum()) == len({d for d, _ in w["pairs"]})
+    stream = torch.cuda.ExternalStream(ctx.stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        ctx.aver_multi(*args)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return {"workload": f"{nd} devices, sizes log-uniform [{MULTI_LO}, {MULTI_HI}] (total {w['total']} entries), "
+                        f"|m|~U[32,256], {len(w['pairs'])} devices with one flipped byte",
+            "value": w["total"] / (ms * 1e-3), "unit": "entries/s", "ms_per_step": ms, "steps": steps,
+            "invalid_found": len(got), "setup_s": setup_s}
+
+
 # ------------------------------------------------------------------------------ CPU oracle arm
 
 def _oracle_worker(args):
@@ -319,6 +395,10 @@ def run_ours(args):
     torch.cuda.synchronize()
     aver_ms = e0.elapsed_time(e1) / args.steps
 
+    multi = None
+    if not args.no_multi and world == 1:
+        multi = bench_multi(ctx, steps=max(2, args.steps // 5), warmup=2)
+
     # end to end through the C ABI from pinned host memory
     p_msgs = torch.from_numpy(msgs.data).pin_memory()
     p_offs = torch.from_numpy(msgs.offs.view(np.int64)).pin_memory()
@@ -375,6 +455,7 @@ def run_ours(args):
             "e2e": {"value": world * n / e2e_s, "unit": "entries/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "roofline": roof,
+            "multi_device": multi,
             "int_peaks": peaks,
             "cpu_baseline": cpu,
             "wall_s_timed": wall,
@@ -393,6 +474,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-per-core", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-multi", action="store_true", help="skip the 4,096-device measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
