@@ -52,7 +52,8 @@ typedef enum {
   POSLO_ETIMEOUT = -4,  /* a bounded device-side wait expired */
   POSLO_EBUFSMALL = -5, /* an output buffer is too small; the needed count is still reported */
   POSLO_EBUSY = -6,     /* serving: admission refused by the memory budget */
-  POSLO_ENOTFOUND = -7  /* serving: unknown key id or ticket */
+  POSLO_ENOTFOUND = -7, /* serving: unknown key id or ticket */
+  POSLO_PENDING = 1     /* serving: the request is not verified yet (not an error) */
 } poslo_status;
 
 enum { POSLO_VARIANT_C = 0, POSLO_VARIANT_F = 1 };
@@ -179,6 +180,43 @@ typedef struct {
  * all devices at once, and only devices that fail their unit aggregate are localised. */
 int poslo_aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, uint8_t* accept, uint64_t* invalid_pairs,
                      uint64_t cap, uint64_t* n_invalid);
+
+/* ---- serving: continuous batching over registered keys ------------------------------------
+ * Not in the paper (which verifies one signer's log at a time); built on poslo_aver_multi.
+ * poslo_serve_start starts `workers` host threads (1..8), each with its own internal context
+ * on the same device.  Requests are copied at submission and admitted against the context's
+ * mem_budget (POSLO_EBUSY when the device memory they would need does not fit; 0 = no limit).
+ * A free worker takes the oldest pending requests, up to max_batch_devices requests and
+ * max_batch_entries entries, and verifies them as one multi-device batch; requests arriving
+ * meanwhile join the next batch.  Each result is what poslo_distill gives for that request
+ * alone.  All serving calls on one context may be made from any host thread. */
+typedef struct {
+  uint32_t key_id;        /* from poslo_register_key */
+  uint32_t n2;
+  uint64_t first_index;
+  const uint8_t* msgs;    /* host memory, copied at submission */
+  const uint64_t* offs;   /* n+1 */
+  uint64_t n;
+  const uint8_t* s;       /* n*32 */
+  const uint8_t* R;       /* n*32 */
+  const uint8_t* ds;      /* ds_nodes*24 */
+  uint32_t ds_nodes;
+} poslo_request;
+
+int poslo_serve_start(poslo_ctx* ctx, uint32_t workers, uint32_t max_batch_devices, uint64_t max_batch_entries);
+int poslo_serve_stop(poslo_ctx* ctx);
+/* Keys are kept by the service for its lifetime; key ids count from 0. */
+int poslo_register_key(poslo_ctx* ctx, const uint8_t Y[32], uint32_t* key_id);
+/* POSLO_EBUSY: over the memory budget (nothing queued); POSLO_ENOTFOUND: unknown key id. */
+int poslo_submit(poslo_ctx* ctx, const poslo_request* req, uint64_t* ticket);
+/* Waits up to wait_ms for the result.  POSLO_PENDING if not ready; otherwise the accept bit
+ * and the invalid entries' global indices (ascending, room for cap) are written, the ticket
+ * is retired (unless EBUFSMALL, which keeps it so it can be polled again with more room) and
+ * the request's own status is returned (POSLO_OK, or the error its verification met). */
+int poslo_poll(poslo_ctx* ctx, uint64_t ticket, uint32_t wait_ms, uint8_t* accept, uint64_t* invalid_idx,
+               uint64_t cap, uint64_t* n_invalid);
+/* Batches run, requests verified in them, budget bytes held by requests not yet polled. */
+int poslo_serve_stats(poslo_ctx* ctx, uint64_t* batches, uint64_t* requests, uint64_t* bytes_in_use);
 
 /* ---- inspection entry points (single steps of the path, for parity tests) ---------------- */
 

@@ -1,0 +1,50 @@
+// Host-side state of a libposlo context (shared by the C-ABI translation units).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+namespace poslo_host {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+struct KernelTimer {
+  double total_ms = 0;
+  uint64_t launches = 0;
+};
+
+struct Server;   // continuous-batching service (serve.cu)
+
+}  // namespace poslo_host
+
+struct poslo_ctx {
+  int device = 0;
+  int sm_count = 0;
+  uint32_t msm_window = 0;
+  uint64_t mem_budget = 0;
+  uint64_t mem_used = 0;
+  uint8_t vseed[32] = {0};
+  cudaStream_t s_main = nullptr, s_table = nullptr, s_points = nullptr;
+  cudaEvent_t ev_table = nullptr, ev_points = nullptr, ev_main = nullptr;
+  std::map<std::string, poslo_host::DevBuf> bufs;
+  uint32_t* tableG = nullptr;     // fixed-window table of G (64 KiB)
+  uint32_t* status = nullptr;     // device status word
+  uint32_t* h_status = nullptr;   // pinned mirror
+  std::string err;
+  bool profiling = false;
+  uint64_t launch_count = 0;      // kernels launched by this context
+  std::map<std::string, poslo_host::KernelTimer> timers;
+  std::vector<std::pair<std::string, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+  std::vector<cudaEvent_t> event_pool;
+  std::map<int, int> msm_tuned;   // (log2 n) * 16 + scalar words -> best window c
+  poslo_host::Server* server = nullptr;
+};
+
+// Stops and frees the context's service, if one runs (serve.cu).
+void poslo_server_release(poslo_ctx* ctx);

@@ -1,0 +1,323 @@
+// Serving: continuous batching of verification requests from many IoT devices over keys
+// registered once and kept by the service.  Not in the paper (it verifies one signer's log
+// at a time); built on the multi-device path.
+//
+// Requests are copied at submission and admitted against a device-memory budget (EBUSY when
+// it would be exceeded).  W worker threads, each with its own internal context (streams and
+// workspace), take the oldest pending requests up to a batch size whenever they are free and
+// verify them as one multi-device batch; with two workers a batch is staged and hashed
+// while the previous one finishes on the GPU.  A request that arrives while the workers are
+// busy joins the next batch.  Each request's result (accept bit and invalid indices) is by
+// definition independent of the batch it was verified in.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/poslo.h"
+#include "ctx.h"
+
+namespace poslo_host {
+
+struct Req {
+  uint64_t ticket = 0;
+  uint32_t key_id = 0, n2 = 1;
+  uint64_t first_index = 0, n = 0;
+  std::vector<uint8_t> msgs, s, R, ds;
+  std::vector<uint64_t> offs;   // n+1, rebased to start at 0
+  uint64_t charge = 0;          // bytes of the budget held until the result is read
+  int state = 0;                // 0 pending, 1 running, 2 done
+  int rc = POSLO_OK;
+  uint8_t accept = 0;
+  std::vector<uint64_t> invalid;
+};
+
+struct Server {
+  poslo_ctx* owner = nullptr;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Req*> pending;
+  std::unordered_map<uint64_t, std::unique_ptr<Req>> reqs;
+  std::vector<std::array<uint8_t, 32>> keys;
+  std::vector<std::thread> workers;
+  std::vector<poslo_ctx*> wctx;
+  bool stop = false;
+  uint64_t next_ticket = 1;
+  uint64_t budget = 0, used = 0;
+  uint32_t max_dev = 4096;
+  uint64_t max_entries = 1ull << 22;
+  uint64_t batches = 0, batched_requests = 0;
+};
+
+namespace {
+
+// Device bytes a request occupies while it is verified: its inputs and the per-entry
+// workspace of the multi-device path (decoded points, e, z, flags, MSM sort and segments).
+uint64_t request_charge(uint64_t n, uint64_t msg_bytes) { return msg_bytes + n * 640 + 4096; }
+
+void run_batch(Server* S, poslo_ctx* w, std::vector<Req*>& batch) {
+  const uint32_t nd = (uint32_t)batch.size();
+  std::vector<uint8_t> Y(32 * (size_t)nd), msgs, s, R, ds;
+  std::vector<uint64_t> start(nd + 1, 0), first(nd), offs;
+  std::vector<uint32_t> n2(nd), ds_off(nd + 1, 0);
+  {
+    std::lock_guard<std::mutex> lock(S->mu);
+    for (uint32_t d = 0; d < nd; ++d) memcpy(Y.data() + 32 * (size_t)d, S->keys[batch[d]->key_id].data(), 32);
+  }
+  uint64_t total = 0, mtotal = 0;
+  for (uint32_t d = 0; d < nd; ++d) {
+    total += batch[d]->n;
+    mtotal += batch[d]->msgs.size();
+  }
+  msgs.reserve(mtotal);
+  s.reserve(32 * total);
+  R.reserve(32 * total);
+  offs.reserve(total + 1);
+  for (uint32_t d = 0; d < nd; ++d) {
+    Req* r = batch[d];
+    start[d + 1] = start[d] + r->n;
+    first[d] = r->first_index;
+    n2[d] = r->n2;
+    const uint64_t base = msgs.size();
+    for (uint64_t t = 0; t < r->n; ++t) offs.push_back(base + r->offs[t]);
+    msgs.insert(msgs.end(), r->msgs.begin(), r->msgs.end());
+    s.insert(s.end(), r->s.begin(), r->s.end());
+    R.insert(R.end(), r->R.begin(), r->R.end());
+    ds.insert(ds.end(), r->ds.begin(), r->ds.end());
+    ds_off[d + 1] = ds_off[d] + (uint32_t)(r->ds.size() / 24);
+  }
+  offs.push_back(msgs.size());
+  if (msgs.empty()) msgs.push_back(0);
+  poslo_multi_batch mb{};
+  mb.n_dev = nd;
+  mb.Y = Y.data();
+  mb.dev_start = start.data();
+  mb.first_index = first.data();
+  mb.n2 = n2.data();
+  mb.ds = ds.data();
+  mb.ds_off = ds_off.data();
+  mb.msgs = msgs.data();
+  mb.offs = offs.data();
+  mb.s = s.data();
+  mb.R = R.data();
+  mb.on_device = 0;
+  std::vector<uint8_t> acc(nd);
+  std::vector<uint64_t> pairs(2 * std::max<uint64_t>(total, 1));
+  uint64_t cnt = 0;
+  int rc = poslo_aver_multi(w, &mb, acc.data(), pairs.data(), total, &cnt);
+  std::vector<int> rcs(nd, rc);
+  std::vector<std::vector<uint64_t>> inv(nd);
+  if (rc == POSLO_OK) {
+    for (uint64_t k = 0; k < cnt; ++k) inv[pairs[2 * k]].push_back(pairs[2 * k + 1]);
+  } else if (nd > 1) {
+    // one malformed request must not fail the others: verify each on its own
+    for (uint32_t d = 0; d < nd; ++d) {
+      poslo_batch b{};
+      Req* r = batch[d];
+      b.variant = POSLO_VARIANT_F;
+      b.n2 = r->n2;
+      b.Y = Y.data() + 32 * (size_t)d;
+      b.msgs = r->msgs.empty() ? msgs.data() : r->msgs.data();
+      b.offs = r->offs.data();
+      b.n = r->n;
+      b.first_index = r->first_index;
+      b.s = r->s.data();
+      b.R = r->R.data();
+      b.R_count = r->n;
+      b.ds = r->ds.data();
+      b.ds_nodes = (uint32_t)(r->ds.size() / 24);
+      std::vector<uint64_t> idx(std::max<uint64_t>(r->n, 1));
+      uint64_t k = 0;
+      rcs[d] = poslo_distill(w, &b, idx.data(), r->n, &k, nullptr, nullptr);
+      acc[d] = (rcs[d] == POSLO_OK && k == 0) ? 1 : 0;
+      inv[d].assign(idx.begin(), idx.begin() + (rcs[d] == POSLO_OK ? k : 0));
+    }
+  }
+  std::lock_guard<std::mutex> lock(S->mu);
+  for (uint32_t d = 0; d < nd; ++d) {
+    Req* r = batch[d];
+    r->rc = rcs[d];
+    r->accept = rcs[d] == POSLO_OK ? acc[d] : 0;
+    r->invalid = std::move(inv[d]);
+    r->state = 2;
+    // the inputs are no longer needed; the budget is released when the result is read
+    std::vector<uint8_t>().swap(r->msgs);
+    std::vector<uint8_t>().swap(r->s);
+    std::vector<uint8_t>().swap(r->R);
+    std::vector<uint64_t>().swap(r->offs);
+  }
+  S->batches += 1;
+  S->batched_requests += nd;
+}
+
+void worker_loop(Server* S, poslo_ctx* w) {
+  cudaSetDevice(w->device);
+  for (;;) {
+    std::vector<Req*> batch;
+    {
+      std::unique_lock<std::mutex> lock(S->mu);
+      S->cv_work.wait(lock, [&] { return S->stop || !S->pending.empty(); });
+      if (S->stop && S->pending.empty()) return;
+      uint64_t ent = 0;
+      while (!S->pending.empty() && batch.size() < S->max_dev) {
+        Req* r = S->pending.front();
+        if (!batch.empty() && ent + r->n > S->max_entries) break;
+        S->pending.pop_front();
+        r->state = 1;
+        batch.push_back(r);
+        ent += r->n;
+      }
+    }
+    run_batch(S, w, batch);
+    S->cv_done.notify_all();
+  }
+}
+
+}  // namespace
+}  // namespace poslo_host
+
+using poslo_host::Req;
+using poslo_host::Server;
+
+void poslo_server_release(poslo_ctx* ctx) {
+  if (!ctx || !ctx->server) return;
+  Server* S = ctx->server;
+  {
+    std::lock_guard<std::mutex> lock(S->mu);
+    S->stop = true;
+  }
+  S->cv_work.notify_all();
+  for (auto& t : S->workers) t.join();
+  for (poslo_ctx* w : S->wctx) poslo_destroy(w);
+  delete S;
+  ctx->server = nullptr;
+}
+
+extern "C" {
+
+int poslo_serve_start(poslo_ctx* ctx, uint32_t workers, uint32_t max_batch_devices, uint64_t max_batch_entries) {
+  if (!ctx || workers == 0 || workers > 8 || max_batch_devices == 0 || max_batch_entries == 0) return POSLO_EINVAL;
+  if (ctx->server) return POSLO_EBUSY;
+  Server* S = new Server();
+  S->owner = ctx;
+  S->budget = ctx->mem_budget;
+  S->max_dev = max_batch_devices;
+  S->max_entries = max_batch_entries;
+  for (uint32_t k = 0; k < workers; ++k) {
+    poslo_params p{};
+    p.device = ctx->device;
+    p.msm_window = ctx->msm_window;
+    p.mem_budget = 0;
+    memcpy(p.verifier_seed, ctx->vseed, 32);
+    p.verifier_seed[31] ^= (uint8_t)(k + 1);   // independent weights per worker
+    poslo_ctx* w = nullptr;
+    const int rc = poslo_create(&p, &w);
+    if (rc != POSLO_OK) {
+      for (poslo_ctx* c : S->wctx) poslo_destroy(c);
+      delete S;
+      return rc;
+    }
+    S->wctx.push_back(w);
+  }
+  for (poslo_ctx* w : S->wctx) S->workers.emplace_back(poslo_host::worker_loop, S, w);
+  ctx->server = S;
+  return POSLO_OK;
+}
+
+int poslo_serve_stop(poslo_ctx* ctx) {
+  if (!ctx || !ctx->server) return POSLO_EINVAL;
+  poslo_server_release(ctx);
+  return POSLO_OK;
+}
+
+int poslo_register_key(poslo_ctx* ctx, const uint8_t Y[32], uint32_t* key_id) {
+  if (!ctx || !ctx->server || !Y || !key_id) return POSLO_EINVAL;
+  Server* S = ctx->server;
+  std::lock_guard<std::mutex> lock(S->mu);
+  std::array<uint8_t, 32> k;
+  memcpy(k.data(), Y, 32);
+  S->keys.push_back(k);
+  *key_id = (uint32_t)(S->keys.size() - 1);
+  return POSLO_OK;
+}
+
+int poslo_submit(poslo_ctx* ctx, const poslo_request* q, uint64_t* ticket) {
+  if (!ctx || !ctx->server || !q || !ticket) return POSLO_EINVAL;
+  Server* S = ctx->server;
+  if (q->n2 == 0 || !q->ds || q->ds_nodes == 0 || (q->n && (!q->offs || !q->s || !q->R || !q->msgs)))
+    return POSLO_EINVAL;
+  for (uint64_t t = 0; t < q->n; ++t)
+    if (q->offs[t + 1] < q->offs[t]) return POSLO_EINVAL;
+  auto r = std::make_unique<Req>();
+  r->key_id = q->key_id;
+  r->n2 = q->n2;
+  r->first_index = q->first_index;
+  r->n = q->n;
+  const uint64_t lo = q->n ? q->offs[0] : 0, hi = q->n ? q->offs[q->n] : 0;
+  r->charge = poslo_host::request_charge(q->n, hi - lo);
+  {
+    std::lock_guard<std::mutex> lock(S->mu);
+    if (q->key_id >= S->keys.size()) return POSLO_ENOTFOUND;
+    if (S->budget && S->used + r->charge > S->budget) return POSLO_EBUSY;
+    S->used += r->charge;   // reserve before copying
+  }
+  r->msgs.assign(q->msgs ? q->msgs + lo : nullptr, q->msgs ? q->msgs + hi : nullptr);
+  r->offs.resize(q->n + 1);
+  for (uint64_t t = 0; t <= q->n; ++t) r->offs[t] = q->n ? q->offs[t] - lo : 0;
+  r->s.assign(q->s, q->s + 32 * q->n);
+  r->R.assign(q->R, q->R + 32 * q->n);
+  r->ds.assign(q->ds, q->ds + 24 * (size_t)q->ds_nodes);
+  {
+    std::lock_guard<std::mutex> lock(S->mu);
+    r->ticket = S->next_ticket++;
+    *ticket = r->ticket;
+    S->pending.push_back(r.get());
+    S->reqs.emplace(r->ticket, std::move(r));
+  }
+  S->cv_work.notify_one();
+  return POSLO_OK;
+}
+
+int poslo_poll(poslo_ctx* ctx, uint64_t ticket, uint32_t wait_ms, uint8_t* accept, uint64_t* invalid_idx,
+               uint64_t cap, uint64_t* n_invalid) {
+  if (!ctx || !ctx->server || !accept || !n_invalid) return POSLO_EINVAL;
+  Server* S = ctx->server;
+  std::unique_lock<std::mutex> lock(S->mu);
+  auto it = S->reqs.find(ticket);
+  if (it == S->reqs.end()) return POSLO_ENOTFOUND;
+  Req* r = it->second.get();
+  if (r->state != 2 && wait_ms)
+    S->cv_done.wait_for(lock, std::chrono::milliseconds(wait_ms), [&] { return r->state == 2; });
+  if (r->state != 2) return POSLO_PENDING;
+  *accept = r->accept;
+  *n_invalid = r->invalid.size();
+  if (invalid_idx)
+    for (uint64_t k = 0; k < std::min<uint64_t>(cap, r->invalid.size()); ++k) invalid_idx[k] = r->invalid[k];
+  const int rc = r->rc != POSLO_OK ? r->rc : (r->invalid.size() > cap ? POSLO_EBUFSMALL : POSLO_OK);
+  if (rc != POSLO_EBUFSMALL) {
+    S->used -= r->charge;
+    S->reqs.erase(it);
+  }
+  return rc;
+}
+
+int poslo_serve_stats(poslo_ctx* ctx, uint64_t* batches, uint64_t* requests, uint64_t* bytes_in_use) {
+  if (!ctx || !ctx->server) return POSLO_EINVAL;
+  Server* S = ctx->server;
+  std::lock_guard<std::mutex> lock(S->mu);
+  if (batches) *batches = S->batches;
+  if (requests) *requests = S->batched_requests;
+  if (bytes_in_use) *bytes_in_use = S->used;
+  return POSLO_OK;
+}
+
+}  // extern "C"

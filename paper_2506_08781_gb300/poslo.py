@@ -29,7 +29,10 @@ EXPORTS = [
     "poslo_aver", "poslo_distill", "poslo_epoch_seeds", "poslo_hash_entries", "poslo_msm",
     "poslo_set_profiling", "poslo_kernel_time", "poslo_reset_kernel_times",
     "poslo_hash_entries_noalloc", "poslo_aver_multi",
+    "poslo_serve_start", "poslo_serve_stop", "poslo_register_key", "poslo_submit", "poslo_poll",
+    "poslo_serve_stats",
 ]
+POSLO_PENDING = 1
 
 
 class PosloError(RuntimeError):
@@ -47,6 +50,12 @@ class MultiBatch(C.Structure):
     _fields_ = [("n_dev", C.c_uint32), ("Y", C.c_void_p), ("dev_start", C.c_void_p), ("first_index", C.c_void_p),
                 ("n2", C.c_void_p), ("ds", C.c_void_p), ("ds_off", C.c_void_p), ("msgs", C.c_void_p),
                 ("offs", C.c_void_p), ("s", C.c_void_p), ("R", C.c_void_p), ("on_device", C.c_uint32)]
+
+
+class Request(C.Structure):
+    _fields_ = [("key_id", C.c_uint32), ("n2", C.c_uint32), ("first_index", C.c_uint64), ("msgs", C.c_void_p),
+                ("offs", C.c_void_p), ("n", C.c_uint64), ("s", C.c_void_p), ("R", C.c_void_p), ("ds", C.c_void_p),
+                ("ds_nodes", C.c_uint32)]
 
 
 class Batch(C.Structure):
@@ -89,6 +98,12 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "poslo_reset_kernel_times": ([vp], None),
         "poslo_hash_entries_noalloc": ([C.POINTER(Batch), u8p, vp], C.c_int),
         "poslo_aver_multi": ([vp, C.POINTER(MultiBatch), u8p, vp, u64, C.POINTER(u64)], C.c_int),
+        "poslo_serve_start": ([vp, u32, u32, u64], C.c_int),
+        "poslo_serve_stop": ([vp], C.c_int),
+        "poslo_register_key": ([vp, u8p, C.POINTER(u32)], C.c_int),
+        "poslo_submit": ([vp, C.POINTER(Request), C.POINTER(u64)], C.c_int),
+        "poslo_poll": ([vp, u64, u32, u8p, vp, u64, C.POINTER(u64)], C.c_int),
+        "poslo_serve_stats": ([vp, C.POINTER(u64), C.POINTER(u64), C.POINTER(u64)], C.c_int),
     }
     for name in EXPORTS:
         f = getattr(lib, name)
@@ -315,6 +330,47 @@ class Context:
         cnt = C.c_uint64()
         self._check(self.lib.poslo_aver_multi(self.h, C.byref(mb), _ptr(acc), _ptr(pairs), cap, C.byref(cnt)))
         return acc.astype(bool), pairs[:2 * cnt.value].reshape(-1, 2).copy()
+
+    # ------------------------------------------------------------------ serving
+    def serve_start(self, workers: int = 2, max_batch_devices: int = 4096, max_batch_entries: int = 1 << 22):
+        self._check(self.lib.poslo_serve_start(self.h, workers, max_batch_devices, max_batch_entries))
+
+    def serve_stop(self):
+        self._check(self.lib.poslo_serve_stop(self.h))
+
+    def register_key(self, Y: bytes) -> int:
+        kid = C.c_uint32()
+        self._check(self.lib.poslo_register_key(self.h, _ptr(bytes(Y)), C.byref(kid)))
+        return kid.value
+
+    def submit(self, key_id: int, n2: int, first_index: int, msgs, offs, s, R, ds: bytes) -> int:
+        """Queue one request (host arrays; copied by the library).  Raises PosloError EBUSY
+        when the memory budget is exhausted."""
+        offs = np.ascontiguousarray(offs, dtype=np.uint64)
+        q = Request()
+        q.key_id, q.n2, q.first_index = key_id, n2, first_index
+        q.msgs, q.offs, q.n = _ptr(_u8(msgs)), _ptr(offs), len(offs) - 1
+        q.s, q.R, q.ds, q.ds_nodes = _ptr(_u8(s)), _ptr(_u8(R)), _ptr(bytes(ds)), len(ds) // 24
+        t = C.c_uint64()
+        self._check(self.lib.poslo_submit(self.h, C.byref(q), C.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int, wait_ms: int = 0, cap: int = 1 << 16):
+        """None while pending, else (accept, invalid indices)."""
+        acc = np.zeros(1, np.uint8)
+        idx = np.zeros(max(cap, 1), np.uint64)
+        cnt = C.c_uint64()
+        rc = self.lib.poslo_poll(self.h, ticket, wait_ms, _ptr(acc), _ptr(idx), cap, C.byref(cnt))
+        if rc == POSLO_PENDING:
+            _keep.clear()
+            return None
+        self._check(rc)
+        return bool(acc[0]), idx[:cnt.value].copy()
+
+    def serve_stats(self):
+        b, r, u = C.c_uint64(), C.c_uint64(), C.c_uint64()
+        self._check(self.lib.poslo_serve_stats(self.h, C.byref(b), C.byref(r), C.byref(u)))
+        return b.value, r.value, u.value
 
     def epoch_seeds(self, ds: bytes, first_epoch: int, n_epochs: int) -> np.ndarray:
         out = np.zeros(16 * max(n_epochs, 1), np.uint8)

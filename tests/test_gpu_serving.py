@@ -1,0 +1,93 @@
+"""Serving loop (continuous batching over registered keys) through the C ABI: each result
+equals the request verified alone and the oracle's per-entry definition, whether the
+request ran alone or mixed with others; admission by memory budget; unknown ids."""
+import numpy as np
+import pytest
+
+from oracle import poslo_oracle as O
+from paper_2506_08781_gb300 import poslo, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _requests(seed, n_keys, n_req, D=4, n2=8, v=16, k=4):
+    keys = []
+    for kk in range(n_keys):
+        km = synth.key_material(seed * 100 + kk, v=v)
+        sk, Y = O.kg_f(km.y, km.root, D, n2, km.bpv_r.tobytes())
+        keys.append((km, sk, Y))
+    sizes = synth.log_uniform_int(seed, "rsize", n_req, 1, 60)
+    reqs = []
+    for r in range(n_req):
+        kk = r % n_keys
+        km, sk, Y = keys[kk]
+        first = int(synth.uniform_int(seed, f"f{r}", 1, 0, 40)[0])
+        msgs = synth.messages(seed * 1000 + r, int(sizes[r]), 0, 80)
+        sub = synth.bpv_subsets(seed * 1000 + r, msgs.n, first_index=first, v=v, k=k)
+        sig = [O.sig_f(sk, first + t, msgs.entry(t), sub[t]) for t in range(msgs.n)]
+        s, R = [x[0] for x in sig], [x[1] for x in sig]
+        if r % 5 == 1:   # tamper 1..3 non-empty entries
+            cand = [t for t in range(msgs.n) if len(msgs.entry(t))]
+            if cand:
+                pick = synth.choose_without_replacement(seed + r, "tp", len(cand), min(len(cand), 1 + r % 3))
+                data = msgs.data.copy()
+                for q in pick:
+                    data[int(msgs.offs[cand[int(q)]])] ^= 0x40
+                msgs = synth.Messages(data, msgs.offs)
+        ds = O.ds_root(km.root, D)
+        want, _, _ = O.distill_f(Y, msgs.as_list(), first, n2, s, R, ds)
+        reqs.append(dict(key=kk, n2=n2, first=first, msgs=msgs, s=b"".join(s), R=b"".join(R),
+                         ds=O.ds_serialize(ds), want=want))
+    return keys, reqs
+
+
+def _submit(ctx, kid, q):
+    return ctx.submit(kid[q["key"]], q["n2"], q["first"], q["msgs"].data, q["msgs"].offs, q["s"], q["R"], q["ds"])
+
+
+def test_serving_alone_equals_mix_equals_definition():
+    import __graft_entry__
+    __graft_entry__.build()
+    keys, reqs = _requests(7, 4, 24)
+    with poslo.Context(device=0, verifier_seed=synth.verifier_seed(7)) as ctx:
+        ctx.serve_start(workers=2, max_batch_devices=8, max_batch_entries=300)
+        kid = [ctx.register_key(Y) for _, _, Y in keys]
+        alone = []
+        for q in reqs:
+            t = _submit(ctx, kid, q)
+            alone.append(ctx.poll(t, wait_ms=60000))
+        tickets = [_submit(ctx, kid, q) for q in reqs]
+        mix = [ctx.poll(t, wait_ms=60000) for t in tickets]
+        batches, requests, in_use = ctx.serve_stats()
+        ctx.serve_stop()
+    for q, a, m in zip(reqs, alone, mix):
+        assert a is not None and m is not None
+        assert (a[0], list(a[1])) == (m[0], list(m[1])) == (not q["want"], q["want"])
+    assert requests == 48 and in_use == 0
+    assert batches < 48            # the mixed submissions were batched together
+
+
+def test_serving_budget_and_unknown_ids():
+    import __graft_entry__
+    __graft_entry__.build()
+    keys, reqs = _requests(8, 1, 3)
+    with poslo.Context(device=0, mem_budget=60_000) as ctx:
+        ctx.serve_start(workers=1)
+        kid = [ctx.register_key(Y) for _, _, Y in keys]
+        big = dict(reqs[0])
+        msgs = synth.messages(99, 200, 100, 100)
+        big["msgs"], big["s"], big["R"] = msgs, bytes(32 * 200), bytes(32 * 200)
+        with pytest.raises(poslo.PosloError) as e:
+            _submit(ctx, kid, big)
+        assert e.value.code == -6                      # EBUSY
+        small = reqs[1]
+        t = _submit(ctx, kid, small)
+        res = ctx.poll(t, wait_ms=60000)
+        assert res[0] is (not small["want"])
+        with pytest.raises(poslo.PosloError) as e:
+            ctx.submit(7, 8, 0, small["msgs"].data, small["msgs"].offs, small["s"], small["R"], small["ds"])
+        assert e.value.code == -7                      # ENOTFOUND
+        with pytest.raises(poslo.PosloError) as e:
+            ctx.poll(12345)
+        assert e.value.code == -7
+        ctx.serve_stop()
