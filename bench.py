@@ -221,6 +221,131 @@ def bench_multi(ctx, steps: int, warmup: int) -> dict:
             "invalid_found": len(got), "setup_s": setup_s}
 
 
+# ------------------------------------------------------------------------------ config 5: serving
+
+SERVE_KEYS = 10000
+SERVE_REQUESTS = 1500
+SERVE_LO, SERVE_HI = 1, 65536
+SERVE_TAMPER_FRAC = 0.01
+SERVE_BUDGET = 64 << 30
+
+
+def make_serving_workload(ctx, seed=5):
+    """10,000 resident keys; SERVE_REQUESTS requests (request r signed under key r) with
+    sizes log-uniform in [1, 65536], messages U[32, 256] bytes, 1 % of them with 1-4
+    flipped entries.  Returns the request arrays and the expected invalid lists."""
+    from paper_2506_08781_gb300 import synth
+    sizes = synth.log_uniform_int(seed, "reqsize", SERVE_REQUESTS, SERVE_LO, SERVE_HI)
+    total = int(sizes.sum())
+    msgs = synth.messages(seed, total, LMIN, LMAX, tag="serve")
+    start = np.zeros(SERVE_REQUESTS + 1, np.int64)
+    start[1:] = np.cumsum(sizes)
+    bad_req = set(int(r) for r in synth.choose_without_replacement(seed, "badreq", SERVE_REQUESTS,
+                                                                    round(SERVE_TAMPER_FRAC * SERVE_REQUESTS)))
+    data = msgs.data.copy()
+    reqs = []
+    for r in range(SERVE_REQUESTS):
+        km = synth.key_material(seed * 1000000 + r, v=64)
+        Y, bpv_R = ctx.keygen_f(km.y, km.bpv_r)
+        lo, hi = int(start[r]), int(start[r + 1])
+        offs = msgs.offs[lo:hi + 1]
+        sub = synth.bpv_subsets(seed * 1000000 + r, hi - lo, v=64, k=4)
+        sv, Rv = ctx.sign_f(km.y, km.root, MULTI_D, MULTI_N2, km.bpv_r, bpv_R, sub, msgs.data, offs)
+        want = []
+        if r in bad_req:
+            nflip = min(hi - lo, 1 + int(synth.uniform_int(seed, f"nf{r}", 1, 0, 3)[0]))
+            for t in synth.choose_without_replacement(seed, f"ft{r}", hi - lo, nflip):
+                t = int(t)
+                o = int(offs[t])
+                data[o] ^= 0x5A       # lengths are >= 32: the first byte exists
+                want.append(t)
+        reqs.append(dict(Y=Y, offs=(offs - offs[0]).astype(np.uint64), lo=int(offs[0]), hi=int(offs[-1]),
+                         s=sv, R=Rv, ds=struct.pack("<II", MULTI_D, 0) + km.root, want=sorted(want), n=hi - lo))
+    for r in reqs:
+        r["msgs"] = data[r["lo"]:r["hi"]].copy()
+    idle = []
+    for k in range(SERVE_REQUESTS, SERVE_KEYS):
+        y = bytearray(synth.random_bytes(seed, f"idle{k}", 32).tobytes())
+        y[31] &= 0x0F
+        Y, _ = ctx.keygen_f(bytes(y), np.zeros(0, np.uint8))
+        idle.append(Y)
+    return reqs, idle, total
+
+
+def bench_serving(ctx_factory) -> dict:
+    import ctypes as C
+    from paper_2506_08781_gb300 import poslo, synth
+    gen_ctx = ctx_factory()
+    t0 = time.perf_counter()
+    reqs, idle, total = make_serving_workload(gen_ctx)
+    setup_s = time.perf_counter() - t0
+    gen_ctx.close()
+    svc = poslo.Context(device=0, mem_budget=SERVE_BUDGET, verifier_seed=synth.verifier_seed(55))
+    svc.serve_start(workers=2, max_batch_devices=4096, max_batch_entries=1 << 22)
+    kid = [svc.register_key(r["Y"]) for r in reqs] + [svc.register_key(Y) for Y in idle]
+    lib = svc.lib
+    structs = []
+    for r, k in zip(reqs, kid):
+        q = poslo.Request()
+        q.key_id, q.n2, q.first_index = k, MULTI_N2, 0
+        q.msgs, q.offs, q.n = r["msgs"].ctypes.data, r["offs"].ctypes.data, r["n"]
+        q.s, q.R = r["s"].ctypes.data, r["R"].ctypes.data
+        dsb = (C.c_uint8 * len(r["ds"])).from_buffer_copy(r["ds"])
+        r["_ds"] = dsb
+        q.ds, q.ds_nodes = C.addressof(dsb), 1
+        structs.append(q)
+    acc = np.zeros(1, np.uint8)
+    idx = np.zeros(1 << 16, np.uint64)
+
+    def run(arrivals):
+        tickets = []
+        tk = C.c_uint64()
+        base = time.perf_counter()
+        for q, at in zip(structs, arrivals):
+            now = time.perf_counter() - base
+            if at > now:
+                time.sleep(at - now)
+            while True:
+                rc = lib.poslo_submit(svc.h, C.byref(q), C.byref(tk))
+                if rc != -6:        # EBUSY: wait for room
+                    break
+                time.sleep(0.0005)
+            assert rc == 0, rc
+            tickets.append(tk.value)
+        lat, results = [], []
+        cnt, ln = C.c_uint64(), C.c_uint64()
+        for t in tickets:
+            rc = lib.poslo_poll(svc.h, t, 600000, acc.ctypes.data, idx.ctypes.data, len(idx), C.byref(cnt),
+                                C.byref(ln))
+            assert rc == 0, rc
+            lat.append(ln.value * 1e-9)
+            results.append((bool(acc[0]), idx[:cnt.value].tolist()))
+        wall = time.perf_counter() - base
+        return np.array(lat), results, wall
+
+    # saturated (every request at t = 0): the service's peak
+    lat, results, wall = run(np.zeros(len(structs)))
+    for r, (a, inv) in zip(reqs, results):
+        assert inv == r["want"] and a == (not r["want"]), "served result differs from the expected one"
+    peak = total / wall
+    mean_size = total / len(reqs)
+    levels = []
+    for load in (0.5, 0.8, 0.95):
+        rate = load * peak / mean_size
+        arr = synth.poisson_arrivals(int(load * 100), len(structs), rate)
+        lat, results, wall = run(arr)
+        assert all(inv == r["want"] for r, (a, inv) in zip(reqs, results))
+        levels.append({"load": load, "offered_requests_per_s": rate, "achieved_entries_per_s": total / wall,
+                       "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3)})
+    batches, nreq, _ = svc.serve_stats()
+    svc.serve_stop()
+    svc.close()
+    return {"workload": f"{SERVE_KEYS} resident keys, {len(reqs)} requests of log-uniform [{SERVE_LO}, {SERVE_HI}] "
+                        f"entries ({total} total), |m|~U[32,256], 1 % tampered, 64 GB budget, 2 workers",
+            "peak_entries_per_s": peak, "levels": levels, "batches": batches, "requests_served": nreq,
+            "setup_s": setup_s}
+
+
 # ------------------------------------------------------------------------------ CPU oracle arm
 
 def _oracle_worker(args):
@@ -398,6 +523,9 @@ def run_ours(args):
     multi = None
     if not args.no_multi and world == 1:
         multi = bench_multi(ctx, steps=max(2, args.steps // 5), warmup=2)
+    serving = None
+    if not args.no_serving and world == 1:
+        serving = bench_serving(lambda: poslo.Context(device=device))
 
     # end to end through the C ABI from pinned host memory
     p_msgs = torch.from_numpy(msgs.data).pin_memory()
@@ -456,6 +584,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": d2h},
             "roofline": roof,
             "multi_device": multi,
+            "serving": serving,
             "int_peaks": peaks,
             "cpu_baseline": cpu,
             "wall_s_timed": wall,
@@ -475,6 +604,7 @@ def main():
     ap.add_argument("--cpu-per-core", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-multi", action="store_true", help="skip the 4,096-device measurement")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

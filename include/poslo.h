@@ -210,11 +210,13 @@ int poslo_register_key(poslo_ctx* ctx, const uint8_t Y[32], uint32_t* key_id);
 /* POSLO_EBUSY: over the memory budget (nothing queued); POSLO_ENOTFOUND: unknown key id. */
 int poslo_submit(poslo_ctx* ctx, const poslo_request* req, uint64_t* ticket);
 /* Waits up to wait_ms for the result.  POSLO_PENDING if not ready; otherwise the accept bit
- * and the invalid entries' global indices (ascending, room for cap) are written, the ticket
- * is retired (unless EBUFSMALL, which keeps it so it can be polled again with more room) and
- * the request's own status is returned (POSLO_OK, or the error its verification met). */
+ * and the invalid entries' global indices (ascending, room for cap) are written, the time the
+ * request spent in the service (from the start of poslo_submit to its result, in ns) goes
+ * to *latency_ns (may be NULL), the ticket is retired (unless EBUFSMALL, which keeps it so it
+ * can be polled again with more room) and the request's own status is returned (POSLO_OK, or
+ * the error its verification met). */
 int poslo_poll(poslo_ctx* ctx, uint64_t ticket, uint32_t wait_ms, uint8_t* accept, uint64_t* invalid_idx,
-               uint64_t cap, uint64_t* n_invalid);
+               uint64_t cap, uint64_t* n_invalid, uint64_t* latency_ns);
 /* Batches run, requests verified in them, budget bytes held by requests not yet polled. */
 int poslo_serve_stats(poslo_ctx* ctx, uint64_t* batches, uint64_t* requests, uint64_t* bytes_in_use);
 

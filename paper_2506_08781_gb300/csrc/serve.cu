@@ -39,6 +39,7 @@ struct Req {
   int rc = POSLO_OK;
   uint8_t accept = 0;
   std::vector<uint64_t> invalid;
+  std::chrono::steady_clock::time_point t_submit, t_done;
 };
 
 struct Server {
@@ -149,6 +150,7 @@ void run_batch(Server* S, poslo_ctx* w, std::vector<Req*>& batch) {
     r->accept = rcs[d] == POSLO_OK ? acc[d] : 0;
     r->invalid = std::move(inv[d]);
     r->state = 2;
+    r->t_done = std::chrono::steady_clock::now();
     // the inputs are no longer needed; the budget is released when the result is read
     std::vector<uint8_t>().swap(r->msgs);
     std::vector<uint8_t>().swap(r->s);
@@ -252,12 +254,14 @@ int poslo_register_key(poslo_ctx* ctx, const uint8_t Y[32], uint32_t* key_id) {
 
 int poslo_submit(poslo_ctx* ctx, const poslo_request* q, uint64_t* ticket) {
   if (!ctx || !ctx->server || !q || !ticket) return POSLO_EINVAL;
+  const auto t_submit = std::chrono::steady_clock::now();
   Server* S = ctx->server;
   if (q->n2 == 0 || !q->ds || q->ds_nodes == 0 || (q->n && (!q->offs || !q->s || !q->R || !q->msgs)))
     return POSLO_EINVAL;
   for (uint64_t t = 0; t < q->n; ++t)
     if (q->offs[t + 1] < q->offs[t]) return POSLO_EINVAL;
   auto r = std::make_unique<Req>();
+  r->t_submit = t_submit;
   r->key_id = q->key_id;
   r->n2 = q->n2;
   r->first_index = q->first_index;
@@ -288,7 +292,7 @@ int poslo_submit(poslo_ctx* ctx, const poslo_request* q, uint64_t* ticket) {
 }
 
 int poslo_poll(poslo_ctx* ctx, uint64_t ticket, uint32_t wait_ms, uint8_t* accept, uint64_t* invalid_idx,
-               uint64_t cap, uint64_t* n_invalid) {
+               uint64_t cap, uint64_t* n_invalid, uint64_t* latency_ns) {
   if (!ctx || !ctx->server || !accept || !n_invalid) return POSLO_EINVAL;
   Server* S = ctx->server;
   std::unique_lock<std::mutex> lock(S->mu);
@@ -300,6 +304,8 @@ int poslo_poll(poslo_ctx* ctx, uint64_t ticket, uint32_t wait_ms, uint8_t* accep
   if (r->state != 2) return POSLO_PENDING;
   *accept = r->accept;
   *n_invalid = r->invalid.size();
+  if (latency_ns)
+    *latency_ns = (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(r->t_done - r->t_submit).count();
   if (invalid_idx)
     for (uint64_t k = 0; k < std::min<uint64_t>(cap, r->invalid.size()); ++k) invalid_idx[k] = r->invalid[k];
   const int rc = r->rc != POSLO_OK ? r->rc : (r->invalid.size() > cap ? POSLO_EBUFSMALL : POSLO_OK);

@@ -102,7 +102,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "poslo_serve_stop": ([vp], C.c_int),
         "poslo_register_key": ([vp, u8p, C.POINTER(u32)], C.c_int),
         "poslo_submit": ([vp, C.POINTER(Request), C.POINTER(u64)], C.c_int),
-        "poslo_poll": ([vp, u64, u32, u8p, vp, u64, C.POINTER(u64)], C.c_int),
+        "poslo_poll": ([vp, u64, u32, u8p, vp, u64, C.POINTER(u64), C.POINTER(u64)], C.c_int),
         "poslo_serve_stats": ([vp, C.POINTER(u64), C.POINTER(u64), C.POINTER(u64)], C.c_int),
     }
     for name in EXPORTS:
@@ -127,8 +127,7 @@ def _ptr(x):
         _keep.append(buf)
         return C.addressof(buf)
     arr = np.ascontiguousarray(x)
-    if arr is not x:
-        _keep.append(arr)
+    _keep.append(arr)          # alive until the call returns (temporaries included)
     return arr.ctypes.data
 
 
@@ -355,17 +354,19 @@ class Context:
         self._check(self.lib.poslo_submit(self.h, C.byref(q), C.byref(t)))
         return t.value
 
-    def poll(self, ticket: int, wait_ms: int = 0, cap: int = 1 << 16):
-        """None while pending, else (accept, invalid indices)."""
+    def poll(self, ticket: int, wait_ms: int = 0, cap: int = 1 << 16, with_latency: bool = False):
+        """None while pending, else (accept, invalid indices[, seconds spent in the service])."""
         acc = np.zeros(1, np.uint8)
         idx = np.zeros(max(cap, 1), np.uint64)
         cnt = C.c_uint64()
-        rc = self.lib.poslo_poll(self.h, ticket, wait_ms, _ptr(acc), _ptr(idx), cap, C.byref(cnt))
+        lat = C.c_uint64()
+        rc = self.lib.poslo_poll(self.h, ticket, wait_ms, _ptr(acc), _ptr(idx), cap, C.byref(cnt), C.byref(lat))
         if rc == POSLO_PENDING:
             _keep.clear()
             return None
         self._check(rc)
-        return bool(acc[0]), idx[:cnt.value].copy()
+        res = (bool(acc[0]), idx[:cnt.value].copy())
+        return res + (lat.value * 1e-9,) if with_latency else res
 
     def serve_stats(self):
         b, r, u = C.c_uint64(), C.c_uint64(), C.c_uint64()
