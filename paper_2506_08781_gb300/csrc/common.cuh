@@ -508,6 +508,15 @@ struct SegSums {
   uint32_t* bad;   // n_dev: malformed entries
 };
 
+struct PrepArgs {
+  const unsigned long long* hash_partial;   // nhash blocks * kPartialWords
+  uint32_t nhash;
+  const uint8_t* s_given;                   // optional: aggregate s (POSLO-C), 32 bytes
+  const uint32_t* tableY;
+  const uint32_t* tableG;
+  uint32_t* prep;                           // out: [e]Y + [s]G (32 words), malformed-s flag (1 word)
+};
+
 // ---- kernel declarations ----
 __global__ void k_epoch_seeds(const DsNode* __restrict__ ds, int nds, uint64_t e0, uint64_t ne,
                               uint32_t* __restrict__ x0_out, uint32_t* __restrict__ status);
@@ -516,6 +525,9 @@ __global__ void __launch_bounds__(kPointThreads) k_points(const PointArgs a);
 __global__ void k_table(const uint32_t* __restrict__ enc, uint32_t* __restrict__ table,
                         uint32_t* __restrict__ status, int use_base);
 __global__ void __launch_bounds__(kFinalThreads) k_finalize(const FinalArgs a);
+__global__ void __launch_bounds__(128) k_final_prep(const PrepArgs a);
+__global__ void k_final_check(const uint32_t* prep, const uint32_t* R, const uint32_t* point_bad,
+                              const uint32_t* status, uint8_t* accept);
 __global__ void __launch_bounds__(128) k_entry_check(const CheckArgs a);
 __global__ void __launch_bounds__(kPointThreads) k_msm_direct(const MsmArgs a);
 __global__ void __launch_bounds__(kHashThreads) k_sum_scalars(const uint8_t* s, uint64_t n, const uint8_t* skip,
@@ -543,7 +555,7 @@ __global__ void __launch_bounds__(128) k_msm_accum(const uint32_t* pts, const ui
 __global__ void __launch_bounds__(128) k_msm_combine(const uint32_t* off, const uint32_t* cnt, uint64_t n, MsmPlan pl,
                                                      const uint32_t* A, const uint32_t* B, uint32_t* buckets);
 __global__ void __launch_bounds__(128) k_msm_chunk(const uint32_t* buckets, MsmPlan pl, uint32_t* L, uint32_t* T);
-__global__ void __launch_bounds__(256) k_msm_groups(const uint32_t* L, const uint32_t* T, MsmPlan pl, uint32_t* groups);
+__global__ void __launch_bounds__(512) k_msm_groups(const uint32_t* L, const uint32_t* T, MsmPlan pl, uint32_t* groups);
 __global__ void __launch_bounds__(32) k_msm_final(const uint32_t* groups, MsmPlan pl, uint32_t* out);
 __global__ void __launch_bounds__(128) k_tree_leaves(const TreeArgs a);
 __global__ void __launch_bounds__(128) k_tree_level(const TreeArgs a, uint64_t in_off, uint64_t out_off,

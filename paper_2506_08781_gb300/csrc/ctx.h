@@ -31,7 +31,7 @@ struct poslo_ctx {
   uint64_t mem_used = 0;
   uint8_t vseed[32] = {0};
   cudaStream_t s_main = nullptr, s_table = nullptr, s_points = nullptr;
-  cudaEvent_t ev_table = nullptr, ev_points = nullptr, ev_main = nullptr;
+  cudaEvent_t ev_table = nullptr, ev_points = nullptr, ev_main = nullptr, ev_hash = nullptr, ev_prep = nullptr;
   std::map<std::string, poslo_host::DevBuf> bufs;
   uint32_t* tableG = nullptr;     // fixed-window table of G (64 KiB)
   uint32_t* status = nullptr;     // device status word

@@ -153,39 +153,51 @@ __global__ void __launch_bounds__(128) k_msm_combine(const uint32_t* off, const 
 }
 
 // Chunk j of window w holds buckets d = 16j .. 16j+15: L = sum_r r B_{16j+r} by running
-// sums, T = sum_r B_{16j+r}.
+// sums, T = sum_r B_{16j+r}.  One quad of lanes per chunk (quad-cooperative additions: the
+// 31 dependent additions are latency-bound).
 __global__ void __launch_bounds__(128) k_msm_chunk(const uint32_t* buckets, MsmPlan pl, uint32_t* L, uint32_t* T) {
-  const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= (uint64_t)pl.windows * pl.nchunks) return;
+  const uint64_t total = (uint64_t)pl.windows * pl.nchunks;
+  const uint64_t quad = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 2;
+  const uint64_t g = quad < total ? quad : total - 1;   // surplus quads repeat the last chunk
   const uint32_t w = (uint32_t)(g / pl.nchunks), j = (uint32_t)(g % pl.nchunks);
   const uint32_t* B = buckets + 32 * ((size_t)w * pl.nb + (size_t)j * kMsmChunk);
   ge run = ge_identity(), acc = ge_identity();
   for (int r = kMsmChunk - 1; r >= 1; --r) {
-    run = ge_add(run, ge_load(B + 32 * r));
-    acc = ge_add(acc, run);
+    run = ge_add_quad(run, ge_load(B + 32 * r));
+    acc = ge_add_quad(acc, run);
   }
-  run = ge_add(run, ge_load(B));
-  ge_store(L + 32 * g, acc);
-  ge_store(T + 32 * g, run);
+  run = ge_add_quad(run, ge_load(B));
+  if ((threadIdx.x & 3) == 0 && quad < total) {
+    ge_store(L + 32 * g, acc);
+    ge_store(T + 32 * g, run);
+  }
 }
 
 // Group sums per window: group 0 = sum_j L_j; group 1+k = sum of T_j over chunks j whose
-// bit k is set.  One block per (window, group).
-constexpr int kGroupThreads = 256;
-__global__ void __launch_bounds__(256) k_msm_groups(const uint32_t* L, const uint32_t* T, MsmPlan pl,
-                                                               uint32_t* groups) {
+// bit k is set.  One block of 256 quads per (window, group); every quad takes part in every
+// addition of the tree (quad operations need all lanes), only the surviving half keeps it.
+constexpr int kGroupThreads = 512;
+__global__ void __launch_bounds__(512) k_msm_groups(const uint32_t* L, const uint32_t* T, MsmPlan pl,
+                                                     uint32_t* groups) {
   const int ng = 1 + pl.jbits;
   const int w = blockIdx.x / ng, grp = blockIdx.x % ng;
   const uint32_t* base = (grp == 0 ? L : T) + 32 * (size_t)w * pl.nchunks;
+  const int quad = threadIdx.x >> 2, nq = kGroupThreads / 4;
   ge acc = ge_identity();
-  for (uint32_t j = threadIdx.x; j < pl.nchunks; j += blockDim.x) {
-    if (grp == 0 || ((j >> (grp - 1)) & 1u)) acc = ge_add(acc, ge_load(base + 32 * (size_t)j));
+  for (uint32_t j0 = 0; j0 < pl.nchunks; j0 += nq) {
+    const uint32_t j = j0 + quad;
+    const bool take = j < pl.nchunks && (grp == 0 || ((j >> (grp - 1)) & 1u));
+    const ge p = take ? ge_load(base + 32 * (size_t)j) : ge_identity();
+    acc = ge_add_quad(acc, p);
   }
-  __shared__ uint32_t sp[kGroupThreads][32];
-  ge_store(sp[threadIdx.x], acc);
+  __shared__ uint32_t sp[kGroupThreads / 4][32];
+  if ((threadIdx.x & 3) == 0) ge_store(sp[quad], acc);
   __syncthreads();
-  for (int h = kGroupThreads / 2; h > 0; h >>= 1) {
-    if (threadIdx.x < h) ge_store(sp[threadIdx.x], ge_add(ge_load(sp[threadIdx.x]), ge_load(sp[threadIdx.x + h])));
+  for (int h = nq / 2; h > 0; h >>= 1) {
+    const ge other = ge_load(sp[(quad + h) % nq]);
+    const ge sum = ge_add_quad(ge_load(sp[quad]), other);
+    __syncthreads();
+    if ((threadIdx.x & 3) == 0 && quad < h) ge_store(sp[quad], sum);
     __syncthreads();
   }
   if (threadIdx.x < 32) groups[32 * (size_t)blockIdx.x + threadIdx.x] = sp[0][threadIdx.x];

@@ -377,4 +377,60 @@ __global__ void __launch_bounds__(kFinalThreads) k_finalize(const FinalArgs a) {
   }
 }
 
+// The final check split in two so that its expensive half overlaps the MSM:
+// k_final_prep (side stream, after hashing and the window table of Y) reduces the scalar
+// partials to e and s and evaluates [e]Y + [s]G from the two window tables (128 terms
+// summed by a shared-memory tree); k_final_check (after the MSM) only forms
+// [8](R - ([e]Y + [s]G)) and tests it for the identity.
+constexpr int kPrepThreads = 128;
+__global__ void __launch_bounds__(128) k_final_prep(const PrepArgs a) {
+  __shared__ unsigned long long sums[kPartialWords];
+  __shared__ int8_t dig_e[64], dig_s[64];
+  __shared__ uint32_t pts_[kPrepThreads][32];
+  __shared__ uint32_t bad_flag;
+  const int tid = threadIdx.x;
+  if (tid < kPartialWords) {
+    unsigned long long v = 0;
+    for (uint32_t b = 0; b < a.nhash; ++b) v += a.hash_partial[(size_t)b * kPartialWords + tid];
+    sums[tid] = v;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const sc e = limb_sums_to_scalar(sums);
+    sc s;
+    uint32_t bf = sums[26] != 0 ? 1u : 0u;
+    if (a.s_given) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        s.v[k] = a.s_given[4 * k] | (a.s_given[4 * k + 1] << 8) | (a.s_given[4 * k + 2] << 16) |
+                 ((uint32_t)a.s_given[4 * k + 3] << 24);
+      if (!sc_is_canonical(s.v)) bf = 1;
+    } else {
+      s = limb_sums_to_scalar(sums + 13);
+    }
+    recode4(e.v, dig_e);
+    recode4(s.v, dig_s);
+    bad_flag = bf;
+  }
+  __syncthreads();
+  const ge term = tid < 64 ? table_pick(a.tableY, tid, dig_e[tid]) : table_pick(a.tableG, tid - 64, dig_s[tid - 64]);
+  ge_store(pts_[tid], term);
+  __syncthreads();
+  for (int h = kPrepThreads / 2; h > 0; h >>= 1) {
+    if (tid < h) ge_store(pts_[tid], ge_add(ge_load(pts_[tid]), ge_load(pts_[tid + h])));
+    __syncthreads();
+  }
+  if (tid < 32) a.prep[tid] = pts_[0][tid];
+  if (tid == 0) a.prep[32] = bad_flag;
+}
+
+__global__ void k_final_check(const uint32_t* prep, const uint32_t* R, const uint32_t* point_bad,
+                              const uint32_t* status, uint8_t* accept) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const ge diff = ge_sub(ge_load(R), ge_load(prep));
+  const bool ok = ge_is_identity(ge_mul_cofactor(diff)) && prep[32] == 0 && !(point_bad && *point_bad) &&
+                  (*status & kErrKey) == 0;
+  accept[0] = ok ? 1 : 0;
+}
+
 }  // namespace poslo

@@ -362,7 +362,7 @@ int run_points(poslo_ctx* ctx, const uint8_t* R, uint64_t count, uint32_t* pts_o
   ++ctx->launch_count;
   CU(cudaGetLastError());
   timer_end(ctx, "points", ctx->s_points, tb, te);
-  CU(cudaEventRecord(ctx->ev_points, ctx->s_points));
+  CU(cudaEventRecord(ctx->ev_points, ctx->s_points));   // callers that add work re-record it
   *partial_out = partial;
   *nblocks_out = (uint32_t)blocks;
   return POSLO_OK;
@@ -483,8 +483,8 @@ int run_msm_finish(poslo_ctx* ctx, cudaStream_t st, const uint32_t* pts, const u
   timer_end(ctx, "msm_bucket", st, sb_, se_);
   timer_begin(ctx, "msm_reduce", st, &sb_, &se_);
   const size_t nch = (size_t)pl.windows * pl.nchunks;
-  k_msm_chunk<<<(unsigned)((nch + 127) / 128), 128, 0, st>>>(buckets, pl, L, T);
-  k_msm_groups<<<pl.windows * (1 + pl.jbits), 256, 0, st>>>(L, T, pl, groups);
+  k_msm_chunk<<<(unsigned)((4 * nch + 127) / 128), 128, 0, st>>>(buckets, pl, L, T);
+  k_msm_groups<<<pl.windows * (1 + pl.jbits), 512, 0, st>>>(L, T, pl, groups);
   ctx->launch_count += 2;
   timer_end(ctx, "msm_reduce", st, sb_, se_);
   timer_begin(ctx, "msm_final", st, &sb_, &se_);
@@ -550,6 +550,62 @@ int run_compact(poslo_ctx* ctx, const uint8_t* flags, uint64_t n, uint64_t first
   return POSLO_OK;
 }
 
+// Points stream, after k_points: the unit sum of the decoded points (extended, 32 words),
+// optionally its compressed encoding, and the count of undecodable points; then ev_points.
+int run_unit_sum(poslo_ctx* ctx, const uint32_t* ppart, uint32_t npb, uint32_t* unitR, uint8_t* enc,
+                 uint32_t* pbad) {
+  k_sum_encode<<<1, kFinalThreads, 0, ctx->s_points>>>(ppart, npb, unitR, enc, pbad);
+  ++ctx->launch_count;
+  CU(cudaGetLastError());
+  CU(cudaEventRecord(ctx->ev_points, ctx->s_points));
+  return POSLO_OK;
+}
+
+// Table stream, once hashing is done: [e]Y + [s]G and the malformed-s flag into prep
+// (33 words); then ev_prep.  Optionally the unit sum of all s_t for ccd^v as well.
+int run_prep(poslo_ctx* ctx, const unsigned long long* hpart, uint32_t nhb, const uint8_t* s_given,
+             const uint32_t* tableY, uint32_t* prep, const uint8_t* s_all, uint64_t n, uint8_t* ccd_s) {
+  CU(cudaEventRecord(ctx->ev_hash, ctx->s_main));
+  CU(cudaStreamWaitEvent(ctx->s_table, ctx->ev_hash, 0));
+  PrepArgs pa{};
+  pa.hash_partial = hpart;
+  pa.nhash = nhb;
+  pa.s_given = s_given;
+  pa.tableY = tableY;
+  pa.tableG = ctx->tableG;
+  pa.prep = prep;
+  cudaEvent_t tb, te;
+  timer_begin(ctx, "prep", ctx->s_table, &tb, &te);
+  k_final_prep<<<1, 128, 0, ctx->s_table>>>(pa);
+  ++ctx->launch_count;
+  timer_end(ctx, "prep", ctx->s_table, tb, te);
+  if (ccd_s) {
+    int rc;
+    const int sblocks = grid_for(ctx, n, kHashThreads, 8);
+    unsigned long long* sp;
+    if ((rc = ensure_t(ctx, "ccd_spart_fast", (size_t)sblocks * 13 * 8, &sp))) return rc;
+    k_sum_scalars<<<sblocks, kHashThreads, 0, ctx->s_table>>>(s_all, n, nullptr, sp);
+    k_reduce_scalars<<<1, 32, 0, ctx->s_table>>>(sp, sblocks, ccd_s);
+    ctx->launch_count += 2;
+  }
+  CU(cudaGetLastError());
+  CU(cudaEventRecord(ctx->ev_prep, ctx->s_table));
+  return POSLO_OK;
+}
+
+// Main stream: [8](R - prep) = O and no malformed input -> accept byte.
+int run_check(poslo_ctx* ctx, const uint32_t* prep, const uint32_t* R, const uint32_t* pbad, uint8_t* d_acc) {
+  CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_prep, 0));
+  CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_points, 0));
+  cudaEvent_t tb, te;
+  timer_begin(ctx, "finalize", ctx->s_main, &tb, &te);
+  k_final_check<<<1, 32, 0, ctx->s_main>>>(prep, R, pbad, ctx->status, d_acc);
+  ++ctx->launch_count;
+  timer_end(ctx, "finalize", ctx->s_main, tb, te);
+  CU(cudaGetLastError());
+  return POSLO_OK;
+}
+
 }  // namespace
 
 // ==========================================================================================
@@ -585,7 +641,9 @@ int poslo_create(const poslo_params* params, poslo_ctx** out) {
       cudaStreamCreateWithFlags(&ctx->s_points, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_table, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_points, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&ctx->ev_main, cudaEventDisableTiming) != cudaSuccess)
+      cudaEventCreateWithFlags(&ctx->ev_main, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_hash, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_prep, cudaEventDisableTiming) != cudaSuccess)
     return bail(POSLO_EDEVICE);
   if (cudaMalloc(&ctx->status, 4) != cudaSuccess) return bail(POSLO_ENOMEM);
   if (cudaMallocHost(&ctx->h_status, 4) != cudaSuccess) return bail(POSLO_ENOMEM);
@@ -618,6 +676,8 @@ void poslo_destroy(poslo_ctx* ctx) {
   if (ctx->ev_table) cudaEventDestroy(ctx->ev_table);
   if (ctx->ev_points) cudaEventDestroy(ctx->ev_points);
   if (ctx->ev_main) cudaEventDestroy(ctx->ev_main);
+  if (ctx->ev_hash) cudaEventDestroy(ctx->ev_hash);
+  if (ctx->ev_prep) cudaEventDestroy(ctx->ev_prep);
   if (ctx->s_main) cudaStreamDestroy(ctx->s_main);
   if (ctx->s_table) cudaStreamDestroy(ctx->s_table);
   if (ctx->s_points) cudaStreamDestroy(ctx->s_points);
@@ -934,25 +994,27 @@ int poslo_aver(poslo_ctx* ctx, const poslo_batch* batch, uint32_t agg_mode, uint
     if ((rc = ensure_t(ctx, "pts", 4 * kPtsWords * std::max<uint64_t>(npts, 1), &pts))) return rc;
     if ((rc = ensure_t(ctx, "badR", std::max<uint64_t>(npts, 1), &badR))) return rc;
   }
+  uint32_t *small;   // unit R (32) | weighted R (32) | prep (33) | point bad count (1)
+  if ((rc = ensure_t(ctx, "aver_small", 4 * 100, &small))) return rc;
+  uint32_t *unitR = small, *Rw = small + 32, *prep = small + 64, *pbad = small + 97;
   uint32_t *ppart, npb;
   if ((rc = run_points(ctx, sb.R, npts, pts, badR, &ppart, &npb))) return rc;
+  if ((rc = run_unit_sum(ctx, ppart, npb, unitR, nullptr, pbad))) return rc;
   uint32_t* z = nullptr;
   if (weighted && (rc = ensure_t(ctx, "z", 16 * std::max<uint64_t>(batch->n, 1), &z))) return rc;
   unsigned long long* hpart;
   uint32_t nhb;
   if ((rc = run_hash(ctx, batch, sb, nullptr, weighted, F, z, &hpart, &nhb))) return rc;
-  MsmState ms;
-  if (weighted && (rc = run_msm_sort(ctx, ctx->s_main, z, 4, nullptr, batch->n, ms))) return rc;
-  CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_table, 0));
-  CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_points, 0));
-  uint32_t* Rw = nullptr;
+  if ((rc = run_prep(ctx, hpart, nhb, F ? nullptr : sb.s, tableY, prep, nullptr, 0, nullptr))) return rc;
   if (weighted) {
-    if ((rc = ensure_t(ctx, "R_weighted", 128, &Rw))) return rc;
+    MsmState ms;
+    if ((rc = run_msm_sort(ctx, ctx->s_main, z, 4, nullptr, batch->n, ms))) return rc;
+    CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_points, 0));
     if ((rc = run_msm_finish(ctx, ctx->s_main, pts, badR, ms, Rw))) return rc;
   }
   uint8_t* d_acc;
   if ((rc = ensure_t(ctx, "accept", 16, &d_acc))) return rc;
-  if ((rc = run_finalize(ctx, hpart, nhb, ppart, npb, Rw, F ? nullptr : sb.s, tableY, d_acc, nullptr))) return rc;
+  if ((rc = run_check(ctx, prep, weighted ? Rw : unitR, pbad, d_acc))) return rc;
   uint8_t h_acc = 0;
   CU(cudaMemcpyAsync(&h_acc, d_acc, 1, cudaMemcpyDeviceToHost, ctx->s_main));
   if ((rc = check_status(ctx))) return rc;
@@ -986,8 +1048,15 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
   if ((rc = ensure_t(ctx, "e_all", 32 * n1, &d_e))) return rc;
   if ((rc = ensure_t(ctx, "invalid", n1, &inv))) return rc;
   // A1-A5: hashing (main stream) overlapped with decoding (points stream)
+  uint32_t* small;   // unit R (32) | weighted R (32) | prep (33) | point bad count (1)
+  if ((rc = ensure_t(ctx, "distill_small", 4 * 100, &small))) return rc;
+  uint32_t *unitR = small, *Rw = small + 32, *prep = small + 64, *pbad = small + 97;
+  uint8_t* d_ccd;
+  if ((rc = ensure_t(ctx, "ccd", 64, &d_ccd))) return rc;
   uint32_t *ppart, npb;
   if ((rc = run_points(ctx, sb.R, n, pts, badR, &ppart, &npb))) return rc;
+  // speculative ccd^v for the all-valid case: R part on the points stream
+  if ((rc = run_unit_sum(ctx, ppart, npb, unitR, d_ccd + 32, pbad))) return rc;
   unsigned long long* hpart;
   uint32_t nhb;
   {
@@ -1027,21 +1096,16 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
     timer_end(ctx, "hash", ctx->s_main, tb, te);
     nhb = (uint32_t)blocks;
   }
+  // [e]Y + [s]G and the s part of ccd^v on the table stream, while the MSM runs
+  if ((rc = run_prep(ctx, hpart, nhb, nullptr, tableY, prep, sb.s, n, d_ccd))) return rc;
   MsmState ms;
   if ((rc = run_msm_sort(ctx, ctx->s_main, z, 4, nullptr, n, ms))) return rc;
-  CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_table, 0));
   CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_points, 0));
   // A5-A6: weighted MSM and the weighted check of the whole batch
-  uint32_t *Rw, *words;
   uint8_t* d_acc;
-  if ((rc = ensure_t(ctx, "R_weighted", 128, &Rw))) return rc;
-  if ((rc = ensure_t(ctx, "final_words", 4 * 48, &words))) return rc;
   if ((rc = ensure_t(ctx, "accept", 16, &d_acc))) return rc;
   if ((rc = run_msm_finish(ctx, ctx->s_main, pts, badR, ms, Rw))) return rc;
-  if ((rc = run_finalize(ctx, hpart, nhb, ppart, npb, Rw, nullptr, tableY, d_acc, nullptr))) return rc;
-  // unit sums of the good entries (ccd^v when every entry is valid)
-  uint8_t* d_ccd;
-  if ((rc = ensure_t(ctx, "ccd", 64, &d_ccd))) return rc;
+  if ((rc = run_check(ctx, prep, Rw, pbad, d_acc))) return rc;
   const int sblocks = grid_for(ctx, n, kHashThreads, 8);
   unsigned long long* sp;
   if ((rc = ensure_t(ctx, "ccd_spart", (size_t)sblocks * 13 * 8, &sp))) return rc;
@@ -1146,13 +1210,8 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
   uint32_t* pp;
   if ((rc = ensure_t(ctx, "ccd_ppart", (size_t)pblocks * kPointPartialWords * 4, &pp))) return rc;
   if (all_valid) {
-    // every entry valid: no list; ccd^v = the unit sums of the whole batch
+    // every entry valid: no list; ccd^v = the unit sums of the whole batch, already in d_ccd
     CU(cudaMemsetAsync(d_cnt, 0, 8, ctx->s_main));
-    k_sum_scalars<<<sblocks, kHashThreads, 0, ctx->s_main>>>(sb.s, n, nullptr, sp);
-    k_reduce_scalars<<<1, 32, 0, ctx->s_main>>>(sp, sblocks, d_ccd);
-    k_sum_encode<<<1, kFinalThreads, 0, ctx->s_main>>>(ppart, npb, nullptr, d_ccd + 32, nullptr);
-    ctx->launch_count += 3;
-    CU(cudaGetLastError());
   } else {
     if ((rc = run_compact(ctx, inv, n, batch->first_index, d_idx, std::min(cap, n), d_cnt))) return rc;
     k_sum_scalars<<<sblocks, kHashThreads, 0, ctx->s_main>>>(sb.s, n, inv, sp);
