@@ -342,10 +342,16 @@ int run_ytable(poslo_ctx* ctx, const uint8_t* Y, uint32_t** table_out) {
   return POSLO_OK;
 }
 
+// Resident decode blocks per SM: below the register-file limit (4) the remaining registers
+// host a hash block, so SHA-256 (ALU pipe) runs beside the field arithmetic (IMAD pipe).
+#ifndef POSLO_POINTS_BLOCKS
+#define POSLO_POINTS_BLOCKS 3
+#endif
+
 int run_points(poslo_ctx* ctx, const uint8_t* R, uint64_t count, uint32_t* pts_out, uint8_t* bad_out,
                uint32_t** partial_out, uint32_t* nblocks_out) {
   int rc;
-  const int blocks = grid_for(ctx, count, kPointThreads, 8);
+  const int blocks = grid_for(ctx, count, kPointThreads, POSLO_POINTS_BLOCKS);
   uint32_t* partial;
   if ((rc = ensure_t(ctx, "point_partial", (size_t)blocks * kPointPartialWords * 4, &partial))) return rc;
   CU(cudaEventRecord(ctx->ev_main, ctx->s_main));
