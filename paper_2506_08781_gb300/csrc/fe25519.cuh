@@ -542,10 +542,6 @@ __device__ __forceinline__ fe fe_sqn(fe a, int n) {
   return a;
 }
 
-// Out-of-line copies for loops whose bodies would otherwise hold many inlined products
-// (a mixed addition is seven): one shared body keeps the loop inside the instruction cache.
-static __device__ __noinline__ fe fe_mul_nl(const fe a, const fe b) { return fe_mul(a, b); }
-
 // Multiply by a small constant k < 2^26 and fold.
 __device__ __forceinline__ fe fe_mul_small(const fe& a, uint32_t k) {
   uint32_t t[16];

@@ -132,18 +132,6 @@ __device__ __forceinline__ ge ge_madd(const ge& p, const fe& x, const fe& y, con
   return r;
 }
 
-// ge_madd with out-of-line field products, for loops over many mixed additions.
-__device__ __forceinline__ ge ge_madd_nl(const ge& p, const fe& x, const fe& y, const fe& t2d) {
-  const fe A = fe_mul_nl(fe_sub(p.Y, p.X), fe_sub(y, x));
-  const fe B = fe_mul_nl(fe_add(p.Y, p.X), fe_add(y, x));
-  const fe C = fe_mul_nl(p.T, t2d);
-  const fe D = fe_add(p.Z, p.Z);
-  const fe E = fe_sub(B, A), F = fe_sub(D, C), G = fe_add(D, C), H = fe_add(B, A);
-  ge r;
-  r.X = fe_mul_nl(E, F); r.Y = fe_mul_nl(G, H); r.Z = fe_mul_nl(F, G); r.T = fe_mul_nl(E, H);
-  return r;
-}
-
 // ---- quad-cooperative point operations ------------------------------------------------
 // Four consecutive lanes of a warp (a quad) hold the same point and split the field
 // multiplications of one group operation between them, then exchange the results by

@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(128) k_msm_accum(const uint32_t* pts, const ui
       pts_load(pts + (size_t)kPtsWords * tn, nx, ny, nt);
     }
     // entries whose point did not decode are sorted but never added
-    if (!(skip && skip[tc])) acc = ge_madd_nl(acc, x, y, t2d);
+    if (!(skip && skip[tc])) acc = ge_madd(acc, x, y, t2d);
     x = nx; y = ny; t2d = nt;
     tc = tn;
   }
