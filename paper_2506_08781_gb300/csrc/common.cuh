@@ -160,22 +160,6 @@ __device__ __forceinline__ void hash_entry(const uint8_t* m, uint32_t L, const u
   }
 }
 
-// z_t = SHA-256("POSLO-Z" || verifier_seed || le64(t))[0..16) as a 128-bit little-endian integer.
-__device__ __forceinline__ void weight_of(const uint32_t zpre[10], uint64_t t, uint32_t z[4]) {
-  uint32_t w[16];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) w[i] = zpre[i];
-  const uint32_t lo = (uint32_t)t, hi = (uint32_t)(t >> 32);
-  w[9] = zpre[9] | (lo & 0xffu);
-  w[10] = ((lo >> 8) & 0xffu) << 24 | ((lo >> 16) & 0xffu) << 16 | ((lo >> 24) & 0xffu) << 8 | (hi & 0xffu);
-  w[11] = ((hi >> 8) & 0xffu) << 24 | ((hi >> 16) & 0xffu) << 16 | ((hi >> 24) & 0xffu) << 8 | 0x80u;
-  w[12] = 0; w[13] = 0; w[14] = 0; w[15] = 47 * 8;
-  uint32_t st[8];
-  sha256_init(st);
-  sha256_compress(st, w);
-  z[0] = bswap32(st[0]); z[1] = bswap32(st[1]); z[2] = bswap32(st[2]); z[3] = bswap32(st[3]);
-}
-
 __device__ __forceinline__ void warp_sum_u64(unsigned long long& v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -444,15 +428,21 @@ struct SignCArgs {
 constexpr int kMsmChunk = 16;
 constexpr int kMsmSeg = 16;     // sorted entries per thread in the bucket accumulation
 
+// Pippenger plan with signed window digits.  Scalars of `sw` words hold at most `bits` bits
+// (127 for the 4-word weights z_t, whose top bit is clear; 256 for 8-word scalars); windows =
+// ceil((bits + 1) / c), so the last window never carries out.  A digit lies in
+// [-(2^(c-1) - 1), 2^(c-1)]; its bucket is |digit| in 1 .. 2^(c-1), and the bucket array of a
+// window is padded to nb = 2^(c-1) + kMsmChunk so that it splits into whole chunks.
 struct MsmPlan {
   int c;              // window bits (8..16)
-  int sw;             // scalar words: 4 (128-bit weights) or 8 (256-bit scalars)
-  int windows;        // ceil(32 sw / c)
-  uint32_t nb;        // buckets per window, 2^c
-  uint32_t nchunks;   // nb / kMsmChunk
-  int jbits;          // log2(nchunks)
+  int sw;             // scalar words: 4 (weights below 2^127) or 8 (256-bit scalars)
+  int windows;        // ceil((bits + 1) / c)
+  uint32_t nb;        // buckets per window, 2^(c-1) + kMsmChunk (bucket 0 and the padding stay empty)
+  uint32_t nchunks;   // nb / kMsmChunk = 2^(c-5) + 1
+  int jbits;          // bits of the largest chunk index 2^(c-5): c - 4
 };
 
+// Unsigned c-bit field w of the scalar (0 past its last word).
 __device__ __forceinline__ uint32_t z_digit(const uint32_t* z, int sw, int w, int c) {
   const int bit = w * c;
   if (bit >= 32 * sw) return 0;
@@ -461,6 +451,20 @@ __device__ __forceinline__ uint32_t z_digit(const uint32_t* z, int sw, int w, in
   if (word + 1 < sw) v |= (uint64_t)z[word + 1] << 32;
   return (uint32_t)(v >> off) & ((1u << c) - 1u);
 }
+
+// Signed recoding, windows taken in increasing order: r = field + carry in [0, 2^c]; above
+// 2^(c-1) the digit is r - 2^c (negative) and 1 carries into the next window.  Returns the
+// bucket |digit| (0: no entry in this window) and its sign.
+__device__ __forceinline__ uint32_t z_sdigit(const uint32_t* z, int sw, int w, int c, uint32_t& carry, bool& neg) {
+  const uint32_t r = z_digit(z, sw, w, c) + carry;
+  neg = r > (1u << (c - 1));
+  carry = neg ? 1u : 0u;
+  return neg ? (1u << c) - r : r;
+}
+
+// Sorted bucket codes: bits 0..14 = bucket - 1, bit 15 = the digit is negative.
+constexpr uint32_t kBktNeg = 0x8000u, kBktMask = 0x7fffu;
+constexpr int kMsmMaxWindows = 40;   // c >= 8: at most ceil(257 / 8) = 33 windows
 
 __device__ __forceinline__ void z_load(const uint32_t* z, int sw, uint64_t t, uint32_t zw[8]) {
   const uint4* p = reinterpret_cast<const uint4*>(z + (size_t)sw * t);

@@ -132,6 +132,19 @@ __device__ __forceinline__ ge ge_madd(const ge& p, const fe& x, const fe& y, con
   return r;
 }
 
+// ge_madd of P or of -P = (-x, y, -t2d): negation swaps y - x with y + x and negates t2d.
+__device__ __forceinline__ ge ge_madd_signed(const ge& p, const fe& x, const fe& y, const fe& t2d, bool neg) {
+  const fe ym = fe_sub(y, x), yp = fe_add(y, x);
+  const fe A = fe_mul(fe_sub(p.Y, p.X), fe_select(ym, yp, neg));
+  const fe B = fe_mul(fe_add(p.Y, p.X), fe_select(yp, ym, neg));
+  const fe C = fe_mul(p.T, fe_select(t2d, fe_neg(t2d), neg));
+  const fe D = fe_add(p.Z, p.Z);
+  const fe E = fe_sub(B, A), F = fe_sub(D, C), G = fe_add(D, C), H = fe_add(B, A);
+  ge r;
+  r.X = fe_mul(E, F); r.Y = fe_mul(G, H); r.Z = fe_mul(F, G); r.T = fe_mul(E, H);
+  return r;
+}
+
 // ---- quad-cooperative point operations ------------------------------------------------
 // Four consecutive lanes of a warp (a quad) hold the same point and split the field
 // multiplications of one group operation between them, then exchange the results by

@@ -14,8 +14,10 @@ __global__ void k_msm_count(const uint32_t* z, const uint8_t* skip, uint64_t n, 
     if (skip && skip[t]) continue;
     uint32_t zw[8];
     z_load(z, pl.sw, t, zw);
+    uint32_t carry = 0;
+    bool neg;
     for (int w = 0; w < pl.windows; ++w) {
-      const uint32_t d = z_digit(zw, pl.sw, w, pl.c);
+      const uint32_t d = z_sdigit(zw, pl.sw, w, pl.c, carry, neg);
       if (d) rank[(size_t)w * n + t] = atomicAdd(&cnt[(size_t)w * pl.nb + d], 1u);
     }
   }
@@ -66,18 +68,21 @@ __global__ void k_msm_scatter(const uint32_t* z, const uint8_t* skip, uint64_t n
     if (skip && skip[t]) continue;
     uint32_t zw[8];
     z_load(z, pl.sw, t, zw);
+    uint32_t carry = 0;
+    bool neg;
     for (int w = 0; w < pl.windows; ++w) {
-      const uint32_t d = z_digit(zw, pl.sw, w, pl.c);
+      const uint32_t d = z_sdigit(zw, pl.sw, w, pl.c, carry, neg);
       if (d) {
         const size_t pos = (size_t)w * n + off[(size_t)w * pl.nb + d] + rank[(size_t)w * n + t];
         idx[pos] = (uint32_t)t;
-        bkt[pos] = (uint16_t)d;
+        bkt[pos] = (uint16_t)((d - 1u) | (neg ? kBktNeg : 0u));
       }
     }
   }
 }
 
-// Bucket sums B_{w,d}, load-balanced: thread (w, tau) adds exactly the kMsmSeg sorted entries
+// Bucket sums B_{w,d} = sum of sign(digit) P_t over the entries whose digit in window w has
+// magnitude d, load-balanced: thread (w, tau) adds exactly the kMsmSeg sorted entries
 // at positions [tau kMsmSeg, (tau+1) kMsmSeg) of window w, cutting its run wherever the
 // bucket changes.  A bucket lying strictly inside the range is written directly; the first
 // run goes to A[w][tau], the last (when different) to B[w][tau], and k_msm_combine joins
@@ -97,16 +102,16 @@ __global__ void __launch_bounds__(128) k_msm_accum(const uint32_t* pts, const ui
   const uint64_t p1 = min(p0 + kMsmSeg, nnz);
   const uint32_t* li = idx + (size_t)w * n;
   const uint16_t* lb = bkt + (size_t)w * n;
-  uint32_t cur = lb[p0];
+  uint32_t cur = lb[p0] & kBktMask;
   bool first = true;
   ge acc = ge_identity();
   fe x, y, t2d;
   uint32_t tc = __ldg(li + p0);
   pts_load(pts + (size_t)kPtsWords * tc, x, y, t2d);
   for (uint64_t p = p0; p < p1; ++p) {
-    const uint32_t d = lb[p];
+    const uint32_t code = lb[p], d = code & kBktMask;
     if (d != cur) {
-      uint32_t* dst = first ? A + 32 * g : buckets + 32 * ((size_t)w * pl.nb + cur);
+      uint32_t* dst = first ? A + 32 * g : buckets + 32 * ((size_t)w * pl.nb + cur + 1);
       ge_store(dst, acc);
       first = false;
       acc = ge_identity();
@@ -119,7 +124,7 @@ __global__ void __launch_bounds__(128) k_msm_accum(const uint32_t* pts, const ui
       pts_load(pts + (size_t)kPtsWords * tn, nx, ny, nt);
     }
     // entries whose point did not decode are sorted but never added
-    if (!(skip && skip[tc])) acc = ge_madd(acc, x, y, t2d);
+    if (!(skip && skip[tc])) acc = ge_madd_signed(acc, x, y, t2d, (code & kBktNeg) != 0);
     x = nx; y = ny; t2d = nt;
     tc = tn;
   }
@@ -207,7 +212,7 @@ __global__ void __launch_bounds__(512) k_msm_groups(const uint32_t* L, const uin
 // sum_w 2^{c w} W_w by Horner's rule in quad 0.  One warp; windows are processed in rounds
 // of eight quads.
 __global__ void __launch_bounds__(32) k_msm_final(const uint32_t* groups, MsmPlan pl, uint32_t* out) {
-  __shared__ uint32_t wsum[32][32];
+  __shared__ uint32_t wsum[kMsmMaxWindows][32];
   const int lane = threadIdx.x & 31, quad = lane >> 2;
   const int ng = 1 + pl.jbits;
   for (int r0 = 0; r0 < pl.windows; r0 += 8) {

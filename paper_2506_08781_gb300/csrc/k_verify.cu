@@ -197,7 +197,8 @@ __global__ void __launch_bounds__(kHashThreads, POSLO_HASH_MIN_BLOCKS) k_hash(co
         if (a.sbad_out) a.sbad_out[t] = canon ? 0 : 1;
       }
       if (a.weighted) {
-        const uint32_t z[4] = {bswap32(st[0]), bswap32(st[1]), bswap32(st[2]), bswap32(st[3])};
+        // z_t: the first 16 digest bytes as a little-endian integer, bit 127 cleared
+        const uint32_t z[4] = {bswap32(st[0]), bswap32(st[1]), bswap32(st[2]), bswap32(st[3]) & 0x7fffffffu};
         if (a.z_out) reinterpret_cast<uint4*>(a.z_out)[t] = make_uint4(z[0], z[1], z[2], z[3]);
         uint32_t pr[12];
         mul_4x8(pr, z, e.v);

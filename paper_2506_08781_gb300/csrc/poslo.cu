@@ -415,8 +415,9 @@ MsmPlan msm_plan(poslo_ctx* ctx, uint64_t n, int sw) {
   MsmPlan pl;
   pl.c = c;
   pl.sw = sw;
-  pl.windows = (32 * sw + c - 1) / c;
-  pl.nb = 1u << c;
+  const int bits = sw == 4 ? 127 : 256;
+  pl.windows = (bits + 1 + c - 1) / c;
+  pl.nb = (1u << (c - 1)) + kMsmChunk;
   pl.nchunks = pl.nb / kMsmChunk;
   pl.jbits = c - 4;
   return pl;

@@ -297,9 +297,36 @@ def test_msm_every_window_width(c):
     ks = [int.from_bytes(synth.random_bytes(c, f"w{i}", 32).tobytes(), "little") >> (i % 5) for i in range(n)]
     ks[3] = 0
     ks[4] = (1 << 256) - 1
+    # signed-digit edges: every c-bit field at 2^(c-1) (largest positive digit), at
+    # 2^(c-1) + 1 (smallest field that turns negative) and at 2^(c-1) - 1 under a carry
+    fields = lambda f: sum(f << (c * w) for w in range(256 // c)) & ((1 << 256) - 1)
+    ks[5] = fields(1 << (c - 1))
+    ks[6] = fields((1 << (c - 1)) + 1)
+    ks[7] = fields((1 << (c - 1)) - 1) + ((1 << c) - 1)
+    ks[8] = 1 << 255
     with poslo.Context(device=0, msm_window=c) as cx:
         got = cx.msm(b"".join(pts), b"".join(k.to_bytes(32, "little") for k in ks))
     assert got == O.msm(ks, pts)
+
+
+@pytest.mark.parametrize("c", [8, 12, 16])
+def test_weighted_checks_every_window_width(c):
+    """Weighted AVer and Distill (127-bit weights, signed window digits) keep the per-entry
+    definition's result at every window width."""
+    import __graft_entry__
+    __graft_entry__.build()
+    D, n2, n = 4, 16, 200
+    km, sk, Y, msgs, subsets, s, R, _ = _f_data(30 + c, n, D, n2, 0, 90)
+    ds_l = O.ds_root(km.root, D)
+    bad = synth.apply_tamper(msgs, synth.tamper_plan(30 + c, msgs, 7))
+    with poslo.Context(device=0, msm_window=c) as cx:
+        for m in (msgs, bad):
+            b = cx.make_batch(poslo.VARIANT_F, n2, Y, m.data, m.offs, b"".join(s), b"".join(R),
+                              O.ds_serialize(ds_l))
+            wi, ws, wR = O.distill_f(Y, m.as_list(), 0, n2, s, R, ds_l)
+            assert cx.aver(b, poslo.AGG_WEIGHTED) is (len(wi) == 0)
+            idx, cs, cR = cx.distill(b)
+            assert list(idx) == wi and cs == ws and cR == wR
 
 
 def test_msm_rejects_undecodable_point(ctx):
