@@ -123,6 +123,10 @@ def probe_int_peaks(device: int) -> dict:
 #     1 (PRF) + ceil((L + 25) / 64) (H)
 IMAD_PER_DECODE = 255 * (72 + 18) + 20 * (128 + 18)
 ALU_PER_COMPRESSION = 64 * 14 + 48 * 10 + 8
+# DRAM bytes (read + write) of one k_points launch over 2^20 entries, from an ncu capture:
+# the 32 MB of encodings read once; of the 100 MB of decoded points written, the part that has
+# left L2 by the end of the launch.
+POINTS_DRAM_BYTES_2P20 = 33_793_280 + 45_625_088
 
 
 def make_workload(n=N_ENTRIES, seed=SEED, tamper=0):
@@ -202,6 +206,7 @@ def bench_multi(ctx, steps: int, warmup: int) -> dict:
     args = (w["Y"], w["sizes"], np.zeros(nd, np.uint64), np.full(nd, MULTI_N2, np.uint32), w["ds"],
             d_msgs, d_offs, d_s, d_R)
     torch.cuda.synchronize()
+    msm_window = ctx.msm_autotune(w["total"], 4)
     for _ in range(warmup):
         acc, pairs = ctx.aver_multi(*args)
     got = [(int(a), int(b)) for a, b in pairs]
@@ -218,7 +223,7 @@ def bench_multi(ctx, steps: int, warmup: int) -> dict:
     return {"workload": f"{nd} devices, sizes log-uniform [{MULTI_LO}, {MULTI_HI}] (total {w['total']} entries), "
                         f"|m|~U[32,256], {len(w['pairs'])} devices with one flipped byte",
             "value": w["total"] / (ms * 1e-3), "unit": "entries/s", "ms_per_step": ms, "steps": steps,
-            "invalid_found": len(got), "setup_s": setup_s}
+            "invalid_found": len(got), "setup_s": setup_s, "msm_window": msm_window}
 
 
 # ------------------------------------------------------------------------------ config 5: serving
@@ -468,6 +473,7 @@ def run_ours(args):
     d_R = torch.from_numpy(R).cuda()
     torch.cuda.synchronize()
     batch = ctx.make_batch(poslo.VARIANT_F, N2, Y, d_msgs, d_offs, d_s, d_R, ds)
+    msm_window = ctx.msm_autotune(n, 4)   # window width of the weighted MSM, timed on this GPU
 
     def step(b):
         idx, cs, cR = ctx.distill(b)
@@ -552,7 +558,9 @@ def run_ours(args):
         ach = work / (kernels[dom]["ms_per_launch"] * 1e-3) / 1e9
         pk = peaks["imad_lo_ops"] / 1e9
         roof = {"bound": "alu", "pipe": "IMAD", "kernel": dom, "achieved": ach, "peak": pk, "unit": "Gop/s",
-                "frac": ach / pk, "traffic": None,
+                "frac": ach / pk, "traffic": POINTS_DRAM_BYTES_2P20 * n / (1 << 20),
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_points launch "
+                                  "at 2^20 entries (profiles/ncu_full_hash_points_msm_2p20.md)",
                 "peak_source": "probed mad.lo.u32 issue rate on this GPU (probe/peaks.cu)",
                 "work": "25,870 IMAD per R_t decode (schoolbook count)"}
     elif dom == "hash" and peaks:
@@ -575,7 +583,8 @@ def run_ours(args):
             "dtype": "u32", "data": "synthetic (seeded SplitMix64 messages; keys and signatures made by "
                                     "poslo_keygen_f/poslo_sign_f)",
             "config": {"workload": WORKLOAD, "entries_per_gpu": n, "message_bytes": int(msgs.data.nbytes),
-                       "l2": "inputs (215 MB) larger than the 129 MB L2; no flush", "parallelism": f"dp{world}"},
+                       "l2": "inputs (215 MB) larger than the 129 MB L2; no flush", "parallelism": f"dp{world}",
+                       "msm_window": msm_window, "msm_window_source": "poslo_msm_autotune"},
             "clocks": clocks,
             "gpu_launches": gpu_launches,
             "kernels": kernels,

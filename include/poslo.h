@@ -236,6 +236,17 @@ int poslo_hash_entries(poslo_ctx* ctx, const poslo_batch* batch, uint8_t* e_out)
 int poslo_msm(poslo_ctx* ctx, const uint8_t* points, const uint8_t* scalars, uint64_t n, uint32_t on_device,
               uint8_t out[32]);
 
+/* Window autotuner for the bucket MSM (no counterpart in the paper, whose aggregate uses unit
+ * coefficients): times every window width c in [max(8, lg - 8), min(16, lg - 1)], lg =
+ * floor(log2 n), on n synthetic points with random scalars of scalar_words 32-bit words (4:
+ * the 127-bit verification weights; 8: 256-bit scalars) and keeps the fastest for every later
+ * MSM of that size class and scalar width on this context, unless poslo_params.msm_window
+ * fixes c.  Untuned classes use c = min(16, max(8, lg - 4)).  Writes the chosen c to
+ * window_out (optional).  Allocates about (96 + 4 scalar_words + 16 windows) bytes per point
+ * of grow-only scratch.  EINVAL for n = 0, n > 2^32 or another scalar width.  Blocks until
+ * the timing runs finish; takes tens of milliseconds per width at n = 2^20. */
+int poslo_msm_autotune(poslo_ctx* ctx, uint64_t n, uint32_t scalar_words, uint32_t* window_out);
+
 /* ---- allocation-free variant ---------------------------------------------------------- */
 
 /* The paper has no counterpart to this entry point: it exists for callers that cannot

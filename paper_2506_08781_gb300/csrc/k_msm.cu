@@ -234,4 +234,27 @@ __global__ void __launch_bounds__(32) k_msm_final(const uint32_t* groups, MsmPla
   if (lane == 0) ge_store(out, acc);
 }
 
+// Synthetic input for timing window widths: every point is G (the cost of a complete
+// addition does not depend on its operands) and the scalars are SplitMix64 output with the
+// top bit of a 4-word weight, or the top 3 bits of an 8-word scalar, cleared.
+__global__ void k_msm_tune_fill(uint32_t* pts, uint32_t* z, uint64_t n, int sw) {
+  const ge G = ge_base();
+  const fe t2d = fe_mul(G.T, fe_d2());
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
+    uint32_t* dst = pts + (size_t)kPtsWords * t;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) { dst[i] = G.X.v[i]; dst[8 + i] = G.Y.v[i]; dst[16 + i] = t2d.v[i]; }
+    for (int k = 0; k < sw / 2; ++k) {
+      uint64_t x = (t * 8 + k) + 0x9e3779b97f4a7c15ull;
+      x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+      x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+      x ^= x >> 31;
+      z[(size_t)sw * t + 2 * k] = (uint32_t)x;
+      z[(size_t)sw * t + 2 * k + 1] = (uint32_t)(x >> 32);
+    }
+    z[(size_t)sw * t + sw - 1] &= sw == 4 ? 0x7fffffffu : 0x1fffffffu;
+  }
+}
+
 }  // namespace poslo

@@ -404,14 +404,7 @@ int run_msm_direct(poslo_ctx* ctx, cudaStream_t st, const uint8_t* points, const
 // Pippenger plan: the window c comes from the context (poslo_params.msm_window) or from the
 // autotuned table for this size class (see autotune_msm); the default before tuning is
 // c = log2(n) - 4 clamped to [8, 16].
-MsmPlan msm_plan(poslo_ctx* ctx, uint64_t n, int sw) {
-  int c = (int)ctx->msm_window;
-  if (c == 0) {
-    int lg = 0;
-    while ((1ull << (lg + 1)) <= std::max<uint64_t>(n, 1)) ++lg;
-    auto it = ctx->msm_tuned.find(lg * 16 + sw);
-    c = it != ctx->msm_tuned.end() ? it->second : std::min(16, std::max(8, lg - 4));
-  }
+MsmPlan msm_plan_c(int c, int sw) {
   MsmPlan pl;
   pl.c = c;
   pl.sw = sw;
@@ -421,6 +414,22 @@ MsmPlan msm_plan(poslo_ctx* ctx, uint64_t n, int sw) {
   pl.nchunks = pl.nb / kMsmChunk;
   pl.jbits = c - 4;
   return pl;
+}
+
+int log2_floor(uint64_t n) {
+  int lg = 0;
+  while ((1ull << (lg + 1)) <= std::max<uint64_t>(n, 1)) ++lg;
+  return lg;
+}
+
+MsmPlan msm_plan(poslo_ctx* ctx, uint64_t n, int sw) {
+  int c = (int)ctx->msm_window;
+  if (c == 0) {
+    const int lg = log2_floor(n);
+    auto it = ctx->msm_tuned.find(lg * 16 + sw);
+    c = it != ctx->msm_tuned.end() ? it->second : std::min(16, std::max(8, lg - 4));
+  }
+  return msm_plan_c(c, sw);
 }
 
 // Pippenger in two halves so the counting sort (which needs only the scalars) can run
@@ -1281,6 +1290,49 @@ int poslo_msm(poslo_ctx* ctx, const uint8_t* points, const uint8_t* scalars, uin
   if ((rc = check_status(ctx))) return rc;
   if (bad_cnt) return fail(ctx, POSLO_EINVAL, "%u points do not decode", bad_cnt);
   memcpy(out, h, 32);
+  return POSLO_OK;
+}
+
+int poslo_msm_autotune(poslo_ctx* ctx, uint64_t n, uint32_t scalar_words, uint32_t* window_out) {
+  if (!ctx || n == 0 || n > (1ull << 32) || (scalar_words != 4 && scalar_words != 8))
+    return fail(ctx, POSLO_EINVAL, "bad msm_autotune arguments");
+  int rc;
+  if ((rc = reset_status(ctx))) return rc;
+  const int sw = (int)scalar_words;
+  const int lg = log2_floor(n);
+  uint32_t *pts, *z, *acc;
+  if ((rc = ensure_t(ctx, "tune_pts", 4 * kPtsWords * n, &pts))) return rc;
+  if ((rc = ensure_t(ctx, "tune_z", 4 * (size_t)sw * n, &z))) return rc;
+  if ((rc = ensure_t(ctx, "msm_acc", 128, &acc))) return rc;
+  k_msm_tune_fill<<<grid_for(ctx, n, 256, 8), 256, 0, ctx->s_main>>>(pts, z, n, sw);
+  ++ctx->launch_count;
+  CU(cudaGetLastError());
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  int best_c = 0;
+  float best_ms = 0.f;
+  const int c_lo = std::max(8, std::min(16, lg - 8)), c_hi = std::min(16, std::max(8, lg - 1));
+  for (int c = c_lo; c <= c_hi && rc == POSLO_OK; ++c) {
+    const MsmPlan forced = msm_plan_c(c, sw);
+    float ms = 0.f;
+    for (int rep = 0; rep < 2 && rc == POSLO_OK; ++rep) {   // the first run grows the buffers
+      MsmState st;
+      cudaEventRecord(e0, ctx->s_main);
+      if ((rc = run_msm_sort(ctx, ctx->s_main, z, sw, nullptr, n, st, &forced))) break;
+      if ((rc = run_msm_finish(ctx, ctx->s_main, pts, nullptr, st, acc))) break;
+      cudaEventRecord(e1, ctx->s_main);
+      if (cudaEventSynchronize(e1) != cudaSuccess) rc = fail(ctx, POSLO_EDEVICE, "msm_autotune: %s", "sync failed");
+      else cudaEventElapsedTime(&ms, e0, e1);
+    }
+    if (rc == POSLO_OK && (best_c == 0 || ms < best_ms)) { best_c = c; best_ms = ms; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  if ((rc = check_status(ctx))) return rc;
+  ctx->msm_tuned[lg * 16 + sw] = best_c;
+  if (window_out) *window_out = (uint32_t)best_c;
   return POSLO_OK;
 }
 

@@ -26,7 +26,7 @@ AGG_UNIT, AGG_WEIGHTED = 0, 1
 EXPORTS = [
     "poslo_create", "poslo_destroy", "poslo_last_error", "poslo_stream",
     "poslo_keygen_c", "poslo_keygen_f", "poslo_sign_c", "poslo_sign_f", "poslo_disclose",
-    "poslo_aver", "poslo_distill", "poslo_epoch_seeds", "poslo_hash_entries", "poslo_msm",
+    "poslo_aver", "poslo_distill", "poslo_epoch_seeds", "poslo_hash_entries", "poslo_msm", "poslo_msm_autotune",
     "poslo_set_profiling", "poslo_kernel_time", "poslo_reset_kernel_times",
     "poslo_hash_entries_noalloc", "poslo_aver_multi",
     "poslo_serve_start", "poslo_serve_stop", "poslo_register_key", "poslo_submit", "poslo_poll",
@@ -93,6 +93,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "poslo_epoch_seeds": ([vp, u8p, u32, u64, u64, u8p], C.c_int),
         "poslo_hash_entries": ([vp, C.POINTER(Batch), u8p], C.c_int),
         "poslo_msm": ([vp, u8p, u8p, u64, u32, u8p], C.c_int),
+        "poslo_msm_autotune": ([vp, u64, u32, C.POINTER(u32)], C.c_int),
         "poslo_set_profiling": ([vp, C.c_int], C.c_int),
         "poslo_kernel_time": ([vp, C.c_char_p, C.POINTER(C.c_double), C.POINTER(u64)], C.c_int),
         "poslo_reset_kernel_times": ([vp], None),
@@ -394,6 +395,13 @@ class Context:
             n = len(points) // 32
         self._check(self.lib.poslo_msm(self.h, _ptr(points), _ptr(scalars), n, 1 if on_device else 0, _ptr(out)))
         return out.tobytes()
+
+    def msm_autotune(self, n: int, scalar_words: int = 4) -> int:
+        """Time the bucket MSM's window widths at size n; later MSMs of that size class use the
+        fastest.  Returns the chosen width."""
+        c = C.c_uint32(0)
+        self._check(self.lib.poslo_msm_autotune(self.h, n, scalar_words, C.byref(c)))
+        return int(c.value)
 
     # ------------------------------------------------------------------ profiling
     def set_profiling(self, on: bool):

@@ -87,3 +87,20 @@ def test_fullsize_distill_config3(big):
             continue
         e = O.entry_scalar(ds, bench.N2, int(t), bad.entry(int(t)))
         assert O.verify_entry_f(Yp, e, bytes(s[t]), bytes(R[t]))
+
+
+def test_fullsize_autotuned_window(big):
+    """bench.py tunes the MSM window before timing; the tuned width gives the same results."""
+    import torch
+    ctx, msgs = big["ctx"], big["msgs"]
+    c = ctx.msm_autotune(msgs.n, 4)
+    assert 8 <= c <= 16
+    b = ctx.make_batch(poslo.VARIANT_F, bench.N2, big["Y"], big["d_msgs"], big["d_offs"], big["d_s"], big["d_R"],
+                       big["ds"])
+    assert ctx.aver(b, poslo.AGG_WEIGHTED) is True
+    plan = synth.tamper_plan(3, msgs, round(0.001 * msgs.n))
+    bad = synth.apply_tamper(msgs, plan)
+    b = ctx.make_batch(poslo.VARIANT_F, bench.N2, big["Y"], torch.from_numpy(bad.data).cuda(), big["d_offs"],
+                       big["d_s"], big["d_R"], big["ds"])
+    torch.cuda.synchronize()
+    assert list(ctx.distill(b)[0]) == list(plan.idx)
