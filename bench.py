@@ -220,10 +220,22 @@ def bench_multi(ctx, steps: int, warmup: int) -> dict:
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
+    # stage times from one more (untimed) call with the context's kernel timers on
+    ctx.set_profiling(True)
+    ctx.reset_kernel_times()
+    ctx.aver_multi(*args)
+    torch.cuda.synchronize()
+    stages = {}
+    for name in ("seeds", "hash", "points", "msm", "msm_sort", "msm_bucket", "msm_reduce", "msm_final", "table",
+                 "prep", "check", "finalize", "tree", "bisect", "localise"):
+        tot, cnt = ctx.kernel_time(name)
+        if cnt:
+            stages[name] = {"ms": tot, "launches": cnt}
+    ctx.set_profiling(False)
     return {"workload": f"{nd} devices, sizes log-uniform [{MULTI_LO}, {MULTI_HI}] (total {w['total']} entries), "
                         f"|m|~U[32,256], {len(w['pairs'])} devices with one flipped byte",
             "value": w["total"] / (ms * 1e-3), "unit": "entries/s", "ms_per_step": ms, "steps": steps,
-            "invalid_found": len(got), "setup_s": setup_s, "msm_window": msm_window}
+            "invalid_found": len(got), "setup_s": setup_s, "msm_window": msm_window, "stages": stages}
 
 
 # ------------------------------------------------------------------------------ config 5: serving

@@ -26,6 +26,8 @@ constexpr int kHashThreads = 128;
 constexpr int kPointThreads = 128;
 constexpr int kTableWindows = 64;   // 4-bit windows over 256 bits
 constexpr int kTableDigits = 8;     // signed digits |d| in 1..8
+constexpr int kTableWords = kTableWindows * kTableDigits * 32;   // one table: 64 KB
+constexpr int kTableThreads = 4 * kTableWindows;                 // one quad per window
 
 // Device-side error codes written to the context's status word.
 enum : uint32_t { kErrNone = 0, kErrSeed = 1, kErrKey = 2, kErrPoint = 4, kErrTimeout = 8, kErrInput = 16 };
@@ -202,8 +204,7 @@ __device__ __forceinline__ ge ge_load(const uint32_t* src) {
 
 
 // ----------------------------------------------------------------------------------------
-// Fixed-window tables: table[w][d-1] = d * 16^w * P for w = 0..63, d = 1..8.  Thread w
-// reaches 16^w P by 4w doublings, so the whole table costs the latency of 252 doublings.
+// Fixed-window tables: table[w][d-1] = d * 16^w * P for w = 0..63, d = 1..8 (k_table).
 // ----------------------------------------------------------------------------------------
 
 
@@ -526,8 +527,11 @@ __global__ void k_epoch_seeds(const DsNode* __restrict__ ds, int nds, uint64_t e
                               uint32_t* __restrict__ x0_out, uint32_t* __restrict__ status);
 __global__ void __launch_bounds__(kHashThreads, POSLO_HASH_MIN_BLOCKS) k_hash(const HashArgs a);
 __global__ void __launch_bounds__(kPointThreads) k_points(const PointArgs a);
-__global__ void k_table(const uint32_t* __restrict__ enc, uint32_t* __restrict__ table,
-                        uint32_t* __restrict__ status, int use_base);
+__global__ void __launch_bounds__(kTableThreads) k_table(const uint32_t* __restrict__ enc,
+                                                         const uint32_t* __restrict__ pts,
+                                                         const uint32_t* __restrict__ list,
+                                                         uint32_t* __restrict__ tables,
+                                                         uint32_t* __restrict__ status, int use_base);
 __global__ void __launch_bounds__(kFinalThreads) k_finalize(const FinalArgs a);
 __global__ void __launch_bounds__(128) k_final_prep(const PrepArgs a);
 __global__ void k_final_check(const uint32_t* prep, const uint32_t* R, const uint32_t* point_bad,
@@ -582,14 +586,30 @@ __global__ void k_rebase_offs(const uint64_t* raw, const uint64_t* slot, const u
 __global__ void __launch_bounds__(256) k_segment_sums(const uint8_t* e, const uint8_t* s, const uint32_t* z,
                                                       const uint32_t* pts, const uint8_t* badR, const uint8_t* badS,
                                                       const uint64_t* start, SegSums out);
-__global__ void __launch_bounds__(kFinalThreads) k_multi_check(const uint32_t* P1, const uint32_t* P2,
+__global__ void __launch_bounds__(kFinalThreads) k_multi_check(const uint32_t* P1, const uint32_t* P1sub, const uint32_t* P2,
                                                                const uint32_t* Sw, const uint8_t* dev_flag,
                                                                uint32_t n_dev, const uint32_t* tableG,
                                                                uint8_t* accept);
 __global__ void __launch_bounds__(128) k_device_unit_check(const uint32_t* Ypts, SegSums ss, uint32_t n_dev,
                                                            const uint32_t* tableG, uint8_t* dev_flag);
+struct MultiCheckArgs {
+  const uint32_t* pts;        // decoded R_t of the whole batch (kPtsWords each)
+  const uint8_t* e;           // e_t, 32 bytes each
+  const uint8_t* s;           // s_t, 32 bytes each
+  const uint8_t* badR;        // 1 = R_t does not decode
+  const uint8_t* badS;        // 1 = s_t is not canonical
+  const uint64_t* seg_start;  // n_dev + 1 entry offsets of the devices
+  const uint32_t* fl;         // the flagged devices, nfl of them
+  const uint64_t* fstart;     // nfl + 1: prefix sums of their entry counts
+  uint32_t nfl;
+  const uint32_t* tables;     // nfl window tables of their keys (kTableWords each)
+  const uint32_t* tableG;
+  uint8_t* inv;               // out: 1 = entry invalid (written for the flagged devices' entries)
+};
+__global__ void __launch_bounds__(128) k_multi_entry_check(const MultiCheckArgs a);
+__global__ void k_segment_any(const uint8_t* inv, const uint64_t* seg_start, const uint32_t* fl, uint8_t* out);
 __global__ void k_device_to_entries(const uint8_t* dev_flag, const uint64_t* start, const uint8_t* badR,
-                                    uint8_t* skip);
+                                    uint8_t* skip, int keep_flagged);
 constexpr uint32_t kFlagChunk = 8192;
 __global__ void __launch_bounds__(1024) k_flag_count(const uint8_t* flags, uint64_t n, uint32_t* blockcnt);
 __global__ void __launch_bounds__(1024) k_flag_scan(const uint32_t* blockcnt, uint32_t nblocks, uint64_t* blockoff,

@@ -132,7 +132,8 @@ __global__ void __launch_bounds__(256) k_segment_sums(const uint8_t* e, const ui
 // Combined weighted check over the devices not flagged:
 // [8](P1 - P2 - (sum_d S_d) G) = O, with P1 = sum_t z_t R_t and P2 = sum_d E_d Y_d already
 // restricted to those devices.  One block.
-__global__ void __launch_bounds__(kFinalThreads) k_multi_check(const uint32_t* P1, const uint32_t* P2,
+__global__ void __launch_bounds__(kFinalThreads) k_multi_check(const uint32_t* P1, const uint32_t* P1sub,
+                                                               const uint32_t* P2,
                                                                const uint32_t* Sw, const uint8_t* dev_flag,
                                                                uint32_t n_dev, const uint32_t* tableG,
                                                                uint8_t* accept) {
@@ -169,7 +170,9 @@ __global__ void __launch_bounds__(kFinalThreads) k_multi_check(const uint32_t* P
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    const ge diff = ge_sub(ge_sub(ge_load(P1), ge_load(P2)), ge_load(pts_[0]));
+    ge p1 = ge_load(P1);
+    if (P1sub) p1 = ge_sub(p1, ge_load(P1sub));
+    const ge diff = ge_sub(ge_sub(p1, ge_load(P2)), ge_load(pts_[0]));
     accept[0] = ge_is_identity(ge_mul_cofactor(diff)) ? 1 : 0;
   }
 }
@@ -206,10 +209,52 @@ __global__ void __launch_bounds__(128) k_device_unit_check(const uint32_t* Ypts,
 // Entry flags from device flags (entries of flagged devices are left out) or'ed with the
 // malformed-point flags.  One block per device.
 __global__ void k_device_to_entries(const uint8_t* dev_flag, const uint64_t* start, const uint8_t* badR,
-                                    uint8_t* skip) {
+                                    uint8_t* skip, int keep_flagged) {
   const uint32_t d = blockIdx.x;
-  const uint8_t f = dev_flag[d];
+  const uint8_t f = keep_flagged ? !dev_flag[d] : dev_flag[d];
   for (uint64_t t = start[d] + threadIdx.x; t < start[d + 1]; t += blockDim.x) skip[t] = (f || badR[t]) ? 1 : 0;
+}
+
+// Single-entry checks [8](R_t - e_t Y_d - s_t G) = O (Fig. 4 with |m| = 1) for every entry of
+// the flagged devices, plus s_t canonical and R_t decodable.  Thread t belongs to flagged
+// device k = the last k with fstart[k] <= t (binary search); R_t comes from the decoded point
+// buffer and [e]Y_d from table slot k.
+__global__ void __launch_bounds__(128) k_multi_entry_check(const MultiCheckArgs a) {
+  const uint64_t total = a.fstart[a.nfl];
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
+    uint32_t lo = 0, hi = a.nfl;   // fstart[lo] <= t < fstart[hi]
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (a.fstart[mid] <= t) lo = mid; else hi = mid;
+    }
+    const uint64_t g = a.seg_start[a.fl[lo]] + (t - a.fstart[lo]);
+    bool ok = !a.badR[g] && !a.badS[g];
+    if (ok) {
+      const uint4* ep = reinterpret_cast<const uint4*>(a.e + 32 * g);
+      const uint4* sp = reinterpret_cast<const uint4*>(a.s + 32 * g);
+      const uint4 e0 = ep[0], e1 = ep[1], s0 = __ldg(sp), s1 = __ldg(sp + 1);
+      const uint32_t e[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
+      const uint32_t s[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+      ge R;
+      fe t2d;
+      pts_load(a.pts + (size_t)kPtsWords * g, R.X, R.Y, t2d);
+      R.Z = fe_one();
+      R.T = fe_mul(R.X, R.Y);
+      const ge d = ge_sub(R, double_scalar_tables(e, s, a.tables + (size_t)lo * kTableWords, a.tableG));
+      ok = ge_is_identity(ge_mul_cofactor(d));
+    }
+    a.inv[g] = ok ? 0 : 1;
+  }
+}
+
+// Per flagged device k: 1 if any of its entries is flagged in inv.
+__global__ void k_segment_any(const uint8_t* inv, const uint64_t* seg_start, const uint32_t* fl, uint8_t* out) {
+  const uint32_t d = fl[blockIdx.x];
+  int any = 0;
+  for (uint64_t t = seg_start[d] + threadIdx.x; t < seg_start[d + 1]; t += blockDim.x) any |= inv[t];
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) out[blockIdx.x] = any ? 1 : 0;
 }
 
 }  // namespace poslo

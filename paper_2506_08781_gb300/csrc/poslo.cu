@@ -327,13 +327,13 @@ int run_ytable(poslo_ctx* ctx, const uint8_t* Y, uint32_t** table_out) {
   uint32_t* d_Y;
   if ((rc = ensure_t(ctx, "Y", 32, &d_Y))) return rc;
   uint32_t* tableY;
-  if ((rc = ensure_t(ctx, "tableY", kTableWindows * kTableDigits * 128, &tableY))) return rc;
+  if ((rc = ensure_t(ctx, "tableY", 4 * (size_t)kTableWords, &tableY))) return rc;
   CU(cudaMemcpyAsync(d_Y, Y, 32, cudaMemcpyHostToDevice, ctx->s_main));
   CU(cudaEventRecord(ctx->ev_main, ctx->s_main));
   CU(cudaStreamWaitEvent(ctx->s_table, ctx->ev_main, 0));
   cudaEvent_t tb, te;
   timer_begin(ctx, "table", ctx->s_table, &tb, &te);
-  k_table<<<1, kTableWindows, 0, ctx->s_table>>>(d_Y, tableY, ctx->status, 0);
+  k_table<<<1, kTableThreads, 0, ctx->s_table>>>(d_Y, nullptr, nullptr, tableY, ctx->status, 0);
   ++ctx->launch_count;
   CU(cudaGetLastError());
   timer_end(ctx, "table", ctx->s_table, tb, te);
@@ -663,9 +663,9 @@ int poslo_create(const poslo_params* params, poslo_ctx** out) {
     return bail(POSLO_EDEVICE);
   if (cudaMalloc(&ctx->status, 4) != cudaSuccess) return bail(POSLO_ENOMEM);
   if (cudaMallocHost(&ctx->h_status, 4) != cudaSuccess) return bail(POSLO_ENOMEM);
-  if (cudaMalloc(&ctx->tableG, kTableWindows * kTableDigits * 128) != cudaSuccess) return bail(POSLO_ENOMEM);
+  if (cudaMalloc(&ctx->tableG, 4 * (size_t)kTableWords) != cudaSuccess) return bail(POSLO_ENOMEM);
   cudaMemsetAsync(ctx->status, 0, 4, ctx->s_main);
-  k_table<<<1, kTableWindows, 0, ctx->s_main>>>(nullptr, ctx->tableG, ctx->status, 1);
+  k_table<<<1, kTableThreads, 0, ctx->s_main>>>(nullptr, nullptr, nullptr, ctx->tableG, ctx->status, 1);
   ++ctx->launch_count;
   if (cudaStreamSynchronize(ctx->s_main) != cudaSuccess) return bail(POSLO_EDEVICE);
   *out = ctx;
@@ -1473,8 +1473,9 @@ int poslo_aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, uint8_t* accep
   // ---- A5-A6: sum_t z_t R_t, per-device sums, sum_d E_d Y_d, one combined check
   uint32_t *P1, *P2, *segbuf;
   uint8_t *d_acc, *dev_flag, *eskip;
-  if ((rc = ensure_t(ctx, "m_P", 256, &P1))) return rc;
+  if ((rc = ensure_t(ctx, "m_P", 384, &P1))) return rc;
   P2 = P1 + 32;
+  uint32_t* P3 = P1 + 64;
   if ((rc = ensure_t(ctx, "accept", 16, &d_acc))) return rc;
   if ((rc = ensure_t(ctx, "m_devflag", nd, &dev_flag))) return rc;
   if ((rc = ensure_t(ctx, "m_eskip", N1, &eskip))) return rc;
@@ -1490,7 +1491,7 @@ int poslo_aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, uint8_t* accep
   k_segment_sums<<<nd, 256, 0, ctx->s_main>>>(d_e, sb.s, z, pts, badR, badS, seg_start, ss);
   ++ctx->launch_count;
   if ((rc = run_msm(ctx, ctx->s_main, Ypts, ss.Ew, 8, nullptr, nd, P2))) return rc;
-  k_multi_check<<<1, kFinalThreads, 0, ctx->s_main>>>(P1, P2, ss.Sw, nullptr, nd, ctx->tableG, d_acc);
+  k_multi_check<<<1, kFinalThreads, 0, ctx->s_main>>>(P1, nullptr, P2, ss.Sw, nullptr, nd, ctx->tableG, d_acc);
   ++ctx->launch_count;
   CU(cudaGetLastError());
   uint8_t all_ok = 0;
@@ -1509,11 +1510,13 @@ int poslo_aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, uint8_t* accep
     // ---- A7 across devices: unit check per device, then confirm the rest together
     k_device_unit_check<<<(unsigned)((4ull * nd + 127) / 128), 128, 0, ctx->s_main>>>(Ypts, ss, nd, ctx->tableG,
                                                                                      dev_flag);
-    k_device_to_entries<<<nd, 256, 0, ctx->s_main>>>(dev_flag, seg_start, badR, eskip);
+    // the weighted sum over the devices not flagged = P1 minus the flagged devices' part,
+    // an MSM over their entries only
+    k_device_to_entries<<<nd, 256, 0, ctx->s_main>>>(dev_flag, seg_start, badR, eskip, 1);
     ctx->launch_count += 2;
-    if ((rc = run_msm(ctx, ctx->s_main, pts, z, 4, eskip, N, P1))) return rc;
+    if ((rc = run_msm(ctx, ctx->s_main, pts, z, 4, eskip, N, P3))) return rc;
     if ((rc = run_msm(ctx, ctx->s_main, Ypts, ss.Ew, 8, dev_flag, nd, P2))) return rc;
-    k_multi_check<<<1, kFinalThreads, 0, ctx->s_main>>>(P1, P2, ss.Sw, dev_flag, nd, ctx->tableG, d_acc);
+    k_multi_check<<<1, kFinalThreads, 0, ctx->s_main>>>(P1, P3, P2, ss.Sw, dev_flag, nd, ctx->tableG, d_acc);
     ++ctx->launch_count;
     uint8_t confirmed = 0;
     CU(cudaMemcpyAsync(&confirmed, d_acc, 1, cudaMemcpyDeviceToHost, ctx->s_main));
@@ -1521,35 +1524,72 @@ int poslo_aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, uint8_t* accep
     if ((rc = check_status(ctx))) return rc;
     if (!confirmed) std::fill(flag.begin(), flag.end(), 1);   // cancelling errors: settle every device
   }
-  // ---- localise inside the flagged devices (entry-level Distill per device)
-  uint64_t cnt = 0;
-  std::vector<uint64_t> idx;
+  // ---- localise inside the flagged devices: the single-entry check of every entry of every
+  // flagged device in one launch (window tables of their keys built together, one block each)
+  std::vector<uint32_t> fl;
+  std::vector<uint64_t> fst(1, 0);
   for (uint32_t d = 0; d < nd; ++d) {
     accept[d] = 1;
-    if (!flag[d]) continue;
-    const uint64_t lo = mb->dev_start[d], nd_ = mb->dev_start[d + 1] - lo;
-    poslo_batch b{};
-    b.variant = POSLO_VARIANT_F;
-    b.n2 = mb->n2[d];
-    b.Y = mb->Y + 32 * (size_t)d;
-    b.msgs = mb->msgs;
-    b.offs = mb->offs + lo;
-    b.n = nd_;
-    b.first_index = mb->first_index[d];
-    b.s = mb->s + 32 * lo;
-    b.R = mb->R + 32 * lo;
-    b.R_count = nd_;
-    b.ds = mb->ds + 24 * (size_t)mb->ds_off[d];
-    b.ds_nodes = mb->ds_off[d + 1] - mb->ds_off[d];
-    b.on_device = mb->on_device;
-    idx.assign(std::max<uint64_t>(nd_, 1), 0);
-    uint64_t k = 0;
-    if ((rc = poslo_distill(ctx, &b, idx.data(), nd_, &k, nullptr, nullptr))) return rc;
-    if (k) accept[d] = 0;
-    for (uint64_t q = 0; q < k; ++q, ++cnt) {
-      if (invalid_pairs && cnt < cap) {
-        invalid_pairs[2 * cnt] = d;
-        invalid_pairs[2 * cnt + 1] = idx[q];
+    if (flag[d]) {
+      fl.push_back(d);
+      fst.push_back(fst.back() + (mb->dev_start[d + 1] - mb->dev_start[d]));
+    }
+  }
+  const uint32_t nfl = (uint32_t)fl.size();
+  uint64_t cnt = 0;
+  if (nfl) {
+    uint32_t *d_fl, *tables;
+    uint64_t *d_fst, *d_idx;
+    uint8_t *inv, *d_any;
+    const uint64_t capn = std::max<uint64_t>(std::min(cap, N), 1);
+    if ((rc = ensure_t(ctx, "m_fl", 4 * (size_t)nfl, &d_fl))) return rc;
+    if ((rc = ensure_t(ctx, "m_fst", 8 * (size_t)(nfl + 1), &d_fst))) return rc;
+    if ((rc = ensure_t(ctx, "m_tables", 4 * (size_t)kTableWords * nfl, &tables))) return rc;
+    if ((rc = ensure_t(ctx, "m_inv", N1, &inv))) return rc;
+    if ((rc = ensure_t(ctx, "m_any", nfl, &d_any))) return rc;
+    if ((rc = ensure_t(ctx, "m_idx", 8 * capn + 8, &d_idx))) return rc;
+    uint64_t* d_cnt = d_idx + capn;
+    CU(cudaMemcpyAsync(d_fl, fl.data(), 4 * (size_t)nfl, cudaMemcpyHostToDevice, ctx->s_main));
+    CU(cudaMemcpyAsync(d_fst, fst.data(), 8 * (size_t)(nfl + 1), cudaMemcpyHostToDevice, ctx->s_main));
+    CU(cudaMemsetAsync(inv, 0, N1, ctx->s_main));
+    cudaEvent_t tb, te;
+    timer_begin(ctx, "localise", ctx->s_main, &tb, &te);
+    k_table<<<nfl, kTableThreads, 0, ctx->s_main>>>(nullptr, Ypts, d_fl, tables, ctx->status, 0);
+    MultiCheckArgs ca{};
+    ca.pts = pts;
+    ca.e = d_e;
+    ca.s = sb.s;
+    ca.badR = badR;
+    ca.badS = badS;
+    ca.seg_start = seg_start;
+    ca.fl = d_fl;
+    ca.fstart = d_fst;
+    ca.nfl = nfl;
+    ca.tables = tables;
+    ca.tableG = ctx->tableG;
+    ca.inv = inv;
+    if (fst[nfl]) k_multi_entry_check<<<grid_for(ctx, fst[nfl], 128, 8), 128, 0, ctx->s_main>>>(ca);
+    k_segment_any<<<nfl, 256, 0, ctx->s_main>>>(inv, seg_start, d_fl, d_any);
+    ctx->launch_count += 3;
+    CU(cudaGetLastError());
+    if ((rc = run_compact(ctx, inv, N, 0, d_idx, std::min(cap, N), d_cnt))) return rc;
+    timer_end(ctx, "localise", ctx->s_main, tb, te);
+    std::vector<uint8_t> any(nfl);
+    CU(cudaMemcpyAsync(&cnt, d_cnt, 8, cudaMemcpyDeviceToHost, ctx->s_main));
+    CU(cudaMemcpyAsync(any.data(), d_any, nfl, cudaMemcpyDeviceToHost, ctx->s_main));
+    if ((rc = check_status(ctx))) return rc;
+    for (uint32_t k = 0; k < nfl; ++k)
+      if (any[k]) accept[fl[k]] = 0;
+    const uint64_t got = std::min(cnt, cap);
+    if (got && invalid_pairs) {
+      std::vector<uint64_t> g(got);
+      CU(cudaMemcpy(g.data(), d_idx, 8 * got, cudaMemcpyDeviceToHost));
+      // global positions ascend, and so do devices: walk the device table once
+      uint32_t d = 0;
+      for (uint64_t q = 0; q < got; ++q) {
+        while (mb->dev_start[d + 1] <= g[q]) ++d;
+        invalid_pairs[2 * q] = d;
+        invalid_pairs[2 * q + 1] = mb->first_index[d] + (g[q] - mb->dev_start[d]);
       }
     }
   }

@@ -93,3 +93,29 @@ def test_multi_device_inputs_and_empty_device(ctx):
                                 dev(np.frombuffer(R, np.uint8)))
     want_acc, want_pairs = O.verify_multi(devs)
     assert list(acc) == want_acc and [tuple(int(x) for x in p) for p in pairs] == want_pairs
+
+
+def test_multi_malformed_entries_and_capacity(ctx):
+    """A non-canonical s_t and an undecodable R_t inside one device are listed like tampered
+    entries; a list longer than the caller's room is EBUFSMALL."""
+    devs, parts = _devices(6, 4, 3, 10, 1)
+    Y, msgs, first, n2, s, R, ds = parts[1]
+    s, R = list(s), list(R)
+    s[0] = (int.from_bytes(s[0], "little") + O.Q).to_bytes(32, "little")
+    y = 2
+    while O.decode_point(y.to_bytes(32, "little")) is not None:
+        y += 1
+    R[2] = y.to_bytes(32, "little")
+    parts[1] = (Y, msgs, first, n2, s, R, ds)
+    d = devs[1]
+    devs[1] = (d[0], d[1], d[2], d[3], s, R, d[6])
+    cat, sb, Rb = _concat(parts)
+    args = ([p[0] for p in parts], [p[1].n for p in parts], [p[2] for p in parts], [p[3] for p in parts],
+            [p[6] for p in parts], cat.data, cat.offs, sb, Rb)
+    acc, pairs = ctx.aver_multi(*args)
+    want_acc, want_pairs = O.verify_multi(devs)
+    assert list(acc) == want_acc and [tuple(int(x) for x in p) for p in pairs] == want_pairs
+    assert (1, first) in want_pairs and (1, first + 2) in want_pairs
+    with pytest.raises(poslo.PosloError) as e:
+        ctx.aver_multi(*args, cap=len(want_pairs) - 1)
+    assert e.value.code == -5
