@@ -32,6 +32,7 @@ struct poslo_ctx {
   uint8_t vseed[32] = {0};
   cudaStream_t s_main = nullptr, s_table = nullptr, s_points = nullptr;
   cudaEvent_t ev_table = nullptr, ev_points = nullptr, ev_main = nullptr, ev_hash = nullptr, ev_prep = nullptr;
+  cudaEvent_t ev_staged = nullptr;   // main stream, right after a batch's R_t have been staged
   std::map<std::string, poslo_host::DevBuf> bufs;
   uint32_t* tableG = nullptr;     // fixed-window table of G (64 KiB)
   uint32_t* status = nullptr;     // device status word

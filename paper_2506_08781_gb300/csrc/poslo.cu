@@ -238,10 +238,17 @@ int validate_batch(poslo_ctx* ctx, const poslo_batch* b) {
   return POSLO_OK;
 }
 
+// Host inputs are copied R_t first: ev_staged marks their arrival, so the decoding (the
+// longest stage) starts while the messages are still on their way.
 int stage_batch(poslo_ctx* ctx, const poslo_batch* b, Staged& sb) {
   int rc;
   const bool dev = b->on_device != 0;
   const void* p;
+  const size_t s_bytes = b->variant == POSLO_VARIANT_F ? 32 * b->n : 32;
+  const size_t R_bytes = 32 * (b->variant == POSLO_VARIANT_F ? b->n : b->R_count);
+  if ((rc = stage(ctx, "R_in", b->R, R_bytes, dev, ctx->s_main, &p))) return rc;
+  sb.R = static_cast<const uint8_t*>(p);
+  CU(cudaEventRecord(ctx->ev_staged, ctx->s_main));
   if (b->n == 0) {
     uint64_t* z;
     if ((rc = ensure_t(ctx, "offs", 16, &z))) return rc;
@@ -263,12 +270,8 @@ int stage_batch(poslo_ctx* ctx, const poslo_batch* b, Staged& sb) {
       sb.base_off = lo;
     }
   }
-  const size_t s_bytes = b->variant == POSLO_VARIANT_F ? 32 * b->n : 32;
-  const size_t R_bytes = 32 * (b->variant == POSLO_VARIANT_F ? b->n : b->R_count);
   if ((rc = stage(ctx, "s_in", b->s, s_bytes, dev, ctx->s_main, &p))) return rc;
   sb.s = static_cast<const uint8_t*>(p);
-  if ((rc = stage(ctx, "R_in", b->R, R_bytes, dev, ctx->s_main, &p))) return rc;
-  sb.R = static_cast<const uint8_t*>(p);
   return POSLO_OK;
 }
 
@@ -348,14 +351,19 @@ int run_ytable(poslo_ctx* ctx, const uint8_t* Y, uint32_t** table_out) {
 #define POSLO_POINTS_BLOCKS 3
 #endif
 
+// The decoding waits for `after` (an event on the main stream) when given, else for all main
+// stream work so far.
 int run_points(poslo_ctx* ctx, const uint8_t* R, uint64_t count, uint32_t* pts_out, uint8_t* bad_out,
-               uint32_t** partial_out, uint32_t* nblocks_out) {
+               uint32_t** partial_out, uint32_t* nblocks_out, cudaEvent_t after = nullptr) {
   int rc;
   const int blocks = grid_for(ctx, count, kPointThreads, POSLO_POINTS_BLOCKS);
   uint32_t* partial;
   if ((rc = ensure_t(ctx, "point_partial", (size_t)blocks * kPointPartialWords * 4, &partial))) return rc;
-  CU(cudaEventRecord(ctx->ev_main, ctx->s_main));
-  CU(cudaStreamWaitEvent(ctx->s_points, ctx->ev_main, 0));
+  if (!after) {
+    CU(cudaEventRecord(ctx->ev_main, ctx->s_main));
+    after = ctx->ev_main;
+  }
+  CU(cudaStreamWaitEvent(ctx->s_points, after, 0));
   PointArgs a{};
   a.R = R;
   a.count = count;
@@ -659,7 +667,8 @@ int poslo_create(const poslo_params* params, poslo_ctx** out) {
       cudaEventCreateWithFlags(&ctx->ev_points, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_main, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_hash, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&ctx->ev_prep, cudaEventDisableTiming) != cudaSuccess)
+      cudaEventCreateWithFlags(&ctx->ev_prep, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_staged, cudaEventDisableTiming) != cudaSuccess)
     return bail(POSLO_EDEVICE);
   if (cudaMalloc(&ctx->status, 4) != cudaSuccess) return bail(POSLO_ENOMEM);
   if (cudaMallocHost(&ctx->h_status, 4) != cudaSuccess) return bail(POSLO_ENOMEM);
@@ -694,6 +703,7 @@ void poslo_destroy(poslo_ctx* ctx) {
   if (ctx->ev_main) cudaEventDestroy(ctx->ev_main);
   if (ctx->ev_hash) cudaEventDestroy(ctx->ev_hash);
   if (ctx->ev_prep) cudaEventDestroy(ctx->ev_prep);
+  if (ctx->ev_staged) cudaEventDestroy(ctx->ev_staged);
   if (ctx->s_main) cudaStreamDestroy(ctx->s_main);
   if (ctx->s_table) cudaStreamDestroy(ctx->s_table);
   if (ctx->s_points) cudaStreamDestroy(ctx->s_points);
@@ -1014,7 +1024,7 @@ int poslo_aver(poslo_ctx* ctx, const poslo_batch* batch, uint32_t agg_mode, uint
   if ((rc = ensure_t(ctx, "aver_small", 4 * 100, &small))) return rc;
   uint32_t *unitR = small, *Rw = small + 32, *prep = small + 64, *pbad = small + 97;
   uint32_t *ppart, npb;
-  if ((rc = run_points(ctx, sb.R, npts, pts, badR, &ppart, &npb))) return rc;
+  if ((rc = run_points(ctx, sb.R, npts, pts, badR, &ppart, &npb, ctx->ev_staged))) return rc;
   if ((rc = run_unit_sum(ctx, ppart, npb, unitR, nullptr, pbad))) return rc;
   uint32_t* z = nullptr;
   if (weighted && (rc = ensure_t(ctx, "z", 16 * std::max<uint64_t>(batch->n, 1), &z))) return rc;
@@ -1070,7 +1080,7 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
   uint8_t* d_ccd;
   if ((rc = ensure_t(ctx, "ccd", 64, &d_ccd))) return rc;
   uint32_t *ppart, npb;
-  if ((rc = run_points(ctx, sb.R, n, pts, badR, &ppart, &npb))) return rc;
+  if ((rc = run_points(ctx, sb.R, n, pts, badR, &ppart, &npb, ctx->ev_staged))) return rc;
   // speculative ccd^v for the all-valid case: R part on the points stream
   if ((rc = run_unit_sum(ctx, ppart, npb, unitR, d_ccd + 32, pbad))) return rc;
   unsigned long long* hpart;
