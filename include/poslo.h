@@ -205,7 +205,10 @@ typedef struct {
 
 int poslo_serve_start(poslo_ctx* ctx, uint32_t workers, uint32_t max_batch_devices, uint64_t max_batch_entries);
 int poslo_serve_stop(poslo_ctx* ctx);
-/* Keys are kept by the service for its lifetime; key ids count from 0. */
+/* Keys are kept by the service for its lifetime; key ids count from 0.  Registration decodes
+ * Y once and keeps its fixed-window table resident on the device (64 KiB per key, outside
+ * mem_budget), so batches of registered keys neither decode nor tabulate them again.
+ * POSLO_EINVAL if Y does not decode (no id is assigned). */
 int poslo_register_key(poslo_ctx* ctx, const uint8_t Y[32], uint32_t* key_id);
 /* POSLO_EBUSY: over the memory budget (nothing queued); POSLO_ENOTFOUND: unknown key id. */
 int poslo_submit(poslo_ctx* ctx, const poslo_request* req, uint64_t* ticket);

@@ -7,7 +7,7 @@
 //   k_hash          A2-A4  x_t = PRF_0(x_0[i] || j), e_t = H(m_t || x_t) mod q, and the
 //                       scalar aggregates sum e_t, sum s_t (or their weighted forms)
 //   k_points        A5  strict decoding of R_t and the unit aggregate sum R_t
-//   k_table         fixed-window tables {d 16^w P : d = 1..8, w = 0..63} for the check
+//   k_table_*       fixed-window tables {d 16^w P : d = 1..8, w = 0..63} for the check
 //   k_finalize      A4/A6  reduce the partial aggregates and evaluate [8](R - eY - sG) = O
 #pragma once
 #include <cstdint>
@@ -27,7 +27,6 @@ constexpr int kPointThreads = 128;
 constexpr int kTableWindows = 64;   // 4-bit windows over 256 bits
 constexpr int kTableDigits = 8;     // signed digits |d| in 1..8
 constexpr int kTableWords = kTableWindows * kTableDigits * 32;   // one table: 64 KB
-constexpr int kTableThreads = 4 * kTableWindows;                 // one quad per window
 
 // Device-side error codes written to the context's status word.
 enum : uint32_t { kErrNone = 0, kErrSeed = 1, kErrKey = 2, kErrPoint = 4, kErrTimeout = 8, kErrInput = 16 };
@@ -204,7 +203,7 @@ __device__ __forceinline__ ge ge_load(const uint32_t* src) {
 
 
 // ----------------------------------------------------------------------------------------
-// Fixed-window tables: table[w][d-1] = d * 16^w * P for w = 0..63, d = 1..8 (k_table).
+// Fixed-window tables: table[w][d-1] = d * 16^w * P for w = 0..63, d = 1..8 (k_table_*).
 // ----------------------------------------------------------------------------------------
 
 
@@ -527,11 +526,12 @@ __global__ void k_epoch_seeds(const DsNode* __restrict__ ds, int nds, uint64_t e
                               uint32_t* __restrict__ x0_out, uint32_t* __restrict__ status);
 __global__ void __launch_bounds__(kHashThreads, POSLO_HASH_MIN_BLOCKS) k_hash(const HashArgs a);
 __global__ void __launch_bounds__(kPointThreads) k_points(const PointArgs a);
-__global__ void __launch_bounds__(kTableThreads) k_table(const uint32_t* __restrict__ enc,
-                                                         const uint32_t* __restrict__ pts,
-                                                         const uint32_t* __restrict__ list,
-                                                         uint32_t* __restrict__ tables,
-                                                         uint32_t* __restrict__ status, int use_base);
+__global__ void __launch_bounds__(128) k_table_chain(const uint32_t* __restrict__ enc,
+                                                     const uint32_t* __restrict__ pts,
+                                                     const uint32_t* __restrict__ list, uint32_t n,
+                                                     uint32_t* __restrict__ tables, uint32_t* __restrict__ status,
+                                                     int use_base, uint8_t* __restrict__ bad_out);
+__global__ void __launch_bounds__(128) k_table_fill(uint32_t n, uint32_t* __restrict__ tables);
 __global__ void __launch_bounds__(kFinalThreads) k_finalize(const FinalArgs a);
 __global__ void __launch_bounds__(128) k_final_prep(const PrepArgs a);
 __global__ void k_final_check(const uint32_t* prep, const uint32_t* R, const uint32_t* point_bad,
@@ -590,7 +590,9 @@ __global__ void __launch_bounds__(kFinalThreads) k_multi_check(const uint32_t* P
                                                                const uint32_t* Sw, const uint8_t* dev_flag,
                                                                uint32_t n_dev, const uint32_t* tableG,
                                                                uint8_t* accept);
-__global__ void __launch_bounds__(128) k_device_unit_check(const uint32_t* Ypts, SegSums ss, uint32_t n_dev,
+__global__ void __launch_bounds__(kPointThreads) k_table_msm(const uint32_t* const* tabs, const uint32_t* k,
+                                                             const uint8_t* skip, uint32_t n, uint32_t* partial);
+__global__ void __launch_bounds__(128) k_device_unit_check(const uint32_t* const* tabs, SegSums ss, uint32_t n_dev,
                                                            const uint32_t* tableG, uint8_t* dev_flag);
 struct MultiCheckArgs {
   const uint32_t* pts;        // decoded R_t of the whole batch (kPtsWords each)
@@ -602,7 +604,7 @@ struct MultiCheckArgs {
   const uint32_t* fl;         // the flagged devices, nfl of them
   const uint64_t* fstart;     // nfl + 1: prefix sums of their entry counts
   uint32_t nfl;
-  const uint32_t* tables;     // nfl window tables of their keys (kTableWords each)
+  const uint32_t* const* tabs;   // window table of each device's key (kTableWords words each)
   const uint32_t* tableG;
   uint8_t* inv;               // out: 1 = entry invalid (written for the flagged devices' entries)
 };

@@ -3,9 +3,12 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstddef>
 #include <map>
 #include <string>
 #include <vector>
+
+#include "../../include/poslo.h"
 
 namespace poslo_host {
 
@@ -49,3 +52,15 @@ struct poslo_ctx {
 
 // Stops and frees the context's service, if one runs (serve.cu).
 void poslo_server_release(poslo_ctx* ctx);
+
+namespace poslo_host {
+// poslo_aver_multi with the devices' window tables given (device pointers, one per device,
+// host array); with key_tables = nullptr the tables are built from the keys (poslo.cu).
+int aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, const uint32_t* const* key_tables, uint8_t* accept,
+               uint64_t* invalid_pairs, uint64_t cap, uint64_t* n_invalid);
+// Decodes Y and writes its window table (kTableWords words) to table_dev; EINVAL if Y does
+// not decode.  Synchronous.
+int build_key_table(poslo_ctx* ctx, const uint8_t Y[32], uint32_t* table_dev);
+// 32-bit words of one window table.
+size_t key_table_words();
+}  // namespace poslo_host

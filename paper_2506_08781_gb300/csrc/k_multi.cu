@@ -177,33 +177,54 @@ __global__ void __launch_bounds__(kFinalThreads) k_multi_check(const uint32_t* P
   }
 }
 
-// Per-device unit check [8](Ru - Eu Y_d - Su G) = O, one quad of lanes per device
-// (quad-cooperative double-and-add for Eu Y_d, the window table of G for Su G).  Devices
-// that fail, or hold malformed entries, are flagged.
-__global__ void __launch_bounds__(128) k_device_unit_check(const uint32_t* Ypts, SegSums ss, uint32_t n_dev,
+// Per-device unit check [8](Ru - Eu Y_d - Su G) = O, one quad of lanes per device: 64 + 64
+// quad-cooperative additions of entries of the window tables of Y_d and of G.  Devices that
+// fail, or hold malformed entries, are flagged.
+__global__ void __launch_bounds__(128) k_device_unit_check(const uint32_t* const* tabs, SegSums ss, uint32_t n_dev,
                                                            const uint32_t* tableG, uint8_t* dev_flag) {
   const uint32_t quad = ((uint32_t)blockIdx.x * blockDim.x + threadIdx.x) >> 2;
   const uint32_t d = quad < n_dev ? quad : n_dev - 1;   // surplus quads repeat the last device
-  ge Y;
-  fe t2d;
-  pts_load(Ypts + (size_t)kPtsWords * d, Y.X, Y.Y, t2d);
-  Y.Z = fe_one();
-  Y.T = fe_mul(Y.X, Y.Y);
+  const uint32_t* tY = tabs[d];
   const uint32_t* eu = ss.Eu + 8 * (size_t)d;
   const uint32_t* su = ss.Su + 8 * (size_t)d;
-  // every lane runs every quad operation (full-mask shuffles): additions are selected, not
-  // branched around
+  // every lane runs every quad operation (full-mask shuffles)
   ge acc = ge_identity();
-  for (int i = 252; i >= 0; --i) {
-    acc = ge_dbl_quad(acc);
-    const ge sum = ge_add_quad(acc, Y);
-    acc = ge_select(acc, sum, ((eu[i >> 5] >> (i & 31)) & 1u) != 0);
+  int ce = 0, cs = 0;
+  for (int w = 0; w < 64; ++w) {
+    acc = ge_add_quad(acc, table_pick(tY, w, sc_digit4(eu, w, ce)));
+    acc = ge_add_quad(acc, table_pick(tableG, w, sc_digit4(su, w, cs)));
   }
-  int carry = 0;
-  for (int w = 0; w < 64; ++w) acc = ge_add_quad(acc, table_pick(tableG, w, sc_digit4(su, w, carry)));
   const ge diff = ge_sub(ge_load(ss.Ru + 32 * (size_t)d), acc);
   const bool ok = ge_is_identity(ge_mul_cofactor(diff)) && ss.bad[d] == 0;
   if ((threadIdx.x & 3) == 0 && quad < n_dev) dev_flag[d] = ok ? 0 : 1;
+}
+
+// sum_d [k_d] Y_d over the keys not skipped, from their window tables: one (key, window)
+// pair per step, 64 table entries per key, no doublings.  Per block: the partial sum in the
+// decode kernel's partial format (kPointPartialWords, bad count 0).
+__global__ void __launch_bounds__(kPointThreads) k_table_msm(const uint32_t* const* tabs, const uint32_t* k,
+                                                             const uint8_t* skip, uint32_t n, uint32_t* partial) {
+  ge acc = ge_identity();
+  const uint64_t total = (uint64_t)n * kTableWindows;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total; p += stride) {
+    const uint32_t d = (uint32_t)(p / kTableWindows);
+    const int w = (int)(p % kTableWindows);
+    if (skip && skip[d]) continue;
+    const uint32_t* kd = k + 8 * (size_t)d;
+    int carry = 0, digit = 0;
+    for (int i = 0; i <= w; ++i) digit = sc_digit4(kd, i, carry);
+    if (digit) acc = ge_add(acc, table_pick(tabs[d], w, digit));
+  }
+  __shared__ uint32_t sp[kPointThreads][32];
+  ge_store(sp[threadIdx.x], acc);
+  __syncthreads();
+  for (int h = kPointThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) ge_store(sp[threadIdx.x], ge_add(ge_load(sp[threadIdx.x]), ge_load(sp[threadIdx.x + h])));
+    __syncthreads();
+  }
+  if (threadIdx.x < 32) partial[(uint64_t)blockIdx.x * kPointPartialWords + threadIdx.x] = sp[0][threadIdx.x];
+  if (threadIdx.x == 0) partial[(uint64_t)blockIdx.x * kPointPartialWords + 32] = 0;
 }
 
 // Entry flags from device flags (entries of flagged devices are left out) or'ed with the
@@ -218,7 +239,7 @@ __global__ void k_device_to_entries(const uint8_t* dev_flag, const uint64_t* sta
 // Single-entry checks [8](R_t - e_t Y_d - s_t G) = O (Fig. 4 with |m| = 1) for every entry of
 // the flagged devices, plus s_t canonical and R_t decodable.  Thread t belongs to flagged
 // device k = the last k with fstart[k] <= t (binary search); R_t comes from the decoded point
-// buffer and [e]Y_d from table slot k.
+// buffer and [e]Y_d from the table of device fl[k].
 __global__ void __launch_bounds__(128) k_multi_entry_check(const MultiCheckArgs a) {
   const uint64_t total = a.fstart[a.nfl];
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -241,7 +262,7 @@ __global__ void __launch_bounds__(128) k_multi_entry_check(const MultiCheckArgs 
       pts_load(a.pts + (size_t)kPtsWords * g, R.X, R.Y, t2d);
       R.Z = fe_one();
       R.T = fe_mul(R.X, R.Y);
-      const ge d = ge_sub(R, double_scalar_tables(e, s, a.tables + (size_t)lo * kTableWords, a.tableG));
+      const ge d = ge_sub(R, double_scalar_tables(e, s, a.tabs[a.fl[lo]], a.tableG));
       ok = ge_is_identity(ge_mul_cofactor(d));
     }
     a.inv[g] = ok ? 0 : 1;

@@ -274,51 +274,58 @@ __global__ void __launch_bounds__(kPointThreads) k_points(const PointArgs a) {
   if (threadIdx.x == 0) a.partial[(uint64_t)blockIdx.x * kPointPartialWords + 32] = sbad[0];
 }
 
-// Fixed-window tables, one per block (kTableThreads threads): warp 0 walks the chain P, 16P,
-// ..., 16^63 P with quad-cooperative doublings (its eight quads in lockstep, all on the same
-// point) into shared memory; then quad w of the block forms d 16^w P for d = 2..8 by
-// quad-cooperative additions.  Latency: 252 doublings at a quarter of the dependent
-// multiplications each, plus 7 additions.  The key of block k is the encoding enc + 8 k, the
-// decoded point pts + kPtsWords * list[k] (affine x, y), or G (use_base).
-__global__ void __launch_bounds__(kTableThreads) k_table(const uint32_t* __restrict__ enc,
-                                                         const uint32_t* __restrict__ pts,
-                                                         const uint32_t* __restrict__ list,
-                                                         uint32_t* __restrict__ tables,
-                                                         uint32_t* __restrict__ status, int use_base) {
-  __shared__ uint32_t base[kTableWindows][32];
-  const int k = blockIdx.x;
-  uint32_t* table = tables + (size_t)k * kTableWords;
-  if (threadIdx.x < 32) {
-    ge P;
-    if (use_base) {
-      P = ge_base();
-    } else if (pts) {
-      fe t2d;
-      pts_load(pts + (size_t)kPtsWords * list[k], P.X, P.Y, t2d);
-      P.Z = fe_one();
-      P.T = fe_mul(P.X, P.Y);
-    } else {
-      uint32_t b[8];
+// Fixed-window tables table[w][d-1] = d 16^w P (w = 0..63, d = 1..8) of n keys, in two
+// launches.  k_table_chain: one quad of lanes per key walks P, 16P, ..., 16^63 P with
+// quad-cooperative doublings (252 of them, at a quarter of a doubling's dependent
+// multiplications each) and writes each 16^w P as table[w][0].  k_table_fill: one quad per
+// (key, window) forms d 16^w P for d = 2..8 by quad-cooperative additions.  The key of
+// index k is the encoding enc + 8 k, the decoded point pts + kPtsWords * list[k] (affine
+// x, y; k itself without a list), or G (use_base).  An encoding that does not decode gives
+// the identity's table and sets bad_out[k] (when given) or the kErrKey status bit.
+__global__ void __launch_bounds__(128) k_table_chain(const uint32_t* __restrict__ enc,
+                                                     const uint32_t* __restrict__ pts,
+                                                     const uint32_t* __restrict__ list, uint32_t n,
+                                                     uint32_t* __restrict__ tables, uint32_t* __restrict__ status,
+                                                     int use_base, uint8_t* __restrict__ bad_out) {
+  const uint32_t quad = ((uint32_t)blockIdx.x * blockDim.x + threadIdx.x) >> 2;
+  const uint32_t k = quad < n ? quad : n - 1;   // surplus quads repeat the last key, unwritten
+  const bool writer = quad < n && (threadIdx.x & 3) == 0;
+  ge P;
+  if (use_base) {
+    P = ge_base();
+  } else if (pts) {
+    fe t2d;
+    pts_load(pts + (size_t)kPtsWords * (list ? list[k] : k), P.X, P.Y, t2d);
+    P.Z = fe_one();
+    P.T = fe_mul(P.X, P.Y);
+  } else {
+    uint32_t b[8];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) b[i] = enc[8 * (size_t)k + i];
-      if (!ge_decode(b, P)) {
-        if (threadIdx.x == 0) atomicOr(status, kErrKey);
-        P = ge_identity();
-      }
-    }
-    for (int w = 0; w < kTableWindows; ++w) {
-      if (threadIdx.x == 0) ge_store(base[w], P);
-      if (w + 1 < kTableWindows)
-        for (int i = 0; i < 4; ++i) P = ge_dbl_quad(P);
+    for (int i = 0; i < 8; ++i) b[i] = enc[8 * (size_t)k + i];
+    const bool ok = ge_decode(b, P);
+    if (!ok) P = ge_identity();
+    if (writer) {
+      if (bad_out) bad_out[k] = ok ? 0 : 1;   // the caller reports which key failed
+      else if (!ok) atomicOr(status, kErrKey);
     }
   }
-  __syncthreads();
-  const int w = threadIdx.x >> 2;
-  const bool writer = (threadIdx.x & 3) == 0;
-  const ge Pw = ge_load(base[w]);
+  uint32_t* table = tables + (size_t)k * kTableWords;
+  // every lane runs every quad doubling (full-mask shuffles)
+  for (int w = 0; w < kTableWindows; ++w) {
+    if (writer) ge_store(table + (size_t)w * kTableDigits * 32, P);
+    if (w + 1 < kTableWindows)
+      for (int i = 0; i < 4; ++i) P = ge_dbl_quad(P);
+  }
+}
+
+__global__ void __launch_bounds__(128) k_table_fill(uint32_t n, uint32_t* __restrict__ tables) {
+  const uint64_t total = (uint64_t)n * kTableWindows;
+  const uint64_t quad = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 2;
+  const uint64_t q = quad < total ? quad : total - 1;
+  const bool writer = quad < total && (threadIdx.x & 3) == 0;
+  uint32_t* row = tables + (q / kTableWindows) * kTableWords + (q % kTableWindows) * kTableDigits * 32;
+  const ge Pw = ge_load(row);
   ge acc = Pw;
-  uint32_t* row = table + (size_t)w * kTableDigits * 32;
-  if (writer) ge_store(row, acc);
   for (int d = 2; d <= kTableDigits; ++d) {
     acc = ge_add_quad(acc, Pw);
     if (writer) ge_store(row + (d - 1) * 32, acc);

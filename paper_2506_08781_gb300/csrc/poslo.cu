@@ -325,6 +325,18 @@ int run_hash(poslo_ctx* ctx, const poslo_batch* b, const Staged& sb, uint8_t* e_
 }
 
 // Window table of Y on the side stream (ordered after the main stream's uploads).
+// Window tables of n keys on stream st (k_table_chain, then k_table_fill).
+int launch_tables(poslo_ctx* ctx, cudaStream_t st, const uint32_t* enc, const uint32_t* pts, const uint32_t* list,
+                  uint32_t n, uint32_t* tables, int use_base, uint8_t* bad_out) {
+  if (n == 0) return POSLO_OK;
+  k_table_chain<<<(unsigned)((4ull * n + 127) / 128), 128, 0, st>>>(enc, pts, list, n, tables, ctx->status, use_base,
+                                                                    bad_out);
+  k_table_fill<<<(unsigned)((4ull * n * kTableWindows + 127) / 128), 128, 0, st>>>(n, tables);
+  ctx->launch_count += 2;
+  CU(cudaGetLastError());
+  return POSLO_OK;
+}
+
 int run_ytable(poslo_ctx* ctx, const uint8_t* Y, uint32_t** table_out) {
   int rc;
   uint32_t* d_Y;
@@ -336,9 +348,7 @@ int run_ytable(poslo_ctx* ctx, const uint8_t* Y, uint32_t** table_out) {
   CU(cudaStreamWaitEvent(ctx->s_table, ctx->ev_main, 0));
   cudaEvent_t tb, te;
   timer_begin(ctx, "table", ctx->s_table, &tb, &te);
-  k_table<<<1, kTableThreads, 0, ctx->s_table>>>(d_Y, nullptr, nullptr, tableY, ctx->status, 0);
-  ++ctx->launch_count;
-  CU(cudaGetLastError());
+  if ((rc = launch_tables(ctx, ctx->s_table, d_Y, nullptr, nullptr, 1, tableY, 0, nullptr))) return rc;
   timer_end(ctx, "table", ctx->s_table, tb, te);
   CU(cudaEventRecord(ctx->ev_table, ctx->s_table));
   *table_out = tableY;
@@ -424,6 +434,21 @@ MsmPlan msm_plan_c(int c, int sw) {
   return pl;
 }
 
+// A width is balanced when the last window still holds at least 5 bits of the scalar: with
+// fewer, its few digit values put a large share of all entries into one or two buckets.
+// (127-bit weights: c = 9 and 14 are not; 8-word scalars below 2^253: c = 9, 10, 12, 14.)
+bool msm_width_balanced(int c, int sw) {
+  const int bits = sw == 4 ? 127 : 253;   // 8-word scalars are usually reduced mod q
+  const int windows = (bits + c - 1) / c;
+  return bits - (windows - 1) * c >= 5;
+}
+
+// The balanced width nearest to c from below (c = 8 is balanced for both scalar widths).
+int msm_balanced_width(int c, int sw) {
+  while (c > 8 && !msm_width_balanced(c, sw)) --c;
+  return c;
+}
+
 int log2_floor(uint64_t n) {
   int lg = 0;
   while ((1ull << (lg + 1)) <= std::max<uint64_t>(n, 1)) ++lg;
@@ -435,7 +460,7 @@ MsmPlan msm_plan(poslo_ctx* ctx, uint64_t n, int sw) {
   if (c == 0) {
     const int lg = log2_floor(n);
     auto it = ctx->msm_tuned.find(lg * 16 + sw);
-    c = it != ctx->msm_tuned.end() ? it->second : std::min(16, std::max(8, lg - 4));
+    c = it != ctx->msm_tuned.end() ? it->second : msm_balanced_width(std::min(16, std::max(8, lg - 4)), sw);
   }
   return msm_plan_c(c, sw);
 }
@@ -674,7 +699,7 @@ int poslo_create(const poslo_params* params, poslo_ctx** out) {
   if (cudaMallocHost(&ctx->h_status, 4) != cudaSuccess) return bail(POSLO_ENOMEM);
   if (cudaMalloc(&ctx->tableG, 4 * (size_t)kTableWords) != cudaSuccess) return bail(POSLO_ENOMEM);
   cudaMemsetAsync(ctx->status, 0, 4, ctx->s_main);
-  k_table<<<1, kTableThreads, 0, ctx->s_main>>>(nullptr, nullptr, nullptr, ctx->tableG, ctx->status, 1);
+  if (launch_tables(ctx, ctx->s_main, nullptr, nullptr, nullptr, 1, ctx->tableG, 1, nullptr)) return bail(POSLO_EDEVICE);
   ++ctx->launch_count;
   if (cudaStreamSynchronize(ctx->s_main) != cudaSuccess) return bail(POSLO_EDEVICE);
   *out = ctx;
@@ -1324,6 +1349,7 @@ int poslo_msm_autotune(poslo_ctx* ctx, uint64_t n, uint32_t scalar_words, uint32
   float best_ms = 0.f;
   const int c_lo = std::max(8, std::min(16, lg - 8)), c_hi = std::min(16, std::max(8, lg - 1));
   for (int c = c_lo; c <= c_hi && rc == POSLO_OK; ++c) {
+    if (!msm_width_balanced(c, sw)) continue;
     const MsmPlan forced = msm_plan_c(c, sw);
     float ms = 0.f;
     for (int rep = 0; rep < 2 && rc == POSLO_OK; ++rep) {   // the first run grows the buffers
@@ -1350,6 +1376,31 @@ int poslo_msm_autotune(poslo_ctx* ctx, uint64_t n, uint32_t scalar_words, uint32
 
 int poslo_aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, uint8_t* accept, uint64_t* invalid_pairs,
                      uint64_t cap, uint64_t* n_invalid) {
+  return poslo_host::aver_multi(ctx, mb, nullptr, accept, invalid_pairs, cap, n_invalid);
+}
+
+}  // extern "C"
+
+size_t poslo_host::key_table_words() { return kTableWords; }
+
+int poslo_host::build_key_table(poslo_ctx* ctx, const uint8_t Y[32], uint32_t* table_dev) {
+  int rc;
+  if ((rc = reset_status(ctx))) return rc;
+  uint32_t* d_Y;
+  uint8_t* d_bad;
+  if ((rc = ensure_t(ctx, "reg_Y", 32, &d_Y))) return rc;
+  if ((rc = ensure_t(ctx, "reg_bad", 16, &d_bad))) return rc;
+  CU(cudaMemcpyAsync(d_Y, Y, 32, cudaMemcpyHostToDevice, ctx->s_main));
+  if ((rc = launch_tables(ctx, ctx->s_main, d_Y, nullptr, nullptr, 1, table_dev, 0, d_bad))) return rc;
+  uint8_t bad = 1;
+  CU(cudaMemcpyAsync(&bad, d_bad, 1, cudaMemcpyDeviceToHost, ctx->s_main));
+  if ((rc = check_status(ctx))) return rc;
+  if (bad) return fail(ctx, POSLO_EINVAL, "key does not decode");
+  return POSLO_OK;
+}
+
+int poslo_host::aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, const uint32_t* const* key_tables,
+                           uint8_t* accept, uint64_t* invalid_pairs, uint64_t cap, uint64_t* n_invalid) {
   if (!ctx || !mb || !accept || !n_invalid || mb->n_dev == 0 || !mb->Y || !mb->dev_start || !mb->first_index ||
       !mb->n2 || !mb->ds || !mb->ds_off)
     return fail(ctx, POSLO_EINVAL, "bad aver_multi arguments");
@@ -1405,6 +1456,32 @@ int poslo_aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, uint8_t* accep
   CU(cudaMemcpyAsync(d_dsoff, mb->ds_off, 4 * (size_t)(nd + 1), cudaMemcpyHostToDevice, ctx->s_main));
   CU(cudaMemcpyAsync(d_nodes, nodes.data(), sizeof(DsNode) * nodes.size(), cudaMemcpyHostToDevice, ctx->s_main));
   CU(cudaMemcpyAsync(d_Y, mb->Y, 32 * (size_t)nd, cudaMemcpyHostToDevice, ctx->s_main));
+  // ---- (table stream) window tables of every device key, decoded from its encoding, unless
+  // the caller holds them resident; tabs[d] points at device d's table
+  uint8_t* badY;
+  const uint32_t** d_tabs;
+  if ((rc = ensure_t(ctx, "m_badY", nd, &badY))) return rc;
+  if ((rc = ensure_t(ctx, "m_tabs", 8 * (size_t)nd, &d_tabs))) return rc;
+  std::vector<const uint32_t*> tabs(nd);
+  if (key_tables) {
+    for (uint32_t d = 0; d < nd; ++d) tabs[d] = key_tables[d];
+    CU(cudaMemsetAsync(badY, 0, nd, ctx->s_main));
+    CU(cudaEventRecord(ctx->ev_table, ctx->s_main));
+  } else {
+    uint32_t* tablesY;
+    if ((rc = ensure_t(ctx, "m_tablesY", 4 * (size_t)kTableWords * nd, &tablesY))) return rc;
+    for (uint32_t d = 0; d < nd; ++d) tabs[d] = tablesY + (size_t)d * kTableWords;
+    CU(cudaEventRecord(ctx->ev_main, ctx->s_main));
+    CU(cudaStreamWaitEvent(ctx->s_table, ctx->ev_main, 0));
+    cudaEvent_t tb, te;
+    timer_begin(ctx, "table", ctx->s_table, &tb, &te);
+    if ((rc = launch_tables(ctx, ctx->s_table, reinterpret_cast<const uint32_t*>(d_Y), nullptr, nullptr, nd, tablesY,
+                            0, badY)))
+      return rc;
+    timer_end(ctx, "table", ctx->s_table, tb, te);
+    CU(cudaEventRecord(ctx->ev_table, ctx->s_table));
+  }
+  CU(cudaMemcpyAsync(d_tabs, tabs.data(), 8 * (size_t)nd, cudaMemcpyHostToDevice, ctx->s_main));
   const uint64_t* seg_start = d_meta;
   const uint64_t* seg_first = d_meta + nd + 1;
   const uint64_t* seg_seed_off = d_meta + 2 * nd + 1;
@@ -1417,32 +1494,17 @@ int poslo_aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, uint8_t* accep
         d_nodes, d_dsoff, seg_seed_off, seg_e0, nd, seeds, ctx->status);
     ++ctx->launch_count;
   }
-  // ---- A5 (side stream): decode every R_t and every Y_d
+  // ---- A5 (side stream): decode every R_t
   const uint64_t N1 = std::max<uint64_t>(N, 1);
-  uint32_t *pts, *Ypts, *ppart, npb, *ypart;
-  uint8_t *badR, *badS, *d_e, *badY;
+  uint32_t *pts, *ppart, npb;
+  uint8_t *badR, *badS, *d_e;
   if ((rc = ensure_t(ctx, "pts", 4 * kPtsWords * N1, &pts))) return rc;
   if ((rc = ensure_t(ctx, "badR", N1, &badR))) return rc;
   if ((rc = ensure_t(ctx, "badS", N1, &badS))) return rc;
   if ((rc = ensure_t(ctx, "e_all", 32 * N1, &d_e))) return rc;
-  if ((rc = ensure_t(ctx, "m_Ypts", 4 * kPtsWords * (size_t)nd, &Ypts))) return rc;
-  if ((rc = ensure_t(ctx, "m_badY", nd, &badY))) return rc;
   uint32_t* z;
   if ((rc = ensure_t(ctx, "z", 16 * N1, &z))) return rc;
   if ((rc = run_points(ctx, sb.R, N, pts, badR, &ppart, &npb))) return rc;
-  {
-    const int yb = grid_for(ctx, nd, kPointThreads, 8);
-    if ((rc = ensure_t(ctx, "m_ypart", (size_t)yb * kPointPartialWords * 4, &ypart))) return rc;
-    PointArgs pa{};
-    pa.R = d_Y;
-    pa.count = nd;
-    pa.partial = ypart;
-    pa.pts_out = Ypts;
-    pa.bad_out = badY;
-    k_points<<<yb, kPointThreads, 0, ctx->s_points>>>(pa);
-    ++ctx->launch_count;
-    CU(cudaEventRecord(ctx->ev_points, ctx->s_points));
-  }
   // ---- A2-A4: segmented hashing with per-entry e_t, z_t
   {
     const int blocks = grid_for(ctx, N, kHashThreads, 8);
@@ -1500,7 +1562,14 @@ int poslo_aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, uint8_t* accep
   if ((rc = run_msm_finish(ctx, ctx->s_main, pts, badR, ms, P1))) return rc;
   k_segment_sums<<<nd, 256, 0, ctx->s_main>>>(d_e, sb.s, z, pts, badR, badS, seg_start, ss);
   ++ctx->launch_count;
-  if ((rc = run_msm(ctx, ctx->s_main, Ypts, ss.Ew, 8, nullptr, nd, P2))) return rc;
+  // sum_d E_d Y_d from the key tables
+  CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_table, 0));
+  const int tmb = grid_for(ctx, (uint64_t)nd * kTableWindows, kPointThreads, 4);
+  uint32_t* tmpart;
+  if ((rc = ensure_t(ctx, "m_tmpart", (size_t)tmb * kPointPartialWords * 4, &tmpart))) return rc;
+  k_table_msm<<<tmb, kPointThreads, 0, ctx->s_main>>>(d_tabs, ss.Ew, nullptr, nd, tmpart);
+  k_sum_encode<<<1, kFinalThreads, 0, ctx->s_main>>>(tmpart, tmb, P2, nullptr, nullptr);
+  ctx->launch_count += 2;
   k_multi_check<<<1, kFinalThreads, 0, ctx->s_main>>>(P1, nullptr, P2, ss.Sw, nullptr, nd, ctx->tableG, d_acc);
   ++ctx->launch_count;
   CU(cudaGetLastError());
@@ -1518,14 +1587,16 @@ int poslo_aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, uint8_t* accep
   std::vector<uint8_t> flag(nd, 0);
   if (!(all_ok && total_bad == 0)) {
     // ---- A7 across devices: unit check per device, then confirm the rest together
-    k_device_unit_check<<<(unsigned)((4ull * nd + 127) / 128), 128, 0, ctx->s_main>>>(Ypts, ss, nd, ctx->tableG,
+    k_device_unit_check<<<(unsigned)((4ull * nd + 127) / 128), 128, 0, ctx->s_main>>>(d_tabs, ss, nd, ctx->tableG,
                                                                                      dev_flag);
     // the weighted sum over the devices not flagged = P1 minus the flagged devices' part,
     // an MSM over their entries only
     k_device_to_entries<<<nd, 256, 0, ctx->s_main>>>(dev_flag, seg_start, badR, eskip, 1);
     ctx->launch_count += 2;
     if ((rc = run_msm(ctx, ctx->s_main, pts, z, 4, eskip, N, P3))) return rc;
-    if ((rc = run_msm(ctx, ctx->s_main, Ypts, ss.Ew, 8, dev_flag, nd, P2))) return rc;
+    k_table_msm<<<tmb, kPointThreads, 0, ctx->s_main>>>(d_tabs, ss.Ew, dev_flag, nd, tmpart);
+    k_sum_encode<<<1, kFinalThreads, 0, ctx->s_main>>>(tmpart, tmb, P2, nullptr, nullptr);
+    ctx->launch_count += 2;
     k_multi_check<<<1, kFinalThreads, 0, ctx->s_main>>>(P1, P3, P2, ss.Sw, dev_flag, nd, ctx->tableG, d_acc);
     ++ctx->launch_count;
     uint8_t confirmed = 0;
@@ -1535,7 +1606,7 @@ int poslo_aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, uint8_t* accep
     if (!confirmed) std::fill(flag.begin(), flag.end(), 1);   // cancelling errors: settle every device
   }
   // ---- localise inside the flagged devices: the single-entry check of every entry of every
-  // flagged device in one launch (window tables of their keys built together, one block each)
+  // flagged device in one launch, with the key tables built above
   std::vector<uint32_t> fl;
   std::vector<uint64_t> fst(1, 0);
   for (uint32_t d = 0; d < nd; ++d) {
@@ -1548,13 +1619,12 @@ int poslo_aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, uint8_t* accep
   const uint32_t nfl = (uint32_t)fl.size();
   uint64_t cnt = 0;
   if (nfl) {
-    uint32_t *d_fl, *tables;
+    uint32_t* d_fl;
     uint64_t *d_fst, *d_idx;
     uint8_t *inv, *d_any;
     const uint64_t capn = std::max<uint64_t>(std::min(cap, N), 1);
     if ((rc = ensure_t(ctx, "m_fl", 4 * (size_t)nfl, &d_fl))) return rc;
     if ((rc = ensure_t(ctx, "m_fst", 8 * (size_t)(nfl + 1), &d_fst))) return rc;
-    if ((rc = ensure_t(ctx, "m_tables", 4 * (size_t)kTableWords * nfl, &tables))) return rc;
     if ((rc = ensure_t(ctx, "m_inv", N1, &inv))) return rc;
     if ((rc = ensure_t(ctx, "m_any", nfl, &d_any))) return rc;
     if ((rc = ensure_t(ctx, "m_idx", 8 * capn + 8, &d_idx))) return rc;
@@ -1564,7 +1634,6 @@ int poslo_aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, uint8_t* accep
     CU(cudaMemsetAsync(inv, 0, N1, ctx->s_main));
     cudaEvent_t tb, te;
     timer_begin(ctx, "localise", ctx->s_main, &tb, &te);
-    k_table<<<nfl, kTableThreads, 0, ctx->s_main>>>(nullptr, Ypts, d_fl, tables, ctx->status, 0);
     MultiCheckArgs ca{};
     ca.pts = pts;
     ca.e = d_e;
@@ -1575,12 +1644,12 @@ int poslo_aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, uint8_t* accep
     ca.fl = d_fl;
     ca.fstart = d_fst;
     ca.nfl = nfl;
-    ca.tables = tables;
+    ca.tabs = d_tabs;
     ca.tableG = ctx->tableG;
     ca.inv = inv;
     if (fst[nfl]) k_multi_entry_check<<<grid_for(ctx, fst[nfl], 128, 8), 128, 0, ctx->s_main>>>(ca);
     k_segment_any<<<nfl, 256, 0, ctx->s_main>>>(inv, seg_start, d_fl, d_any);
-    ctx->launch_count += 3;
+    ctx->launch_count += 2;
     CU(cudaGetLastError());
     if ((rc = run_compact(ctx, inv, N, 0, d_idx, std::min(cap, N), d_cnt))) return rc;
     timer_end(ctx, "localise", ctx->s_main, tb, te);
@@ -1608,5 +1677,7 @@ int poslo_aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, uint8_t* accep
                              (unsigned long long)cap);
   return POSLO_OK;
 }
+
+extern "C" {
 
 }  // extern "C"

@@ -49,6 +49,11 @@ struct Server {
   std::deque<Req*> pending;
   std::unordered_map<uint64_t, std::unique_ptr<Req>> reqs;
   std::vector<std::array<uint8_t, 32>> keys;
+  // Resident window tables of the registered keys, kKeysPerBlock keys per device allocation;
+  // blocks never move, so workers read them while new keys are added.
+  static constexpr uint32_t kKeysPerBlock = 256;
+  std::vector<uint32_t*> table_blocks;
+  std::mutex reg_mu;   // serialises key registration (it uses the owner context's stream)
   std::vector<std::thread> workers;
   std::vector<poslo_ctx*> wctx;
   bool stop = false;
@@ -70,9 +75,15 @@ void run_batch(Server* S, poslo_ctx* w, std::vector<Req*>& batch) {
   std::vector<uint8_t> Y(32 * (size_t)nd), msgs, s, R, ds;
   std::vector<uint64_t> start(nd + 1, 0), first(nd), offs;
   std::vector<uint32_t> n2(nd), ds_off(nd + 1, 0);
+  std::vector<const uint32_t*> tabs(nd);
   {
     std::lock_guard<std::mutex> lock(S->mu);
-    for (uint32_t d = 0; d < nd; ++d) memcpy(Y.data() + 32 * (size_t)d, S->keys[batch[d]->key_id].data(), 32);
+    const size_t words = key_table_words();
+    for (uint32_t d = 0; d < nd; ++d) {
+      const uint32_t k = batch[d]->key_id;
+      memcpy(Y.data() + 32 * (size_t)d, S->keys[k].data(), 32);
+      tabs[d] = S->table_blocks[k / Server::kKeysPerBlock] + (size_t)(k % Server::kKeysPerBlock) * words;
+    }
   }
   uint64_t total = 0, mtotal = 0;
   for (uint32_t d = 0; d < nd; ++d) {
@@ -114,7 +125,7 @@ void run_batch(Server* S, poslo_ctx* w, std::vector<Req*>& batch) {
   std::vector<uint8_t> acc(nd);
   std::vector<uint64_t> pairs(2 * std::max<uint64_t>(total, 1));
   uint64_t cnt = 0;
-  int rc = poslo_aver_multi(w, &mb, acc.data(), pairs.data(), total, &cnt);
+  int rc = aver_multi(w, &mb, tabs.data(), acc.data(), pairs.data(), total, &cnt);
   std::vector<int> rcs(nd, rc);
   std::vector<std::vector<uint64_t>> inv(nd);
   if (rc == POSLO_OK) {
@@ -200,6 +211,8 @@ void poslo_server_release(poslo_ctx* ctx) {
   S->cv_work.notify_all();
   for (auto& t : S->workers) t.join();
   for (poslo_ctx* w : S->wctx) poslo_destroy(w);
+  cudaSetDevice(ctx->device);
+  for (uint32_t* b : S->table_blocks) cudaFree(b);
   delete S;
   ctx->server = nullptr;
 }
@@ -244,11 +257,29 @@ int poslo_serve_stop(poslo_ctx* ctx) {
 int poslo_register_key(poslo_ctx* ctx, const uint8_t Y[32], uint32_t* key_id) {
   if (!ctx || !ctx->server || !Y || !key_id) return POSLO_EINVAL;
   Server* S = ctx->server;
-  std::lock_guard<std::mutex> lock(S->mu);
+  std::lock_guard<std::mutex> reg(S->reg_mu);
+  uint32_t id;
+  uint32_t* block = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(S->mu);
+    id = (uint32_t)S->keys.size();
+    if (id / Server::kKeysPerBlock < S->table_blocks.size()) block = S->table_blocks[id / Server::kKeysPerBlock];
+  }
+  const size_t words = poslo_host::key_table_words();
+  if (!block) {
+    cudaSetDevice(ctx->device);
+    if (cudaMalloc(&block, 4 * words * Server::kKeysPerBlock) != cudaSuccess) return POSLO_ENOMEM;
+    std::lock_guard<std::mutex> lock(S->mu);
+    S->table_blocks.push_back(block);
+  }
+  // decode Y once and keep its window table resident (EINVAL if Y does not decode)
+  const int rc = poslo_host::build_key_table(ctx, Y, block + (size_t)(id % Server::kKeysPerBlock) * words);
+  if (rc != POSLO_OK) return rc;
   std::array<uint8_t, 32> k;
   memcpy(k.data(), Y, 32);
+  std::lock_guard<std::mutex> lock(S->mu);
   S->keys.push_back(k);
-  *key_id = (uint32_t)(S->keys.size() - 1);
+  *key_id = id;
   return POSLO_OK;
 }
 

@@ -73,7 +73,15 @@ def test_serving_budget_and_unknown_ids():
     keys, reqs = _requests(8, 1, 3)
     with poslo.Context(device=0, mem_budget=60_000) as ctx:
         ctx.serve_start(workers=1)
+        # a key that does not decode is refused at registration and takes no id
+        y = 2
+        while O.decode_point(y.to_bytes(32, "little")) is not None:
+            y += 1
+        with pytest.raises(poslo.PosloError) as e:
+            ctx.register_key(y.to_bytes(32, "little"))
+        assert e.value.code == -1                      # EINVAL
         kid = [ctx.register_key(Y) for _, _, Y in keys]
+        assert kid == list(range(len(keys)))
         big = dict(reqs[0])
         msgs = synth.messages(99, 200, 100, 100)
         big["msgs"], big["s"], big["R"] = msgs, bytes(32 * 200), bytes(32 * 200)
