@@ -562,7 +562,12 @@ __global__ void __launch_bounds__(128) k_msm_accum(const uint32_t* pts, const ui
                                                    const uint32_t* off, const uint32_t* cnt, uint64_t n, MsmPlan pl,
                                                    const uint8_t* skip, uint32_t* buckets, uint32_t* A, uint32_t* B);
 __global__ void __launch_bounds__(128) k_msm_combine(const uint32_t* off, const uint32_t* cnt, uint64_t n, MsmPlan pl,
-                                                     const uint32_t* A, const uint32_t* B, uint32_t* buckets);
+                                                     const uint32_t* A, const uint32_t* B, uint32_t* buckets,
+                                                     uint32_t* big_list, uint32_t* big_count);
+__global__ void __launch_bounds__(128) k_msm_combine_big(const uint32_t* off, const uint32_t* cnt, uint64_t n,
+                                                         MsmPlan pl, const uint32_t* A, const uint32_t* B,
+                                                         uint32_t* buckets, const uint32_t* big_list,
+                                                         const uint32_t* big_count);
 __global__ void __launch_bounds__(128) k_msm_chunk(const uint32_t* buckets, MsmPlan pl, uint32_t* L, uint32_t* T);
 __global__ void __launch_bounds__(512) k_msm_groups(const uint32_t* L, const uint32_t* T, MsmPlan pl, uint32_t* groups);
 __global__ void __launch_bounds__(32) k_msm_final(const uint32_t* groups, MsmPlan pl, uint32_t* out);

@@ -133,8 +133,34 @@ __global__ void __launch_bounds__(128) k_msm_accum(const uint32_t* pts, const ui
 
 // Buckets that were not written whole by k_msm_accum: the run in the range holding the
 // bucket's first entry (A or B of that range) plus the first runs of the following ranges.
+// Buckets spanning more than kCombineSpan ranges (a narrow window can put thousands of
+// entries into one digit) are listed for k_msm_combine_big instead of summed here.
+constexpr uint64_t kCombineSpan = 8;
+
+struct CombineSpan {
+  uint64_t ts, te;       // first and last range of the bucket
+  bool starts_range;     // the first run is range ts's A (else its B)
+  bool whole;            // strictly inside one range: k_msm_accum wrote it
+};
+
+__device__ __forceinline__ CombineSpan combine_span(const uint32_t* off, const uint32_t* cnt, const MsmPlan& pl,
+                                                    uint64_t b) {
+  const uint32_t w = (uint32_t)(b / pl.nb);
+  const size_t last = (size_t)w * pl.nb + pl.nb - 1;
+  const uint64_t nnz = (uint64_t)off[last] + cnt[last];
+  const uint64_t s = off[b], e = s + cnt[b] - 1;
+  CombineSpan c;
+  c.ts = s / kMsmSeg;
+  c.te = e / kMsmSeg;
+  const uint64_t r_end = min((c.ts + 1) * kMsmSeg, nnz) - 1;   // last position of range ts
+  c.starts_range = s == c.ts * kMsmSeg;
+  c.whole = !c.starts_range && e < r_end;
+  return c;
+}
+
 __global__ void __launch_bounds__(128) k_msm_combine(const uint32_t* off, const uint32_t* cnt, uint64_t n, MsmPlan pl,
-                                                     const uint32_t* A, const uint32_t* B, uint32_t* buckets) {
+                                                     const uint32_t* A, const uint32_t* B, uint32_t* buckets,
+                                                     uint32_t* big_list, uint32_t* big_count) {
   const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= (uint64_t)pl.windows * pl.nb) return;
   const uint32_t w = (uint32_t)(b / pl.nb), d = (uint32_t)(b % pl.nb);
@@ -143,18 +169,50 @@ __global__ void __launch_bounds__(128) k_msm_combine(const uint32_t* off, const 
     ge_store(buckets + 32 * b, ge_identity());
     return;
   }
-  const uint64_t nseg = (n + kMsmSeg - 1) / kMsmSeg;
-  const size_t last = (size_t)w * pl.nb + pl.nb - 1;
-  const uint64_t nnz = (uint64_t)off[last] + cnt[last];
-  const uint64_t s = off[b], e = s + len - 1;
-  const uint64_t ts = s / kMsmSeg, te = e / kMsmSeg;
-  const uint64_t r_end = min((ts + 1) * kMsmSeg, nnz) - 1;   // last position of range ts
-  const bool starts_range = s == ts * kMsmSeg;
-  if (!starts_range && e < r_end) return;                    // strictly inside: written whole
-  const uint64_t g0 = (uint64_t)w * nseg;
-  ge acc = ge_load((starts_range ? A : B) + 32 * (g0 + ts));
-  for (uint64_t t = ts + 1; t <= te; ++t) acc = ge_add(acc, ge_load(A + 32 * (g0 + t)));
+  const CombineSpan c = combine_span(off, cnt, pl, b);
+  if (c.whole) return;
+  if (c.te - c.ts > kCombineSpan) {
+    big_list[atomicAdd(big_count, 1u)] = (uint32_t)b;
+    return;
+  }
+  const uint64_t g0 = (uint64_t)w * ((n + kMsmSeg - 1) / kMsmSeg);
+  ge acc = ge_load((c.starts_range ? A : B) + 32 * (g0 + c.ts));
+  for (uint64_t t = c.ts + 1; t <= c.te; ++t) acc = ge_add(acc, ge_load(A + 32 * (g0 + t)));
   ge_store(buckets + 32 * b, acc);
+}
+
+__device__ __forceinline__ ge ge_shfl_down(const ge& p, int delta) {
+  ge r;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    r.X.v[i] = __shfl_down_sync(0xffffffffu, p.X.v[i], delta);
+    r.Y.v[i] = __shfl_down_sync(0xffffffffu, p.Y.v[i], delta);
+    r.Z.v[i] = __shfl_down_sync(0xffffffffu, p.Z.v[i], delta);
+    r.T.v[i] = __shfl_down_sync(0xffffffffu, p.T.v[i], delta);
+  }
+  return r;
+}
+
+// The listed wide buckets, one warp each: lanes sum the ranges' first runs with stride 32,
+// then a shuffle tree joins the lanes.  The grid is fixed; warps stride over the list.
+__global__ void __launch_bounds__(128) k_msm_combine_big(const uint32_t* off, const uint32_t* cnt, uint64_t n,
+                                                         MsmPlan pl, const uint32_t* A, const uint32_t* B,
+                                                         uint32_t* buckets, const uint32_t* big_list,
+                                                         const uint32_t* big_count) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+  const uint32_t total = *big_count;
+  const uint64_t nseg = (n + kMsmSeg - 1) / kMsmSeg;
+  for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < total; i += nwarps) {
+    const uint64_t b = big_list[i];
+    const uint32_t w = (uint32_t)(b / pl.nb);
+    const CombineSpan c = combine_span(off, cnt, pl, b);
+    const uint64_t g0 = (uint64_t)w * nseg;
+    ge acc = lane == 0 ? ge_load((c.starts_range ? A : B) + 32 * (g0 + c.ts)) : ge_identity();
+    for (uint64_t t = c.ts + 1 + lane; t <= c.te; t += 32) acc = ge_add(acc, ge_load(A + 32 * (g0 + t)));
+    for (int delta = 16; delta > 0; delta >>= 1) acc = ge_add(acc, ge_shfl_down(acc, delta));
+    if (lane == 0) ge_store(buckets + 32 * b, acc);
+  }
 }
 
 // Chunk j of window w holds buckets d = 16j .. 16j+15: L = sum_r r B_{16j+r} by running

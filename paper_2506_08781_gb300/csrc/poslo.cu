@@ -526,9 +526,14 @@ int run_msm_finish(poslo_ctx* ctx, cudaStream_t st, const uint32_t* pts, const u
                                                                buckets, segA, segB);
     ++ctx->launch_count;
   }
+  uint32_t* big;   // count, then the list of buckets spanning many ranges
+  if ((rc = ensure_t(ctx, "msm_big", 4 * (nbw + 1), &big))) return rc;
+  CU(cudaMemsetAsync(big, 0, 4, st));
   k_msm_combine<<<(unsigned)((nbw + 127) / 128), 128, 0, st>>>(ms.off, ms.cnt, std::max<uint64_t>(n, 1), pl, segA,
-                                                              segB, buckets);
-  ++ctx->launch_count;
+                                                              segB, buckets, big + 1, big);
+  k_msm_combine_big<<<2 * ctx->sm_count, 128, 0, st>>>(ms.off, ms.cnt, std::max<uint64_t>(n, 1), pl, segA, segB,
+                                                       buckets, big + 1, big);
+  ctx->launch_count += 2;
   timer_end(ctx, "msm_bucket", st, sb_, se_);
   timer_begin(ctx, "msm_reduce", st, &sb_, &se_);
   const size_t nch = (size_t)pl.windows * pl.nchunks;

@@ -329,6 +329,32 @@ def test_weighted_checks_every_window_width(c):
             assert list(idx) == wi and cs == ws and cR == wR
 
 
+@pytest.mark.parametrize("c", [8, 16])
+def test_msm_concentrated_scalars(c):
+    """Every scalar one of two values: each window's entries fall into at most two buckets
+    that span many 16-entry ranges (the wide-bucket combine).  The definition is evaluated
+    as a sum over the two classes."""
+    import __graft_entry__
+    __graft_entry__.build()
+    n = 1500
+    P = [O.G]
+    for _ in range(n - 1):
+        P.append(O.point_add(P[-1], O.G))
+    a = int.from_bytes(synth.random_bytes(c, "ca", 32).tobytes(), "little") % O.Q
+    b = int.from_bytes(synth.random_bytes(c, "cb", 32).tobytes(), "little") % O.Q
+    ks = [a if i % 3 else b for i in range(n)]
+    Sa, Sb = O.IDENTITY, O.IDENTITY
+    for i in range(n):
+        if i % 3:
+            Sa = O.point_add(Sa, P[i])
+        else:
+            Sb = O.point_add(Sb, P[i])
+    want = O.encode_point(O.point_add(O.scalar_mult(a, Sa), O.scalar_mult(b, Sb)))
+    with poslo.Context(device=0, msm_window=c) as cx:
+        got = cx.msm(b"".join(O.encode_point(p) for p in P), b"".join(k.to_bytes(32, "little") for k in ks))
+    assert got == want
+
+
 def test_msm_rejects_undecodable_point(ctx):
     y = 2
     while O.decode_point(y.to_bytes(32, "little")) is not None:
