@@ -16,6 +16,8 @@ Readings of points the paper leaves open:
   * PRF_b(z) = SHA-256(z || byte b)[:16] for the seed tree; the per-entry seed is
     x_i^j = PRF_0(x_0[i] || j) = SHA-256(x_0[i] || le32(j) || 0x00)[:16], j 0-based;
   * e = SHA-256(m || x) read little-endian, reduced mod q;
+  * POSLO+ (``instantiation("POSLO+")``): PRF = MMO-AES-128 with kappa = 127, H = MDC-2
+    over AES-128, with the initial values and padding stated beside ``mmo``;
   * POSLO-C nonces r_i^j = SHA-256(r || le32(i) || le32(j) || 0x00) mod q;
   * points are 32-byte compressed edwards25519 encodings, decoded strictly; scalars are
     32-byte little-endian and must be canonical (< q);
@@ -172,19 +174,210 @@ def sha256(data: bytes) -> bytes:
     return hashlib.sha256(data).digest()
 
 
-def prf(bit: int, z: bytes) -> bytes:
+def prf_sha(bit: int, z: bytes) -> bytes:
     """PRF_bit(z) = F(z || bit) with F = SHA-256 truncated to kappa = 128 bits."""
     return sha256(z + bytes([bit]))[:16]
 
 
-def entry_seed(x0: bytes, j: int) -> bytes:
+def entry_seed_sha(x0: bytes, j: int) -> bytes:
     """x_i^j = PRF_0(x_0[i] || j) (Fig. 3a AVer, Fig. 6 Agg-eKeys)."""
     return sha256(x0 + struct.pack("<I", j) + b"\x00")[:16]
 
 
-def hash_to_scalar(m: bytes, x: bytes) -> int:
+def hash_to_scalar_sha(m: bytes, x: bytes) -> int:
     """e = H(m || x) mod q."""
     return int.from_bytes(sha256(m + x), "little") % Q
+
+
+# ----------------------------------------------------------------------------------
+# AES-128 (FIPS-197), the block cipher E of the POSLO+ instantiation (Sec. 7.2)
+# ----------------------------------------------------------------------------------
+
+def gf_mul(a: int, b: int) -> int:
+    """Product in GF(2^8) modulo x^8 + x^4 + x^3 + x + 1 (FIPS-197 Sec. 4.2)."""
+    r = 0
+    for _ in range(8):
+        if b & 1:
+            r ^= a
+        b >>= 1
+        a <<= 1
+        if a & 0x100:
+            a ^= 0x11B
+    return r
+
+
+def _sbox_entry(x: int) -> int:
+    """SubBytes (FIPS-197 Sec. 5.1.1): the multiplicative inverse in GF(2^8) ({00} maps
+    to {00}), then the affine map b_i ^ b_{i+4} ^ b_{i+5} ^ b_{i+6} ^ b_{i+7} ^ c_i with
+    c = {63}."""
+    inv = 0
+    if x:
+        inv = 1
+        for _ in range(254):          # x^254 = x^-1 in a field of 256 elements
+            inv = gf_mul(inv, x)
+    out = 0
+    for i in range(8):
+        bit = 0
+        for k in (0, 4, 5, 6, 7):
+            bit ^= (inv >> ((i + k) % 8)) & 1
+        out |= (bit ^ ((0x63 >> i) & 1)) << i
+    return out
+
+
+SBOX = [_sbox_entry(x) for x in range(256)]
+
+
+def aes128_key_expansion(key: bytes) -> list:
+    """KeyExpansion (FIPS-197 Sec. 5.2): 44 words w[i], each a list of 4 bytes."""
+    w = [list(key[4 * i:4 * i + 4]) for i in range(4)]
+    rcon = 1
+    for i in range(4, 44):
+        t = list(w[i - 1])
+        if i % 4 == 0:
+            t = t[1:] + t[:1]                     # RotWord
+            t = [SBOX[b] for b in t]              # SubWord
+            t[0] ^= rcon
+            rcon = gf_mul(rcon, 2)
+        w.append([a ^ b for a, b in zip(w[i - 4], t)])
+    return w
+
+
+def aes128_encrypt(key: bytes, block: bytes) -> bytes:
+    """Cipher (FIPS-197 Sec. 5.1): the state is 4x4 bytes, state[r][c] = in[r + 4c]."""
+    w = aes128_key_expansion(key)
+    st = [[block[r + 4 * c] for c in range(4)] for r in range(4)]
+
+    def add_round_key(rnd):
+        for c in range(4):
+            for r in range(4):
+                st[r][c] ^= w[4 * rnd + c][r]
+
+    add_round_key(0)
+    for rnd in range(1, 11):
+        for r in range(4):                        # SubBytes
+            for c in range(4):
+                st[r][c] = SBOX[st[r][c]]
+        for r in range(1, 4):                     # ShiftRows: row r rotates left by r
+            st[r] = st[r][r:] + st[r][:r]
+        if rnd < 10:                              # MixColumns
+            for c in range(4):
+                a = [st[r][c] for r in range(4)]
+                st[0][c] = gf_mul(a[0], 2) ^ gf_mul(a[1], 3) ^ a[2] ^ a[3]
+                st[1][c] = a[0] ^ gf_mul(a[1], 2) ^ gf_mul(a[2], 3) ^ a[3]
+                st[2][c] = a[0] ^ a[1] ^ gf_mul(a[2], 2) ^ gf_mul(a[3], 3)
+                st[3][c] = gf_mul(a[0], 3) ^ a[1] ^ a[2] ^ gf_mul(a[3], 2)
+        add_round_key(rnd)
+    return bytes(st[r][c] for c in range(4) for r in range(4))
+
+
+def _xor(a: bytes, b: bytes) -> bytes:
+    return bytes(x ^ y for x, y in zip(a, b))
+
+
+# ----------------------------------------------------------------------------------
+# MMO and MDC-2 over AES-128 (Def. MMO, Def. MDC-2; Sec. 7.2 instantiation "POSLO+")
+# ----------------------------------------------------------------------------------
+# Readings: the initial values are 16 bytes of 0x52 (MMO and the first MDC-2 chain) and 16
+# bytes of 0x25 (the second MDC-2 chain), the DES-era MDC-2 values widened to the AES block;
+# padding is a 1 bit then 0 bits up to a whole number of blocks, t = ceil((k+1)/128) blocks
+# for MDC-2 (an input of whole blocks gains a padding block); MMO pads only an input that
+# is not a whole number of blocks, so the kappa = 127 PRF input (127 + 1 bits) is one block
+# and one AES call, as Sec. 7.2 states.
+
+IV_A = b"\x52" * 16
+IV_B = b"\x25" * 16
+
+
+def _pad_blocks(data: bytes, always: bool) -> list:
+    if always or len(data) % 16:
+        data = data + b"\x80" + bytes((-len(data) - 1) % 16)
+    return [data[i:i + 16] for i in range(0, len(data), 16)]
+
+
+def mmo(data: bytes) -> bytes:
+    """MMO: h_i = E_{h_{i-1}}(m_i) xor m_i, h_0 = IV_A; the digest is h_t (16 bytes)."""
+    h = IV_A
+    for m in _pad_blocks(data, always=False):
+        h = _xor(aes128_encrypt(h, m), m)
+    return h
+
+
+def mdc2(data: bytes) -> bytes:
+    """MDC-2: two MMO chains from IV_A and IV_B over the same blocks; after each block the
+    chains exchange their right halves (bytes 8..15).  The digest is h_t || h'_t (32 bytes)."""
+    h, h2 = IV_A, IV_B
+    for m in _pad_blocks(data, always=True):
+        a = _xor(aes128_encrypt(h, m), m)
+        b = _xor(aes128_encrypt(h2, m), m)
+        h, h2 = a[:8] + b[8:], b[:8] + a[8:]
+    return h + h2
+
+
+def _k127(x: bytes, bit: int) -> bytes:
+    """A 16-byte seed whose least significant bit (bit 0 of byte 15) carries the PRF bit:
+    the kappa = 127 seed x (its first 127 bits) followed by j (Sec. 7.2)."""
+    return x[:15] + bytes([(x[15] & 0xFE) | bit])
+
+
+def prf_aes(bit: int, z: bytes) -> bytes:
+    """PRF_bit(z) = MMO-AES-128(z || bit) with kappa = 127: one block, one AES call; the
+    output is truncated to 127 bits (bit 0 of byte 15 cleared)."""
+    return _k127(mmo(_k127(z, bit)), 0)
+
+
+def entry_seed_aes(x0: bytes, j: int) -> bytes:
+    """x_i^j = PRF_0(x_0[i] || j): MMO over the 127-bit seed, the PRF bit 0 and le32(j)
+    (20 bytes, padded to two blocks), truncated to 127 bits."""
+    return _k127(mmo(_k127(x0, 0) + struct.pack("<I", j)), 0)
+
+
+def hash_to_scalar_aes(m: bytes, x: bytes) -> int:
+    """e = H(m || x) mod q with H = MDC-2-AES-128 (32-byte digest read little-endian)."""
+    return int.from_bytes(mdc2(m + x), "little") % Q
+
+
+# ----------------------------------------------------------------------------------
+# Instantiation in force (Table "instantiations", Sec. 7.2): POSLO = SHA-256 for PRF and H,
+# POSLO+ = MMO-AES-128 for PRF and MDC-2-AES-128 for H.  The POSLO-C nonces stay SHA-256
+# (a signer-side derivation the verifier never recomputes).
+# ----------------------------------------------------------------------------------
+
+INSTANTIATIONS = {
+    "POSLO": (prf_sha, entry_seed_sha, hash_to_scalar_sha),
+    "POSLO+": (prf_aes, entry_seed_aes, hash_to_scalar_aes),
+}
+_current = ["POSLO"]
+
+
+def prf(bit: int, z: bytes) -> bytes:
+    return INSTANTIATIONS[_current[0]][0](bit, z)
+
+
+def entry_seed(x0: bytes, j: int) -> bytes:
+    return INSTANTIATIONS[_current[0]][1](x0, j)
+
+
+def hash_to_scalar(m: bytes, x: bytes) -> int:
+    return INSTANTIATIONS[_current[0]][2](m, x)
+
+
+class instantiation:
+    """``with instantiation("POSLO+"): ...`` evaluates every definition below with the
+    AES-based PRF and H."""
+
+    def __init__(self, name: str):
+        if name not in INSTANTIATIONS:
+            raise ValueError(name)
+        self.name = name
+
+    def __enter__(self):
+        self.prev = _current[0]
+        _current[0] = self.name
+        return self
+
+    def __exit__(self, *exc):
+        _current[0] = self.prev
+        return False
 
 
 def nonce_c(r: bytes, i: int, j: int) -> int:

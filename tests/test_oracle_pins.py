@@ -367,3 +367,119 @@ def test_cofactor_matters_for_torsion():
     assert O.verify_entry_f(Yp, e, s[0], R2[0])
     diff = O.point_sub(O.point_sub(Rt, O.scalar_mult(e, Yp)), O.scalar_mult(int.from_bytes(s[0], "little"), O.G))
     assert not O.is_identity(diff)
+
+
+# ------------------------------------------------------------------------------ POSLO+ (AES)
+
+def test_aes128_fips197_values():
+    """AES-128 against the worked values of FIPS-197 (cipher, key expansion, S-box)."""
+    seen = set()
+    for kind, key, inp, out in golden_lines("aes128_fips197.txt"):
+        seen.add(kind)
+        if kind == "cipher":
+            assert O.aes128_encrypt(bytes.fromhex(key), bytes.fromhex(inp)).hex() == out
+        elif kind == "lastkey":
+            assert bytes(O.aes128_key_expansion(bytes.fromhex(key))[43]).hex() == out
+        elif kind == "sbox":
+            assert O.SBOX[int(inp, 16)] == int(out, 16)
+    assert seen == {"cipher", "lastkey", "sbox"}
+
+
+def test_aes_sbox_is_a_permutation_with_no_fixed_point():
+    # SubBytes is a bijection with no fixed point and no "opposite" fixed point (S(a) != a,
+    # S(a) != ~a), the design properties stated for it in the AES proposal.
+    assert sorted(O.SBOX) == list(range(256))
+    assert all(O.SBOX[a] != a and O.SBOX[a] != a ^ 0xFF for a in range(256))
+
+
+def test_aes128_matches_library_on_random_blocks():
+    crypto = pytest.importorskip("cryptography.hazmat.primitives.ciphers")
+    for i in range(40):
+        key = synth.random_bytes(100 + i, "aeskey", 16).tobytes()
+        blk = synth.random_bytes(100 + i, "aesblk", 16).tobytes()
+        enc = crypto.Cipher(crypto.algorithms.AES(key), crypto.modes.ECB()).encryptor()
+        assert enc.update(blk) + enc.finalize() == O.aes128_encrypt(key, blk)
+
+
+def test_mmo_mdc2_structure_with_library_cipher():
+    """MMO and MDC-2 (Def. MMO, Def. MDC-2) recomputed block by block with the library's
+    AES: chaining through the key, the xor of the block, the swap of right halves, the
+    padding rule.  Pins the composition's AES steps; the composition itself (initial values,
+    padding) is the reading stated in the oracle."""
+    crypto = pytest.importorskip("cryptography.hazmat.primitives.ciphers")
+
+    def E(k, b):
+        e = crypto.Cipher(crypto.algorithms.AES(k), crypto.modes.ECB()).encryptor()
+        return e.update(b) + e.finalize()
+
+    x = lambda a, b: bytes(p ^ q for p, q in zip(a, b))
+    for L in (0, 1, 15, 16, 17, 31, 32, 33, 100):
+        m = synth.random_bytes(L, "mdc", L).tobytes()
+        padded = m + b"\x80" + bytes((-L - 1) % 16)
+        h, h2 = b"\x52" * 16, b"\x25" * 16
+        for i in range(0, len(padded), 16):
+            blk = padded[i:i + 16]
+            a, b = x(E(h, blk), blk), x(E(h2, blk), blk)
+            h, h2 = a[:8] + b[8:], b[:8] + a[8:]
+        assert O.mdc2(m) == h + h2
+        assert len(padded) // 16 == (8 * L + 1 + 127) // 128     # t = ceil((k+1)/128)
+    blk = synth.random_bytes(7, "mmo", 16).tobytes()
+    assert O.mmo(blk) == x(E(b"\x52" * 16, blk), blk)             # one block, no padding
+    two = synth.random_bytes(8, "mmo", 20).tobytes()
+    p = two + b"\x80" + bytes(11)
+    h1 = x(E(b"\x52" * 16, p[:16]), p[:16])
+    assert O.mmo(two) == x(E(h1, p[16:]), p[16:])
+
+
+def test_poslo_plus_prf_is_one_aes_block_with_kappa_127():
+    # Sec. 7.2: with kappa = 127 the PRF input x || j is exactly one AES block; outputs keep
+    # 127 bits; the two children of a node differ
+    z = synth.random_bytes(9, "node", 16).tobytes()
+    c0, c1 = O.prf_aes(0, z), O.prf_aes(1, z)
+    assert c0 != c1 and c0[15] & 1 == 0 and c1[15] & 1 == 0
+    assert O.prf_aes(0, z) == O.prf_aes(0, z[:15] + bytes([z[15] ^ 1]))   # bit 0 is not seed
+    with O.instantiation("POSLO+"):
+        assert O.prf(1, z) == c1
+    assert O.prf(1, z) == O.prf_sha(1, z)                         # default restored
+
+
+@pytest.mark.parametrize("variant", ["F", "C"])
+def test_poslo_plus_signatures_verify_and_tamper_rejects(variant):
+    """Under POSLO+ honest batches verify, the extraction identity r = s + e y holds, and a
+    flipped byte is rejected and localised (the same checks as for POSLO)."""
+    with O.instantiation("POSLO+"):
+        D, n2, n = 2, 4, 12
+        km = synth.key_material(40)
+        msgs = synth.messages(40, n, 0, 70)
+        if variant == "F":
+            sk, Y = O.kg_f(km.y, km.root, D, n2, km.bpv_r.tobytes())
+            subsets = synth.bpv_subsets(40, n, v=32, k=4)
+            sig = [O.sig_f(sk, t, msgs.entry(t), subsets[t]) for t in range(n)]
+            s, R = [x[0] for x in sig], [x[1] for x in sig]
+            ds = O.ds_root(km.root, D)
+            assert O.aver_f(Y, msgs.as_list(), 0, n2, s, R, ds) is True
+            y = int.from_bytes(km.y, "little") % O.Q
+            for t in range(n):
+                e = O.entry_scalar(ds, n2, t, msgs.entry(t))
+                r = (int.from_bytes(s[t], "little") + e * y) % O.Q
+                assert O.encode_point(O.scalar_mult(r, O.G)) == R[t]
+            bad = synth.apply_tamper(msgs, synth.tamper_plan(40, msgs, 2))
+            inv, _, _ = O.distill_f(Y, bad.as_list(), 0, n2, s, R, ds)
+            assert O.aver_f(Y, bad.as_list(), 0, n2, s, R, ds) is False
+            assert inv == list(synth.tamper_plan(40, msgs, 2).idx)
+        else:
+            sk, Y, epoch_R = O.kg_c(km.y, km.r, km.root, D, n2)
+            ms = [[msgs.entry(i * n2 + j) for j in range(n2)] for i in range(n // n2)]
+            s_ep = [O.sig_c(sk, i, ms[i]) for i in range(n // n2)]
+            ds = O.ds_after(km.root, D, n // n2 - 1)
+            I = list(range(n // n2))
+            assert O.aver_c(Y, I, ms, n2, O.agg_scalars(s_ep), epoch_R[:len(I)], ds) is True
+            ms[1][2] = bytes([ms[1][2][0] ^ 1]) + ms[1][2][1:] if ms[1][2] else b"\x01"
+            assert O.aver_c(Y, I, ms, n2, O.agg_scalars(s_ep), epoch_R[:len(I)], ds) is False
+
+
+def test_poslo_and_poslo_plus_differ():
+    # the two instantiations give different one-time seeds and entry scalars
+    x0 = synth.random_bytes(3, "x0", 16).tobytes()
+    assert O.entry_seed_sha(x0, 5) != O.entry_seed_aes(x0, 5)
+    assert O.hash_to_scalar_sha(b"abc", x0) != O.hash_to_scalar_aes(b"abc", x0)
