@@ -58,6 +58,17 @@ typedef enum {
 
 enum { POSLO_VARIANT_C = 0, POSLO_VARIANT_F = 1 };
 enum { POSLO_AGG_UNIT = 0, POSLO_AGG_WEIGHTED = 1 };
+/* Instantiations of PRF and H (Sec. 7.2, table of instantiations):
+ *   POSLO_INST_SHA256  "POSLO": SHA-256 for both; seeds kappa = 128 bits.
+ *   POSLO_INST_AES     "POSLO+": PRF = MMO over AES-128 with kappa = 127 (a node and its
+ *                      child bit fill one AES block), H = MDC-2 over AES-128.  Seeds are 16
+ *                      bytes whose least significant bit (bit 0 of byte 15) is not part of
+ *                      the seed.  Initial values 16 x 0x52 (MMO, first MDC-2 chain) and
+ *                      16 x 0x25 (second chain); MDC-2 pads with 0x80 then zeros to whole
+ *                      blocks, always; the one-time seed x_i^j is MMO over the seed (bit 0)
+ *                      and le32(j), 20 bytes padded the same way.
+ * POSLO-C nonces and the verifier's weights z_t use SHA-256 in both. */
+enum { POSLO_INST_SHA256 = 0, POSLO_INST_AES = 1 };
 
 typedef struct poslo_ctx poslo_ctx;
 
@@ -66,6 +77,8 @@ typedef struct {
   uint32_t msm_window;        /* Pippenger window in bits, 8..16; 0 = autotune */
   uint64_t mem_budget;        /* bytes of device memory the context may hold; 0 = no limit */
   uint8_t verifier_seed[32];  /* secret randomness of the verifier for the weights z_t */
+  uint32_t instantiation;     /* POSLO_INST_SHA256 (0) or POSLO_INST_AES; every call on the
+                                 context (keys, signing, verification, serving) uses it */
 } poslo_params;
 
 /*

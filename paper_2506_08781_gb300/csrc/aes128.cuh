@@ -1,0 +1,167 @@
+// AES-128 (FIPS-197) and the two constructions of the POSLO+ instantiation (Sec. 7.2):
+// the PRF is MMO-AES-128 with kappa = 127 (Def. MMO), H is MDC-2 over AES-128 (Def. MDC-2).
+//
+// Round function.  After SubBytes and ShiftRows, output column j takes row r from input
+// column j + r; MixColumns then multiplies each substituted byte a by one column of the
+// circulant matrix (2 3 1 1 / 1 2 3 1 / 1 1 2 3 / 3 1 1 2).  The table T[a] holds
+// (2 S(a), S(a), S(a), 3 S(a)) as a big-endian word (rows 0..3); the contributions of rows
+// 1, 2, 3 are T rotated right by 8, 16, 24 bits.  S(a) itself is byte 1 of T[a].
+//
+// Shared memory.  The table has 32 copies, entry a of copy c at word 32 a + c, i.e. in bank
+// c: lane c of a warp reads only copy c, so data-dependent lookups never conflict (32 KiB
+// per block).  Each block builds it at start from the S-box definition (the inverse in
+// GF(2^8) followed by the affine map of FIPS-197 Sec. 5.1.1); no table is stored anywhere.
+//
+// Words are big-endian columns: state column c is bytes 4c..4c+3 of the block, row 0 in the
+// most significant byte, which is how the message stream hands out words.  Round keys are
+// derived on the fly, one per round (FIPS-197 Sec. 5.2 with Nk = 4), because in MMO and
+// MDC-2 every block is enciphered under a new key (the chaining value).
+#pragma once
+#include <cstdint>
+
+namespace poslo {
+
+constexpr int kAesCopies = 32;
+struct AesShared {
+  uint32_t t[256][kAesCopies];
+};
+
+// x * {02} in GF(2^8) (FIPS-197 Sec. 4.2.1), on a byte held in the low 8 bits.
+__device__ __forceinline__ uint32_t gf8_xtime(uint32_t a) { return ((a << 1) ^ ((a & 0x80u) ? 0x1bu : 0u)) & 0xffu; }
+
+__device__ __forceinline__ uint32_t gf8_mul(uint32_t a, uint32_t b) {
+  uint32_t r = 0;
+  for (int i = 0; i < 8; ++i) {
+    if (b & 1u) r ^= a;
+    b >>= 1;
+    a = gf8_xtime(a);
+  }
+  return r;
+}
+
+// S(x) = affine(x^-1), with 0 mapped through the affine map alone (x^254 = x^-1 for x != 0).
+__device__ __forceinline__ uint32_t aes_sbox_entry(uint32_t x) {
+  uint32_t inv = 1, base = x;
+  for (uint32_t e = 254; e; e >>= 1) {
+    if (e & 1u) inv = gf8_mul(inv, base);
+    base = gf8_mul(base, base);
+  }
+  if (x == 0) inv = 0;
+  // b'_i = b_i ^ b_{i+4} ^ b_{i+5} ^ b_{i+6} ^ b_{i+7} ^ c_i, c = 0x63 (indices mod 8)
+  uint32_t out = 0;
+  for (int i = 0; i < 8; ++i) {
+    uint32_t bit = 0;
+    for (int k = 0; k < 8; k += (k == 0 ? 4 : 1)) bit ^= (inv >> ((i + k) & 7)) & 1u;
+    out |= (bit ^ ((0x63u >> i) & 1u)) << i;
+  }
+  return out;
+}
+
+// Every thread of the block must call this (it ends with a barrier).
+__device__ __forceinline__ void aes_tables_init(AesShared& sh) {
+  for (uint32_t a = threadIdx.x; a < 256; a += blockDim.x) {
+    const uint32_t s = aes_sbox_entry(a), s2 = gf8_xtime(s);
+    const uint32_t t = (s2 << 24) | (s << 16) | (s << 8) | (s2 ^ s);
+    for (int c = 0; c < kAesCopies; ++c) sh.t[a][c] = t;
+  }
+  __syncthreads();
+}
+
+struct AesCtx {
+  const AesShared* sh;
+  uint32_t lane;
+  __device__ __forceinline__ uint32_t T(uint32_t a) const { return sh->t[a][lane]; }
+  __device__ __forceinline__ uint32_t S(uint32_t a) const { return (sh->t[a][lane] >> 16) & 0xffu; }
+};
+
+__device__ __forceinline__ AesCtx aes_ctx(const AesShared* sh) { return AesCtx{sh, threadIdx.x & 31u}; }
+
+__device__ __forceinline__ uint32_t ror32(uint32_t x, uint32_t n) { return __funnelshift_r(x, x, n); }
+
+// E_key(in): FIPS-197 Cipher with Nk = 4, Nr = 10.
+__device__ __forceinline__ void aes128_encrypt(const AesCtx& c, const uint32_t key[4], const uint32_t in[4],
+                                               uint32_t out[4]) {
+  uint32_t k0 = key[0], k1 = key[1], k2 = key[2], k3 = key[3];
+  uint32_t s0 = in[0] ^ k0, s1 = in[1] ^ k1, s2 = in[2] ^ k2, s3 = in[3] ^ k3;
+  uint32_t rcon = 0x01u;
+#pragma unroll 1
+  for (int r = 1; r <= 10; ++r) {
+    // round key r from round key r-1: SubWord(RotWord(w3)) ^ Rcon into w0, then the chain
+    const uint32_t rot = __funnelshift_l(k3, k3, 8);
+    const uint32_t sub = (c.S(rot >> 24) << 24) | (c.S((rot >> 16) & 0xffu) << 16) |
+                         (c.S((rot >> 8) & 0xffu) << 8) | c.S(rot & 0xffu);
+    k0 ^= sub ^ (rcon << 24);
+    k1 ^= k0;
+    k2 ^= k1;
+    k3 ^= k2;
+    rcon = gf8_xtime(rcon);
+    uint32_t t0, t1, t2, t3;
+    if (r < 10) {
+      t0 = c.T(s0 >> 24) ^ ror32(c.T((s1 >> 16) & 0xffu), 8) ^ ror32(c.T((s2 >> 8) & 0xffu), 16) ^
+           ror32(c.T(s3 & 0xffu), 24) ^ k0;
+      t1 = c.T(s1 >> 24) ^ ror32(c.T((s2 >> 16) & 0xffu), 8) ^ ror32(c.T((s3 >> 8) & 0xffu), 16) ^
+           ror32(c.T(s0 & 0xffu), 24) ^ k1;
+      t2 = c.T(s2 >> 24) ^ ror32(c.T((s3 >> 16) & 0xffu), 8) ^ ror32(c.T((s0 >> 8) & 0xffu), 16) ^
+           ror32(c.T(s1 & 0xffu), 24) ^ k2;
+      t3 = c.T(s3 >> 24) ^ ror32(c.T((s0 >> 16) & 0xffu), 8) ^ ror32(c.T((s1 >> 8) & 0xffu), 16) ^
+           ror32(c.T(s2 & 0xffu), 24) ^ k3;
+    } else {   // last round: no MixColumns
+      t0 = ((c.S(s0 >> 24) << 24) | (c.S((s1 >> 16) & 0xffu) << 16) | (c.S((s2 >> 8) & 0xffu) << 8) |
+            c.S(s3 & 0xffu)) ^ k0;
+      t1 = ((c.S(s1 >> 24) << 24) | (c.S((s2 >> 16) & 0xffu) << 16) | (c.S((s3 >> 8) & 0xffu) << 8) |
+            c.S(s0 & 0xffu)) ^ k1;
+      t2 = ((c.S(s2 >> 24) << 24) | (c.S((s3 >> 16) & 0xffu) << 16) | (c.S((s0 >> 8) & 0xffu) << 8) |
+            c.S(s1 & 0xffu)) ^ k2;
+      t3 = ((c.S(s3 >> 24) << 24) | (c.S((s0 >> 16) & 0xffu) << 16) | (c.S((s1 >> 8) & 0xffu) << 8) |
+            c.S(s2 & 0xffu)) ^ k3;
+    }
+    s0 = t0; s1 = t1; s2 = t2; s3 = t3;
+  }
+  out[0] = s0; out[1] = s1; out[2] = s2; out[3] = s3;
+}
+
+// Initial values (the MDC-2 constants 0x52.. and 0x25.. widened to 16 bytes): MMO and the
+// first MDC-2 chain start from kIvA, the second MDC-2 chain from kIvB.
+constexpr uint32_t kIvA = 0x52525252u, kIvB = 0x25252525u;
+
+// One MMO step: h <- E_h(m) ^ m.
+__device__ __forceinline__ void mmo_step(const AesCtx& c, uint32_t h[4], const uint32_t m[4]) {
+  uint32_t o[4];
+  aes128_encrypt(c, h, m, o);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) h[i] = o[i] ^ m[i];
+}
+
+// PRF_bit(z) with kappa = 127: the seed's first 127 bits and the bit fill one block, one
+// AES call; the output keeps 127 bits (bit 0 of byte 15 cleared).
+__device__ __forceinline__ void prf_node_aes(const AesCtx& c, const uint32_t z[4], uint32_t bit, uint32_t out[4]) {
+  const uint32_t m[4] = {z[0], z[1], z[2], (z[3] & ~1u) | bit};
+  uint32_t h[4] = {kIvA, kIvA, kIvA, kIvA};
+  mmo_step(c, h, m);
+  out[0] = h[0]; out[1] = h[1]; out[2] = h[2]; out[3] = h[3] & ~1u;
+}
+
+// x_i^j = PRF_0(x_0[i] || j): MMO over seed (PRF bit 0) || le32(j), 20 bytes padded with
+// 0x80 and zeros to two blocks; truncated to 127 bits.
+__device__ __forceinline__ void prf_entry_aes(const AesCtx& c, const uint32_t x0[4], uint32_t j, uint32_t out[4]) {
+  const uint32_t m1[4] = {x0[0], x0[1], x0[2], x0[3] & ~1u};
+  const uint32_t m2[4] = {__byte_perm(j, 0, 0x0123), 0x80000000u, 0u, 0u};
+  uint32_t h[4] = {kIvA, kIvA, kIvA, kIvA};
+  mmo_step(c, h, m1);
+  mmo_step(c, h, m2);
+  out[0] = h[0]; out[1] = h[1]; out[2] = h[2]; out[3] = h[3] & ~1u;
+}
+
+// One MDC-2 step on block m: both chains take an MMO step, then exchange their right
+// halves (words 2 and 3).
+__device__ __forceinline__ void mdc2_step(const AesCtx& c, uint32_t h[4], uint32_t g[4], const uint32_t m[4]) {
+  uint32_t a[4], b[4];
+  aes128_encrypt(c, h, m, a);
+  aes128_encrypt(c, g, m, b);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) { a[i] ^= m[i]; b[i] ^= m[i]; }
+  h[0] = a[0]; h[1] = a[1]; h[2] = b[2]; h[3] = b[3];
+  g[0] = b[0]; g[1] = b[1]; g[2] = a[2]; g[3] = a[3];
+}
+
+}  // namespace poslo

@@ -12,6 +12,7 @@
 #pragma once
 #include <cstdint>
 
+#include "aes128.cuh"
 #include "ge25519.cuh"
 #include "sc25519.cuh"
 #include "sha256.cuh"
@@ -122,8 +123,8 @@ __device__ __forceinline__ uint32_t stream_word(const EntryStream& es, uint32_t 
   return mw | tw;
 }
 
-// SHA-256(m || x) for one entry; returns the 8 state words.
-__device__ __forceinline__ void hash_entry(const uint8_t* m, uint32_t L, const uint32_t x[4], uint32_t st[8]) {
+// The stream m || x || 0x80 || 0... of one entry (x given as 4 big-endian words).
+__device__ __forceinline__ EntryStream entry_stream(const uint8_t* m, uint32_t L, const uint32_t x[4]) {
   EntryStream es;
   const uintptr_t p = reinterpret_cast<uintptr_t>(m);
   const uint32_t sh = (uint32_t)(p & 3u);
@@ -140,6 +141,12 @@ __device__ __forceinline__ void hash_entry(const uint8_t* m, uint32_t L, const u
   es.S[2] = __funnelshift_r(x[2], x[1], sr);
   es.S[3] = __funnelshift_r(x[3], x[2], sr);
   es.S[4] = __funnelshift_r(0x80000000u, x[3], sr);
+  return es;
+}
+
+// SHA-256(m || x) for one entry; returns the 8 state words.
+__device__ __forceinline__ void hash_entry(const uint8_t* m, uint32_t L, const uint32_t x[4], uint32_t st[8]) {
+  const EntryStream es = entry_stream(m, L, x);
   const uint32_t total = L + 16;
   const uint32_t nb = (total + 9 + 63) >> 6;
   sha256_init(st);
@@ -158,6 +165,62 @@ __device__ __forceinline__ void hash_entry(const uint8_t* m, uint32_t L, const u
       }
     }
     sha256_compress(st, w);
+  }
+}
+
+// ----------------------------------------------------------------------------------------
+// Instantiations of PRF and H (Sec. 7.2): POSLO = SHA-256 for both, POSLO+ = MMO-AES-128
+// (kappa = 127) and MDC-2-AES-128.  Kernels that hash are templates on the instantiation;
+// a POSLO+ kernel builds its AES table in shared memory first (aes_tables_init).
+// ----------------------------------------------------------------------------------------
+enum : int { kInstSha = 0, kInstAes = 1 };
+
+template <int INST>
+__device__ __forceinline__ void prf_node_i(const AesCtx& c, const uint32_t z[4], uint32_t bit, uint32_t out[4]) {
+  if constexpr (INST == kInstAes) prf_node_aes(c, z, bit, out);
+  else prf_node(z, bit, out);
+}
+
+template <int INST>
+__device__ __forceinline__ void prf_entry_i(const AesCtx& c, const uint32_t x0[4], uint32_t j, uint32_t out[4]) {
+  if constexpr (INST == kInstAes) prf_entry_aes(c, x0, j, out);
+  else prf_entry(x0, j, out);
+}
+
+// MDC-2-AES-128 over the padded stream: (L + 16 + 16) / 16 blocks (the 0x80 byte always
+// fits, a whole-block input gains a block).  dig = the 32-byte digest as 8 little-endian
+// words (the integer H(m || x) before reduction mod q).
+__device__ __forceinline__ void mdc2_stream(const AesCtx& c, const EntryStream& es, uint32_t dig[8]) {
+  uint32_t h[4] = {kIvA, kIvA, kIvA, kIvA}, g[4] = {kIvB, kIvB, kIvB, kIvB};
+  const uint32_t nb = (es.L + 32) >> 4;
+#pragma unroll 1
+  for (uint32_t b = 0; b < nb; ++b) {
+    const uint32_t o = b << 4;
+    uint32_t m[4];
+    if (o + 16 <= es.L) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) m[q] = load_msg_word(es, (o >> 2) + q);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) m[q] = stream_word(es, o + 4 * q);
+    }
+    mdc2_step(c, h, g, m);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) { dig[q] = bswap32(h[q]); dig[4 + q] = bswap32(g[q]); }
+}
+
+// H(m || x) as 8 little-endian digest words for the instantiation.
+template <int INST>
+__device__ __forceinline__ void entry_digest(const AesCtx& c, const uint8_t* m, uint32_t L, const uint32_t x[4],
+                                             uint32_t dig[8]) {
+  if constexpr (INST == kInstAes) {
+    mdc2_stream(c, entry_stream(m, L, x), dig);
+  } else {
+    uint32_t st[8];
+    hash_entry(m, L, x, st);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) dig[q] = bswap32(st[q]);
   }
 }
 
@@ -522,9 +585,9 @@ struct PrepArgs {
 };
 
 // ---- kernel declarations ----
-__global__ void k_epoch_seeds(const DsNode* __restrict__ ds, int nds, uint64_t e0, uint64_t ne,
-                              uint32_t* __restrict__ x0_out, uint32_t* __restrict__ status);
-__global__ void __launch_bounds__(kHashThreads, POSLO_HASH_MIN_BLOCKS) k_hash(const HashArgs a);
+void launch_epoch_seeds(int inst, unsigned grid, unsigned block, cudaStream_t st, const DsNode* ds, int nds,
+                        uint64_t e0, uint64_t ne, uint32_t* x0_out, uint32_t* status);
+void launch_hash(int inst, unsigned grid, cudaStream_t st, const HashArgs& a);
 __global__ void __launch_bounds__(kPointThreads) k_points(const PointArgs a);
 __global__ void __launch_bounds__(128) k_table_chain(const uint32_t* __restrict__ enc,
                                                      const uint32_t* __restrict__ pts,
@@ -550,8 +613,8 @@ __global__ void k_keygen_c_epochs(const uint8_t* r, uint32_t n1, uint32_t n2, co
                                   uint8_t* epoch_R);
 __global__ void k_keygen_bpv(const uint8_t* bpv_r, uint32_t v, const uint32_t* tableG, uint8_t* bpv_R);
 __global__ void k_decode_table(const uint8_t* enc, uint32_t v, uint32_t* out, uint32_t* status);
-__global__ void k_sign_f(const SignFArgs a);
-__global__ void k_sign_c(const SignCArgs a);
+void launch_sign_f(int inst, unsigned grid, unsigned block, cudaStream_t st, const SignFArgs& a);
+void launch_sign_c(int inst, unsigned grid, unsigned block, cudaStream_t st, const SignCArgs& a);
 __global__ void k_msm_count(const uint32_t* z, const uint8_t* skip, uint64_t n, MsmPlan pl, uint32_t* cnt,
                             uint32_t* rank);
 __global__ void __launch_bounds__(1024) k_msm_scan(const uint32_t* cnt, uint32_t* off, MsmPlan pl);
@@ -584,8 +647,9 @@ __global__ void __launch_bounds__(kPointThreads) k_pts_sum(const uint32_t* pts, 
                           uint32_t* partial);
 __global__ void k_flags_or(const uint8_t* a, const uint8_t* b, const uint8_t* c, uint64_t n, uint8_t* out);
 __global__ void k_encode_ext(const uint32_t* point, uint8_t* out);
-__global__ void k_epoch_seeds_multi(const DsNode* ds_all, const uint32_t* ds_off, const uint64_t* seed_off,
-                                    const uint64_t* e0, uint32_t n_dev, uint32_t* seeds, uint32_t* status);
+void launch_epoch_seeds_multi(int inst, unsigned grid, unsigned block, cudaStream_t st, const DsNode* ds_all,
+                              const uint32_t* ds_off, const uint64_t* seed_off, const uint64_t* e0, uint32_t n_dev,
+                              uint32_t* seeds, uint32_t* status);
 __global__ void k_rebase_offs(const uint64_t* raw, const uint64_t* slot, const uint64_t* start,
                               const uint64_t* msg_base, uint32_t n_dev, uint64_t* out, uint32_t* status);
 __global__ void __launch_bounds__(256) k_segment_sums(const uint8_t* e, const uint8_t* s, const uint32_t* z,

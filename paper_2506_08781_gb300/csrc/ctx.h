@@ -30,6 +30,7 @@ struct poslo_ctx {
   int device = 0;
   int sm_count = 0;
   uint32_t msm_window = 0;
+  uint32_t inst = 0;              // POSLO_INST_SHA256 or POSLO_INST_AES
   uint64_t mem_budget = 0;
   uint64_t mem_used = 0;
   uint8_t vseed[32] = {0};

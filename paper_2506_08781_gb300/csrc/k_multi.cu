@@ -9,8 +9,15 @@ namespace poslo {
 
 // SRet for every (device, epoch) pair of the batch: seeds[s] for s in
 // [seed_off[d], seed_off[d+1]) is x_0[e0[d] + s - seed_off[d]] under device d's ds.
+template <int INST>
 __global__ void k_epoch_seeds_multi(const DsNode* ds_all, const uint32_t* ds_off, const uint64_t* seed_off,
                                     const uint64_t* e0, uint32_t n_dev, uint32_t* seeds, uint32_t* status) {
+  AesCtx c{};
+  if constexpr (INST == kInstAes) {
+    __shared__ AesShared sh;
+    aes_tables_init(sh);
+    c = aes_ctx(&sh);
+  }
   const uint64_t total = seed_off[n_dev];
   const uint64_t sidx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (sidx >= total) return;
@@ -30,7 +37,7 @@ __global__ void k_epoch_seeds_multi(const DsNode* ds_all, const uint32_t* ds_off
     const uint64_t off = target - ((uint64_t)n.i << n.d);
     for (int j = (int)n.d - 1; j >= 0; --j) {
       uint32_t y[4];
-      prf_node(x, (uint32_t)(off >> j) & 1u, y);
+      prf_node_i<INST>(c, x, (uint32_t)(off >> j) & 1u, y);
       x[0] = y[0]; x[1] = y[1]; x[2] = y[2]; x[3] = y[3];
     }
   } else {
@@ -276,6 +283,15 @@ __global__ void k_segment_any(const uint8_t* inv, const uint64_t* seg_start, con
   for (uint64_t t = seg_start[d] + threadIdx.x; t < seg_start[d + 1]; t += blockDim.x) any |= inv[t];
   any = __syncthreads_or(any);
   if (threadIdx.x == 0) out[blockIdx.x] = any ? 1 : 0;
+}
+
+void launch_epoch_seeds_multi(int inst, unsigned grid, unsigned block, cudaStream_t st, const DsNode* ds_all,
+                              const uint32_t* ds_off, const uint64_t* seed_off, const uint64_t* e0, uint32_t n_dev,
+                              uint32_t* seeds, uint32_t* status) {
+  if (inst == kInstAes)
+    k_epoch_seeds_multi<kInstAes><<<grid, block, 0, st>>>(ds_all, ds_off, seed_off, e0, n_dev, seeds, status);
+  else
+    k_epoch_seeds_multi<kInstSha><<<grid, block, 0, st>>>(ds_all, ds_off, seed_off, e0, n_dev, seeds, status);
 }
 
 }  // namespace poslo

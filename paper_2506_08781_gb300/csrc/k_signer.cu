@@ -47,7 +47,14 @@ __global__ void k_decode_table(const uint8_t* enc, uint32_t v, uint32_t* out, ui
   ge_store(out + 32 * (size_t)k, P);
 }
 
+template <int INST>
 __global__ void k_sign_f(const SignFArgs a) {
+  AesCtx c{};
+  if constexpr (INST == kInstAes) {
+    __shared__ AesShared sh;
+    aes_tables_init(sh);
+    c = aes_ctx(&sh);
+  }
   const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= a.n) return;
   const uint64_t gi = a.first_index + t;
@@ -55,13 +62,10 @@ __global__ void k_sign_f(const SignFArgs a) {
   const uint4 xs = a.seeds ? reinterpret_cast<const uint4*>(a.seeds)[i - a.e0] : make_uint4(0, 0, 0, 0);
   const uint32_t x0[4] = {xs.x, xs.y, xs.z, xs.w};
   uint32_t x[4];
-  prf_entry(x0, (uint32_t)j, x);
+  prf_entry_i<INST>(c, x0, (uint32_t)j, x);
   const uint64_t o0 = a.offs[t] - a.base_off, o1 = a.offs[t + 1] - a.base_off;
-  uint32_t st[8];
-  hash_entry(a.msgs + o0, (uint32_t)(o1 - o0), x, st);
   uint32_t d[8];
-#pragma unroll
-  for (int k = 0; k < 8; ++k) d[k] = bswap32(st[k]);
+  entry_digest<INST>(c, a.msgs + o0, (uint32_t)(o1 - o0), x, d);
   const sc e = sc_reduce256(d);
   sc r;
 #pragma unroll
@@ -92,7 +96,14 @@ __global__ void k_sign_f(const SignFArgs a) {
   }
 }
 
+template <int INST>
 __global__ void k_sign_c(const SignCArgs a) {
+  AesCtx c{};
+  if constexpr (INST == kInstAes) {
+    __shared__ AesShared sh;
+    aes_tables_init(sh);
+    c = aes_ctx(&sh);
+  }
   const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= a.n_epochs) return;
   const uint64_t i = a.first_epoch + k;
@@ -110,17 +121,24 @@ __global__ void k_sign_c(const SignCArgs a) {
   for (uint32_t j = 0; j < a.n2; ++j) {
     const uint64_t t = k * a.n2 + j;
     uint32_t x[4];
-    prf_entry(x0, j, x);
+    prf_entry_i<INST>(c, x0, j, x);
     const uint64_t o0 = a.offs[t] - a.base_off, o1 = a.offs[t + 1] - a.base_off;
-    uint32_t st[8];
-    hash_entry(a.msgs + o0, (uint32_t)(o1 - o0), x, st);
     uint32_t d[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) d[q] = bswap32(st[q]);
+    entry_digest<INST>(c, a.msgs + o0, (uint32_t)(o1 - o0), x, d);
     const sc e = sc_reduce256(d);
     acc = sc_add(acc, sc_sub(nonce_c(rw, (uint32_t)i, j), sc_mul(e, y)));
   }
   store_words_bytes(a.s_out + 32 * k, acc.v);
+}
+
+void launch_sign_f(int inst, unsigned grid, unsigned block, cudaStream_t st, const SignFArgs& a) {
+  if (inst == kInstAes) k_sign_f<kInstAes><<<grid, block, 0, st>>>(a);
+  else k_sign_f<kInstSha><<<grid, block, 0, st>>>(a);
+}
+
+void launch_sign_c(int inst, unsigned grid, unsigned block, cudaStream_t st, const SignCArgs& a) {
+  if (inst == kInstAes) k_sign_c<kInstAes><<<grid, block, 0, st>>>(a);
+  else k_sign_c<kInstSha><<<grid, block, 0, st>>>(a);
 }
 
 }  // namespace poslo

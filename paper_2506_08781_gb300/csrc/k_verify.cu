@@ -3,8 +3,15 @@
 
 namespace poslo {
 
+template <int INST>
 __global__ void k_epoch_seeds(const DsNode* __restrict__ ds, int nds, uint64_t e0, uint64_t ne,
                               uint32_t* __restrict__ x0_out, uint32_t* __restrict__ status) {
+  AesCtx c{};
+  if constexpr (INST == kInstAes) {
+    __shared__ AesShared sh;
+    aes_tables_init(sh);
+    c = aes_ctx(&sh);
+  }
   const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= ne) return;
   const uint64_t target = e0 + k;
@@ -26,7 +33,7 @@ __global__ void k_epoch_seeds(const DsNode* __restrict__ ds, int nds, uint64_t e
     const uint64_t off = target - ((uint64_t)n.i << n.d);
     for (int j = (int)n.d - 1; j >= 0; --j) {
       uint32_t y[4];
-      prf_node(x, (uint32_t)(off >> j) & 1u, y);
+      prf_node_i<INST>(c, x, (uint32_t)(off >> j) & 1u, y);
       x[0] = y[0]; x[1] = y[1]; x[2] = y[2]; x[3] = y[3];
     }
   } else {
@@ -44,7 +51,25 @@ __global__ void k_epoch_seeds(const DsNode* __restrict__ ds, int nds, uint64_t e
 constexpr int kHashTile = 256;
 constexpr int kHashClasses = 8;
 
+// z_t = SHA-256("POSLO-Z" || verifier_seed || le64(t)): the single padded block.
+__device__ __forceinline__ void weight_block(const uint32_t zpre[10], uint64_t zi, uint32_t w[16]) {
+  const uint32_t lo = (uint32_t)zi, hi = (uint32_t)(zi >> 32);
+#pragma unroll
+  for (int q = 0; q < 9; ++q) w[q] = zpre[q];
+  w[9] = zpre[9] | (lo & 0xffu);
+  w[10] = ((lo >> 8) & 0xffu) << 24 | ((lo >> 16) & 0xffu) << 16 | ((lo >> 24) & 0xffu) << 8 | (hi & 0xffu);
+  w[11] = ((hi >> 8) & 0xffu) << 24 | ((hi >> 16) & 0xffu) << 16 | ((hi >> 24) & 0xffu) << 8 | 0x80u;
+  w[12] = 0; w[13] = 0; w[14] = 0; w[15] = 47 * 8;
+}
+
+template <int INST>
 __global__ void __launch_bounds__(kHashThreads, POSLO_HASH_MIN_BLOCKS) k_hash(const HashArgs a) {
+  AesCtx c{};
+  if constexpr (INST == kInstAes) {
+    __shared__ AesShared sh;
+    aes_tables_init(sh);
+    c = aes_ctx(&sh);
+  }
   acc13 acc_e, acc_s;
   acc_zero(acc_e);
   acc_zero(acc_s);
@@ -114,71 +139,78 @@ __global__ void __launch_bounds__(kHashThreads, POSLO_HASH_MIN_BLOCKS) k_hash(co
       const uint64_t o0 = a.offs[t] - a.base_off, o1 = a.offs[t + 1] - a.base_off;
       // malformed offsets (flagged above) hash as empty messages and never read memory
       const uint32_t L = (o1 >= o0 && o1 - o0 <= 0xffffffffull && a.offs[t] >= a.base_off) ? (uint32_t)(o1 - o0) : 0u;
-      // padded stream of m || x (x is known after the PRF block)
-      EntryStream es;
-      {
-        const uintptr_t p = reinterpret_cast<uintptr_t>(a.msgs + o0);
-        const uint32_t sh = (uint32_t)(p & 3u);
-        es.base = reinterpret_cast<const uint32_t*>(p - sh);
-        es.sel = (sh + 3) | ((sh + 2) << 4) | ((sh + 1) << 8) | (sh << 12);
-        es.sh_nz = sh != 0;
-        es.L = L;
-        es.kmax = L > 0 ? (int32_t)((L + sh - 1) >> 2) : 0;
-        es.a = L & ~3u;
-      }
-      const uint32_t total = L + 16;
-      const uint32_t nb = (total + 9 + 63) >> 6;
-      const uint32_t iters = 1 + nb + (a.weighted ? 1u : 0u);
       uint32_t st[8], dig[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-      sha256_init(st);
-#pragma unroll 1
-      for (uint32_t it = 0; it < iters; ++it) {
-        uint32_t w[16];
-        if (it == 0) {
-          // PRF_0(x_0[i] || le32(j)): x0 || le32(j) || 0x00 || 0x80 ... || bitlen(21 bytes)
-          w[0] = xs.x; w[1] = xs.y; w[2] = xs.z; w[3] = xs.w;
-          w[4] = bswap32((uint32_t)j);
-          w[5] = 0x00800000u;
-#pragma unroll
-          for (int q = 6; q < 15; ++q) w[q] = 0;
-          w[15] = 21 * 8;
-        } else if (it <= nb) {
-          const uint32_t o = (it - 1) << 6;
-          if (o + 64 <= L) {
-#pragma unroll
-            for (int q = 0; q < 16; ++q) w[q] = load_msg_word(es, (o >> 2) + q);
-          } else {
-#pragma unroll
-            for (int q = 0; q < 16; ++q) w[q] = stream_word(es, o + 4 * q);
-            if (it == nb) {
-              w[14] |= total >> 29;
-              w[15] |= total << 3;
-            }
-          }
-        } else {
-          // z_t = SHA-256("POSLO-Z" || verifier_seed || le64(t))[0..16)
-          const uint32_t lo = (uint32_t)zi, hi = (uint32_t)(zi >> 32);
-#pragma unroll
-          for (int q = 0; q < 9; ++q) w[q] = a.zpre[q];
-          w[9] = a.zpre[9] | (lo & 0xffu);
-          w[10] = ((lo >> 8) & 0xffu) << 24 | ((lo >> 16) & 0xffu) << 16 | ((lo >> 24) & 0xffu) << 8 | (hi & 0xffu);
-          w[11] = ((hi >> 8) & 0xffu) << 24 | ((hi >> 16) & 0xffu) << 16 | ((hi >> 24) & 0xffu) << 8 | 0x80u;
-          w[12] = 0; w[13] = 0; w[14] = 0; w[15] = 47 * 8;
+      if constexpr (INST == kInstAes) {
+        // x_t = MMO-AES-128 PRF, e_t from MDC-2-AES-128 over m || x_t, then z_t by SHA-256
+        const uint32_t x0[4] = {xs.x, xs.y, xs.z, xs.w};
+        uint32_t x[4];
+        prf_entry_aes(c, x0, (uint32_t)j, x);
+        mdc2_stream(c, entry_stream(a.msgs + o0, L, x), dig);
+        if (a.weighted) {
+          uint32_t w[16];
+          weight_block(a.zpre, zi, w);
+          sha256_init(st);
+          sha256_compress(st, w);
         }
-        sha256_compress(st, w);
-        if (it == 0) {
-          // x = first 16 bytes of the PRF digest, shifted into the stream after m
-          const uint32_t sr = 8u * (L & 3u);
-          es.S[0] = __funnelshift_r(st[0], 0u, sr);
-          es.S[1] = __funnelshift_r(st[1], st[0], sr);
-          es.S[2] = __funnelshift_r(st[2], st[1], sr);
-          es.S[3] = __funnelshift_r(st[3], st[2], sr);
-          es.S[4] = __funnelshift_r(0x80000000u, st[3], sr);
-          sha256_init(st);
-        } else if (it == nb) {
+      } else {
+        // padded stream of m || x (x is known after the PRF block)
+        EntryStream es;
+        {
+          const uintptr_t p = reinterpret_cast<uintptr_t>(a.msgs + o0);
+          const uint32_t sh = (uint32_t)(p & 3u);
+          es.base = reinterpret_cast<const uint32_t*>(p - sh);
+          es.sel = (sh + 3) | ((sh + 2) << 4) | ((sh + 1) << 8) | (sh << 12);
+          es.sh_nz = sh != 0;
+          es.L = L;
+          es.kmax = L > 0 ? (int32_t)((L + sh - 1) >> 2) : 0;
+          es.a = L & ~3u;
+        }
+        const uint32_t total = L + 16;
+        const uint32_t nb = (total + 9 + 63) >> 6;
+        const uint32_t iters = 1 + nb + (a.weighted ? 1u : 0u);
+        sha256_init(st);
+#pragma unroll 1
+        for (uint32_t it = 0; it < iters; ++it) {
+          uint32_t w[16];
+          if (it == 0) {
+            // PRF_0(x_0[i] || le32(j)): x0 || le32(j) || 0x00 || 0x80 ... || bitlen(21 bytes)
+            w[0] = xs.x; w[1] = xs.y; w[2] = xs.z; w[3] = xs.w;
+            w[4] = bswap32((uint32_t)j);
+            w[5] = 0x00800000u;
 #pragma unroll
-          for (int q = 0; q < 8; ++q) dig[q] = bswap32(st[q]);
-          sha256_init(st);
+            for (int q = 6; q < 15; ++q) w[q] = 0;
+            w[15] = 21 * 8;
+          } else if (it <= nb) {
+            const uint32_t o = (it - 1) << 6;
+            if (o + 64 <= L) {
+#pragma unroll
+              for (int q = 0; q < 16; ++q) w[q] = load_msg_word(es, (o >> 2) + q);
+            } else {
+#pragma unroll
+              for (int q = 0; q < 16; ++q) w[q] = stream_word(es, o + 4 * q);
+              if (it == nb) {
+                w[14] |= total >> 29;
+                w[15] |= total << 3;
+              }
+            }
+          } else {
+            weight_block(a.zpre, zi, w);
+          }
+          sha256_compress(st, w);
+          if (it == 0) {
+            // x = first 16 bytes of the PRF digest, shifted into the stream after m
+            const uint32_t sr = 8u * (L & 3u);
+            es.S[0] = __funnelshift_r(st[0], 0u, sr);
+            es.S[1] = __funnelshift_r(st[1], st[0], sr);
+            es.S[2] = __funnelshift_r(st[2], st[1], sr);
+            es.S[3] = __funnelshift_r(st[3], st[2], sr);
+            es.S[4] = __funnelshift_r(0x80000000u, st[3], sr);
+            sha256_init(st);
+          } else if (it == nb) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) dig[q] = bswap32(st[q]);
+            sha256_init(st);
+          }
         }
       }
       const sc e = sc_reduce256(dig);
@@ -464,6 +496,18 @@ __global__ void k_final_check(const uint32_t* prep, const uint32_t* R, const uin
   const bool ok = ge_is_identity(ge_mul_cofactor(diff)) && prep[32] == 0 && !(point_bad && *point_bad) &&
                   (*status & kErrKey) == 0;
   accept[0] = ok ? 1 : 0;
+}
+
+// Host launchers (kernel templates are launched from the translation unit that defines them).
+void launch_epoch_seeds(int inst, unsigned grid, unsigned block, cudaStream_t st, const DsNode* ds, int nds,
+                        uint64_t e0, uint64_t ne, uint32_t* x0_out, uint32_t* status) {
+  if (inst == kInstAes) k_epoch_seeds<kInstAes><<<grid, block, 0, st>>>(ds, nds, e0, ne, x0_out, status);
+  else k_epoch_seeds<kInstSha><<<grid, block, 0, st>>>(ds, nds, e0, ne, x0_out, status);
+}
+
+void launch_hash(int inst, unsigned grid, cudaStream_t st, const HashArgs& a) {
+  if (inst == kInstAes) k_hash<kInstAes><<<grid, kHashThreads, 0, st>>>(a);
+  else k_hash<kInstSha><<<grid, kHashThreads, 0, st>>>(a);
 }
 
 }  // namespace poslo

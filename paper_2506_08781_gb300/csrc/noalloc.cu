@@ -98,7 +98,7 @@ extern "C" int poslo_hash_entries_noalloc(const poslo_batch* batch, uint8_t* e_o
   if (cudaMemcpyAsync(d_ds, h, b.ds_nodes * sizeof(DsNode), cudaMemcpyHostToDevice, st) != cudaSuccess)
     return POSLO_EDEVICE;
   if (ne) {
-    k_epoch_seeds<<<(unsigned)((ne + 127) / 128), 128, 0, st>>>(d_ds, (int)b.ds_nodes, e0, ne, seeds, status);
+    launch_epoch_seeds(kInstSha, (unsigned)((ne + 127) / 128), 128, st, d_ds, (int)b.ds_nodes, e0, ne, seeds, status);
   }
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return POSLO_EDEVICE;
@@ -122,7 +122,7 @@ extern "C" int poslo_hash_entries_noalloc(const poslo_batch* batch, uint8_t* e_o
   a.e_out = e_out;
   a.partial = partial;
   a.status = status;
-  k_hash<<<blocks, kHashThreads, 0, st>>>(a);
+  launch_hash(kInstSha, (unsigned)blocks, st, a);
   if (cudaGetLastError() != cudaSuccess) return POSLO_EDEVICE;
   uint32_t h_status = 0;
   if (cudaMemcpyAsync(&h_status, status, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) return POSLO_EDEVICE;

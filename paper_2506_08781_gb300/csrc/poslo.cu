@@ -20,6 +20,7 @@
 
 using namespace poslo;
 
+
 #include "ctx.h"
 
 using poslo_host::DevBuf;
@@ -202,9 +203,9 @@ int run_epoch_seeds(poslo_ctx* ctx, const uint8_t* ds, uint32_t nodes, uint64_t 
     const uint64_t blocks = (n_epochs + threads - 1) / threads;
     cudaEvent_t b, e;
     timer_begin(ctx, "seeds", ctx->s_main, &b, &e);
-    k_epoch_seeds<<<(unsigned)blocks, threads, 0, ctx->s_main>>>(d_ds, (int)h.size(), first_epoch, n_epochs, seeds,
-                                                                ctx->status);
-                                                                ++ctx->launch_count;
+    launch_epoch_seeds((int)ctx->inst, (unsigned)blocks, threads, ctx->s_main, d_ds, (int)h.size(), first_epoch,
+                       n_epochs, seeds, ctx->status);
+    ++ctx->launch_count;
     CU(cudaGetLastError());
     timer_end(ctx, "seeds", ctx->s_main, b, e);
   }
@@ -315,7 +316,7 @@ int run_hash(poslo_ctx* ctx, const poslo_batch* b, const Staged& sb, uint8_t* e_
   a.status = ctx->status;
   cudaEvent_t tb, te;
   timer_begin(ctx, "hash", ctx->s_main, &tb, &te);
-  k_hash<<<blocks, kHashThreads, 0, ctx->s_main>>>(a);
+  launch_hash((int)ctx->inst, (unsigned)blocks, ctx->s_main, a);
   ++ctx->launch_count;
   CU(cudaGetLastError());
   timer_end(ctx, "hash", ctx->s_main, tb, te);
@@ -671,6 +672,8 @@ int poslo_create(const poslo_params* params, poslo_ctx** out) {
   poslo_ctx* ctx = nullptr;
   if (!out) return POSLO_EINVAL;
   *out = nullptr;
+  if (params && params->instantiation != POSLO_INST_SHA256 && params->instantiation != POSLO_INST_AES)
+    return POSLO_EINVAL;
   const int device = params ? params->device : 0;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= device || device < 0) return POSLO_EDEVICE;
@@ -682,6 +685,7 @@ int poslo_create(const poslo_params* params, poslo_ctx** out) {
   ctx->sm_count = prop.multiProcessorCount;
   if (params) {
     ctx->msm_window = params->msm_window;
+    ctx->inst = params->instantiation;
     ctx->mem_budget = params->mem_budget;
     memcpy(ctx->vseed, params->verifier_seed, 32);
   }
@@ -884,7 +888,7 @@ int poslo_sign_f(poslo_ctx* ctx, const uint8_t y[32], const uint8_t root[16], ui
   a.s_out = d_s;
   a.R_out = d_R;
   a.x_out = d_x;
-  k_sign_f<<<(unsigned)((n + 127) / 128), 128, 0, ctx->s_main>>>(a);
+  launch_sign_f((int)ctx->inst, (unsigned)((n + 127) / 128), 128, ctx->s_main, a);
   ++ctx->launch_count;
   CU(cudaGetLastError());
   CU(cudaMemcpyAsync(s_out, d_s, 32 * n, cudaMemcpyDeviceToHost, ctx->s_main));
@@ -932,7 +936,7 @@ int poslo_sign_c(poslo_ctx* ctx, const uint8_t y[32], const uint8_t r[32], const
   a.y = d_yr;
   a.r = d_yr + 32;
   a.s_out = d_s;
-  k_sign_c<<<(unsigned)((n_epochs + 63) / 64), 64, 0, ctx->s_main>>>(a);
+  launch_sign_c((int)ctx->inst, (unsigned)((n_epochs + 63) / 64), 64, ctx->s_main, a);
   ++ctx->launch_count;
   CU(cudaGetLastError());
   CU(cudaMemcpyAsync(s_out, d_s, 32 * n_epochs, cudaMemcpyDeviceToHost, ctx->s_main));
@@ -1146,7 +1150,7 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
     a.status = ctx->status;
     cudaEvent_t tb, te;
     timer_begin(ctx, "hash", ctx->s_main, &tb, &te);
-    k_hash<<<blocks, kHashThreads, 0, ctx->s_main>>>(a);
+    launch_hash((int)ctx->inst, (unsigned)blocks, ctx->s_main, a);
     ++ctx->launch_count;
     CU(cudaGetLastError());
     timer_end(ctx, "hash", ctx->s_main, tb, te);
@@ -1495,8 +1499,8 @@ int poslo_host::aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, const ui
   uint32_t* seeds;
   if ((rc = ensure_t(ctx, "seeds", 16 * std::max<uint64_t>(seed_off[nd], 1), &seeds))) return rc;
   if (seed_off[nd]) {
-    k_epoch_seeds_multi<<<(unsigned)((seed_off[nd] + 127) / 128), 128, 0, ctx->s_main>>>(
-        d_nodes, d_dsoff, seg_seed_off, seg_e0, nd, seeds, ctx->status);
+    launch_epoch_seeds_multi((int)ctx->inst, (unsigned)((seed_off[nd] + 127) / 128), 128, ctx->s_main, d_nodes,
+                             d_dsoff, seg_seed_off, seg_e0, nd, seeds, ctx->status);
     ++ctx->launch_count;
   }
   // ---- A5 (side stream): decode every R_t
@@ -1539,7 +1543,7 @@ int poslo_host::aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, const ui
     a.seg_n2 = d_n2;
     cudaEvent_t tb, te;
     timer_begin(ctx, "hash", ctx->s_main, &tb, &te);
-    k_hash<<<blocks, kHashThreads, 0, ctx->s_main>>>(a);
+    launch_hash((int)ctx->inst, (unsigned)blocks, ctx->s_main, a);
     ++ctx->launch_count;
     CU(cudaGetLastError());
     timer_end(ctx, "hash", ctx->s_main, tb, te);

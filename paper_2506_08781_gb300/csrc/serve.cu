@@ -231,6 +231,7 @@ int poslo_serve_start(poslo_ctx* ctx, uint32_t workers, uint32_t max_batch_devic
     poslo_params p{};
     p.device = ctx->device;
     p.msm_window = ctx->msm_window;
+    p.instantiation = ctx->inst;
     p.mem_budget = 0;
     memcpy(p.verifier_seed, ctx->vseed, 32);
     p.verifier_seed[31] ^= (uint8_t)(k + 1);   // independent weights per worker

@@ -21,6 +21,7 @@ STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "EDEVICE", -4: "ETIMEOUT", -5
           -7: "ENOTFOUND"}
 VARIANT_C, VARIANT_F = 0, 1
 AGG_UNIT, AGG_WEIGHTED = 0, 1
+INST_SHA256, INST_AES = 0, 1          # POSLO and POSLO+ (Sec. 7.2)
 
 # Every entry point declared in include/poslo.h.
 EXPORTS = [
@@ -43,7 +44,7 @@ class PosloError(RuntimeError):
 
 class Params(C.Structure):
     _fields_ = [("device", C.c_int), ("msm_window", C.c_uint32), ("mem_budget", C.c_uint64),
-                ("verifier_seed", C.c_uint8 * 32)]
+                ("verifier_seed", C.c_uint8 * 32), ("instantiation", C.c_uint32)]
 
 
 class MultiBatch(C.Structure):
@@ -175,12 +176,13 @@ class Context:
     """A libposlo context on one device."""
 
     def __init__(self, device: int = 0, msm_window: int = 0, mem_budget: int = 0,
-                 verifier_seed: bytes = bytes(32)):
+                 verifier_seed: bytes = bytes(32), instantiation: int = INST_SHA256):
         self.lib = load_library()
         p = Params()
         p.device = device
         p.msm_window = msm_window
         p.mem_budget = mem_budget
+        p.instantiation = instantiation
         for i, b in enumerate(verifier_seed[:32]):
             p.verifier_seed[i] = b
         h = C.c_void_p()
