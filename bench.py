@@ -238,6 +238,72 @@ def bench_multi(ctx, steps: int, warmup: int) -> dict:
             "invalid_found": len(got), "setup_s": setup_s, "msm_window": msm_window, "stages": stages}
 
 
+# ------------------------------------------------------------------------------ POSLO-C, hash-bound
+
+Q_ORDER = 2 ** 252 + 27742317777372353535851937790883648493   # order of the group (edwards25519)
+AES_LOOKUPS = 10 * 16 + 10 * 4          # shared-memory table reads per AES-128 (rounds + key schedule)
+
+
+def bench_hash_bound(device: int, steps: int, warmup: int) -> dict:
+    """POSLO-C AVer (Fig. 3a with the epochs' R~_i from pk): hashing of every entry, one
+    aggregate check, no per-entry group work -- the paper's PAVer workload -- at 2^20 entries
+    (n2 = 256, n1 = 4096), under POSLO (SHA-256) and POSLO+ (AES: MMO PRF, MDC-2 H), for the
+    bench's U[32, 256] messages and for the paper's 16-byte messages (Table 6)."""
+    import torch
+    from paper_2506_08781_gb300 import poslo, synth
+    out = {}
+    for label, lmin, lmax in (("U[32,256] B", LMIN, LMAX), ("16 B", 16, 16)):
+        km = synth.key_material(SEED + 7)
+        msgs = synth.messages(SEED + 7, N_ENTRIES, lmin, lmax)
+        L = (msgs.offs[1:] - msgs.offs[:-1]).astype(np.int64)
+        d_msgs = torch.from_numpy(msgs.data).cuda()
+        d_offs = torch.from_numpy(msgs.offs.view(np.int64)).cuda()
+        row = {}
+        for name, inst in (("POSLO", poslo.INST_SHA256), ("POSLO+", poslo.INST_AES)):
+            ctx = poslo.Context(device=device, instantiation=inst)
+            Y, epoch_R = ctx.keygen_c(km.y, km.r, D, N2)
+            s_ep = ctx.sign_c(km.y, km.r, km.root, D, N2, msgs.data, msgs.offs, 0, 1 << D).reshape(-1, 32)
+            s_agg = sum(int.from_bytes(bytes(r), "little") for r in s_ep) % Q_ORDER
+            d_s = torch.from_numpy(np.frombuffer(s_agg.to_bytes(32, "little"), np.uint8).copy()).cuda()
+            d_R = torch.from_numpy(np.asarray(epoch_R, np.uint8).copy()).cuda()
+            ds = struct.pack("<II", D, 0) + km.root
+            torch.cuda.synchronize()
+            b = ctx.make_batch(poslo.VARIANT_C, N2, Y, d_msgs, d_offs, d_s, d_R, ds)
+            for _ in range(warmup):
+                assert ctx.aver(b) is True
+            stream = torch.cuda.ExternalStream(ctx.stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ctx.set_profiling(True)
+            ctx.reset_kernel_times()
+            e0.record(stream)
+            for _ in range(steps):
+                ctx.aver(b)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            tot, cnt = ctx.kernel_time("hash")
+            hash_ms = tot / cnt
+            ctx.set_profiling(False)
+            ctx.close()
+            if inst == poslo.INST_AES:
+                aes = int(np.sum(2 * ((L + 32) // 16) + 2))           # MDC-2 blocks x 2 + the PRF's 2
+                work = {"unit": "G lookups/s", "per_launch": aes * AES_LOOKUPS, "pipe": "LSU (shared memory)",
+                        "peak_note": "32 table reads per clock per SM"}
+                peak = 32 * 152 * 2.07e9
+            else:
+                work = {"unit": "G ALU ops/s", "per_launch": compressions(msgs) * ALU_PER_COMPRESSION,
+                        "pipe": "ALU (LOP3/SHF/IADD3)", "peak_note": "64 ops per clock per SM"}
+                peak = 64 * 152 * 2.07e9
+            ach = work["per_launch"] / (hash_ms * 1e-3)
+            row[name] = {"entries_per_s": N_ENTRIES / (ms * 1e-3), "ms_per_aver": ms, "hash_kernel_ms": hash_ms,
+                         "hash_roofline": {"bound": work["pipe"], "achieved": ach / 1e9, "peak": peak / 1e9,
+                                           "unit": work["unit"], "frac": ach / peak,
+                                           "peak_source": work["peak_note"] + " at 2070 MHz, 152 SMs"}}
+        out[label] = row
+    return {"workload": "POSLO-C AVer, 2^20 entries, n2 = 256, n1 = 4096 (root disclosed), R~_i from pk, "
+                        "device-resident inputs", "results": out}
+
+
 # ------------------------------------------------------------------------------ config 5: serving
 
 SERVE_KEYS = 10000
@@ -544,6 +610,9 @@ def run_ours(args):
     serving = None
     if not args.no_serving and world == 1:
         serving = bench_serving(lambda: poslo.Context(device=device))
+    hash_bound = None
+    if not args.no_hash_bound and world == 1:
+        hash_bound = bench_hash_bound(device, steps=max(3, args.steps // 2), warmup=2)
 
     # end to end through the C ABI from pinned host memory
     p_msgs = torch.from_numpy(msgs.data).pin_memory()
@@ -605,6 +674,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": d2h},
             "roofline": roof,
             "multi_device": multi,
+            "hash_bound_poslo_c": hash_bound,
             "serving": serving,
             "int_peaks": peaks,
             "cpu_baseline": cpu,
@@ -626,6 +696,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-multi", action="store_true", help="skip the 4,096-device measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop measurement")
+    ap.add_argument("--no-hash-bound", action="store_true", help="skip the POSLO-C / POSLO+ hash-bound measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
