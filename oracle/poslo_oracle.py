@@ -562,6 +562,74 @@ def aver_c(Y_bytes: bytes, epochs: list, msgs: list, n2: int, s_agg: bytes, R_ag
 
 
 # ----------------------------------------------------------------------------------
+# POSLO-C distillation and selective batch verification (Fig. 3b)
+# ----------------------------------------------------------------------------------
+# Readings: epochs are numbered from 0 and processed in order; umbrella l covers the g =
+# n1 / n^u consecutive epochs [l g, (l+1) g) of the batch and is closed after the last of
+# them, valid or not (the listing tests "i = 0 mod floor(n1/n^u)" inside the valid branch,
+# which would merge two groups whenever a group ends with an invalid epoch, and SeBVer's U
+# mode verifies exactly one group per umbrella; its range "floor(n^u/n)" is read as g); an
+# umbrella collects the valid epochs of its group, so a group with none holds (0, O).
+
+@dataclass
+class CcdC:
+    sv: bytes                 # s~^v: sum of the valid epochs' s~_i mod q
+    Rv: bytes                 # R~^v: sum of their R~_i (encoded)
+    umbrellas: list           # [(s~^u, R~^u, l)] for l = 0 .. n^u - 1
+    invalid: list             # [(s~_i, R~_i, i)] for the invalid epochs, ascending i
+
+
+def distill_c(Y_bytes: bytes, epochs: list, msgs: list, n2: int, s_list: list, R_list: list, ds: list,
+              n_umbrella: int):
+    """POSLO-C.Distill over epochs (Fig. 3b, C.Distill, one call per epoch in order):
+    epoch i is verified on its own, b_i = C.AVer(pk, m_i, (s~_i, R~_i)); a valid epoch joins
+    ccd^v and its group's umbrella, an invalid one is listed in ccd^i.  Returns (b, ccd)."""
+    n1 = len(epochs)
+    if n_umbrella <= 0 or n1 % n_umbrella:
+        raise ValueError("n1 must be a multiple of n^u")
+    g = n1 // n_umbrella
+    b = []
+    sv, Rv = 0, IDENTITY
+    su, Ru = 0, IDENTITY
+    umbrellas, invalid = [], []
+    for k, i in enumerate(epochs):
+        ok = aver_c(Y_bytes, [i], [msgs[k]], n2, s_list[k], [R_list[k]], ds)
+        b.append(ok)
+        if ok:
+            si = int.from_bytes(s_list[k], "little")
+            Ri = decode_point(R_list[k])
+            sv, Rv = (sv + si) % Q, point_add(Rv, Ri)
+            su, Ru = (su + si) % Q, point_add(Ru, Ri)
+        else:
+            invalid.append((s_list[k], R_list[k], i))
+        if (k + 1) % g == 0:
+            umbrellas.append((scalar_to_bytes(su), encode_point(Ru), k // g))
+            su, Ru = 0, IDENTITY
+    return b, CcdC(scalar_to_bytes(sv), encode_point(Rv), umbrellas, invalid)
+
+
+def sebver_c(Y_bytes: bytes, epochs: list, msgs: list, n2: int, ccd: CcdC, ds: list, mode: str) -> list:
+    """POSLO-C.SeBVer (Fig. 3b): 'V' verifies every epoch outside ccd^i against ccd^v (one
+    bit); 'U' verifies, per umbrella, its group's epochs outside ccd^i against the umbrella
+    (one bit each); 'I' verifies each invalid epoch against its own sigma~_i (one bit each)."""
+    bad = {i for _, _, i in ccd.invalid}
+    pos = {i: k for k, i in enumerate(epochs)}
+    if mode == "V":
+        keep = [k for k, i in enumerate(epochs) if i not in bad]
+        return [aver_c(Y_bytes, [epochs[k] for k in keep], [msgs[k] for k in keep], n2, ccd.sv, ccd.Rv, ds)]
+    if mode == "U":
+        g = len(epochs) // len(ccd.umbrellas)
+        out = []
+        for su, Ru, l in ccd.umbrellas:
+            keep = [k for k in range(l * g, (l + 1) * g) if epochs[k] not in bad]
+            out.append(aver_c(Y_bytes, [epochs[k] for k in keep], [msgs[k] for k in keep], n2, su, Ru, ds))
+        return out
+    if mode == "I":
+        return [aver_c(Y_bytes, [i], [msgs[pos[i]]], n2, si, [Ri], ds) for si, Ri, i in ccd.invalid]
+    raise ValueError("mode must be V, U or I")
+
+
+# ----------------------------------------------------------------------------------
 # POSLO-F (Fig. 4) with the BPV generator (Definition 3)
 # ----------------------------------------------------------------------------------
 

@@ -483,3 +483,62 @@ def test_poslo_and_poslo_plus_differ():
     x0 = synth.random_bytes(3, "x0", 16).tobytes()
     assert O.entry_seed_sha(x0, 5) != O.entry_seed_aes(x0, 5)
     assert O.hash_to_scalar_sha(b"abc", x0) != O.hash_to_scalar_aes(b"abc", x0)
+
+
+# ------------------------------------------------------------------------------ POSLO-C Distill / SeBVer
+
+def _c_epochs(seed, D, n2, n1):
+    km = synth.key_material(seed)
+    sk, Y, epoch_R = O.kg_c(km.y, km.r, km.root, D, n2)
+    msgs = synth.messages(seed, n1 * n2, 1, 40)
+    ms = [[msgs.entry(i * n2 + j) for j in range(n2)] for i in range(n1)]
+    s_ep = [O.sig_c(sk, i, ms[i]) for i in range(n1)]
+    return Y, epoch_R[:n1], ms, s_ep, O.ds_root(km.root, D)
+
+
+def test_distill_c_all_valid_closed_forms():
+    """Every epoch valid: ccd^v is the aggregate signature of the batch (Agg, Fig. 3a), each
+    umbrella the aggregate of its group, ccd^i empty, SeBVer V and U accept."""
+    Y, R, ms, s_ep, ds = _c_epochs(51, 3, 4, 8)
+    b, ccd = O.distill_c(Y, list(range(8)), ms, 4, s_ep, R, ds, 2)
+    assert b == [True] * 8 and ccd.invalid == []
+    assert (ccd.sv, ccd.Rv) == (O.agg_scalars(s_ep), O.agg_points(R))
+    assert [(su, Ru, l) for su, Ru, l in ccd.umbrellas] == \
+        [(O.agg_scalars(s_ep[4 * l:4 * l + 4]), O.agg_points(R[4 * l:4 * l + 4]), l) for l in range(2)]
+    assert O.sebver_c(Y, list(range(8)), ms, 4, ccd, ds, "V") == [True]
+    assert O.sebver_c(Y, list(range(8)), ms, 4, ccd, ds, "U") == [True, True]
+    assert O.sebver_c(Y, list(range(8)), ms, 4, ccd, ds, "I") == []
+
+
+@pytest.mark.parametrize("k", range(8))
+def test_distill_c_each_epoch_tampered(k):
+    """Brute force over the tampered epoch: exactly that epoch is invalid (its own C.AVer
+    rejects), ccd^v and the umbrellas aggregate the others, V and U accept, I rejects it."""
+    Y, R, ms, s_ep, ds = _c_epochs(52, 3, 4, 8)
+    m = ms[k][2]
+    ms[k][2] = bytes([m[0] ^ 0x40]) + m[1:]
+    b, ccd = O.distill_c(Y, list(range(8)), ms, 4, s_ep, R, ds, 4)
+    assert b == [i != k for i in range(8)]
+    assert b == [O.aver_c(Y, [i], [ms[i]], 4, s_ep[i], [R[i]], ds) for i in range(8)]
+    assert [(si, Ri, i) for si, Ri, i in ccd.invalid] == [(s_ep[k], R[k], k)]
+    keep = [i for i in range(8) if i != k]
+    assert (ccd.sv, ccd.Rv) == (O.agg_scalars([s_ep[i] for i in keep]), O.agg_points([R[i] for i in keep]))
+    # umbrellas of g = 2 epochs: the tampered epoch's group holds its other epoch only
+    for su, Ru, l in ccd.umbrellas:
+        grp = [i for i in (2 * l, 2 * l + 1) if i != k]
+        assert (su, Ru) == (O.agg_scalars([s_ep[i] for i in grp]), O.agg_points([R[i] for i in grp]))
+    assert O.sebver_c(Y, list(range(8)), ms, 4, ccd, ds, "V") == [True]
+    assert O.sebver_c(Y, list(range(8)), ms, 4, ccd, ds, "U") == [True] * 4
+    assert O.sebver_c(Y, list(range(8)), ms, 4, ccd, ds, "I") == [False]
+
+
+def test_distill_c_whole_invalid_group_and_swapped_signatures():
+    # a group with no valid epoch keeps an empty umbrella (0, O); swapping two epochs'
+    # signatures makes both invalid, and SeBVer I rejects both
+    Y, R, ms, s_ep, ds = _c_epochs(53, 2, 4, 4)
+    s2 = [s_ep[1], s_ep[0], s_ep[2], s_ep[3]]
+    b, ccd = O.distill_c(Y, list(range(4)), ms, 4, s2, R, ds, 2)
+    assert b == [False, False, True, True]
+    assert ccd.umbrellas[0][:2] == (bytes(32), O.encode_point(O.IDENTITY))
+    assert O.sebver_c(Y, list(range(4)), ms, 4, ccd, ds, "U") == [True, True]
+    assert O.sebver_c(Y, list(range(4)), ms, 4, ccd, ds, "I") == [False, False]
