@@ -263,6 +263,38 @@ int poslo_msm(poslo_ctx* ctx, const uint8_t* points, const uint8_t* scalars, uin
  * the timing runs finish; takes tens of milliseconds per width at n = 2^20. */
 int poslo_msm_autotune(poslo_ctx* ctx, uint64_t n, uint32_t scalar_words, uint32_t* window_out);
 
+/* ---- POSLO-C distillation and selective batch verification (Fig. 3b) ------------------- */
+
+/* The distilled record ccd of a POSLO-C batch: the aggregate of its valid epochs (ccd^v),
+ * one umbrella aggregate per group of g = n1 / n_umbrella consecutive epochs over the
+ * group's valid epochs (ccd^u; a group with no valid epoch holds s = 0, R = identity), and
+ * the invalid epochs (ccd^i; their sigma~_i are the batch's own s~_i, R~_i).  All buffers
+ * belong to the caller (host memory). */
+typedef struct {
+  uint8_t* s_v;           /* 32 B: s~^v */
+  uint8_t* R_v;           /* 32 B: R~^v, encoded */
+  uint8_t* umbrellas;     /* n_umbrella * 64 B: s~^u || R~^u of group l at l * 64 */
+  uint64_t* invalid;      /* global epoch indices of ccd^i, ascending; room for cap */
+  uint64_t cap;
+  uint64_t n_invalid;     /* set by poslo_distill_c; read by poslo_sebver_c */
+} poslo_ccd_c;
+
+/* C.Distill (Fig. 3b) over a POSLO-C batch of n1 = n / n2 whole epochs, every epoch checked
+ * on its own: b_i = C.AVer(m_i, s~_i, R~_i).  batch->s holds the n1 per-epoch signatures
+ * s~_i (32 B each, epoch order) and batch->R the n1 R~_i of pk (R_count = n1).  n_umbrella
+ * must divide n1.  valid: n1 bytes (b_i).  EINVAL on a malformed batch or n_umbrella;
+ * EBUFSMALL (after filling everything else) if more than ccd->cap epochs are invalid. */
+int poslo_distill_c(poslo_ctx* ctx, const poslo_batch* batch, uint32_t n_umbrella, uint8_t* valid,
+                    poslo_ccd_c* ccd);
+
+/* SeBVer (Fig. 3b) of the same batch layout against a ccd: mode 'V' writes one bit (every
+ * epoch outside ccd^i against ccd^v), 'U' one bit per umbrella (its group's epochs outside
+ * ccd^i against the umbrella), 'I' one bit per invalid epoch (its messages against its own
+ * s~_i, R~_i from the batch).  bits: room for 1, n_umbrella or ccd->n_invalid bytes. */
+enum { POSLO_SEBVER_V = 'V', POSLO_SEBVER_U = 'U', POSLO_SEBVER_I = 'I' };
+int poslo_sebver_c(poslo_ctx* ctx, const poslo_batch* batch, uint32_t n_umbrella, const poslo_ccd_c* ccd,
+                   uint32_t mode, uint8_t* bits);
+
 /* ---- allocation-free variant ---------------------------------------------------------- */
 
 /* The paper has no counterpart to this entry point: it exists for callers that cannot

@@ -679,6 +679,17 @@ struct MultiCheckArgs {
 };
 __global__ void __launch_bounds__(128) k_multi_entry_check(const MultiCheckArgs a);
 __global__ void k_segment_any(const uint8_t* inv, const uint64_t* seg_start, const uint32_t* fl, uint8_t* out);
+// ---- POSLO-C distillation and SeBVer (k_ccd.cu) ----
+constexpr int kCcdThreads = 128;
+__global__ void __launch_bounds__(kCcdThreads) k_scalar_group_sums(const uint8_t* x, uint64_t G, uint64_t n,
+                                                                   const uint8_t* skip, uint32_t* out);
+__global__ void __launch_bounds__(kCcdThreads) k_point_group_sums(const uint32_t* pts, const uint8_t* bad, uint64_t G,
+                                                                  uint64_t n, const uint8_t* skip, uint8_t* enc);
+__global__ void __launch_bounds__(128) k_check_list(const uint32_t* e, const uint8_t* s, const uint32_t* pts,
+                                                    const uint8_t* bad, uint32_t n, const uint32_t* tableY,
+                                                    const uint32_t* tableG, uint8_t* ok);
+__global__ void k_gather32(const uint8_t* src, const uint64_t* idx, uint64_t n, uint8_t* dst);
+__global__ void k_flip(const uint8_t* ok, uint64_t n, uint8_t* flag);
 __global__ void k_device_to_entries(const uint8_t* dev_flag, const uint64_t* start, const uint8_t* badR,
                                     uint8_t* skip, int keep_flagged);
 constexpr uint32_t kFlagChunk = 8192;

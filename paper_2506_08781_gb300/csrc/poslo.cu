@@ -241,11 +241,11 @@ int validate_batch(poslo_ctx* ctx, const poslo_batch* b) {
 
 // Host inputs are copied R_t first: ev_staged marks their arrival, so the decoding (the
 // longest stage) starts while the messages are still on their way.
-int stage_batch(poslo_ctx* ctx, const poslo_batch* b, Staged& sb) {
+int stage_batch(poslo_ctx* ctx, const poslo_batch* b, Staged& sb, size_t s_bytes_override = 0) {
   int rc;
   const bool dev = b->on_device != 0;
   const void* p;
-  const size_t s_bytes = b->variant == POSLO_VARIANT_F ? 32 * b->n : 32;
+  const size_t s_bytes = s_bytes_override ? s_bytes_override : (b->variant == POSLO_VARIANT_F ? 32 * b->n : 32);
   const size_t R_bytes = 32 * (b->variant == POSLO_VARIANT_F ? b->n : b->R_count);
   if ((rc = stage(ctx, "R_in", b->R, R_bytes, dev, ctx->s_main, &p))) return rc;
   sb.R = static_cast<const uint8_t*>(p);
@@ -1380,6 +1380,186 @@ int poslo_msm_autotune(poslo_ctx* ctx, uint64_t n, uint32_t scalar_words, uint32
   if (window_out) *window_out = (uint32_t)best_c;
   return POSLO_OK;
 }
+
+// ---------------------------------------------------------------------------- POSLO-C ccd
+
+namespace {
+
+// 8 little-endian 32-bit limbs to 32 bytes.
+void store_le_words(const uint32_t* w, uint8_t* out) {
+  for (int k = 0; k < 8; ++k)
+    for (int b = 0; b < 4; ++b) out[4 * k + b] = (uint8_t)(w[k] >> (8 * b));
+}
+
+// Shared part of C.Distill and SeBVer: checks the batch (whole epochs, per-epoch s~_i and
+// R~_i), stages it, starts the key table, and leaves the per-epoch sums e~_i (n1 x 32 bytes,
+// limbs little-endian) in *esum.
+int ccd_common(poslo_ctx* ctx, const poslo_batch* batch, uint32_t n_umbrella, Staged& sb, uint64_t& n1,
+               uint32_t** tableY, uint8_t** esum) {
+  int rc;
+  if ((rc = validate_batch(ctx, batch))) return rc;
+  if (batch->variant != POSLO_VARIANT_C) return fail(ctx, POSLO_EINVAL, "distillation with ccd is POSLO-C");
+  n1 = batch->n / batch->n2;
+  if (n1 == 0) return fail(ctx, POSLO_EINVAL, "empty batch");
+  if (batch->R_count != n1) return fail(ctx, POSLO_EINVAL, "one R~_i per epoch is required");
+  if (n_umbrella == 0 || n1 % n_umbrella) return fail(ctx, POSLO_EINVAL, "n_umbrella must divide n1 = %llu",
+                                                      (unsigned long long)n1);
+  if ((rc = reset_status(ctx))) return rc;
+  if ((rc = stage_batch(ctx, batch, sb, 32 * n1))) return rc;
+  if ((rc = run_ytable(ctx, batch->Y, tableY))) return rc;
+  uint8_t* d_e;
+  if ((rc = ensure_t(ctx, "e_all", 32 * batch->n, &d_e))) return rc;
+  if ((rc = ensure_t(ctx, "ccd_esum", 32 * n1, esum))) return rc;
+  unsigned long long* hpart;
+  uint32_t nhb;
+  if ((rc = run_hash(ctx, batch, sb, d_e, false, false, nullptr, &hpart, &nhb))) return rc;
+  k_scalar_group_sums<<<(unsigned)n1, kCcdThreads, 0, ctx->s_main>>>(d_e, batch->n2, batch->n, nullptr,
+                                                                      reinterpret_cast<uint32_t*>(*esum));
+  ++ctx->launch_count;
+  CU(cudaGetLastError());
+  return POSLO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int poslo_distill_c(poslo_ctx* ctx, const poslo_batch* batch, uint32_t n_umbrella, uint8_t* valid,
+                    poslo_ccd_c* ccd) {
+  if (!ctx || !valid || !ccd || !ccd->s_v || !ccd->R_v || !ccd->umbrellas)
+    return fail(ctx, POSLO_EINVAL, "bad distill_c arguments");
+  int rc;
+  Staged sb;
+  uint64_t n1 = 0;
+  uint32_t* tableY;
+  uint8_t* esum;
+  if ((rc = ccd_common(ctx, batch, n_umbrella, sb, n1, &tableY, &esum))) return rc;
+  const uint64_t g = n1 / n_umbrella;
+  uint32_t *pts, *ppart, npb, *words;
+  uint8_t *badR, *ok, *inv, *encs;
+  uint64_t* d_idx;
+  if ((rc = ensure_t(ctx, "ccd_pts", 4 * kPtsWords * n1, &pts))) return rc;
+  if ((rc = ensure_t(ctx, "ccd_badR", n1, &badR))) return rc;
+  if ((rc = ensure_t(ctx, "ccd_ok", 2 * n1, &ok))) return rc;
+  inv = ok + n1;
+  if ((rc = ensure_t(ctx, "ccd_words", 32 * (1 + (size_t)n_umbrella), &words))) return rc;
+  if ((rc = ensure_t(ctx, "ccd_encs", 32 * (1 + (size_t)n_umbrella), &encs))) return rc;
+  const uint64_t capn = std::max<uint64_t>(std::min<uint64_t>(ccd->cap, n1), 1);
+  if ((rc = ensure_t(ctx, "ccd_idx", 8 * capn + 8, &d_idx))) return rc;
+  uint64_t* d_cnt = d_idx + capn;
+  if ((rc = run_points(ctx, sb.R, n1, pts, badR, &ppart, &npb, ctx->ev_staged))) return rc;
+  CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_points, 0));
+  CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_table, 0));
+  // b_i for every epoch, then ccd^v (group 0) and the umbrellas (groups 1..n^u)
+  k_check_list<<<(unsigned)((4 * n1 + 127) / 128), 128, 0, ctx->s_main>>>(
+      reinterpret_cast<const uint32_t*>(esum), sb.s, pts, badR, (uint32_t)n1, tableY, ctx->tableG, ok);
+  k_flip<<<(unsigned)((n1 + 255) / 256), 256, 0, ctx->s_main>>>(ok, n1, inv);
+  k_scalar_group_sums<<<1, kCcdThreads, 0, ctx->s_main>>>(sb.s, n1, n1, inv, words);
+  k_point_group_sums<<<1, kCcdThreads, 0, ctx->s_main>>>(pts, badR, n1, n1, inv, encs);
+  k_scalar_group_sums<<<n_umbrella, kCcdThreads, 0, ctx->s_main>>>(sb.s, g, n1, inv, words + 8);
+  k_point_group_sums<<<n_umbrella, kCcdThreads, 0, ctx->s_main>>>(pts, badR, g, n1, inv, encs + 32);
+  ctx->launch_count += 6;
+  CU(cudaGetLastError());
+  const uint64_t first_epoch = batch->first_index / batch->n2;
+  if ((rc = run_compact(ctx, inv, n1, first_epoch, d_idx, std::min<uint64_t>(ccd->cap, n1), d_cnt))) return rc;
+  std::vector<uint32_t> hw(8 * (1 + (size_t)n_umbrella));
+  std::vector<uint8_t> he(32 * (1 + (size_t)n_umbrella));
+  uint64_t cnt = 0;
+  CU(cudaMemcpyAsync(valid, ok, n1, cudaMemcpyDeviceToHost, ctx->s_main));
+  CU(cudaMemcpyAsync(hw.data(), words, 4 * hw.size(), cudaMemcpyDeviceToHost, ctx->s_main));
+  CU(cudaMemcpyAsync(he.data(), encs, he.size(), cudaMemcpyDeviceToHost, ctx->s_main));
+  CU(cudaMemcpyAsync(&cnt, d_cnt, 8, cudaMemcpyDeviceToHost, ctx->s_main));
+  if ((rc = check_status(ctx))) return rc;
+  store_le_words(hw.data(), ccd->s_v);
+  memcpy(ccd->R_v, he.data(), 32);
+  for (uint32_t l = 0; l < n_umbrella; ++l) {
+    store_le_words(hw.data() + 8 * (1 + (size_t)l), ccd->umbrellas + 64 * (size_t)l);
+    memcpy(ccd->umbrellas + 64 * (size_t)l + 32, he.data() + 32 * (1 + (size_t)l), 32);
+  }
+  const uint64_t got = std::min(cnt, ccd->cap);
+  if (got && ccd->invalid) CU(cudaMemcpy(ccd->invalid, d_idx, 8 * got, cudaMemcpyDeviceToHost));
+  ccd->n_invalid = cnt;
+  if (cnt > ccd->cap) return fail(ctx, POSLO_EBUFSMALL, "%llu invalid epochs, room for %llu",
+                                  (unsigned long long)cnt, (unsigned long long)ccd->cap);
+  return POSLO_OK;
+}
+
+int poslo_sebver_c(poslo_ctx* ctx, const poslo_batch* batch, uint32_t n_umbrella, const poslo_ccd_c* ccd,
+                   uint32_t mode, uint8_t* bits) {
+  if (!ctx || !ccd || !bits || (mode != POSLO_SEBVER_V && mode != POSLO_SEBVER_U && mode != POSLO_SEBVER_I) ||
+      (ccd->n_invalid && !ccd->invalid) || (mode == POSLO_SEBVER_V && (!ccd->s_v || !ccd->R_v)) ||
+      (mode == POSLO_SEBVER_U && !ccd->umbrellas))
+    return fail(ctx, POSLO_EINVAL, "bad sebver_c arguments");
+  int rc;
+  Staged sb;
+  uint64_t n1 = 0;
+  uint32_t* tableY;
+  uint8_t* esum;
+  if ((rc = ccd_common(ctx, batch, n_umbrella, sb, n1, &tableY, &esum))) return rc;
+  const uint64_t g = n1 / n_umbrella;
+  const uint64_t first_epoch = batch->first_index / batch->n2;
+  // the epochs of ccd^i, as positions in the batch
+  std::vector<uint8_t> mask(n1, 0);
+  std::vector<uint64_t> pos(ccd->n_invalid);
+  for (uint64_t k = 0; k < ccd->n_invalid; ++k) {
+    const uint64_t i = ccd->invalid[k];
+    if (i < first_epoch || i - first_epoch >= n1) return fail(ctx, POSLO_EINVAL, "invalid epoch %llu outside the batch",
+                                                              (unsigned long long)i);
+    pos[k] = i - first_epoch;
+    mask[pos[k]] = 1;
+  }
+  const uint64_t nchk = mode == POSLO_SEBVER_V ? 1 : (mode == POSLO_SEBVER_U ? n_umbrella : ccd->n_invalid);
+  if (nchk == 0) return check_status(ctx);
+  uint8_t *d_mask, *s_chk, *R_chk, *bad, *d_bits;
+  uint32_t *e_chk, *pts, *ppart, npb;
+  uint64_t* d_pos;
+  if ((rc = ensure_t(ctx, "seb_mask", n1, &d_mask))) return rc;
+  if ((rc = ensure_t(ctx, "seb_pos", 8 * std::max<uint64_t>(ccd->n_invalid, 1), &d_pos))) return rc;
+  if ((rc = ensure_t(ctx, "seb_e", 32 * nchk, &e_chk))) return rc;
+  if ((rc = ensure_t(ctx, "seb_s", 32 * nchk, &s_chk))) return rc;
+  if ((rc = ensure_t(ctx, "seb_R", 32 * nchk, &R_chk))) return rc;
+  if ((rc = ensure_t(ctx, "seb_pts", 4 * kPtsWords * nchk, &pts))) return rc;
+  if ((rc = ensure_t(ctx, "seb_bad", 2 * nchk, &bad))) return rc;
+  d_bits = bad + nchk;
+  CU(cudaMemcpyAsync(d_mask, mask.data(), n1, cudaMemcpyHostToDevice, ctx->s_main));
+  if (mode == POSLO_SEBVER_V) {
+    k_scalar_group_sums<<<1, kCcdThreads, 0, ctx->s_main>>>(esum, n1, n1, d_mask, e_chk);
+    CU(cudaMemcpyAsync(s_chk, ccd->s_v, 32, cudaMemcpyHostToDevice, ctx->s_main));
+    CU(cudaMemcpyAsync(R_chk, ccd->R_v, 32, cudaMemcpyHostToDevice, ctx->s_main));
+    ++ctx->launch_count;
+  } else if (mode == POSLO_SEBVER_U) {
+    k_scalar_group_sums<<<n_umbrella, kCcdThreads, 0, ctx->s_main>>>(esum, g, n1, d_mask, e_chk);
+    ++ctx->launch_count;
+    std::vector<uint8_t> hs(32 * nchk), hR(32 * nchk);
+    for (uint64_t l = 0; l < nchk; ++l) {
+      memcpy(hs.data() + 32 * l, ccd->umbrellas + 64 * l, 32);
+      memcpy(hR.data() + 32 * l, ccd->umbrellas + 64 * l + 32, 32);
+    }
+    CU(cudaMemcpyAsync(s_chk, hs.data(), hs.size(), cudaMemcpyHostToDevice, ctx->s_main));
+    CU(cudaMemcpyAsync(R_chk, hR.data(), hR.size(), cudaMemcpyHostToDevice, ctx->s_main));
+    CU(cudaStreamSynchronize(ctx->s_main));   // the host staging vectors end here
+  } else {
+    CU(cudaMemcpyAsync(d_pos, pos.data(), 8 * nchk, cudaMemcpyHostToDevice, ctx->s_main));
+    const unsigned gb = (unsigned)((2 * nchk + 255) / 256);
+    k_gather32<<<gb, 256, 0, ctx->s_main>>>(esum, d_pos, nchk, reinterpret_cast<uint8_t*>(e_chk));
+    k_gather32<<<gb, 256, 0, ctx->s_main>>>(sb.s, d_pos, nchk, s_chk);
+    k_gather32<<<gb, 256, 0, ctx->s_main>>>(sb.R, d_pos, nchk, R_chk);
+    ctx->launch_count += 3;
+    CU(cudaStreamSynchronize(ctx->s_main));   // pos ends here
+  }
+  CU(cudaGetLastError());
+  if ((rc = run_points(ctx, R_chk, nchk, pts, bad, &ppart, &npb))) return rc;
+  CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_points, 0));
+  CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_table, 0));
+  k_check_list<<<(unsigned)((4 * nchk + 127) / 128), 128, 0, ctx->s_main>>>(e_chk, s_chk, pts, bad, (uint32_t)nchk,
+                                                                             tableY, ctx->tableG, d_bits);
+  ++ctx->launch_count;
+  CU(cudaGetLastError());
+  CU(cudaMemcpyAsync(bits, d_bits, nchk, cudaMemcpyDeviceToHost, ctx->s_main));
+  return check_status(ctx);
+}
+
+}  // extern "C"
 
 // ---------------------------------------------------------------------------- multi-device
 

@@ -29,7 +29,7 @@ EXPORTS = [
     "poslo_keygen_c", "poslo_keygen_f", "poslo_sign_c", "poslo_sign_f", "poslo_disclose",
     "poslo_aver", "poslo_distill", "poslo_epoch_seeds", "poslo_hash_entries", "poslo_msm", "poslo_msm_autotune",
     "poslo_set_profiling", "poslo_kernel_time", "poslo_reset_kernel_times",
-    "poslo_hash_entries_noalloc", "poslo_aver_multi",
+    "poslo_hash_entries_noalloc", "poslo_aver_multi", "poslo_distill_c", "poslo_sebver_c",
     "poslo_serve_start", "poslo_serve_stop", "poslo_register_key", "poslo_submit", "poslo_poll",
     "poslo_serve_stats",
 ]
@@ -57,6 +57,11 @@ class Request(C.Structure):
     _fields_ = [("key_id", C.c_uint32), ("n2", C.c_uint32), ("first_index", C.c_uint64), ("msgs", C.c_void_p),
                 ("offs", C.c_void_p), ("n", C.c_uint64), ("s", C.c_void_p), ("R", C.c_void_p), ("ds", C.c_void_p),
                 ("ds_nodes", C.c_uint32)]
+
+
+class CcdC(C.Structure):
+    _fields_ = [("s_v", C.c_void_p), ("R_v", C.c_void_p), ("umbrellas", C.c_void_p), ("invalid", C.c_void_p),
+                ("cap", C.c_uint64), ("n_invalid", C.c_uint64)]
 
 
 class Batch(C.Structure):
@@ -100,6 +105,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "poslo_reset_kernel_times": ([vp], None),
         "poslo_hash_entries_noalloc": ([C.POINTER(Batch), u8p, vp], C.c_int),
         "poslo_aver_multi": ([vp, C.POINTER(MultiBatch), u8p, vp, u64, C.POINTER(u64)], C.c_int),
+        "poslo_distill_c": ([vp, C.POINTER(Batch), u32, u8p, C.POINTER(CcdC)], C.c_int),
+        "poslo_sebver_c": ([vp, C.POINTER(Batch), u32, C.POINTER(CcdC), u32, u8p], C.c_int),
         "poslo_serve_start": ([vp, u32, u32, u64], C.c_int),
         "poslo_serve_stop": ([vp], C.c_int),
         "poslo_register_key": ([vp, u8p, C.POINTER(u32)], C.c_int),
@@ -332,6 +339,38 @@ class Context:
         cnt = C.c_uint64()
         self._check(self.lib.poslo_aver_multi(self.h, C.byref(mb), _ptr(acc), _ptr(pairs), cap, C.byref(cnt)))
         return acc.astype(bool), pairs[:2 * cnt.value].reshape(-1, 2).copy()
+
+    # ------------------------------------------------------------------ POSLO-C ccd (Fig. 3b)
+    def distill_c(self, b: BatchData, n_umbrella: int, cap: int | None = None):
+        """C.Distill: returns (valid per epoch, ccd) with ccd = dict(s_v, R_v, umbrellas=[(s, R)],
+        invalid=[global epoch indices])."""
+        n1 = b.n // b.n2
+        cap = n1 if cap is None else cap
+        valid = np.zeros(max(n1, 1), np.uint8)
+        sv, Rv = np.zeros(32, np.uint8), np.zeros(32, np.uint8)
+        umb = np.zeros(64 * max(n_umbrella, 1), np.uint8)
+        inv = np.zeros(max(cap, 1), np.uint64)
+        c = CcdC(_ptr(sv), _ptr(Rv), _ptr(umb), _ptr(inv), cap, 0)
+        cb = self._cbatch(b)
+        self._check(self.lib.poslo_distill_c(self.h, C.byref(cb), n_umbrella, _ptr(valid), C.byref(c)))
+        ccd = dict(s_v=sv.tobytes(), R_v=Rv.tobytes(),
+                   umbrellas=[(umb[64 * l:64 * l + 32].tobytes(), umb[64 * l + 32:64 * l + 64].tobytes())
+                              for l in range(n_umbrella)],
+                   invalid=[int(x) for x in inv[:c.n_invalid]])
+        return [bool(v) for v in valid[:n1]], ccd
+
+    def sebver_c(self, b: BatchData, n_umbrella: int, ccd: dict, mode: str):
+        """SeBVer in mode 'V', 'U' or 'I' against a ccd from distill_c; returns the bits."""
+        sv = np.frombuffer(ccd["s_v"], np.uint8).copy()
+        Rv = np.frombuffer(ccd["R_v"], np.uint8).copy()
+        umb = np.frombuffer(b"".join(s + R for s, R in ccd["umbrellas"]) or bytes(64), np.uint8).copy()
+        inv = np.asarray(ccd["invalid"] or [0], np.uint64)
+        c = CcdC(_ptr(sv), _ptr(Rv), _ptr(umb), _ptr(inv), len(ccd["invalid"]), len(ccd["invalid"]))
+        n = {"V": 1, "U": n_umbrella, "I": len(ccd["invalid"])}[mode]
+        bits = np.zeros(max(n, 1), np.uint8)
+        cb = self._cbatch(b)
+        self._check(self.lib.poslo_sebver_c(self.h, C.byref(cb), n_umbrella, C.byref(c), ord(mode), _ptr(bits)))
+        return [bool(x) for x in bits[:n]]
 
     # ------------------------------------------------------------------ serving
     def serve_start(self, workers: int = 2, max_batch_devices: int = 4096, max_batch_entries: int = 1 << 22):
