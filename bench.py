@@ -244,6 +244,43 @@ Q_ORDER = 2 ** 252 + 27742317777372353535851937790883648493   # order of the gro
 AES_LOOKUPS = 10 * 16 + 10 * 4          # shared-memory table reads per AES-128 (rounds + key schedule)
 
 
+CCD_UMBRELLAS = 64
+
+
+def bench_distill_c(ctx_inst, device, km, msgs, Y, epoch_R, s_ep, steps, warmup) -> dict:
+    """C.Distill (Fig. 3b) of the same 2^20 entries with 0.1 % of them flipped by one byte
+    (config 3's tamper rate), 64 umbrellas, then SeBVer in each mode."""
+    import torch
+    from paper_2506_08781_gb300 import poslo, synth
+    plan = synth.tamper_plan(SEED + 8, msgs, round(0.001 * msgs.n))
+    bad = synth.apply_tamper(msgs, plan)
+    want = sorted({int(t) // N2 for t in plan.idx})
+    ctx = poslo.Context(device=device, instantiation=ctx_inst)
+    b = ctx.make_batch(poslo.VARIANT_C, N2, Y, torch.from_numpy(bad.data).cuda(),
+                       torch.from_numpy(bad.offs.view(np.int64)).cuda(),
+                       torch.from_numpy(np.ascontiguousarray(s_ep).reshape(-1).copy()).cuda(),
+                       torch.from_numpy(np.asarray(epoch_R, np.uint8).copy()).cuda(), struct.pack("<II", D, 0) + km.root)
+    torch.cuda.synchronize()
+    for _ in range(warmup):
+        valid, ccd = ctx.distill_c(b, CCD_UMBRELLAS)
+    assert ccd["invalid"] == want, "C.Distill differs from the tamper plan"
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        ctx.distill_c(b, CCD_UMBRELLAS)
+    dms = (time.perf_counter() - t0) / steps * 1e3
+    out = {"invalid_epochs": len(want), "umbrellas": CCD_UMBRELLAS, "ms_distill": dms,
+           "entries_per_s_distill": N_ENTRIES / (dms * 1e-3)}
+    for mode in "VUI":
+        bits = ctx.sebver_c(b, CCD_UMBRELLAS, ccd, mode)
+        assert all(bits) if mode != "I" else not any(bits)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            ctx.sebver_c(b, CCD_UMBRELLAS, ccd, mode)
+        out[f"ms_sebver_{mode}"] = (time.perf_counter() - t0) / steps * 1e3
+    ctx.close()
+    return out
+
+
 def bench_hash_bound(device: int, steps: int, warmup: int) -> dict:
     """POSLO-C AVer (Fig. 3a with the epochs' R~_i from pk): hashing of every entry, one
     aggregate check, no per-entry group work -- the paper's PAVer workload -- at 2^20 entries
@@ -299,6 +336,9 @@ def bench_hash_bound(device: int, steps: int, warmup: int) -> dict:
                          "hash_roofline": {"bound": work["pipe"], "achieved": ach / 1e9, "peak": peak / 1e9,
                                            "unit": work["unit"], "frac": ach / peak,
                                            "peak_source": work["peak_note"] + " at 2070 MHz, 152 SMs"}}
+            if label.startswith("U"):
+                row[name]["distill_c"] = bench_distill_c(ctx_inst=inst, device=device, km=km, msgs=msgs, Y=Y,
+                                                         epoch_R=epoch_R, s_ep=s_ep, steps=steps, warmup=warmup)
         out[label] = row
     return {"workload": "POSLO-C AVer, 2^20 entries, n2 = 256, n1 = 4096 (root disclosed), R~_i from pk, "
                         "device-resident inputs", "results": out}
