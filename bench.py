@@ -238,6 +238,49 @@ def bench_multi(ctx, steps: int, warmup: int) -> dict:
             "invalid_found": len(got), "setup_s": setup_s, "msm_window": msm_window, "stages": stages}
 
 
+# ------------------------------------------------------------------------------ out of core
+
+STREAM_CHUNKS = 8                      # 8 x 2^20 entries (1.2 GB of messages) from pinned host memory
+STREAM_D = 15                          # n1 = 32,768 epochs of 256 entries
+
+
+def bench_stream(device: int) -> dict:
+    """Out-of-core AVer + Distill (poslo_distill_stream) of 8 x 2^20 POSLO-F entries held in
+    pinned host memory, verified 2^20 entries at a time while the next chunk is copied; the
+    per-chunk workload is config 2's (the messages repeat, the signatures do not: each chunk
+    is signed at its own global indices)."""
+    import torch
+    from paper_2506_08781_gb300 import poslo, synth
+    ctx = poslo.Context(device=device)
+    km, msgs, subsets, _ = make_workload()
+    Y, bpv_R = ctx.keygen_f(km.y, km.bpv_r)
+    n = STREAM_CHUNKS * N_ENTRIES
+    s_all = np.empty((STREAM_CHUNKS, 32 * N_ENTRIES), np.uint8)
+    R_all = np.empty((STREAM_CHUNKS, 32 * N_ENTRIES), np.uint8)
+    for k in range(STREAM_CHUNKS):
+        s_all[k], R_all[k] = ctx.sign_f(km.y, km.root, STREAM_D, N2, km.bpv_r, bpv_R, subsets, msgs.data, msgs.offs,
+                                        first_index=k * N_ENTRIES)
+    L = int(msgs.offs[-1])
+    offs = np.concatenate([msgs.offs[:-1].astype(np.int64) + k * L for k in range(STREAM_CHUNKS)] +
+                          [np.array([STREAM_CHUNKS * L], np.int64)])
+    p_msgs = torch.from_numpy(np.tile(msgs.data, STREAM_CHUNKS)).pin_memory()
+    p_offs = torch.from_numpy(offs).pin_memory()
+    p_s = torch.from_numpy(s_all.reshape(-1)).pin_memory()
+    p_R = torch.from_numpy(R_all.reshape(-1)).pin_memory()
+    b = ctx.make_batch(poslo.VARIANT_F, N2, Y, p_msgs, p_offs, p_s, p_R, struct.pack("<II", STREAM_D, 0) + km.root)
+    acc, idx = ctx.distill_stream(b, N_ENTRIES)           # warm-up
+    assert acc and len(idx) == 0
+    t0 = time.perf_counter()
+    acc, idx = ctx.distill_stream(b, N_ENTRIES)
+    wall = time.perf_counter() - t0
+    ctx.close()
+    host_bytes = int(p_msgs.numel() + p_offs.numel() * 8 + p_s.numel() + p_R.numel())
+    per_entry = host_bytes / n
+    return {"workload": f"{n} POSLO-F entries (|m|~U[32,256] B) in pinned host memory, chunks of {N_ENTRIES}",
+            "entries_per_s": n / wall, "wall_s": wall, "host_GB_per_s": host_bytes / wall / 1e9,
+            "bytes_per_entry": per_entry, "s_per_TB_of_log_data": 1e12 / per_entry / (n / wall)}
+
+
 # ------------------------------------------------------------------------------ POSLO-C, hash-bound
 
 Q_ORDER = 2 ** 252 + 27742317777372353535851937790883648493   # order of the group (edwards25519)
@@ -653,6 +696,9 @@ def run_ours(args):
     hash_bound = None
     if not args.no_hash_bound and world == 1:
         hash_bound = bench_hash_bound(device, steps=max(3, args.steps // 2), warmup=2)
+    stream = None
+    if not args.no_stream and world == 1:
+        stream = bench_stream(device)
 
     # end to end through the C ABI from pinned host memory
     p_msgs = torch.from_numpy(msgs.data).pin_memory()
@@ -715,6 +761,7 @@ def run_ours(args):
             "roofline": roof,
             "multi_device": multi,
             "hash_bound_poslo_c": hash_bound,
+            "out_of_core": stream,
             "serving": serving,
             "int_peaks": peaks,
             "cpu_baseline": cpu,
@@ -737,6 +784,7 @@ def main():
     ap.add_argument("--no-multi", action="store_true", help="skip the 4,096-device measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop measurement")
     ap.add_argument("--no-hash-bound", action="store_true", help="skip the POSLO-C / POSLO+ hash-bound measurement")
+    ap.add_argument("--no-stream", action="store_true", help="skip the out-of-core streaming measurement")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

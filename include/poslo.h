@@ -263,6 +263,20 @@ int poslo_msm(poslo_ctx* ctx, const uint8_t* points, const uint8_t* scalars, uin
  * the timing runs finish; takes tens of milliseconds per width at n = 2^20. */
 int poslo_msm_autotune(poslo_ctx* ctx, uint64_t n, uint32_t scalar_words, uint32_t* window_out);
 
+/* ---- out-of-core verification --------------------------------------------------------- */
+
+/* AVer + Distill of a POSLO-F batch held in HOST memory, chunk_entries entries at a time
+ * (the last chunk shorter), for logs larger than device memory (Sec. 7.4 verifies 1 TB of
+ * log data chunk by chunk).  While chunk k is verified, chunk k+1 is copied on a separate
+ * stream into the other of two staging buffers; with pinned host memory the copies overlap
+ * the verification, with pageable memory they are correct but serialised.  The result equals
+ * poslo_distill over the whole batch: the invalid entries' global indices, ascending (room
+ * for cap; EBUFSMALL after counting them all if more), and *accept = 1 iff there are none.
+ * Device memory: two chunks of inputs plus poslo_distill's workspace for one chunk.  EINVAL
+ * for a device-resident or POSLO-C batch, chunk_entries = 0 or decreasing offsets. */
+int poslo_distill_stream(poslo_ctx* ctx, const poslo_batch* batch, uint64_t chunk_entries, uint8_t* accept,
+                         uint64_t* invalid_idx, uint64_t cap, uint64_t* n_invalid);
+
 /* ---- POSLO-C distillation and selective batch verification (Fig. 3b) ------------------- */
 
 /* The distilled record ccd of a POSLO-C batch: the aggregate of its valid epochs (ccd^v),

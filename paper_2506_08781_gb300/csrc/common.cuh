@@ -690,6 +690,7 @@ __global__ void __launch_bounds__(128) k_check_list(const uint32_t* e, const uin
                                                     const uint32_t* tableG, uint8_t* ok);
 __global__ void k_gather32(const uint8_t* src, const uint64_t* idx, uint64_t n, uint8_t* dst);
 __global__ void k_flip(const uint8_t* ok, uint64_t n, uint8_t* flag);
+__global__ void k_offs_sub(uint64_t* offs, uint64_t n, uint64_t base);
 __global__ void k_device_to_entries(const uint8_t* dev_flag, const uint64_t* start, const uint8_t* badR,
                                     uint8_t* skip, int keep_flagged);
 constexpr uint32_t kFlagChunk = 8192;

@@ -46,6 +46,12 @@ __global__ void k_epoch_seeds_multi(const DsNode* ds_all, const uint32_t* ds_off
   reinterpret_cast<uint4*>(seeds)[sidx] = make_uint4(x[0], x[1], x[2], x[3]);
 }
 
+// offs[t] -= base for t < n (a chunk's offsets made relative to its first message byte).
+__global__ void k_offs_sub(uint64_t* offs, uint64_t n, uint64_t base) {
+  const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) offs[t] -= base;   // a decreasing offset wraps and is flagged by k_hash
+}
+
 // Concatenated offsets: raw holds each device's n_d + 1 offsets at slot[d]; entry k of
 // device d becomes msg_base[d] + raw[slot[d] + k] - raw[slot[d]] at position start[d] + k.
 __global__ void k_rebase_offs(const uint64_t* raw, const uint64_t* slot, const uint64_t* start,

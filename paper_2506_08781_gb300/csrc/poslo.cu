@@ -697,6 +697,9 @@ int poslo_create(const poslo_params* params, poslo_ctx** out) {
   if (cudaStreamCreateWithFlags(&ctx->s_main, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&ctx->s_table, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&ctx->s_points, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->s_copy, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_copy[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_copy[1], cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_table, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_points, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_main, cudaEventDisableTiming) != cudaSuccess ||
@@ -741,6 +744,9 @@ void poslo_destroy(poslo_ctx* ctx) {
   if (ctx->s_main) cudaStreamDestroy(ctx->s_main);
   if (ctx->s_table) cudaStreamDestroy(ctx->s_table);
   if (ctx->s_points) cudaStreamDestroy(ctx->s_points);
+  if (ctx->s_copy) cudaStreamDestroy(ctx->s_copy);
+  for (cudaEvent_t e : ctx->ev_copy)
+    if (e) cudaEventDestroy(e);
   delete ctx;
 }
 
@@ -1380,6 +1386,88 @@ int poslo_msm_autotune(poslo_ctx* ctx, uint64_t n, uint32_t scalar_words, uint32
   if (window_out) *window_out = (uint32_t)best_c;
   return POSLO_OK;
 }
+
+// ---------------------------------------------------------------------------- out of core
+
+extern "C" {
+
+int poslo_distill_stream(poslo_ctx* ctx, const poslo_batch* batch, uint64_t chunk_entries, uint8_t* accept,
+                         uint64_t* invalid_idx, uint64_t cap, uint64_t* n_invalid) {
+  if (!ctx || !accept || !n_invalid || chunk_entries == 0) return fail(ctx, POSLO_EINVAL, "bad distill_stream arguments");
+  int rc;
+  if ((rc = validate_batch(ctx, batch))) return rc;
+  if (batch->variant != POSLO_VARIANT_F) return fail(ctx, POSLO_EINVAL, "streaming Distill is entry-granular: POSLO-F");
+  if (batch->on_device) return fail(ctx, POSLO_EINVAL, "streaming takes a batch in host memory");
+  const uint64_t n = batch->n;
+  const uint64_t nchunks = n ? (n + chunk_entries - 1) / chunk_entries : 0;
+  uint64_t max_bytes = 1, max_n = 1;
+  for (uint64_t k = 0; k < nchunks; ++k) {   // offsets inside a chunk are checked on the device
+    const uint64_t lo = k * chunk_entries, hi = std::min(n, lo + chunk_entries);
+    if (batch->offs[hi] < batch->offs[lo]) return fail(ctx, POSLO_EINVAL, "offsets decrease in chunk %llu",
+                                                       (unsigned long long)k);
+    max_bytes = std::max<uint64_t>(max_bytes, batch->offs[hi] - batch->offs[lo]);
+    max_n = std::max(max_n, hi - lo);
+  }
+  // two sets of staging buffers: messages, offsets (rebased to the chunk), s, R
+  uint8_t *msgs[2], *sv[2], *Rv[2];
+  uint64_t* offs[2];
+  for (int b = 0; b < 2; ++b) {
+    const std::string tag = b ? "1" : "0";
+    if ((rc = ensure_t(ctx, ("st_msgs" + tag).c_str(), max_bytes, &msgs[b]))) return rc;
+    if ((rc = ensure_t(ctx, ("st_offs" + tag).c_str(), 8 * (max_n + 1), &offs[b]))) return rc;
+    if ((rc = ensure_t(ctx, ("st_s" + tag).c_str(), 32 * max_n, &sv[b]))) return rc;
+    if ((rc = ensure_t(ctx, ("st_R" + tag).c_str(), 32 * max_n, &Rv[b]))) return rc;
+  }
+  // chunk k's inputs go to set k % 2 on the copy stream; its offsets are rebased there too
+  auto issue = [&](uint64_t k) -> int {
+    const int b = (int)(k & 1);
+    const uint64_t lo = k * chunk_entries, hi = std::min(n, lo + chunk_entries), m = hi - lo;
+    const uint64_t base = batch->offs[lo];
+    CU(cudaMemcpyAsync(msgs[b], batch->msgs + base, batch->offs[hi] - base, cudaMemcpyHostToDevice, ctx->s_copy));
+    CU(cudaMemcpyAsync(offs[b], batch->offs + lo, 8 * (m + 1), cudaMemcpyHostToDevice, ctx->s_copy));
+    CU(cudaMemcpyAsync(sv[b], batch->s + 32 * lo, 32 * m, cudaMemcpyHostToDevice, ctx->s_copy));
+    CU(cudaMemcpyAsync(Rv[b], batch->R + 32 * lo, 32 * m, cudaMemcpyHostToDevice, ctx->s_copy));
+    k_offs_sub<<<(unsigned)((m + 1 + 255) / 256), 256, 0, ctx->s_copy>>>(offs[b], m + 1, base);
+    ++ctx->launch_count;
+    CU(cudaGetLastError());
+    CU(cudaEventRecord(ctx->ev_copy[b], ctx->s_copy));
+    return POSLO_OK;
+  };
+  uint64_t total = 0;
+  if (nchunks && (rc = issue(0))) return rc;
+  for (uint64_t k = 0; k < nchunks; ++k) {
+    const int b = (int)(k & 1);
+    const uint64_t lo = k * chunk_entries, hi = std::min(n, lo + chunk_entries);
+    // chunk k's verification waits for its copies; chunk k+1's copies start meanwhile (the
+    // other set is free: chunk k-1's verification has returned)
+    CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_copy[b], 0));
+    if (k + 1 < nchunks && (rc = issue(k + 1))) return rc;
+    poslo_batch view = *batch;
+    view.msgs = msgs[b];
+    view.offs = offs[b];
+    view.n = hi - lo;
+    view.first_index = batch->first_index + lo;
+    view.s = sv[b];
+    view.R = Rv[b];
+    view.R_count = hi - lo;
+    view.on_device = 1;
+    const uint64_t room = invalid_idx ? (total < cap ? cap - total : 0) : 0;
+    uint64_t got = 0;
+    rc = poslo_distill(ctx, &view, invalid_idx ? invalid_idx + std::min(total, cap) : nullptr, room, &got, nullptr,
+                       nullptr);
+    if (rc != POSLO_OK && rc != POSLO_EBUFSMALL) return rc;
+    total += got;
+  }
+  CU(cudaStreamSynchronize(ctx->s_copy));
+  *n_invalid = total;
+  *accept = total == 0 ? 1 : 0;
+  if (total > cap || (total && !invalid_idx))
+    return fail(ctx, POSLO_EBUFSMALL, "%llu invalid entries, room for %llu", (unsigned long long)total,
+                (unsigned long long)cap);
+  return POSLO_OK;
+}
+
+}  // extern "C"
 
 // ---------------------------------------------------------------------------- POSLO-C ccd
 

@@ -29,7 +29,7 @@ EXPORTS = [
     "poslo_keygen_c", "poslo_keygen_f", "poslo_sign_c", "poslo_sign_f", "poslo_disclose",
     "poslo_aver", "poslo_distill", "poslo_epoch_seeds", "poslo_hash_entries", "poslo_msm", "poslo_msm_autotune",
     "poslo_set_profiling", "poslo_kernel_time", "poslo_reset_kernel_times",
-    "poslo_hash_entries_noalloc", "poslo_aver_multi", "poslo_distill_c", "poslo_sebver_c",
+    "poslo_hash_entries_noalloc", "poslo_aver_multi", "poslo_distill_c", "poslo_sebver_c", "poslo_distill_stream",
     "poslo_serve_start", "poslo_serve_stop", "poslo_register_key", "poslo_submit", "poslo_poll",
     "poslo_serve_stats",
 ]
@@ -106,6 +106,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "poslo_hash_entries_noalloc": ([C.POINTER(Batch), u8p, vp], C.c_int),
         "poslo_aver_multi": ([vp, C.POINTER(MultiBatch), u8p, vp, u64, C.POINTER(u64)], C.c_int),
         "poslo_distill_c": ([vp, C.POINTER(Batch), u32, u8p, C.POINTER(CcdC)], C.c_int),
+        "poslo_distill_stream": ([vp, C.POINTER(Batch), u64, u8p, vp, u64, C.POINTER(u64)], C.c_int),
         "poslo_sebver_c": ([vp, C.POINTER(Batch), u32, C.POINTER(CcdC), u32, u8p], C.c_int),
         "poslo_serve_start": ([vp, u32, u32, u64], C.c_int),
         "poslo_serve_stop": ([vp], C.c_int),
@@ -339,6 +340,17 @@ class Context:
         cnt = C.c_uint64()
         self._check(self.lib.poslo_aver_multi(self.h, C.byref(mb), _ptr(acc), _ptr(pairs), cap, C.byref(cnt)))
         return acc.astype(bool), pairs[:2 * cnt.value].reshape(-1, 2).copy()
+
+    def distill_stream(self, b: BatchData, chunk_entries: int, cap: int | None = None):
+        """Out-of-core AVer + Distill of a host-resident POSLO-F batch; returns (accept, indices)."""
+        cap = b.n if cap is None else cap
+        idx = np.zeros(max(cap, 1), np.uint64)
+        acc = np.zeros(1, np.uint8)
+        cnt = C.c_uint64()
+        cb = self._cbatch(b)
+        self._check(self.lib.poslo_distill_stream(self.h, C.byref(cb), chunk_entries, _ptr(acc), _ptr(idx), cap,
+                                                  C.byref(cnt)))
+        return bool(acc[0]), idx[:cnt.value].copy()
 
     # ------------------------------------------------------------------ POSLO-C ccd (Fig. 3b)
     def distill_c(self, b: BatchData, n_umbrella: int, cap: int | None = None):
