@@ -197,8 +197,11 @@ int poslo_aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, uint8_t* accep
 /* ---- serving: continuous batching over registered keys ------------------------------------
  * Not in the paper (which verifies one signer's log at a time); built on poslo_aver_multi.
  * poslo_serve_start starts `workers` host threads (1..8), each with its own internal context
- * on the same device.  Requests are copied at submission and admitted against the context's
- * mem_budget (POSLO_EBUSY when the device memory they would need does not fit; 0 = no limit).
+ * on the same device.  Requests are copied at submission (unless flagged POSLO_REQ_BORROW)
+ * and admitted against the context's mem_budget (POSLO_EBUSY when the device memory they
+ * would need does not fit; 0 = no limit).  A worker copies each request of a batch straight
+ * from its buffers into device staging (no host concatenation); pinned request buffers make
+ * these copies asynchronous DMA.
  * A free worker takes the oldest pending requests, up to max_batch_devices requests and
  * max_batch_entries entries, and verifies them as one multi-device batch; requests arriving
  * meanwhile join the next batch.  Each result is what poslo_distill gives for that request
@@ -212,9 +215,13 @@ typedef struct {
   uint64_t n;
   const uint8_t* s;       /* n*32 */
   const uint8_t* R;       /* n*32 */
-  const uint8_t* ds;      /* ds_nodes*24 */
+  const uint8_t* ds;      /* ds_nodes*24 (always copied) */
   uint32_t ds_nodes;
+  uint32_t flags;         /* POSLO_REQ_BORROW: msgs, offs, s and R are not copied at submission;
+                             the caller keeps them alive and unchanged until the request's
+                             result has been read by poslo_poll */
 } poslo_request;
+enum { POSLO_REQ_BORROW = 1 };
 
 int poslo_serve_start(poslo_ctx* ctx, uint32_t workers, uint32_t max_batch_devices, uint64_t max_batch_entries);
 int poslo_serve_stop(poslo_ctx* ctx);

@@ -66,4 +66,16 @@ int aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, const uint32_t* cons
 int build_key_table(poslo_ctx* ctx, const uint8_t Y[32], uint32_t* table_dev);
 // 32-bit words of one window table.
 size_t key_table_words();
+// One request's inputs in host memory: entry t's message is msgs[offs[t] .. offs[t+1]).
+struct ReqView {
+  const uint8_t* msgs;
+  const uint64_t* offs;   // n+1, absolute into msgs
+  uint64_t n;
+  const uint8_t* s;
+  const uint8_t* R;
+};
+// Copies the requests' inputs one by one into device staging buffers of ctx (the messages
+// back to back, offsets rebased on the device) and points mb's msgs, offs, s, R at them
+// (mb->on_device = 1).  The copies are issued on ctx's main stream.
+int stage_requests(poslo_ctx* ctx, const ReqView* reqs, uint32_t nd, poslo_multi_batch* mb);
 }  // namespace poslo_host

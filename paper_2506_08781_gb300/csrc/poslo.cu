@@ -1676,6 +1676,59 @@ int poslo_host::build_key_table(poslo_ctx* ctx, const uint8_t Y[32], uint32_t* t
   return POSLO_OK;
 }
 
+int poslo_host::stage_requests(poslo_ctx* ctx, const ReqView* reqs, uint32_t nd, poslo_multi_batch* mb) {
+  int rc;
+  // slot: raw offsets of request d at [slot[d], slot[d+1]); start: its first entry in the
+  // batch; base: its first message byte in the batch
+  std::vector<uint64_t> meta(3 * ((size_t)nd + 1), 0);
+  uint64_t* slot = meta.data();
+  uint64_t* start = slot + nd + 1;
+  uint64_t* base = start + nd + 1;
+  for (uint32_t d = 0; d < nd; ++d) {
+    const ReqView& r = reqs[d];
+    if (r.n && r.offs[r.n] < r.offs[0]) return fail(ctx, POSLO_EINVAL, "request %u: offsets decrease", d);
+    slot[d + 1] = slot[d] + r.n + 1;
+    start[d + 1] = start[d] + r.n;
+    base[d + 1] = base[d] + (r.n ? r.offs[r.n] - r.offs[0] : 0);
+  }
+  const uint64_t N = start[nd], M = base[nd];
+  uint8_t *msgs, *sv, *Rv;
+  uint64_t *raw, *offs, *d_meta;
+  if ((rc = ensure_t(ctx, "sv_msgs", std::max<uint64_t>(M, 16), &msgs))) return rc;
+  if ((rc = ensure_t(ctx, "sv_raw", 8 * std::max<uint64_t>(slot[nd], 1), &raw))) return rc;
+  if ((rc = ensure_t(ctx, "sv_offs", 8 * (N + 1), &offs))) return rc;
+  if ((rc = ensure_t(ctx, "sv_s", 32 * std::max<uint64_t>(N, 1), &sv))) return rc;
+  if ((rc = ensure_t(ctx, "sv_R", 32 * std::max<uint64_t>(N, 1), &Rv))) return rc;
+  if ((rc = ensure_t(ctx, "sv_meta", 8 * meta.size(), &d_meta))) return rc;
+  cudaStream_t st = ctx->s_main;
+  for (uint32_t d = 0; d < nd; ++d) {
+    const ReqView& r = reqs[d];
+    if (r.n == 0) continue;
+    const uint64_t lo = r.offs[0], len = r.offs[r.n] - lo;
+    if (len) CU(cudaMemcpyAsync(msgs + base[d], r.msgs + lo, len, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(raw + slot[d], r.offs, 8 * (r.n + 1), cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(sv + 32 * start[d], r.s, 32 * r.n, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(Rv + 32 * start[d], r.R, 32 * r.n, cudaMemcpyHostToDevice, st));
+  }
+  CU(cudaMemcpyAsync(d_meta, meta.data(), 8 * meta.size(), cudaMemcpyHostToDevice, st));
+  CU(cudaMemsetAsync(offs, 0, 8, st));   // an empty batch still has offs[0] = 0
+  if (slot[nd]) {
+    k_rebase_offs<<<(unsigned)((slot[nd] + 255) / 256), 256, 0, st>>>(raw, d_meta, d_meta + nd + 1,
+                                                                       d_meta + 2 * ((size_t)nd + 1), nd, offs,
+                                                                       ctx->status);
+    ++ctx->launch_count;
+  }
+  CU(cudaGetLastError());
+  // the staging copies read host memory that the caller may release after this call returns
+  CU(cudaStreamSynchronize(st));
+  mb->msgs = msgs;
+  mb->offs = offs;
+  mb->s = sv;
+  mb->R = Rv;
+  mb->on_device = 1;
+  return POSLO_OK;
+}
+
 int poslo_host::aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, const uint32_t* const* key_tables,
                            uint8_t* accept, uint64_t* invalid_pairs, uint64_t cap, uint64_t* n_invalid) {
   if (!ctx || !mb || !accept || !n_invalid || mb->n_dev == 0 || !mb->Y || !mb->dev_start || !mb->first_index ||

@@ -34,6 +34,7 @@ struct Req {
   uint64_t first_index = 0, n = 0;
   std::vector<uint8_t> msgs, s, R, ds;
   std::vector<uint64_t> offs;   // n+1, rebased to start at 0
+  ReqView view{};               // where the inputs are: the vectors above, or the caller's (borrowed)
   uint64_t charge = 0;          // bytes of the budget held until the result is read
   int state = 0;                // 0 pending, 1 running, 2 done
   int rc = POSLO_OK;
@@ -72,10 +73,11 @@ uint64_t request_charge(uint64_t n, uint64_t msg_bytes) { return msg_bytes + n *
 
 void run_batch(Server* S, poslo_ctx* w, std::vector<Req*>& batch) {
   const uint32_t nd = (uint32_t)batch.size();
-  std::vector<uint8_t> Y(32 * (size_t)nd), msgs, s, R, ds;
-  std::vector<uint64_t> start(nd + 1, 0), first(nd), offs;
+  std::vector<uint8_t> Y(32 * (size_t)nd), ds;
+  std::vector<uint64_t> start(nd + 1, 0), first(nd);
   std::vector<uint32_t> n2(nd), ds_off(nd + 1, 0);
   std::vector<const uint32_t*> tabs(nd);
+  std::vector<ReqView> views(nd);
   {
     std::lock_guard<std::mutex> lock(S->mu);
     const size_t words = key_table_words();
@@ -85,30 +87,17 @@ void run_batch(Server* S, poslo_ctx* w, std::vector<Req*>& batch) {
       tabs[d] = S->table_blocks[k / Server::kKeysPerBlock] + (size_t)(k % Server::kKeysPerBlock) * words;
     }
   }
-  uint64_t total = 0, mtotal = 0;
-  for (uint32_t d = 0; d < nd; ++d) {
-    total += batch[d]->n;
-    mtotal += batch[d]->msgs.size();
-  }
-  msgs.reserve(mtotal);
-  s.reserve(32 * total);
-  R.reserve(32 * total);
-  offs.reserve(total + 1);
+  uint64_t total = 0;
   for (uint32_t d = 0; d < nd; ++d) {
     Req* r = batch[d];
+    views[d] = r->view;
+    total += r->n;
     start[d + 1] = start[d] + r->n;
     first[d] = r->first_index;
     n2[d] = r->n2;
-    const uint64_t base = msgs.size();
-    for (uint64_t t = 0; t < r->n; ++t) offs.push_back(base + r->offs[t]);
-    msgs.insert(msgs.end(), r->msgs.begin(), r->msgs.end());
-    s.insert(s.end(), r->s.begin(), r->s.end());
-    R.insert(R.end(), r->R.begin(), r->R.end());
     ds.insert(ds.end(), r->ds.begin(), r->ds.end());
     ds_off[d + 1] = ds_off[d] + (uint32_t)(r->ds.size() / 24);
   }
-  offs.push_back(msgs.size());
-  if (msgs.empty()) msgs.push_back(0);
   poslo_multi_batch mb{};
   mb.n_dev = nd;
   mb.Y = Y.data();
@@ -117,15 +106,12 @@ void run_batch(Server* S, poslo_ctx* w, std::vector<Req*>& batch) {
   mb.n2 = n2.data();
   mb.ds = ds.data();
   mb.ds_off = ds_off.data();
-  mb.msgs = msgs.data();
-  mb.offs = offs.data();
-  mb.s = s.data();
-  mb.R = R.data();
-  mb.on_device = 0;
+  // each request's inputs go straight from its own buffers into the worker's device staging
+  int rc = stage_requests(w, views.data(), nd, &mb);
   std::vector<uint8_t> acc(nd);
   std::vector<uint64_t> pairs(2 * std::max<uint64_t>(total, 1));
   uint64_t cnt = 0;
-  int rc = aver_multi(w, &mb, tabs.data(), acc.data(), pairs.data(), total, &cnt);
+  if (rc == POSLO_OK) rc = aver_multi(w, &mb, tabs.data(), acc.data(), pairs.data(), total, &cnt);
   std::vector<int> rcs(nd, rc);
   std::vector<std::vector<uint64_t>> inv(nd);
   if (rc == POSLO_OK) {
@@ -137,13 +123,14 @@ void run_batch(Server* S, poslo_ctx* w, std::vector<Req*>& batch) {
       Req* r = batch[d];
       b.variant = POSLO_VARIANT_F;
       b.n2 = r->n2;
+      static const uint8_t kNone[32] = {0};
       b.Y = Y.data() + 32 * (size_t)d;
-      b.msgs = r->msgs.empty() ? msgs.data() : r->msgs.data();
-      b.offs = r->offs.data();
+      b.msgs = r->view.msgs ? r->view.msgs : kNone;
+      b.offs = r->view.offs;
       b.n = r->n;
       b.first_index = r->first_index;
-      b.s = r->s.data();
-      b.R = r->R.data();
+      b.s = r->view.s ? r->view.s : kNone;
+      b.R = r->view.R ? r->view.R : kNone;
       b.R_count = r->n;
       b.ds = r->ds.data();
       b.ds_nodes = (uint32_t)(r->ds.size() / 24);
@@ -167,6 +154,7 @@ void run_batch(Server* S, poslo_ctx* w, std::vector<Req*>& batch) {
     std::vector<uint8_t>().swap(r->s);
     std::vector<uint8_t>().swap(r->R);
     std::vector<uint64_t>().swap(r->offs);
+    r->view = ReqView{};
   }
   S->batches += 1;
   S->batched_requests += nd;
@@ -306,11 +294,21 @@ int poslo_submit(poslo_ctx* ctx, const poslo_request* q, uint64_t* ticket) {
     if (S->budget && S->used + r->charge > S->budget) return POSLO_EBUSY;
     S->used += r->charge;   // reserve before copying
   }
-  r->msgs.assign(q->msgs ? q->msgs + lo : nullptr, q->msgs ? q->msgs + hi : nullptr);
-  r->offs.resize(q->n + 1);
-  for (uint64_t t = 0; t <= q->n; ++t) r->offs[t] = q->n ? q->offs[t] - lo : 0;
-  r->s.assign(q->s, q->s + 32 * q->n);
-  r->R.assign(q->R, q->R + 32 * q->n);
+  if (q->flags & POSLO_REQ_BORROW) {
+    // the caller keeps the inputs until the result is read; the offsets stay absolute
+    r->view = poslo_host::ReqView{q->msgs, q->offs, q->n, q->s, q->R};
+    if (q->n == 0) {
+      r->offs.assign(1, 0);
+      r->view.offs = r->offs.data();
+    }
+  } else {
+    r->msgs.assign(q->msgs ? q->msgs + lo : nullptr, q->msgs ? q->msgs + hi : nullptr);
+    r->offs.resize(q->n + 1);
+    for (uint64_t t = 0; t <= q->n; ++t) r->offs[t] = q->n ? q->offs[t] - lo : 0;
+    r->s.assign(q->s, q->s + 32 * q->n);
+    r->R.assign(q->R, q->R + 32 * q->n);
+    r->view = poslo_host::ReqView{r->msgs.data(), r->offs.data(), q->n, r->s.data(), r->R.data()};
+  }
   r->ds.assign(q->ds, q->ds + 24 * (size_t)q->ds_nodes);
   {
     std::lock_guard<std::mutex> lock(S->mu);

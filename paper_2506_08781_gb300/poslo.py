@@ -34,6 +34,7 @@ EXPORTS = [
     "poslo_serve_stats",
 ]
 POSLO_PENDING = 1
+POSLO_EBUFSMALL = -5
 
 
 class PosloError(RuntimeError):
@@ -56,7 +57,10 @@ class MultiBatch(C.Structure):
 class Request(C.Structure):
     _fields_ = [("key_id", C.c_uint32), ("n2", C.c_uint32), ("first_index", C.c_uint64), ("msgs", C.c_void_p),
                 ("offs", C.c_void_p), ("n", C.c_uint64), ("s", C.c_void_p), ("R", C.c_void_p), ("ds", C.c_void_p),
-                ("ds_nodes", C.c_uint32)]
+                ("ds_nodes", C.c_uint32), ("flags", C.c_uint32)]
+
+
+REQ_BORROW = 1
 
 
 class CcdC(C.Structure):
@@ -198,6 +202,7 @@ class Context:
         if rc != POSLO_OK:
             raise PosloError(rc, "poslo_create failed (needs an sm_103 GPU)")
         self.h = h
+        self._borrowed = {}
 
     def close(self):
         if getattr(self, "h", None):
@@ -396,16 +401,22 @@ class Context:
         self._check(self.lib.poslo_register_key(self.h, _ptr(bytes(Y)), C.byref(kid)))
         return kid.value
 
-    def submit(self, key_id: int, n2: int, first_index: int, msgs, offs, s, R, ds: bytes) -> int:
-        """Queue one request (host arrays; copied by the library).  Raises PosloError EBUSY
-        when the memory budget is exhausted."""
+    def submit(self, key_id: int, n2: int, first_index: int, msgs, offs, s, R, ds: bytes,
+               borrow: bool = False) -> int:
+        """Queue one request (host arrays; copied by the library unless borrow, in which case
+        the arrays must stay alive and unchanged until the result is polled).  Raises
+        PosloError EBUSY when the memory budget is exhausted."""
         offs = np.ascontiguousarray(offs, dtype=np.uint64)
+        arrays = (_u8(msgs), offs, _u8(s), _u8(R))
         q = Request()
         q.key_id, q.n2, q.first_index = key_id, n2, first_index
-        q.msgs, q.offs, q.n = _ptr(_u8(msgs)), _ptr(offs), len(offs) - 1
-        q.s, q.R, q.ds, q.ds_nodes = _ptr(_u8(s)), _ptr(_u8(R)), _ptr(bytes(ds)), len(ds) // 24
+        q.msgs, q.offs, q.n = _ptr(arrays[0]), _ptr(offs), len(offs) - 1
+        q.s, q.R, q.ds, q.ds_nodes = _ptr(arrays[2]), _ptr(arrays[3]), _ptr(bytes(ds)), len(ds) // 24
+        q.flags = REQ_BORROW if borrow else 0
         t = C.c_uint64()
         self._check(self.lib.poslo_submit(self.h, C.byref(q), C.byref(t)))
+        if borrow:
+            self._borrowed[t.value] = arrays     # alive until the result has been polled
         return t.value
 
     def poll(self, ticket: int, wait_ms: int = 0, cap: int = 1 << 16, with_latency: bool = False):
@@ -418,6 +429,8 @@ class Context:
         if rc == POSLO_PENDING:
             _keep.clear()
             return None
+        if rc != POSLO_EBUFSMALL:
+            self._borrowed.pop(ticket, None)
         self._check(rc)
         res = (bool(acc[0]), idx[:cnt.value].copy())
         return res + (lat.value * 1e-9,) if with_latency else res

@@ -99,3 +99,31 @@ def test_serving_budget_and_unknown_ids():
             ctx.poll(12345)
         assert e.value.code == -7
         ctx.serve_stop()
+
+
+def test_serving_borrowed_and_copied_requests_mix():
+    """Borrowed requests (POSLO_REQ_BORROW: read from the caller's buffers, offsets absolute
+    into a larger message buffer) and copied ones batch together with the same results."""
+    import __graft_entry__
+    __graft_entry__.build()
+    keys, reqs = _requests(9, 3, 18)
+    with poslo.Context(device=0, verifier_seed=synth.verifier_seed(9)) as ctx:
+        ctx.serve_start(workers=2, max_batch_devices=6, max_batch_entries=200)
+        kid = [ctx.register_key(Y) for _, _, Y in keys]
+        tickets = []
+        for i, q in enumerate(reqs):
+            if i % 2:
+                # messages at an offset inside a bigger buffer, offsets absolute into it
+                pad = 13 + i
+                buf = np.concatenate([np.full(pad, 0xEE, np.uint8), q["msgs"].data, np.full(7, 0xEE, np.uint8)])
+                offs = q["msgs"].offs.astype(np.uint64) + pad
+                s_arr = np.frombuffer(q["s"], np.uint8).copy()
+                R_arr = np.frombuffer(q["R"], np.uint8).copy()
+                tickets.append(ctx.submit(kid[q["key"]], q["n2"], q["first"], buf, offs, s_arr, R_arr, q["ds"],
+                                          borrow=True))
+            else:
+                tickets.append(_submit(ctx, kid, q))
+        res = [ctx.poll(t, wait_ms=60000) for t in tickets]
+        ctx.serve_stop()
+    for q, r in zip(reqs, res):
+        assert (r[0], list(r[1])) == (not q["want"], q["want"])
