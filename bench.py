@@ -52,6 +52,26 @@ def dist_env():
     return rank, world, local
 
 
+def shard_seed(rank: int) -> int:
+    """Each rank verifies its own independent batch (weak scaling, no data-path exchange)."""
+    return SEED + rank
+
+
+def max_over_ranks(ms: float, world: int) -> float:
+    """The slowest rank's time per step (the job's time): all-reduce MAX over the ranks."""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(entries_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job entries/s: every rank's entries over the slowest rank's step time."""
+    return world * entries_per_rank / (ms * 1e-3)
+
+
 class ClockSampler:
     """nvidia-smi clock and throttle-reason samples during the timed region."""
 
@@ -636,7 +656,7 @@ def run_ours(args):
     torch.cuda.set_device(device)
     __graft_entry__.build()
     ctx = poslo.Context(device=device, verifier_seed=synth.verifier_seed(1000 + rank))
-    km, msgs, subsets, _ = make_workload(seed=SEED + rank)
+    km, msgs, subsets, _ = make_workload(seed=shard_seed(rank))
     Y, s, R = sign_workload(ctx, km, msgs, subsets)
     ds = struct.pack("<II", D, 0) + km.root      # final disclosure: the root x_D[0] alone
     n = msgs.n
@@ -683,11 +703,8 @@ def run_ours(args):
         if cnt:
             kernels[name] = {"ms_per_launch": tot / cnt, "launches": cnt}
     ctx.set_profiling(False)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * n / (ms * 1e-3)
+    ms = max_over_ranks(ms, world)
+    value = job_throughput(n, world, ms)
 
     # unit AVer (the paper's equation) on the same resident inputs, for context
     for _ in range(2):
