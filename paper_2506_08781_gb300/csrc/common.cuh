@@ -230,7 +230,6 @@ __device__ __forceinline__ void warp_sum_u64(unsigned long long& v) {
 }
 
 
-
 // ----------------------------------------------------------------------------------------
 // A5 (unit): decode R_t, flag malformed ones, sum the rest.
 // ----------------------------------------------------------------------------------------
@@ -262,7 +261,6 @@ __device__ __forceinline__ ge ge_load(const uint32_t* src) {
   }
   return p;
 }
-
 
 
 // ----------------------------------------------------------------------------------------
@@ -315,16 +313,11 @@ __device__ __forceinline__ sc limb_sums_to_scalar(const unsigned long long* sums
 }
 
 
-
-
-// ---- per-entry checks and reference MSM (see k_check.cu) ----
-// Per-entry verification and a reference multi-scalar multiplication.
+// ---- per-entry checks (see k_check.cu) ----
 //
 //   k_entry_check  the single-entry POSLO-F check of Fig. 4 (|m| = 1) for every entry:
 //                  s_t canonical, R_t decodable, [8](R_t - e_t Y - s_t G) = O, with
 //                  [e]Y + [s]G taken from the two fixed-window tables (128 additions)
-//   k_msm_direct   sum_t [k_t]P_t with one double-and-add per term, for short MSMs and as
-//                  the definition the bucket method is checked against
 
 
 __device__ __forceinline__ ge double_scalar_tables(const uint32_t e[8], const uint32_t s[8],
@@ -351,19 +344,6 @@ struct CheckArgs {
 };
 
 
-
-struct MsmArgs {
-  const uint8_t* points;     // n*32 compressed (or NULL when pts is given)
-  const uint32_t* pts;       // n*kPtsWords words (x, y, t2d) already decoded (or NULL)
-  const uint8_t* scalars;    // n*scalar_bytes little-endian
-  uint32_t scalar_bytes;     // 16 or 32
-  uint64_t n;
-  const uint8_t* skip;       // optional: n bytes, 1 = leave the term out
-  uint32_t* partial;         // per block: kPointPartialWords words
-};
-
-
-
 // Masked scalar sum: per block, 13 u64 limb sums of the s_t whose skip byte is 0.
 
 
@@ -377,7 +357,6 @@ constexpr int kCompactThreads = 1024;
 
 
 // Sum point partials (one block) and encode the result.
-
 
 
 // ---- signer helpers (see k_signer.cu) ----
@@ -477,7 +456,6 @@ struct SignCArgs {
 };
 
 // POSLO-C.Sig: s~_i = sum_j (r_i^j - e_i^j y) mod q, one thread per epoch.
-
 
 
 // ---- Pippenger multi-scalar multiplication (k_msm.cu) ----
@@ -600,7 +578,6 @@ __global__ void __launch_bounds__(128) k_final_prep(const PrepArgs a);
 __global__ void k_final_check(const uint32_t* prep, const uint32_t* R, const uint32_t* point_bad,
                               const uint32_t* status, uint8_t* accept);
 __global__ void __launch_bounds__(128) k_entry_check(const CheckArgs a);
-__global__ void __launch_bounds__(kPointThreads) k_msm_direct(const MsmArgs a);
 __global__ void __launch_bounds__(kHashThreads) k_sum_scalars(const uint8_t* s, uint64_t n, const uint8_t* skip,
                                                              unsigned long long* partial);
 __global__ void k_reduce_scalars(const unsigned long long* partial, uint32_t nparts, uint8_t* out);

@@ -24,46 +24,6 @@ __global__ void __launch_bounds__(128) k_entry_check(const CheckArgs a) {
   }
 }
 
-__global__ void __launch_bounds__(kPointThreads) k_msm_direct(const MsmArgs a) {
-  ge acc = ge_identity();
-  uint32_t bad = 0;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.n; t += stride) {
-    if (a.skip && a.skip[t]) continue;
-    ge P;
-    if (a.pts) {
-      fe t2d;
-      pts_load(a.pts + (size_t)kPtsWords * t, P.X, P.Y, t2d);
-      P.Z = fe_one();
-      P.T = fe_mul(P.X, P.Y);
-    } else {
-      const uint4* rp = reinterpret_cast<const uint4*>(a.points + 32 * t);
-      const uint4 r0 = __ldg(rp), r1 = __ldg(rp + 1);
-      const uint32_t b[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
-      if (!ge_decode(b, P)) { ++bad; continue; }
-    }
-    uint32_t k[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    const uint8_t* kb = a.scalars + (size_t)a.scalar_bytes * t;
-    for (uint32_t q = 0; q < a.scalar_bytes / 4; ++q)
-      k[q] = kb[4 * q] | (kb[4 * q + 1] << 8) | (kb[4 * q + 2] << 16) | ((uint32_t)kb[4 * q + 3] << 24);
-    acc = ge_add(acc, ge_scalarmult(k, P, 8 * (int)a.scalar_bytes));
-  }
-  __shared__ uint32_t sp[kPointThreads][32];
-  __shared__ uint32_t sbad[kPointThreads];
-  ge_store(sp[threadIdx.x], acc);
-  sbad[threadIdx.x] = bad;
-  __syncthreads();
-  for (int h = kPointThreads / 2; h > 0; h >>= 1) {
-    if (threadIdx.x < h) {
-      ge_store(sp[threadIdx.x], ge_add(ge_load(sp[threadIdx.x]), ge_load(sp[threadIdx.x + h])));
-      sbad[threadIdx.x] += sbad[threadIdx.x + h];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x < 32) a.partial[(uint64_t)blockIdx.x * kPointPartialWords + threadIdx.x] = sp[0][threadIdx.x];
-  if (threadIdx.x == 0) a.partial[(uint64_t)blockIdx.x * kPointPartialWords + 32] = sbad[0];
-}
-
 __global__ void __launch_bounds__(kHashThreads) k_sum_scalars(const uint8_t* s, uint64_t n, const uint8_t* skip,
                                                              unsigned long long* partial) {
   acc13 acc;

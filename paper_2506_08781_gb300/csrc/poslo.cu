@@ -393,33 +393,6 @@ int run_points(poslo_ctx* ctx, const uint8_t* R, uint64_t count, uint32_t* pts_o
   return POSLO_OK;
 }
 
-int run_msm_direct(poslo_ctx* ctx, cudaStream_t st, const uint8_t* points, const uint32_t* pts,
-                   const uint8_t* scalars, uint32_t scalar_bytes, uint64_t n, const uint8_t* skip,
-                   uint32_t* point_out, uint8_t* enc_out, uint32_t* bad_out) {
-  int rc;
-  const int blocks = grid_for(ctx, n, kPointThreads, 8);
-  uint32_t* partial;
-  if ((rc = ensure_t(ctx, "msm_partial", (size_t)blocks * kPointPartialWords * 4, &partial))) return rc;
-  MsmArgs a{};
-  a.points = points;
-  a.pts = pts;
-  a.scalars = scalars;
-  a.scalar_bytes = scalar_bytes;
-  a.n = n;
-  a.skip = skip;
-  a.partial = partial;
-  cudaEvent_t tb, te;
-  timer_begin(ctx, "msm", st, &tb, &te);
-  k_msm_direct<<<blocks, kPointThreads, 0, st>>>(a);
-  ++ctx->launch_count;
-  CU(cudaGetLastError());
-  k_sum_encode<<<1, kFinalThreads, 0, st>>>(partial, blocks, point_out, enc_out, bad_out);
-  ++ctx->launch_count;
-  CU(cudaGetLastError());
-  timer_end(ctx, "msm", st, tb, te);
-  return POSLO_OK;
-}
-
 // Pippenger plan: the window c comes from the context (poslo_params.msm_window) or from the
 // autotuned table for this size class (see autotune_msm); the default before tuning is
 // c = log2(n) - 4 clamped to [8, 16].
