@@ -57,6 +57,7 @@ struct HashArgs {
   uint32_t weighted;           // 1: aggregate z_t e_t and z_t s_t
   uint32_t zpre[10];           // weighted: BE words of "POSLO-Z" || verifier_seed || (byte 39 = 0)
   uint32_t* z_out;             // optional (weighted): n*4 words of z_t
+  const uint32_t* z_in;        // optional (weighted): z_t already computed (k_weights); read, not hashed
   uint8_t* sbad_out;           // optional: n bytes, 1 = s_t is not canonical
   unsigned long long* partial; // per block: 13 u64 limb sums of e, 13 of s, 1 bad count (27 u64)
   uint32_t* status;            // device status word (kErrInput for decreasing offsets)
@@ -566,6 +567,8 @@ struct PrepArgs {
 void launch_epoch_seeds(int inst, unsigned grid, unsigned block, cudaStream_t st, const DsNode* ds, int nds,
                         uint64_t e0, uint64_t ne, uint32_t* x0_out, uint32_t* status);
 void launch_hash(int inst, unsigned grid, cudaStream_t st, const HashArgs& a);
+struct ZPre { uint32_t w[10]; };   // BE words of "POSLO-Z" || verifier_seed || (byte 39 = 0)
+__global__ void k_weights(const ZPre zp, uint64_t n, uint64_t first, uint32_t* z_out);
 __global__ void __launch_bounds__(kPointThreads) k_points(const PointArgs a);
 __global__ void __launch_bounds__(128) k_table_chain(const uint32_t* __restrict__ enc,
                                                      const uint32_t* __restrict__ pts,
@@ -604,10 +607,12 @@ __global__ void __launch_bounds__(128) k_msm_accum(const uint32_t* pts, const ui
 __global__ void __launch_bounds__(128) k_msm_combine(const uint32_t* off, const uint32_t* cnt, uint64_t n, MsmPlan pl,
                                                      const uint32_t* A, const uint32_t* B, uint32_t* buckets,
                                                      uint32_t* big_list, uint32_t* big_count);
-__global__ void __launch_bounds__(128) k_msm_combine_big(const uint32_t* off, const uint32_t* cnt, uint64_t n,
-                                                         MsmPlan pl, const uint32_t* A, const uint32_t* B,
-                                                         uint32_t* buckets, const uint32_t* big_list,
-                                                         const uint32_t* big_count);
+constexpr int kCombineBigThreads = 512;
+__global__ void __launch_bounds__(kCombineBigThreads) k_msm_combine_big(const uint32_t* off, const uint32_t* cnt,
+                                                                        uint64_t n, MsmPlan pl, const uint32_t* A,
+                                                                        const uint32_t* B, uint32_t* buckets,
+                                                                        const uint32_t* big_list,
+                                                                        const uint32_t* big_count);
 __global__ void __launch_bounds__(128) k_msm_chunk(const uint32_t* buckets, MsmPlan pl, uint32_t* L, uint32_t* T);
 __global__ void __launch_bounds__(512) k_msm_groups(const uint32_t* L, const uint32_t* T, MsmPlan pl, uint32_t* groups);
 __global__ void __launch_bounds__(32) k_msm_final(const uint32_t* groups, MsmPlan pl, uint32_t* out);

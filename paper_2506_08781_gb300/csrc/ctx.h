@@ -36,6 +36,7 @@ struct poslo_ctx {
   uint8_t vseed[32] = {0};
   cudaStream_t s_main = nullptr, s_table = nullptr, s_points = nullptr;
   cudaStream_t s_copy = nullptr;                 // host-to-device copies of the next chunk
+  cudaStream_t s_hash = nullptr;                 // message hashing of Distill
   cudaEvent_t ev_copy[2] = {nullptr, nullptr};   // chunk k's inputs have landed in set k % 2
   cudaEvent_t ev_table = nullptr, ev_points = nullptr, ev_main = nullptr, ev_hash = nullptr, ev_prep = nullptr;
   cudaEvent_t ev_staged = nullptr;   // main stream, right after a batch's R_t have been staged

@@ -193,25 +193,34 @@ __device__ __forceinline__ ge ge_shfl_down(const ge& p, int delta) {
   return r;
 }
 
-// The listed wide buckets, one warp each: lanes sum the ranges' first runs with stride 32,
-// then a shuffle tree joins the lanes.  The grid is fixed; warps stride over the list.
-__global__ void __launch_bounds__(128) k_msm_combine_big(const uint32_t* off, const uint32_t* cnt, uint64_t n,
-                                                         MsmPlan pl, const uint32_t* A, const uint32_t* B,
-                                                         uint32_t* buckets, const uint32_t* big_list,
-                                                         const uint32_t* big_count) {
-  const uint32_t lane = threadIdx.x & 31;
-  const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+// The listed wide buckets, one block each: the threads sum the ranges' first runs with a
+// stride of the block size, a shuffle tree joins each warp, and the first warp joins the
+// warps' sums.  The grid is fixed; blocks stride over the list.
+__global__ void __launch_bounds__(kCombineBigThreads) k_msm_combine_big(const uint32_t* off, const uint32_t* cnt,
+                                                                        uint64_t n, MsmPlan pl, const uint32_t* A,
+                                                                        const uint32_t* B, uint32_t* buckets,
+                                                                        const uint32_t* big_list,
+                                                                        const uint32_t* big_count) {
+  __shared__ uint32_t ws[kCombineBigThreads / 32][32];
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t total = *big_count;
   const uint64_t nseg = (n + kMsmSeg - 1) / kMsmSeg;
-  for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < total; i += nwarps) {
+  for (uint32_t i = blockIdx.x; i < total; i += gridDim.x) {
     const uint64_t b = big_list[i];
     const uint32_t w = (uint32_t)(b / pl.nb);
     const CombineSpan c = combine_span(off, cnt, pl, b);
     const uint64_t g0 = (uint64_t)w * nseg;
-    ge acc = lane == 0 ? ge_load((c.starts_range ? A : B) + 32 * (g0 + c.ts)) : ge_identity();
-    for (uint64_t t = c.ts + 1 + lane; t <= c.te; t += 32) acc = ge_add(acc, ge_load(A + 32 * (g0 + t)));
+    ge acc = threadIdx.x == 0 ? ge_load((c.starts_range ? A : B) + 32 * (g0 + c.ts)) : ge_identity();
+    for (uint64_t t = c.ts + 1 + threadIdx.x; t <= c.te; t += blockDim.x) acc = ge_add(acc, ge_load(A + 32 * (g0 + t)));
     for (int delta = 16; delta > 0; delta >>= 1) acc = ge_add(acc, ge_shfl_down(acc, delta));
-    if (lane == 0) ge_store(buckets + 32 * b, acc);
+    if (lane == 0) ge_store(ws[warp], acc);
+    __syncthreads();
+    if (warp == 0) {
+      acc = lane < kCombineBigThreads / 32 ? ge_load(ws[lane]) : ge_identity();
+      for (int delta = 16; delta > 0; delta >>= 1) acc = ge_add(acc, ge_shfl_down(acc, delta));
+      if (lane == 0) ge_store(buckets + 32 * b, acc);
+    }
+    __syncthreads();
   }
 }
 

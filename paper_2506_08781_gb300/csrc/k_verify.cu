@@ -62,6 +62,23 @@ __device__ __forceinline__ void weight_block(const uint32_t zpre[10], uint64_t z
   w[12] = 0; w[13] = 0; w[14] = 0; w[15] = 47 * 8;
 }
 
+// The verifier's weights alone: z_t for entries first .. first + n - 1 (one SHA-256 block
+// each), so that the MSM's counting sort need not wait for the message hashing.
+__global__ void k_weights(const ZPre zp, uint64_t n, uint64_t first, uint32_t* z_out) {
+  uint32_t pre[10];
+#pragma unroll
+  for (int q = 0; q < 10; ++q) pre[q] = zp.w[q];
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
+    uint32_t w[16], st[8];
+    weight_block(pre, first + t, w);
+    sha256_init(st);
+    sha256_compress(st, w);
+    reinterpret_cast<uint4*>(z_out)[t] =
+        make_uint4(bswap32(st[0]), bswap32(st[1]), bswap32(st[2]), bswap32(st[3]) & 0x7fffffffu);
+  }
+}
+
 template <int INST>
 __global__ void __launch_bounds__(kHashThreads, POSLO_HASH_MIN_BLOCKS) k_hash(const HashArgs a) {
   AesCtx c{};
@@ -146,7 +163,7 @@ __global__ void __launch_bounds__(kHashThreads, POSLO_HASH_MIN_BLOCKS) k_hash(co
         uint32_t x[4];
         prf_entry_aes(c, x0, (uint32_t)j, x);
         mdc2_stream(c, entry_stream(a.msgs + o0, L, x), dig);
-        if (a.weighted) {
+        if (a.weighted && !a.z_in) {
           uint32_t w[16];
           weight_block(a.zpre, zi, w);
           sha256_init(st);
@@ -167,7 +184,7 @@ __global__ void __launch_bounds__(kHashThreads, POSLO_HASH_MIN_BLOCKS) k_hash(co
         }
         const uint32_t total = L + 16;
         const uint32_t nb = (total + 9 + 63) >> 6;
-        const uint32_t iters = 1 + nb + (a.weighted ? 1u : 0u);
+        const uint32_t iters = 1 + nb + (a.weighted && !a.z_in ? 1u : 0u);
         sha256_init(st);
 #pragma unroll 1
         for (uint32_t it = 0; it < iters; ++it) {
@@ -230,7 +247,13 @@ __global__ void __launch_bounds__(kHashThreads, POSLO_HASH_MIN_BLOCKS) k_hash(co
       }
       if (a.weighted) {
         // z_t: the first 16 digest bytes as a little-endian integer, bit 127 cleared
-        const uint32_t z[4] = {bswap32(st[0]), bswap32(st[1]), bswap32(st[2]), bswap32(st[3]) & 0x7fffffffu};
+        uint32_t z[4];
+        if (a.z_in) {
+          const uint4 zz = __ldg(reinterpret_cast<const uint4*>(a.z_in) + t);
+          z[0] = zz.x; z[1] = zz.y; z[2] = zz.z; z[3] = zz.w;
+        } else {
+          z[0] = bswap32(st[0]); z[1] = bswap32(st[1]); z[2] = bswap32(st[2]); z[3] = bswap32(st[3]) & 0x7fffffffu;
+        }
         if (a.z_out) reinterpret_cast<uint4*>(a.z_out)[t] = make_uint4(z[0], z[1], z[2], z[3]);
         uint32_t pr[12];
         mul_4x8(pr, z, e.v);
