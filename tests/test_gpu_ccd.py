@@ -102,3 +102,23 @@ def test_distill_c_errors(env):
     with pytest.raises(poslo.PosloError) as e:
         ctx.distill_c(b, 2, cap=2)                   # 4 invalid epochs, room for 2
     assert e.value.code == -5
+
+
+@pytest.mark.parametrize("n_u", [1, 8])
+def test_distill_c_umbrella_extremes(env, n_u):
+    # one umbrella over the whole batch, and one umbrella per epoch
+    ctx, _ = env
+    km, Y, R, ms, s_ep = _epochs(64, 3, 4, 8)
+    _flip(ms, 2, 1)
+    _flip(ms, 5, 3)
+    valid, ccd = _run(ctx, Y, ms, 4, s_ep, R, O.ds_root(km.root, 3), n_u)
+    assert ccd["invalid"] == [2, 5] and len(ccd["umbrellas"]) == n_u
+
+
+def test_distill_c_every_epoch_invalid(env):
+    ctx, _ = env
+    km, Y, R, ms, s_ep = _epochs(65, 2, 4, 4)
+    for i in range(4):
+        _flip(ms, i, 0)
+    valid, ccd = _run(ctx, Y, ms, 4, s_ep, R, O.ds_root(km.root, 2), 2)
+    assert valid == [False] * 4 and ccd["s_v"] == bytes(32) and ccd["R_v"] == O.encode_point(O.IDENTITY)

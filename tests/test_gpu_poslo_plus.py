@@ -149,3 +149,29 @@ def test_multi_device_matches_definition(ctx):
     want_acc, want_pairs = O.verify_multi(devs)
     assert list(acc) == want_acc and [tuple(int(x) for x in p) for p in pairs] == want_pairs
     assert want_acc.count(False) == 2
+
+
+def test_serving_in_poslo_plus():
+    """The serving loop's workers inherit the context's instantiation."""
+    import __graft_entry__
+    __graft_entry__.build()
+    with O.instantiation("POSLO+"):
+        reqs = []
+        keys = []
+        for r in range(4):
+            km, sk, Y, msgs, subsets, s, R, _ = _f_data(2700 + r, 10 + 7 * r, 3, 4, 1, 40)
+            if r == 2:
+                msgs = synth.apply_tamper(msgs, synth.tamper_plan(2700 + r, msgs, 2))
+            ds_l = O.ds_root(km.root, 3)
+            want, _, _ = O.distill_f(Y, msgs.as_list(), 0, 4, s, R, ds_l)
+            keys.append(Y)
+            reqs.append((msgs, b"".join(s), b"".join(R), O.ds_serialize(ds_l), want))
+    with poslo.Context(device=0, instantiation=poslo.INST_AES) as ctx:
+        ctx.serve_start(workers=2)
+        kid = [ctx.register_key(Y) for Y in keys]
+        tickets = [ctx.submit(kid[i], 4, 0, m.data, m.offs, s, R, ds) for i, (m, s, R, ds, _) in enumerate(reqs)]
+        res = [ctx.poll(t, wait_ms=60000) for t in tickets]
+        ctx.serve_stop()
+    for (m, s, R, ds, want), r in zip(reqs, res):
+        assert (r[0], list(r[1])) == (not want, want)
+    assert any(want for *_, want in reqs)

@@ -67,3 +67,11 @@ def test_stream_honest_and_errors(data):
     with pytest.raises(poslo.PosloError) as e:
         ctx.distill_stream(b, 0)
     assert e.value.code == -1
+
+
+def test_stream_empty_batch(data):
+    ctx, Y, bad, s, R, ds_l, n2, want = data
+    e = synth.pack([])
+    b = ctx.make_batch(poslo.VARIANT_F, n2, Y, e.data, e.offs, b"", b"", O.ds_serialize(ds_l))
+    acc, idx = ctx.distill_stream(b, 16)
+    assert acc is True and len(idx) == 0
