@@ -539,10 +539,31 @@ def bench_serving(ctx_factory) -> dict:
     batches, nreq, _ = svc.serve_stats()
     svc.serve_stop()
     svc.close()
+    # the plain path for comparison: one request at a time through poslo_distill on one
+    # context, from the same pinned buffers, no batching
+    one = poslo.Context(device=0, verifier_seed=synth.verifier_seed(56))
+    single_lat = []
+    t_all = time.perf_counter()
+    for i, r in enumerate(reqs):
+        lo, hi = int(ebase[i]), int(ebase[i + 1])
+        b = one.make_batch(poslo.VARIANT_F, MULTI_N2, r["Y"], p_msgs, p_offs[int(obase[i]):int(obase[i + 1])],
+                           p_s[32 * lo:32 * hi], p_R[32 * lo:32 * hi], r["ds"])
+        t0 = time.perf_counter()
+        inv, _, _ = one.distill(b)
+        single_lat.append(time.perf_counter() - t0)
+        assert list(inv) == r["want"]
+    single_wall = time.perf_counter() - t_all
+    one.close()
+    single_lat = np.array(single_lat)
     return {"workload": f"{SERVE_KEYS} resident keys, {len(reqs)} requests of log-uniform [{SERVE_LO}, {SERVE_HI}] "
                         f"entries ({total} total), |m|~U[32,256], 1 % tampered, 64 GB budget, {SERVE_WORKERS} workers, "
                         "request data lent from pinned host memory (POSLO_REQ_BORROW)",
             "peak_entries_per_s": peak, "levels": levels, "batches": batches, "requests_served": nreq,
+            "one_request_at_a_time": {"entries_per_s": total / single_wall,
+                                      "p50_ms": float(np.percentile(single_lat, 50) * 1e3),
+                                      "p99_ms": float(np.percentile(single_lat, 99) * 1e3),
+                                      "note": "poslo_distill per request, sequential, same pinned inputs; "
+                                              "latency = its own verification time (no queue)"},
             "setup_s": setup_s}
 
 
