@@ -135,13 +135,20 @@ def probe_int_peaks(device: int) -> dict:
 
 # Algorithmic integer work per entry for the roofline (counted from the algorithms, not
 # from the compiled code):
-#   decoding R_t: 255 squarings + 20 multiplications in F_p; a schoolbook 8x8-limb product
-#     is 64 low + 64 high 32-bit multiply-adds, a squaring 36 + 36, each followed by a
-#     16 multiply-add fold by 38  -> 255*(72+18) + 20*(128+18) = 25,870 IMAD per entry
+#   decoding R_t (k_points): 255 squarings and 21 multiplications in F_p, plus the 7
+#     multiplications of its mixed addition into the unit sum.  Counted per half of a
+#     32x32-bit product: a squaring has 28 cross products and 8 diagonal squares (low and
+#     high halves) and a fold by 38 (8 low + 8 high + 1 low): 45 low, 44 high; a
+#     multiplication has 64 products and the fold: 73 low, 72 high.
+#   mad.hi issues at half the rate of mad.lo on this GPU (probed), so the work is expressed
+#     in mad.lo issue slots: low + high x (mad.lo rate / mad.hi rate).
 #   SHA-256: 1,384 ALU instructions per compression with 3-input LOP3/IADD3 and funnel
 #     shifts (64 rounds x 14 + 48 schedule words x 10 + 8); compressions per entry =
 #     1 (PRF) + ceil((L + 25) / 64) (H)
-IMAD_PER_DECODE = 255 * (72 + 18) + 20 * (128 + 18)
+SQ_LO, SQ_HI, MUL_LO, MUL_HI = 45, 44, 73, 72
+DECODE_SQ, DECODE_MUL = 255, 21 + 7
+IMAD_LO_PER_DECODE = DECODE_SQ * SQ_LO + DECODE_MUL * MUL_LO    # 13,519
+IMAD_HI_PER_DECODE = DECODE_SQ * SQ_HI + DECODE_MUL * MUL_HI    # 13,236
 ALU_PER_COMPRESSION = 64 * 14 + 48 * 10 + 8
 # DRAM bytes (read + write) of one k_points launch over 2^20 entries, from an ncu capture:
 # the 32 MB of encodings read once; of the 100 MB of decoded points written, the part that has
@@ -227,6 +234,7 @@ def bench_multi(ctx, steps: int, warmup: int) -> dict:
             d_msgs, d_offs, d_s, d_R)
     torch.cuda.synchronize()
     msm_window = ctx.msm_autotune(w["total"], 4)
+    msm_range = ctx.msm_get_plan(w["total"], 4)[1]
     for _ in range(warmup):
         acc, pairs = ctx.aver_multi(*args)
     got = [(int(a), int(b)) for a, b in pairs]
@@ -255,7 +263,8 @@ def bench_multi(ctx, steps: int, warmup: int) -> dict:
     return {"workload": f"{nd} devices, sizes log-uniform [{MULTI_LO}, {MULTI_HI}] (total {w['total']} entries), "
                         f"|m|~U[32,256], {len(w['pairs'])} devices with one flipped byte",
             "value": w["total"] / (ms * 1e-3), "unit": "entries/s", "ms_per_step": ms, "steps": steps,
-            "invalid_found": len(got), "setup_s": setup_s, "msm_window": msm_window, "stages": stages}
+            "invalid_found": len(got), "setup_s": setup_s, "msm_window": msm_window, "msm_range_log2": msm_range,
+            "stages": stages}
 
 
 # ------------------------------------------------------------------------------ out of core
@@ -690,6 +699,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     batch = ctx.make_batch(poslo.VARIANT_F, N2, Y, d_msgs, d_offs, d_s, d_R, ds)
     msm_window = ctx.msm_autotune(n, 4)   # window width of the weighted MSM, timed on this GPU
+    msm_range = ctx.msm_get_plan(n, 4)[1]
 
     def step(b):
         idx, cs, cR = ctx.distill(b)
@@ -773,7 +783,8 @@ def run_ours(args):
         if kernels else None
     roof = None
     if dom in ("points", "check") and peaks:
-        work = n * IMAD_PER_DECODE
+        hi_cost = peaks["imad_lo_ops"] / peaks["imad_hi_ops"]
+        work = n * (IMAD_LO_PER_DECODE + IMAD_HI_PER_DECODE * hi_cost)
         ach = work / (kernels[dom]["ms_per_launch"] * 1e-3) / 1e9
         pk = peaks["imad_lo_ops"] / 1e9
         roof = {"bound": "alu", "pipe": "IMAD", "kernel": dom, "achieved": ach, "peak": pk, "unit": "Gop/s",
@@ -781,7 +792,10 @@ def run_ours(args):
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_points launch "
                                   "at 2^20 entries (profiles/ncu_full_hash_points_msm_2p20.md)",
                 "peak_source": "probed mad.lo.u32 issue rate on this GPU (probe/peaks.cu)",
-                "work": "25,870 IMAD per R_t decode (schoolbook count)"}
+                "work": f"{IMAD_LO_PER_DECODE:,} mad.lo + {IMAD_HI_PER_DECODE:,} mad.hi per R_t decode and its "
+                        f"unit-sum addition; mad.hi counted as {hi_cost:.2f} mad.lo issue slots (probed rate ratio)",
+                "timing": "k_points duration on its own stream during the timed steps (it shares the GPU with "
+                          "the hashing and the counting sort, so this understates the kernel alone)"}
     elif dom == "hash" and peaks:
         work = compressions(msgs) * ALU_PER_COMPRESSION
         ach = work / (kernels[dom]["ms_per_launch"] * 1e-3) / 1e9
@@ -803,7 +817,8 @@ def run_ours(args):
                                     "poslo_keygen_f/poslo_sign_f)",
             "config": {"workload": WORKLOAD, "entries_per_gpu": n, "message_bytes": int(msgs.data.nbytes),
                        "l2": "inputs (215 MB) larger than the 129 MB L2; no flush", "parallelism": f"dp{world}",
-                       "msm_window": msm_window, "msm_window_source": "poslo_msm_autotune"},
+                       "msm_window": msm_window, "msm_range_log2": msm_range,
+                       "msm_plan_source": "poslo_msm_autotune"},
             "clocks": clocks,
             "gpu_launches": gpu_launches,
             "kernels": kernels,

@@ -264,11 +264,29 @@ int poslo_msm(poslo_ctx* ctx, const uint8_t* points, const uint8_t* scalars, uin
  * floor(log2 n), on n synthetic points with random scalars of scalar_words 32-bit words (4:
  * the 127-bit verification weights; 8: 256-bit scalars) and keeps the fastest for every later
  * MSM of that size class and scalar width on this context, unless poslo_params.msm_window
- * fixes c.  Untuned classes use c = min(16, max(8, lg - 4)).  Writes the chosen c to
+ * fixes c; with each width it also times the accumulation's range lengths (see
+ * poslo_msm_get_plan).  Untuned classes use c = min(16, max(8, lg - 4)).  Writes the chosen c to
  * window_out (optional).  Allocates about (96 + 4 scalar_words + 16 windows) bytes per point
  * of grow-only scratch.  EINVAL for n = 0, n > 2^32 or another scalar width.  Blocks until
  * the timing runs finish; takes tens of milliseconds per width at n = 2^20. */
 int poslo_msm_autotune(poslo_ctx* ctx, uint64_t n, uint32_t scalar_words, uint32_t* window_out);
+
+/* The bucket-MSM plan of a size class (no counterpart in the paper).  A plan is the window
+ * width c and the range length 2^range_log2: each thread of the bucket accumulation adds
+ * 2^range_log2 consecutive entries of the digit-sorted list, and the pieces of a bucket that
+ * crosses ranges are joined afterwards.  poslo_msm_autotune times every range length from
+ * 2^4 up to the average bucket size (at most 2^8) beside every width; untuned classes take
+ * 2^4, doubled while a bucket averages at least two ranges of the doubled length and the
+ * accumulation keeps 1,024 threads per SM.
+ * poslo_msm_get_plan writes the plan the next MSM of n entries with scalar_words-word scalars
+ * would use (either output may be NULL).  poslo_msm_set_plan stores a plan for n's size class
+ * floor(log2 n), e.g. one that an earlier process's autotuner found; a width fixed by
+ * poslo_params.msm_window still wins over it.  Both only touch the context's host-side
+ * table: no device work, no allocation.  EINVAL for another scalar width, c outside
+ * [8, 16] or range_log2 outside [4, 8]. */
+int poslo_msm_get_plan(poslo_ctx* ctx, uint64_t n, uint32_t scalar_words, uint32_t* window_out,
+                       uint32_t* range_log2_out);
+int poslo_msm_set_plan(poslo_ctx* ctx, uint64_t n, uint32_t scalar_words, uint32_t window, uint32_t range_log2);
 
 /* ---- out-of-core verification --------------------------------------------------------- */
 

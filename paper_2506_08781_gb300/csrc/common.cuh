@@ -468,7 +468,8 @@ struct SignCArgs {
 // index), and the windows are joined by Horner's rule in one warp with quad-cooperative
 // doublings.
 constexpr int kMsmChunk = 16;
-constexpr int kMsmSeg = 16;     // sorted entries per thread in the bucket accumulation
+constexpr int kMsmSegLog2Min = 4;    // sorted entries per accumulation thread: 2^4 .. 2^8
+constexpr int kMsmSegLog2Max = 8;
 
 // Pippenger plan with signed window digits.  Scalars of `sw` words hold at most `bits` bits
 // (127 for the 4-word weights z_t, whose top bit is clear; 256 for 8-word scalars); windows =
@@ -482,6 +483,7 @@ struct MsmPlan {
   uint32_t nb;        // buckets per window, 2^(c-1) + kMsmChunk (bucket 0 and the padding stay empty)
   uint32_t nchunks;   // nb / kMsmChunk = 2^(c-5) + 1
   int jbits;          // bits of the largest chunk index 2^(c-5): c - 4
+  int seg_log2;       // each accumulation thread adds 2^seg_log2 sorted entries (a range)
 };
 
 // Unsigned c-bit field w of the scalar (0 past its last word).
@@ -607,7 +609,7 @@ __global__ void __launch_bounds__(128) k_msm_accum(const uint32_t* pts, const ui
 __global__ void __launch_bounds__(128) k_msm_combine(const uint32_t* off, const uint32_t* cnt, uint64_t n, MsmPlan pl,
                                                      const uint32_t* A, const uint32_t* B, uint32_t* buckets,
                                                      uint32_t* big_list, uint32_t* big_count);
-constexpr int kCombineBigThreads = 512;
+constexpr int kCombineBigThreads = 128;
 __global__ void __launch_bounds__(kCombineBigThreads) k_msm_combine_big(const uint32_t* off, const uint32_t* cnt,
                                                                         uint64_t n, MsmPlan pl, const uint32_t* A,
                                                                         const uint32_t* B, uint32_t* buckets,

@@ -50,7 +50,7 @@ struct poslo_ctx {
   std::map<std::string, poslo_host::KernelTimer> timers;
   std::vector<std::pair<std::string, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
   std::vector<cudaEvent_t> event_pool;
-  std::map<int, int> msm_tuned;   // (log2 n) * 16 + scalar words -> best window c
+  std::map<int, int> msm_tuned;   // (log2 n) * 16 + scalar words -> best window c | range log2 << 8
   poslo_host::Server* server = nullptr;
 };
 

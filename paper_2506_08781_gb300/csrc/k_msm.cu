@@ -82,24 +82,25 @@ __global__ void k_msm_scatter(const uint32_t* z, const uint8_t* skip, uint64_t n
 }
 
 // Bucket sums B_{w,d} = sum of sign(digit) P_t over the entries whose digit in window w has
-// magnitude d, load-balanced: thread (w, tau) adds exactly the kMsmSeg sorted entries
-// at positions [tau kMsmSeg, (tau+1) kMsmSeg) of window w, cutting its run wherever the
+// magnitude d, load-balanced: thread (w, tau) adds exactly the S = 2^seg_log2 sorted entries
+// at positions [tau S, (tau+1) S) of window w (range tau), cutting its run wherever the
 // bucket changes.  A bucket lying strictly inside the range is written directly; the first
 // run goes to A[w][tau], the last (when different) to B[w][tau], and k_msm_combine joins
 // the pieces of buckets that cross range boundaries.
 __global__ void __launch_bounds__(128) k_msm_accum(const uint32_t* pts, const uint32_t* idx, const uint16_t* bkt,
                                                    const uint32_t* off, const uint32_t* cnt, uint64_t n, MsmPlan pl,
                                                    const uint8_t* skip, uint32_t* buckets, uint32_t* A, uint32_t* B) {
-  const uint64_t nseg = (n + kMsmSeg - 1) / kMsmSeg;
+  const uint64_t seg = 1ull << pl.seg_log2;
+  const uint64_t nseg = (n + seg - 1) >> pl.seg_log2;
   const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= (uint64_t)pl.windows * nseg) return;
   const uint32_t w = (uint32_t)(g / nseg);
   const uint64_t tau = g % nseg;
   const size_t last = (size_t)w * pl.nb + pl.nb - 1;
   const uint64_t nnz = (uint64_t)off[last] + cnt[last];
-  const uint64_t p0 = tau * kMsmSeg;
+  const uint64_t p0 = tau << pl.seg_log2;
   if (p0 >= nnz) return;
-  const uint64_t p1 = min(p0 + kMsmSeg, nnz);
+  const uint64_t p1 = min(p0 + seg, nnz);
   const uint32_t* li = idx + (size_t)w * n;
   const uint16_t* lb = bkt + (size_t)w * n;
   uint32_t cur = lb[p0] & kBktMask;
@@ -150,10 +151,10 @@ __device__ __forceinline__ CombineSpan combine_span(const uint32_t* off, const u
   const uint64_t nnz = (uint64_t)off[last] + cnt[last];
   const uint64_t s = off[b], e = s + cnt[b] - 1;
   CombineSpan c;
-  c.ts = s / kMsmSeg;
-  c.te = e / kMsmSeg;
-  const uint64_t r_end = min((c.ts + 1) * kMsmSeg, nnz) - 1;   // last position of range ts
-  c.starts_range = s == c.ts * kMsmSeg;
+  c.ts = s >> pl.seg_log2;
+  c.te = e >> pl.seg_log2;
+  const uint64_t r_end = min((c.ts + 1) << pl.seg_log2, nnz) - 1;   // last position of range ts
+  c.starts_range = s == c.ts << pl.seg_log2;
   c.whole = !c.starts_range && e < r_end;
   return c;
 }
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(128) k_msm_combine(const uint32_t* off, const 
     big_list[atomicAdd(big_count, 1u)] = (uint32_t)b;
     return;
   }
-  const uint64_t g0 = (uint64_t)w * ((n + kMsmSeg - 1) / kMsmSeg);
+  const uint64_t g0 = (uint64_t)w * ((n + (1ull << pl.seg_log2) - 1) >> pl.seg_log2);
   ge acc = ge_load((c.starts_range ? A : B) + 32 * (g0 + c.ts));
   for (uint64_t t = c.ts + 1; t <= c.te; ++t) acc = ge_add(acc, ge_load(A + 32 * (g0 + t)));
   ge_store(buckets + 32 * b, acc);
@@ -193,34 +194,29 @@ __device__ __forceinline__ ge ge_shfl_down(const ge& p, int delta) {
   return r;
 }
 
-// The listed wide buckets, one block each: the threads sum the ranges' first runs with a
-// stride of the block size, a shuffle tree joins each warp, and the first warp joins the
-// warps' sums.  The grid is fixed; blocks stride over the list.
+// The listed wide buckets, one warp each: the lanes sum the ranges' first runs with a
+// stride of 32 (lane 0 starting from the bucket's first run), and a shuffle tree joins the
+// lanes.  The grid is fixed; warps stride over the list (the trip count is uniform across a
+// warp, so every lane takes part in every shuffle).
 __global__ void __launch_bounds__(kCombineBigThreads) k_msm_combine_big(const uint32_t* off, const uint32_t* cnt,
                                                                         uint64_t n, MsmPlan pl, const uint32_t* A,
                                                                         const uint32_t* B, uint32_t* buckets,
                                                                         const uint32_t* big_list,
                                                                         const uint32_t* big_count) {
-  __shared__ uint32_t ws[kCombineBigThreads / 32][32];
-  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t warp = ((uint32_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = ((uint32_t)gridDim.x * blockDim.x) >> 5;
   const uint32_t total = *big_count;
-  const uint64_t nseg = (n + kMsmSeg - 1) / kMsmSeg;
-  for (uint32_t i = blockIdx.x; i < total; i += gridDim.x) {
+  const uint64_t nseg = (n + (1ull << pl.seg_log2) - 1) >> pl.seg_log2;
+  for (uint32_t i = warp; i < total; i += nwarps) {
     const uint64_t b = big_list[i];
     const uint32_t w = (uint32_t)(b / pl.nb);
     const CombineSpan c = combine_span(off, cnt, pl, b);
     const uint64_t g0 = (uint64_t)w * nseg;
-    ge acc = threadIdx.x == 0 ? ge_load((c.starts_range ? A : B) + 32 * (g0 + c.ts)) : ge_identity();
-    for (uint64_t t = c.ts + 1 + threadIdx.x; t <= c.te; t += blockDim.x) acc = ge_add(acc, ge_load(A + 32 * (g0 + t)));
+    ge acc = lane == 0 ? ge_load((c.starts_range ? A : B) + 32 * (g0 + c.ts)) : ge_identity();
+    for (uint64_t t = c.ts + 1 + lane; t <= c.te; t += 32) acc = ge_add(acc, ge_load(A + 32 * (g0 + t)));
     for (int delta = 16; delta > 0; delta >>= 1) acc = ge_add(acc, ge_shfl_down(acc, delta));
-    if (lane == 0) ge_store(ws[warp], acc);
-    __syncthreads();
-    if (warp == 0) {
-      acc = lane < kCombineBigThreads / 32 ? ge_load(ws[lane]) : ge_identity();
-      for (int delta = 16; delta > 0; delta >>= 1) acc = ge_add(acc, ge_shfl_down(acc, delta));
-      if (lane == 0) ge_store(buckets + 32 * b, acc);
-    }
-    __syncthreads();
+    if (lane == 0) ge_store(buckets + 32 * b, acc);
   }
 }
 

@@ -394,9 +394,9 @@ int run_points(poslo_ctx* ctx, const uint8_t* R, uint64_t count, uint32_t* pts_o
 }
 
 // Pippenger plan: the window c comes from the context (poslo_params.msm_window) or from the
-// autotuned table for this size class (see autotune_msm); the default before tuning is
+// autotuned table for this size class (see poslo_msm_autotune); the default before tuning is
 // c = log2(n) - 4 clamped to [8, 16].
-MsmPlan msm_plan_c(int c, int sw) {
+MsmPlan msm_plan_c(int c, int sw, int seg_log2 = kMsmSegLog2Min) {
   MsmPlan pl;
   pl.c = c;
   pl.sw = sw;
@@ -405,7 +405,21 @@ MsmPlan msm_plan_c(int c, int sw) {
   pl.nb = (1u << (c - 1)) + kMsmChunk;
   pl.nchunks = pl.nb / kMsmChunk;
   pl.jbits = c - 4;
+  pl.seg_log2 = seg_log2;
   return pl;
+}
+
+// Range length 2^lg of the bucket accumulation when it is not tuned: 16 sorted entries,
+// doubled while a bucket still averages at least two ranges of the doubled length (so that
+// joining the pieces of a bucket stays a short chain) and the accumulation keeps at least
+// 1,024 threads per SM.
+int msm_seg_default(const MsmPlan& pl, uint64_t n, int sm_count) {
+  int lg = kMsmSegLog2Min;
+  const uint64_t per_bucket = n >> (pl.c - 1);
+  while (lg < kMsmSegLog2Max && (4ull << lg) <= per_bucket &&
+         ((uint64_t)pl.windows * n >> (lg + 1)) >= 1024ull * (uint64_t)sm_count)
+    ++lg;
+  return lg;
 }
 
 // A width is balanced when the last window still holds at least 5 bits of the scalar: with
@@ -434,9 +448,12 @@ MsmPlan msm_plan(poslo_ctx* ctx, uint64_t n, int sw) {
   if (c == 0) {
     const int lg = log2_floor(n);
     auto it = ctx->msm_tuned.find(lg * 16 + sw);
-    c = it != ctx->msm_tuned.end() ? it->second : msm_balanced_width(std::min(16, std::max(8, lg - 4)), sw);
+    if (it != ctx->msm_tuned.end()) return msm_plan_c(it->second & 0xff, sw, it->second >> 8);
+    c = msm_balanced_width(std::min(16, std::max(8, lg - 4)), sw);
   }
-  return msm_plan_c(c, sw);
+  MsmPlan pl = msm_plan_c(c, sw);
+  pl.seg_log2 = msm_seg_default(pl, n, ctx->sm_count);
+  return pl;
 }
 
 // Pippenger in two halves so the counting sort (which needs only the scalars) can run
@@ -484,7 +501,7 @@ int run_msm_finish(poslo_ctx* ctx, cudaStream_t st, const uint32_t* pts, const u
   const MsmPlan& pl = ms.pl;
   const uint64_t n = ms.n;
   const size_t nbw = (size_t)pl.windows * pl.nb;
-  const uint64_t nseg = (std::max<uint64_t>(n, 1) + kMsmSeg - 1) / kMsmSeg;
+  const uint64_t nseg = (std::max<uint64_t>(n, 1) + (1ull << pl.seg_log2) - 1) >> pl.seg_log2;
   uint32_t *buckets, *L, *T, *groups, *segA, *segB;
   if ((rc = ensure_t(ctx, "msm_buckets", 128 * nbw, &buckets))) return rc;
   if ((rc = ensure_t(ctx, "msm_segA", 128 * (size_t)pl.windows * nseg, &segA))) return rc;
@@ -505,7 +522,7 @@ int run_msm_finish(poslo_ctx* ctx, cudaStream_t st, const uint32_t* pts, const u
   CU(cudaMemsetAsync(big, 0, 4, st));
   k_msm_combine<<<(unsigned)((nbw + 127) / 128), 128, 0, st>>>(ms.off, ms.cnt, std::max<uint64_t>(n, 1), pl, segA,
                                                               segB, buckets, big + 1, big);
-  k_msm_combine_big<<<2 * ctx->sm_count, kCombineBigThreads, 0, st>>>(ms.off, ms.cnt, std::max<uint64_t>(n, 1), pl,
+  k_msm_combine_big<<<3 * ctx->sm_count, kCombineBigThreads, 0, st>>>(ms.off, ms.cnt, std::max<uint64_t>(n, 1), pl,
                                                                       segA, segB, buckets, big + 1, big);
   ctx->launch_count += 2;
   timer_end(ctx, "msm_bucket", st, sb_, se_);
@@ -1349,30 +1366,55 @@ int poslo_msm_autotune(poslo_ctx* ctx, uint64_t n, uint32_t scalar_words, uint32
   cudaEvent_t e0, e1;
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
-  int best_c = 0;
+  int best_c = 0, best_seg = kMsmSegLog2Min;
   float best_ms = 0.f;
   const int c_lo = std::max(8, std::min(16, lg - 8)), c_hi = std::min(16, std::max(8, lg - 1));
   for (int c = c_lo; c <= c_hi && rc == POSLO_OK; ++c) {
     if (!msm_width_balanced(c, sw)) continue;
-    const MsmPlan forced = msm_plan_c(c, sw);
-    float ms = 0.f;
-    for (int rep = 0; rep < 2 && rc == POSLO_OK; ++rep) {   // the first run grows the buffers
-      MsmState st;
-      cudaEventRecord(e0, ctx->s_main);
-      if ((rc = run_msm_sort(ctx, ctx->s_main, z, sw, nullptr, n, st, &forced))) break;
-      if ((rc = run_msm_finish(ctx, ctx->s_main, pts, nullptr, st, acc))) break;
-      cudaEventRecord(e1, ctx->s_main);
-      if (cudaEventSynchronize(e1) != cudaSuccess) rc = fail(ctx, POSLO_EDEVICE, "msm_autotune: %s", "sync failed");
-      else cudaEventElapsedTime(&ms, e0, e1);
+    // range lengths 2^4 .. 2^8, no longer than an average bucket and leaving at least 512
+    // accumulation threads per SM
+    const uint64_t per_bucket = n >> (c - 1);
+    for (int sl = kMsmSegLog2Min; sl <= kMsmSegLog2Max && rc == POSLO_OK; ++sl) {
+      const MsmPlan forced = msm_plan_c(c, sw, sl);
+      if (sl > kMsmSegLog2Min &&
+          ((1ull << sl) > per_bucket || ((uint64_t)forced.windows * n >> sl) < 512ull * (uint64_t)ctx->sm_count))
+        break;
+      float ms = 0.f;
+      for (int rep = 0; rep < 2 && rc == POSLO_OK; ++rep) {   // the first run grows the buffers
+        MsmState st;
+        cudaEventRecord(e0, ctx->s_main);
+        if ((rc = run_msm_sort(ctx, ctx->s_main, z, sw, nullptr, n, st, &forced))) break;
+        if ((rc = run_msm_finish(ctx, ctx->s_main, pts, nullptr, st, acc))) break;
+        cudaEventRecord(e1, ctx->s_main);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = fail(ctx, POSLO_EDEVICE, "msm_autotune: %s", "sync failed");
+        else cudaEventElapsedTime(&ms, e0, e1);
+      }
+      if (rc == POSLO_OK && (best_c == 0 || ms < best_ms)) { best_c = c; best_seg = sl; best_ms = ms; }
     }
-    if (rc == POSLO_OK && (best_c == 0 || ms < best_ms)) { best_c = c; best_ms = ms; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) return rc;
   if ((rc = check_status(ctx))) return rc;
-  ctx->msm_tuned[lg * 16 + sw] = best_c;
+  ctx->msm_tuned[lg * 16 + sw] = best_c | (best_seg << 8);
   if (window_out) *window_out = (uint32_t)best_c;
+  return POSLO_OK;
+}
+
+int poslo_msm_get_plan(poslo_ctx* ctx, uint64_t n, uint32_t scalar_words, uint32_t* window_out,
+                       uint32_t* range_log2_out) {
+  if (!ctx || (scalar_words != 4 && scalar_words != 8)) return fail(ctx, POSLO_EINVAL, "bad msm_get_plan arguments");
+  const MsmPlan pl = msm_plan(ctx, n, (int)scalar_words);
+  if (window_out) *window_out = (uint32_t)pl.c;
+  if (range_log2_out) *range_log2_out = (uint32_t)pl.seg_log2;
+  return POSLO_OK;
+}
+
+int poslo_msm_set_plan(poslo_ctx* ctx, uint64_t n, uint32_t scalar_words, uint32_t window, uint32_t range_log2) {
+  if (!ctx || (scalar_words != 4 && scalar_words != 8) || window < 8 || window > 16 ||
+      range_log2 < (uint32_t)kMsmSegLog2Min || range_log2 > (uint32_t)kMsmSegLog2Max)
+    return fail(ctx, POSLO_EINVAL, "bad msm_set_plan arguments");
+  ctx->msm_tuned[log2_floor(n) * 16 + (int)scalar_words] = (int)window | ((int)range_log2 << 8);
   return POSLO_OK;
 }
 

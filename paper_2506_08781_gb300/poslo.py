@@ -28,6 +28,7 @@ EXPORTS = [
     "poslo_create", "poslo_destroy", "poslo_last_error", "poslo_stream",
     "poslo_keygen_c", "poslo_keygen_f", "poslo_sign_c", "poslo_sign_f", "poslo_disclose",
     "poslo_aver", "poslo_distill", "poslo_epoch_seeds", "poslo_hash_entries", "poslo_msm", "poslo_msm_autotune",
+    "poslo_msm_get_plan", "poslo_msm_set_plan",
     "poslo_set_profiling", "poslo_kernel_time", "poslo_reset_kernel_times",
     "poslo_hash_entries_noalloc", "poslo_aver_multi", "poslo_distill_c", "poslo_sebver_c", "poslo_distill_stream",
     "poslo_serve_start", "poslo_serve_stop", "poslo_register_key", "poslo_submit", "poslo_poll",
@@ -104,6 +105,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "poslo_hash_entries": ([vp, C.POINTER(Batch), u8p], C.c_int),
         "poslo_msm": ([vp, u8p, u8p, u64, u32, u8p], C.c_int),
         "poslo_msm_autotune": ([vp, u64, u32, C.POINTER(u32)], C.c_int),
+        "poslo_msm_get_plan": ([vp, u64, u32, C.POINTER(u32), C.POINTER(u32)], C.c_int),
+        "poslo_msm_set_plan": ([vp, u64, u32, u32, u32], C.c_int),
         "poslo_set_profiling": ([vp, C.c_int], C.c_int),
         "poslo_kernel_time": ([vp, C.c_char_p, C.POINTER(C.c_double), C.POINTER(u64)], C.c_int),
         "poslo_reset_kernel_times": ([vp], None),
@@ -468,6 +471,16 @@ class Context:
         c = C.c_uint32(0)
         self._check(self.lib.poslo_msm_autotune(self.h, n, scalar_words, C.byref(c)))
         return int(c.value)
+
+    def msm_get_plan(self, n: int, scalar_words: int = 4):
+        """(window c, range log2) the next MSM of n entries would use."""
+        c, r = C.c_uint32(0), C.c_uint32(0)
+        self._check(self.lib.poslo_msm_get_plan(self.h, n, scalar_words, C.byref(c), C.byref(r)))
+        return int(c.value), int(r.value)
+
+    def msm_set_plan(self, n: int, window: int, range_log2: int, scalar_words: int = 4):
+        """Store a plan for the size class of n."""
+        self._check(self.lib.poslo_msm_set_plan(self.h, n, scalar_words, window, range_log2))
 
     # ------------------------------------------------------------------ profiling
     def set_profiling(self, on: bool):

@@ -355,6 +355,88 @@ def test_msm_concentrated_scalars(c):
     assert got == want
 
 
+@pytest.mark.parametrize("r", [4, 5, 6, 7, 8])
+def test_msm_every_range_length(r):
+    """Every range length 2^r of the bucket accumulation (buckets inside one range, buckets
+    across ranges, a ragged last range) gives the definition's result."""
+    import __graft_entry__
+    __graft_entry__.build()
+    n = 700
+    pts = [O.encode_point(O.scalar_mult(9 + 13 * i, O.G)) for i in range(n)]
+    ks = [int.from_bytes(synth.random_bytes(40 + r, f"r{i}", 32).tobytes(), "little") % O.Q for i in range(n)]
+    with poslo.Context(device=0) as cx:
+        cx.msm_set_plan(n, 10, r, scalar_words=8)
+        assert cx.msm_get_plan(n, 8) == (10, r)
+        got = cx.msm(b"".join(pts), b"".join(k.to_bytes(32, "little") for k in ks))
+    assert got == O.msm(ks, pts)
+
+
+@pytest.mark.parametrize("c,r", [(8, 6), (12, 8)])
+def test_msm_concentrated_scalars_long_ranges(c, r):
+    """Two scalar values over 2,500 entries with ranges of 2^r: each window's two buckets span
+    many ranges (the wide-bucket join with warps striding over the ranges)."""
+    import __graft_entry__
+    __graft_entry__.build()
+    n = 2500
+    P = [O.G]
+    for _ in range(n - 1):
+        P.append(O.point_add(P[-1], O.G))
+    a = int.from_bytes(synth.random_bytes(c + r, "la", 32).tobytes(), "little") % O.Q
+    b = int.from_bytes(synth.random_bytes(c + r, "lb", 32).tobytes(), "little") % O.Q
+    ks = [a if i % 4 else b for i in range(n)]
+    Sa, Sb = O.IDENTITY, O.IDENTITY
+    for i in range(n):
+        if i % 4:
+            Sa = O.point_add(Sa, P[i])
+        else:
+            Sb = O.point_add(Sb, P[i])
+    want = O.encode_point(O.point_add(O.scalar_mult(a, Sa), O.scalar_mult(b, Sb)))
+    with poslo.Context(device=0) as cx:
+        cx.msm_set_plan(n, c, r, scalar_words=8)
+        got = cx.msm(b"".join(O.encode_point(p) for p in P), b"".join(k.to_bytes(32, "little") for k in ks))
+    assert got == want
+
+
+@pytest.mark.parametrize("r", [5, 8])
+def test_weighted_checks_every_range_length(r):
+    """Weighted AVer and Distill with 127-bit weights keep the per-entry definition's result
+    when the accumulation ranges are long."""
+    import __graft_entry__
+    __graft_entry__.build()
+    D, n2, n = 6, 16, 600
+    km, sk, Y, msgs, subsets, s, R, _ = _f_data(60 + r, n, D, n2, 1, 60)
+    ds_l = O.ds_root(km.root, D)
+    bad = synth.apply_tamper(msgs, synth.tamper_plan(60 + r, msgs, 9))
+    with poslo.Context(device=0) as cx:
+        for k in (1, 2, 4, 8, 16, 32, 64, 128, 256, 512):
+            cx.msm_set_plan(k, 10, r)     # every size class the bisection's MSMs can fall in
+        for m in (msgs, bad):
+            b = cx.make_batch(poslo.VARIANT_F, n2, Y, m.data, m.offs, b"".join(s), b"".join(R),
+                              O.ds_serialize(ds_l))
+            wi, ws, wR = O.distill_f(Y, m.as_list(), 0, n2, s, R, ds_l)
+            assert cx.aver(b, poslo.AGG_WEIGHTED) is (len(wi) == 0)
+            idx, cs, cR = cx.distill(b)
+            assert list(idx) == wi and cs == ws and cR == wR
+
+
+def test_msm_plan_table():
+    """The plan table: defaults, a stored plan per size class, a fixed width winning, and
+    argument checks."""
+    with poslo.Context(device=0) as cx:
+        assert cx.msm_get_plan(1 << 20) == (16, 4)
+        assert cx.msm_get_plan(30_000_000) == (16, 8)
+        cx.msm_set_plan(1 << 20, 13, 6)
+        assert cx.msm_get_plan((1 << 21) - 1) == (13, 6)
+        assert cx.msm_get_plan(1 << 21) == (16, 5)      # 64 entries per bucket: ranges of 32
+        for bad in [(1 << 20, 7, 4), (1 << 20, 17, 4), (1 << 20, 12, 3), (1 << 20, 12, 9)]:
+            with pytest.raises(poslo.PosloError) as e:
+                cx.msm_set_plan(*bad)
+            assert e.value.code == -1
+    with poslo.Context(device=0, msm_window=11) as cx:
+        cx.msm_set_plan(1 << 20, 13, 6)
+        assert cx.msm_get_plan(1 << 20)[0] == 11
+
+
 def test_msm_rejects_undecodable_point(ctx):
     y = 2
     while O.decode_point(y.to_bytes(32, "little")) is not None:
