@@ -267,6 +267,42 @@ def bench_multi(ctx, steps: int, warmup: int) -> dict:
             "stages": stages}
 
 
+# ------------------------------------------------------------------------------ graph replay
+
+REPLAY_DEVICES, REPLAY_LO, REPLAY_HI, REPLAY_CALLS = 64, 16, 1024, 40
+
+
+def bench_graph_replay(ctx) -> dict:
+    """A small multi-device batch verified again and again with the same layout (a gateway
+    re-checking a fixed fleet): per-call wall time with the launch sequence replayed from a
+    CUDA graph against the same calls launched kernel by kernel."""
+    import torch
+    w = make_multi_workload(ctx, n_dev=REPLAY_DEVICES, lo=REPLAY_LO, hi=REPLAY_HI, seed=6)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    args = (w["Y"], w["sizes"], np.zeros(REPLAY_DEVICES, np.uint64), np.full(REPLAY_DEVICES, MULTI_N2, np.uint32),
+            w["ds"], dev(w["msgs"].data), dev(w["msgs"].offs.view(np.int64)), dev(w["s"]), dev(w["R"]))
+    torch.cuda.synchronize()
+    out = {"workload": f"{REPLAY_DEVICES} devices, sizes log-uniform [{REPLAY_LO}, {REPLAY_HI}] "
+                       f"(total {w['total']} entries), device-resident, {len(w['pairs'])} tampered devices",
+           "calls": REPLAY_CALLS}
+    for mode in ("launched", "graph"):
+        ctx.set_graphs(mode == "graph")
+        for _ in range(3):
+            ctx.aver_multi(*args)
+        c0 = ctx.graph_stats()
+        times = []
+        for _ in range(REPLAY_CALLS):
+            t0 = time.perf_counter()
+            acc, pairs = ctx.aver_multi(*args)
+            times.append(time.perf_counter() - t0)
+        assert [(int(a), int(b)) for a, b in pairs] == w["pairs"]
+        c1 = ctx.graph_stats()
+        out[mode] = {"ms_per_call_p50": float(np.percentile(times, 50) * 1e3),
+                     "ms_per_call_mean": float(np.mean(times) * 1e3), "replays": c1[1] - c0[1]}
+    ctx.set_graphs(True)
+    return out
+
+
 # ------------------------------------------------------------------------------ out of core
 
 STREAM_CHUNKS = 8                      # 8 x 2^20 entries (1.2 GB of messages) from pinned host memory
@@ -749,9 +785,23 @@ def run_ours(args):
     torch.cuda.synchronize()
     aver_ms = e0.elapsed_time(e1) / args.steps
 
+    # the same step with the launch sequence replayed from a CUDA graph (no per-kernel events)
+    for _ in range(2):
+        step(batch)
+    g0 = ctx.graph_stats()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(batch)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    g1 = ctx.graph_stats()
+    graph_step = {"ms_per_step": e0.elapsed_time(e1) / args.steps, "replays": g1[1] - g0[1]}
+
     multi = None
+    replay = None
     if not args.no_multi and world == 1:
         multi = bench_multi(ctx, steps=max(2, args.steps // 5), warmup=2)
+        replay = bench_graph_replay(ctx)
     serving = None
     if not args.no_serving and world == 1:
         serving = bench_serving(lambda: poslo.Context(device=device))
@@ -823,10 +873,12 @@ def run_ours(args):
             "gpu_launches": gpu_launches,
             "kernels": kernels,
             "aver_unit": {"value": n / (aver_ms * 1e-3), "ms_per_step": aver_ms},
+            "step_graph_replay": graph_step,
             "e2e": {"value": world * n / e2e_s, "unit": "entries/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "roofline": roof,
             "multi_device": multi,
+            "small_batch_graph_replay": replay,
             "hash_bound_poslo_c": hash_bound,
             "out_of_core": stream,
             "serving": serving,

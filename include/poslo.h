@@ -369,6 +369,23 @@ int poslo_set_profiling(poslo_ctx* ctx, int enabled);
 int poslo_kernel_time(poslo_ctx* ctx, const char* name, double* total_ms, uint64_t* launches);
 void poslo_reset_kernel_times(poslo_ctx* ctx);
 
+/* ---- CUDA-graph replay (no counterpart in the paper) ------------------------------------ */
+
+/* poslo_aver_multi and poslo_distill run their work up to the first host decision (the
+ * combined weighted check) as a fixed sequence of launches.  When a call has the same shape
+ * as the previous call of that entry point on this context -- for poslo_aver_multi the
+ * device count, segment tables, seeds layout, batch pointers (device-resident inputs) and
+ * MSM plan; for poslo_distill a device-resident batch with the same pointers, n, n2,
+ * first_index and ds layout -- the sequence is captured into a CUDA graph, and later calls of
+ * that shape launch the graph instead of the individual kernels.  The contents of every
+ * input (messages, signatures, keys, seeds) are read afresh on each call; the uploads of
+ * host-side tables happen before the graph runs.  A workspace reallocation in between, or
+ * profiling (poslo_set_profiling), makes the call run its launches directly.  Enabled by
+ * default; poslo_set_graphs(ctx, 0) turns it off and frees the graphs.
+ * poslo_graph_stats reports how many graphs were captured and how many replays ran. */
+int poslo_set_graphs(poslo_ctx* ctx, int enabled);
+int poslo_graph_stats(poslo_ctx* ctx, uint64_t* captures, uint64_t* replays);
+
 #ifdef __cplusplus
 }
 #endif

@@ -24,6 +24,17 @@ struct KernelTimer {
 
 struct Server;   // continuous-batching service (serve.cu)
 
+// A captured launch sequence (CUDA graph) and the shape of the call it was captured from.
+// A call whose shape equals the previous call's is captured; later calls of that shape
+// replay it, as long as no workspace buffer has been reallocated since (alloc_gen).
+struct GraphSlot {
+  std::vector<uint64_t> sig;        // shape of the captured call
+  std::vector<uint64_t> last_sig;   // shape of the previous call
+  uint64_t gen = 0;                 // ctx->alloc_gen at capture
+  uint64_t launches = 0;            // kernels in the graph
+  cudaGraphExec_t exec = nullptr;
+};
+
 }  // namespace poslo_host
 
 struct poslo_ctx {
@@ -52,6 +63,12 @@ struct poslo_ctx {
   std::vector<cudaEvent_t> event_pool;
   std::map<int, int> msm_tuned;   // (log2 n) * 16 + scalar words -> best window c | range log2 << 8
   poslo_host::Server* server = nullptr;
+  bool graphs = true;             // replay repeated call shapes from CUDA graphs
+  bool capturing = false;         // a stream capture is open on s_main
+  uint64_t alloc_gen = 0;         // counts workspace (re)allocations
+  uint64_t graph_captures = 0, graph_replays = 0;
+  poslo_host::GraphSlot g_multi;  // poslo_aver_multi up to its combined check
+  poslo_host::GraphSlot g_distill;   // poslo_distill up to its weighted check
 };
 
 // Stops and frees the context's service, if one runs (serve.cu).

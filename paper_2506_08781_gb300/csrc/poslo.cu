@@ -44,11 +44,18 @@ int fail(poslo_ctx* c, int code, const char* fmt, ...) {
     if (e_ != cudaSuccess) return fail(ctx, POSLO_EDEVICE, "%s: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
 
+// Internal status: a workspace buffer would have to grow during a stream capture.
+constexpr int kCaptureGrow = -100;
+
 // Grow-only named workspace buffers.
 int ensure(poslo_ctx* ctx, const char* name, size_t bytes, void** out) {
   DevBuf& b = ctx->bufs[name];
   if (bytes == 0) bytes = 16;
   if (b.cap < bytes) {
+    // no allocation (and none of its synchronisation) inside a stream capture: the caller
+    // abandons the capture and runs the sequence directly
+    if (ctx->capturing) return kCaptureGrow;
+    ++ctx->alloc_gen;
     size_t want = std::max(bytes, b.cap + b.cap / 2);
     want = (want + 255) & ~size_t(255);
     if (ctx->mem_budget && ctx->mem_used - b.cap + want > ctx->mem_budget)
@@ -177,6 +184,69 @@ int check_status(poslo_ctx* ctx) {
 
 int reset_status(poslo_ctx* ctx) {
   CU(cudaMemsetAsync(ctx->status, 0, 4, ctx->s_main));
+  return POSLO_OK;
+}
+
+void graph_reset(poslo_host::GraphSlot& g) {
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  g.exec = nullptr;
+  g.sig.clear();
+}
+
+// Runs launch() -- a sequence of launches, device-side copies and event waits that starts
+// and ends on s_main, allocates nothing and does not synchronise -- or replays it.  The
+// first call of a shape runs it directly; a second call of the same shape in a row captures
+// it into a CUDA graph (thread-local capture on s_main; the side streams join through their
+// events) and launches the graph; later calls of that shape launch the graph again.  A
+// workspace reallocation since the capture, profiling (whose timers are host-side events)
+// or graphs switched off fall back to running it directly.
+template <class F>
+int run_replayable(poslo_ctx* ctx, poslo_host::GraphSlot& g, const std::vector<uint64_t>& sig, F&& launch) {
+  if (!ctx->graphs || ctx->profiling) {
+    graph_reset(g);
+    g.last_sig.clear();
+    return launch();
+  }
+  if (g.exec && g.sig == sig && g.gen == ctx->alloc_gen) {
+    CU(cudaGraphLaunch(g.exec, ctx->s_main));
+    ctx->launch_count += g.launches;
+    ++ctx->graph_replays;
+    return POSLO_OK;
+  }
+  if (g.last_sig != sig) {
+    g.last_sig = sig;
+    return launch();
+  }
+  graph_reset(g);
+  const uint64_t launches0 = ctx->launch_count;
+  CU(cudaStreamBeginCapture(ctx->s_main, cudaStreamCaptureModeThreadLocal));
+  ctx->capturing = true;
+  int rc = launch();
+  ctx->capturing = false;
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(ctx->s_main, &graph);
+  if (rc != POSLO_OK || ce != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();   // a failed capture leaves its error behind
+    g.last_sig.clear();
+    ctx->launch_count = launches0;
+    return launch();   // run it directly (a genuine error shows there again)
+  }
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) {
+    cudaGetLastError();
+    g.last_sig.clear();
+    ctx->launch_count = launches0;
+    return launch();
+  }
+  g.exec = exec;
+  g.sig = sig;
+  g.gen = ctx->alloc_gen;
+  g.launches = ctx->launch_count - launches0;
+  ++ctx->graph_captures;
+  CU(cudaGraphLaunch(g.exec, ctx->s_main));
   return POSLO_OK;
 }
 
@@ -717,6 +787,8 @@ void poslo_destroy(poslo_ctx* ctx) {
   if (ctx->s_main) cudaStreamSynchronize(ctx->s_main);
   if (ctx->s_table) cudaStreamSynchronize(ctx->s_table);
   if (ctx->s_points) cudaStreamSynchronize(ctx->s_points);
+  graph_reset(ctx->g_multi);
+  graph_reset(ctx->g_distill);
   for (auto& kv : ctx->bufs)
     if (kv.second.p) cudaFree(kv.second.p);
   for (auto& p : ctx->pending) {
@@ -750,6 +822,24 @@ void* poslo_stream(poslo_ctx* ctx) { return ctx ? (void*)ctx->s_main : nullptr; 
 int poslo_set_profiling(poslo_ctx* ctx, int enabled) {
   if (!ctx) return POSLO_EINVAL;
   ctx->profiling = enabled != 0;
+  return POSLO_OK;
+}
+
+int poslo_set_graphs(poslo_ctx* ctx, int enabled) {
+  if (!ctx) return POSLO_EINVAL;
+  ctx->graphs = enabled != 0;
+  if (!ctx->graphs) {
+    cudaStreamSynchronize(ctx->s_main);
+    graph_reset(ctx->g_multi);
+    graph_reset(ctx->g_distill);
+  }
+  return POSLO_OK;
+}
+
+int poslo_graph_stats(poslo_ctx* ctx, uint64_t* captures, uint64_t* replays) {
+  if (!ctx) return POSLO_EINVAL;
+  if (captures) *captures = ctx->graph_captures;
+  if (replays) *replays = ctx->graph_replays;
   return POSLO_OK;
 }
 
@@ -1096,40 +1186,72 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
   if ((rc = reset_status(ctx))) return rc;
   Staged sb;
   if ((rc = stage_batch(ctx, batch, sb))) return rc;
-  uint32_t* tableY;
-  if ((rc = run_ytable(ctx, batch->Y, &tableY))) return rc;
-  uint32_t *pts, *z;
-  uint8_t *badR, *badS, *d_e, *inv;
+  // uploads: the key's encoding and the disclosed seeds
+  uint32_t *d_Y, *tableY;
+  if ((rc = ensure_t(ctx, "Y", 32, &d_Y))) return rc;
+  if ((rc = ensure_t(ctx, "tableY", 4 * (size_t)kTableWords, &tableY))) return rc;
+  CU(cudaMemcpyAsync(d_Y, batch->Y, 32, cudaMemcpyHostToDevice, ctx->s_main));
+  std::vector<DsNode> ds_nodes;
+  if ((rc = parse_ds(ctx, batch->ds, batch->ds_nodes, ds_nodes))) return rc;
+  DsNode* d_ds;
+  if ((rc = ensure_t(ctx, "ds", ds_nodes.size() * sizeof(DsNode), &d_ds))) return rc;
+  CU(cudaMemcpyAsync(d_ds, ds_nodes.data(), ds_nodes.size() * sizeof(DsNode), cudaMemcpyHostToDevice, ctx->s_main));
+  uint64_t e_first = 0, ne = 0;
+  if (n) {
+    e_first = batch->first_index / batch->n2;
+    ne = (batch->first_index + n - 1) / batch->n2 - e_first + 1;
+  }
+  // workspace
+  uint32_t *pts, *z, *small, *seeds;
+  uint8_t *badR, *badS, *d_e, *inv, *d_ccd, *d_acc;
+  unsigned long long *hpart, *sp;
+  const int hblocks = grid_for(ctx, n, kHashThreads, 8);
+  const int sblocks = hblocks;
   if ((rc = ensure_t(ctx, "pts", 4 * kPtsWords * n1, &pts))) return rc;
   if ((rc = ensure_t(ctx, "badR", n1, &badR))) return rc;
   if ((rc = ensure_t(ctx, "badS", n1, &badS))) return rc;
   if ((rc = ensure_t(ctx, "z", 16 * n1, &z))) return rc;
   if ((rc = ensure_t(ctx, "e_all", 32 * n1, &d_e))) return rc;
   if ((rc = ensure_t(ctx, "invalid", n1, &inv))) return rc;
-  // A1-A5: hashing (main stream) overlapped with decoding (points stream)
-  uint32_t* small;   // unit R (32) | weighted R (32) | prep (33) | point bad count (1)
-  if ((rc = ensure_t(ctx, "distill_small", 4 * 100, &small))) return rc;
-  uint32_t *unitR = small, *Rw = small + 32, *prep = small + 64, *pbad = small + 97;
-  uint8_t* d_ccd;
+  if ((rc = ensure_t(ctx, "distill_small", 4 * 100, &small))) return rc;   // unit R | weighted R | prep | bad count
   if ((rc = ensure_t(ctx, "ccd", 64, &d_ccd))) return rc;
-  uint32_t *ppart, npb;
-  if ((rc = run_points(ctx, sb.R, n, pts, badR, &ppart, &npb, ctx->ev_staged))) return rc;
-  // speculative ccd^v for the all-valid case: R part on the points stream
-  if ((rc = run_unit_sum(ctx, ppart, npb, unitR, d_ccd + 32, pbad))) return rc;
-  unsigned long long* hpart;
-  uint32_t nhb;
-  MsmState ms;
-  {
-    // A1 seeds, then the weights z_t alone (they do not depend on the messages) so the MSM's
-    // counting sort starts at once; the message hashing (A2-A4, with the per-entry outputs
-    // Distill needs) runs on its own stream
-    uint64_t e_first = 0, ne = 0;
-    if (n) {
-      e_first = batch->first_index / batch->n2;
-      ne = (batch->first_index + n - 1) / batch->n2 - e_first + 1;
+  if ((rc = ensure_t(ctx, "seeds", std::max<uint64_t>(1, ne) * 16, &seeds))) return rc;
+  if ((rc = ensure_t(ctx, "hash_partial", (size_t)hblocks * kPartialWords * 8, &hpart))) return rc;
+  if ((rc = ensure_t(ctx, "accept", 16, &d_acc))) return rc;
+  if ((rc = ensure_t(ctx, "ccd_spart", (size_t)sblocks * 13 * 8, &sp))) return rc;
+  uint32_t *unitR = small, *Rw = small + 32, *prep = small + 64, *pbad = small + 97;
+  // ---- up to the weighted check of the whole batch; a device-resident batch of the previous
+  // call's shape replays it from a CUDA graph
+  const bool replayable = batch->on_device != 0;
+  auto stage1 = [&]() -> int {
+    int rc;
+    // window table of Y (table stream)
+    CU(cudaEventRecord(ctx->ev_main, ctx->s_main));
+    CU(cudaStreamWaitEvent(ctx->s_table, ctx->ev_main, 0));
+    {
+      cudaEvent_t tb, te;
+      timer_begin(ctx, "table", ctx->s_table, &tb, &te);
+      if ((rc = launch_tables(ctx, ctx->s_table, d_Y, nullptr, nullptr, 1, tableY, 0, nullptr))) return rc;
+      timer_end(ctx, "table", ctx->s_table, tb, te);
+      CU(cudaEventRecord(ctx->ev_table, ctx->s_table));
     }
-    uint32_t* seeds;
-    if ((rc = run_epoch_seeds(ctx, batch->ds, batch->ds_nodes, e_first, ne, &seeds))) return rc;
+    // decoding (points stream), from the moment the R_t have landed; then the speculative
+    // ccd^v of the all-valid case (its R part)
+    uint32_t *ppart, npb;
+    if ((rc = run_points(ctx, sb.R, n, pts, badR, &ppart, &npb, replayable ? nullptr : ctx->ev_staged))) return rc;
+    if ((rc = run_unit_sum(ctx, ppart, npb, unitR, d_ccd + 32, pbad))) return rc;
+    // epoch seeds, then the weights z_t alone (they do not depend on the messages) so the
+    // MSM's counting sort starts at once; the message hashing (with the per-entry outputs
+    // Distill needs) runs on its own stream
+    if (ne) {
+      cudaEvent_t b, e;
+      timer_begin(ctx, "seeds", ctx->s_main, &b, &e);
+      launch_epoch_seeds((int)ctx->inst, (unsigned)((ne + 127) / 128), 128, ctx->s_main, d_ds, (int)ds_nodes.size(),
+                         e_first, ne, seeds, ctx->status);
+      ++ctx->launch_count;
+      CU(cudaGetLastError());
+      timer_end(ctx, "seeds", ctx->s_main, b, e);
+    }
     ZPre zp;
     make_zpre(ctx->vseed, zp.w);
     if (n) {
@@ -1141,8 +1263,6 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
     // (measured: hashing beside the decoding, 4.78 ms per 2^20-entry step, beats hashing on the
     // main stream before the sort, 4.88 ms, and beside the bucket accumulation, 4.95 ms)
     cudaStream_t hs = ctx->s_hash;
-    const int blocks = grid_for(ctx, n, kHashThreads, 8);
-    if ((rc = ensure_t(ctx, "hash_partial", (size_t)blocks * kPartialWords * 8, &hpart))) return rc;
     HashArgs a{};
     a.msgs = sb.msgs;
     a.offs = sb.offs;
@@ -1161,26 +1281,34 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
     a.sbad_out = badS;
     a.partial = hpart;
     a.status = ctx->status;
+    MsmState ms;
     if ((rc = run_msm_sort(ctx, ctx->s_main, z, 4, nullptr, n, ms))) return rc;
-    cudaEvent_t tb, te;
-    timer_begin(ctx, "hash", hs, &tb, &te);
-    launch_hash((int)ctx->inst, (unsigned)blocks, hs, a);
-    ++ctx->launch_count;
-    CU(cudaGetLastError());
-    timer_end(ctx, "hash", hs, tb, te);
-    nhb = (uint32_t)blocks;
+    {
+      cudaEvent_t tb, te;
+      timer_begin(ctx, "hash", hs, &tb, &te);
+      launch_hash((int)ctx->inst, (unsigned)hblocks, hs, a);
+      ++ctx->launch_count;
+      CU(cudaGetLastError());
+      timer_end(ctx, "hash", hs, tb, te);
+    }
     // [e]Y + [s]G and the s part of ccd^v on the table stream, while the MSM runs
-    if ((rc = run_prep(ctx, hpart, nhb, nullptr, tableY, prep, sb.s, n, d_ccd, hs))) return rc;
+    if ((rc = run_prep(ctx, hpart, (uint32_t)hblocks, nullptr, tableY, prep, sb.s, n, d_ccd, hs))) return rc;
+    CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_points, 0));
+    // weighted MSM and the weighted check of the whole batch
+    if ((rc = run_msm_finish(ctx, ctx->s_main, pts, badR, ms, Rw))) return rc;
+    if ((rc = run_check(ctx, prep, Rw, pbad, d_acc))) return rc;
+    return POSLO_OK;
+  };
+  if (replayable) {
+    const MsmPlan plan = msm_plan(ctx, n, 4);
+    const std::vector<uint64_t> sig = {n, batch->n2, batch->first_index, reinterpret_cast<uint64_t>(sb.msgs),
+                                       reinterpret_cast<uint64_t>(sb.offs), reinterpret_cast<uint64_t>(sb.s),
+                                       reinterpret_cast<uint64_t>(sb.R), sb.base_off, ds_nodes.size(),
+                                       (uint64_t)plan.c, (uint64_t)plan.seg_log2, ctx->inst};
+    if ((rc = run_replayable(ctx, ctx->g_distill, sig, stage1))) return rc;
+  } else if ((rc = stage1())) {
+    return rc;
   }
-  CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_points, 0));
-  // A5-A6: weighted MSM and the weighted check of the whole batch
-  uint8_t* d_acc;
-  if ((rc = ensure_t(ctx, "accept", 16, &d_acc))) return rc;
-  if ((rc = run_msm_finish(ctx, ctx->s_main, pts, badR, ms, Rw))) return rc;
-  if ((rc = run_check(ctx, prep, Rw, pbad, d_acc))) return rc;
-  const int sblocks = grid_for(ctx, n, kHashThreads, 8);
-  unsigned long long* sp;
-  if ((rc = ensure_t(ctx, "ccd_spart", (size_t)sblocks * 13 * 8, &sp))) return rc;
   uint8_t h_acc = 0;
   CU(cudaMemcpyAsync(&h_acc, d_acc, 1, cudaMemcpyDeviceToHost, ctx->s_main));
   if ((rc = check_status(ctx))) return rc;   // synchronises: h_acc is ready
@@ -1817,102 +1945,43 @@ int poslo_host::aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, const ui
   CU(cudaMemcpyAsync(d_dsoff, mb->ds_off, 4 * (size_t)(nd + 1), cudaMemcpyHostToDevice, ctx->s_main));
   CU(cudaMemcpyAsync(d_nodes, nodes.data(), sizeof(DsNode) * nodes.size(), cudaMemcpyHostToDevice, ctx->s_main));
   CU(cudaMemcpyAsync(d_Y, mb->Y, 32 * (size_t)nd, cudaMemcpyHostToDevice, ctx->s_main));
-  // ---- (table stream) window tables of every device key, decoded from its encoding, unless
-  // the caller holds them resident; tabs[d] points at device d's table
+  // ---- window tables of every device key (built on the table stream from the encodings,
+  // unless the caller holds them resident); tabs[d] points at device d's table
   uint8_t* badY;
   const uint32_t** d_tabs;
+  uint32_t* tablesY = nullptr;
   if ((rc = ensure_t(ctx, "m_badY", nd, &badY))) return rc;
   if ((rc = ensure_t(ctx, "m_tabs", 8 * (size_t)nd, &d_tabs))) return rc;
   std::vector<const uint32_t*> tabs(nd);
   if (key_tables) {
     for (uint32_t d = 0; d < nd; ++d) tabs[d] = key_tables[d];
-    CU(cudaMemsetAsync(badY, 0, nd, ctx->s_main));
-    CU(cudaEventRecord(ctx->ev_table, ctx->s_main));
   } else {
-    uint32_t* tablesY;
     if ((rc = ensure_t(ctx, "m_tablesY", 4 * (size_t)kTableWords * nd, &tablesY))) return rc;
     for (uint32_t d = 0; d < nd; ++d) tabs[d] = tablesY + (size_t)d * kTableWords;
-    CU(cudaEventRecord(ctx->ev_main, ctx->s_main));
-    CU(cudaStreamWaitEvent(ctx->s_table, ctx->ev_main, 0));
-    cudaEvent_t tb, te;
-    timer_begin(ctx, "table", ctx->s_table, &tb, &te);
-    if ((rc = launch_tables(ctx, ctx->s_table, reinterpret_cast<const uint32_t*>(d_Y), nullptr, nullptr, nd, tablesY,
-                            0, badY)))
-      return rc;
-    timer_end(ctx, "table", ctx->s_table, tb, te);
-    CU(cudaEventRecord(ctx->ev_table, ctx->s_table));
   }
   CU(cudaMemcpyAsync(d_tabs, tabs.data(), 8 * (size_t)nd, cudaMemcpyHostToDevice, ctx->s_main));
   const uint64_t* seg_start = d_meta;
   const uint64_t* seg_first = d_meta + nd + 1;
   const uint64_t* seg_seed_off = d_meta + 2 * nd + 1;
   const uint64_t* seg_e0 = d_meta + 3 * nd + 2;
-  // ---- A1: epoch seeds of every device
-  uint32_t* seeds;
-  if ((rc = ensure_t(ctx, "seeds", 16 * std::max<uint64_t>(seed_off[nd], 1), &seeds))) return rc;
-  if (seed_off[nd]) {
-    launch_epoch_seeds_multi((int)ctx->inst, (unsigned)((seed_off[nd] + 127) / 128), 128, ctx->s_main, d_nodes,
-                             d_dsoff, seg_seed_off, seg_e0, nd, seeds, ctx->status);
-    ++ctx->launch_count;
-  }
-  // ---- A5 (side stream): decode every R_t
+  // ---- workspace of the first stage
   const uint64_t N1 = std::max<uint64_t>(N, 1);
-  uint32_t *pts, *ppart, npb;
-  uint8_t *badR, *badS, *d_e;
+  uint32_t *seeds, *pts, *z, *P1, *segbuf, *tmpart;
+  uint8_t *badR, *badS, *d_e, *d_acc, *dev_flag, *eskip;
+  const int tmb = grid_for(ctx, (uint64_t)nd * kTableWindows, kPointThreads, 4);
+  if ((rc = ensure_t(ctx, "seeds", 16 * std::max<uint64_t>(seed_off[nd], 1), &seeds))) return rc;
   if ((rc = ensure_t(ctx, "pts", 4 * kPtsWords * N1, &pts))) return rc;
   if ((rc = ensure_t(ctx, "badR", N1, &badR))) return rc;
   if ((rc = ensure_t(ctx, "badS", N1, &badS))) return rc;
   if ((rc = ensure_t(ctx, "e_all", 32 * N1, &d_e))) return rc;
-  uint32_t* z;
   if ((rc = ensure_t(ctx, "z", 16 * N1, &z))) return rc;
-  if ((rc = run_points(ctx, sb.R, N, pts, badR, &ppart, &npb))) return rc;
-  // ---- A2-A4: segmented hashing with per-entry e_t, z_t
-  {
-    const int blocks = grid_for(ctx, N, kHashThreads, 8);
-    unsigned long long* hpart;
-    if ((rc = ensure_t(ctx, "hash_partial", (size_t)blocks * kPartialWords * 8, &hpart))) return rc;
-    HashArgs a{};
-    a.msgs = sb.msgs;
-    a.offs = sb.offs;
-    a.base_off = sb.base_off;
-    a.n = N;
-    a.n2 = 1;
-    a.n2_log2 = 0xffffffffu;
-    a.seeds = seeds;
-    a.e_out = d_e;
-    a.s = sb.s;
-    a.weighted = 1;
-    make_zpre(ctx->vseed, a.zpre);
-    a.z_out = z;
-    a.sbad_out = badS;
-    a.partial = hpart;
-    a.status = ctx->status;
-    a.n_seg = nd;
-    a.seg_start = seg_start;
-    a.seg_first = seg_first;
-    a.seg_seed_off = seg_seed_off;
-    a.seg_e0 = seg_e0;
-    a.seg_n2 = d_n2;
-    cudaEvent_t tb, te;
-    timer_begin(ctx, "hash", ctx->s_main, &tb, &te);
-    launch_hash((int)ctx->inst, (unsigned)blocks, ctx->s_main, a);
-    ++ctx->launch_count;
-    CU(cudaGetLastError());
-    timer_end(ctx, "hash", ctx->s_main, tb, te);
-  }
-  MsmState ms;
-  if ((rc = run_msm_sort(ctx, ctx->s_main, z, 4, nullptr, N, ms))) return rc;
-  CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_points, 0));
-  // ---- A5-A6: sum_t z_t R_t, per-device sums, sum_d E_d Y_d, one combined check
-  uint32_t *P1, *P2, *segbuf;
-  uint8_t *d_acc, *dev_flag, *eskip;
   if ((rc = ensure_t(ctx, "m_P", 384, &P1))) return rc;
-  P2 = P1 + 32;
-  uint32_t* P3 = P1 + 64;
   if ((rc = ensure_t(ctx, "accept", 16, &d_acc))) return rc;
   if ((rc = ensure_t(ctx, "m_devflag", nd, &dev_flag))) return rc;
   if ((rc = ensure_t(ctx, "m_eskip", N1, &eskip))) return rc;
   if ((rc = ensure_t(ctx, "m_seg", (size_t)nd * (32 + 32 + 1) * 4, &segbuf))) return rc;
+  if ((rc = ensure_t(ctx, "m_tmpart", (size_t)tmb * kPointPartialWords * 4, &tmpart))) return rc;
+  uint32_t *P2 = P1 + 32, *P3 = P1 + 64;
   SegSums ss;
   ss.Ew = segbuf;
   ss.Sw = ss.Ew + 8 * (size_t)nd;
@@ -1920,20 +1989,94 @@ int poslo_host::aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, const ui
   ss.Su = ss.Eu + 8 * (size_t)nd;
   ss.Ru = ss.Su + 8 * (size_t)nd;
   ss.bad = ss.Ru + 32 * (size_t)nd;
-  if ((rc = run_msm_finish(ctx, ctx->s_main, pts, badR, ms, P1))) return rc;
-  k_segment_sums<<<nd, 256, 0, ctx->s_main>>>(d_e, sb.s, z, pts, badR, badS, seg_start, ss);
-  ++ctx->launch_count;
-  // sum_d E_d Y_d from the key tables
-  CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_table, 0));
-  const int tmb = grid_for(ctx, (uint64_t)nd * kTableWindows, kPointThreads, 4);
-  uint32_t* tmpart;
-  if ((rc = ensure_t(ctx, "m_tmpart", (size_t)tmb * kPointPartialWords * 4, &tmpart))) return rc;
-  k_table_msm<<<tmb, kPointThreads, 0, ctx->s_main>>>(d_tabs, ss.Ew, nullptr, nd, tmpart);
-  k_sum_encode<<<1, kFinalThreads, 0, ctx->s_main>>>(tmpart, tmb, P2, nullptr, nullptr);
-  ctx->launch_count += 2;
-  k_multi_check<<<1, kFinalThreads, 0, ctx->s_main>>>(P1, nullptr, P2, ss.Sw, nullptr, nd, ctx->tableG, d_acc);
-  ++ctx->launch_count;
-  CU(cudaGetLastError());
+  // ---- first stage, up to the combined check: one launch per step over the device segment
+  // table, replayed from a CUDA graph when the call has the shape of the previous one
+  const MsmPlan plan = msm_plan(ctx, N, 4);
+  std::vector<uint64_t> sig = {nd, N, mb->on_device, key_tables ? 1u : 0u, sb.base_off,
+                               reinterpret_cast<uint64_t>(sb.msgs), reinterpret_cast<uint64_t>(sb.offs),
+                               reinterpret_cast<uint64_t>(sb.s), reinterpret_cast<uint64_t>(sb.R),
+                               nodes.size(), (uint64_t)plan.c, (uint64_t)plan.seg_log2, ctx->inst};
+  sig.insert(sig.end(), mb->dev_start, mb->dev_start + nd + 1);
+  sig.insert(sig.end(), mb->first_index, mb->first_index + nd);
+  sig.insert(sig.end(), mb->n2, mb->n2 + nd);
+  sig.insert(sig.end(), mb->ds_off, mb->ds_off + nd + 1);
+  auto stage1 = [&]() -> int {
+    int rc;
+    if (key_tables) {
+      CU(cudaMemsetAsync(badY, 0, nd, ctx->s_main));
+      CU(cudaEventRecord(ctx->ev_table, ctx->s_main));
+    } else {
+      CU(cudaEventRecord(ctx->ev_main, ctx->s_main));
+      CU(cudaStreamWaitEvent(ctx->s_table, ctx->ev_main, 0));
+      cudaEvent_t tb, te;
+      timer_begin(ctx, "table", ctx->s_table, &tb, &te);
+      if ((rc = launch_tables(ctx, ctx->s_table, reinterpret_cast<const uint32_t*>(d_Y), nullptr, nullptr, nd,
+                              tablesY, 0, badY)))
+        return rc;
+      timer_end(ctx, "table", ctx->s_table, tb, te);
+      CU(cudaEventRecord(ctx->ev_table, ctx->s_table));
+    }
+    // epoch seeds of every device
+    if (seed_off[nd]) {
+      launch_epoch_seeds_multi((int)ctx->inst, (unsigned)((seed_off[nd] + 127) / 128), 128, ctx->s_main, d_nodes,
+                               d_dsoff, seg_seed_off, seg_e0, nd, seeds, ctx->status);
+      ++ctx->launch_count;
+    }
+    // (side stream) decode every R_t
+    uint32_t *ppart, npb;
+    if ((rc = run_points(ctx, sb.R, N, pts, badR, &ppart, &npb))) return rc;
+    // segmented hashing with per-entry e_t, z_t
+    {
+      const int blocks = grid_for(ctx, N, kHashThreads, 8);
+      unsigned long long* hpart;
+      if ((rc = ensure_t(ctx, "hash_partial", (size_t)blocks * kPartialWords * 8, &hpart))) return rc;
+      HashArgs a{};
+      a.msgs = sb.msgs;
+      a.offs = sb.offs;
+      a.base_off = sb.base_off;
+      a.n = N;
+      a.n2 = 1;
+      a.n2_log2 = 0xffffffffu;
+      a.seeds = seeds;
+      a.e_out = d_e;
+      a.s = sb.s;
+      a.weighted = 1;
+      make_zpre(ctx->vseed, a.zpre);
+      a.z_out = z;
+      a.sbad_out = badS;
+      a.partial = hpart;
+      a.status = ctx->status;
+      a.n_seg = nd;
+      a.seg_start = seg_start;
+      a.seg_first = seg_first;
+      a.seg_seed_off = seg_seed_off;
+      a.seg_e0 = seg_e0;
+      a.seg_n2 = d_n2;
+      cudaEvent_t tb, te;
+      timer_begin(ctx, "hash", ctx->s_main, &tb, &te);
+      launch_hash((int)ctx->inst, (unsigned)blocks, ctx->s_main, a);
+      ++ctx->launch_count;
+      CU(cudaGetLastError());
+      timer_end(ctx, "hash", ctx->s_main, tb, te);
+    }
+    MsmState ms;
+    if ((rc = run_msm_sort(ctx, ctx->s_main, z, 4, nullptr, N, ms))) return rc;
+    CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_points, 0));
+    // sum_t z_t R_t, per-device sums, sum_d E_d Y_d, one combined check
+    if ((rc = run_msm_finish(ctx, ctx->s_main, pts, badR, ms, P1))) return rc;
+    k_segment_sums<<<nd, 256, 0, ctx->s_main>>>(d_e, sb.s, z, pts, badR, badS, seg_start, ss);
+    ++ctx->launch_count;
+    // sum_d E_d Y_d from the key tables
+    CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_table, 0));
+    k_table_msm<<<tmb, kPointThreads, 0, ctx->s_main>>>(d_tabs, ss.Ew, nullptr, nd, tmpart);
+    k_sum_encode<<<1, kFinalThreads, 0, ctx->s_main>>>(tmpart, tmb, P2, nullptr, nullptr);
+    ctx->launch_count += 2;
+    k_multi_check<<<1, kFinalThreads, 0, ctx->s_main>>>(P1, nullptr, P2, ss.Sw, nullptr, nd, ctx->tableG, d_acc);
+    ++ctx->launch_count;
+    CU(cudaGetLastError());
+    return POSLO_OK;
+  };
+  if ((rc = run_replayable(ctx, ctx->g_multi, sig, stage1))) return rc;
   uint8_t all_ok = 0;
   std::vector<uint32_t> bad(nd);
   std::vector<uint8_t> hbadY(nd);

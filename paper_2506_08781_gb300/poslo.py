@@ -29,7 +29,7 @@ EXPORTS = [
     "poslo_keygen_c", "poslo_keygen_f", "poslo_sign_c", "poslo_sign_f", "poslo_disclose",
     "poslo_aver", "poslo_distill", "poslo_epoch_seeds", "poslo_hash_entries", "poslo_msm", "poslo_msm_autotune",
     "poslo_msm_get_plan", "poslo_msm_set_plan",
-    "poslo_set_profiling", "poslo_kernel_time", "poslo_reset_kernel_times",
+    "poslo_set_profiling", "poslo_kernel_time", "poslo_reset_kernel_times", "poslo_set_graphs", "poslo_graph_stats",
     "poslo_hash_entries_noalloc", "poslo_aver_multi", "poslo_distill_c", "poslo_sebver_c", "poslo_distill_stream",
     "poslo_serve_start", "poslo_serve_stop", "poslo_register_key", "poslo_submit", "poslo_poll",
     "poslo_serve_stats",
@@ -108,6 +108,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "poslo_msm_get_plan": ([vp, u64, u32, C.POINTER(u32), C.POINTER(u32)], C.c_int),
         "poslo_msm_set_plan": ([vp, u64, u32, u32, u32], C.c_int),
         "poslo_set_profiling": ([vp, C.c_int], C.c_int),
+        "poslo_set_graphs": ([vp, C.c_int], C.c_int),
+        "poslo_graph_stats": ([vp, C.POINTER(u64), C.POINTER(u64)], C.c_int),
         "poslo_kernel_time": ([vp, C.c_char_p, C.POINTER(C.c_double), C.POINTER(u64)], C.c_int),
         "poslo_reset_kernel_times": ([vp], None),
         "poslo_hash_entries_noalloc": ([C.POINTER(Batch), u8p, vp], C.c_int),
@@ -485,6 +487,16 @@ class Context:
     # ------------------------------------------------------------------ profiling
     def set_profiling(self, on: bool):
         self._check(self.lib.poslo_set_profiling(self.h, 1 if on else 0))
+
+    def set_graphs(self, on: bool):
+        """Replay repeated call shapes of aver_multi / distill from CUDA graphs (default on)."""
+        self._check(self.lib.poslo_set_graphs(self.h, 1 if on else 0))
+
+    def graph_stats(self):
+        """(graphs captured, replays run) on this context."""
+        c, r = C.c_uint64(0), C.c_uint64(0)
+        self._check(self.lib.poslo_graph_stats(self.h, C.byref(c), C.byref(r)))
+        return int(c.value), int(r.value)
 
     def kernel_time(self, name: str):
         ms = C.c_double()

@@ -119,3 +119,86 @@ def test_multi_malformed_entries_and_capacity(ctx):
     with pytest.raises(poslo.PosloError) as e:
         ctx.aver_multi(*args, cap=len(want_pairs) - 1)
     assert e.value.code == -5
+
+
+def _flip_entry(data, offs, t):
+    out = data.copy()
+    out[int(offs[t])] ^= 0x5a
+    return out
+
+
+@pytest.mark.parametrize("on_device", [False, True])
+def test_multi_graph_replay_reads_each_calls_inputs(on_device):
+    """Calls of one shape are captured into a CUDA graph and replayed; every call still reads
+    its own message bytes (a different entry is tampered on each call)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    devs, parts = _devices(7, 6, 2, 20, 0)
+    cat, s, R = _concat(parts)
+    starts = np.concatenate([[0], np.cumsum([p[1].n for p in parts])])
+    args = ([p[0] for p in parts], [p[1].n for p in parts], [p[2] for p in parts], [p[3] for p in parts],
+            [p[6] for p in parts])
+    with poslo.Context(device=0, verifier_seed=synth.verifier_seed(7)) as cx:
+        if on_device:
+            d_msgs = torch.from_numpy(cat.data.copy()).cuda()
+            d_offs = torch.from_numpy(cat.offs.view(np.int64).copy()).cuda()
+            d_s = torch.from_numpy(np.frombuffer(s, np.uint8).copy()).cuda()
+            d_R = torch.from_numpy(np.frombuffer(R, np.uint8).copy()).cuda()
+        # trial 1's data first: the localisation of a failing call grows its own workspace
+        # once, which would invalidate a graph captured before it
+        for trial in [1] + list(range(5)):
+            data = cat.data
+            want_devs = [tuple(d) for d in devs]
+            if trial:
+                dev = trial % len(parts)
+                lens = np.diff(cat.offs[starts[dev]:starts[dev + 1] + 1])
+                t = int(starts[dev] + int(np.argmax(lens > 0)))
+                data = _flip_entry(cat.data, cat.offs, t)
+                d = devs[dev]
+                ms = list(d[1])
+                ms[t - starts[dev]] = bytes(data[int(cat.offs[t]):int(cat.offs[t + 1])])
+                want_devs[dev] = (d[0], ms, d[2], d[3], d[4], d[5], d[6])
+            if on_device:
+                d_msgs.copy_(torch.from_numpy(data))
+                torch.cuda.synchronize()
+                acc, pairs = cx.aver_multi(*args, d_msgs, d_offs, d_s, d_R)
+            else:
+                acc, pairs = cx.aver_multi(*args, data, cat.offs, s, R)
+            want_acc, want_pairs = O.verify_multi(want_devs)
+            assert list(acc) == want_acc, trial
+            assert [tuple(int(x) for x in p) for p in pairs] == want_pairs, trial
+        captures, replays = cx.graph_stats()
+        assert captures == 1 and replays == 4
+        # a larger call in between regrows the workspace: the next call of the first shape
+        # must not replay the stale graph
+        devs2, parts2 = _devices(8, 9, 30, 60, 1)
+        cat2, s2, R2 = _concat(parts2)
+        acc2, pairs2 = cx.aver_multi([p[0] for p in parts2], [p[1].n for p in parts2], [p[2] for p in parts2],
+                                     [p[3] for p in parts2], [p[6] for p in parts2], cat2.data, cat2.offs, s2, R2)
+        w2 = O.verify_multi(devs2)
+        assert list(acc2) == w2[0]
+        if on_device:
+            d_msgs.copy_(torch.from_numpy(cat.data))
+            torch.cuda.synchronize()
+            acc, pairs = cx.aver_multi(*args, d_msgs, d_offs, d_s, d_R)
+        else:
+            acc, pairs = cx.aver_multi(*args, cat.data, cat.offs, s, R)
+        assert list(acc) == [True] * len(parts) and len(pairs) == 0
+        assert cx.graph_stats()[1] == 4
+
+
+def test_multi_graphs_off_same_results():
+    import __graft_entry__
+    __graft_entry__.build()
+    devs, parts = _devices(9, 5, 2, 16, 2)
+    cat, s, R = _concat(parts)
+    args = ([p[0] for p in parts], [p[1].n for p in parts], [p[2] for p in parts], [p[3] for p in parts],
+            [p[6] for p in parts], cat.data, cat.offs, s, R)
+    want_acc, want_pairs = O.verify_multi(devs)
+    with poslo.Context(device=0) as cx:
+        cx.set_graphs(False)
+        for _ in range(3):
+            acc, pairs = cx.aver_multi(*args)
+            assert list(acc) == want_acc and [tuple(int(x) for x in p) for p in pairs] == want_pairs
+        assert cx.graph_stats() == (0, 0)

@@ -504,3 +504,35 @@ def test_decreasing_offsets_are_einval(ctx):
     # the context stays usable
     good = ctx.make_batch(poslo.VARIANT_F, n2, Y, msgs.data, msgs.offs, b"".join(s), b"".join(R), ds)
     assert ctx.aver(good) is True
+
+
+def test_distill_graph_replay_device_batch():
+    """Distill calls on one device-resident batch are captured into a CUDA graph and replayed;
+    every call still reads its own bytes (a different entry is tampered on each call)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    D, n2, n = 4, 16, 120
+    km, sk, Y, msgs, subsets, s, R, _ = _f_data(91, n, D, n2, 1, 80)
+    ds_l = O.ds_root(km.root, D)
+    with poslo.Context(device=0) as cx:
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).copy()).cuda()
+        d_msgs = dev(msgs.data)
+        b = cx.make_batch(poslo.VARIANT_F, n2, Y, d_msgs, dev(msgs.offs.astype(np.int64)),
+                          dev(np.frombuffer(b"".join(s), np.uint8)), dev(np.frombuffer(b"".join(R), np.uint8)),
+                          O.ds_serialize(ds_l))
+        # trial 1's data first: the localisation of a failing call grows its own workspace
+        # once, which would invalidate a graph captured before it
+        for trial in [1] + list(range(5)):
+            data = msgs.data.copy()
+            tampered = []
+            if trial:
+                t = (17 * trial) % n
+                data[int(msgs.offs[t])] ^= 0x33
+                tampered = [t]
+            d_msgs.copy_(torch.from_numpy(data))
+            torch.cuda.synchronize()
+            idx, cs, cR = cx.distill(b)
+            wi, ws, wR = O.distill_f(Y, synth.Messages(data, msgs.offs).as_list(), 0, n2, s, R, ds_l)
+            assert list(idx) == wi == tampered and cs == ws and cR == wR, trial
+        assert cx.graph_stats() == (1, 4)
