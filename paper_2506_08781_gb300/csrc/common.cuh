@@ -618,6 +618,16 @@ __global__ void __launch_bounds__(kCombineBigThreads) k_msm_combine_big(const ui
 __global__ void __launch_bounds__(128) k_msm_chunk(const uint32_t* buckets, MsmPlan pl, uint32_t* L, uint32_t* T);
 __global__ void __launch_bounds__(512) k_msm_groups(const uint32_t* L, const uint32_t* T, MsmPlan pl, uint32_t* groups);
 __global__ void __launch_bounds__(32) k_msm_final(const uint32_t* groups, MsmPlan pl, uint32_t* out);
+__global__ void __launch_bounds__(32) k_msm_window_check(const uint32_t* groups, MsmPlan pl, const uint32_t* Pw,
+                                                         const uint32_t* bad, const uint32_t* point_bad,
+                                                         const uint32_t* status, uint8_t* accept);
+constexpr int kWindowThreads = 128;
+__global__ void __launch_bounds__(kWindowThreads) k_window_sums(const uint8_t* e, const uint8_t* s, const uint32_t* z,
+                                                                uint64_t n, MsmPlan pl, unsigned long long* partial);
+__global__ void __launch_bounds__(kWindowThreads) k_window_prep(const unsigned long long* partial, uint32_t nblocks,
+                                                                const unsigned long long* hash_partial, uint32_t nhash,
+                                                                const uint32_t* tableY, const uint32_t* tableG,
+                                                                uint32_t* Pw, uint32_t* bad);
 __global__ void __launch_bounds__(128) k_tree_leaves(const TreeArgs a);
 __global__ void __launch_bounds__(128) k_tree_level(const TreeArgs a, uint64_t in_off, uint64_t out_off,
                                                     uint64_t count);

@@ -297,6 +297,33 @@ __global__ void __launch_bounds__(32) k_msm_final(const uint32_t* groups, MsmPla
   if (lane == 0) ge_store(out, acc);
 }
 
+// Per-window weighted check, group side: quad w forms the window sum W_w = G_0 + 16 sum_k 2^k
+// G_{1+k} of window w from its group sums (as k_msm_final does) and tests
+// [8](W_w - P_w) = O against P_w = [E_w] Y + [S_w] G (k_window_prep); windows are processed in
+// rounds of eight quads.  accept = every window holds, no malformed s (*bad), no undecodable
+// R (*point_bad) and a decodable key.  One warp.
+__global__ void __launch_bounds__(32) k_msm_window_check(const uint32_t* groups, MsmPlan pl, const uint32_t* Pw,
+                                                         const uint32_t* bad, const uint32_t* point_bad,
+                                                         const uint32_t* status, uint8_t* accept) {
+  const int lane = threadIdx.x & 31, quad = lane >> 2;
+  const int ng = 1 + pl.jbits;
+  bool ok = true;
+  for (int r0 = 0; r0 < pl.windows; r0 += 8) {
+    const int w = r0 + quad;
+    const int wc = w < pl.windows ? w : pl.windows - 1;
+    const uint32_t* G = groups + 32 * (size_t)wc * ng;
+    ge acc = ge_load(G + 32 * pl.jbits);
+    for (int k = pl.jbits - 2; k >= 0; --k) acc = ge_add_quad(ge_dbl_quad(acc), ge_load(G + 32 * (1 + k)));
+    for (int i = 0; i < 4; ++i) acc = ge_dbl_quad(acc);   // times kMsmChunk = 16
+    acc = ge_add_quad(acc, ge_load(G));
+    ge diff = ge_add_quad(acc, ge_neg(ge_load(Pw + 32 * (size_t)wc)));
+    for (int i = 0; i < 3; ++i) diff = ge_dbl_quad(diff);   // cofactor 8
+    if (w < pl.windows) ok = ok && ge_is_identity(diff);
+  }
+  const bool all = __all_sync(0xffffffffu, ok);
+  if (lane == 0) *accept = (all && *bad == 0 && !(point_bad && *point_bad) && (*status & kErrKey) == 0) ? 1 : 0;
+}
+
 // Synthetic input for timing window widths: every point is G (the cost of a complete
 // addition does not depend on its operands) and the scalars are SplitMix64 output with the
 // top bit of a 4-word weight, or the top 3 bits of an 8-word scalar, cleared.

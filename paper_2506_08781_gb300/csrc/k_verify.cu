@@ -512,6 +512,120 @@ __global__ void __launch_bounds__(128) k_final_prep(const PrepArgs a) {
   if (tid == 0) a.prep[32] = bad_flag;
 }
 
+// Per-window weighted check, scalar side.  With z_t = sum_w d_{t,w} 2^(c w) in the MSM's
+// signed window digits, window w of the batch equation is
+//   sum_t d_{t,w} R_t = [E_w] Y + [S_w] G,  E_w = sum_t d_{t,w} e_t,  S_w = sum_t d_{t,w} s_t (mod q).
+// k_window_sums: grid (x, windows), blockIdx.y = w; each thread recodes the weights of its
+// entries up to window w and adds |d| x, with x = e_t (s_t) for a positive digit and q - x for
+// a negative one, into exact 416-bit accumulators; per block 13 limb sums of E_w and 13 of
+// S_w (26 u64 at partial[(w * gridDim.x + blockIdx.x) * 26]).
+__global__ void __launch_bounds__(kWindowThreads) k_window_sums(const uint8_t* e, const uint8_t* s, const uint32_t* z,
+                                                                uint64_t n, MsmPlan pl,
+                                                                unsigned long long* partial) {
+  const int w = blockIdx.y;
+  acc13 ae, as;
+  acc_zero(ae);
+  acc_zero(as);
+  uint32_t q[8];
+  sc_qlimbs(q);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
+    uint32_t zw[8];
+    z_load(z, 4, t, zw);
+    uint32_t carry = 0, d = 0;
+    bool neg = false;
+    for (int k = 0; k <= w; ++k) d = z_sdigit(zw, 4, k, pl.c, carry, neg);
+    if (d == 0) continue;
+    const uint4* ep = reinterpret_cast<const uint4*>(e + 32 * t);
+    const uint4* sp = reinterpret_cast<const uint4*>(s + 32 * t);
+    const uint4 e0 = ep[0], e1 = ep[1], s0 = sp[0], s1 = sp[1];
+    uint32_t x[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
+    uint32_t y[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+    if (neg) {
+      int64_t bx = 0, by = 0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        bx += (int64_t)q[k] - x[k];
+        by += (int64_t)q[k] - y[k];
+        x[k] = (uint32_t)bx;
+        y[k] = (uint32_t)by;
+        bx >>= 32;
+        by >>= 32;
+      }
+    }
+    uint32_t r[9];
+    uint64_t c0 = 0, c1 = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      c0 += (uint64_t)d * x[k];
+      r[k] = (uint32_t)c0;
+      c0 >>= 32;
+    }
+    r[8] = (uint32_t)c0;
+    acc_add<9>(ae, r);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      c1 += (uint64_t)d * y[k];
+      r[k] = (uint32_t)c1;
+      c1 >>= 32;
+    }
+    r[8] = (uint32_t)c1;
+    acc_add<9>(as, r);
+  }
+  __shared__ unsigned long long red[kWindowThreads / 32][26];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 26; ++k) {
+    unsigned long long v = k < 13 ? ae.v[k] : as.v[k - 13];
+    warp_sum_u64(v);
+    if (lane == 0) red[warp][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 26) {
+    unsigned long long v = 0;
+    for (int i = 0; i < kWindowThreads / 32; ++i) v += red[i][threadIdx.x];
+    partial[((size_t)w * gridDim.x + blockIdx.x) * 26 + threadIdx.x] = v;
+  }
+}
+
+// One block per window: E_w and S_w from the partials of k_window_sums, then
+// P_w = [E_w] Y + [S_w] G from the two window tables (128 terms, shared-memory tree) into
+// Pw[w] (32 words).  Block 0 also writes the malformed-s flag of the hashing partials to *bad.
+__global__ void __launch_bounds__(kWindowThreads) k_window_prep(const unsigned long long* partial, uint32_t nblocks,
+                                                                const unsigned long long* hash_partial, uint32_t nhash,
+                                                                const uint32_t* tableY, const uint32_t* tableG,
+                                                                uint32_t* Pw, uint32_t* bad) {
+  __shared__ unsigned long long sums[26];
+  __shared__ int8_t dig_e[64], dig_s[64];
+  __shared__ uint32_t pts_[kWindowThreads][32];
+  const int w = blockIdx.x, tid = threadIdx.x;
+  if (tid < 26) {
+    unsigned long long v = 0;
+    for (uint32_t b = 0; b < nblocks; ++b) v += partial[((size_t)w * nblocks + b) * 26 + tid];
+    sums[tid] = v;
+  }
+  if (w == 0 && tid == 32) {
+    unsigned long long v = 0;
+    for (uint32_t b = 0; b < nhash; ++b) v += hash_partial[(size_t)b * kPartialWords + 26];
+    *bad = v != 0 ? 1u : 0u;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const sc E = limb_sums_to_scalar(sums), S = limb_sums_to_scalar(sums + 13);
+    recode4(E.v, dig_e);
+    recode4(S.v, dig_s);
+  }
+  __syncthreads();
+  const ge term = tid < 64 ? table_pick(tableY, tid, dig_e[tid]) : table_pick(tableG, tid - 64, dig_s[tid - 64]);
+  ge_store(pts_[tid], term);
+  __syncthreads();
+  for (int h = kWindowThreads / 2; h > 0; h >>= 1) {
+    if (tid < h) ge_store(pts_[tid], ge_add(ge_load(pts_[tid]), ge_load(pts_[tid + h])));
+    __syncthreads();
+  }
+  if (tid < 32) Pw[32 * w + tid] = pts_[0][tid];
+}
+
 __global__ void k_final_check(const uint32_t* prep, const uint32_t* R, const uint32_t* point_bad,
                               const uint32_t* status, uint8_t* accept) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;

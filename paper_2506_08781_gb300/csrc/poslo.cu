@@ -566,7 +566,7 @@ int run_msm_sort(poslo_ctx* ctx, cudaStream_t st, const uint32_t* z, int sw, con
 
 // Bucket sums (entries flagged in skip_add are left out), window sums and Horner's rule.
 int run_msm_finish(poslo_ctx* ctx, cudaStream_t st, const uint32_t* pts, const uint8_t* skip_add, MsmState& ms,
-                   uint32_t* out) {
+                   uint32_t* out, uint32_t** groups_out = nullptr) {
   int rc;
   const MsmPlan& pl = ms.pl;
   const uint64_t n = ms.n;
@@ -602,6 +602,11 @@ int run_msm_finish(poslo_ctx* ctx, cudaStream_t st, const uint32_t* pts, const u
   k_msm_groups<<<pl.windows * (1 + pl.jbits), 512, 0, st>>>(L, T, pl, groups);
   ctx->launch_count += 2;
   timer_end(ctx, "msm_reduce", st, sb_, se_);
+  if (groups_out) {   // the caller checks window by window (k_msm_window_check)
+    *groups_out = groups;
+    CU(cudaGetLastError());
+    return POSLO_OK;
+  }
   timer_begin(ctx, "msm_final", st, &sb_, &se_);
   k_msm_final<<<1, 32, 0, st>>>(groups, pl, out);
   ++ctx->launch_count;
@@ -710,6 +715,52 @@ int run_prep(poslo_ctx* ctx, const unsigned long long* hpart, uint32_t nhb, cons
 }
 
 // Main stream: [8](R - prep) = O and no malformed input -> accept byte.
+// Table stream, once hashing is done: the per-window scalar sums E_w, S_w of the MSM plan pl
+// and P_w = [E_w] Y + [S_w] G for every window into Pw (32 words each), the malformed-s flag
+// into *bad; optionally the unit sum of all s_t for ccd^v; then ev_prep.
+int run_prep_windows(poslo_ctx* ctx, const unsigned long long* hpart, uint32_t nhb, const uint32_t* tableY,
+                     const uint8_t* e, const uint8_t* s_all, const uint32_t* z, uint64_t n, const MsmPlan& pl,
+                     uint32_t* Pw, uint32_t* bad, uint8_t* ccd_s, cudaStream_t hash_stream) {
+  int rc;
+  CU(cudaEventRecord(ctx->ev_hash, hash_stream));
+  CU(cudaStreamWaitEvent(ctx->s_table, ctx->ev_hash, 0));
+  const unsigned bx = (unsigned)std::max<int>(1, grid_for(ctx, n, kWindowThreads, 4) / pl.windows);
+  unsigned long long* wpart;
+  if ((rc = ensure_t(ctx, "win_partial", (size_t)bx * pl.windows * 26 * 8, &wpart))) return rc;
+  cudaEvent_t tb, te;
+  timer_begin(ctx, "prep", ctx->s_table, &tb, &te);
+  k_window_sums<<<dim3(bx, (unsigned)pl.windows), kWindowThreads, 0, ctx->s_table>>>(e, s_all, z, n, pl, wpart);
+  k_window_prep<<<(unsigned)pl.windows, kWindowThreads, 0, ctx->s_table>>>(wpart, bx, hpart, nhb, tableY,
+                                                                           ctx->tableG, Pw, bad);
+  ctx->launch_count += 2;
+  timer_end(ctx, "prep", ctx->s_table, tb, te);
+  if (ccd_s) {
+    const int sblocks = grid_for(ctx, n, kHashThreads, 8);
+    unsigned long long* sp;
+    if ((rc = ensure_t(ctx, "ccd_spart_fast", (size_t)sblocks * 13 * 8, &sp))) return rc;
+    k_sum_scalars<<<sblocks, kHashThreads, 0, ctx->s_table>>>(s_all, n, nullptr, sp);
+    k_reduce_scalars<<<1, 32, 0, ctx->s_table>>>(sp, sblocks, ccd_s);
+    ctx->launch_count += 2;
+  }
+  CU(cudaGetLastError());
+  CU(cudaEventRecord(ctx->ev_prep, ctx->s_table));
+  return POSLO_OK;
+}
+
+// Main stream, after the MSM's group sums: the per-window check into d_acc.
+int run_window_check(poslo_ctx* ctx, const uint32_t* groups, const MsmPlan& pl, const uint32_t* Pw,
+                     const uint32_t* bad, const uint32_t* pbad, uint8_t* d_acc) {
+  CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_prep, 0));
+  CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_points, 0));
+  cudaEvent_t tb, te;
+  timer_begin(ctx, "finalize", ctx->s_main, &tb, &te);
+  k_msm_window_check<<<1, 32, 0, ctx->s_main>>>(groups, pl, Pw, bad, pbad, ctx->status, d_acc);
+  ++ctx->launch_count;
+  timer_end(ctx, "finalize", ctx->s_main, tb, te);
+  CU(cudaGetLastError());
+  return POSLO_OK;
+}
+
 int run_check(poslo_ctx* ctx, const uint32_t* prep, const uint32_t* R, const uint32_t* pbad, uint8_t* d_acc) {
   CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_prep, 0));
   CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_points, 0));
@@ -1219,7 +1270,10 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
   if ((rc = ensure_t(ctx, "hash_partial", (size_t)hblocks * kPartialWords * 8, &hpart))) return rc;
   if ((rc = ensure_t(ctx, "accept", 16, &d_acc))) return rc;
   if ((rc = ensure_t(ctx, "ccd_spart", (size_t)sblocks * 13 * 8, &sp))) return rc;
-  uint32_t *unitR = small, *Rw = small + 32, *prep = small + 64, *pbad = small + 97;
+  uint32_t *unitR = small, *Rw = small + 32, *pbad = small + 97;
+  uint32_t* Pw;   // per-window [E_w]Y + [S_w]G (32 words each), then the malformed-s flag
+  if ((rc = ensure_t(ctx, "win_P", 4 * (32 * (size_t)kMsmMaxWindows + 1), &Pw))) return rc;
+  uint32_t* Pw_bad = Pw + 32 * kMsmMaxWindows;
   // ---- up to the weighted check of the whole batch; a device-resident batch of the previous
   // call's shape replays it from a CUDA graph
   const bool replayable = batch->on_device != 0;
@@ -1291,12 +1345,17 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
       CU(cudaGetLastError());
       timer_end(ctx, "hash", hs, tb, te);
     }
-    // [e]Y + [s]G and the s part of ccd^v on the table stream, while the MSM runs
-    if ((rc = run_prep(ctx, hpart, (uint32_t)hblocks, nullptr, tableY, prep, sb.s, n, d_ccd, hs))) return rc;
+    // per-window [E_w]Y + [S_w]G and the s part of ccd^v on the table stream, while the MSM runs
+    if ((rc = run_prep_windows(ctx, hpart, (uint32_t)hblocks, tableY, d_e, sb.s, z, n, ms.pl, Pw, Pw_bad, d_ccd,
+                               hs)))
+      return rc;
     CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_points, 0));
-    // weighted MSM and the weighted check of the whole batch
-    if ((rc = run_msm_finish(ctx, ctx->s_main, pts, badR, ms, Rw))) return rc;
-    if ((rc = run_check(ctx, prep, Rw, pbad, d_acc))) return rc;
+    // weighted MSM up to its window sums, and the weighted check of the whole batch window by
+    // window (it implies the check of the combined equation, and needs no doublings between
+    // the windows)
+    uint32_t* groups;
+    if ((rc = run_msm_finish(ctx, ctx->s_main, pts, badR, ms, nullptr, &groups))) return rc;
+    if ((rc = run_window_check(ctx, groups, ms.pl, Pw, Pw_bad, pbad, d_acc))) return rc;
     return POSLO_OK;
   };
   if (replayable) {
