@@ -734,8 +734,14 @@ def run_ours(args):
     d_R = torch.from_numpy(R).cuda()
     torch.cuda.synchronize()
     batch = ctx.make_batch(poslo.VARIANT_F, N2, Y, d_msgs, d_offs, d_s, d_R, ds)
-    msm_window = ctx.msm_autotune(n, 4)   # window width of the weighted MSM, timed on this GPU
-    msm_range = ctx.msm_get_plan(n, 4)[1]
+    if args.msm_plan:
+        c_fix, r_fix = (int(v) for v in args.msm_plan.split(","))
+        ctx.msm_set_plan(n, c_fix, r_fix)
+        plan_source = "fixed by --msm-plan"
+    else:
+        ctx.msm_autotune(n, 4)            # window and range length of the weighted MSM, timed on this GPU
+        plan_source = "poslo_msm_autotune"
+    msm_window, msm_range = ctx.msm_get_plan(n, 4)
 
     def step(b):
         idx, cs, cR = ctx.distill(b)
@@ -868,7 +874,7 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "entries_per_gpu": n, "message_bytes": int(msgs.data.nbytes),
                        "l2": "inputs (215 MB) larger than the 129 MB L2; no flush", "parallelism": f"dp{world}",
                        "msm_window": msm_window, "msm_range_log2": msm_range,
-                       "msm_plan_source": "poslo_msm_autotune"},
+                       "msm_plan_source": plan_source},
             "clocks": clocks,
             "gpu_launches": gpu_launches,
             "kernels": kernels,
@@ -904,6 +910,9 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop measurement")
     ap.add_argument("--no-hash-bound", action="store_true", help="skip the POSLO-C / POSLO+ hash-bound measurement")
     ap.add_argument("--no-stream", action="store_true", help="skip the out-of-core streaming measurement")
+    ap.add_argument("--msm-plan", default=None,
+                    help="C,R: fix the Distill MSM plan (window C, ranges of 2^R entries) instead of autotuning it "
+                         "(autotuner timings taken under a profiler are distorted)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
