@@ -25,6 +25,7 @@ import os
 import statistics
 import struct
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -82,7 +83,9 @@ class ClockSampler:
     def __init__(self, device: int):
         self.device = device
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # the raw samples go to POSLO_CLOCKS_DIR (default: the system's temporary directory)
+        out_dir = os.environ.get("POSLO_CLOCKS_DIR", tempfile.gettempdir())
+        self.path = os.path.join(out_dir, f"poslo_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)

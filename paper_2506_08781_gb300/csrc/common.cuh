@@ -2,13 +2,13 @@
 // helpers and the declarations of every kernel (defined in k_verify.cu, k_check.cu,
 // k_signer.cu).
 //
-//   k_epoch_seeds   A1  x_0[i] = SRet(ds, i), hoisted once per epoch (Fig. 2a; the paper's
-//                       Agg-eKeys recomputes it in every thread, Fig. 6)
-//   k_hash          A2-A4  x_t = PRF_0(x_0[i] || j), e_t = H(m_t || x_t) mod q, and the
-//                       scalar aggregates sum e_t, sum s_t (or their weighted forms)
-//   k_points        A5  strict decoding of R_t and the unit aggregate sum R_t
+//   k_epoch_seeds   x_0[i] = SRet(ds, i), hoisted once per epoch (Fig. 2a; the paper's
+//                   Agg-eKeys recomputes it in every thread, Fig. 6)
+//   k_hash          x_t = PRF_0(x_0[i] || j), e_t = H(m_t || x_t) mod q, and the scalar
+//                   aggregates sum e_t, sum s_t (or their weighted forms)
+//   k_points        strict decoding of R_t and the unit aggregate sum R_t
 //   k_table_*       fixed-window tables {d 16^w P : d = 1..8, w = 0..63} for the check
-//   k_finalize      A4/A6  reduce the partial aggregates and evaluate [8](R - eY - sG) = O
+//   k_finalize      reduce the partial aggregates and evaluate [8](R - eY - sG) = O
 #pragma once
 #include <cstdint>
 
@@ -35,12 +35,12 @@ enum : uint32_t { kErrNone = 0, kErrSeed = 1, kErrKey = 2, kErrPoint = 4, kErrTi
 struct DsNode { uint32_t d, i; uint32_t seed[4]; };   // seed as 4 big-endian words
 
 // ----------------------------------------------------------------------------------------
-// A1: SRet per epoch.
+// Epoch seeds: SRet per epoch.
 // ----------------------------------------------------------------------------------------
 
 
 // ----------------------------------------------------------------------------------------
-// A2-A4: per-entry hashing and scalar aggregation.
+// Per-entry hashing and scalar aggregation.
 // ----------------------------------------------------------------------------------------
 struct HashArgs {
   const uint8_t* msgs;
@@ -232,7 +232,7 @@ __device__ __forceinline__ void warp_sum_u64(unsigned long long& v) {
 
 
 // ----------------------------------------------------------------------------------------
-// A5 (unit): decode R_t, flag malformed ones, sum the rest.
+// Unit aggregation of the commitments: decode R_t, flag malformed ones, sum the rest.
 // ----------------------------------------------------------------------------------------
 struct PointArgs {
   const uint8_t* R;       // count*32
@@ -282,7 +282,7 @@ __device__ __forceinline__ ge table_pick(const uint32_t* table, int w, int d) {
 }
 
 // ----------------------------------------------------------------------------------------
-// A4 + A6: combine the partial aggregates and evaluate the cofactored check.
+// Combine the partial aggregates and evaluate the cofactored check.
 // ----------------------------------------------------------------------------------------
 struct FinalArgs {
   const unsigned long long* hash_partial;   // nhash blocks * kPartialWords

@@ -1,4 +1,5 @@
-// Verification kernels: epoch seeds (A1), hashing and scalar aggregation (A2-A4), point decoding and sums (A5), window tables and the final cofactored check (A6).
+// Verification kernels: epoch seeds, hashing and scalar aggregation, point decoding and sums,
+// window tables and the final cofactored check.
 #include "common.cuh"
 
 namespace poslo {

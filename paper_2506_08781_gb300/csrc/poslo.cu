@@ -1,8 +1,9 @@
 // libposlo: host orchestration and the C ABI declared in include/poslo.h.
 //
-// One context owns three CUDA streams: the main stream runs the hashing (A1-A4) and the
-// final check; a side stream builds the window table of the public key Y while hashing
-// runs; a third stream decodes and sums the commitments R_t (A5).  The hash kernel is
+// One context owns its CUDA streams: the main stream runs the seeds, weights, counting sort
+// and MSM and the final check; a side stream builds the window table of the public key Y
+// while hashing runs; a third stream decodes and sums the commitments R_t; a fourth hashes
+// the messages during the decoding.  The hash kernel is
 // bound by the integer ALU pipe (SHA-256) and the point kernel by the IMAD pipe (field
 // multiplication), so running them concurrently lets both pipes issue on every SM.
 #include <cuda_runtime.h>
@@ -1380,7 +1381,7 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
   if (all_valid) {
     CU(cudaMemsetAsync(inv, 0, n1, ctx->s_main));
   } else {
-    // ---- A7: segment-tree bisection over unit aggregates ----
+    // ---- localisation: segment-tree bisection over unit aggregates ----
     uint64_t M = 2, L = 1;
     while (M < n) { M <<= 1; ++L; }
     TreeArgs ta{};
@@ -2149,7 +2150,7 @@ int poslo_host::aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, const ui
   for (uint32_t d = 0; d < nd; ++d) total_bad += bad[d];
   std::vector<uint8_t> flag(nd, 0);
   if (!(all_ok && total_bad == 0)) {
-    // ---- A7 across devices: unit check per device, then confirm the rest together
+    // ---- localisation across devices: unit check per device, then confirm the rest together
     k_device_unit_check<<<(unsigned)((4ull * nd + 127) / 128), 128, 0, ctx->s_main>>>(d_tabs, ss, nd, ctx->tableG,
                                                                                      dev_flag);
     // the weighted sum over the devices not flagged = P1 minus the flagged devices' part,

@@ -32,7 +32,7 @@ def _f_data(seed, n, D, n2, lmin, lmax, v=32, k=4, first_index=0, msgs=None):
     return km, sk, Y, msgs, subsets, [x[0] for x in sig], [x[1] for x in sig], [x[2] for x in sig]
 
 
-# ------------------------------------------------------------------------------ A1 seeds
+# ------------------------------------------------------------------------------ epoch seeds
 
 @pytest.mark.parametrize("D", [3, 5])
 def test_epoch_seeds_every_ds(ctx, D):
@@ -66,7 +66,7 @@ def test_disclose_matches_sso(ctx):
         assert ctx.disclose(root, D, i) == O.ds_serialize(O.ds_after(root, D, i))
 
 
-# ------------------------------------------------------------------------------ A2-A3 hashing
+# ------------------------------------------------------------------------------ hashing
 
 def test_hash_every_length_and_alignment(ctx):
     """Message lengths 0..300 (all SHA-256 padding boundaries) at every byte alignment."""
@@ -126,7 +126,7 @@ def test_keygen_and_sign_c_match_oracle(ctx):
         assert gs[32 * i:32 * i + 32].tobytes() == O.sig_c(sk, i, [msgs.entry(i * n2 + j) for j in range(n2)])
 
 
-# ------------------------------------------------------------------------------ A4-A6 AVer
+# ------------------------------------------------------------------------------ AVer
 
 @pytest.mark.parametrize("mode", [poslo.AGG_UNIT, poslo.AGG_WEIGHTED])
 def test_aver_f_config1_shape(ctx, mode):
@@ -224,7 +224,7 @@ def test_aver_empty_and_single(ctx):
     assert ctx.aver(b) is True and ctx.aver(b, poslo.AGG_WEIGHTED) is True
 
 
-# ------------------------------------------------------------------------------ A7 Distill
+# ------------------------------------------------------------------------------ Distill
 
 def test_distill_random_patterns_ragged(ctx):
     D, n2, n = 4, 16, 150
