@@ -258,7 +258,7 @@ def bench_multi(ctx, steps: int, warmup: int) -> dict:
     torch.cuda.synchronize()
     stages = {}
     for name in ("seeds", "hash", "points", "msm", "msm_sort", "msm_bucket", "msm_reduce", "msm_final", "table",
-                 "prep", "check", "finalize", "tree", "bisect", "localise"):
+                 "prep", "segment_sums", "check", "finalize", "tree", "bisect", "localise"):
         tot, cnt = ctx.kernel_time(name)
         if cnt:
             stages[name] = {"ms": tot, "launches": cnt}

@@ -2085,7 +2085,16 @@ int poslo_host::aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, const ui
     // (side stream) decode every R_t
     uint32_t *ppart, npb;
     if ((rc = run_points(ctx, sb.R, N, pts, badR, &ppart, &npb))) return rc;
-    // segmented hashing with per-entry e_t, z_t
+    // the weights z_t alone (they depend only on the batch position), so the MSM's counting
+    // sort runs beside the decoding; the segmented hashing (per-entry e_t) on its own stream
+    ZPre zp;
+    make_zpre(ctx->vseed, zp.w);
+    if (N) {
+      k_weights<<<grid_for(ctx, N, 256, 4), 256, 0, ctx->s_main>>>(zp, N, 0, z);
+      ++ctx->launch_count;
+    }
+    CU(cudaEventRecord(ctx->ev_main, ctx->s_main));
+    CU(cudaStreamWaitEvent(ctx->s_hash, ctx->ev_main, 0));
     {
       const int blocks = grid_for(ctx, N, kHashThreads, 8);
       unsigned long long* hpart;
@@ -2101,8 +2110,8 @@ int poslo_host::aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, const ui
       a.e_out = d_e;
       a.s = sb.s;
       a.weighted = 1;
-      make_zpre(ctx->vseed, a.zpre);
-      a.z_out = z;
+      for (int q = 0; q < 10; ++q) a.zpre[q] = zp.w[q];
+      a.z_in = z;
       a.sbad_out = badS;
       a.partial = hpart;
       a.status = ctx->status;
@@ -2113,19 +2122,26 @@ int poslo_host::aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, const ui
       a.seg_e0 = seg_e0;
       a.seg_n2 = d_n2;
       cudaEvent_t tb, te;
-      timer_begin(ctx, "hash", ctx->s_main, &tb, &te);
-      launch_hash((int)ctx->inst, (unsigned)blocks, ctx->s_main, a);
+      timer_begin(ctx, "hash", ctx->s_hash, &tb, &te);
+      launch_hash((int)ctx->inst, (unsigned)blocks, ctx->s_hash, a);
       ++ctx->launch_count;
       CU(cudaGetLastError());
-      timer_end(ctx, "hash", ctx->s_main, tb, te);
+      timer_end(ctx, "hash", ctx->s_hash, tb, te);
+      CU(cudaEventRecord(ctx->ev_hash, ctx->s_hash));
     }
     MsmState ms;
     if ((rc = run_msm_sort(ctx, ctx->s_main, z, 4, nullptr, N, ms))) return rc;
     CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_points, 0));
     // sum_t z_t R_t, per-device sums, sum_d E_d Y_d, one combined check
     if ((rc = run_msm_finish(ctx, ctx->s_main, pts, badR, ms, P1))) return rc;
-    k_segment_sums<<<nd, 256, 0, ctx->s_main>>>(d_e, sb.s, z, pts, badR, badS, seg_start, ss);
-    ++ctx->launch_count;
+    CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_hash, 0));
+    {
+      cudaEvent_t tb, te;
+      timer_begin(ctx, "segment_sums", ctx->s_main, &tb, &te);
+      k_segment_sums<<<nd, 256, 0, ctx->s_main>>>(d_e, sb.s, z, pts, badR, badS, seg_start, ss);
+      ++ctx->launch_count;
+      timer_end(ctx, "segment_sums", ctx->s_main, tb, te);
+    }
     // sum_d E_d Y_d from the key tables
     CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_table, 0));
     k_table_msm<<<tmb, kPointThreads, 0, ctx->s_main>>>(d_tabs, ss.Ew, nullptr, nd, tmpart);
