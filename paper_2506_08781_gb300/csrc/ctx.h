@@ -50,6 +50,7 @@ struct poslo_ctx {
   cudaStream_t s_hash = nullptr;                 // message hashing of Distill
   cudaEvent_t ev_copy[2] = {nullptr, nullptr};   // chunk k's inputs have landed in set k % 2
   cudaEvent_t ev_table = nullptr, ev_points = nullptr, ev_main = nullptr, ev_hash = nullptr, ev_prep = nullptr;
+  cudaEvent_t ev_decoded = nullptr;   // points stream, right after the decoding (before its sums)
   cudaEvent_t ev_staged = nullptr;   // main stream, right after a batch's R_t have been staged
   std::map<std::string, poslo_host::DevBuf> bufs;
   uint32_t* tableG = nullptr;     // fixed-window table of G (64 KiB)

@@ -458,7 +458,8 @@ int run_points(poslo_ctx* ctx, const uint8_t* R, uint64_t count, uint32_t* pts_o
   ++ctx->launch_count;
   CU(cudaGetLastError());
   timer_end(ctx, "points", ctx->s_points, tb, te);
-  CU(cudaEventRecord(ctx->ev_points, ctx->s_points));   // callers that add work re-record it
+  CU(cudaEventRecord(ctx->ev_decoded, ctx->s_points));   // the decoded points alone
+  CU(cudaEventRecord(ctx->ev_points, ctx->s_points));    // callers that add work re-record it
   *partial_out = partial;
   *nblocks_out = (uint32_t)blocks;
   return POSLO_OK;
@@ -816,6 +817,7 @@ int poslo_create(const poslo_params* params, poslo_ctx** out) {
       cudaEventCreateWithFlags(&ctx->ev_copy[1], cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_table, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_points, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_decoded, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_main, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_hash, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_prep, cudaEventDisableTiming) != cudaSuccess ||
@@ -853,6 +855,7 @@ void poslo_destroy(poslo_ctx* ctx) {
   if (ctx->h_status) cudaFreeHost(ctx->h_status);
   if (ctx->ev_table) cudaEventDestroy(ctx->ev_table);
   if (ctx->ev_points) cudaEventDestroy(ctx->ev_points);
+  if (ctx->ev_decoded) cudaEventDestroy(ctx->ev_decoded);
   if (ctx->ev_main) cudaEventDestroy(ctx->ev_main);
   if (ctx->ev_hash) cudaEventDestroy(ctx->ev_hash);
   if (ctx->ev_prep) cudaEventDestroy(ctx->ev_prep);
@@ -1210,7 +1213,7 @@ int poslo_aver(poslo_ctx* ctx, const poslo_batch* batch, uint32_t agg_mode, uint
   if (weighted) {
     MsmState ms;
     if ((rc = run_msm_sort(ctx, ctx->s_main, z, 4, nullptr, batch->n, ms))) return rc;
-    CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_points, 0));
+    CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_decoded, 0));
     if ((rc = run_msm_finish(ctx, ctx->s_main, pts, badR, ms, Rw))) return rc;
   }
   uint8_t* d_acc;
@@ -1350,7 +1353,9 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
     if ((rc = run_prep_windows(ctx, hpart, (uint32_t)hblocks, tableY, d_e, sb.s, z, n, ms.pl, Pw, Pw_bad, d_ccd,
                                hs)))
       return rc;
-    CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_points, 0));
+    // the MSM needs the decoded points only; the unit sum behind them on the points stream
+    // (its encoding is a long inversion chain) is waited for by the check
+    CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_decoded, 0));
     // weighted MSM up to its window sums, and the weighted check of the whole batch window by
     // window (it implies the check of the combined equation, and needs no doublings between
     // the windows)
