@@ -463,6 +463,7 @@ SERVE_LO, SERVE_HI = 1, 65536
 SERVE_TAMPER_FRAC = 0.01
 SERVE_BUDGET = 64 << 30
 SERVE_WORKERS = 3
+SERVE_MAX_BATCH = 1 << 22              # entries per served batch at most
 
 
 def make_serving_workload(ctx, seed=5):
@@ -507,17 +508,20 @@ def make_serving_workload(ctx, seed=5):
     return reqs, idle, total
 
 
-def bench_serving(ctx_factory) -> dict:
+def bench_serving(ctx_factory, workers: int = SERVE_WORKERS, max_batch_entries: int = SERVE_MAX_BATCH,
+                  workload=None, plain_path: bool = True) -> dict:
     import ctypes as C
     from paper_2506_08781_gb300 import poslo, synth
-    gen_ctx = ctx_factory()
     t0 = time.perf_counter()
-    reqs, idle, total = make_serving_workload(gen_ctx)
+    if workload is None:
+        gen_ctx = ctx_factory()
+        workload = make_serving_workload(gen_ctx)
+        gen_ctx.close()
+    reqs, idle, total = workload
     setup_s = time.perf_counter() - t0
-    gen_ctx.close()
     import torch
     svc = poslo.Context(device=0, mem_budget=SERVE_BUDGET, verifier_seed=synth.verifier_seed(55))
-    svc.serve_start(workers=SERVE_WORKERS, max_batch_devices=4096, max_batch_entries=1 << 22)
+    svc.serve_start(workers=workers, max_batch_devices=4096, max_batch_entries=max_batch_entries)
     kid = [svc.register_key(r["Y"]) for r in reqs] + [svc.register_key(Y) for Y in idle]
     lib = svc.lib
     # the clients' data sit in pinned host memory and are lent to the service (POSLO_REQ_BORROW):
@@ -587,6 +591,14 @@ def bench_serving(ctx_factory) -> dict:
     batches, nreq, _ = svc.serve_stats()
     svc.serve_stop()
     svc.close()
+    head = {"workload": f"{SERVE_KEYS} resident keys, {len(reqs)} requests of log-uniform [{SERVE_LO}, {SERVE_HI}] "
+                        f"entries ({total} total), |m|~U[32,256], 1 % tampered, 64 GB budget, {workers} workers, "
+                        f"batches of at most {max_batch_entries} entries, request data lent from pinned host "
+                        "memory (POSLO_REQ_BORROW)",
+            "peak_entries_per_s": peak, "levels": levels, "batches": batches, "requests_served": nreq,
+            "setup_s": setup_s}
+    if not plain_path:
+        return head
     # the plain path for comparison: one request at a time through poslo_distill on one
     # context, from the same pinned buffers, no batching
     one = poslo.Context(device=0, verifier_seed=synth.verifier_seed(56))
@@ -603,16 +615,12 @@ def bench_serving(ctx_factory) -> dict:
     single_wall = time.perf_counter() - t_all
     one.close()
     single_lat = np.array(single_lat)
-    return {"workload": f"{SERVE_KEYS} resident keys, {len(reqs)} requests of log-uniform [{SERVE_LO}, {SERVE_HI}] "
-                        f"entries ({total} total), |m|~U[32,256], 1 % tampered, 64 GB budget, {SERVE_WORKERS} workers, "
-                        "request data lent from pinned host memory (POSLO_REQ_BORROW)",
-            "peak_entries_per_s": peak, "levels": levels, "batches": batches, "requests_served": nreq,
-            "one_request_at_a_time": {"entries_per_s": total / single_wall,
-                                      "p50_ms": float(np.percentile(single_lat, 50) * 1e3),
-                                      "p99_ms": float(np.percentile(single_lat, 99) * 1e3),
-                                      "note": "poslo_distill per request, sequential, same pinned inputs; "
-                                              "latency = its own verification time (no queue)"},
-            "setup_s": setup_s}
+    head["one_request_at_a_time"] = {"entries_per_s": total / single_wall,
+                                     "p50_ms": float(np.percentile(single_lat, 50) * 1e3),
+                                     "p99_ms": float(np.percentile(single_lat, 99) * 1e3),
+                                     "note": "poslo_distill per request, sequential, same pinned inputs; "
+                                             "latency = its own verification time (no queue)"}
+    return head
 
 
 # ------------------------------------------------------------------------------ CPU oracle arm
