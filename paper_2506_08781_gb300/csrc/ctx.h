@@ -4,6 +4,7 @@
 
 #include <cstdint>
 #include <cstddef>
+#include <functional>
 #include <map>
 #include <string>
 #include <vector>
@@ -78,8 +79,12 @@ void poslo_server_release(poslo_ctx* ctx);
 namespace poslo_host {
 // poslo_aver_multi with the devices' window tables given (device pointers, one per device,
 // host array); with key_tables = nullptr the tables are built from the keys (poslo.cu).
+// When settled is given, it is called once the devices that need no entry-level localisation
+// are known (flagged[d] = 0: device d is accepted, its result is final), before the
+// localisation of the others runs; a service publishes those results early.
 int aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, const uint32_t* const* key_tables, uint8_t* accept,
-               uint64_t* invalid_pairs, uint64_t cap, uint64_t* n_invalid);
+               uint64_t* invalid_pairs, uint64_t cap, uint64_t* n_invalid,
+               const std::function<void(const uint8_t* flagged)>* settled = nullptr);
 // Decodes Y and writes its window table (kTableWords words) to table_dev; EINVAL if Y does
 // not decode.  Synchronous.
 int build_key_table(poslo_ctx* ctx, const uint8_t Y[32], uint32_t* table_dev);

@@ -1954,7 +1954,8 @@ int poslo_host::stage_requests(poslo_ctx* ctx, const ReqView* reqs, uint32_t nd,
 }
 
 int poslo_host::aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, const uint32_t* const* key_tables,
-                           uint8_t* accept, uint64_t* invalid_pairs, uint64_t cap, uint64_t* n_invalid) {
+                           uint8_t* accept, uint64_t* invalid_pairs, uint64_t cap, uint64_t* n_invalid,
+                           const std::function<void(const uint8_t* flagged)>* settled) {
   if (!ctx || !mb || !accept || !n_invalid || mb->n_dev == 0 || !mb->Y || !mb->dev_start || !mb->first_index ||
       !mb->n2 || !mb->ds || !mb->ds_off)
     return fail(ctx, POSLO_EINVAL, "bad aver_multi arguments");
@@ -2190,6 +2191,7 @@ int poslo_host::aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, const ui
     if ((rc = check_status(ctx))) return rc;
     if (!confirmed) std::fill(flag.begin(), flag.end(), 1);   // cancelling errors: settle every device
   }
+  if (settled) (*settled)(flag.data());
   // ---- localise inside the flagged devices: the single-entry check of every entry of every
   // flagged device in one launch, with the key tables built above
   std::vector<uint32_t> fl;

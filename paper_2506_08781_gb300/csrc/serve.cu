@@ -17,6 +17,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <functional>
 #include <memory>
 #include <mutex>
 #include <thread>
@@ -111,7 +112,33 @@ void run_batch(Server* S, poslo_ctx* w, std::vector<Req*>& batch) {
   std::vector<uint8_t> acc(nd);
   std::vector<uint64_t> pairs(2 * std::max<uint64_t>(total, 1));
   uint64_t cnt = 0;
-  if (rc == POSLO_OK) rc = aver_multi(w, &mb, tabs.data(), acc.data(), pairs.data(), total, &cnt);
+  // requests whose device passes the device-level checks are final before the entry-level
+  // localisation of the others: publish them at once (a reader may then release them, so
+  // they are not touched again here)
+  std::vector<uint8_t> published(nd, 0);
+  const std::function<void(const uint8_t*)> settled = [&](const uint8_t* flagged) {
+    {
+      std::lock_guard<std::mutex> lock(S->mu);
+      const auto now = std::chrono::steady_clock::now();
+      for (uint32_t d = 0; d < nd; ++d) {
+        if (flagged[d]) continue;
+        Req* r = batch[d];
+        r->rc = POSLO_OK;
+        r->accept = 1;
+        r->invalid.clear();
+        r->state = 2;
+        r->t_done = now;
+        std::vector<uint8_t>().swap(r->msgs);
+        std::vector<uint8_t>().swap(r->s);
+        std::vector<uint8_t>().swap(r->R);
+        std::vector<uint64_t>().swap(r->offs);
+        r->view = ReqView{};
+        published[d] = 1;
+      }
+    }
+    S->cv_done.notify_all();
+  };
+  if (rc == POSLO_OK) rc = aver_multi(w, &mb, tabs.data(), acc.data(), pairs.data(), total, &cnt, &settled);
   std::vector<int> rcs(nd, rc);
   std::vector<std::vector<uint64_t>> inv(nd);
   if (rc == POSLO_OK) {
@@ -119,6 +146,7 @@ void run_batch(Server* S, poslo_ctx* w, std::vector<Req*>& batch) {
   } else if (nd > 1) {
     // one malformed request must not fail the others: verify each on its own
     for (uint32_t d = 0; d < nd; ++d) {
+      if (published[d]) continue;
       poslo_batch b{};
       Req* r = batch[d];
       b.variant = POSLO_VARIANT_F;
@@ -143,6 +171,7 @@ void run_batch(Server* S, poslo_ctx* w, std::vector<Req*>& batch) {
   }
   std::lock_guard<std::mutex> lock(S->mu);
   for (uint32_t d = 0; d < nd; ++d) {
+    if (published[d]) continue;
     Req* r = batch[d];
     r->rc = rcs[d];
     r->accept = rcs[d] == POSLO_OK ? acc[d] : 0;
