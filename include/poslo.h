@@ -384,6 +384,15 @@ void poslo_reset_kernel_times(poslo_ctx* ctx);
  * default; poslo_set_graphs(ctx, 0) turns it off and frees the graphs.
  * poslo_graph_stats reports how many graphs were captured and how many replays ran. */
 int poslo_set_graphs(poslo_ctx* ctx, int enabled);
+
+/* Form of poslo_aver_multi's combined weighted check (no counterpart in the paper).  Batches
+ * of at most max_entries entries (default 2^21) check it window by window of the weights'
+ * signed digits -- sum_t d_{t,w} R_t = sum_d (sum_{t in d} d_{t,w} e_t) Y_d + (sum_t d_{t,w} s_t) G
+ * for every window w, which together imply the check with the full weights -- and so skip the
+ * MSM's doublings between windows on their critical path; larger batches check the full
+ * weights, where the per-device, per-window scalar sums cost more than those doublings.
+ * Results are the same either way.  EINVAL for a null context. */
+int poslo_set_multi_window_limit(poslo_ctx* ctx, uint64_t max_entries);
 int poslo_graph_stats(poslo_ctx* ctx, uint64_t* captures, uint64_t* replays);
 
 #ifdef __cplusplus

@@ -522,6 +522,60 @@ __device__ __forceinline__ void z_load(const uint32_t* z, int sw, uint64_t t, ui
   }
 }
 
+// Window w of entry t's weight in the MSM's signed digits: magnitude d and sign neg.
+__device__ __forceinline__ uint32_t weight_digit(const uint32_t* z, uint64_t t, int w, int c, bool& neg) {
+  uint32_t zw[8];
+  z_load(z, 4, t, zw);
+  uint32_t carry = 0, d = 0;
+  neg = false;
+  for (int k = 0; k <= w; ++k) d = z_sdigit(zw, 4, k, c, carry, neg);
+  return d;
+}
+
+// ae += digit e_t, as += digit s_t (mod q, exactly in 416-bit accumulators) for the digit of
+// magnitude d and sign neg: a negative digit adds d (q - x).
+__device__ __forceinline__ void add_window_terms(acc13& ae, acc13& as, const uint8_t* e32, const uint8_t* s32,
+                                                 uint32_t d, bool neg) {
+  const uint4* ep = reinterpret_cast<const uint4*>(e32);
+  const uint4* sp = reinterpret_cast<const uint4*>(s32);
+  const uint4 e0 = ep[0], e1 = ep[1], s0 = sp[0], s1 = sp[1];
+  uint32_t x[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
+  uint32_t y[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+  if (neg) {
+    uint32_t q[8];
+    sc_qlimbs(q);
+    int64_t bx = 0, by = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      bx += (int64_t)q[k] - x[k];
+      by += (int64_t)q[k] - y[k];
+      x[k] = (uint32_t)bx;
+      y[k] = (uint32_t)by;
+      bx >>= 32;
+      by >>= 32;
+    }
+  }
+  uint32_t r[9];
+  uint64_t c0 = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    c0 += (uint64_t)d * x[k];
+    r[k] = (uint32_t)c0;
+    c0 >>= 32;
+  }
+  r[8] = (uint32_t)c0;
+  acc_add<9>(ae, r);
+  uint64_t c1 = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    c1 += (uint64_t)d * y[k];
+    r[k] = (uint32_t)c1;
+    c1 >>= 32;
+  }
+  r[8] = (uint32_t)c1;
+  acc_add<9>(as, r);
+}
+
 __device__ __forceinline__ void pts_load(const uint32_t* src, fe& x, fe& y, fe& t2d) {
   const uint4* s4 = reinterpret_cast<const uint4*>(src);
   uint4 v[6];
@@ -618,6 +672,7 @@ __global__ void __launch_bounds__(kCombineBigThreads) k_msm_combine_big(const ui
 __global__ void __launch_bounds__(128) k_msm_chunk(const uint32_t* buckets, MsmPlan pl, uint32_t* L, uint32_t* T);
 __global__ void __launch_bounds__(512) k_msm_groups(const uint32_t* L, const uint32_t* T, MsmPlan pl, uint32_t* groups);
 __global__ void __launch_bounds__(32) k_msm_final(const uint32_t* groups, MsmPlan pl, uint32_t* out);
+__global__ void __launch_bounds__(32) k_msm_windows(const uint32_t* groups, MsmPlan pl, uint32_t* W);
 __global__ void __launch_bounds__(32) k_msm_window_check(const uint32_t* groups, MsmPlan pl, const uint32_t* Pw,
                                                          const uint32_t* bad, const uint32_t* point_bad,
                                                          const uint32_t* status, uint8_t* accept);
@@ -655,6 +710,19 @@ __global__ void __launch_bounds__(kFinalThreads) k_multi_check(const uint32_t* P
                                                                uint8_t* accept);
 __global__ void __launch_bounds__(kPointThreads) k_table_msm(const uint32_t* const* tabs, const uint32_t* k,
                                                              const uint8_t* skip, uint32_t n, uint32_t* partial);
+__global__ void __launch_bounds__(256) k_segment_window_sums(const uint8_t* e, const uint8_t* s, const uint32_t* z,
+                                                             const uint8_t* badR, const uint8_t* badS,
+                                                             const uint64_t* start, uint32_t n_dev, MsmPlan pl,
+                                                             uint32_t* Ewd, uint32_t* Swd);
+__global__ void __launch_bounds__(kFinalThreads) k_multi_window_check(const uint32_t* W, const uint32_t* Wsub,
+                                                                      const uint32_t* P2w, const uint32_t* Swd,
+                                                                      const uint8_t* dev_flag, uint32_t n_dev,
+                                                                      const uint32_t* tableG, uint8_t* accept);
+__global__ void __launch_bounds__(kPointThreads) k_table_msm_windows(const uint32_t* const* tabs, const uint32_t* k,
+                                                                     const uint8_t* skip, uint32_t n,
+                                                                     uint32_t* partial);
+__global__ void __launch_bounds__(kPointThreads) k_window_point_sums(const uint32_t* partial, uint32_t nblocks,
+                                                                     uint32_t* out);
 __global__ void __launch_bounds__(128) k_device_unit_check(const uint32_t* const* tabs, SegSums ss, uint32_t n_dev,
                                                            const uint32_t* tableG, uint8_t* dev_flag);
 struct MultiCheckArgs {

@@ -297,8 +297,29 @@ __global__ void __launch_bounds__(32) k_msm_final(const uint32_t* groups, MsmPla
   if (lane == 0) ge_store(out, acc);
 }
 
-// Per-window weighted check, group side: quad w forms the window sum W_w = G_0 + 16 sum_k 2^k
-// G_{1+k} of window w from its group sums (as k_msm_final does) and tests
+// Window sum W_w = G_0 + 16 sum_k 2^k G_{1+k} of window w from its group sums (quad-cooperative
+// Horner over the group bits; every lane of the quad ends with the whole point).
+__device__ __forceinline__ ge window_sum_quad(const uint32_t* groups, const MsmPlan& pl, int w) {
+  const int ng = 1 + pl.jbits;
+  const uint32_t* G = groups + 32 * (size_t)w * ng;
+  ge acc = ge_load(G + 32 * pl.jbits);
+  for (int k = pl.jbits - 2; k >= 0; --k) acc = ge_add_quad(ge_dbl_quad(acc), ge_load(G + 32 * (1 + k)));
+  for (int i = 0; i < 4; ++i) acc = ge_dbl_quad(acc);   // times kMsmChunk = 16
+  return ge_add_quad(acc, ge_load(G));
+}
+
+// The window sums W_w of every window into W (32 words each): quad w per window, in rounds
+// of eight quads.  One warp.
+__global__ void __launch_bounds__(32) k_msm_windows(const uint32_t* groups, MsmPlan pl, uint32_t* W) {
+  const int lane = threadIdx.x & 31, quad = lane >> 2;
+  for (int r0 = 0; r0 < pl.windows; r0 += 8) {
+    const int w = r0 + quad;
+    const ge acc = window_sum_quad(groups, pl, w < pl.windows ? w : pl.windows - 1);
+    if ((lane & 3) == 0 && w < pl.windows) ge_store(W + 32 * (size_t)w, acc);
+  }
+}
+
+// Per-window weighted check, group side: quad w forms the window sum W_w and tests
 // [8](W_w - P_w) = O against P_w = [E_w] Y + [S_w] G (k_window_prep); windows are processed in
 // rounds of eight quads.  accept = every window holds, no malformed s (*bad), no undecodable
 // R (*point_bad) and a decodable key.  One warp.
@@ -306,16 +327,11 @@ __global__ void __launch_bounds__(32) k_msm_window_check(const uint32_t* groups,
                                                          const uint32_t* bad, const uint32_t* point_bad,
                                                          const uint32_t* status, uint8_t* accept) {
   const int lane = threadIdx.x & 31, quad = lane >> 2;
-  const int ng = 1 + pl.jbits;
   bool ok = true;
   for (int r0 = 0; r0 < pl.windows; r0 += 8) {
     const int w = r0 + quad;
     const int wc = w < pl.windows ? w : pl.windows - 1;
-    const uint32_t* G = groups + 32 * (size_t)wc * ng;
-    ge acc = ge_load(G + 32 * pl.jbits);
-    for (int k = pl.jbits - 2; k >= 0; --k) acc = ge_add_quad(ge_dbl_quad(acc), ge_load(G + 32 * (1 + k)));
-    for (int i = 0; i < 4; ++i) acc = ge_dbl_quad(acc);   // times kMsmChunk = 16
-    acc = ge_add_quad(acc, ge_load(G));
+    const ge acc = window_sum_quad(groups, pl, wc);
     ge diff = ge_add_quad(acc, ge_neg(ge_load(Pw + 32 * (size_t)wc)));
     for (int i = 0; i < 3; ++i) diff = ge_dbl_quad(diff);   // cofactor 8
     if (w < pl.windows) ok = ok && ge_is_identity(diff);

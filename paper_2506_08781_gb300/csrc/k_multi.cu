@@ -142,6 +142,149 @@ __global__ void __launch_bounds__(256) k_segment_sums(const uint8_t* e, const ui
   }
 }
 
+// Per-device, per-window weighted sums (the per-window form of the combined check, used for
+// batches small enough that the MSM's Horner over windows is a large share of the latency):
+// block b = d windows + w adds d_{t,w} e_t and d_{t,w} s_t over the well-formed entries of
+// device d (a negative digit adds |d| (q - x)) and writes them reduced mod q to
+// Ewd[8 (w n_dev + d)] and Swd[8 (w n_dev + d)].  The blocks of one device are consecutive,
+// so its entries come from DRAM once and from L2 for the other windows.
+__global__ void __launch_bounds__(kSegThreads) k_segment_window_sums(const uint8_t* e, const uint8_t* s,
+                                                                     const uint32_t* z, const uint8_t* badR,
+                                                                     const uint8_t* badS, const uint64_t* start,
+                                                                     uint32_t n_dev, MsmPlan pl, uint32_t* Ewd,
+                                                                     uint32_t* Swd) {
+  const uint32_t d = blockIdx.x / (uint32_t)pl.windows;
+  const int w = (int)(blockIdx.x % (uint32_t)pl.windows);
+  acc13 ae, as;
+  acc_zero(ae);
+  acc_zero(as);
+  for (uint64_t t = start[d] + threadIdx.x; t < start[d + 1]; t += blockDim.x) {
+    if (badR[t] || badS[t]) continue;
+    bool neg;
+    const uint32_t dg = weight_digit(z, t, w, pl.c, neg);
+    if (dg) add_window_terms(ae, as, e + 32 * t, s + 32 * t, dg, neg);
+  }
+  __shared__ unsigned long long red[kSegThreads / 32][26];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = 0; k < 26; ++k) {
+    unsigned long long v = k < 13 ? ae.v[k] : as.v[k - 13];
+    warp_sum_u64(v);
+    if (lane == 0) red[warp][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    unsigned long long sums[13];
+    for (int k = 0; k < 13; ++k) {
+      unsigned long long v = 0;
+      for (int i = 0; i < kSegThreads / 32; ++i) v += red[i][13 * threadIdx.x + k];
+      sums[k] = v;
+    }
+    const sc r = limb_sums_to_scalar(sums);
+    uint32_t* dst = (threadIdx.x == 0 ? Ewd : Swd) + 8 * ((size_t)w * n_dev + d);
+    for (int k = 0; k < 8; ++k) dst[k] = r.v[k];
+  }
+}
+
+// Combined weighted check of window w over the devices not flagged (block w):
+// [8](W_w - Wsub_w - P2_w - (sum_d S_{d,w}) G) = O, with W_w = sum_t d_{t,w} R_t over the whole
+// batch, Wsub_w the same sum over the flagged devices' entries (none when Wsub is null) and
+// P2_w = sum_d E_{d,w} Y_d already restricted to the devices not flagged.  A window that fails
+// clears accept[0] (set to 1 beforehand).  The windows together imply the check with the full
+// weights z_t.
+__global__ void __launch_bounds__(kFinalThreads) k_multi_window_check(const uint32_t* W, const uint32_t* Wsub,
+                                                                      const uint32_t* P2w, const uint32_t* Swd,
+                                                                      const uint8_t* dev_flag, uint32_t n_dev,
+                                                                      const uint32_t* tableG, uint8_t* accept) {
+  const int w = blockIdx.x;
+  __shared__ unsigned long long red[kFinalThreads / 32][13];
+  __shared__ int8_t dig[64];
+  __shared__ uint32_t pts_[kFinalThreads][32];
+  acc13 a;
+  acc_zero(a);
+  for (uint32_t d = threadIdx.x; d < n_dev; d += blockDim.x)
+    if (!(dev_flag && dev_flag[d])) acc_add<8>(a, Swd + 8 * ((size_t)w * n_dev + d));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = 0; k < 13; ++k) {
+    unsigned long long v = a.v[k];
+    warp_sum_u64(v);
+    if (lane == 0) red[warp][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long sums[13];
+    for (int k = 0; k < 13; ++k) {
+      unsigned long long v = 0;
+      for (int i = 0; i < kFinalThreads / 32; ++i) v += red[i][k];
+      sums[k] = v;
+    }
+    const sc S = limb_sums_to_scalar(sums);
+    recode4(S.v, dig);
+  }
+  __syncthreads();
+  ge term = threadIdx.x < kTableWindows ? table_pick(tableG, threadIdx.x, dig[threadIdx.x]) : ge_identity();
+  ge_store(pts_[threadIdx.x], term);
+  __syncthreads();
+  for (int h = kTableWindows / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) ge_store(pts_[threadIdx.x], ge_add(ge_load(pts_[threadIdx.x]), ge_load(pts_[threadIdx.x + h])));
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    ge p1 = ge_load(W + 32 * (size_t)w);
+    if (Wsub) p1 = ge_sub(p1, ge_load(Wsub + 32 * (size_t)w));
+    const ge diff = ge_sub(ge_sub(p1, ge_load(P2w + 32 * (size_t)w)), ge_load(pts_[0]));
+    if (!ge_is_identity(ge_mul_cofactor(diff))) accept[0] = 0;
+  }
+}
+
+// sum over the devices not skipped of [k_{d,w}] Y_d for every window w, from the devices'
+// fixed-window tables: block (x, w) adds the table terms of its share of the (device, table
+// window) pairs for the scalars k + 8 (w n + d), no doublings; per block one partial point
+// at partial[33 (w gridDim.x + x)].
+__global__ void __launch_bounds__(kPointThreads) k_table_msm_windows(const uint32_t* const* tabs, const uint32_t* k,
+                                                                     const uint8_t* skip, uint32_t n,
+                                                                     uint32_t* partial) {
+  const int win = blockIdx.y;
+  ge acc = ge_identity();
+  const uint64_t total = (uint64_t)n * kTableWindows;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total; p += stride) {
+    const uint32_t d = (uint32_t)(p / kTableWindows);
+    const int w = (int)(p % kTableWindows);
+    if (skip && skip[d]) continue;
+    const uint32_t* kd = k + 8 * ((size_t)win * n + d);
+    int carry = 0, digit = 0;
+    for (int i = 0; i <= w; ++i) digit = sc_digit4(kd, i, carry);
+    if (digit) acc = ge_add(acc, table_pick(tabs[d], w, digit));
+  }
+  __shared__ uint32_t sp[kPointThreads][32];
+  ge_store(sp[threadIdx.x], acc);
+  __syncthreads();
+  for (int h = kPointThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) ge_store(sp[threadIdx.x], ge_add(ge_load(sp[threadIdx.x]), ge_load(sp[threadIdx.x + h])));
+    __syncthreads();
+  }
+  const size_t o = ((size_t)win * gridDim.x + blockIdx.x) * kPointPartialWords;
+  if (threadIdx.x < 32) partial[o + threadIdx.x] = sp[0][threadIdx.x];
+  if (threadIdx.x == 0) partial[o + 32] = 0;
+}
+
+// out[w] = the sum of the nblocks partial points of window w (block w).
+__global__ void __launch_bounds__(kPointThreads) k_window_point_sums(const uint32_t* partial, uint32_t nblocks,
+                                                                     uint32_t* out) {
+  const int w = blockIdx.x;
+  ge acc = ge_identity();
+  for (uint32_t b = threadIdx.x; b < nblocks; b += blockDim.x)
+    acc = ge_add(acc, ge_load(partial + ((size_t)w * nblocks + b) * kPointPartialWords));
+  __shared__ uint32_t sp[kPointThreads][32];
+  ge_store(sp[threadIdx.x], acc);
+  __syncthreads();
+  for (int h = kPointThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) ge_store(sp[threadIdx.x], ge_add(ge_load(sp[threadIdx.x]), ge_load(sp[threadIdx.x + h])));
+    __syncthreads();
+  }
+  if (threadIdx.x < 32) out[32 * (size_t)w + threadIdx.x] = sp[0][threadIdx.x];
+}
+
 // Combined weighted check over the devices not flagged:
 // [8](P1 - P2 - (sum_d S_d) G) = O, with P1 = sum_t z_t R_t and P2 = sum_d E_d Y_d already
 // restricted to those devices.  One block.

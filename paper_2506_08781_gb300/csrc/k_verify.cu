@@ -527,51 +527,11 @@ __global__ void __launch_bounds__(kWindowThreads) k_window_sums(const uint8_t* e
   acc13 ae, as;
   acc_zero(ae);
   acc_zero(as);
-  uint32_t q[8];
-  sc_qlimbs(q);
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
-    uint32_t zw[8];
-    z_load(z, 4, t, zw);
-    uint32_t carry = 0, d = 0;
-    bool neg = false;
-    for (int k = 0; k <= w; ++k) d = z_sdigit(zw, 4, k, pl.c, carry, neg);
-    if (d == 0) continue;
-    const uint4* ep = reinterpret_cast<const uint4*>(e + 32 * t);
-    const uint4* sp = reinterpret_cast<const uint4*>(s + 32 * t);
-    const uint4 e0 = ep[0], e1 = ep[1], s0 = sp[0], s1 = sp[1];
-    uint32_t x[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
-    uint32_t y[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
-    if (neg) {
-      int64_t bx = 0, by = 0;
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        bx += (int64_t)q[k] - x[k];
-        by += (int64_t)q[k] - y[k];
-        x[k] = (uint32_t)bx;
-        y[k] = (uint32_t)by;
-        bx >>= 32;
-        by >>= 32;
-      }
-    }
-    uint32_t r[9];
-    uint64_t c0 = 0, c1 = 0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      c0 += (uint64_t)d * x[k];
-      r[k] = (uint32_t)c0;
-      c0 >>= 32;
-    }
-    r[8] = (uint32_t)c0;
-    acc_add<9>(ae, r);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      c1 += (uint64_t)d * y[k];
-      r[k] = (uint32_t)c1;
-      c1 >>= 32;
-    }
-    r[8] = (uint32_t)c1;
-    acc_add<9>(as, r);
+    bool neg;
+    const uint32_t d = weight_digit(z, t, w, pl.c, neg);
+    if (d) add_window_terms(ae, as, e + 32 * t, s + 32 * t, d, neg);
   }
   __shared__ unsigned long long red[kWindowThreads / 32][26];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

@@ -880,6 +880,12 @@ int poslo_set_profiling(poslo_ctx* ctx, int enabled) {
   return POSLO_OK;
 }
 
+int poslo_set_multi_window_limit(poslo_ctx* ctx, uint64_t max_entries) {
+  if (!ctx) return POSLO_EINVAL;
+  ctx->multi_window_max = max_entries;
+  return POSLO_OK;
+}
+
 int poslo_set_graphs(poslo_ctx* ctx, int enabled) {
   if (!ctx) return POSLO_EINVAL;
   ctx->graphs = enabled != 0;
@@ -2048,6 +2054,21 @@ int poslo_host::aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, const ui
   if ((rc = ensure_t(ctx, "m_seg", (size_t)nd * (32 + 32 + 1) * 4, &segbuf))) return rc;
   if ((rc = ensure_t(ctx, "m_tmpart", (size_t)tmb * kPointPartialWords * 4, &tmpart))) return rc;
   uint32_t *P2 = P1 + 32, *P3 = P1 + 64;
+  // batches up to multi_window_max entries check window by window (no Horner over the windows
+  // on the critical path); larger ones with the full weights, where the per-device,
+  // per-window scalar sums would cost more than the Horner they remove
+  const MsmPlan plan = msm_plan(ctx, N, 4);
+  const bool per_window = N <= ctx->multi_window_max;
+  const uint32_t nw = (uint32_t)plan.windows;
+  const int tmbw = std::max(1, tmb / (int)nw);
+  uint32_t *Wbuf = nullptr, *EWd = nullptr, *tmpw = nullptr;
+  if (per_window) {
+    if ((rc = ensure_t(ctx, "m_W", 4 * 3 * 32 * (size_t)nw, &Wbuf))) return rc;
+    if ((rc = ensure_t(ctx, "m_EWd", 4 * 2 * 8 * (size_t)nw * nd, &EWd))) return rc;
+    if ((rc = ensure_t(ctx, "m_tmpw", (size_t)tmbw * nw * kPointPartialWords * 4, &tmpw))) return rc;
+  }
+  uint32_t *Wall = Wbuf, *Wsub = Wbuf ? Wbuf + 32 * (size_t)nw : nullptr, *P2w = Wbuf ? Wbuf + 64 * (size_t)nw : nullptr;
+  uint32_t *Ewd = EWd, *Swd = EWd ? EWd + 8 * (size_t)nw * nd : nullptr;
   SegSums ss;
   ss.Ew = segbuf;
   ss.Sw = ss.Ew + 8 * (size_t)nd;
@@ -2057,11 +2078,11 @@ int poslo_host::aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, const ui
   ss.bad = ss.Ru + 32 * (size_t)nd;
   // ---- first stage, up to the combined check: one launch per step over the device segment
   // table, replayed from a CUDA graph when the call has the shape of the previous one
-  const MsmPlan plan = msm_plan(ctx, N, 4);
   std::vector<uint64_t> sig = {nd, N, mb->on_device, key_tables ? 1u : 0u, sb.base_off,
                                reinterpret_cast<uint64_t>(sb.msgs), reinterpret_cast<uint64_t>(sb.offs),
                                reinterpret_cast<uint64_t>(sb.s), reinterpret_cast<uint64_t>(sb.R),
-                               nodes.size(), (uint64_t)plan.c, (uint64_t)plan.seg_log2, ctx->inst};
+                               nodes.size(), (uint64_t)plan.c, (uint64_t)plan.seg_log2, ctx->inst,
+                               per_window ? 1u : 0u};
   sig.insert(sig.end(), mb->dev_start, mb->dev_start + nd + 1);
   sig.insert(sig.end(), mb->first_index, mb->first_index + nd);
   sig.insert(sig.end(), mb->n2, mb->n2 + nd);
@@ -2138,15 +2159,36 @@ int poslo_host::aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, const ui
     MsmState ms;
     if ((rc = run_msm_sort(ctx, ctx->s_main, z, 4, nullptr, N, ms))) return rc;
     CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_points, 0));
-    // sum_t z_t R_t, per-device sums, sum_d E_d Y_d, one combined check
-    if ((rc = run_msm_finish(ctx, ctx->s_main, pts, badR, ms, P1))) return rc;
+    // sum_t z_t R_t (or its window sums), per-device sums, sum_d E_d Y_d, the combined check
+    uint32_t* groups = nullptr;
+    if ((rc = run_msm_finish(ctx, ctx->s_main, pts, badR, ms, P1, per_window ? &groups : nullptr))) return rc;
+    if (per_window) {
+      k_msm_windows<<<1, 32, 0, ctx->s_main>>>(groups, ms.pl, Wall);
+      ++ctx->launch_count;
+    }
     CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_hash, 0));
     {
       cudaEvent_t tb, te;
       timer_begin(ctx, "segment_sums", ctx->s_main, &tb, &te);
       k_segment_sums<<<nd, 256, 0, ctx->s_main>>>(d_e, sb.s, z, pts, badR, badS, seg_start, ss);
       ++ctx->launch_count;
+      if (per_window) {
+        k_segment_window_sums<<<nd * nw, 256, 0, ctx->s_main>>>(d_e, sb.s, z, badR, badS, seg_start, nd, ms.pl,
+                                                                Ewd, Swd);
+        ++ctx->launch_count;
+      }
       timer_end(ctx, "segment_sums", ctx->s_main, tb, te);
+    }
+    if (per_window) {
+      CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_table, 0));
+      k_table_msm_windows<<<dim3(tmbw, nw), kPointThreads, 0, ctx->s_main>>>(d_tabs, Ewd, nullptr, nd, tmpw);
+      k_window_point_sums<<<nw, kPointThreads, 0, ctx->s_main>>>(tmpw, tmbw, P2w);
+      CU(cudaMemsetAsync(d_acc, 1, 1, ctx->s_main));
+      k_multi_window_check<<<nw, kFinalThreads, 0, ctx->s_main>>>(Wall, nullptr, P2w, Swd, nullptr, nd,
+                                                                 ctx->tableG, d_acc);
+      ctx->launch_count += 3;
+      CU(cudaGetLastError());
+      return POSLO_OK;
     }
     // sum_d E_d Y_d from the key tables
     CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_table, 0));
@@ -2179,12 +2221,27 @@ int poslo_host::aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, const ui
     // an MSM over their entries only
     k_device_to_entries<<<nd, 256, 0, ctx->s_main>>>(dev_flag, seg_start, badR, eskip, 1);
     ctx->launch_count += 2;
-    if ((rc = run_msm(ctx, ctx->s_main, pts, z, 4, eskip, N, P3))) return rc;
-    k_table_msm<<<tmb, kPointThreads, 0, ctx->s_main>>>(d_tabs, ss.Ew, dev_flag, nd, tmpart);
-    k_sum_encode<<<1, kFinalThreads, 0, ctx->s_main>>>(tmpart, tmb, P2, nullptr, nullptr);
-    ctx->launch_count += 2;
-    k_multi_check<<<1, kFinalThreads, 0, ctx->s_main>>>(P1, P3, P2, ss.Sw, dev_flag, nd, ctx->tableG, d_acc);
-    ++ctx->launch_count;
+    if (per_window) {
+      // the same plan, so the flagged part's windows line up with the whole batch's
+      MsmState ms2;
+      uint32_t* groups2;
+      if ((rc = run_msm_sort(ctx, ctx->s_main, z, 4, eskip, N, ms2))) return rc;
+      if ((rc = run_msm_finish(ctx, ctx->s_main, pts, eskip, ms2, nullptr, &groups2))) return rc;
+      k_msm_windows<<<1, 32, 0, ctx->s_main>>>(groups2, ms2.pl, Wsub);
+      k_table_msm_windows<<<dim3(tmbw, nw), kPointThreads, 0, ctx->s_main>>>(d_tabs, Ewd, dev_flag, nd, tmpw);
+      k_window_point_sums<<<nw, kPointThreads, 0, ctx->s_main>>>(tmpw, tmbw, P2w);
+      CU(cudaMemsetAsync(d_acc, 1, 1, ctx->s_main));
+      k_multi_window_check<<<nw, kFinalThreads, 0, ctx->s_main>>>(Wall, Wsub, P2w, Swd, dev_flag, nd, ctx->tableG,
+                                                                 d_acc);
+      ctx->launch_count += 4;
+    } else {
+      if ((rc = run_msm(ctx, ctx->s_main, pts, z, 4, eskip, N, P3))) return rc;
+      k_table_msm<<<tmb, kPointThreads, 0, ctx->s_main>>>(d_tabs, ss.Ew, dev_flag, nd, tmpart);
+      k_sum_encode<<<1, kFinalThreads, 0, ctx->s_main>>>(tmpart, tmb, P2, nullptr, nullptr);
+      ctx->launch_count += 2;
+      k_multi_check<<<1, kFinalThreads, 0, ctx->s_main>>>(P1, P3, P2, ss.Sw, dev_flag, nd, ctx->tableG, d_acc);
+      ++ctx->launch_count;
+    }
     uint8_t confirmed = 0;
     CU(cudaMemcpyAsync(&confirmed, d_acc, 1, cudaMemcpyDeviceToHost, ctx->s_main));
     CU(cudaMemcpyAsync(flag.data(), dev_flag, nd, cudaMemcpyDeviceToHost, ctx->s_main));

@@ -30,6 +30,7 @@ EXPORTS = [
     "poslo_aver", "poslo_distill", "poslo_epoch_seeds", "poslo_hash_entries", "poslo_msm", "poslo_msm_autotune",
     "poslo_msm_get_plan", "poslo_msm_set_plan",
     "poslo_set_profiling", "poslo_kernel_time", "poslo_reset_kernel_times", "poslo_set_graphs", "poslo_graph_stats",
+    "poslo_set_multi_window_limit",
     "poslo_hash_entries_noalloc", "poslo_aver_multi", "poslo_distill_c", "poslo_sebver_c", "poslo_distill_stream",
     "poslo_serve_start", "poslo_serve_stop", "poslo_register_key", "poslo_submit", "poslo_poll",
     "poslo_serve_stats",
@@ -109,6 +110,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "poslo_msm_set_plan": ([vp, u64, u32, u32, u32], C.c_int),
         "poslo_set_profiling": ([vp, C.c_int], C.c_int),
         "poslo_set_graphs": ([vp, C.c_int], C.c_int),
+        "poslo_set_multi_window_limit": ([vp, u64], C.c_int),
         "poslo_graph_stats": ([vp, C.POINTER(u64), C.POINTER(u64)], C.c_int),
         "poslo_kernel_time": ([vp, C.c_char_p, C.POINTER(C.c_double), C.POINTER(u64)], C.c_int),
         "poslo_reset_kernel_times": ([vp], None),
@@ -491,6 +493,10 @@ class Context:
     def set_graphs(self, on: bool):
         """Replay repeated call shapes of aver_multi / distill from CUDA graphs (default on)."""
         self._check(self.lib.poslo_set_graphs(self.h, 1 if on else 0))
+
+    def set_multi_window_limit(self, max_entries: int):
+        """Multi-device batches up to max_entries check window by window (default 2^21)."""
+        self._check(self.lib.poslo_set_multi_window_limit(self.h, max_entries))
 
     def graph_stats(self):
         """(graphs captured, replays run) on this context."""

@@ -202,3 +202,30 @@ def test_multi_graphs_off_same_results():
             acc, pairs = cx.aver_multi(*args)
             assert list(acc) == want_acc and [tuple(int(x) for x in p) for p in pairs] == want_pairs
         assert cx.graph_stats() == (0, 0)
+
+
+@pytest.mark.parametrize("limit", [0, 1 << 40])
+def test_multi_both_check_forms(limit):
+    """The combined weighted check with the full weights (limit 0) and window by window (any
+    batch below the limit) give the same per-device results: tampered devices, malformed
+    entries and cancelling s-shifts."""
+    import __graft_entry__
+    __graft_entry__.build()
+    devs, parts = _devices(11, 9, 1, 30, 3)
+    Y, msgs, first, n2, s, R, ds = parts[4]
+    s = list(s)
+    s[0] = O.scalar_to_bytes(int.from_bytes(s[0], "little") + 9)
+    s[-1] = O.scalar_to_bytes(int.from_bytes(s[-1], "little") - 9)
+    parts[4] = (Y, msgs, first, n2, s, R, ds)
+    d = devs[4]
+    devs[4] = (d[0], d[1], d[2], d[3], s, d[5], d[6])
+    cat, sb, Rb = _concat(parts)
+    want_acc, want_pairs = O.verify_multi(devs)
+    with poslo.Context(device=0, verifier_seed=synth.verifier_seed(11)) as cx:
+        cx.set_multi_window_limit(limit)
+        for _ in range(2):
+            acc, pairs = cx.aver_multi([p[0] for p in parts], [p[1].n for p in parts], [p[2] for p in parts],
+                                       [p[3] for p in parts], [p[6] for p in parts], cat.data, cat.offs, sb, Rb)
+            assert list(acc) == want_acc
+            assert [tuple(int(x) for x in p) for p in pairs] == want_pairs
+    assert want_acc.count(False) >= 2
