@@ -393,6 +393,19 @@ int poslo_set_graphs(poslo_ctx* ctx, int enabled);
  * weights, where the per-device, per-window scalar sums cost more than those doublings.
  * Results are the same either way.  EINVAL for a null context. */
 int poslo_set_multi_window_limit(poslo_ctx* ctx, uint64_t max_entries);
+
+/* Key cache (no counterpart in the paper).  poslo_distill and poslo_aver_multi (without
+ * resident tables) need the fixed-window table of every public key they check, whose
+ * construction is a chain of 252 dependent point doublings (about 0.3 ms, however many keys
+ * are built at once).  The context keeps the tables of the `capacity` most recently used keys
+ * (64 KiB each, device memory allocated in blocks of 256 keys, counted against
+ * poslo_params.mem_budget; default 4,096 keys) and builds only the keys it misses.  A key
+ * whose encoding does not decode, or whose call fails, is not kept.  A call with more keys
+ * than the capacity builds all of its tables without the cache.  poslo_set_key_cache drops
+ * every cached table and sets the capacity (0 turns the cache off); poslo_key_cache_stats
+ * counts lookups that hit and missed.  EINVAL for a null context. */
+int poslo_set_key_cache(poslo_ctx* ctx, uint32_t capacity);
+int poslo_key_cache_stats(poslo_ctx* ctx, uint64_t* hits, uint64_t* misses);
 int poslo_graph_stats(poslo_ctx* ctx, uint64_t* captures, uint64_t* replays);
 
 #ifdef __cplusplus

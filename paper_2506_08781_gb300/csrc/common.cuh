@@ -241,9 +241,11 @@ struct PointArgs {
   uint32_t* pts_out;      // optional: count*24 words (x, y, 2d x y) of decoded points
   uint8_t* bad_out;       // optional: count bytes, 1 = undecodable
   const uint8_t* skip;    // optional: count bytes, 1 = leave the point out of the sum
+  uint32_t* work;         // chunk counter, zero at launch: blocks take kPointChunk points at a time
 };
 
 constexpr int kPtsWords = 24;   // stored decoded point: x, y, t2d = 2d x y (8 words each)
+constexpr uint32_t kPointChunk = 512;
 
 constexpr int kPointPartialWords = 33;
 
@@ -626,12 +628,15 @@ void launch_hash(int inst, unsigned grid, cudaStream_t st, const HashArgs& a);
 struct ZPre { uint32_t w[10]; };   // BE words of "POSLO-Z" || verifier_seed || (byte 39 = 0)
 __global__ void k_weights(const ZPre zp, uint64_t n, uint64_t first, uint32_t* z_out);
 __global__ void __launch_bounds__(kPointThreads) k_points(const PointArgs a);
+// (Key k's table is dst[k] when a destination list is given -- tables scattered over a
+// cache -- else tables + k kTableWords.)
 __global__ void __launch_bounds__(128) k_table_chain(const uint32_t* __restrict__ enc,
                                                      const uint32_t* __restrict__ pts,
                                                      const uint32_t* __restrict__ list, uint32_t n,
-                                                     uint32_t* __restrict__ tables, uint32_t* __restrict__ status,
-                                                     int use_base, uint8_t* __restrict__ bad_out);
-__global__ void __launch_bounds__(128) k_table_fill(uint32_t n, uint32_t* __restrict__ tables);
+                                                     uint32_t* __restrict__ tables, uint32_t* const* dst,
+                                                     uint32_t* __restrict__ status, int use_base,
+                                                     uint8_t* __restrict__ bad_out);
+__global__ void __launch_bounds__(128) k_table_fill(uint32_t n, uint32_t* __restrict__ tables, uint32_t* const* dst);
 __global__ void __launch_bounds__(kFinalThreads) k_finalize(const FinalArgs a);
 __global__ void __launch_bounds__(128) k_final_prep(const PrepArgs a);
 __global__ void k_final_check(const uint32_t* prep, const uint32_t* R, const uint32_t* point_bad,

@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cstddef>
 #include <functional>
+#include <array>
+#include <list>
 #include <map>
 #include <string>
 #include <vector>
@@ -24,6 +26,22 @@ struct KernelTimer {
 };
 
 struct Server;   // continuous-batching service (serve.cu)
+
+// Window tables of recently used public keys, kept on the device so that a later call with
+// the same key skips the 252-doubling table chain.  Slots live in blocks of kBlock keys that
+// never move; least recently used keys are evicted.
+struct KeyCache {
+  static constexpr uint32_t kBlock = 256;
+  uint32_t capacity = 4096;                          // keys (0: no cache)
+  std::vector<uint32_t*> blocks;                     // kBlock tables each
+  std::map<std::array<uint8_t, 32>, uint32_t> slot_of;
+  std::vector<std::array<uint8_t, 32>> key_of;       // slot -> key
+  std::list<uint32_t> lru;                           // slots in use, most recent first
+  std::vector<std::list<uint32_t>::iterator> pos;    // slot -> its place in lru
+  std::vector<uint32_t> free_slots;
+  uint32_t nslots = 0;                               // slots handed out so far
+  uint64_t hits = 0, misses = 0;
+};
 
 // A captured launch sequence (CUDA graph) and the shape of the call it was captured from.
 // A call whose shape equals the previous call's is captured; later calls of that shape
@@ -72,6 +90,7 @@ struct poslo_ctx {
   uint64_t graph_captures = 0, graph_replays = 0;
   poslo_host::GraphSlot g_multi;  // poslo_aver_multi up to its combined check
   poslo_host::GraphSlot g_distill;   // poslo_distill up to its weighted check
+  poslo_host::KeyCache keys;         // window tables of recently used keys
 };
 
 // Stops and frees the context's service, if one runs (serve.cu).

@@ -287,30 +287,55 @@ __global__ void __launch_bounds__(kHashThreads, POSLO_HASH_MIN_BLOCKS) k_hash(co
   }
 }
 
+#ifndef POSLO_POINTS_DYNAMIC
+#define POSLO_POINTS_DYNAMIC 1
+#endif
+
+// Strict decoding of R_t, its affine form for the MSM and its decode flag, and its addition
+// into the thread's unit sum.
+__device__ __forceinline__ void decode_one(const PointArgs& a, uint64_t t, ge& acc, uint32_t& bad) {
+  const uint4* rp = reinterpret_cast<const uint4*>(a.R + 32 * t);
+  const uint4 r0 = __ldg(rp), r1 = __ldg(rp + 1);
+  const uint32_t b[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+  ge P;
+  const bool ok = ge_decode(b, P);
+  bad += ok ? 0u : 1u;
+  if (a.bad_out) a.bad_out[t] = ok ? 0 : 1;
+  const fe t2d = fe_mul(P.T, fe_d2());
+  if (a.pts_out) {
+    uint4* dst = reinterpret_cast<uint4*>(a.pts_out + (size_t)kPtsWords * t);
+    dst[0] = make_uint4(P.X.v[0], P.X.v[1], P.X.v[2], P.X.v[3]);
+    dst[1] = make_uint4(P.X.v[4], P.X.v[5], P.X.v[6], P.X.v[7]);
+    dst[2] = make_uint4(P.Y.v[0], P.Y.v[1], P.Y.v[2], P.Y.v[3]);
+    dst[3] = make_uint4(P.Y.v[4], P.Y.v[5], P.Y.v[6], P.Y.v[7]);
+    dst[4] = make_uint4(t2d.v[0], t2d.v[1], t2d.v[2], t2d.v[3]);
+    dst[5] = make_uint4(t2d.v[4], t2d.v[5], t2d.v[6], t2d.v[7]);
+  }
+  if (ok && !(a.skip && a.skip[t])) acc = ge_madd(acc, P.X, P.Y, t2d);
+}
+
+// Every R_t: blocks take chunks of kPointChunk points from a shared counter, so a block that
+// starts late (its SM busy with the hashing beside it) simply takes fewer chunks; then the
+// block's unit sum and decode-failure count.
 __global__ void __launch_bounds__(kPointThreads) k_points(const PointArgs a) {
   ge acc = ge_identity();
   uint32_t bad = 0;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.count; t += stride) {
-    const uint4* rp = reinterpret_cast<const uint4*>(a.R + 32 * t);
-    const uint4 r0 = __ldg(rp), r1 = __ldg(rp + 1);
-    const uint32_t b[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
-    ge P;
-    const bool ok = ge_decode(b, P);
-    bad += ok ? 0u : 1u;
-    if (a.bad_out) a.bad_out[t] = ok ? 0 : 1;
-    const fe t2d = fe_mul(P.T, fe_d2());
-    if (a.pts_out) {
-      uint4* dst = reinterpret_cast<uint4*>(a.pts_out + (size_t)kPtsWords * t);
-      dst[0] = make_uint4(P.X.v[0], P.X.v[1], P.X.v[2], P.X.v[3]);
-      dst[1] = make_uint4(P.X.v[4], P.X.v[5], P.X.v[6], P.X.v[7]);
-      dst[2] = make_uint4(P.Y.v[0], P.Y.v[1], P.Y.v[2], P.Y.v[3]);
-      dst[3] = make_uint4(P.Y.v[4], P.Y.v[5], P.Y.v[6], P.Y.v[7]);
-      dst[4] = make_uint4(t2d.v[0], t2d.v[1], t2d.v[2], t2d.v[3]);
-      dst[5] = make_uint4(t2d.v[4], t2d.v[5], t2d.v[6], t2d.v[7]);
-    }
-    if (ok && !(a.skip && a.skip[t])) acc = ge_madd(acc, P.X, P.Y, t2d);
+#if POSLO_POINTS_DYNAMIC
+  __shared__ uint64_t s_base;
+  for (;;) {
+    if (threadIdx.x == 0) s_base = (uint64_t)atomicAdd(a.work, 1u) * kPointChunk;
+    __syncthreads();
+    const uint64_t base = s_base;
+    __syncthreads();
+    if (base >= a.count) break;
+    const uint64_t end = min(base + kPointChunk, a.count);
+    for (uint64_t t = base + threadIdx.x; t < end; t += blockDim.x) decode_one(a, t, acc, bad);
   }
+#else
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.count; t += stride)
+    decode_one(a, t, acc, bad);
+#endif
   // tree reduction in shared memory
   __shared__ uint32_t sp[kPointThreads][32];
   __shared__ uint32_t sbad[kPointThreads];
@@ -341,8 +366,9 @@ __global__ void __launch_bounds__(kPointThreads) k_points(const PointArgs a) {
 __global__ void __launch_bounds__(128) k_table_chain(const uint32_t* __restrict__ enc,
                                                      const uint32_t* __restrict__ pts,
                                                      const uint32_t* __restrict__ list, uint32_t n,
-                                                     uint32_t* __restrict__ tables, uint32_t* __restrict__ status,
-                                                     int use_base, uint8_t* __restrict__ bad_out) {
+                                                     uint32_t* __restrict__ tables, uint32_t* const* dst,
+                                                     uint32_t* __restrict__ status, int use_base,
+                                                     uint8_t* __restrict__ bad_out) {
   const uint32_t quad = ((uint32_t)blockIdx.x * blockDim.x + threadIdx.x) >> 2;
   const uint32_t k = quad < n ? quad : n - 1;   // surplus quads repeat the last key, unwritten
   const bool writer = quad < n && (threadIdx.x & 3) == 0;
@@ -365,7 +391,7 @@ __global__ void __launch_bounds__(128) k_table_chain(const uint32_t* __restrict_
       else if (!ok) atomicOr(status, kErrKey);
     }
   }
-  uint32_t* table = tables + (size_t)k * kTableWords;
+  uint32_t* table = dst ? dst[k] : tables + (size_t)k * kTableWords;
   // every lane runs every quad doubling (full-mask shuffles)
   for (int w = 0; w < kTableWindows; ++w) {
     if (writer) ge_store(table + (size_t)w * kTableDigits * 32, P);
@@ -374,12 +400,13 @@ __global__ void __launch_bounds__(128) k_table_chain(const uint32_t* __restrict_
   }
 }
 
-__global__ void __launch_bounds__(128) k_table_fill(uint32_t n, uint32_t* __restrict__ tables) {
+__global__ void __launch_bounds__(128) k_table_fill(uint32_t n, uint32_t* __restrict__ tables, uint32_t* const* dst) {
   const uint64_t total = (uint64_t)n * kTableWindows;
   const uint64_t quad = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 2;
   const uint64_t q = quad < total ? quad : total - 1;
   const bool writer = quad < total && (threadIdx.x & 3) == 0;
-  uint32_t* row = tables + (q / kTableWindows) * kTableWords + (q % kTableWindows) * kTableDigits * 32;
+  const uint64_t key = q / kTableWindows;
+  uint32_t* row = (dst ? dst[key] : tables + key * kTableWords) + (q % kTableWindows) * kTableDigits * 32;
   const ge Pw = ge_load(row);
   ge acc = Pw;
   for (int d = 2; d <= kTableDigits; ++d) {

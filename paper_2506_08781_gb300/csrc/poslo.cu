@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -399,15 +400,107 @@ int run_hash(poslo_ctx* ctx, const poslo_batch* b, const Staged& sb, uint8_t* e_
 // Window table of Y on the side stream (ordered after the main stream's uploads).
 // Window tables of n keys on stream st (k_table_chain, then k_table_fill).
 int launch_tables(poslo_ctx* ctx, cudaStream_t st, const uint32_t* enc, const uint32_t* pts, const uint32_t* list,
-                  uint32_t n, uint32_t* tables, int use_base, uint8_t* bad_out) {
+                  uint32_t n, uint32_t* tables, int use_base, uint8_t* bad_out, uint32_t* const* dst = nullptr) {
   if (n == 0) return POSLO_OK;
-  k_table_chain<<<(unsigned)((4ull * n + 127) / 128), 128, 0, st>>>(enc, pts, list, n, tables, ctx->status, use_base,
-                                                                    bad_out);
-  k_table_fill<<<(unsigned)((4ull * n * kTableWindows + 127) / 128), 128, 0, st>>>(n, tables);
+  k_table_chain<<<(unsigned)((4ull * n + 127) / 128), 128, 0, st>>>(enc, pts, list, n, tables, dst, ctx->status,
+                                                                    use_base, bad_out);
+  k_table_fill<<<(unsigned)((4ull * n * kTableWindows + 127) / 128), 128, 0, st>>>(n, tables, dst);
   ctx->launch_count += 2;
   CU(cudaGetLastError());
   return POSLO_OK;
 }
+
+// ---- key cache ----
+uint32_t* key_slot_table(const poslo_host::KeyCache& C, uint32_t slot) {
+  return C.blocks[slot / poslo_host::KeyCache::kBlock] + (size_t)(slot % poslo_host::KeyCache::kBlock) * kTableWords;
+}
+
+// Window tables of nd keys (host encodings, 32 bytes each) from the context's key cache:
+// tabs[d] is key d's table.  Keys not cached get a slot -- a free one, else the least
+// recently used -- and are listed in miss (their index d) and miss_dst (their table) for the
+// caller to build.  Returns false, leaving the cache untouched, when the cache is off, holds
+// fewer slots than the call has keys, or cannot grow within the memory budget.
+bool key_cache_lookup(poslo_ctx* ctx, const uint8_t* Y, uint32_t nd, std::vector<const uint32_t*>& tabs,
+                      std::vector<uint32_t>& miss, std::vector<uint32_t*>& miss_dst) {
+  poslo_host::KeyCache& C = ctx->keys;
+  if (C.capacity == 0 || C.capacity < nd) return false;
+  // grow the slot blocks first, so that no key is assigned a slot the cache then cannot hold
+  const uint32_t want = std::min(C.capacity, std::max(C.nslots, nd + C.nslots - (uint32_t)C.free_slots.size()));
+  while ((size_t)C.blocks.size() * poslo_host::KeyCache::kBlock < want) {
+    const size_t bytes = (size_t)poslo_host::KeyCache::kBlock * kTableWords * 4;
+    if (ctx->mem_budget && ctx->mem_used + bytes > ctx->mem_budget) return false;
+    uint32_t* b = nullptr;
+    if (cudaMalloc(&b, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    ctx->mem_used += bytes;
+    C.blocks.push_back(b);
+  }
+  tabs.assign(nd, nullptr);
+  miss.clear();
+  miss_dst.clear();
+  for (uint32_t d = 0; d < nd; ++d) {
+    std::array<uint8_t, 32> k;
+    memcpy(k.data(), Y + 32 * (size_t)d, 32);
+    uint32_t slot;
+    auto it = C.slot_of.find(k);
+    if (it != C.slot_of.end()) {
+      slot = it->second;
+      C.lru.splice(C.lru.begin(), C.lru, C.pos[slot]);
+      ++C.hits;
+    } else {
+      ++C.misses;
+      if (!C.free_slots.empty()) {
+        slot = C.free_slots.back();
+        C.free_slots.pop_back();
+      } else if (C.nslots < C.capacity && C.nslots < (uint32_t)C.blocks.size() * poslo_host::KeyCache::kBlock) {
+        slot = C.nslots++;
+        C.key_of.resize(C.nslots);
+        C.pos.resize(C.nslots);
+      } else {   // evict the least recently used key (never one of this call: nd <= capacity)
+        slot = C.lru.back();
+        C.lru.pop_back();
+        C.slot_of.erase(C.key_of[slot]);
+      }
+      C.key_of[slot] = k;
+      C.slot_of[k] = slot;
+      C.lru.push_front(slot);
+      C.pos[slot] = C.lru.begin();
+      miss.push_back(d);
+      miss_dst.push_back(key_slot_table(C, slot));
+    }
+    tabs[d] = key_slot_table(C, slot);
+  }
+  return true;
+}
+
+// Drops a key from the cache (its table was built from an encoding that does not decode, or
+// the call that built it failed).
+void key_cache_forget(poslo_ctx* ctx, const uint8_t* Y32) {
+  poslo_host::KeyCache& C = ctx->keys;
+  std::array<uint8_t, 32> k;
+  memcpy(k.data(), Y32, 32);
+  auto it = C.slot_of.find(k);
+  if (it == C.slot_of.end()) return;
+  const uint32_t slot = it->second;
+  C.lru.erase(C.pos[slot]);
+  C.slot_of.erase(it);
+  C.free_slots.push_back(slot);
+}
+
+// Until a call has built them, the key cache must not keep the tables of the keys it missed:
+// on any early return they are dropped again (armed until the build is known sound).
+struct KeyForget {
+  poslo_ctx* ctx;
+  const uint8_t* Y;                      // the call's key encodings
+  const std::vector<uint32_t>* miss;     // indices of the missed keys
+  bool armed;
+  ~KeyForget() {
+    if (armed)
+      for (uint32_t k : *miss) key_cache_forget(ctx, Y + 32 * (size_t)k);
+  }
+};
 
 int run_ytable(poslo_ctx* ctx, const uint8_t* Y, uint32_t** table_out) {
   int rc;
@@ -446,12 +539,16 @@ int run_points(poslo_ctx* ctx, const uint8_t* R, uint64_t count, uint32_t* pts_o
     after = ctx->ev_main;
   }
   CU(cudaStreamWaitEvent(ctx->s_points, after, 0));
+  uint32_t* work;
+  if ((rc = ensure_t(ctx, "point_work", 16, &work))) return rc;
   PointArgs a{};
   a.R = R;
   a.count = count;
   a.partial = partial;
   a.pts_out = pts_out;
   a.bad_out = bad_out;
+  a.work = work;
+  CU(cudaMemsetAsync(work, 0, 4, ctx->s_points));
   cudaEvent_t tb, te;
   timer_begin(ctx, "points", ctx->s_points, &tb, &te);
   k_points<<<blocks, kPointThreads, 0, ctx->s_points>>>(a);
@@ -843,6 +940,7 @@ void poslo_destroy(poslo_ctx* ctx) {
   if (ctx->s_points) cudaStreamSynchronize(ctx->s_points);
   graph_reset(ctx->g_multi);
   graph_reset(ctx->g_distill);
+  for (uint32_t* b : ctx->keys.blocks) cudaFree(b);
   for (auto& kv : ctx->bufs)
     if (kv.second.p) cudaFree(kv.second.p);
   for (auto& p : ctx->pending) {
@@ -877,6 +975,31 @@ void* poslo_stream(poslo_ctx* ctx) { return ctx ? (void*)ctx->s_main : nullptr; 
 int poslo_set_profiling(poslo_ctx* ctx, int enabled) {
   if (!ctx) return POSLO_EINVAL;
   ctx->profiling = enabled != 0;
+  return POSLO_OK;
+}
+
+int poslo_set_key_cache(poslo_ctx* ctx, uint32_t capacity) {
+  if (!ctx) return POSLO_EINVAL;
+  poslo_host::KeyCache& C = ctx->keys;
+  cudaStreamSynchronize(ctx->s_main);
+  cudaStreamSynchronize(ctx->s_table);
+  graph_reset(ctx->g_distill);   // it may hold a cached table's address
+  for (uint32_t* b : C.blocks) {
+    cudaFree(b);
+    ctx->mem_used -= (size_t)poslo_host::KeyCache::kBlock * kTableWords * 4;
+  }
+  const uint64_t hits = C.hits, misses = C.misses;
+  C = poslo_host::KeyCache();
+  C.capacity = capacity;
+  C.hits = hits;
+  C.misses = misses;
+  return POSLO_OK;
+}
+
+int poslo_key_cache_stats(poslo_ctx* ctx, uint64_t* hits, uint64_t* misses) {
+  if (!ctx) return POSLO_EINVAL;
+  if (hits) *hits = ctx->keys.hits;
+  if (misses) *misses = ctx->keys.misses;
   return POSLO_OK;
 }
 
@@ -1247,11 +1370,25 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
   if ((rc = reset_status(ctx))) return rc;
   Staged sb;
   if ((rc = stage_batch(ctx, batch, sb))) return rc;
-  // uploads: the key's encoding and the disclosed seeds
+  // uploads: the key's encoding and the disclosed seeds; the key's window table comes from the
+  // key cache (built only when the key is not cached)
   uint32_t *d_Y, *tableY;
+  uint32_t** d_ydst;
   if ((rc = ensure_t(ctx, "Y", 32, &d_Y))) return rc;
-  if ((rc = ensure_t(ctx, "tableY", 4 * (size_t)kTableWords, &tableY))) return rc;
+  if ((rc = ensure_t(ctx, "ydst", 8, &d_ydst))) return rc;
   CU(cudaMemcpyAsync(d_Y, batch->Y, 32, cudaMemcpyHostToDevice, ctx->s_main));
+  std::vector<const uint32_t*> ktab;
+  std::vector<uint32_t> kmiss;
+  std::vector<uint32_t*> kdst;
+  const bool kcached = key_cache_lookup(ctx, batch->Y, 1, ktab, kmiss, kdst);
+  const bool kbuild = !kcached || !kmiss.empty();
+  KeyForget kforget{ctx, batch->Y, &kmiss, kcached && kbuild};
+  if (kcached) {
+    tableY = const_cast<uint32_t*>(ktab[0]);
+    if (kbuild) CU(cudaMemcpyAsync(d_ydst, kdst.data(), 8, cudaMemcpyHostToDevice, ctx->s_main));
+  } else if ((rc = ensure_t(ctx, "tableY", 4 * (size_t)kTableWords, &tableY))) {
+    return rc;
+  }
   std::vector<DsNode> ds_nodes;
   if ((rc = parse_ds(ctx, batch->ds, batch->ds_nodes, ds_nodes))) return rc;
   DsNode* d_ds;
@@ -1289,15 +1426,19 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
   const bool replayable = batch->on_device != 0;
   auto stage1 = [&]() -> int {
     int rc;
-    // window table of Y (table stream)
-    CU(cudaEventRecord(ctx->ev_main, ctx->s_main));
-    CU(cudaStreamWaitEvent(ctx->s_table, ctx->ev_main, 0));
-    {
+    // window table of Y (table stream), unless cached
+    if (kbuild) {
+      CU(cudaEventRecord(ctx->ev_main, ctx->s_main));
+      CU(cudaStreamWaitEvent(ctx->s_table, ctx->ev_main, 0));
       cudaEvent_t tb, te;
       timer_begin(ctx, "table", ctx->s_table, &tb, &te);
-      if ((rc = launch_tables(ctx, ctx->s_table, d_Y, nullptr, nullptr, 1, tableY, 0, nullptr))) return rc;
+      if ((rc = launch_tables(ctx, ctx->s_table, d_Y, nullptr, nullptr, 1, kcached ? nullptr : tableY, 0, nullptr,
+                              kcached ? d_ydst : nullptr)))
+        return rc;
       timer_end(ctx, "table", ctx->s_table, tb, te);
       CU(cudaEventRecord(ctx->ev_table, ctx->s_table));
+    } else {
+      CU(cudaEventRecord(ctx->ev_table, ctx->s_main));
     }
     // decoding (points stream), from the moment the R_t have landed; then the speculative
     // ccd^v of the all-valid case (its R part)
@@ -1375,14 +1516,19 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
     const std::vector<uint64_t> sig = {n, batch->n2, batch->first_index, reinterpret_cast<uint64_t>(sb.msgs),
                                        reinterpret_cast<uint64_t>(sb.offs), reinterpret_cast<uint64_t>(sb.s),
                                        reinterpret_cast<uint64_t>(sb.R), sb.base_off, ds_nodes.size(),
-                                       (uint64_t)plan.c, (uint64_t)plan.seg_log2, ctx->inst};
-    if ((rc = run_replayable(ctx, ctx->g_distill, sig, stage1))) return rc;
-  } else if ((rc = stage1())) {
-    return rc;
+                                       (uint64_t)plan.c, (uint64_t)plan.seg_log2, ctx->inst,
+                                       reinterpret_cast<uint64_t>(tableY), kbuild ? 1u : 0u};
+    rc = run_replayable(ctx, ctx->g_distill, sig, stage1);
+  } else {
+    rc = stage1();
   }
   uint8_t h_acc = 0;
-  CU(cudaMemcpyAsync(&h_acc, d_acc, 1, cudaMemcpyDeviceToHost, ctx->s_main));
-  if ((rc = check_status(ctx))) return rc;   // synchronises: h_acc is ready
+  if (rc == POSLO_OK) {
+    CU(cudaMemcpyAsync(&h_acc, d_acc, 1, cudaMemcpyDeviceToHost, ctx->s_main));
+    rc = check_status(ctx);   // synchronises: h_acc is ready
+  }
+  if (rc != POSLO_OK) return rc;
+  kforget.armed = false;   // the key decoded: its table is sound
   // h_acc covers "no malformed entry and the weighted equation holds"
   uint64_t* d_idx;
   const uint64_t capn = std::max<uint64_t>(std::min(cap, n), 1);
@@ -2025,8 +2171,31 @@ int poslo_host::aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, const ui
   if ((rc = ensure_t(ctx, "m_badY", nd, &badY))) return rc;
   if ((rc = ensure_t(ctx, "m_tabs", 8 * (size_t)nd, &d_tabs))) return rc;
   std::vector<const uint32_t*> tabs(nd);
+  // without resident tables: the context's key cache, building only the keys it misses (their
+  // encodings gathered into m_Ymiss, destinations in m_mdst, decode flags in m_mbad); a
+  // cache too small for the call builds every table into m_tablesY
+  std::vector<uint32_t> kmiss;
+  std::vector<uint32_t*> kdst;
+  bool kcached = false;
+  uint32_t nbuild = 0;
+  uint32_t* d_Ymiss = nullptr;
+  uint32_t** d_mdst = nullptr;
+  uint8_t* d_mbad = nullptr;
+  KeyForget forget{ctx, mb->Y, &kmiss, false};
   if (key_tables) {
     for (uint32_t d = 0; d < nd; ++d) tabs[d] = key_tables[d];
+  } else if ((kcached = key_cache_lookup(ctx, mb->Y, nd, tabs, kmiss, kdst))) {
+    forget.armed = !kmiss.empty();
+    nbuild = (uint32_t)kmiss.size();
+    if (nbuild) {
+      std::vector<uint8_t> ym(32 * (size_t)nbuild);
+      for (uint32_t k = 0; k < nbuild; ++k) memcpy(ym.data() + 32 * (size_t)k, mb->Y + 32 * (size_t)kmiss[k], 32);
+      if ((rc = ensure_t(ctx, "m_Ymiss", ym.size(), &d_Ymiss))) return rc;
+      if ((rc = ensure_t(ctx, "m_mdst", 8 * (size_t)nbuild, &d_mdst))) return rc;
+      if ((rc = ensure_t(ctx, "m_mbad", nbuild, &d_mbad))) return rc;
+      CU(cudaMemcpyAsync(d_Ymiss, ym.data(), ym.size(), cudaMemcpyHostToDevice, ctx->s_main));
+      CU(cudaMemcpyAsync(d_mdst, kdst.data(), 8 * (size_t)nbuild, cudaMemcpyHostToDevice, ctx->s_main));
+    }
   } else {
     if ((rc = ensure_t(ctx, "m_tablesY", 4 * (size_t)kTableWords * nd, &tablesY))) return rc;
     for (uint32_t d = 0; d < nd; ++d) tabs[d] = tablesY + (size_t)d * kTableWords;
@@ -2082,16 +2251,26 @@ int poslo_host::aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, const ui
                                reinterpret_cast<uint64_t>(sb.msgs), reinterpret_cast<uint64_t>(sb.offs),
                                reinterpret_cast<uint64_t>(sb.s), reinterpret_cast<uint64_t>(sb.R),
                                nodes.size(), (uint64_t)plan.c, (uint64_t)plan.seg_log2, ctx->inst,
-                               per_window ? 1u : 0u};
+                               per_window ? 1u : 0u, kcached ? 1u : 0u, nbuild};
   sig.insert(sig.end(), mb->dev_start, mb->dev_start + nd + 1);
   sig.insert(sig.end(), mb->first_index, mb->first_index + nd);
   sig.insert(sig.end(), mb->n2, mb->n2 + nd);
   sig.insert(sig.end(), mb->ds_off, mb->ds_off + nd + 1);
   auto stage1 = [&]() -> int {
     int rc;
-    if (key_tables) {
+    if (key_tables || (kcached && nbuild == 0)) {
       CU(cudaMemsetAsync(badY, 0, nd, ctx->s_main));
       CU(cudaEventRecord(ctx->ev_table, ctx->s_main));
+    } else if (kcached) {
+      CU(cudaMemsetAsync(badY, 0, nd, ctx->s_main));
+      CU(cudaEventRecord(ctx->ev_main, ctx->s_main));
+      CU(cudaStreamWaitEvent(ctx->s_table, ctx->ev_main, 0));
+      cudaEvent_t tb, te;
+      timer_begin(ctx, "table", ctx->s_table, &tb, &te);
+      if ((rc = launch_tables(ctx, ctx->s_table, d_Ymiss, nullptr, nullptr, nbuild, nullptr, 0, d_mbad, d_mdst)))
+        return rc;
+      timer_end(ctx, "table", ctx->s_table, tb, te);
+      CU(cudaEventRecord(ctx->ev_table, ctx->s_table));
     } else {
       CU(cudaEventRecord(ctx->ev_main, ctx->s_main));
       CU(cudaStreamWaitEvent(ctx->s_table, ctx->ev_main, 0));
@@ -2207,9 +2386,14 @@ int poslo_host::aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, const ui
   CU(cudaMemcpyAsync(&all_ok, d_acc, 1, cudaMemcpyDeviceToHost, ctx->s_main));
   CU(cudaMemcpyAsync(bad.data(), ss.bad, 4 * (size_t)nd, cudaMemcpyDeviceToHost, ctx->s_main));
   CU(cudaMemcpyAsync(hbadY.data(), badY, nd, cudaMemcpyDeviceToHost, ctx->s_main));
+  std::vector<uint8_t> hmbad(nbuild);
+  if (nbuild) CU(cudaMemcpyAsync(hmbad.data(), d_mbad, nbuild, cudaMemcpyDeviceToHost, ctx->s_main));
   if ((rc = check_status(ctx))) return rc;
+  for (uint32_t k = 0; k < nbuild; ++k)
+    if (hmbad[k]) hbadY[kmiss[k]] = 1;
   for (uint32_t d = 0; d < nd; ++d)
     if (hbadY[d]) return fail(ctx, POSLO_EINVAL, "public key of device %u does not decode", d);
+  forget.armed = false;   // the built tables are sound
   uint64_t total_bad = 0;
   for (uint32_t d = 0; d < nd; ++d) total_bad += bad[d];
   std::vector<uint8_t> flag(nd, 0);

@@ -30,7 +30,7 @@ EXPORTS = [
     "poslo_aver", "poslo_distill", "poslo_epoch_seeds", "poslo_hash_entries", "poslo_msm", "poslo_msm_autotune",
     "poslo_msm_get_plan", "poslo_msm_set_plan",
     "poslo_set_profiling", "poslo_kernel_time", "poslo_reset_kernel_times", "poslo_set_graphs", "poslo_graph_stats",
-    "poslo_set_multi_window_limit",
+    "poslo_set_multi_window_limit", "poslo_set_key_cache", "poslo_key_cache_stats",
     "poslo_hash_entries_noalloc", "poslo_aver_multi", "poslo_distill_c", "poslo_sebver_c", "poslo_distill_stream",
     "poslo_serve_start", "poslo_serve_stop", "poslo_register_key", "poslo_submit", "poslo_poll",
     "poslo_serve_stats",
@@ -111,6 +111,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "poslo_set_profiling": ([vp, C.c_int], C.c_int),
         "poslo_set_graphs": ([vp, C.c_int], C.c_int),
         "poslo_set_multi_window_limit": ([vp, u64], C.c_int),
+        "poslo_set_key_cache": ([vp, u32], C.c_int),
+        "poslo_key_cache_stats": ([vp, C.POINTER(u64), C.POINTER(u64)], C.c_int),
         "poslo_graph_stats": ([vp, C.POINTER(u64), C.POINTER(u64)], C.c_int),
         "poslo_kernel_time": ([vp, C.c_char_p, C.POINTER(C.c_double), C.POINTER(u64)], C.c_int),
         "poslo_reset_kernel_times": ([vp], None),
@@ -497,6 +499,16 @@ class Context:
     def set_multi_window_limit(self, max_entries: int):
         """Multi-device batches up to max_entries check window by window (default 2^21)."""
         self._check(self.lib.poslo_set_multi_window_limit(self.h, max_entries))
+
+    def set_key_cache(self, capacity: int):
+        """Drop every cached key table and keep at most `capacity` keys' tables (0: off)."""
+        self._check(self.lib.poslo_set_key_cache(self.h, capacity))
+
+    def key_cache_stats(self):
+        """(hits, misses) of the key-table cache."""
+        h, m = C.c_uint64(0), C.c_uint64(0)
+        self._check(self.lib.poslo_key_cache_stats(self.h, C.byref(h), C.byref(m)))
+        return int(h.value), int(m.value)
 
     def graph_stats(self):
         """(graphs captured, replays run) on this context."""

@@ -146,7 +146,8 @@ def test_multi_graph_replay_reads_each_calls_inputs(on_device):
             d_s = torch.from_numpy(np.frombuffer(s, np.uint8).copy()).cuda()
             d_R = torch.from_numpy(np.frombuffer(R, np.uint8).copy()).cuda()
         # trial 1's data first: the localisation of a failing call grows its own workspace
-        # once, which would invalidate a graph captured before it
+        # once, which would invalidate a graph captured before it; that first call also builds
+        # the key tables (a shape of its own), so the second call of the cached shape captures
         for trial in [1] + list(range(5)):
             data = cat.data
             want_devs = [tuple(d) for d in devs]
@@ -169,7 +170,7 @@ def test_multi_graph_replay_reads_each_calls_inputs(on_device):
             assert list(acc) == want_acc, trial
             assert [tuple(int(x) for x in p) for p in pairs] == want_pairs, trial
         captures, replays = cx.graph_stats()
-        assert captures == 1 and replays == 4
+        assert captures == 1 and replays == 3
         # a larger call in between regrows the workspace: the next call of the first shape
         # must not replay the stale graph
         devs2, parts2 = _devices(8, 9, 30, 60, 1)
@@ -185,7 +186,7 @@ def test_multi_graph_replay_reads_each_calls_inputs(on_device):
         else:
             acc, pairs = cx.aver_multi(*args, cat.data, cat.offs, s, R)
         assert list(acc) == [True] * len(parts) and len(pairs) == 0
-        assert cx.graph_stats()[1] == 4
+        assert cx.graph_stats()[1] == 3
 
 
 def test_multi_graphs_off_same_results():
