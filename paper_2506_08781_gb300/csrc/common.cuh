@@ -706,19 +706,23 @@ void launch_epoch_seeds_multi(int inst, unsigned grid, unsigned block, cudaStrea
                               uint32_t* seeds, uint32_t* status);
 __global__ void k_rebase_offs(const uint64_t* raw, const uint64_t* slot, const uint64_t* start,
                               const uint64_t* msg_base, uint32_t n_dev, uint64_t* out, uint32_t* status);
-__global__ void __launch_bounds__(256) k_segment_sums(const uint8_t* e, const uint8_t* s, const uint32_t* z,
+#ifndef POSLO_SEG_THREADS
+#define POSLO_SEG_THREADS 128
+#endif
+constexpr int kSegThreads = POSLO_SEG_THREADS;   // threads per device block of the segment sums
+__global__ void __launch_bounds__(kSegThreads) k_segment_sums(const uint8_t* e, const uint8_t* s, const uint32_t* z,
                                                       const uint32_t* pts, const uint8_t* badR, const uint8_t* badS,
-                                                      const uint64_t* start, SegSums out);
+                                                      const uint64_t* start, const uint64_t* order, SegSums out);
 __global__ void __launch_bounds__(kFinalThreads) k_multi_check(const uint32_t* P1, const uint32_t* P1sub, const uint32_t* P2,
                                                                const uint32_t* Sw, const uint8_t* dev_flag,
                                                                uint32_t n_dev, const uint32_t* tableG,
                                                                uint8_t* accept);
 __global__ void __launch_bounds__(kPointThreads) k_table_msm(const uint32_t* const* tabs, const uint32_t* k,
                                                              const uint8_t* skip, uint32_t n, uint32_t* partial);
-__global__ void __launch_bounds__(256) k_segment_window_sums(const uint8_t* e, const uint8_t* s, const uint32_t* z,
+__global__ void __launch_bounds__(kSegThreads) k_segment_window_sums(const uint8_t* e, const uint8_t* s, const uint32_t* z,
                                                              const uint8_t* badR, const uint8_t* badS,
-                                                             const uint64_t* start, uint32_t n_dev, MsmPlan pl,
-                                                             uint32_t* Ewd, uint32_t* Swd);
+                                                             const uint64_t* start, const uint64_t* order,
+                                                             uint32_t n_dev, MsmPlan pl, uint32_t* Ewd, uint32_t* Swd);
 __global__ void __launch_bounds__(kFinalThreads) k_multi_window_check(const uint32_t* W, const uint32_t* Wsub,
                                                                       const uint32_t* P2w, const uint32_t* Swd,
                                                                       const uint8_t* dev_flag, uint32_t n_dev,

@@ -67,13 +67,13 @@ __global__ void k_rebase_offs(const uint64_t* raw, const uint64_t* slot, const u
 }
 
 // Per-device sums: weighted E_d = sum z e, S_d = sum z s (mod q), unit Eu_d, Su_d, the unit
-// point sum Ru_d and the count of malformed entries.  One block per device.
-constexpr int kSegThreads = 256;
-__global__ void __launch_bounds__(256) k_segment_sums(const uint8_t* e, const uint8_t* s, const uint32_t* z,
+// point sum Ru_d and the count of malformed entries.  One block per device, taken in the
+// order `order` (largest devices first, so that no long block starts last).
+__global__ void __launch_bounds__(kSegThreads) k_segment_sums(const uint8_t* e, const uint8_t* s, const uint32_t* z,
                                                               const uint32_t* pts, const uint8_t* badR,
                                                               const uint8_t* badS, const uint64_t* start,
-                                                              SegSums out) {
-  const uint32_t d = blockIdx.x;
+                                                              const uint64_t* order, SegSums out) {
+  const uint32_t d = (uint32_t)order[blockIdx.x];
   const uint64_t lo = start[d], hi = start[d + 1];
   acc13 Ew, Sw, Eu, Su;
   acc_zero(Ew); acc_zero(Sw); acc_zero(Eu); acc_zero(Su);
@@ -151,9 +151,9 @@ __global__ void __launch_bounds__(256) k_segment_sums(const uint8_t* e, const ui
 __global__ void __launch_bounds__(kSegThreads) k_segment_window_sums(const uint8_t* e, const uint8_t* s,
                                                                      const uint32_t* z, const uint8_t* badR,
                                                                      const uint8_t* badS, const uint64_t* start,
-                                                                     uint32_t n_dev, MsmPlan pl, uint32_t* Ewd,
-                                                                     uint32_t* Swd) {
-  const uint32_t d = blockIdx.x / (uint32_t)pl.windows;
+                                                                     const uint64_t* order, uint32_t n_dev,
+                                                                     MsmPlan pl, uint32_t* Ewd, uint32_t* Swd) {
+  const uint32_t d = (uint32_t)order[blockIdx.x / (uint32_t)pl.windows];
   const int w = (int)(blockIdx.x % (uint32_t)pl.windows);
   acc13 ae, as;
   acc_zero(ae);

@@ -2144,11 +2144,19 @@ int poslo_host::aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, const ui
   if ((rc = stage_batch(ctx, &view, sb))) return rc;
   std::vector<DsNode> nodes;
   if ((rc = parse_ds(ctx, mb->ds, mb->ds_off[nd], nodes))) return rc;
-  std::vector<uint64_t> meta;   // start | first | seed_off | e0
+  std::vector<uint64_t> meta;   // start | first | seed_off | e0 | devices by size, largest first
   meta.insert(meta.end(), mb->dev_start, mb->dev_start + nd + 1);
   meta.insert(meta.end(), mb->first_index, mb->first_index + nd);
   meta.insert(meta.end(), seed_off.begin(), seed_off.end());
   meta.insert(meta.end(), e0.begin(), e0.end());
+  {
+    std::vector<uint64_t> order(nd);
+    for (uint32_t d = 0; d < nd; ++d) order[d] = d;
+    std::stable_sort(order.begin(), order.end(), [&](uint64_t a, uint64_t b) {
+      return mb->dev_start[a + 1] - mb->dev_start[a] > mb->dev_start[b + 1] - mb->dev_start[b];
+    });
+    meta.insert(meta.end(), order.begin(), order.end());
+  }
   uint64_t* d_meta;
   uint32_t *d_n2, *d_dsoff;
   DsNode* d_nodes;
@@ -2205,6 +2213,7 @@ int poslo_host::aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, const ui
   const uint64_t* seg_first = d_meta + nd + 1;
   const uint64_t* seg_seed_off = d_meta + 2 * nd + 1;
   const uint64_t* seg_e0 = d_meta + 3 * nd + 2;
+  const uint64_t* seg_order = d_meta + 4 * nd + 2;
   // ---- workspace of the first stage
   const uint64_t N1 = std::max<uint64_t>(N, 1);
   uint32_t *seeds, *pts, *z, *P1, *segbuf, *tmpart;
@@ -2349,11 +2358,11 @@ int poslo_host::aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, const ui
     {
       cudaEvent_t tb, te;
       timer_begin(ctx, "segment_sums", ctx->s_main, &tb, &te);
-      k_segment_sums<<<nd, 256, 0, ctx->s_main>>>(d_e, sb.s, z, pts, badR, badS, seg_start, ss);
+      k_segment_sums<<<nd, kSegThreads, 0, ctx->s_main>>>(d_e, sb.s, z, pts, badR, badS, seg_start, seg_order, ss);
       ++ctx->launch_count;
       if (per_window) {
-        k_segment_window_sums<<<nd * nw, 256, 0, ctx->s_main>>>(d_e, sb.s, z, badR, badS, seg_start, nd, ms.pl,
-                                                                Ewd, Swd);
+        k_segment_window_sums<<<nd * nw, kSegThreads, 0, ctx->s_main>>>(d_e, sb.s, z, badR, badS, seg_start,
+                                                                        seg_order, nd, ms.pl, Ewd, Swd);
         ++ctx->launch_count;
       }
       timer_end(ctx, "segment_sums", ctx->s_main, tb, te);
