@@ -386,12 +386,12 @@ void poslo_reset_kernel_times(poslo_ctx* ctx);
 int poslo_set_graphs(poslo_ctx* ctx, int enabled);
 
 /* Form of poslo_aver_multi's combined weighted check (no counterpart in the paper).  Batches
- * of at most max_entries entries (default 2^21) check it window by window of the weights'
+ * of at most max_entries entries (default 0: none) check it window by window of the weights'
  * signed digits -- sum_t d_{t,w} R_t = sum_d (sum_{t in d} d_{t,w} e_t) Y_d + (sum_t d_{t,w} s_t) G
  * for every window w, which together imply the check with the full weights -- and so skip the
- * MSM's doublings between windows on their critical path; larger batches check the full
- * weights, where the per-device, per-window scalar sums cost more than those doublings.
- * Results are the same either way.  EINVAL for a null context. */
+ * MSM's doublings between windows on their critical path, at the cost of per-device,
+ * per-window scalar sums (one block per device and window).  Results are the same either way.
+ * EINVAL for a null context. */
 int poslo_set_multi_window_limit(poslo_ctx* ctx, uint64_t max_entries);
 
 /* Key cache (no counterpart in the paper).  poslo_distill and poslo_aver_multi (without

@@ -245,7 +245,7 @@ struct PointArgs {
 };
 
 constexpr int kPtsWords = 24;   // stored decoded point: x, y, t2d = 2d x y (8 words each)
-constexpr uint32_t kPointChunk = 512;
+constexpr uint32_t kPointChunk = kPointThreads;   // one point per thread per grab: small batches keep their parallelism
 
 constexpr int kPointPartialWords = 33;
 
@@ -707,7 +707,7 @@ void launch_epoch_seeds_multi(int inst, unsigned grid, unsigned block, cudaStrea
 __global__ void k_rebase_offs(const uint64_t* raw, const uint64_t* slot, const uint64_t* start,
                               const uint64_t* msg_base, uint32_t n_dev, uint64_t* out, uint32_t* status);
 #ifndef POSLO_SEG_THREADS
-#define POSLO_SEG_THREADS 128
+#define POSLO_SEG_THREADS 256
 #endif
 constexpr int kSegThreads = POSLO_SEG_THREADS;   // threads per device block of the segment sums
 __global__ void __launch_bounds__(kSegThreads) k_segment_sums(const uint8_t* e, const uint8_t* s, const uint32_t* z,

@@ -83,7 +83,7 @@ struct poslo_ctx {
   std::vector<cudaEvent_t> event_pool;
   std::map<int, int> msm_tuned;   // (log2 n) * 16 + scalar words -> best window c | range log2 << 8
   poslo_host::Server* server = nullptr;
-  uint64_t multi_window_max = 1ull << 21;   // multi-device batches up to this size check per window
+  uint64_t multi_window_max = 0;  // multi-device batches up to this size check per window (off)
   bool graphs = true;             // replay repeated call shapes from CUDA graphs
   bool capturing = false;         // a stream capture is open on s_main
   uint64_t alloc_gen = 0;         // counts workspace (re)allocations

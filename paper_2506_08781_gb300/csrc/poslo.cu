@@ -1522,22 +1522,29 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
   } else {
     rc = stage1();
   }
+  // the decision and the speculative ccd^v of the all-valid case in one round trip
   uint8_t h_acc = 0;
+  uint8_t hccd[64];
   if (rc == POSLO_OK) {
     CU(cudaMemcpyAsync(&h_acc, d_acc, 1, cudaMemcpyDeviceToHost, ctx->s_main));
-    rc = check_status(ctx);   // synchronises: h_acc is ready
+    CU(cudaMemcpyAsync(hccd, d_ccd, 64, cudaMemcpyDeviceToHost, ctx->s_main));
+    rc = check_status(ctx);   // synchronises: h_acc and hccd are ready
   }
   if (rc != POSLO_OK) return rc;
   kforget.armed = false;   // the key decoded: its table is sound
-  // h_acc covers "no malformed entry and the weighted equation holds"
+  // h_acc covers "no malformed entry and the weighted equation holds": then no entry is
+  // invalid and ccd^v is the unit sums of the whole batch, already read
+  if (h_acc) {
+    *n_invalid = 0;
+    if (ccd_s) memcpy(ccd_s, hccd, 32);
+    if (ccd_R) memcpy(ccd_R, hccd + 32, 32);
+    return POSLO_OK;
+  }
   uint64_t* d_idx;
   const uint64_t capn = std::max<uint64_t>(std::min(cap, n), 1);
   if ((rc = ensure_t(ctx, "invalid_idx", 8 * capn + 8, &d_idx))) return rc;
   uint64_t* d_cnt = d_idx + capn;
-  const bool all_valid = h_acc != 0;   // the fast path: no malformed entry, weighted check holds
-  if (all_valid) {
-    CU(cudaMemsetAsync(inv, 0, n1, ctx->s_main));
-  } else {
+  {
     // ---- localisation: segment-tree bisection over unit aggregates ----
     uint64_t M = 2, L = 1;
     while (M < n) { M <<= 1; ++L; }
@@ -1626,10 +1633,7 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
   const int pblocks = grid_for(ctx, n, kPointThreads, 8);
   uint32_t* pp;
   if ((rc = ensure_t(ctx, "ccd_ppart", (size_t)pblocks * kPointPartialWords * 4, &pp))) return rc;
-  if (all_valid) {
-    // every entry valid: no list; ccd^v = the unit sums of the whole batch, already in d_ccd
-    CU(cudaMemsetAsync(d_cnt, 0, 8, ctx->s_main));
-  } else {
+  {
     if ((rc = run_compact(ctx, inv, n, batch->first_index, d_idx, std::min(cap, n), d_cnt))) return rc;
     k_sum_scalars<<<sblocks, kHashThreads, 0, ctx->s_main>>>(sb.s, n, inv, sp);
     k_reduce_scalars<<<1, 32, 0, ctx->s_main>>>(sp, sblocks, d_ccd);
@@ -1639,7 +1643,6 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
     CU(cudaGetLastError());
   }
   uint64_t cnt = 0;
-  uint8_t hccd[64];
   CU(cudaMemcpyAsync(&cnt, d_cnt, 8, cudaMemcpyDeviceToHost, ctx->s_main));
   CU(cudaMemcpyAsync(hccd, d_ccd, 64, cudaMemcpyDeviceToHost, ctx->s_main));
   if ((rc = check_status(ctx))) return rc;
@@ -2232,9 +2235,11 @@ int poslo_host::aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, const ui
   if ((rc = ensure_t(ctx, "m_seg", (size_t)nd * (32 + 32 + 1) * 4, &segbuf))) return rc;
   if ((rc = ensure_t(ctx, "m_tmpart", (size_t)tmb * kPointPartialWords * 4, &tmpart))) return rc;
   uint32_t *P2 = P1 + 32, *P3 = P1 + 64;
-  // batches up to multi_window_max entries check window by window (no Horner over the windows
-  // on the critical path); larger ones with the full weights, where the per-device,
-  // per-window scalar sums would cost more than the Horner they remove
+  // batches up to multi_window_max entries (0 by default) check window by window (no Horner
+  // over the windows on the critical path); others with the full weights.  Measured: no gain
+  // on small batches, whose latency is the decoding's and the key tables' chains, and a loss
+  // on served batches with large requests, whose per-device, per-window sums run one block
+  // per (device, window) over all of the device's entries
   const MsmPlan plan = msm_plan(ctx, N, 4);
   const bool per_window = N <= ctx->multi_window_max;
   const uint32_t nw = (uint32_t)plan.windows;
