@@ -25,6 +25,13 @@ constexpr int kHashThreads = 128;
 #define POSLO_HASH_MIN_BLOCKS 3   // resident blocks per SM the hash kernel is compiled for
 #endif
 constexpr int kPointThreads = 128;
+// Block size of the short kernels that run beside the decoding (weights, counting sort):
+// small enough that one of their blocks fits in the registers the three resident decoding
+// blocks of an SM leave free, so they progress during the decoding instead of after it.
+#ifndef POSLO_SIDE_THREADS
+#define POSLO_SIDE_THREADS 128
+#endif
+constexpr int kSideThreads = POSLO_SIDE_THREADS;
 constexpr int kTableWindows = 64;   // 4-bit windows over 256 bits
 constexpr int kTableDigits = 8;     // signed digits |d| in 1..8
 constexpr int kTableWords = kTableWindows * kTableDigits * 32;   // one table: 64 KB
@@ -624,10 +631,15 @@ struct PrepArgs {
 // ---- kernel declarations ----
 void launch_epoch_seeds(int inst, unsigned grid, unsigned block, cudaStream_t st, const DsNode* ds, int nds,
                         uint64_t e0, uint64_t ne, uint32_t* x0_out, uint32_t* status);
-void launch_hash(int inst, unsigned grid, cudaStream_t st, const HashArgs& a);
+// Multi-device batches compile their decoding and hashing for this many blocks per SM (128
+// registers a thread), so that three decoding blocks and one hashing block share an SM and
+// the hashing (ALU pipe) runs during the decoding (IMAD pipe) instead of after it.
+constexpr int kCoresidentMinBlocks = 4;
+void launch_hash(int inst, unsigned grid, cudaStream_t st, const HashArgs& a, bool coresident = false);
+void launch_points(unsigned grid, cudaStream_t st, const PointArgs& a, bool coresident = false);
 struct ZPre { uint32_t w[10]; };   // BE words of "POSLO-Z" || verifier_seed || (byte 39 = 0)
 __global__ void k_weights(const ZPre zp, uint64_t n, uint64_t first, uint32_t* z_out);
-__global__ void __launch_bounds__(kPointThreads) k_points(const PointArgs a);
+
 // (Key k's table is dst[k] when a destination list is given -- tables scattered over a
 // cache -- else tables + k kTableWords.)
 __global__ void __launch_bounds__(128) k_table_chain(const uint32_t* __restrict__ enc,

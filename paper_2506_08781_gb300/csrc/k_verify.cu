@@ -80,8 +80,11 @@ __global__ void k_weights(const ZPre zp, uint64_t n, uint64_t first, uint32_t* z
   }
 }
 
-template <int INST>
-__global__ void __launch_bounds__(kHashThreads, POSLO_HASH_MIN_BLOCKS) k_hash(const HashArgs a) {
+// MINB: resident blocks per SM the kernel is compiled for -- POSLO_HASH_MIN_BLOCKS when it runs
+// on its own, kCoresidentMinBlocks (128 registers) when it is to share the SMs with the
+// decoding of a multi-device batch.
+template <int INST, int MINB>
+__global__ void __launch_bounds__(kHashThreads, MINB) k_hash(const HashArgs a) {
   AesCtx c{};
   if constexpr (INST == kInstAes) {
     __shared__ AesShared sh;
@@ -317,7 +320,10 @@ __device__ __forceinline__ void decode_one(const PointArgs& a, uint64_t t, ge& a
 // Every R_t: blocks take chunks of kPointChunk points from a shared counter, so a block that
 // starts late (its SM busy with the hashing beside it) simply takes fewer chunks; then the
 // block's unit sum and decode-failure count.
-__global__ void __launch_bounds__(kPointThreads) k_points(const PointArgs a) {
+// MINB: 1 when the decoding runs on its own (146 registers), kCoresidentMinBlocks (128
+// registers) when three of its blocks share each SM with a hashing block.
+template <int MINB>
+__global__ void __launch_bounds__(kPointThreads, MINB) k_points(const PointArgs a) {
   ge acc = ge_identity();
   uint32_t bad = 0;
 #if POSLO_POINTS_DYNAMIC
@@ -630,9 +636,19 @@ void launch_epoch_seeds(int inst, unsigned grid, unsigned block, cudaStream_t st
   else k_epoch_seeds<kInstSha><<<grid, block, 0, st>>>(ds, nds, e0, ne, x0_out, status);
 }
 
-void launch_hash(int inst, unsigned grid, cudaStream_t st, const HashArgs& a) {
-  if (inst == kInstAes) k_hash<kInstAes><<<grid, kHashThreads, 0, st>>>(a);
-  else k_hash<kInstSha><<<grid, kHashThreads, 0, st>>>(a);
+void launch_hash(int inst, unsigned grid, cudaStream_t st, const HashArgs& a, bool coresident) {
+  if (coresident) {
+    if (inst == kInstAes) k_hash<kInstAes, kCoresidentMinBlocks><<<grid, kHashThreads, 0, st>>>(a);
+    else k_hash<kInstSha, kCoresidentMinBlocks><<<grid, kHashThreads, 0, st>>>(a);
+  } else {
+    if (inst == kInstAes) k_hash<kInstAes, POSLO_HASH_MIN_BLOCKS><<<grid, kHashThreads, 0, st>>>(a);
+    else k_hash<kInstSha, POSLO_HASH_MIN_BLOCKS><<<grid, kHashThreads, 0, st>>>(a);
+  }
+}
+
+void launch_points(unsigned grid, cudaStream_t st, const PointArgs& a, bool coresident) {
+  if (coresident) k_points<kCoresidentMinBlocks><<<grid, kPointThreads, 0, st>>>(a);
+  else k_points<1><<<grid, kPointThreads, 0, st>>>(a);
 }
 
 }  // namespace poslo

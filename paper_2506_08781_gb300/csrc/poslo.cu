@@ -529,7 +529,7 @@ int run_ytable(poslo_ctx* ctx, const uint8_t* Y, uint32_t** table_out) {
 // The decoding waits for `after` (an event on the main stream) when given, else for all main
 // stream work so far.
 int run_points(poslo_ctx* ctx, const uint8_t* R, uint64_t count, uint32_t* pts_out, uint8_t* bad_out,
-               uint32_t** partial_out, uint32_t* nblocks_out, cudaEvent_t after = nullptr) {
+               uint32_t** partial_out, uint32_t* nblocks_out, cudaEvent_t after = nullptr, bool coresident = false) {
   int rc;
   const int blocks = grid_for(ctx, count, kPointThreads, POSLO_POINTS_BLOCKS);
   uint32_t* partial;
@@ -551,7 +551,7 @@ int run_points(poslo_ctx* ctx, const uint8_t* R, uint64_t count, uint32_t* pts_o
   CU(cudaMemsetAsync(work, 0, 4, ctx->s_points));
   cudaEvent_t tb, te;
   timer_begin(ctx, "points", ctx->s_points, &tb, &te);
-  k_points<<<blocks, kPointThreads, 0, ctx->s_points>>>(a);
+  launch_points((unsigned)blocks, ctx->s_points, a, coresident);
   ++ctx->launch_count;
   CU(cudaGetLastError());
   timer_end(ctx, "points", ctx->s_points, tb, te);
@@ -652,10 +652,10 @@ int run_msm_sort(poslo_ctx* ctx, cudaStream_t st, const uint32_t* z, int sw, con
   timer_begin(ctx, "msm_sort", st, &sb_, &se_);
   CU(cudaMemsetAsync(ms.cnt, 0, 4 * nbw, st));
   if (n) {
-    const int g = grid_for(ctx, n, 256, 8);
-    k_msm_count<<<g, 256, 0, st>>>(z, skip_sort, n, pl, ms.cnt, rank);
-    k_msm_scan<<<pl.windows, 1024, 0, st>>>(ms.cnt, ms.off, pl);
-    k_msm_scatter<<<g, 256, 0, st>>>(z, skip_sort, n, pl, ms.off, rank, ms.idx, ms.bkt);
+    const int g = grid_for(ctx, n, kSideThreads, 16);
+    k_msm_count<<<g, kSideThreads, 0, st>>>(z, skip_sort, n, pl, ms.cnt, rank);
+    k_msm_scan<<<pl.windows, kSideThreads, 0, st>>>(ms.cnt, ms.off, pl);
+    k_msm_scatter<<<g, kSideThreads, 0, st>>>(z, skip_sort, n, pl, ms.off, rank, ms.idx, ms.bkt);
     ctx->launch_count += 3;
   }
   CU(cudaGetLastError());
@@ -1460,7 +1460,7 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
     ZPre zp;
     make_zpre(ctx->vseed, zp.w);
     if (n) {
-      k_weights<<<grid_for(ctx, n, 256, 4), 256, 0, ctx->s_main>>>(zp, n, batch->first_index, z);
+      k_weights<<<grid_for(ctx, n, kSideThreads, 8), kSideThreads, 0, ctx->s_main>>>(zp, n, batch->first_index, z);
       ++ctx->launch_count;
     }
     CU(cudaEventRecord(ctx->ev_main, ctx->s_main));
@@ -2302,15 +2302,15 @@ int poslo_host::aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, const ui
                                d_dsoff, seg_seed_off, seg_e0, nd, seeds, ctx->status);
       ++ctx->launch_count;
     }
-    // (side stream) decode every R_t
+    // (side stream) decode every R_t, compiled to share the SMs with the hashing
     uint32_t *ppart, npb;
-    if ((rc = run_points(ctx, sb.R, N, pts, badR, &ppart, &npb))) return rc;
+    if ((rc = run_points(ctx, sb.R, N, pts, badR, &ppart, &npb, nullptr, true))) return rc;
     // the weights z_t alone (they depend only on the batch position), so the MSM's counting
     // sort runs beside the decoding; the segmented hashing (per-entry e_t) on its own stream
     ZPre zp;
     make_zpre(ctx->vseed, zp.w);
     if (N) {
-      k_weights<<<grid_for(ctx, N, 256, 4), 256, 0, ctx->s_main>>>(zp, N, 0, z);
+      k_weights<<<grid_for(ctx, N, kSideThreads, 8), kSideThreads, 0, ctx->s_main>>>(zp, N, 0, z);
       ++ctx->launch_count;
     }
     CU(cudaEventRecord(ctx->ev_main, ctx->s_main));
@@ -2343,7 +2343,7 @@ int poslo_host::aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, const ui
       a.seg_n2 = d_n2;
       cudaEvent_t tb, te;
       timer_begin(ctx, "hash", ctx->s_hash, &tb, &te);
-      launch_hash((int)ctx->inst, (unsigned)blocks, ctx->s_hash, a);
+      launch_hash((int)ctx->inst, (unsigned)blocks, ctx->s_hash, a, true);
       ++ctx->launch_count;
       CU(cudaGetLastError());
       timer_end(ctx, "hash", ctx->s_hash, tb, te);
