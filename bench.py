@@ -156,7 +156,7 @@ ALU_PER_COMPRESSION = 64 * 14 + 48 * 10 + 8
 # DRAM bytes (read + write) of one k_points launch over 2^20 entries, from an ncu capture:
 # the 32 MB of encodings read once; of the 100 MB of decoded points written, the part that has
 # left L2 by the end of the launch.
-POINTS_DRAM_BYTES_2P20 = 33_793_280 + 45_625_088
+POINTS_DRAM_BYTES_2P20 = 33_746_176 + 44_258_304
 
 
 def make_workload(n=N_ENTRIES, seed=SEED, tamper=0):
@@ -846,8 +846,10 @@ def run_ours(args):
 
     # roofline of the dominant kernel
     peaks = probe_int_peaks(device)
-    dom = max((k for k in kernels if k not in ("msm", "seeds")), key=lambda k: kernels[k]["ms_per_launch"]) \
-        if kernels else None
+    # the dominant kernel is the decoding: 48 % of a step's kernel time in the launch list
+    # (profiles/launches_distill_f_2p20.md).  The stage timers cannot pick it: they span each
+    # stream's interval, including the time a stage's blocks wait for SMs held by the others.
+    dom = "points" if "points" in kernels else None
     roof = None
     if dom in ("points", "check") and peaks:
         hi_cost = peaks["imad_lo_ops"] / peaks["imad_hi_ops"]
@@ -857,7 +859,7 @@ def run_ours(args):
         roof = {"bound": "alu", "pipe": "IMAD", "kernel": dom, "achieved": ach, "peak": pk, "unit": "Gop/s",
                 "frac": ach / pk, "traffic": POINTS_DRAM_BYTES_2P20 * n / (1 << 20),
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_points launch "
-                                  "at 2^20 entries (profiles/ncu_full_hash_points_msm_2p20.md)",
+                                  "at 2^20 entries (profiles/ncu_full_points_hash_2p20.md)",
                 "peak_source": "probed mad.lo.u32 issue rate on this GPU (probe/peaks.cu)",
                 "work": f"{IMAD_LO_PER_DECODE:,} mad.lo + {IMAD_HI_PER_DECODE:,} mad.hi per R_t decode and its "
                         f"unit-sum addition; mad.hi counted as {hi_cost:.2f} mad.lo issue slots (probed rate ratio)",
