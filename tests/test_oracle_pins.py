@@ -542,3 +542,73 @@ def test_distill_c_whole_invalid_group_and_swapped_signatures():
     assert ccd.umbrellas[0][:2] == (bytes(32), O.encode_point(O.IDENTITY))
     assert O.sebver_c(Y, list(range(4)), ms, 4, ccd, ds, "U") == [True, True]
     assert O.sebver_c(Y, list(range(4)), ms, 4, ccd, ds, "I") == [False, False]
+
+
+def _signed_window_digits(z: int, c: int, windows: int):
+    """Signed c-bit window digits of z, the recoding the weighted checks sort by: field plus
+    carry r; a field above 2^(c-1) becomes r - 2^c with a carry into the next window."""
+    out, carry = [], 0
+    for w in range(windows):
+        r = ((z >> (c * w)) & ((1 << c) - 1)) + carry
+        if r > (1 << (c - 1)):
+            out.append(r - (1 << c))
+            carry = 1
+        else:
+            out.append(r)
+            carry = 0
+    return out, carry
+
+
+@pytest.mark.parametrize("c", [8, 12, 15, 16])
+def test_signed_window_digits_recompose_weights(c):
+    """Every 127-bit weight is the sum of its signed window digits times 2^(c w); the digits
+    lie in (-2^(c-1), 2^(c-1)] and the last window never carries out."""
+    windows = (127 + 1 + c - 1) // c
+    zs = [int.from_bytes(synth.random_bytes(c, f"z{i}", 16).tobytes(), "little") & ((1 << 127) - 1)
+          for i in range(200)] + [0, 1, (1 << 127) - 1, (1 << (c - 1)), (1 << (c - 1)) + 1]
+    for z in zs:
+        d, carry = _signed_window_digits(z, c, windows)
+        assert carry == 0
+        assert sum(dw << (c * w) for w, dw in enumerate(d)) == z
+        assert all(-(1 << (c - 1)) < dw <= (1 << (c - 1)) for dw in d)
+
+
+def test_window_equations_imply_the_weighted_equation():
+    """With per-entry errors Delta_t = R_t - e_t Y - s_t G, the window sums
+    sum_t d_{t,w} Delta_t recombine with weights 2^(c w) to sum_t z_t Delta_t: every window
+    holding implies the weighted check, and a single bad entry breaks at least one window."""
+    c, windows = 12, 11
+    y = 0x1234567
+    Y = O.scalar_mult(y, O.G)
+    rnd = lambda tag, i, nb: int.from_bytes(synth.random_bytes(77, f"{tag}{i}", nb).tobytes(), "little")
+    n = 6
+    e = [rnd("e", i, 32) % O.Q for i in range(n)]
+    s = [rnd("s", i, 32) % O.Q for i in range(n)]
+    z = [rnd("z", i, 16) & ((1 << 127) - 1) for i in range(n)]
+    r = [rnd("r", i, 32) % O.Q for i in range(n)]
+    R = [O.scalar_mult((s[i] + e[i] * y) % O.Q, O.G) for i in range(n)]   # valid: R = e Y + s G
+    R[3] = O.scalar_mult(r[3], O.G)                                       # one forged entry
+
+    def delta(i):
+        return O.point_add(R[i], O.point_neg(O.point_add(O.scalar_mult(e[i], Y), O.scalar_mult(s[i], O.G))))
+
+    digits = [_signed_window_digits(zi, c, windows)[0] for zi in z]
+    win = []
+    for w in range(windows):
+        acc = O.IDENTITY
+        for i in range(n):
+            d = digits[i][w]
+            if d:
+                acc = O.point_add(acc, O.scalar_mult(d % O.Q, delta(i)))
+        win.append(acc)
+    combined = O.IDENTITY
+    for w in reversed(range(windows)):
+        combined = O.point_add(O.scalar_mult(1 << c, combined), win[w])
+    direct = O.IDENTITY
+    for i in range(n):
+        direct = O.point_add(direct, O.scalar_mult(z[i], delta(i)))
+    assert O.encode_point(combined) == O.encode_point(direct)
+    assert any(O.encode_point(wp) != O.encode_point(O.IDENTITY) for wp in win)
+    # without the forged entry every window holds
+    assert all(O.encode_point(O.scalar_mult(digits[i][w] % O.Q, delta(i))) == O.encode_point(O.IDENTITY)
+               for i in range(n) if i != 3 for w in range(windows))
