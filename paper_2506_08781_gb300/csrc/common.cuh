@@ -674,7 +674,10 @@ __global__ void __launch_bounds__(1024) k_msm_scan(const uint32_t* cnt, uint32_t
 __global__ void k_msm_scatter(const uint32_t* z, const uint8_t* skip, uint64_t n, MsmPlan pl, const uint32_t* off,
                               const uint32_t* rank, uint32_t* idx, uint16_t* bkt);
 __global__ void k_msm_tune_fill(uint32_t* pts, uint32_t* z, uint64_t n, int sw);
-__global__ void __launch_bounds__(128) k_msm_accum(const uint32_t* pts, const uint32_t* idx, const uint16_t* bkt,
+#ifndef POSLO_ACCUM_MINB
+#define POSLO_ACCUM_MINB 4   // resident blocks per SM the bucket accumulation is compiled for (128 registers)
+#endif
+__global__ void __launch_bounds__(128, POSLO_ACCUM_MINB) k_msm_accum(const uint32_t* pts, const uint32_t* idx, const uint16_t* bkt,
                                                    const uint32_t* off, const uint32_t* cnt, uint64_t n, MsmPlan pl,
                                                    const uint8_t* skip, uint32_t* buckets, uint32_t* A, uint32_t* B);
 __global__ void __launch_bounds__(128) k_msm_combine(const uint32_t* off, const uint32_t* cnt, uint64_t n, MsmPlan pl,

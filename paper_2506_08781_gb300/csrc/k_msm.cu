@@ -87,7 +87,7 @@ __global__ void k_msm_scatter(const uint32_t* z, const uint8_t* skip, uint64_t n
 // bucket changes.  A bucket lying strictly inside the range is written directly; the first
 // run goes to A[w][tau], the last (when different) to B[w][tau], and k_msm_combine joins
 // the pieces of buckets that cross range boundaries.
-__global__ void __launch_bounds__(128) k_msm_accum(const uint32_t* pts, const uint32_t* idx, const uint16_t* bkt,
+__global__ void __launch_bounds__(128, POSLO_ACCUM_MINB) k_msm_accum(const uint32_t* pts, const uint32_t* idx, const uint16_t* bkt,
                                                    const uint32_t* off, const uint32_t* cnt, uint64_t n, MsmPlan pl,
                                                    const uint8_t* skip, uint32_t* buckets, uint32_t* A, uint32_t* B) {
   const uint64_t seg = 1ull << pl.seg_log2;
