@@ -179,7 +179,7 @@ def compressions(msgs) -> int:
     return int(np.sum(1 + (L + 16 + 9 + 63) // 64))
 
 
-# ------------------------------------------------------------------------------ config 4: many devices
+# ------------------------------------------------------------------------------ many devices (4,096 signers)
 
 MULTI_DEVICES = 4096
 MULTI_LO, MULTI_HI = 16, 65536
@@ -315,7 +315,7 @@ STREAM_D = 15                          # n1 = 32,768 epochs of 256 entries
 def bench_stream(device: int) -> dict:
     """Out-of-core AVer + Distill (poslo_distill_stream) of 8 x 2^20 POSLO-F entries held in
     pinned host memory, verified 2^20 entries at a time while the next chunk is copied; the
-    per-chunk workload is config 2's (the messages repeat, the signatures do not: each chunk
+    per-chunk workload is the 2^20-entry single-signer one (the messages repeat, the signatures do not: each chunk
     is signed at its own global indices)."""
     import torch
     from paper_2506_08781_gb300 import poslo, synth
@@ -360,7 +360,7 @@ CCD_UMBRELLAS = 64
 
 def bench_distill_c(ctx_inst, device, km, msgs, Y, epoch_R, s_ep, steps, warmup) -> dict:
     """C.Distill (Fig. 3b) of the same 2^20 entries with 0.1 % of them flipped by one byte
-    (config 3's tamper rate), 64 umbrellas, then SeBVer in each mode."""
+    (0.1 % of the entries, one flipped byte each), 64 umbrellas, then SeBVer in each mode."""
     import torch
     from paper_2506_08781_gb300 import poslo, synth
     plan = synth.tamper_plan(SEED + 8, msgs, round(0.001 * msgs.n))
@@ -455,7 +455,7 @@ def bench_hash_bound(device: int, steps: int, warmup: int) -> dict:
                         "device-resident inputs", "results": out}
 
 
-# ------------------------------------------------------------------------------ config 5: serving
+# ------------------------------------------------------------------------------ serving (10,000 resident keys)
 
 SERVE_KEYS = 10000
 SERVE_REQUESTS = 1500

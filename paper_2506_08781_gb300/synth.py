@@ -12,7 +12,7 @@ seed gives the same bytes on every machine and numpy version.
 Workload shapes follow the paper's cold-storage experiments: epochs of n2 = 2^8 entries
 (Sec. 7, Fig. 6 caption), random log entries, and a small fraction of flagged entries
 (tau_F, Sec. 7.4).  Message lengths, batch-size distributions and tamper rates are the
-parameters of the synthetic workloads (configs 1-5 of the benchmark suite).
+parameters of the synthetic workloads the tests and the benchmark build.
 """
 from __future__ import annotations
 

@@ -129,7 +129,7 @@ def test_keygen_and_sign_c_match_oracle(ctx):
 # ------------------------------------------------------------------------------ AVer
 
 @pytest.mark.parametrize("mode", [poslo.AGG_UNIT, poslo.AGG_WEIGHTED])
-def test_aver_f_config1_shape(ctx, mode):
+def test_aver_f_1024_entries_of_64_bytes(ctx, mode):
     """POSLO-F, 1,024 entries of 64 bytes: the valid copy accepts, a one-byte flip rejects."""
     D, n2, n = 2, 256, 1024
     km, sk, Y, msgs, subsets, s, R, _ = _f_data(1, n, D, n2, 64, 64)
@@ -142,7 +142,7 @@ def test_aver_f_config1_shape(ctx, mode):
     assert O.aver_f(Y, bad.as_list(), 0, n2, s, R, O.ds_root(km.root, D)) is False
 
 
-def test_aver_c_config1_shape(ctx):
+def test_aver_c_4_epochs_of_256_entries(ctx):
     """POSLO-C, n1 = 4 epochs of 256 entries of 64 bytes, both R~ forms of AVer step 2."""
     D, n2 = 2, 256
     km = synth.key_material(11)
