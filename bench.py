@@ -712,7 +712,7 @@ def run_reference(args):
             "value": value, "unit": "entries/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot_t / max(args.steps, 1), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": WORKLOAD},
+            "config": {"workload": WORKLOAD, "entries_per_gpu": N_ENTRIES, "parallelism": f"dp{world}"},
             "cpu_baseline": {"value": value, "unit": "entries/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "entries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
