@@ -151,15 +151,17 @@ int poslo_disclose(poslo_ctx* ctx, const uint8_t root[16], uint32_t D, uint64_t 
 /* POSLO.AVer / PAVer (Fig. 3a, Fig. 4, Fig. 6): one accept bit for the whole batch.
  *   agg_mode = POSLO_AGG_UNIT: the paper's equation with unit coefficients,
  *     [8](sum R - (sum e) Y - (sum s) G) = O, plus "every s_t canonical, every R_t decodable".
- *   agg_mode = POSLO_AGG_WEIGHTED (POSLO-F only): each entry weighted by a secret 128-bit z_t,
- *     accepts iff every entry passes its own check, except with probability <= 2^-128.
- * Errors: EINVAL for malformed sizes, an undecodable Y, or a seed the ds does not disclose. */
+ *   agg_mode = POSLO_AGG_WEIGHTED (POSLO-F only): each entry weighted by a secret 127-bit z_t,
+ *     accepts iff every entry passes its own check, except with probability <= 2^-127.
+ * Errors: EINVAL for malformed sizes, more than 2^32 - 1 entries (longer logs: the streaming
+ * call below), an undecodable Y, or a seed the ds does not disclose. */
 int poslo_aver(poslo_ctx* ctx, const poslo_batch* batch, uint32_t agg_mode, uint8_t* accept);
 
 /* POSLO-F Distill / SeBVer at entry granularity (Fig. 3b semantics, Sec. 4.3): the sorted
  * global indices of every entry that fails its own check (malformed s_t or R_t included),
  * and ccd^v = (sum of valid s_t, sum of valid R_t).  invalid_idx has room for cap indices;
- * *n_invalid is the full count (EBUFSMALL if it exceeds cap). */
+ * *n_invalid is the full count (EBUFSMALL if it exceeds cap).  At most 2^32 - 1 entries per
+ * call (EINVAL beyond). */
 int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_idx, uint64_t cap,
                   uint64_t* n_invalid, uint8_t ccd_s[32], uint8_t ccd_R[32]);
 
@@ -186,11 +188,12 @@ typedef struct {
 } poslo_multi_batch;
 
 /* Per-device AVer + Distill for a multi-device batch: accept[d] = 1 iff every entry of
- * device d passes its own check (except with probability <= 2^-128); invalid_pairs receives
+ * device d passes its own check (except with probability <= 2^-127); invalid_pairs receives
  * (device, global index) pairs of the failing entries, 2 uint64 per pair, sorted by device
  * then index, room for cap pairs; *n_invalid is the full count (EBUFSMALL if it exceeds cap).
  * Every stage is one launch over the segment table; one random linear combination checks
- * all devices at once, and only devices that fail their unit aggregate are localised. */
+ * all devices at once, and only devices that fail their unit aggregate are localised.
+ * At most 2^32 - 1 entries over all devices (EINVAL beyond). */
 int poslo_aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, uint8_t* accept, uint64_t* invalid_pairs,
                      uint64_t cap, uint64_t* n_invalid);
 

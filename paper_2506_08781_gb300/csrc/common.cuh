@@ -469,9 +469,10 @@ struct SignCArgs {
 
 
 // ---- Pippenger multi-scalar multiplication (k_msm.cu) ----
-// sum_t [z_t] P_t for 128-bit scalars z_t (4 words each) and stored points P_t (kPtsWords
-// each).  Scalars are cut into windows of c bits; in window w every point goes to bucket
-// digit_w(z_t), found by a counting sort (count with atomics, scan, scatter).  Bucket sums
+// sum_t [z_t] P_t for scalars z_t of 4 words (the verifier's weights, below 2^127) or 8
+// words (any 256-bit value) and stored points P_t (kPtsWords each).  Scalars are cut into
+// signed windows of c bits covering the width plus one bit (for the last carry); in
+// window w every point goes to bucket |digit_w(z_t)|, found by a counting sort (count with atomics, scan, scatter).  Bucket sums
 // B_{w,d} come from a load-balanced pass over the sorted entries; the window sum sum_d d B_{w,d} from chunks of
 // kMsmChunk buckets (running sums inside a chunk, then a binary decomposition of the chunk
 // index), and the windows are joined by Horner's rule in one warp with quad-cooperative

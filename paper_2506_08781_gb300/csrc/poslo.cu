@@ -311,6 +311,10 @@ int validate_batch(poslo_ctx* ctx, const poslo_batch* b) {
   return POSLO_OK;
 }
 
+// One verification call indexes its entries with 32-bit indices inside the MSM and the
+// localisation; longer logs go through poslo_distill_stream in chunks.
+constexpr uint64_t kMaxCallEntries = (1ull << 32) - 1;
+
 // Host inputs are copied R_t first: ev_staged marks their arrival, so the decoding (the
 // longest stage) starts while the messages are still on their way.
 int stage_batch(poslo_ctx* ctx, const poslo_batch* b, Staged& sb, size_t s_bytes_override = 0) {
@@ -1311,6 +1315,7 @@ int poslo_aver(poslo_ctx* ctx, const poslo_batch* batch, uint32_t agg_mode, uint
   if (!ctx || !accept) return fail(ctx, POSLO_EINVAL, "bad aver arguments");
   int rc;
   if ((rc = validate_batch(ctx, batch))) return rc;
+  if (batch->n > kMaxCallEntries) return fail(ctx, POSLO_EINVAL, "more than 2^32 - 1 entries in one call");
   const bool F = batch->variant == POSLO_VARIANT_F;
   if (agg_mode == POSLO_AGG_WEIGHTED && !F) return fail(ctx, POSLO_EINVAL, "weighted aggregation needs POSLO-F");
   if (agg_mode > POSLO_AGG_WEIGHTED) return fail(ctx, POSLO_EINVAL, "bad aggregation mode");
@@ -1365,6 +1370,7 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
   int rc;
   if ((rc = validate_batch(ctx, batch))) return rc;
   if (batch->variant != POSLO_VARIANT_F) return fail(ctx, POSLO_EINVAL, "distill is entry-granular: POSLO-F batches");
+  if (batch->n > kMaxCallEntries) return fail(ctx, POSLO_EINVAL, "more than 2^32 - 1 entries in one call");
   const uint64_t n = batch->n;
   const uint64_t n1 = std::max<uint64_t>(n, 1);
   if ((rc = reset_status(ctx))) return rc;
@@ -2118,6 +2124,7 @@ int poslo_host::aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, const ui
   const uint32_t nd = mb->n_dev;
   const uint64_t N = mb->dev_start[nd];
   if (mb->dev_start[0] != 0 || mb->ds_off[0] != 0) return fail(ctx, POSLO_EINVAL, "segment tables must start at 0");
+  if (N > kMaxCallEntries) return fail(ctx, POSLO_EINVAL, "more than 2^32 - 1 entries in one call");
   std::vector<uint64_t> e0(nd), seed_off(nd + 1, 0);
   for (uint32_t d = 0; d < nd; ++d) {
     if (mb->dev_start[d + 1] < mb->dev_start[d]) return fail(ctx, POSLO_EINVAL, "dev_start decreases at %u", d);

@@ -104,3 +104,46 @@ def test_fullsize_autotuned_window(big):
                        big["d_s"], big["d_R"], big["ds"])
     torch.cuda.synchronize()
     assert list(ctx.distill(b)[0]) == list(plan.idx)
+
+
+def test_fullsize_multi_device_4096():
+    """The 4,096-device batch bench.py times (sizes log-uniform in [16, 65536], about 3.1e7
+    entries, 20 devices with one entry flipped by one byte), under the autotuned MSM plan:
+    the (device, index) list equals the tamper plan, a device is rejected exactly when it has
+    a listed entry, and the oracle's single-entry check rejects every listed entry and
+    accepts a sample of the others."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    with poslo.Context(device=0, verifier_seed=synth.verifier_seed(7)) as ctx:
+        w = bench.make_multi_workload(ctx)
+        nd = len(w["Y"])
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        args = (w["Y"], w["sizes"], np.zeros(nd, np.uint64), np.full(nd, bench.MULTI_N2, np.uint32), w["ds"],
+                dev(w["msgs"].data), dev(w["msgs"].offs.view(np.int64)), dev(w["s"]), dev(w["R"]))
+        torch.cuda.synchronize()
+        ctx.msm_autotune(w["total"], 4)
+        for _ in range(2):                           # the second call is the captured one
+            acc, pairs = ctx.aver_multi(*args)
+            got = [(int(a), int(b)) for a, b in pairs]
+            assert got == w["pairs"]
+            assert [not a for a in acc] == [d in {p[0] for p in got} for d in range(nd)]
+    start = np.zeros(nd + 1, np.int64)
+    start[1:] = np.cumsum(w["sizes"])
+    s, R = w["s"].reshape(-1, 32), w["R"].reshape(-1, 32)
+
+    def oracle_ok(d, t):
+        g = int(start[d]) + t
+        ds = O.ds_root(w["ds"][d][8:], bench.MULTI_D)
+        e = O.entry_scalar(ds, bench.MULTI_N2, t, w["msgs"].entry(g))
+        return O.verify_entry_f(O.decode_point(w["Y"][d]), e, bytes(s[g]), bytes(R[g]))
+
+    for d, t in got:
+        assert not oracle_ok(d, t)
+    flagged = set(got)
+    devs = synth.uniform_int(11, "devs", 24, 0, nd - 1)
+    for k, d in enumerate(devs):
+        d = int(d)
+        t = int(synth.uniform_int(11, f"t{k}", 1, 0, int(w["sizes"][d]) - 1)[0])
+        if (d, t) not in flagged:
+            assert oracle_ok(d, t)
