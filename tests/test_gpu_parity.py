@@ -537,3 +537,24 @@ def test_distill_graph_replay_device_batch():
             wi, ws, wR = O.distill_f(Y, synth.Messages(data, msgs.offs).as_list(), 0, n2, s, R, ds_l)
             assert list(idx) == wi == tampered and cs == ws and cR == wR, trial
         assert cx.graph_stats() == (1, 3)
+
+
+def test_more_than_2p32_minus_1_entries_is_einval(ctx):
+    """A call over more entries than 32-bit entry indices can name fails with EINVAL before it
+    reads any input (the pointers below lead to a few bytes only)."""
+    import ctypes as C
+    buf = np.zeros(64, np.uint8)
+    p = buf.ctypes.data
+    n = 1 << 32
+    b = poslo.Batch()
+    b.variant, b.n2, b.Y, b.msgs, b.offs, b.s, b.R = poslo.VARIANT_F, 8, p, p, p, p, p
+    b.n, b.first_index, b.R_count, b.ds, b.ds_nodes, b.on_device = n, 0, n, p, 1, 0
+    acc, cnt = np.zeros(1, np.uint8), C.c_uint64()
+    assert ctx.lib.poslo_aver(ctx.h, C.byref(b), poslo.AGG_UNIT, acc.ctypes.data) == -1
+    assert ctx.lib.poslo_distill(ctx.h, C.byref(b), p, 0, C.byref(cnt), None, None) == -1
+    start = np.array([0, n], np.uint64)
+    zero64, n2, dsoff = np.zeros(1, np.uint64), np.full(1, 8, np.uint32), np.array([0, 1], np.uint32)
+    mb = poslo.MultiBatch()
+    mb.n_dev, mb.Y, mb.dev_start, mb.first_index, mb.n2 = 1, p, start.ctypes.data, zero64.ctypes.data, n2.ctypes.data
+    mb.ds, mb.ds_off, mb.msgs, mb.offs, mb.s, mb.R, mb.on_device = p, dsoff.ctypes.data, p, p, p, p, 0
+    assert ctx.lib.poslo_aver_multi(ctx.h, C.byref(mb), acc.ctypes.data, p, 0, C.byref(cnt)) == -1

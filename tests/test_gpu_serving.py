@@ -127,3 +127,32 @@ def test_serving_borrowed_and_copied_requests_mix():
         ctx.serve_stop()
     for q, r in zip(reqs, res):
         assert (r[0], list(r[1])) == (not q["want"], q["want"])
+
+
+def test_serving_malformed_request_fails_alone():
+    """A request whose disclosed seeds do not cover its epochs fails with EINVAL; the requests
+    batched with it still get the per-entry definition's results."""
+    import __graft_entry__
+    __graft_entry__.build()
+    keys, reqs = _requests(11, 3, 8)
+    bad = dict(reqs[6])
+    bad["ds"] = O.ds_serialize([O.Node(0, 15, bytes(16))])   # epoch 15 only; the request's are 0..12
+    reqs[6] = bad
+    with poslo.Context(device=0, verifier_seed=synth.verifier_seed(11)) as ctx:
+        ctx.serve_start(workers=1, max_batch_devices=8, max_batch_entries=1 << 20)
+        kid = [ctx.register_key(Y) for _, _, Y in keys]
+        tickets = [_submit(ctx, kid, q) for q in reqs]
+        res = []
+        for t in tickets:
+            try:
+                res.append(ctx.poll(t, wait_ms=60000))
+            except poslo.PosloError as e:
+                res.append(e.code)
+        batches, requests, in_use = ctx.serve_stats()
+        ctx.serve_stop()
+    for k, (q, r) in enumerate(zip(reqs, res)):
+        if k == 6:
+            assert r == -1                                   # EINVAL
+        else:
+            assert (r[0], list(r[1])) == (not q["want"], q["want"])
+    assert requests == 8 and in_use == 0
