@@ -942,6 +942,8 @@ void poslo_destroy(poslo_ctx* ctx) {
   if (ctx->s_main) cudaStreamSynchronize(ctx->s_main);
   if (ctx->s_table) cudaStreamSynchronize(ctx->s_table);
   if (ctx->s_points) cudaStreamSynchronize(ctx->s_points);
+  if (ctx->s_hash) cudaStreamSynchronize(ctx->s_hash);
+  if (ctx->s_copy) cudaStreamSynchronize(ctx->s_copy);
   graph_reset(ctx->g_multi);
   graph_reset(ctx->g_distill);
   for (uint32_t* b : ctx->keys.blocks) cudaFree(b);
