@@ -25,6 +25,7 @@ def _check(line, n_gpus):
     assert cfg["entries_per_gpu"] == 1 << 20 and cfg["parallelism"] == f"dp{n_gpus}" and "workload" in cfg
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
+    assert cb["single_thread_value"] > 0
     assert line["e2e"] == {"value": line["value"], "unit": "entries/s", "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
 
