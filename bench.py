@@ -312,6 +312,61 @@ STREAM_CHUNKS = 8                      # 8 x 2^20 entries (1.2 GB of messages) f
 STREAM_D = 15                          # n1 = 32,768 epochs of 256 entries
 
 
+# ------------------------------------------------------------------------------ 1,024 entries of 64 bytes (latency)
+
+SMALL_N, SMALL_L, SMALL_D, SMALL_CALLS = 1024, 64, 2, 200     # n1 = 4 epochs of n2 = 256
+
+
+def bench_small_latency(device: int, calls: int = SMALL_CALLS) -> dict:
+    """The smallest workload: 1,024 entries of 64-byte messages under POSLO-C (n1 = 4, n2 = 256)
+    and POSLO-F, a valid copy and a copy with one flipped byte.  Per-call wall time of the
+    synchronous calls a user makes with host buffers (inputs copied in, results read back),
+    p50 and p99 in microseconds over `calls` calls after 5 warm-up calls."""
+    from paper_2506_08781_gb300 import poslo, synth
+    km = synth.key_material(SEED + 11, v=64)
+    msgs = synth.messages(SEED + 11, SMALL_N, SMALL_L, SMALL_L)
+    plan = synth.tamper_plan(SEED + 11, msgs, 1)
+    bad = synth.apply_tamper(msgs, plan)
+    ctx = poslo.Context(device=device, verifier_seed=synth.verifier_seed(11))
+    ds = struct.pack("<II", SMALL_D, 0) + km.root
+    Yc, epoch_R = ctx.keygen_c(km.y, km.r, SMALL_D, N2)
+    s_ep = ctx.sign_c(km.y, km.r, km.root, SMALL_D, N2, msgs.data, msgs.offs, 0, 1 << SMALL_D).reshape(-1, 32)
+    # C.Agg of the four epochs' signatures (test-data side, outside the timed calls)
+    s_agg = (sum(int.from_bytes(bytes(r), "little") for r in s_ep) % Q_ORDER).to_bytes(32, "little")
+    Yf, bpv_R = ctx.keygen_f(km.y, km.bpv_r)
+    sub = synth.bpv_subsets(SEED + 11, SMALL_N, v=64, k=4)
+    s_f, R_f = ctx.sign_f(km.y, km.root, SMALL_D, N2, km.bpv_r, bpv_R, sub, msgs.data, msgs.offs)
+    mk = lambda v, Y, m, s_, R_: ctx.make_batch(v, N2, Y, m.data, m.offs, s_, R_, ds)
+    bc, bc_bad = mk(poslo.VARIANT_C, Yc, msgs, s_agg, epoch_R), mk(poslo.VARIANT_C, Yc, bad, s_agg, epoch_R)
+    bf, bf_bad = mk(poslo.VARIANT_F, Yf, msgs, s_f, R_f), mk(poslo.VARIANT_F, Yf, bad, s_f, R_f)
+    assert ctx.aver(bc) is True and ctx.aver(bc_bad) is False
+    assert ctx.aver(bf) is True and ctx.aver(bf_bad) is False
+    assert len(ctx.distill(bf)[0]) == 0 and list(ctx.distill(bf_bad)[0]) == list(plan.idx)
+
+    def lat(fn):
+        for _ in range(5):
+            fn()
+        ts = []
+        for _ in range(calls):
+            t0 = time.perf_counter()
+            fn()
+            ts.append(time.perf_counter() - t0)
+        ts = np.array(ts) * 1e6
+        return {"p50_us": float(np.percentile(ts, 50)), "p99_us": float(np.percentile(ts, 99))}
+
+    out = {"workload": f"{SMALL_N} entries of {SMALL_L}-byte messages, n2 = {N2}, n1 = {1 << SMALL_D} "
+                       "(root disclosed), host buffers, one flipped byte in the tampered copy",
+           "calls": calls,
+           "poslo_c_aver_valid": lat(lambda: ctx.aver(bc)),
+           "poslo_c_aver_tampered": lat(lambda: ctx.aver(bc_bad)),
+           "poslo_f_aver_valid": lat(lambda: ctx.aver(bf)),
+           "poslo_f_aver_tampered": lat(lambda: ctx.aver(bf_bad)),
+           "poslo_f_distill_valid": lat(lambda: ctx.distill(bf)),
+           "poslo_f_distill_tampered": lat(lambda: ctx.distill(bf_bad))}
+    ctx.close()
+    return out
+
+
 def bench_stream(device: int) -> dict:
     """Out-of-core AVer + Distill (poslo_distill_stream) of 8 x 2^20 POSLO-F entries held in
     pinned host memory, verified 2^20 entries at a time while the next chunk is copied; the
@@ -833,6 +888,9 @@ def run_ours(args):
     stream = None
     if not args.no_stream and world == 1:
         stream = bench_stream(device)
+    small = None
+    if not args.no_small and world == 1:
+        small = bench_small_latency(device)
 
     # end to end through the C ABI from pinned host memory
     p_msgs = torch.from_numpy(msgs.data).pin_memory()
@@ -851,8 +909,9 @@ def run_ours(args):
 
     # roofline of the dominant kernel
     peaks = probe_int_peaks(device)
-    # the dominant kernel is the decoding: 48 % of a step's kernel time in the launch list
-    # (profiles/launches_distill_f_2p20.md).  The stage timers cannot pick it: they span each
+    # the dominant kernel is the decoding: the largest share of kernel time in the launch list
+    # (profiles/launches_distill_f_2p20.md: 41 % of all launches listed, signing and peak probes
+    # included; about half of the Distill steps' own kernel time).  The stage timers cannot pick it: they span each
     # stream's interval, including the time a stage's blocks wait for SMs held by the others.
     dom = "points" if "points" in kernels else None
     roof = None
@@ -905,6 +964,7 @@ def run_ours(args):
             "small_batch_graph_replay": replay,
             "hash_bound_poslo_c": hash_bound,
             "out_of_core": stream,
+            "latency_1024_entries": small,
             "serving": serving,
             "int_peaks": peaks,
             "cpu_baseline": cpu,
@@ -928,6 +988,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop measurement")
     ap.add_argument("--no-hash-bound", action="store_true", help="skip the POSLO-C / POSLO+ hash-bound measurement")
     ap.add_argument("--no-stream", action="store_true", help="skip the out-of-core streaming measurement")
+    ap.add_argument("--no-small", action="store_true", help="skip the 1,024-entry latency measurement")
     ap.add_argument("--msm-plan", default=None,
                     help="C,R: fix the Distill MSM plan (window C, ranges of 2^R entries) instead of autotuning it "
                          "(autotuner timings taken under a profiler are distorted)")

@@ -506,12 +506,14 @@ struct KeyForget {
   }
 };
 
-int run_ytable(poslo_ctx* ctx, const uint8_t* Y, uint32_t** table_out) {
+// The window table of Y, built on the table stream into `into` (a key-cache slot) or, when
+// null, into the context's scratch table.
+int run_ytable(poslo_ctx* ctx, const uint8_t* Y, uint32_t** table_out, uint32_t* into = nullptr) {
   int rc;
   uint32_t* d_Y;
   if ((rc = ensure_t(ctx, "Y", 32, &d_Y))) return rc;
-  uint32_t* tableY;
-  if ((rc = ensure_t(ctx, "tableY", 4 * (size_t)kTableWords, &tableY))) return rc;
+  uint32_t* tableY = into;
+  if (!tableY && (rc = ensure_t(ctx, "tableY", 4 * (size_t)kTableWords, &tableY))) return rc;
   CU(cudaMemcpyAsync(d_Y, Y, 32, cudaMemcpyHostToDevice, ctx->s_main));
   CU(cudaEventRecord(ctx->ev_main, ctx->s_main));
   CU(cudaStreamWaitEvent(ctx->s_table, ctx->ev_main, 0));
@@ -1325,8 +1327,18 @@ int poslo_aver(poslo_ctx* ctx, const poslo_batch* batch, uint32_t agg_mode, uint
   if ((rc = reset_status(ctx))) return rc;
   Staged sb;
   if ((rc = stage_batch(ctx, batch, sb))) return rc;
+  // the key's window table from the key cache; built (into its slot) only on a miss
   uint32_t* tableY;
-  if ((rc = run_ytable(ctx, batch->Y, &tableY))) return rc;
+  std::vector<const uint32_t*> ktab;
+  std::vector<uint32_t> kmiss;
+  std::vector<uint32_t*> kdst;
+  const bool kcached = key_cache_lookup(ctx, batch->Y, 1, ktab, kmiss, kdst);
+  KeyForget kforget{ctx, batch->Y, &kmiss, kcached && !kmiss.empty()};
+  if (kcached && kmiss.empty()) {
+    tableY = const_cast<uint32_t*>(ktab[0]);
+  } else if ((rc = run_ytable(ctx, batch->Y, &tableY, kcached ? kdst[0] : nullptr))) {
+    return rc;
+  }
   const uint64_t npts = F ? batch->n : batch->R_count;
   uint32_t* pts = nullptr;
   uint8_t* badR = nullptr;
@@ -1358,6 +1370,7 @@ int poslo_aver(poslo_ctx* ctx, const poslo_batch* batch, uint32_t agg_mode, uint
   uint8_t h_acc = 0;
   CU(cudaMemcpyAsync(&h_acc, d_acc, 1, cudaMemcpyDeviceToHost, ctx->s_main));
   if ((rc = check_status(ctx))) return rc;
+  kforget.armed = false;   // the key decoded: its table is sound
   *accept = h_acc;
   return POSLO_OK;
 }

@@ -123,3 +123,32 @@ def test_multi_cache_duplicates_and_fallback():
         assert e.value.code == -1
         acc, pairs = _multi(cx, parts)
         assert list(acc) == want_acc
+
+
+def test_aver_shares_the_cache():
+    """AVer takes the key's table from the cache too (unit and weighted, valid and tampered),
+    shares it with Distill, and keeps no table of a key that does not decode."""
+    import __graft_entry__
+    __graft_entry__.build()
+    Y, msgs, s, R, ds_l, n2 = sig = _signer(330, 24)
+    bad_msgs = synth.apply_tamper(msgs, synth.tamper_plan(330, msgs, 1))
+    mk = lambda cx, key, m: cx.make_batch(poslo.VARIANT_F, n2, key, m.data, m.offs, b"".join(s), b"".join(R),
+                                          O.ds_serialize(ds_l))
+    with poslo.Context(device=0) as cx:
+        assert cx.aver(mk(cx, Y, msgs)) is True
+        assert cx.aver(mk(cx, Y, msgs), poslo.AGG_WEIGHTED) is True
+        assert cx.aver(mk(cx, Y, bad_msgs)) is False
+        assert cx.aver(mk(cx, Y, bad_msgs), poslo.AGG_WEIGHTED) is False
+        assert cx.key_cache_stats() == (3, 1)
+        _distill(cx, sig)
+        assert cx.key_cache_stats() == (4, 1)
+        bad = _undecodable()
+        for _ in range(2):
+            with pytest.raises(poslo.PosloError) as e:
+                cx.aver(mk(cx, bad, msgs))
+            assert e.value.code == -1
+        assert cx.key_cache_stats() == (4, 3)
+        assert cx.aver(mk(cx, Y, msgs)) is True
+        cx.set_key_cache(0)
+        assert cx.aver(mk(cx, Y, bad_msgs)) is False
+        assert cx.key_cache_stats() == (5, 3)
