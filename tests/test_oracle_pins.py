@@ -612,3 +612,26 @@ def test_window_equations_imply_the_weighted_equation():
     # without the forged entry every window holds
     assert all(O.encode_point(O.scalar_mult(digits[i][w] % O.Q, delta(i))) == O.encode_point(O.IDENTITY)
                for i in range(n) if i != 3 for w in range(windows))
+
+
+def test_multi_device_definition_composes_per_device():
+    """The multi-device definition is the single-signer one per device: a device with a
+    flipped byte lists exactly that entry; a device whose entries are checked under another
+    device's key fails on every entry (R_t = (s_t + e_t y) G holds only for its own y); pairs
+    come sorted by device, then index, with indices local to each device's batch."""
+    devs = [_f_instance(60 + d, n) for d, n in enumerate((3, 4, 2))]
+    parts = []
+    for d, (km, sk, Y, msgs, s, R, _, _) in enumerate(devs):
+        ds = O.ds_root(km.root, sk.D)
+        if d == 1:
+            msgs = list(msgs)
+            mt = bytearray(msgs[2]); mt[0] ^= 0x11; msgs[2] = bytes(mt)
+        key = devs[0][2] if d == 2 else Y
+        parts.append((key, msgs, 0, sk.n2, s, R, ds))
+    accept, pairs = O.verify_multi(parts)
+    assert accept == [True, False, False]
+    assert pairs == [(1, 2), (2, 0), (2, 1)]
+    # each device alone gives the same verdict
+    for d, p in enumerate(parts):
+        inv, _, _ = O.distill_f(*p)
+        assert inv == [t for dd, t in pairs if dd == d]
