@@ -26,7 +26,10 @@
  * Ownership and errors.  The caller owns every buffer it passes.  Unless a call says
  * otherwise, pointers are host pointers; batch pointers marked "device-capable" may be
  * device pointers when poslo_batch.on_device = 1 (they must then stay valid and unmodified
- * until the call returns).  Every call is synchronous: it returns when its outputs are in
+ * until the call returns).  Device-resident offsets must be 8-byte aligned and device-resident
+ * s, R, e_out, points and scalars 16-byte aligned (every cudaMalloc or torch allocation is);
+ * misaligned ones are refused with POSLO_EINVAL before any device work.  Messages may start at
+ * any byte.  Every call is synchronous: it returns when its outputs are in
  * the caller's buffers.  Calls on one context must not overlap (they share its streams and
  * workspace); different contexts are independent.  A call returns POSLO_OK or a negative
  * poslo_status; poslo_last_error() then describes the failure.  "Signature invalid" is not

@@ -67,6 +67,8 @@ extern "C" int poslo_hash_entries_noalloc(const poslo_batch* batch, uint8_t* e_o
   const poslo_batch& b = *batch;
   if (!b.on_device) return POSLO_EINVAL;                  // device buffers only: no staging copies
   if (b.n2 == 0 || (b.n && (!b.msgs || !b.offs))) return POSLO_EINVAL;
+  // offsets are read as 8-byte words, e_t written as 16-byte vectors
+  if ((reinterpret_cast<uintptr_t>(b.offs) & 7) || (reinterpret_cast<uintptr_t>(e_out) & 15)) return POSLO_EINVAL;
   if (!b.ds || b.ds_nodes == 0 || b.ds_nodes > kMaxDsNodes) return POSLO_EINVAL;
   uint64_t e0 = 0, ne = 0;
   if (b.n) {

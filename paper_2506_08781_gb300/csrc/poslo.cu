@@ -293,6 +293,11 @@ struct Staged {
   const uint8_t* R = nullptr;
 };
 
+bool device_aligned(const void* offs, const void* s, const void* R) {
+  return !(reinterpret_cast<uintptr_t>(offs) & 7) && !(reinterpret_cast<uintptr_t>(s) & 15) &&
+         !(reinterpret_cast<uintptr_t>(R) & 15);
+}
+
 int validate_batch(poslo_ctx* ctx, const poslo_batch* b) {
   if (!b) return fail(ctx, POSLO_EINVAL, "null batch");
   if (b->variant != POSLO_VARIANT_C && b->variant != POSLO_VARIANT_F) return fail(ctx, POSLO_EINVAL, "bad variant");
@@ -308,6 +313,9 @@ int validate_batch(poslo_ctx* ctx, const poslo_batch* b) {
   } else {
     if (b->R_count != b->n) return fail(ctx, POSLO_EINVAL, "POSLO-F R_count must equal n");
   }
+  // the kernels read device-resident offsets as 8-byte words and s, R as 16-byte vectors
+  if (b->on_device && b->n && !device_aligned(b->offs, b->s, b->R))
+    return fail(ctx, POSLO_EINVAL, "device-resident offs must be 8-byte aligned, s and R 16-byte aligned");
   return POSLO_OK;
 }
 
@@ -1302,6 +1310,8 @@ int poslo_hash_entries(poslo_ctx* ctx, const poslo_batch* batch, uint8_t* e_out)
   if (!ctx || !e_out) return fail(ctx, POSLO_EINVAL, "bad hash_entries arguments");
   int rc;
   if ((rc = validate_batch(ctx, batch))) return rc;
+  if (batch->on_device && (reinterpret_cast<uintptr_t>(e_out) & 15))
+    return fail(ctx, POSLO_EINVAL, "device-resident e_out must be 16-byte aligned");
   if ((rc = reset_status(ctx))) return rc;
   Staged sb;
   if ((rc = stage_batch(ctx, batch, sb))) return rc;
@@ -1680,6 +1690,8 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
 int poslo_msm(poslo_ctx* ctx, const uint8_t* points, const uint8_t* scalars, uint64_t n, uint32_t on_device,
               uint8_t out[32]) {
   if (!ctx || !out || (n && (!points || !scalars))) return fail(ctx, POSLO_EINVAL, "bad msm arguments");
+  if (on_device && n && ((reinterpret_cast<uintptr_t>(points) | reinterpret_cast<uintptr_t>(scalars)) & 15))
+    return fail(ctx, POSLO_EINVAL, "device-resident points and scalars must be 16-byte aligned");
   int rc;
   if ((rc = reset_status(ctx))) return rc;
   const void *dp, *ds;
@@ -2152,6 +2164,8 @@ int poslo_host::aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, const ui
     seed_off[d + 1] = seed_off[d] + ne;
   }
   if (N && (!mb->offs || !mb->s || !mb->R)) return fail(ctx, POSLO_EINVAL, "missing batch arrays");
+  if (mb->on_device && N && !device_aligned(mb->offs, mb->s, mb->R))
+    return fail(ctx, POSLO_EINVAL, "device-resident offs must be 8-byte aligned, s and R 16-byte aligned");
   if ((rc = reset_status(ctx))) return rc;
   // ---- stage the concatenated batch and the segment tables
   poslo_batch view{};

@@ -50,3 +50,18 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(poslo, "_lib", None)
     with pytest.raises(ImportError):
         poslo.load_library(str(tmp_path / "nope.so"))
+
+
+def test_noalloc_rejects_misaligned_device_pointers_before_any_cuda_call(lib):
+    """Device-resident offsets are read as 8-byte words and e_t written as 16-byte vectors:
+    misaligned addresses are refused on the host (EINVAL) before the device is touched, so
+    this runs without a GPU.  The addresses are never dereferenced."""
+    import ctypes as C
+    import struct
+    ds = (C.c_uint8 * 24).from_buffer_copy(struct.pack("<II", 4, 0) + bytes(16))
+    base = 1 << 20                               # 256-byte aligned fake device addresses
+    for offs, e_out in [(base + 4, base), (base, base + 8), (base + 1, base + 1)]:
+        b = poslo.Batch()
+        b.variant, b.n2, b.Y, b.msgs, b.offs, b.s, b.R = poslo.VARIANT_F, 16, base, base, offs, base, base
+        b.n, b.first_index, b.R_count, b.ds, b.ds_nodes, b.on_device = 8, 0, 8, C.addressof(ds), 1, 1
+        assert lib.poslo_hash_entries_noalloc(C.byref(b), e_out, None) == -1
