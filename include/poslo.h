@@ -144,6 +144,13 @@ int poslo_sign_f(poslo_ctx* ctx, const uint8_t y[32], const uint8_t root[16], ui
                  const uint8_t* msgs, const uint64_t* offs, uint64_t n, uint64_t first_index, uint8_t* s_out,
                  uint8_t* R_out, uint8_t* x_out);
 
+/* Agg (Fig. 3a C.Agg, Fig. 4 F.Agg): s~ = sum of the n scalars mod q (each taken as the
+ * integer its 32 bytes encode) and R~ = sum of the n points, both encoded.  scalars and
+ * points are n*32 bytes, device-capable per on_device.  n = 0 gives s~ = 0 and R~ = O.
+ * Errors: EINVAL if a point does not decode (the outputs are then not written). */
+int poslo_agg(poslo_ctx* ctx, const uint8_t* scalars, const uint8_t* points, uint64_t n, uint32_t on_device,
+              uint8_t s_out[32], uint8_t R_out[32]);
+
 /* SSO (Fig. 2a) run for epochs 0..i from an empty stack: writes ds_i (24 bytes per node,
  * bottom first) to ds_out (capacity cap_nodes) and its node count to *nodes. */
 int poslo_disclose(poslo_ctx* ctx, const uint8_t root[16], uint32_t D, uint64_t i, uint8_t* ds_out,

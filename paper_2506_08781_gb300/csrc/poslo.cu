@@ -1687,6 +1687,51 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
   return POSLO_OK;
 }
 
+// Agg: the scalar sum on the main stream beside the decoding and unit sum of the points on
+// the points stream; one round trip for both results and the count of undecodable points.
+int poslo_agg(poslo_ctx* ctx, const uint8_t* scalars, const uint8_t* points, uint64_t n, uint32_t on_device,
+              uint8_t s_out[32], uint8_t R_out[32]) {
+  if (!ctx || !s_out || !R_out || (n && (!points || !scalars))) return fail(ctx, POSLO_EINVAL, "bad agg arguments");
+  if (n > kMaxCallEntries) return fail(ctx, POSLO_EINVAL, "more than 2^32 - 1 entries in one call");
+  if (on_device && n && ((reinterpret_cast<uintptr_t>(points) | reinterpret_cast<uintptr_t>(scalars)) & 15))
+    return fail(ctx, POSLO_EINVAL, "device-resident points and scalars must be 16-byte aligned");
+  if (n == 0) {   // s~ = 0, R~ = O (encoded y = 1)
+    memset(s_out, 0, 32);
+    R_out[0] = 1;
+    memset(R_out + 1, 0, 31);
+    return POSLO_OK;
+  }
+  int rc;
+  if ((rc = reset_status(ctx))) return rc;
+  const void *dp, *dsc;
+  if ((rc = stage(ctx, "agg_pts_in", points, 32 * n, on_device, ctx->s_main, &dp))) return rc;
+  if ((rc = stage(ctx, "agg_sc_in", scalars, 32 * n, on_device, ctx->s_main, &dsc))) return rc;
+  uint32_t *ppart, npb;
+  if ((rc = run_points(ctx, static_cast<const uint8_t*>(dp), n, nullptr, nullptr, &ppart, &npb))) return rc;
+  const int sblocks = grid_for(ctx, n, kHashThreads, 8);
+  unsigned long long* sp;
+  uint8_t* d_out;   // s~ (32 bytes) | R~ (32 bytes)
+  uint32_t* d_bad;
+  if ((rc = ensure_t(ctx, "agg_spart", (size_t)sblocks * 13 * 8, &sp))) return rc;
+  if ((rc = ensure_t(ctx, "agg_out", 64, &d_out))) return rc;
+  if ((rc = ensure_t(ctx, "agg_bad", 16, &d_bad))) return rc;
+  k_sum_scalars<<<sblocks, kHashThreads, 0, ctx->s_main>>>(static_cast<const uint8_t*>(dsc), n, nullptr, sp);
+  k_reduce_scalars<<<1, 32, 0, ctx->s_main>>>(sp, sblocks, d_out);
+  CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_points, 0));
+  k_sum_encode<<<1, kFinalThreads, 0, ctx->s_main>>>(ppart, npb, nullptr, d_out + 32, d_bad);
+  ctx->launch_count += 3;
+  CU(cudaGetLastError());
+  uint8_t h[64];
+  uint32_t bad = 0;
+  CU(cudaMemcpyAsync(h, d_out, 64, cudaMemcpyDeviceToHost, ctx->s_main));
+  CU(cudaMemcpyAsync(&bad, d_bad, 4, cudaMemcpyDeviceToHost, ctx->s_main));
+  if ((rc = check_status(ctx))) return rc;
+  if (bad) return fail(ctx, POSLO_EINVAL, "%u points do not decode", bad);
+  memcpy(s_out, h, 32);
+  memcpy(R_out, h + 32, 32);
+  return POSLO_OK;
+}
+
 int poslo_msm(poslo_ctx* ctx, const uint8_t* points, const uint8_t* scalars, uint64_t n, uint32_t on_device,
               uint8_t out[32]) {
   if (!ctx || !out || (n && (!points || !scalars))) return fail(ctx, POSLO_EINVAL, "bad msm arguments");

@@ -27,7 +27,7 @@ INST_SHA256, INST_AES = 0, 1          # POSLO and POSLO+ (Sec. 7.2)
 EXPORTS = [
     "poslo_create", "poslo_destroy", "poslo_last_error", "poslo_stream",
     "poslo_keygen_c", "poslo_keygen_f", "poslo_sign_c", "poslo_sign_f", "poslo_disclose",
-    "poslo_aver", "poslo_distill", "poslo_epoch_seeds", "poslo_hash_entries", "poslo_msm", "poslo_msm_autotune",
+    "poslo_agg", "poslo_aver", "poslo_distill", "poslo_epoch_seeds", "poslo_hash_entries", "poslo_msm", "poslo_msm_autotune",
     "poslo_msm_get_plan", "poslo_msm_set_plan",
     "poslo_set_profiling", "poslo_kernel_time", "poslo_reset_kernel_times", "poslo_set_graphs", "poslo_graph_stats",
     "poslo_set_multi_window_limit", "poslo_set_key_cache", "poslo_key_cache_stats",
@@ -100,6 +100,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "poslo_sign_f": ([vp, u8p, u8p, u32, u32, u8p, u8p, u32, u32, vp, u8p, vp, u64, u64, u8p, u8p, u8p],
                          C.c_int),
         "poslo_disclose": ([vp, u8p, u32, u64, u8p, u32, C.POINTER(u32)], C.c_int),
+        "poslo_agg": ([vp, u8p, u8p, u64, u32, u8p, u8p], C.c_int),
         "poslo_aver": ([vp, C.POINTER(Batch), u32, u8p], C.c_int),
         "poslo_distill": ([vp, C.POINTER(Batch), vp, u64, C.POINTER(u64), u8p, u8p], C.c_int),
         "poslo_epoch_seeds": ([vp, u8p, u32, u64, u64, u8p], C.c_int),
@@ -460,6 +461,19 @@ class Context:
             out = np.zeros(32 * max(b.n, 1), np.uint8)
         self._check(self.lib.poslo_hash_entries(self.h, C.byref(cb), _ptr(out)))
         return out
+
+    def agg(self, scalars, points, on_device: bool = False):
+        """Agg: (sum of the scalars mod q, sum of the points), 32 bytes each."""
+        s_out = np.zeros(32, np.uint8)
+        R_out = np.zeros(32, np.uint8)
+        if on_device:
+            n = points.numel() // 32
+        else:
+            points, scalars = _u8(points), _u8(scalars)
+            n = len(points) // 32
+        self._check(self.lib.poslo_agg(self.h, _ptr(scalars), _ptr(points), n, 1 if on_device else 0, _ptr(s_out),
+                                       _ptr(R_out)))
+        return s_out.tobytes(), R_out.tobytes()
 
     def msm(self, points, scalars, on_device: bool = False) -> bytes:
         out = np.zeros(32, np.uint8)
