@@ -268,7 +268,7 @@ int poslo_hash_entries(poslo_ctx* ctx, const poslo_batch* batch, uint8_t* e_out)
 
 /* sum_t [k_t]P_t for n compressed points and n 32-byte scalars (any value below 2^256 is
  * taken as the integer it encodes).  Host or device memory per on_device.  EINVAL if a
- * point does not decode. */
+ * point does not decode or n > 2^32 - 1. */
 int poslo_msm(poslo_ctx* ctx, const uint8_t* points, const uint8_t* scalars, uint64_t n, uint32_t on_device,
               uint8_t out[32]);
 

@@ -1735,6 +1735,7 @@ int poslo_agg(poslo_ctx* ctx, const uint8_t* scalars, const uint8_t* points, uin
 int poslo_msm(poslo_ctx* ctx, const uint8_t* points, const uint8_t* scalars, uint64_t n, uint32_t on_device,
               uint8_t out[32]) {
   if (!ctx || !out || (n && (!points || !scalars))) return fail(ctx, POSLO_EINVAL, "bad msm arguments");
+  if (n > kMaxCallEntries) return fail(ctx, POSLO_EINVAL, "more than 2^32 - 1 points in one call");
   if (on_device && n && ((reinterpret_cast<uintptr_t>(points) | reinterpret_cast<uintptr_t>(scalars)) & 15))
     return fail(ctx, POSLO_EINVAL, "device-resident points and scalars must be 16-byte aligned");
   int rc;
