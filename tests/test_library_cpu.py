@@ -65,3 +65,35 @@ def test_noalloc_rejects_misaligned_device_pointers_before_any_cuda_call(lib):
         b.variant, b.n2, b.Y, b.msgs, b.offs, b.s, b.R = poslo.VARIANT_F, 16, base, base, offs, base, base
         b.n, b.first_index, b.R_count, b.ds, b.ds_nodes, b.on_device = 8, 0, 8, C.addressof(ds), 1, 1
         assert lib.poslo_hash_entries_noalloc(C.byref(b), e_out, None) == -1
+
+
+def test_header_is_plain_c_and_links(lib, tmp_path):
+    """include/poslo.h compiles as C99 and a C program links against the library and gets a
+    clean status from it (no GPU here: poslo_create reports POSLO_EDEVICE or another error,
+    poslo_last_error(NULL) answers, and invalid arguments are refused)."""
+    import shutil
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include "poslo.h"
+int main(void) {
+  poslo_params p = {0};
+  poslo_ctx* ctx = (poslo_ctx*)1;
+  int rc = poslo_create(&p, &ctx);
+  if (rc == POSLO_OK || ctx != NULL) return 2;
+  if (poslo_create(&p, NULL) != POSLO_EINVAL) return 3;
+  if (poslo_last_error(NULL) == NULL) return 4;
+  poslo_destroy(NULL);
+  printf("%d\n", rc);
+  return 0;
+}
+''')
+    exe = tmp_path / "use"
+    subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+                    build.LIB, "-Wl,-rpath," + os.path.dirname(build.LIB)], check=True, capture_output=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, (r.returncode, r.stderr)
+    assert int(r.stdout.strip()) < 0
