@@ -97,3 +97,27 @@ int main(void) {
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, (r.returncode, r.stderr)
     assert int(r.stdout.strip()) < 0
+
+
+def test_product_path_never_imports_the_oracle():
+    """The package (binding, inputs, build) imports nothing from oracle/, statically or at
+    run time: the oracle is test infrastructure only."""
+    import ast
+    import sys
+    pkg = os.path.join(ROOT, "paper_2506_08781_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if not f.endswith(".py"):
+                continue
+            tree = ast.parse(open(os.path.join(dirpath, f)).read())
+            for node in ast.walk(tree):
+                names = []
+                if isinstance(node, ast.Import):
+                    names = [a.name for a in node.names]
+                elif isinstance(node, ast.ImportFrom) and node.module:
+                    names = [node.module]
+                assert not any(n == "oracle" or n.startswith("oracle.") for n in names), (f, names)
+    code = ("import sys; import paper_2506_08781_gb300.poslo, paper_2506_08781_gb300.synth; "
+            "print(any(m == 'oracle' or m.startswith('oracle.') for m in sys.modules))")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and r.stdout.strip() == "False", r.stderr
