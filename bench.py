@@ -20,7 +20,6 @@ from __future__ import annotations
 import argparse
 import ctypes as C
 import json
-import multiprocessing as mp
 import os
 import statistics
 import struct
@@ -268,6 +267,76 @@ def bench_multi(ctx, steps: int, warmup: int) -> dict:
             "value": w["total"] / (ms * 1e-3), "unit": "entries/s", "ms_per_step": ms, "steps": steps,
             "invalid_found": len(got), "setup_s": setup_s, "msm_window": msm_window, "msm_range_log2": msm_range,
             "stages": stages}
+
+
+# ------------------------------------------------------------------------------ Distill with tampered entries
+
+TAMPER_FRAC = 0.001
+TAMPER_SEED = 3
+
+
+def bench_distill_tampered(ctx, msgs, Y, s, R, ds, steps: int, warmup: int) -> dict:
+    """The localisation workload: the same 2^20 signed entries with round(0.001 * 2^20) = 1,049
+    of them flipped by one byte (uniform entries, offsets and non-zero masks), inputs resident
+    in HBM; then the same calls from pinned host memory.  Asserts that the invalid list equals
+    the tamper plan."""
+    import torch
+    from paper_2506_08781_gb300 import poslo, synth
+    n = msgs.n
+    plan = synth.tamper_plan(TAMPER_SEED, msgs, round(TAMPER_FRAC * n))
+    bad = synth.apply_tamper(msgs, plan)
+    want = [int(t) for t in plan.idx]
+    d_msgs = torch.from_numpy(bad.data).cuda()
+    d_offs = torch.from_numpy(bad.offs.view(np.int64)).cuda()
+    d_s, d_R = torch.from_numpy(s).cuda(), torch.from_numpy(R).cuda()
+    torch.cuda.synchronize()
+    batch = ctx.make_batch(poslo.VARIANT_F, N2, Y, d_msgs, d_offs, d_s, d_R, ds)
+    for _ in range(warmup):
+        idx, _, _ = ctx.distill(batch)
+    assert [int(t) for t in idx] == want, "tampered Distill differs from the tamper plan"
+    stream = torch.cuda.ExternalStream(ctx.stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        idx, _, _ = ctx.distill(batch)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    assert [int(t) for t in idx] == want
+    # stage times from further (untimed) calls with the context's kernel timers on
+    ctx.set_profiling(True)
+    ctx.reset_kernel_times()
+    prof_calls = 3
+    for _ in range(prof_calls):
+        ctx.distill(batch)
+    torch.cuda.synchronize()
+    stages = {}
+    for name in ("table", "seeds", "hash", "points", "msm", "msm_sort", "msm_bucket", "msm_reduce", "msm_final",
+                 "finalize", "tree", "bisect", "check"):
+        tot, cnt = ctx.kernel_time(name)
+        if cnt:
+            stages[name] = {"ms_per_call": tot / prof_calls, "launches_per_call": cnt / prof_calls}
+    ctx.set_profiling(False)
+    # end to end from pinned host memory
+    p = [torch.from_numpy(a).pin_memory() for a in (bad.data, bad.offs.view(np.int64), s, R)]
+    hbatch = ctx.make_batch(poslo.VARIANT_F, N2, Y, p[0], p[1], p[2], p[3], ds)
+    for _ in range(2):
+        ctx.distill(hbatch)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        idx, _, _ = ctx.distill(hbatch)
+    e2e_s = (time.perf_counter() - t0) / steps
+    assert [int(t) for t in idx] == want
+    del d_msgs, d_offs, d_s, d_R
+    return {"workload": f"POSLO-F Distill, single signer: N=2^20 entries, |m|~U[32,256] B, n2=256, "
+                        f"{len(want)} entries ({TAMPER_FRAC:.1%}) flipped by one byte at seeded uniform positions",
+            "value": n / (ms * 1e-3), "unit": "entries/s", "ms_per_step": ms, "steps": steps,
+            "invalid_found": len(want), "list_equals_plan": True,
+            "stages": stages,
+            "e2e": {"value": n / e2e_s, "unit": "entries/s",
+                    "h2d_bytes_per_step": int(bad.data.nbytes + bad.offs.nbytes + s.nbytes + R.nbytes + 32 + len(ds)),
+                    "d2h_bytes_per_step": 8 * len(want) + 72}}
 
 
 # ------------------------------------------------------------------------------ graph replay
@@ -680,16 +749,6 @@ def bench_serving(ctx_factory, workers: int = SERVE_WORKERS, max_batch_entries: 
 
 # ------------------------------------------------------------------------------ CPU oracle arm
 
-def _oracle_worker(args):
-    Y, entries, first, s, R, ds_ser = args
-    from oracle import poslo_oracle as O
-    ds = [O.Node(*struct.unpack("<II", ds_ser[24 * k:24 * k + 8]), ds_ser[24 * k + 8:24 * k + 24])
-          for k in range(len(ds_ser) // 24)]
-    t0 = time.perf_counter()
-    inv, _, _ = O.distill_f(Y, entries, first, N2, s, R, ds)
-    return time.perf_counter() - t0, len(entries), len(inv)
-
-
 def host_cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -698,52 +757,48 @@ def host_cores() -> int:
 
 
 class OracleSample:
-    """A bounded sample of the workload signed by the oracle's own signer, verified by the
-    oracle's per-entry Distill (which also decides AVer) in one spawned process per core."""
+    """A bounded sample of the workload (the same message generator, lengths U[32, 256],
+    n2 = 256 under a D = 12 tree with the root disclosed) signed by the C++ oracle's own
+    signer and verified by the C++ oracle's per-entry Distill, which also decides AVer:
+    textbook 4 x 64-bit field arithmetic, double-and-add, SHA-256 from FIPS 180-4, entries
+    split over std::thread workers (oracle/poslo_oracle.cpp)."""
 
     def __init__(self, n: int, cores: int):
-        from oracle import poslo_oracle as O
+        from oracle import cpp_oracle as X
         from paper_2506_08781_gb300 import synth
+        self.X = X
         self.cores = cores
         km = synth.key_material(SEED, v=64)
-        sk, self.Y = O.kg_f(km.y, km.root, D, N2, km.bpv_r.tobytes())
-        msgs = synth.messages(SEED, n, LMIN, LMAX)
+        self.msgs = synth.messages(SEED, n, LMIN, LMAX)
         subsets = synth.bpv_subsets(SEED, n, v=64)
-        self.entries = msgs.as_list()
-        sig = [O.sig_f(sk, t, self.entries[t], subsets[t]) for t in range(n)]
-        self.s = [x[0] for x in sig]
-        self.R = [x[1] for x in sig]
-        self.ds = O.ds_serialize(O.ds_root(km.root, D))
-        self.pool = mp.get_context("spawn").Pool(cores)
+        self.Y = X.base_mult(int.from_bytes(km.y, "little"))
+        self.s, self.R = X.sign_f(km.y, km.root, D, N2, km.bpv_r, subsets, self.msgs.data, self.msgs.offs, 0,
+                                  threads=cores)
+        self.ds = struct.pack("<II", D, 0) + km.root
 
-    def run(self, lo: int, per_core: int):
-        jobs = []
-        for c in range(self.cores):
-            a, b = lo + c * per_core, lo + (c + 1) * per_core
-            jobs.append((self.Y, self.entries[a:b], a, self.s[a:b], self.R[a:b], self.ds))
+    def run(self, lo: int, count: int, threads: int):
+        """Verify entries lo .. lo+count-1; returns (entries, seconds, invalid found)."""
+        offs = self.msgs.offs[lo:lo + count + 1]
         t0 = time.perf_counter()
-        res = self.pool.map(_oracle_worker, jobs)
-        wall = time.perf_counter() - t0
-        self.last_busy_sum = sum(r[0] for r in res)      # single-thread seconds over all processes
-        return self.cores * per_core, max(r[0] for r in res), wall
-
-    def close(self):
-        self.pool.close()
-        self.pool.join()
+        inv, _, _ = self.X.distill_f(self.Y, self.msgs.data, offs, lo, N2, self.s[32 * lo:32 * (lo + count)],
+                                     self.R[32 * lo:32 * (lo + count)], self.ds, threads)
+        return count, time.perf_counter() - t0, len(inv)
 
 
-def cpu_oracle_baseline(per_core: int = 256):
+def cpu_oracle_baseline(per_core: int = 2048):
     cores = host_cores()
-    smp = OracleSample(cores * per_core, cores)
-    try:
-        n, busy, wall = smp.run(0, per_core)
-        busy_sum = smp.last_busy_sum
-    finally:
-        smp.close()
-    return {"value": n / busy, "unit": "entries/s", "cores": cores, "kind": "oracle",
-            "single_thread_value": n / busy_sum,
-            "sample": f"{n} entries of the same workload ({per_core} per core, one spawned process per core); "
-                      f"per-entry Distill (the definition); slowest core {busy:.1f} s, pool wall {wall:.1f} s"}
+    n_all = cores * per_core
+    one = max(64, per_core // 4)
+    smp = OracleSample(n_all + one, cores)
+    n, sec, bad = smp.run(0, n_all, cores)
+    n1, sec1, bad1 = smp.run(n_all, one, 1)
+    assert bad == 0 and bad1 == 0, "the C++ oracle rejected honest entries"
+    return {"value": n / sec, "unit": "entries/s", "cores": cores, "kind": "oracle",
+            "implementation": "C++ oracle (oracle/poslo_oracle.cpp)",
+            "single_thread_value": n1 / sec1,
+            "sample": f"{n} entries of the same workload ({per_core} per core) verified by the C++ oracle's "
+                      f"per-entry Distill (the definition) on {cores} std::thread workers in {sec:.1f} s; "
+                      f"single thread: {n1} further entries in {sec1:.1f} s"}
 
 
 def run_reference(args):
@@ -751,29 +806,29 @@ def run_reference(args):
     if rank != 0:
         return
     cores = host_cores()
-    per_step = max(4, args.cpu_per_core // 8)
-    smp = OracleSample(cores * per_step * (args.steps + args.warmup), cores)
-    try:
-        for w in range(args.warmup):
-            smp.run(w * cores * per_step, per_step)
-        tot_n, tot_t, tot_busy = 0, 0.0, 0.0
-        for k in range(args.steps):
-            n, busy, wall = smp.run((args.warmup + k) * cores * per_step, per_step)
-            tot_n += n
-            tot_t += wall
-            tot_busy += smp.last_busy_sum
-    finally:
-        smp.close()
+    per_step = max(16, args.cpu_per_core // 8)
+    step_n = cores * per_step
+    smp = OracleSample(step_n * (args.steps + args.warmup), cores)
+    for w in range(args.warmup):
+        smp.run(w * step_n, step_n, cores)
+    tot_n, tot_t = 0, 0.0
+    for k in range(args.steps):
+        n, sec, bad = smp.run((args.warmup + k) * step_n, step_n, cores)
+        assert bad == 0
+        tot_n += n
+        tot_t += sec
+    n1, sec1, _ = smp.run(0, max(16, per_step // 2), 1)
     value = tot_n / tot_t
-    sample = (f"{cores * per_step} entries per step ({per_step} per core, one spawned process per core), "
-              f"per-entry Distill (the definition)")
+    sample = (f"{step_n} entries per step ({per_step} per core) verified by the C++ oracle's per-entry Distill "
+              f"(the definition) on {cores} std::thread workers")
     line = {"impl": "reference", "metric": "verified log entries/sec at 1 GB300 (AVer+Distill)",
             "value": value, "unit": "entries/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot_t / max(args.steps, 1), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "entries_per_gpu": N_ENTRIES, "parallelism": f"dp{world}"},
-            "cpu_baseline": {"value": value, "unit": "entries/s", "cores": cores, "kind": "oracle", "sample": sample,
-                             "single_thread_value": tot_n / tot_busy},
+            "cpu_baseline": {"value": value, "unit": "entries/s", "cores": cores, "kind": "oracle",
+                             "implementation": "C++ oracle (oracle/poslo_oracle.cpp)",
+                             "sample": sample, "single_thread_value": n1 / sec1},
             "e2e": {"value": value, "unit": "entries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -874,6 +929,10 @@ def run_ours(args):
     g1 = ctx.graph_stats()
     graph_step = {"ms_per_step": e0.elapsed_time(e1) / args.steps, "replays": g1[1] - g0[1]}
 
+    tampered = None
+    if not args.no_tampered:
+        tampered = bench_distill_tampered(ctx, msgs, Y, s, R, ds, steps=args.steps, warmup=max(2, args.warmup))
+
     multi = None
     replay = None
     if not args.no_multi and world == 1:
@@ -909,10 +968,10 @@ def run_ours(args):
 
     # roofline of the dominant kernel
     peaks = probe_int_peaks(device)
-    # the dominant kernel is the decoding: the largest share of kernel time in the launch list
-    # (profiles/launches_distill_f_2p20.md: 41 % of all launches listed, signing and peak probes
-    # included; about half of the Distill steps' own kernel time).  The stage timers cannot pick it: they span each
-    # stream's interval, including the time a stage's blocks wait for SMs held by the others.
+    # the dominant kernel is the decoding: the largest share of kernel time in the ncu launch list
+    # of this step (about half of the Distill step's own kernel time).  The stage timers cannot
+    # pick it: they span each stream's interval, including the time a stage's blocks wait for
+    # SMs held by the others.
     dom = "points" if "points" in kernels else None
     roof = None
     if dom in ("points", "check") and peaks:
@@ -923,7 +982,7 @@ def run_ours(args):
         roof = {"bound": "alu", "pipe": "IMAD", "kernel": dom, "achieved": ach, "peak": pk, "unit": "Gop/s",
                 "frac": ach / pk, "traffic": POINTS_DRAM_BYTES_2P20 * n / (1 << 20),
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_points launch "
-                                  "at 2^20 entries (profiles/ncu_full_points_hash_2p20.md)",
+                                  "at 2^20 entries",
                 "peak_source": "probed mad.lo.u32 issue rate on this GPU (probe/peaks.cu)",
                 "work": f"{IMAD_LO_PER_DECODE:,} mad.lo + {IMAD_HI_PER_DECODE:,} mad.hi per R_t decode and its "
                         f"unit-sum addition; mad.hi counted as {hi_cost:.2f} mad.lo issue slots (probed rate ratio)",
@@ -960,6 +1019,7 @@ def run_ours(args):
             "e2e": {"value": world * n / e2e_s, "unit": "entries/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "roofline": roof,
+            "distill_tampered": tampered,
             "multi_device": multi,
             "small_batch_graph_replay": replay,
             "hash_bound_poslo_c": hash_bound,
@@ -982,9 +1042,10 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-per-core", type=int, default=256)
+    ap.add_argument("--cpu-per-core", type=int, default=2048)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-multi", action="store_true", help="skip the 4,096-device measurement")
+    ap.add_argument("--no-tampered", action="store_true", help="skip the Distill measurement with 1,049 flipped entries")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop measurement")
     ap.add_argument("--no-hash-bound", action="store_true", help="skip the POSLO-C / POSLO+ hash-bound measurement")
     ap.add_argument("--no-stream", action="store_true", help="skip the out-of-core streaming measurement")

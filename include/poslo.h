@@ -354,16 +354,21 @@ int poslo_sebver_c(poslo_ctx* ctx, const poslo_batch* batch, uint32_t n_umbrella
  * allocator that has reserved all of it (a framework's caching allocator, a fixed pool
  * sized at start-up) or a service that forbids allocation after its initialisation.
  *
- * It computes exactly what poslo_hash_entries computes (e_t = H(m_t || x_t) mod q for every
- * entry, n*32 bytes to e_out) without a context and without allocating: no cudaMalloc,
- * no cudaFree, no allocating library routine.  Its scratch memory is one file-scope device
- * array of about 1.3 MiB that every GPU loading the library keeps until the process exits.
+ * It computes what poslo_hash_entries computes on a context of the POSLO_INST_SHA256
+ * instantiation (e_t = SHA-256(m_t || x_t) mod q for every entry, n*32 bytes to e_out)
+ * without a context and without allocating: no cudaMalloc, no cudaFree, no allocating library
+ * routine.  It has no POSLO+ (AES) form: a batch has no instantiation field, and a log signed
+ * under POSLO_INST_AES must be hashed through poslo_hash_entries on a POSLO+ context.  Its
+ * scratch memory is one file-scope device array of about 1.3 MiB that every GPU loading the
+ * library keeps until the process exits.
  *   - batch->on_device must be 1: msgs, offs (and e_out) are device pointers; Y, s and R are
- *     not read; batch->ds is host memory with at most 64 nodes.
+ *     not read; batch->ds is host memory with at most 64 nodes.  The variant and, for
+ *     POSLO-C, the whole-epoch rule are checked as poslo_hash_entries checks them; n = 0
+ *     returns POSLO_OK without device work.
  *   - Limits: the batch may span at most 65,536 epochs; larger batches return POSLO_EINVAL
  *     before any work is queued.  A seed that ds does not disclose returns POSLO_EINVAL.
- *   - stream: the cudaStream_t to run on (NULL = the legacy default stream); the call returns
- *     after that stream has finished its work.
+ *   - stream: the cudaStream_t to run on (NULL = the legacy default stream).  The call is
+ *     synchronous: it returns after that stream has finished its work.
  *   - The first call on each device looks up the scratch array's device address (with that
  *     device current); make that first call before any stream capture.
  *   - Every call on a device shares the one scratch array.  Calls that overlap on the GPU

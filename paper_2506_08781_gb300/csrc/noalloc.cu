@@ -66,7 +66,10 @@ extern "C" int poslo_hash_entries_noalloc(const poslo_batch* batch, uint8_t* e_o
   if (!batch || !e_out) return POSLO_EINVAL;
   const poslo_batch& b = *batch;
   if (!b.on_device) return POSLO_EINVAL;                  // device buffers only: no staging copies
+  if (b.variant != POSLO_VARIANT_C && b.variant != POSLO_VARIANT_F) return POSLO_EINVAL;
   if (b.n2 == 0 || (b.n && (!b.msgs || !b.offs))) return POSLO_EINVAL;
+  // a POSLO-C batch is whole epochs, as poslo_hash_entries requires (Y, s and R are not read)
+  if (b.variant == POSLO_VARIANT_C && (b.n % b.n2 || b.first_index % b.n2)) return POSLO_EINVAL;
   // offsets are read as 8-byte words, e_t written as 16-byte vectors
   if ((reinterpret_cast<uintptr_t>(b.offs) & 7) || (reinterpret_cast<uintptr_t>(e_out) & 15)) return POSLO_EINVAL;
   if (!b.ds || b.ds_nodes == 0 || b.ds_nodes > kMaxDsNodes) return POSLO_EINVAL;
@@ -76,6 +79,7 @@ extern "C" int poslo_hash_entries_noalloc(const poslo_batch* batch, uint8_t* e_o
     ne = (b.first_index + b.n - 1) / b.n2 - e0 + 1;
   }
   if (ne > kMaxEpochs) return POSLO_EINVAL;                // the batch spans too many epochs
+  if (b.n == 0) return POSLO_OK;                           // nothing to hash, no device work
   int device = 0;
   if (cudaGetDevice(&device) != cudaSuccess) return POSLO_EDEVICE;
   uint8_t* scratch;

@@ -78,3 +78,43 @@ def test_noalloc_limits_and_errors():
         assert torch.equal(got, want)
     finally:
         ctx.close()
+
+
+def test_noalloc_on_a_caller_stream_empty_batch_and_poslo_c_rule():
+    """The caller's own stream, a batch of no entries, and the whole-epoch rule of POSLO-C
+    batches, which poslo_hash_entries applies too."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    ctx = poslo.Context(device=0)
+    try:
+        b = _batch(46, 777, 32, 8, 5)
+        want = torch.zeros(32 * 777, dtype=torch.uint8, device="cuda")
+        got = torch.zeros(32 * 777, dtype=torch.uint8, device="cuda")
+        torch.cuda.synchronize()
+        ctx.hash_entries(b, out=want)
+        st = torch.cuda.Stream()
+        poslo.hash_entries_noalloc(b, got, stream=st.cuda_stream)
+        st.synchronize()
+        assert torch.equal(got, want)
+        # no entries: OK, nothing written
+        b0 = _batch(47, 0, 4, 3, 0)
+        out0 = torch.full((32,), 0x5A, dtype=torch.uint8, device="cuda")
+        torch.cuda.synchronize()
+        poslo.hash_entries_noalloc(b0, out0)
+        torch.cuda.synchronize()
+        assert bool((out0 == 0x5A).all())
+        # a POSLO-C batch that is not whole epochs is refused by both entry points
+        bc = _batch(48, 40, 16, 4, 0)
+        bc.variant = poslo.VARIANT_C
+        bc.R_count = 1
+        out = torch.zeros(32 * 40, dtype=torch.uint8, device="cuda")
+        torch.cuda.synchronize()
+        with pytest.raises(poslo.PosloError) as e:
+            poslo.hash_entries_noalloc(bc, out)
+        assert e.value.code == -1
+        with pytest.raises(poslo.PosloError) as e:
+            ctx.hash_entries(bc, out=out)
+        assert e.value.code == -1
+    finally:
+        ctx.close()
