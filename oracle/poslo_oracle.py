@@ -294,23 +294,39 @@ def _pad_blocks(data: bytes, always: bool) -> list:
     return [data[i:i + 16] for i in range(0, len(data), 16)]
 
 
-def mmo(data: bytes) -> bytes:
-    """MMO: h_i = E_{h_{i-1}}(m_i) xor m_i, h_0 = IV_A; the digest is h_t (16 bytes)."""
-    h = IV_A
-    for m in _pad_blocks(data, always=False):
-        h = _xor(aes128_encrypt(h, m), m)
+def mmo_chain(E, iv: bytes, blocks: list) -> bytes:
+    """The MMO chaining of Def. MMO over already padded blocks: h_0 = iv,
+    h_i = E_{h_{i-1}}(m_i) xor m_i (the chaining value keys the cipher, the block is
+    enciphered); returns h_t.  E(key, block) is the block cipher."""
+    h = iv
+    for m in blocks:
+        h = _xor(E(h, m), m)
     return h
 
 
-def mdc2(data: bytes) -> bytes:
-    """MDC-2: two MMO chains from IV_A and IV_B over the same blocks; after each block the
-    chains exchange their right halves (bytes 8..15).  The digest is h_t || h'_t (32 bytes)."""
-    h, h2 = IV_A, IV_B
-    for m in _pad_blocks(data, always=True):
-        a = _xor(aes128_encrypt(h, m), m)
-        b = _xor(aes128_encrypt(h2, m), m)
-        h, h2 = a[:8] + b[8:], b[:8] + a[8:]
+def mdc2_chain(E, iv1: bytes, iv2: bytes, blocks: list, key1=None, key2=None) -> bytes:
+    """The MDC-2 chaining of Def. MDC-2 over already padded blocks: two MMO steps on the same
+    block from the two chaining values (keyed through key1/key2 when the cipher needs a key
+    transform, none for AES), then the chains exchange their right halves:
+    h_i = A_L || B_R and h'_i = B_L || A_R.  Returns h_t || h'_t."""
+    h, h2 = iv1, iv2
+    half = len(iv1) // 2
+    for m in blocks:
+        a = _xor(E(key1(h) if key1 else h, m), m)
+        b = _xor(E(key2(h2) if key2 else h2, m), m)
+        h, h2 = a[:half] + b[half:], b[:half] + a[half:]
     return h + h2
+
+
+def mmo(data: bytes) -> bytes:
+    """MMO over AES-128: h_0 = IV_A, padding as stated above; the digest is h_t (16 bytes)."""
+    return mmo_chain(aes128_encrypt, IV_A, _pad_blocks(data, always=False))
+
+
+def mdc2(data: bytes) -> bytes:
+    """MDC-2 over AES-128: chains from IV_A and IV_B, exchanging bytes 8..15 after each
+    block; the digest is h_t || h'_t (32 bytes)."""
+    return mdc2_chain(aes128_encrypt, IV_A, IV_B, _pad_blocks(data, always=True))
 
 
 def _k127(x: bytes, bit: int) -> bytes:

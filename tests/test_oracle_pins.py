@@ -431,6 +431,50 @@ def test_mmo_mdc2_structure_with_library_cipher():
     assert O.mmo(two) == x(E(h1, p[16:]), p[16:])
 
 
+def _kat(name):
+    return [(bytes.fromhex(a), bytes.fromhex(b)) for n, a, b in golden_lines("mmo_mdc2_kat.txt") if n == name]
+
+
+def test_mmo_chaining_against_the_zigbee_aes_mmo_example():
+    """The oracle's MMO chaining (Def. MMO) with the oracle's own AES, under the ZigBee
+    standard's initial value and padding, reproduces the standard's published install-code
+    example.  Fails if key and block are swapped in the chaining (E_m(h) instead of E_h(m)),
+    if the xor of the block is dropped or replaced by the chaining value, or if AES is wrong."""
+    for data, digest in _kat("zigbee_aes_mmo"):
+        bits = 8 * len(data)
+        p = data + b"\x80"
+        p += bytes((14 - len(p)) % 16) + bits.to_bytes(2, "big")
+        blocks = [p[i:i + 16] for i in range(0, len(p), 16)]
+        assert len(blocks) == 2
+        assert O.mmo_chain(O.aes128_encrypt, bytes(16), blocks) == digest
+        # the plausible slips give other values
+        swapped = lambda k, m: O.aes128_encrypt(m, k)
+        assert O.mmo_chain(swapped, bytes(16), blocks) != digest
+
+
+def test_mdc2_chaining_against_the_des_known_answer():
+    """The oracle's MDC-2 chaining (Def. MDC-2), run with DES, the ISO/IEC 10118-2 initial
+    values and key bit settings, reproduces the standard's known-answer value.  Pins the two
+    MMO steps on one block and the exchange of right halves (A_L || B_R, B_L || A_R): a swap
+    of the halves, of the chains or of key and block fails."""
+    try:
+        from cryptography.hazmat.decrepit.ciphers.algorithms import TripleDES
+    except ImportError:
+        TripleDES = pytest.importorskip("cryptography.hazmat.primitives.ciphers.algorithms").TripleDES
+    from cryptography.hazmat.primitives.ciphers import Cipher, modes
+
+    def des(k, b):          # single DES as three-key DES with equal keys
+        e = Cipher(TripleDES(k * 3), modes.ECB()).encryptor()
+        return e.update(b) + e.finalize()
+
+    key1 = lambda h: bytes([(h[0] & 0x9F) | 0x40]) + h[1:]
+    key2 = lambda h: bytes([(h[0] & 0x9F) | 0x20]) + h[1:]
+    for data, digest in _kat("mdc2_des"):
+        blocks = [data[i:i + 8] for i in range(0, len(data), 8)]
+        assert O.mdc2_chain(des, b"\x52" * 8, b"\x25" * 8, blocks, key1, key2) == digest
+        assert O.mdc2_chain(des, b"\x25" * 8, b"\x52" * 8, blocks, key2, key1) != digest
+
+
 def test_poslo_plus_prf_is_one_aes_block_with_kappa_127():
     # Sec. 7.2: with kappa = 127 the PRF input x || j is exactly one AES block; outputs keep
     # 127 bits; the two children of a node differ
