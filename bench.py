@@ -1,19 +1,29 @@
-"""Benchmark: verified POSLO log entries per second on one GB300 (AVer + Distill).
+"""Benchmark: verified POSLO log entries per second on GB300 (AVer + Distill).
 
-One step = one poslo_distill call over the large single-signer workload: 2^20 POSLO-F
-entries, message lengths uniform in [32, 256] bytes, epochs of n2 = 256 (n1 = 4096, the
-seed tree's root disclosed), all entries valid.  The call runs every stage of the hot path:
-epoch seeds (SRet), per-entry PRF and H (SHA-256), scalar aggregation mod q, decoding of
-the 2^20 commitments R_t, their aggregation, the cofactored group check, and the
-localisation of invalid entries with the ccd^v aggregate of the valid ones.
+The workload is one signer's log: 2^20 POSLO-F entries per GPU, message lengths uniform in
+[32, 256] bytes, epochs of n2 = 256 (the seed tree's root disclosed), all entries valid.  With
+N GPUs (one process each) the log holds N * 2^20 entries and rank r verifies the contiguous
+shard of global indices [r 2^20, (r + 1) 2^20).
+
+One step is AVer + Distill of the whole log: every rank reduces its shard to the weighted
+aggregate record of poslo_aver_partial (epoch seeds, per-entry PRF and H, the weights z_t,
+the scalar sums mod q, decoding of the 2^20 commitments R_t and their bucket MSM), the ranks
+exchange the 216-byte records (all-gather), and each runs the cofactored check of the whole
+log on its device (poslo_combine_check); only when the log is rejected does every rank run
+Distill on its shard and the ranks gather the ascending invalid lists.  On one GPU the same
+calls run without the exchange.
 
 Inputs are resident in HBM when the timed region starts (value); the e2e figure repeats the
-step through the same C-ABI call with pinned host buffers, so the host-to-device copies of
-the inputs and the device-to-host copy of the results are inside its timed region.  The
+step through the same C-ABI calls with pinned host buffers, so the host-to-device copies of
+the inputs and the device-to-host copies of the results are inside its timed region.  The
 inputs (151 MB of messages + 64 MB of signatures) exceed the 129 MB L2 between steps.
 
---impl reference times the CPU oracle (the plain per-entry definition) on a bounded sample
-of the same workload on this machine's host cores.
+Further objects in the line: the shard's own poslo_distill call, Distill with 0.1 % of the
+entries tampered, the 4,096-device batch, serving, the hash-bound POSLO-C workloads, out of
+core, and the 1,024-entry latencies.
+
+--impl reference times the C++ oracle (the plain per-entry definition) on a bounded sample of
+the same workload on this machine's host cores.
 """
 from __future__ import annotations
 
@@ -39,8 +49,8 @@ D = 12
 LMIN, LMAX = 32, 256
 SEED = 2
 
-WORKLOAD = ("POSLO-F AVer+Distill, single signer: N=2^20 entries, |m|~U[32,256] B, n2=256, "
-            "n1=4096 (root disclosed), all valid, edwards25519 + SHA-256")
+WORKLOAD = ("POSLO-F AVer+Distill, single signer: N=2^20 entries per GPU (one log of N_gpus x 2^20 entries, "
+            "contiguous shards), |m|~U[32,256] B, n2=256 (root disclosed), all valid, edwards25519 + SHA-256")
 
 
 # ------------------------------------------------------------------------------ helpers
@@ -52,9 +62,11 @@ def dist_env():
     return rank, world, local
 
 
-def shard_seed(rank: int) -> int:
-    """Each rank verifies its own independent batch (weak scaling, no data-path exchange)."""
-    return SEED + rank
+def shard_plan(rank: int, world: int, n_per_rank: int = N_ENTRIES) -> tuple[int, int]:
+    """One log of world * n_per_rank entries of one signer, split into contiguous shards: rank r
+    verifies global indices [r n, (r + 1) n).  Returns (first index of the shard, depth of the
+    signer's seed tree), the tree deep enough for every epoch of the whole log (n2 = 256)."""
+    return rank * n_per_rank, D + (world - 1).bit_length()
 
 
 def max_over_ranks(ms: float, world: int) -> float:
@@ -158,18 +170,22 @@ ALU_PER_COMPRESSION = 64 * 14 + 48 * 10 + 8
 POINTS_DRAM_BYTES_2P20 = 33_746_176 + 44_258_304
 
 
-def make_workload(n=N_ENTRIES, seed=SEED, tamper=0):
+def make_workload(n=N_ENTRIES, seed=SEED, tamper=0, rank=0, world=1):
+    """Shard `rank` of the log: the one signer's key material, the shard's messages (rank 0's
+    are the single-GPU workload's) and the BPV subsets at the shard's global indices."""
     from paper_2506_08781_gb300 import synth
     km = synth.key_material(seed)
-    msgs = synth.messages(seed, n, LMIN, LMAX)
-    subsets = synth.bpv_subsets(seed, n)
+    first, _ = shard_plan(rank, world, n)
+    msgs = synth.messages(seed, n, LMIN, LMAX, tag="msg" if rank == 0 else f"msg.shard{rank}")
+    subsets = synth.bpv_subsets(seed, n, first_index=first)
     plan = synth.tamper_plan(seed, msgs, tamper) if tamper else None
     return km, msgs, subsets, plan
 
 
-def sign_workload(ctx, km, msgs, subsets):
+def sign_workload(ctx, km, msgs, subsets, first_index=0, depth=D):
     Y, bpv_R = ctx.keygen_f(km.y, km.bpv_r)
-    s, R = ctx.sign_f(km.y, km.root, D, N2, km.bpv_r, bpv_R, subsets, msgs.data, msgs.offs)
+    s, R = ctx.sign_f(km.y, km.root, depth, N2, km.bpv_r, bpv_R, subsets, msgs.data, msgs.offs,
+                      first_index=first_index)
     return Y, s, R
 
 
@@ -476,7 +492,15 @@ def bench_stream(device: int) -> dict:
 # ------------------------------------------------------------------------------ POSLO-C, hash-bound
 
 Q_ORDER = 2 ** 252 + 27742317777372353535851937790883648493   # order of the group (edwards25519)
-AES_LOOKUPS = 10 * 16 + 10 * 4          # shared-memory table reads per AES-128 (rounds + key schedule)
+# Thread instructions per AES-128 of the table cipher with its on-the-fly key schedule, counted
+# from the algorithm (not the compiled code): each of the 16 round lookups and 4 key-schedule
+# S-box lookups is a byte extract, an address computation and a shared-memory read (3); a full
+# round adds 12 rotations, 8 three-input XORs and 15 key-schedule operations (masks, shifts,
+# the XOR chain, Rcon): 9 x (60 + 12 + 8 + 15) = 855; the last round's 16 S-box reads with their
+# masks and shifts (4 x 20) + 4 XORs + its key schedule (27) = 111; the initial AddRoundKey 4;
+# the MMO/MDC-2 feed-forward XOR 4: about 974.  The kernel is bound by instruction issue (the
+# ALU and shared-memory pipes share the 4 schedulers of an SM), so this count is its roofline.
+AES_INSTR = 9 * (16 * 3 + 4 * 3 + 12 + 8 + 15) + (4 * 20 + 4 + 27) + 4 + 4
 
 
 CCD_UMBRELLAS = 64
@@ -559,9 +583,10 @@ def bench_hash_bound(device: int, steps: int, warmup: int) -> dict:
             ctx.close()
             if inst == poslo.INST_AES:
                 aes = int(np.sum(2 * ((L + 32) // 16) + 2))           # MDC-2 blocks x 2 + the PRF's 2
-                work = {"unit": "G lookups/s", "per_launch": aes * AES_LOOKUPS, "pipe": "LSU (shared memory)",
-                        "peak_note": "32 table reads per clock per SM"}
-                peak = 32 * 152 * 2.07e9
+                work = {"unit": "G thread-instructions/s", "per_launch": aes * AES_INSTR, "pipe": "issue",
+                        "peak_note": "4 warp instructions per clock per SM (32 threads each)",
+                        "aes_calls": aes, "instr_per_aes": AES_INSTR}
+                peak = 4 * 32 * 152 * 2.07e9
             else:
                 work = {"unit": "G ALU ops/s", "per_launch": compressions(msgs) * ALU_PER_COMPRESSION,
                         "pipe": "ALU (LOP3/SHF/IADD3)", "peak_note": "64 ops per clock per SM"}
@@ -588,6 +613,7 @@ SERVE_TAMPER_FRAC = 0.01
 SERVE_BUDGET = 64 << 30
 SERVE_WORKERS = 3
 SERVE_MAX_BATCH = 1 << 22              # entries per served batch at most
+SERVE_PER_LEVEL = 20000                # requests per load level, drawn from the SERVE_REQUESTS payloads
 
 
 def make_serving_workload(ctx, seed=5):
@@ -672,11 +698,18 @@ def bench_serving(ctx_factory, workers: int = SERVE_WORKERS, max_batch_entries: 
     acc = np.zeros(1, np.uint8)
     idx = np.zeros(1 << 16, np.uint64)
 
+    # each load level submits SERVE_PER_LEVEL requests, each one of the distinct signed payloads
+    # drawn uniformly (with replacement): a payload may be in flight in several requests at once
+    order = synth.uniform_int(5, "serve.order", SERVE_PER_LEVEL, 0, len(reqs) - 1)
+    seq = [structs[int(i)] for i in order]
+    seq_reqs = [reqs[int(i)] for i in order]
+    seq_total = int(sum(r["n"] for r in seq_reqs))
+
     def run(arrivals):
         tickets = []
         tk = C.c_uint64()
         base = time.perf_counter()
-        for q, at in zip(structs, arrivals):
+        for q, at in zip(seq, arrivals):
             now = time.perf_counter() - base
             if at > now:
                 time.sleep(at - now)
@@ -699,24 +732,26 @@ def bench_serving(ctx_factory, workers: int = SERVE_WORKERS, max_batch_entries: 
         return np.array(lat), results, wall
 
     # saturated (every request at t = 0): the service's peak
-    lat, results, wall = run(np.zeros(len(structs)))
-    for r, (a, inv) in zip(reqs, results):
+    lat, results, wall = run(np.zeros(len(seq)))
+    for r, (a, inv) in zip(seq_reqs, results):
         assert inv == r["want"] and a == (not r["want"]), "served result differs from the expected one"
-    peak = total / wall
-    mean_size = total / len(reqs)
+    peak = seq_total / wall
+    mean_size = seq_total / len(seq)
     levels = []
     for load in (0.5, 0.8, 0.95):
         rate = load * peak / mean_size
-        arr = synth.poisson_arrivals(int(load * 100), len(structs), rate)
+        arr = synth.poisson_arrivals(int(load * 100), len(seq), rate)
         lat, results, wall = run(arr)
-        assert all(inv == r["want"] for r, (a, inv) in zip(reqs, results))
-        levels.append({"load": load, "offered_requests_per_s": rate, "achieved_entries_per_s": total / wall,
-                       "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3)})
+        assert all(inv == r["want"] for r, (a, inv) in zip(seq_reqs, results))
+        levels.append({"load": load, "offered_requests_per_s": rate, "achieved_entries_per_s": seq_total / wall,
+                       "requests": len(seq), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                       "p99_ms": float(np.percentile(lat, 99) * 1e3)})
     batches, nreq, _ = svc.serve_stats()
     svc.serve_stop()
     svc.close()
-    head = {"workload": f"{SERVE_KEYS} resident keys, {len(reqs)} requests of log-uniform [{SERVE_LO}, {SERVE_HI}] "
-                        f"entries ({total} total), |m|~U[32,256], 1 % tampered, 64 GB budget, {workers} workers, "
+    head = {"workload": f"{SERVE_KEYS} resident keys; per load level {len(seq)} requests ({seq_total} entries), "
+                        f"each one of {len(reqs)} distinct signed payloads of log-uniform [{SERVE_LO}, {SERVE_HI}] "
+                        f"entries drawn uniformly; |m|~U[32,256], 1 % of payloads tampered, 64 GB budget, {workers} workers, "
                         f"batches of at most {max_batch_entries} entries, request data lent from pinned host "
                         "memory (POSLO_REQ_BORROW)",
             "peak_entries_per_s": peak, "levels": levels, "batches": batches, "requests_served": nreq,
@@ -825,7 +860,8 @@ def run_reference(args):
             "value": value, "unit": "entries/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot_t / max(args.steps, 1), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "entries_per_gpu": N_ENTRIES, "parallelism": f"dp{world}"},
+            "config": {"workload": WORKLOAD, "entries_per_gpu": N_ENTRIES, "log_entries": N_ENTRIES * world,
+                       "parallelism": f"dp{world}"},
             "cpu_baseline": {"value": value, "unit": "entries/s", "cores": cores, "kind": "oracle",
                              "implementation": "C++ oracle (oracle/poslo_oracle.cpp)",
                              "sample": sample, "single_thread_value": n1 / sec1},
@@ -840,18 +876,25 @@ def run_ours(args):
     import __graft_entry__
     from paper_2506_08781_gb300 import poslo, synth
 
+    from paper_2506_08781_gb300 import shard
+
     rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("gloo")
     device = local
     torch.cuda.set_device(device)
+    if world > 1:
+        import torch.distributed as dist
+        # host-side bookkeeping (timing maxima) over gloo, the shard records over NCCL
+        dist.init_process_group("cpu:gloo,cuda:nccl")
     __graft_entry__.build()
-    ctx = poslo.Context(device=device, verifier_seed=synth.verifier_seed(1000 + rank))
-    km, msgs, subsets, _ = make_workload(seed=shard_seed(rank))
-    Y, s, R = sign_workload(ctx, km, msgs, subsets)
-    ds = struct.pack("<II", D, 0) + km.root      # final disclosure: the root x_D[0] alone
+    # one verifier: every rank holds the same secret weight seed, so the shards' weighted
+    # records combine into the weighted check of the whole log
+    ctx = poslo.Context(device=device, verifier_seed=synth.verifier_seed(1000))
+    first, depth = shard_plan(rank, world)
+    km, msgs, subsets, _ = make_workload(rank=rank, world=world)
+    Y, s, R = sign_workload(ctx, km, msgs, subsets, first_index=first, depth=depth)
+    ds = struct.pack("<II", depth, 0) + km.root      # final disclosure: the root x_D[0] alone
     n = msgs.n
+    exch = f"cuda:{device}"
 
     # device-resident inputs
     d_msgs = torch.from_numpy(msgs.data).cuda()
@@ -859,7 +902,7 @@ def run_ours(args):
     d_s = torch.from_numpy(s).cuda()
     d_R = torch.from_numpy(R).cuda()
     torch.cuda.synchronize()
-    batch = ctx.make_batch(poslo.VARIANT_F, N2, Y, d_msgs, d_offs, d_s, d_R, ds)
+    batch = ctx.make_batch(poslo.VARIANT_F, N2, Y, d_msgs, d_offs, d_s, d_R, ds, first_index=first)
     if args.msm_plan:
         c_fix, r_fix = (int(v) for v in args.msm_plan.split(","))
         ctx.msm_set_plan(n, c_fix, r_fix)
@@ -870,8 +913,17 @@ def run_ours(args):
     msm_window, msm_range = ctx.msm_get_plan(n, 4)
 
     def step(b):
-        idx, cs, cR = ctx.distill(b)
-        return idx
+        """AVer + Distill of the log: this shard's weighted aggregate record, the exchange of the
+        records (an all-gather of 216 bytes per rank), the combined check of the whole log on the
+        device; only when the log is rejected, Distill of this shard and the gather of the
+        shards' invalid lists.  One rank: the same calls without the exchange."""
+        rec = ctx.aver_partial(b, poslo.AGG_WEIGHTED)
+        recs = shard.all_gather_records(rec.to_bytes(), device=exch) if world > 1 else [rec]
+        accepted, _ = ctx.combine_check(Y, recs)
+        if accepted:
+            return np.zeros(0, np.uint64)
+        idx, _, _ = ctx.distill(b)
+        return shard.gather_lists(idx, device=exch) if world > 1 else idx
 
     for _ in range(args.warmup):
         idx = step(batch)
@@ -917,20 +969,26 @@ def run_ours(args):
     torch.cuda.synchronize()
     aver_ms = e0.elapsed_time(e1) / args.steps
 
-    # the same step with the launch sequence replayed from a CUDA graph (no per-kernel events)
+    # the shard's own Distill on the same resident inputs (its launch sequence replayed from a
+    # CUDA graph): the call a single-GPU user makes for AVer + Distill in one
     for _ in range(2):
-        step(batch)
+        ctx.distill(batch)
     g0 = ctx.graph_stats()
     e0.record(stream)
     for _ in range(args.steps):
-        step(batch)
+        idx_d, _, _ = ctx.distill(batch)
     e1.record(stream)
     torch.cuda.synchronize()
     g1 = ctx.graph_stats()
-    graph_step = {"ms_per_step": e0.elapsed_time(e1) / args.steps, "replays": g1[1] - g0[1]}
+    assert len(idx_d) == 0
+    distill_ms = e0.elapsed_time(e1) / args.steps
+    distill_step = {"value": n / (distill_ms * 1e-3), "unit": "entries/s", "ms_per_step": distill_ms,
+                    "replays": g1[1] - g0[1],
+                    "call": "poslo_distill of the shard (weighted check window by window, then localisation "
+                            "when it fails), launch sequence replayed from its CUDA graph"}
 
     tampered = None
-    if not args.no_tampered:
+    if not args.no_tampered and world == 1:
         tampered = bench_distill_tampered(ctx, msgs, Y, s, R, ds, steps=args.steps, warmup=max(2, args.warmup))
 
     multi = None
@@ -956,15 +1014,16 @@ def run_ours(args):
     p_offs = torch.from_numpy(msgs.offs.view(np.int64)).pin_memory()
     p_s = torch.from_numpy(s).pin_memory()
     p_R = torch.from_numpy(R).pin_memory()
-    hbatch = ctx.make_batch(poslo.VARIANT_F, N2, Y, p_msgs, p_offs, p_s, p_R, ds)
+    hbatch = ctx.make_batch(poslo.VARIANT_F, N2, Y, p_msgs, p_offs, p_s, p_R, ds, first_index=first)
     for _ in range(2):
         step(hbatch)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         idx = step(hbatch)
     e2e_s = (time.perf_counter() - t0) / args.steps
-    h2d = msgs.data.nbytes + msgs.offs.nbytes + s.nbytes + R.nbytes + 32 + len(ds)
-    d2h = 8 * len(idx) + 64 + 8
+    e2e_s = max_over_ranks(e2e_s * 1e3, world) * 1e-3
+    h2d = msgs.data.nbytes + msgs.offs.nbytes + s.nbytes + R.nbytes + 32 + len(ds) + 216 * world
+    d2h = 8 * len(idx) + 2 * 216 + 1 + 8
 
     # roofline of the dominant kernel
     peaks = probe_int_peaks(device)
@@ -1007,7 +1066,8 @@ def run_ours(args):
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u32", "data": "synthetic (seeded SplitMix64 messages; keys and signatures made by "
                                     "poslo_keygen_f/poslo_sign_f)",
-            "config": {"workload": WORKLOAD, "entries_per_gpu": n, "message_bytes": int(msgs.data.nbytes),
+            "config": {"workload": WORKLOAD, "entries_per_gpu": n, "log_entries": n * world,
+                       "message_bytes": int(msgs.data.nbytes),
                        "l2": "inputs (215 MB) larger than the 129 MB L2; no flush", "parallelism": f"dp{world}",
                        "msm_window": msm_window, "msm_range_log2": msm_range,
                        "msm_plan_source": plan_source},
@@ -1015,7 +1075,7 @@ def run_ours(args):
             "gpu_launches": gpu_launches,
             "kernels": kernels,
             "aver_unit": {"value": n / (aver_ms * 1e-3), "ms_per_step": aver_ms},
-            "step_graph_replay": graph_step,
+            "distill_step": distill_step,
             "e2e": {"value": world * n / e2e_s, "unit": "entries/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "roofline": roof,

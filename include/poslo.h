@@ -207,6 +207,45 @@ typedef struct {
 int poslo_aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, uint8_t* accept, uint64_t* invalid_pairs,
                      uint64_t cap, uint64_t* n_invalid);
 
+/* ---- one log split over several GPUs -------------------------------------------------------
+ * A log of one signer split into contiguous ranges of global indices (shards, e.g. one per
+ * GPU) is checked by aggregating each shard on its own GPU and combining the aggregates: AVer
+ * (Fig. 3a, Fig. 4) needs only the sums e~ = sum e_t, s~ = sum s_t mod q and R~ = sum R_t
+ * before its single group check, so a shard's contribution is these three values.  Sums mod q
+ * and point sums are not reductions a collective library provides: the shards exchange the
+ * fixed-size records below (an all-gather of 216 bytes per shard) and each runs the combined
+ * check on its own device.  The localisation of invalid entries (poslo_distill) stays local to
+ * each shard; since shards are contiguous and in index order, the concatenation of their
+ * ascending lists is the log's list.  Not in the paper, whose verifier is one machine; the
+ * paper does split 1 TB logs into chunks aggregated separately (Sec. 7.4). */
+typedef struct {
+  uint8_t e[32];           /* e~ = sum of e_t mod q (weighted: of z_t e_t), canonical LE */
+  uint8_t s[32];           /* s~ = sum of s_t mod q (weighted: of z_t s_t); POSLO-C: the batch's s~ */
+  uint8_t R[128];          /* R~ = sum of R_t (weighted: of [z_t]R_t) in extended coordinates X, Y, Z, T
+                              (x = X/Z, y = Y/Z, xy = T/Z), 32 bytes LE each, every one below p */
+  uint64_t first_index;    /* global index of the shard's first entry */
+  uint64_t n;              /* entries in the shard */
+  uint32_t malformed;      /* non-canonical s_t plus undecodable R_t of the shard (left out of the
+                              sums; any makes the combined check fail); saturates at 2^32 - 1 */
+  uint32_t agg_mode;       /* POSLO_AGG_UNIT or POSLO_AGG_WEIGHTED */
+} poslo_partial;           /* 216 bytes, no padding */
+
+/* The record of one shard: the aggregate of poslo_aver over the batch, before its group check.
+ * agg_mode as for poslo_aver; for weighted records every shard's context must hold the same
+ * verifier_seed (z_t depends on it and on the global index t, not on the shard).  Y is not
+ * read.  Errors as poslo_aver (EINVAL for malformed sizes or an undisclosed seed). */
+int poslo_aver_partial(poslo_ctx* ctx, const poslo_batch* batch, uint32_t agg_mode, poslo_partial* out);
+
+/* The combined check of a log from its shards' records (host memory, n_parts >= 1, in index
+ * order, each starting where the previous ends, all of one agg_mode): sums them on the device
+ * and evaluates [8](R~ - e~ Y - s~ G) = O there.  *accept = 1 iff no shard reported a malformed
+ * entry, every record is well formed (scalars below q, point coordinates below p on the curve)
+ * and the equation holds -- the bit poslo_aver gives for the whole log.  total (optional)
+ * receives the summed record (first_index of the first shard, n of all).  EINVAL for records
+ * out of order, gaps, mixed modes or a Y that does not decode. */
+int poslo_combine_check(poslo_ctx* ctx, const uint8_t Y[32], const poslo_partial* parts, uint32_t n_parts,
+                        uint8_t* accept, poslo_partial* total);
+
 /* ---- serving: continuous batching over registered keys ------------------------------------
  * Not in the paper (which verifies one signer's log at a time); built on poslo_aver_multi.
  * poslo_serve_start starts `workers` host threads (1..8), each with its own internal context

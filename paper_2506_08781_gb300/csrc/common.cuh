@@ -786,5 +786,16 @@ __global__ void __launch_bounds__(1024) k_flag_scan(const uint32_t* blockcnt, ui
                                                    uint64_t* total);
 __global__ void __launch_bounds__(1024) k_flag_scatter(const uint8_t* flags, uint64_t n, uint64_t first_index,
                                                       const uint64_t* blockoff, uint64_t* out, uint64_t cap);
+// ---- shard partials and their combination (k_shard.cu) ----
+constexpr int kShardWords = 54;     // one poslo_partial record in 32-bit words
+constexpr int kShardBadWord = 52;   // its malformed count (after e~, s~, R~, first_index, n)
+constexpr int kShardThreads = 128;
+__global__ void __launch_bounds__(kShardThreads) k_partial_out(const unsigned long long* hash_partial, uint32_t nhash,
+                                                              const uint8_t* s_given, const uint32_t* R,
+                                                              const uint32_t* point_bad, uint32_t* out);
+__global__ void __launch_bounds__(kShardThreads) k_combine_check(const uint32_t* parts, uint32_t nparts,
+                                                                const uint32_t* tableY, const uint32_t* tableG,
+                                                                const uint32_t* status, uint32_t* total,
+                                                                uint8_t* accept);
 
 }  // namespace poslo

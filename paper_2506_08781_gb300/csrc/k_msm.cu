@@ -103,14 +103,18 @@ __global__ void __launch_bounds__(128, POSLO_ACCUM_MINB) k_msm_accum(const uint3
   const uint64_t p1 = min(p0 + seg, nnz);
   const uint32_t* li = idx + (size_t)w * n;
   const uint16_t* lb = bkt + (size_t)w * n;
-  uint32_t cur = lb[p0] & kBktMask;
+  // Entry p's bucket code, point and skip flag are fetched during entry p - 1's addition: the
+  // point and the flag are gathers at a random index, whose latency the addition hides.
+  uint32_t code = lb[p0];
+  uint32_t cur = code & kBktMask;
   bool first = true;
   ge acc = ge_identity();
   fe x, y, t2d;
-  uint32_t tc = __ldg(li + p0);
-  pts_load(pts + (size_t)kPtsWords * tc, x, y, t2d);
+  const uint32_t t0 = __ldg(li + p0);
+  pts_load(pts + (size_t)kPtsWords * t0, x, y, t2d);
+  bool skip_c = skip && skip[t0];
   for (uint64_t p = p0; p < p1; ++p) {
-    const uint32_t code = lb[p], d = code & kBktMask;
+    const uint32_t d = code & kBktMask;
     if (d != cur) {
       uint32_t* dst = first ? A + 32 * g : buckets + 32 * ((size_t)w * pl.nb + cur + 1);
       ge_store(dst, acc);
@@ -119,15 +123,19 @@ __global__ void __launch_bounds__(128, POSLO_ACCUM_MINB) k_msm_accum(const uint3
       cur = d;
     }
     fe nx = x, ny = y, nt = t2d;
-    uint32_t tn = tc;
+    uint32_t ncode = code;
+    bool nskip = skip_c;
     if (p + 1 < p1) {
-      tn = __ldg(li + p + 1);
+      const uint32_t tn = __ldg(li + p + 1);
+      ncode = lb[p + 1];
       pts_load(pts + (size_t)kPtsWords * tn, nx, ny, nt);
+      nskip = skip && __ldg(skip + tn);
     }
     // entries whose point did not decode are sorted but never added
-    if (!(skip && skip[tc])) acc = ge_madd_signed(acc, x, y, t2d, (code & kBktNeg) != 0);
+    if (!skip_c) acc = ge_madd_signed(acc, x, y, t2d, (code & kBktNeg) != 0);
     x = nx; y = ny; t2d = nt;
-    tc = tn;
+    code = ncode;
+    skip_c = nskip;
   }
   ge_store(first ? A + 32 * g : B + 32 * g, acc);
 }

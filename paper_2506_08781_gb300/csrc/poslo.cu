@@ -1385,6 +1385,174 @@ int poslo_aver(poslo_ctx* ctx, const poslo_batch* batch, uint32_t agg_mode, uint
   return POSLO_OK;
 }
 
+// Shard partials: the aggregate of poslo_aver up to (not including) its group check, as a
+// record other shards of the same log can combine (k_shard.cu).
+int poslo_aver_partial(poslo_ctx* ctx, const poslo_batch* batch, uint32_t agg_mode, poslo_partial* out) {
+  if (!ctx || !out) return fail(ctx, POSLO_EINVAL, "bad aver_partial arguments");
+  int rc;
+  if ((rc = validate_batch(ctx, batch))) return rc;
+  if (batch->n > kMaxCallEntries) return fail(ctx, POSLO_EINVAL, "more than 2^32 - 1 entries in one call");
+  const bool F = batch->variant == POSLO_VARIANT_F;
+  if (agg_mode == POSLO_AGG_WEIGHTED && !F) return fail(ctx, POSLO_EINVAL, "weighted aggregation needs POSLO-F");
+  if (agg_mode > POSLO_AGG_WEIGHTED) return fail(ctx, POSLO_EINVAL, "bad aggregation mode");
+  const bool weighted = agg_mode == POSLO_AGG_WEIGHTED;
+  if ((rc = reset_status(ctx))) return rc;
+  Staged sb;
+  if ((rc = stage_batch(ctx, batch, sb))) return rc;
+  const uint64_t npts = F ? batch->n : batch->R_count;
+  uint32_t* pts = nullptr;
+  uint8_t* badR = nullptr;
+  if (weighted) {
+    if ((rc = ensure_t(ctx, "pts", 4 * kPtsWords * std::max<uint64_t>(npts, 1), &pts))) return rc;
+    if ((rc = ensure_t(ctx, "badR", std::max<uint64_t>(npts, 1), &badR))) return rc;
+  }
+  uint32_t* small;   // unit R (32) | weighted R (32) | point bad count (1) | record (kShardWords)
+  if ((rc = ensure_t(ctx, "partial_small", 4 * (65 + (size_t)kShardWords), &small))) return rc;
+  uint32_t *unitR = small, *Rw = small + 32, *pbad = small + 64, *rec = small + 65;
+  uint32_t *ppart, npb;
+  if ((rc = run_points(ctx, sb.R, npts, pts, badR, &ppart, &npb, ctx->ev_staged))) return rc;
+  if ((rc = run_unit_sum(ctx, ppart, npb, unitR, nullptr, pbad))) return rc;
+  unsigned long long* hpart;
+  uint32_t nhb;
+  if (!weighted) {
+    if ((rc = run_hash(ctx, batch, sb, nullptr, false, F, nullptr, &hpart, &nhb))) return rc;
+  } else {
+    // as in Distill: the weights z_t first (they need no message), so the MSM's counting sort
+    // runs on the main stream while the messages are hashed on the hashing stream and the
+    // points decoded on the points stream
+    const uint64_t n = batch->n;
+    uint32_t* z;
+    if ((rc = ensure_t(ctx, "z", 16 * std::max<uint64_t>(n, 1), &z))) return rc;
+    uint64_t e_first = 0, ne = 0;
+    if (n) {
+      e_first = batch->first_index / batch->n2;
+      ne = (batch->first_index + n - 1) / batch->n2 - e_first + 1;
+    }
+    uint32_t* seeds;
+    if ((rc = run_epoch_seeds(ctx, batch->ds, batch->ds_nodes, e_first, ne, &seeds))) return rc;
+    ZPre zp;
+    make_zpre(ctx->vseed, zp.w);
+    if (n) {
+      k_weights<<<grid_for(ctx, n, kSideThreads, 8), kSideThreads, 0, ctx->s_main>>>(zp, n, batch->first_index, z);
+      ++ctx->launch_count;
+    }
+    nhb = (uint32_t)grid_for(ctx, n, kHashThreads, 8);
+    if ((rc = ensure_t(ctx, "hash_partial", (size_t)nhb * kPartialWords * 8, &hpart))) return rc;
+    CU(cudaEventRecord(ctx->ev_main, ctx->s_main));
+    CU(cudaStreamWaitEvent(ctx->s_hash, ctx->ev_main, 0));
+    HashArgs a{};
+    a.msgs = sb.msgs;
+    a.offs = sb.offs;
+    a.base_off = sb.base_off;
+    a.n = n;
+    a.first_index = batch->first_index;
+    a.e0 = e_first;
+    a.n2 = batch->n2;
+    a.n2_log2 = log2_exact(batch->n2);
+    a.seeds = seeds;
+    a.s = sb.s;
+    a.weighted = 1;
+    for (int q = 0; q < 10; ++q) a.zpre[q] = zp.w[q];
+    a.z_in = z;
+    a.partial = hpart;
+    a.status = ctx->status;
+    MsmState ms;
+    if ((rc = run_msm_sort(ctx, ctx->s_main, z, 4, nullptr, n, ms))) return rc;
+    {
+      cudaEvent_t tb, te;
+      timer_begin(ctx, "hash", ctx->s_hash, &tb, &te);
+      launch_hash((int)ctx->inst, nhb, ctx->s_hash, a);
+      ++ctx->launch_count;
+      CU(cudaGetLastError());
+      timer_end(ctx, "hash", ctx->s_hash, tb, te);
+    }
+    CU(cudaEventRecord(ctx->ev_hash, ctx->s_hash));
+    CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_decoded, 0));
+    if ((rc = run_msm_finish(ctx, ctx->s_main, pts, badR, ms, Rw))) return rc;
+    CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_hash, 0));
+  }
+  CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_points, 0));
+  cudaEvent_t tb, te;
+  timer_begin(ctx, "finalize", ctx->s_main, &tb, &te);
+  k_partial_out<<<1, kShardThreads, 0, ctx->s_main>>>(hpart, nhb, F ? nullptr : sb.s, weighted ? Rw : unitR, pbad,
+                                                      rec);
+  ++ctx->launch_count;
+  CU(cudaGetLastError());
+  timer_end(ctx, "finalize", ctx->s_main, tb, te);
+  uint32_t h[kShardWords];
+  CU(cudaMemcpyAsync(h, rec, 4 * kShardWords, cudaMemcpyDeviceToHost, ctx->s_main));
+  if ((rc = check_status(ctx))) return rc;
+  memcpy(out->e, h, 32);
+  memcpy(out->s, h + 8, 32);
+  memcpy(out->R, h + 16, 128);
+  out->first_index = batch->first_index;
+  out->n = batch->n;
+  out->malformed = h[kShardBadWord];
+  out->agg_mode = agg_mode;
+  return POSLO_OK;
+}
+
+// The check of a whole log from its shards' records: sums and [8](R~ - e~ Y - s~ G) = O on the
+// device (k_combine_check), with the window table of Y from the key cache.
+int poslo_combine_check(poslo_ctx* ctx, const uint8_t Y[32], const poslo_partial* parts, uint32_t n_parts,
+                        uint8_t* accept, poslo_partial* total) {
+  if (!ctx || !Y || !parts || !accept || n_parts == 0) return fail(ctx, POSLO_EINVAL, "bad combine arguments");
+  static_assert(sizeof(poslo_partial) == 4 * kShardWords, "poslo_partial is one 54-word record");
+  uint64_t n_all = 0;
+  for (uint32_t i = 0; i < n_parts; ++i) {
+    if (parts[i].agg_mode != parts[0].agg_mode || parts[i].agg_mode > POSLO_AGG_WEIGHTED)
+      return fail(ctx, POSLO_EINVAL, "records of different aggregation modes");
+    if (i && parts[i].first_index != parts[i - 1].first_index + parts[i - 1].n)
+      return fail(ctx, POSLO_EINVAL, "shard %u does not start where shard %u ends", i, i - 1);
+    n_all += parts[i].n;
+  }
+  int rc;
+  if ((rc = reset_status(ctx))) return rc;
+  uint32_t* tableY;
+  std::vector<const uint32_t*> ktab;
+  std::vector<uint32_t> kmiss;
+  std::vector<uint32_t*> kdst;
+  const bool kcached = key_cache_lookup(ctx, Y, 1, ktab, kmiss, kdst);
+  KeyForget kforget{ctx, Y, &kmiss, kcached && !kmiss.empty()};
+  const bool built = !(kcached && kmiss.empty());
+  if (!built) {
+    tableY = const_cast<uint32_t*>(ktab[0]);
+  } else if ((rc = run_ytable(ctx, Y, &tableY, kcached ? kdst[0] : nullptr))) {
+    return rc;
+  }
+  uint32_t *d_parts, *d_total;
+  uint8_t* d_acc;
+  if ((rc = ensure_t(ctx, "combine_parts", sizeof(poslo_partial) * (size_t)n_parts, &d_parts))) return rc;
+  if ((rc = ensure_t(ctx, "combine_total", sizeof(poslo_partial), &d_total))) return rc;
+  if ((rc = ensure_t(ctx, "accept", 16, &d_acc))) return rc;
+  CU(cudaMemcpyAsync(d_parts, parts, sizeof(poslo_partial) * (size_t)n_parts, cudaMemcpyHostToDevice, ctx->s_main));
+  if (built) CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_table, 0));   // the table this call built
+  cudaEvent_t tb, te;
+  timer_begin(ctx, "finalize", ctx->s_main, &tb, &te);
+  k_combine_check<<<1, kShardThreads, 0, ctx->s_main>>>(d_parts, n_parts, tableY, ctx->tableG, ctx->status, d_total,
+                                                        d_acc);
+  ++ctx->launch_count;
+  CU(cudaGetLastError());
+  timer_end(ctx, "finalize", ctx->s_main, tb, te);
+  uint32_t h[kShardWords];
+  uint8_t h_acc = 0;
+  CU(cudaMemcpyAsync(h, d_total, 4 * kShardWords, cudaMemcpyDeviceToHost, ctx->s_main));
+  CU(cudaMemcpyAsync(&h_acc, d_acc, 1, cudaMemcpyDeviceToHost, ctx->s_main));
+  if ((rc = check_status(ctx))) return rc;
+  kforget.armed = false;   // the key decoded: its table is sound
+  *accept = h_acc;
+  if (total) {
+    memcpy(total->e, h, 32);
+    memcpy(total->s, h + 8, 32);
+    memcpy(total->R, h + 16, 128);
+    total->first_index = parts[0].first_index;
+    total->n = n_all;
+    total->malformed = h[kShardBadWord];
+    total->agg_mode = parts[0].agg_mode;
+  }
+  return POSLO_OK;
+}
+
 // Distill: weighted check of the whole batch first; when it fails (or entries are
 // malformed) the segment-tree bisection finds the failing entries, the weighted check of
 // the remaining entries confirms them, and per-entry checks of all entries settle the rare

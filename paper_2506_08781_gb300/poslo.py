@@ -33,7 +33,7 @@ EXPORTS = [
     "poslo_set_multi_window_limit", "poslo_set_key_cache", "poslo_key_cache_stats",
     "poslo_hash_entries_noalloc", "poslo_aver_multi", "poslo_distill_c", "poslo_sebver_c", "poslo_distill_stream",
     "poslo_serve_start", "poslo_serve_stop", "poslo_register_key", "poslo_submit", "poslo_poll",
-    "poslo_serve_stats",
+    "poslo_serve_stats", "poslo_aver_partial", "poslo_combine_check",
 ]
 POSLO_PENDING = 1
 POSLO_EBUFSMALL = -5
@@ -54,6 +54,21 @@ class MultiBatch(C.Structure):
     _fields_ = [("n_dev", C.c_uint32), ("Y", C.c_void_p), ("dev_start", C.c_void_p), ("first_index", C.c_void_p),
                 ("n2", C.c_void_p), ("ds", C.c_void_p), ("ds_off", C.c_void_p), ("msgs", C.c_void_p),
                 ("offs", C.c_void_p), ("s", C.c_void_p), ("R", C.c_void_p), ("on_device", C.c_uint32)]
+
+
+class Partial(C.Structure):
+    """poslo_partial: one shard's aggregate record (216 bytes)."""
+    _fields_ = [("e", C.c_uint8 * 32), ("s", C.c_uint8 * 32), ("R", C.c_uint8 * 128), ("first_index", C.c_uint64),
+                ("n", C.c_uint64), ("malformed", C.c_uint32), ("agg_mode", C.c_uint32)]
+
+    def to_bytes(self) -> bytes:
+        return bytes(memoryview(self).cast("B"))
+
+    @classmethod
+    def from_bytes(cls, b: bytes) -> "Partial":
+        if len(b) != C.sizeof(cls):
+            raise ValueError("a poslo_partial record is 216 bytes")
+        return cls.from_buffer_copy(b)
 
 
 class Request(C.Structure):
@@ -128,6 +143,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "poslo_submit": ([vp, C.POINTER(Request), C.POINTER(u64)], C.c_int),
         "poslo_poll": ([vp, u64, u32, u8p, vp, u64, C.POINTER(u64), C.POINTER(u64)], C.c_int),
         "poslo_serve_stats": ([vp, C.POINTER(u64), C.POINTER(u64), C.POINTER(u64)], C.c_int),
+        "poslo_aver_partial": ([vp, C.POINTER(Batch), u32, C.POINTER(Partial)], C.c_int),
+        "poslo_combine_check": ([vp, u8p, vp, u32, u8p, C.POINTER(Partial)], C.c_int),
     }
     for name in EXPORTS:
         f = getattr(lib, name)
@@ -315,6 +332,24 @@ class Context:
         cb = self._cbatch(b)
         self._check(self.lib.poslo_aver(self.h, C.byref(cb), agg_mode, _ptr(acc)))
         return bool(acc[0])
+
+    def aver_partial(self, b: BatchData, agg_mode: int = AGG_UNIT) -> Partial:
+        """The shard record of poslo_aver_partial (aggregate before the group check)."""
+        out = Partial()
+        cb = self._cbatch(b)
+        self._check(self.lib.poslo_aver_partial(self.h, C.byref(cb), agg_mode, C.byref(out)))
+        return out
+
+    def combine_check(self, Y: bytes, parts) -> tuple:
+        """poslo_combine_check over shard records (Partial objects or 216-byte strings, in
+        index order): returns (accept, summed record)."""
+        recs = b"".join(p.to_bytes() if isinstance(p, Partial) else bytes(p) for p in parts)
+        arr = np.frombuffer(recs, np.uint8).copy()
+        acc = np.zeros(1, np.uint8)
+        total = Partial()
+        self._check(self.lib.poslo_combine_check(self.h, _ptr(bytes(Y)), _ptr(arr), len(recs) // C.sizeof(Partial),
+                                                 _ptr(acc), C.byref(total)))
+        return bool(acc[0]), total
 
     def distill(self, b: BatchData, cap: int | None = None):
         cap = b.n if cap is None else cap

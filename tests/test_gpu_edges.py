@@ -18,7 +18,7 @@ from paper_2506_08781_gb300 import poslo, synth
 
 pytestmark = pytest.mark.gpu
 
-D, N2, N = 4, 4, 40
+D, N2, N = 5, 4, 40
 
 
 @pytest.fixture(scope="module")
