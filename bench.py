@@ -28,6 +28,7 @@ the same workload on this machine's host cores.
 from __future__ import annotations
 
 import argparse
+import collections
 import ctypes as C
 import json
 import os
@@ -706,33 +707,59 @@ def bench_serving(ctx_factory, workers: int = SERVE_WORKERS, max_batch_entries: 
     seq_total = int(sum(r["n"] for r in seq_reqs))
 
     def run(arrivals):
-        tickets = []
+        """Submit the requests at their arrival times.  The budget a request holds is released
+        when its result is read, so when the service refuses a request (EBUSY) the oldest
+        outstanding result is read first; the rest are read after the last submission."""
+        outstanding = collections.deque()
+        lat, results = [None] * len(seq), [None] * len(seq)
         tk = C.c_uint64()
+        cnt, ln = C.c_uint64(), C.c_uint64()
+
+        def read_oldest():
+            i, t = outstanding.popleft()
+            rc = lib.poslo_poll(svc.h, t, 600000, acc.ctypes.data, idx.ctypes.data, len(idx), C.byref(cnt),
+                                C.byref(ln))
+            assert rc == 0, rc
+            lat[i] = ln.value * 1e-9
+            results[i] = (bool(acc[0]), idx[:cnt.value].tolist())
+
         base = time.perf_counter()
-        for q, at in zip(seq, arrivals):
+        for i, (q, at) in enumerate(zip(seq, arrivals)):
             now = time.perf_counter() - base
             if at > now:
                 time.sleep(at - now)
             while True:
                 rc = lib.poslo_submit(svc.h, C.byref(q), C.byref(tk))
-                if rc != -6:        # EBUSY: wait for room
+                if rc != -6:        # EBUSY: over the memory budget
                     break
-                time.sleep(0.0005)
+                assert outstanding, "a single request exceeds the memory budget"
+                read_oldest()
             assert rc == 0, rc
-            tickets.append(tk.value)
-        lat, results = [], []
-        cnt, ln = C.c_uint64(), C.c_uint64()
-        for t in tickets:
-            rc = lib.poslo_poll(svc.h, t, 600000, acc.ctypes.data, idx.ctypes.data, len(idx), C.byref(cnt),
-                                C.byref(ln))
-            assert rc == 0, rc
-            lat.append(ln.value * 1e-9)
-            results.append((bool(acc[0]), idx[:cnt.value].tolist()))
+            outstanding.append((i, tk.value))
+        while outstanding:
+            read_oldest()
         wall = time.perf_counter() - base
         return np.array(lat), results, wall
 
+    def timeline(wall):
+        """Where the workers' time went in the last run, from the service's batch records."""
+        recs = svc.serve_timeline(1 << 20)
+        if not recs:
+            return None
+        stage = sum(r["t_staged_ns"] - r["t_take_ns"] for r in recs) * 1e-9
+        check = sum(r["t_checked_ns"] - r["t_staged_ns"] for r in recs) * 1e-9
+        publish = sum(r["t_done_ns"] - r["t_checked_ns"] for r in recs) * 1e-9
+        busy = stage + check + publish
+        return {"batches": len(recs), "requests_per_batch": float(np.mean([r["requests"] for r in recs])),
+                "entries_per_batch": float(np.mean([r["entries"] for r in recs])),
+                "worker_s_staging": stage, "worker_s_verifying": check, "worker_s_publishing": publish,
+                "worker_idle_frac": max(0.0, 1.0 - busy / (workers * wall)),
+                "staging_GB_per_s": sum(r["entries"] for r in recs) * 216e-9 / max(stage, 1e-9)}
+
+    svc.serve_timeline(1 << 20)      # drop the records of the warm-up
     # saturated (every request at t = 0): the service's peak
     lat, results, wall = run(np.zeros(len(seq)))
+    sat_timeline = timeline(wall)
     for r, (a, inv) in zip(seq_reqs, results):
         assert inv == r["want"] and a == (not r["want"]), "served result differs from the expected one"
     peak = seq_total / wall
@@ -745,7 +772,7 @@ def bench_serving(ctx_factory, workers: int = SERVE_WORKERS, max_batch_entries: 
         assert all(inv == r["want"] for r, (a, inv) in zip(seq_reqs, results))
         levels.append({"load": load, "offered_requests_per_s": rate, "achieved_entries_per_s": seq_total / wall,
                        "requests": len(seq), "p50_ms": float(np.percentile(lat, 50) * 1e3),
-                       "p99_ms": float(np.percentile(lat, 99) * 1e3)})
+                       "p99_ms": float(np.percentile(lat, 99) * 1e3), "timeline": timeline(wall)})
     batches, nreq, _ = svc.serve_stats()
     svc.serve_stop()
     svc.close()
@@ -754,7 +781,8 @@ def bench_serving(ctx_factory, workers: int = SERVE_WORKERS, max_batch_entries: 
                         f"entries drawn uniformly; |m|~U[32,256], 1 % of payloads tampered, 64 GB budget, {workers} workers, "
                         f"batches of at most {max_batch_entries} entries, request data lent from pinned host "
                         "memory (POSLO_REQ_BORROW)",
-            "peak_entries_per_s": peak, "levels": levels, "batches": batches, "requests_served": nreq,
+            "peak_entries_per_s": peak, "peak_timeline": sat_timeline, "levels": levels, "batches": batches,
+            "requests_served": nreq,
             "setup_s": setup_s}
     if not plain_path:
         return head

@@ -707,10 +707,27 @@ __global__ void __launch_bounds__(kWindowThreads) k_window_prep(const unsigned l
 __global__ void __launch_bounds__(128) k_tree_leaves(const TreeArgs a);
 __global__ void __launch_bounds__(128) k_tree_level(const TreeArgs a, uint64_t in_off, uint64_t out_off,
                                                     uint64_t count);
-__global__ void __launch_bounds__(128) k_bisect(const TreeArgs a, int lvl, uint64_t lvl_off, const uint64_t* front, const uint64_t* front_cnt,
-                         uint64_t* next, uint64_t* next_cnt, const uint32_t* tY, const uint32_t* tG);
-__global__ void __launch_bounds__(128) k_bisect_leaves(const TreeArgs a, const uint64_t* front, const uint64_t* front_cnt, const uint32_t* tY,
-                                const uint32_t* tG, uint8_t* invalid);
+// The descent's state on the device: three failing-node lists with their counters (rotated
+// by step), two level words.  Node (l, k) of the tree, l >= 1, is at M - (M >> (l - 1)) + k
+// in the node arrays (levels 1 .. l-1 come first).
+struct BisectState {
+  uint64_t* fail[3];
+  uint64_t* cnt;     // 3 counters
+  int* level;        // 2 words
+};
+// Resident blocks per SM the descent is compiled for (its checks are latency-bound chains of
+// point additions: more warps per SM hide more of it, at the cost of registers).
+#ifndef POSLO_BISECT_MINB
+#define POSLO_BISECT_MINB 2
+#endif
+#ifndef POSLO_BISECT_WAVES
+#define POSLO_BISECT_WAVES 1   // the descent's grid: this many waves of resident blocks
+#endif
+__global__ void __launch_bounds__(128, POSLO_BISECT_MINB) k_bisect_step(const TreeArgs a, BisectState st, int step,
+                                                     const uint32_t* tY, const uint32_t* tG, uint8_t* invalid);
+__global__ void k_gather_flagged(const uint32_t* pts, const uint32_t* z, const uint8_t* badR, const uint64_t* idx,
+                                 uint64_t cnt, uint32_t* gp, uint32_t* gz, uint8_t* gs);
+__global__ void k_point_diff(const uint32_t* a, const uint32_t* b, uint32_t* out);
 __global__ void __launch_bounds__(kHashThreads) k_weighted_sums(const uint8_t* e, const uint8_t* s, const uint32_t* z, const uint8_t* skip1,
                                 const uint8_t* skip2, uint64_t n, unsigned long long* partial);
 __global__ void __launch_bounds__(kPointThreads) k_pts_sum(const uint32_t* pts, const uint8_t* skip1, const uint8_t* skip2, uint64_t n,
@@ -720,6 +737,13 @@ __global__ void k_encode_ext(const uint32_t* point, uint8_t* out);
 void launch_epoch_seeds_multi(int inst, unsigned grid, unsigned block, cudaStream_t st, const DsNode* ds_all,
                               const uint32_t* ds_off, const uint64_t* seed_off, const uint64_t* e0, uint32_t n_dev,
                               uint32_t* seeds, uint32_t* status);
+constexpr uint64_t kGatherChunk = 1ull << 16;   // bytes of one chunk of the staging gather
+struct GatherRegion {
+  const uint8_t* src;   // device-readable (mapped page-locked host memory)
+  uint8_t* dst;         // device memory
+  uint64_t bytes;
+};
+__global__ void __launch_bounds__(256) k_stage_gather(const GatherRegion* regions, uint32_t n_regions);
 __global__ void k_rebase_offs(const uint64_t* raw, const uint64_t* slot, const uint64_t* start,
                               const uint64_t* msg_base, uint32_t n_dev, uint64_t* out, uint32_t* status);
 #ifndef POSLO_SEG_THREADS

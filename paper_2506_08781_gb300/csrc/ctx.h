@@ -15,6 +15,8 @@
 
 namespace poslo_host {
 
+constexpr size_t kSmallHostBytes = 4096;   // page-locked scratch of a context for small transfers
+
 struct DevBuf {
   void* p = nullptr;
   size_t cap = 0;
@@ -75,6 +77,7 @@ struct poslo_ctx {
   uint32_t* tableG = nullptr;     // fixed-window table of G (64 KiB)
   uint32_t* status = nullptr;     // device status word
   uint32_t* h_status = nullptr;   // pinned mirror
+  uint8_t* h_small = nullptr;     // pinned, kSmallHostBytes: small results and shard records
   std::string err;
   bool profiling = false;
   uint64_t launch_count = 0;      // kernels launched by this context
@@ -90,6 +93,7 @@ struct poslo_ctx {
   uint64_t graph_captures = 0, graph_replays = 0;
   poslo_host::GraphSlot g_multi;  // poslo_aver_multi up to its combined check
   poslo_host::GraphSlot g_distill;   // poslo_distill up to its weighted check
+  poslo_host::GraphSlot g_partial;   // poslo_aver_partial up to its record
   poslo_host::KeyCache keys;         // window tables of recently used keys
 };
 
@@ -117,6 +121,13 @@ struct ReqView {
   uint64_t n;
   const uint8_t* s;
   const uint8_t* R;
+  // When all four arrays are page-locked host memory mapped into the device's address space,
+  // their device addresses (the staging then reads them with one gather kernel instead of a
+  // copy per array); null otherwise.
+  const uint8_t* d_msgs = nullptr;
+  const uint64_t* d_offs = nullptr;
+  const uint8_t* d_s = nullptr;
+  const uint8_t* d_R = nullptr;
 };
 // Copies the requests' inputs one by one into device staging buffers of ctx (the messages
 // back to back, offsets rebased on the device) and points mb's msgs, offs, s, R at them

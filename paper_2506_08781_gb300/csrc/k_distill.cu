@@ -3,8 +3,8 @@
 //
 // The subsets are the nodes of a segment tree over the entries: node (l, k) aggregates
 // entries [k 2^l, (k+1) 2^l) as (sum R_t, sum e_t mod q, sum s_t mod q).  A node is checked
-// with the paper's aggregate equation [8](R - eY - sG) = O; the children of failing nodes
-// form the next frontier, down to single entries.  Unit sums can hide a pair of invalid
+// with the paper's aggregate equation [8](R - eY - sG) = O; the descendants of failing nodes
+// (one or several levels down) are checked next, down to single entries.  Unit sums can hide a pair of invalid
 // entries whose errors cancel, so the host confirms the rest of the batch with the weighted
 // check afterwards and falls back to per-entry checks of everything when that fails.
 #include "common.cuh"
@@ -76,11 +76,31 @@ __global__ void __launch_bounds__(128) k_tree_level(const TreeArgs a, uint64_t i
   sc_store(a.tree_s + 32 * o, sc_add(sc_load(a.tree_s + 32 * c0), sc_load(a.tree_s + 32 * c1)));
 }
 
-// Signed 4-bit digit of window w (carry recomputed from the low windows).
-__device__ __forceinline__ int digit_at(const uint32_t k[8], int w) {
-  int carry = 0, d = 0;
-  for (int i = 0; i <= w; ++i) d = sc_digit4(k, i, carry);
-  return d;
+// Lane l's two signed 4-bit digits (windows 2l and 2l+1) of the recoding of sc_digit4, with
+// the carries of the lower windows from a warp scan instead of a walk over them: a window
+// generates a carry when its nibble is 8 or more and propagates the incoming one when it is
+// 7, so the carry into lane l is the scan of (generate, propagate) over lanes 0 .. l-1.
+__device__ __forceinline__ void lane_digits(const uint32_t k[8], int lane, int& d0, int& d1) {
+  uint32_t word = 0;                                         // windows 2l, 2l+1 = byte (l & 3) of word l / 4
+#pragma unroll
+  for (int i = 0; i < 8; ++i) word = i == (lane >> 2) ? k[i] : word;   // (no dynamic register index)
+  const int n0 = (int)((word >> (8 * (lane & 3))) & 15u), n1 = (int)((word >> (8 * (lane & 3) + 4)) & 15u);
+  uint32_t G = (n1 >= 8) | ((n1 == 7) & (n0 >= 8)), P = (n1 == 7) & (n0 == 7);
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t Gp = __shfl_up_sync(0xffffffffu, G, o), Pp = __shfl_up_sync(0xffffffffu, P, o);
+    if (lane >= o) {
+      G = G | (P & Gp);
+      P = P & Pp;
+    }
+  }
+  const uint32_t up = __shfl_up_sync(0xffffffffu, G, 1);
+  int carry = lane ? (int)up : 0;
+  d0 = n0 + carry;
+  carry = d0 >= 8 ? 1 : 0;
+  d0 -= carry << 4;
+  d1 = n1 + carry;
+  d1 -= (d1 >= 8 ? 1 : 0) << 4;
 }
 
 // [8](P - eY - sG) = O evaluated by one warp: lane l adds the table terms of windows 2l and
@@ -89,9 +109,12 @@ __device__ __forceinline__ bool warp_check(const ge& P, const sc& e, const sc& s
                                            const uint32_t* tG) {
   const int lane = threadIdx.x & 31;
   const int w0 = 2 * lane, w1 = w0 + 1;
-  ge acc = ge_add(table_pick(tY, w0, digit_at(e.v, w0)), table_pick(tY, w1, digit_at(e.v, w1)));
-  acc = ge_add(acc, table_pick(tG, w0, digit_at(s.v, w0)));
-  acc = ge_add(acc, table_pick(tG, w1, digit_at(s.v, w1)));
+  int de0, de1, ds0, ds1;
+  lane_digits(e.v, lane, de0, de1);
+  lane_digits(s.v, lane, ds0, ds1);
+  ge acc = ge_add(table_pick(tY, w0, de0), table_pick(tY, w1, de1));
+  acc = ge_add(acc, table_pick(tG, w0, ds0));
+  acc = ge_add(acc, table_pick(tG, w1, ds1));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     ge other;
@@ -102,45 +125,148 @@ __device__ __forceinline__ bool warp_check(const ge& P, const sc& e, const sc& s
   return ge_is_identity(ge_mul_cofactor(ge_sub(P, acc)));
 }
 
-// One frontier level: each warp checks nodes of level `lvl`; failing nodes push their
-// children (level lvl-1) to the next frontier, or their entries to the leaf frontier when
-// lvl == 1.
-__global__ void __launch_bounds__(128) k_bisect(const TreeArgs a, int lvl, uint64_t lvl_off, const uint64_t* front,
-                                                const uint64_t* front_cnt, uint64_t* next, uint64_t* next_cnt,
-                                                const uint32_t* tY, const uint32_t* tG) {
-  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  const uint64_t cnt = *front_cnt;
-  for (uint64_t f = warp; f < cnt; f += nwarps) {
-    const uint64_t k = front[f];
-    const uint64_t node = lvl_off + k;
-    const ge P = ge_load(a.tree_pts + 32 * node);
-    const sc e = sc_load(a.tree_e + 32 * node), s = sc_load(a.tree_s + 32 * node);
-    const bool ok = warp_check(P, e, s, tY, tG);
-    if (!ok && (threadIdx.x & 31) == 0) {
-      const uint64_t pos = atomicAdd(reinterpret_cast<unsigned long long*>(next_cnt), 2ull);
-      next[pos] = 2 * k;
-      next[pos + 1] = 2 * k + 1;
+// [8](P - eY - sG) = O evaluated by a group of 8 lanes (lanes 8g .. 8g+7 of the warp hold the
+// same P, e, s; four groups check four nodes at once).  Lane r of the group takes word r of
+// each scalar, i.e. the 8 windows 8r .. 8r+7: it recodes them into signed 4-bit digits (the
+// carry into its first window from a scan over the group's lower lanes, as in lane_digits),
+// adds their 16 table terms, and a shuffle tree over the group sums the 8 partial points.
+// Fewer lanes per check than warp_check, so fewer instructions per check: each lane's chain is
+// longer (15 additions instead of 3), but the work of the tree and of the final check is shared
+// by 8 lanes instead of 32.  Every lane of the group returns the same answer.
+__device__ __forceinline__ void group8_digits(uint32_t word, int r, int8_t d[8]) {
+  uint32_t G = 0, Pp = 1;   // carry out of this lane's 8 windows with no carry in; all-7 propagate
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const uint32_t n = (word >> (4 * i)) & 15u;
+    G = (n >= 8) | ((n == 7) & G);
+    Pp &= (n == 7);
+  }
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) {
+    const uint32_t Gu = __shfl_up_sync(0xffffffffu, G, o, 8), Pu = __shfl_up_sync(0xffffffffu, Pp, o, 8);
+    if (r >= o) {
+      G = G | (Pp & Gu);
+      Pp = Pp & Pu;
     }
   }
-  (void)lvl;
+  const uint32_t up = __shfl_up_sync(0xffffffffu, G, 1, 8);
+  int carry = r ? (int)up : 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    int v = (int)((word >> (4 * i)) & 15u) + carry;
+    carry = v >= 8 ? 1 : 0;
+    d[i] = (int8_t)(v - (carry << 4));
+  }
 }
 
-// Leaf frontier: single-entry checks; failing entries are marked invalid.
-__global__ void __launch_bounds__(128) k_bisect_leaves(const TreeArgs a, const uint64_t* front,
-                                                       const uint64_t* front_cnt, const uint32_t* tY,
-                                                       const uint32_t* tG, uint8_t* invalid) {
+__device__ __forceinline__ bool group8_check(const ge& P, const sc& e, const sc& s, const uint32_t* tY,
+                                             const uint32_t* tG) {
+  const int lane = threadIdx.x & 31, r = lane & 7;
+  uint32_t we = 0, ws = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {   // word r of each scalar (no dynamic register index)
+    we = i == r ? e.v[i] : we;
+    ws = i == r ? s.v[i] : ws;
+  }
+  int8_t de[8], ds[8];
+  group8_digits(we, r, de);
+  group8_digits(ws, r, ds);
+  ge acc = table_pick(tY, 8 * r, de[0]);
+#pragma unroll
+  for (int i = 1; i < 8; ++i) acc = ge_add(acc, table_pick(tY, 8 * r + i, de[i]));
+#pragma unroll
+  for (int i = 0; i < 8; ++i) acc = ge_add(acc, table_pick(tG, 8 * r + i, ds[i]));
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) {
+    ge other;
+    other.X = fe_shfl(acc.X, lane ^ o); other.Y = fe_shfl(acc.Y, lane ^ o);
+    other.Z = fe_shfl(acc.Z, lane ^ o); other.T = fe_shfl(acc.T, lane ^ o);
+    acc = ge_add(acc, other);
+  }
+  return ge_is_identity(ge_mul_cofactor(ge_sub(P, acc)));
+}
+
+// One step of the descent, several levels at a time.  The step reads the failing nodes of
+// level l (state.fail[s % 3], count state.cnt[s % 3], level state.level[s % 2]) and checks
+// their descendants j levels further down, j the largest depth for which all of them fit in
+// one pass of the grid's check slots (4 per warp; at least 1, at most l): with few failing nodes a step jumps
+// many levels, with many it descends one.  Failing descendants go to the next list
+// (state.fail[(s+1) % 3]); at level 0 the descendants are entries, checked on their own, and
+// failing ones are marked invalid.  Each step also clears the counter the step after it will
+// fill, and block 0 publishes the level it reached; a step that starts at level 0 (done)
+// returns at once, so the host issues as many steps as the tree has levels without reading
+// anything back.  Checking the descendants of a failing node directly, instead of its
+// children first, only adds checks of nodes whose ancestors failed: every entry that fails
+// its own check is still found, and entries are flagged only by their own check.
+__global__ void __launch_bounds__(128, POSLO_BISECT_MINB) k_bisect_step(const TreeArgs a, BisectState st, int step,
+                                                     const uint32_t* tY, const uint32_t* tG, uint8_t* invalid) {
+  const int l = st.level[step & 1];
+  const uint64_t* fail_in = st.fail[step % 3];
+  uint64_t* fail_out = st.fail[(step + 1) % 3];
+  unsigned long long* cnt_out = reinterpret_cast<unsigned long long*>(st.cnt + (step + 1) % 3);
+  if (blockIdx.x == 0 && threadIdx.x == 0) st.cnt[(step + 2) % 3] = 0;
+  if (l <= 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) st.level[(step + 1) & 1] = l;
+    return;
+  }
+  const uint64_t F = st.cnt[step % 3];
+  // four checks per warp (one per group of 8 lanes)
+  const uint64_t slots = ((uint64_t)gridDim.x * blockDim.x) >> 3;
+  int j = 1;
+  while (j < l && (F << (j + 1)) <= slots) ++j;
+  const int tl = l - j;
+  if (blockIdx.x == 0 && threadIdx.x == 0) st.level[(step + 1) & 1] = tl;
+  const uint64_t total = F << j;
+  const uint64_t mask = (1ull << j) - 1;
+  // the loop runs the same number of times for all lanes of a warp (the check shuffles across
+  // the warp); a group past the end checks the identity and records nothing
   const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  const uint64_t cnt = *front_cnt;
-  for (uint64_t f = warp; f < cnt; f += nwarps) {
-    const uint64_t t = front[f];
-    ge P;
-    sc e, s;
-    leaf(a, t, P, e, s);
-    const bool ok = warp_check(P, e, s, tY, tG);
-    if (!ok && (threadIdx.x & 31) == 0 && t < a.n) invalid[t] = 1;
+  const uint32_t grp = (threadIdx.x & 31) >> 3;
+  for (uint64_t w0 = 4 * warp; w0 < total; w0 += 4 * nwarps) {
+    const uint64_t w = w0 + grp;
+    const bool live = w < total;
+    const uint64_t k = live ? ((fail_in[w >> j] << j) | (w & mask)) : 0;
+    ge P = ge_identity();
+    sc e = sc_zero(), s = sc_zero();
+    if (live) {
+      if (tl > 0) {
+        const uint64_t node = a.M - (a.M >> (tl - 1)) + k;   // levels 1 .. tl-1 hold M/2 + ... + M/2^(tl-1) nodes
+        P = ge_load(a.tree_pts + 32 * node);
+        e = sc_load(a.tree_e + 32 * node);
+        s = sc_load(a.tree_s + 32 * node);
+      } else {
+        leaf(a, k, P, e, s);
+      }
+    }
+    const bool ok = group8_check(P, e, s, tY, tG);
+    if (live && !ok && (threadIdx.x & 7) == 0) {
+      if (tl > 0) fail_out[atomicAdd(cnt_out, 1ull)] = k;
+      else if (k < a.n) invalid[k] = 1;
+    }
   }
+}
+
+// The flagged entries' rows for the MSM of the confirmation: decoded point (kPtsWords words),
+// weight z_t (4 words) and "point did not decode" (the MSM leaves those out), at the local
+// indices idx[0 .. cnt).
+__global__ void k_gather_flagged(const uint32_t* pts, const uint32_t* z, const uint8_t* badR, const uint64_t* idx,
+                                 uint64_t cnt, uint32_t* gp, uint32_t* gz, uint8_t* gs) {
+  const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= cnt) return;
+  const uint64_t k = idx[t];
+  const uint4* src = reinterpret_cast<const uint4*>(pts + (size_t)kPtsWords * k);
+  uint4* dst = reinterpret_cast<uint4*>(gp + (size_t)kPtsWords * t);
+#pragma unroll
+  for (int i = 0; i < kPtsWords / 4; ++i) dst[i] = src[i];
+  reinterpret_cast<uint4*>(gz)[t] = reinterpret_cast<const uint4*>(z)[k];
+  gs[t] = badR ? badR[k] : 0;
+}
+
+// out = a - b (b = nullptr: out = a), extended points of 32 words.
+__global__ void k_point_diff(const uint32_t* a, const uint32_t* b, uint32_t* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  ge_store(out, b ? ge_sub(ge_load(a), ge_load(b)) : ge_load(a));
 }
 
 // Weighted scalar sums sum z_t e_t, sum z_t s_t over the entries not flagged (same partial

@@ -443,4 +443,70 @@ void launch_epoch_seeds_multi(int inst, unsigned grid, unsigned block, cudaStrea
     k_epoch_seeds_multi<kInstSha><<<grid, block, 0, st>>>(ds_all, ds_off, seed_off, e0, n_dev, seeds, status);
 }
 
+// Staging of requests whose inputs are page-locked host memory the device reads directly:
+// the blocks stride over a table of chunks (source, destination, bytes; no chunk is longer
+// than kGatherChunk, so a large request spreads over many blocks), each copying its chunk in
+// 16-byte words where source and destination agree modulo 16, 8-byte words where they agree
+// modulo 8, and otherwise in 4-byte destination words, each assembled from the two aligned
+// source words it straddles.  (The entries of consecutive requests are back to back in the
+// batch, so the destination's alignment is not the source's in general.)
+template <typename W>
+__device__ __forceinline__ void copy_words(uint8_t* dst, const uint8_t* src, uint64_t len) {
+  constexpr uint64_t B = sizeof(W);
+  const uint64_t lead = (B - (reinterpret_cast<uintptr_t>(dst) & (B - 1))) & (B - 1);
+  const uint64_t head = len < lead ? len : lead;
+  if (threadIdx.x < head) dst[threadIdx.x] = src[threadIdx.x];
+  const uint64_t words = (len - head) / B;
+  const W* s = reinterpret_cast<const W*>(src + head);
+  W* d = reinterpret_cast<W*>(dst + head);
+  uint64_t i = threadIdx.x;
+  for (; i + 3 * blockDim.x < words; i += 4 * blockDim.x) {   // four loads in flight per thread
+    const W a = s[i], b = s[i + blockDim.x], c = s[i + 2 * blockDim.x], e = s[i + 3 * blockDim.x];
+    d[i] = a;
+    d[i + blockDim.x] = b;
+    d[i + 2 * blockDim.x] = c;
+    d[i + 3 * blockDim.x] = e;
+  }
+  for (; i < words; i += blockDim.x) d[i] = s[i];
+  const uint64_t done = head + words * B;
+  if (threadIdx.x < len - done) dst[done + threadIdx.x] = src[done + threadIdx.x];
+}
+
+// dst in aligned 4-byte words whatever the source's alignment: word w of the destination is
+// bytes m .. m+3 of the source's aligned words w, w+1 (m = the source's misalignment).  The
+// second word may extend past the source's last byte, but never past its aligned 4-byte word,
+// so it stays on the same page.
+__device__ __forceinline__ void copy_shifted(uint8_t* dst, const uint8_t* src, uint64_t len) {
+  const uint64_t lead = (4 - (reinterpret_cast<uintptr_t>(dst) & 3)) & 3;
+  const uint64_t head = len < lead ? len : lead;
+  if (threadIdx.x < head) dst[threadIdx.x] = src[threadIdx.x];
+  dst += head;
+  src += head;
+  len -= head;
+  const uint32_t m = (uint32_t)(reinterpret_cast<uintptr_t>(src) & 3);
+  const uint32_t* s0 = reinterpret_cast<const uint32_t*>(src - m);
+  uint32_t* d = reinterpret_cast<uint32_t*>(dst);
+  const uint64_t words = len >> 2;
+  for (uint64_t w = threadIdx.x; w < words; w += blockDim.x) {
+    const uint32_t lo = s0[w];
+    d[w] = m ? __funnelshift_r(lo, s0[w + 1], 8 * m) : lo;
+  }
+  const uint64_t done = words << 2;
+  if (threadIdx.x < len - done) dst[done + threadIdx.x] = src[done + threadIdx.x];
+}
+
+__global__ void __launch_bounds__(256) k_stage_gather(const GatherRegion* regions, uint32_t n_regions) {
+  for (uint32_t g = blockIdx.x; g < n_regions; g += gridDim.x) {
+    const GatherRegion r = regions[g];
+    const uintptr_t x = reinterpret_cast<uintptr_t>(r.src) ^ reinterpret_cast<uintptr_t>(r.dst);
+    if ((x & 15) == 0) {
+      copy_words<uint4>(r.dst, r.src, r.bytes);
+    } else if ((x & 7) == 0) {
+      copy_words<uint2>(r.dst, r.src, r.bytes);
+    } else {
+      copy_shifted(r.dst, r.src, r.bytes);
+    }
+  }
+}
+
 }  // namespace poslo

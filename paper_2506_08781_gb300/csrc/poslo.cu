@@ -27,6 +27,7 @@ using namespace poslo;
 
 using poslo_host::DevBuf;
 using poslo_host::KernelTimer;
+using poslo_host::kSmallHostBytes;
 
 namespace {
 
@@ -935,7 +936,9 @@ int poslo_create(const poslo_params* params, poslo_ctx** out) {
       cudaEventCreateWithFlags(&ctx->ev_staged, cudaEventDisableTiming) != cudaSuccess)
     return bail(POSLO_EDEVICE);
   if (cudaMalloc(&ctx->status, 4) != cudaSuccess) return bail(POSLO_ENOMEM);
-  if (cudaMallocHost(&ctx->h_status, 4) != cudaSuccess) return bail(POSLO_ENOMEM);
+  // page-locked: the status word, then kSmallHostBytes for small results and records
+  if (cudaMallocHost(&ctx->h_status, 256 + kSmallHostBytes) != cudaSuccess) return bail(POSLO_ENOMEM);
+  ctx->h_small = reinterpret_cast<uint8_t*>(ctx->h_status) + 256;
   if (cudaMalloc(&ctx->tableG, 4 * (size_t)kTableWords) != cudaSuccess) return bail(POSLO_ENOMEM);
   cudaMemsetAsync(ctx->status, 0, 4, ctx->s_main);
   if (launch_tables(ctx, ctx->s_main, nullptr, nullptr, nullptr, 1, ctx->tableG, 1, nullptr)) return bail(POSLO_EDEVICE);
@@ -956,6 +959,7 @@ void poslo_destroy(poslo_ctx* ctx) {
   if (ctx->s_copy) cudaStreamSynchronize(ctx->s_copy);
   graph_reset(ctx->g_multi);
   graph_reset(ctx->g_distill);
+  graph_reset(ctx->g_partial);
   for (uint32_t* b : ctx->keys.blocks) cudaFree(b);
   for (auto& kv : ctx->bufs)
     if (kv.second.p) cudaFree(kv.second.p);
@@ -1032,6 +1036,7 @@ int poslo_set_graphs(poslo_ctx* ctx, int enabled) {
     cudaStreamSynchronize(ctx->s_main);
     graph_reset(ctx->g_multi);
     graph_reset(ctx->g_distill);
+    graph_reset(ctx->g_partial);
   }
   return POSLO_OK;
 }
@@ -1386,7 +1391,9 @@ int poslo_aver(poslo_ctx* ctx, const poslo_batch* batch, uint32_t agg_mode, uint
 }
 
 // Shard partials: the aggregate of poslo_aver up to (not including) its group check, as a
-// record other shards of the same log can combine (k_shard.cu).
+// record other shards of the same log can combine (k_shard.cu).  The uploads come first; the
+// rest is a fixed launch sequence that a device-resident batch of the previous call's shape
+// replays from a CUDA graph.
 int poslo_aver_partial(poslo_ctx* ctx, const poslo_batch* batch, uint32_t agg_mode, poslo_partial* out) {
   if (!ctx || !out) return fail(ctx, POSLO_EINVAL, "bad aver_partial arguments");
   int rc;
@@ -1396,90 +1403,123 @@ int poslo_aver_partial(poslo_ctx* ctx, const poslo_batch* batch, uint32_t agg_mo
   if (agg_mode == POSLO_AGG_WEIGHTED && !F) return fail(ctx, POSLO_EINVAL, "weighted aggregation needs POSLO-F");
   if (agg_mode > POSLO_AGG_WEIGHTED) return fail(ctx, POSLO_EINVAL, "bad aggregation mode");
   const bool weighted = agg_mode == POSLO_AGG_WEIGHTED;
+  const uint64_t n = batch->n;
   if ((rc = reset_status(ctx))) return rc;
   Staged sb;
   if ((rc = stage_batch(ctx, batch, sb))) return rc;
-  const uint64_t npts = F ? batch->n : batch->R_count;
+  // uploads: the disclosed seeds
+  std::vector<DsNode> ds_nodes;
+  if ((rc = parse_ds(ctx, batch->ds, batch->ds_nodes, ds_nodes))) return rc;
+  DsNode* d_ds;
+  if ((rc = ensure_t(ctx, "ds", ds_nodes.size() * sizeof(DsNode), &d_ds))) return rc;
+  CU(cudaMemcpyAsync(d_ds, ds_nodes.data(), ds_nodes.size() * sizeof(DsNode), cudaMemcpyHostToDevice, ctx->s_main));
+  uint64_t e_first = 0, ne = 0;
+  if (n) {
+    e_first = batch->first_index / batch->n2;
+    ne = (batch->first_index + n - 1) / batch->n2 - e_first + 1;
+  }
+  // workspace, all of it before any launch (a capture cannot allocate)
+  const uint64_t npts = F ? n : batch->R_count;
   uint32_t* pts = nullptr;
   uint8_t* badR = nullptr;
+  uint32_t *z = nullptr, *seeds;
   if (weighted) {
     if ((rc = ensure_t(ctx, "pts", 4 * kPtsWords * std::max<uint64_t>(npts, 1), &pts))) return rc;
     if ((rc = ensure_t(ctx, "badR", std::max<uint64_t>(npts, 1), &badR))) return rc;
+    if ((rc = ensure_t(ctx, "z", 16 * std::max<uint64_t>(n, 1), &z))) return rc;
   }
   uint32_t* small;   // unit R (32) | weighted R (32) | point bad count (1) | record (kShardWords)
   if ((rc = ensure_t(ctx, "partial_small", 4 * (65 + (size_t)kShardWords), &small))) return rc;
   uint32_t *unitR = small, *Rw = small + 32, *pbad = small + 64, *rec = small + 65;
-  uint32_t *ppart, npb;
-  if ((rc = run_points(ctx, sb.R, npts, pts, badR, &ppart, &npb, ctx->ev_staged))) return rc;
-  if ((rc = run_unit_sum(ctx, ppart, npb, unitR, nullptr, pbad))) return rc;
+  if ((rc = ensure_t(ctx, "seeds", std::max<uint64_t>(1, ne) * 16, &seeds))) return rc;
+  const uint32_t nhb = (uint32_t)grid_for(ctx, n, kHashThreads, 8);
   unsigned long long* hpart;
-  uint32_t nhb;
-  if (!weighted) {
-    if ((rc = run_hash(ctx, batch, sb, nullptr, false, F, nullptr, &hpart, &nhb))) return rc;
-  } else {
-    // as in Distill: the weights z_t first (they need no message), so the MSM's counting sort
-    // runs on the main stream while the messages are hashed on the hashing stream and the
-    // points decoded on the points stream
-    const uint64_t n = batch->n;
-    uint32_t* z;
-    if ((rc = ensure_t(ctx, "z", 16 * std::max<uint64_t>(n, 1), &z))) return rc;
-    uint64_t e_first = 0, ne = 0;
-    if (n) {
-      e_first = batch->first_index / batch->n2;
-      ne = (batch->first_index + n - 1) / batch->n2 - e_first + 1;
-    }
-    uint32_t* seeds;
-    if ((rc = run_epoch_seeds(ctx, batch->ds, batch->ds_nodes, e_first, ne, &seeds))) return rc;
-    ZPre zp;
-    make_zpre(ctx->vseed, zp.w);
-    if (n) {
-      k_weights<<<grid_for(ctx, n, kSideThreads, 8), kSideThreads, 0, ctx->s_main>>>(zp, n, batch->first_index, z);
+  if ((rc = ensure_t(ctx, "hash_partial", (size_t)nhb * kPartialWords * 8, &hpart))) return rc;
+  const bool replayable = batch->on_device != 0;
+  ZPre zp;
+  make_zpre(ctx->vseed, zp.w);
+  HashArgs a{};
+  a.msgs = sb.msgs;
+  a.offs = sb.offs;
+  a.base_off = sb.base_off;
+  a.n = n;
+  a.first_index = batch->first_index;
+  a.e0 = e_first;
+  a.n2 = batch->n2;
+  a.n2_log2 = log2_exact(batch->n2);
+  a.seeds = seeds;
+  a.s = F ? sb.s : nullptr;
+  a.weighted = weighted ? 1u : 0u;
+  for (int q = 0; q < 10; ++q) a.zpre[q] = zp.w[q];
+  a.z_in = z;
+  a.partial = hpart;
+  a.status = ctx->status;
+  auto launch = [&]() -> int {
+    int rc;
+    uint32_t *ppart, npb;
+    if ((rc = run_points(ctx, sb.R, npts, pts, badR, &ppart, &npb, replayable ? nullptr : ctx->ev_staged)))
+      return rc;
+    if ((rc = run_unit_sum(ctx, ppart, npb, unitR, nullptr, pbad))) return rc;
+    if (ne) {
+      cudaEvent_t b, e;
+      timer_begin(ctx, "seeds", ctx->s_main, &b, &e);
+      launch_epoch_seeds((int)ctx->inst, (unsigned)((ne + 127) / 128), 128, ctx->s_main, d_ds, (int)ds_nodes.size(),
+                         e_first, ne, seeds, ctx->status);
       ++ctx->launch_count;
+      CU(cudaGetLastError());
+      timer_end(ctx, "seeds", ctx->s_main, b, e);
     }
-    nhb = (uint32_t)grid_for(ctx, n, kHashThreads, 8);
-    if ((rc = ensure_t(ctx, "hash_partial", (size_t)nhb * kPartialWords * 8, &hpart))) return rc;
-    CU(cudaEventRecord(ctx->ev_main, ctx->s_main));
-    CU(cudaStreamWaitEvent(ctx->s_hash, ctx->ev_main, 0));
-    HashArgs a{};
-    a.msgs = sb.msgs;
-    a.offs = sb.offs;
-    a.base_off = sb.base_off;
-    a.n = n;
-    a.first_index = batch->first_index;
-    a.e0 = e_first;
-    a.n2 = batch->n2;
-    a.n2_log2 = log2_exact(batch->n2);
-    a.seeds = seeds;
-    a.s = sb.s;
-    a.weighted = 1;
-    for (int q = 0; q < 10; ++q) a.zpre[q] = zp.w[q];
-    a.z_in = z;
-    a.partial = hpart;
-    a.status = ctx->status;
-    MsmState ms;
-    if ((rc = run_msm_sort(ctx, ctx->s_main, z, 4, nullptr, n, ms))) return rc;
-    {
-      cudaEvent_t tb, te;
+    cudaEvent_t tb, te;
+    if (!weighted) {
+      timer_begin(ctx, "hash", ctx->s_main, &tb, &te);
+      launch_hash((int)ctx->inst, nhb, ctx->s_main, a);
+      ++ctx->launch_count;
+      CU(cudaGetLastError());
+      timer_end(ctx, "hash", ctx->s_main, tb, te);
+    } else {
+      // as in Distill: the weights z_t first (they need no message), so the MSM's counting
+      // sort runs on the main stream while the messages are hashed on the hashing stream and
+      // the points decoded on the points stream
+      if (n) {
+        k_weights<<<grid_for(ctx, n, kSideThreads, 8), kSideThreads, 0, ctx->s_main>>>(zp, n, batch->first_index, z);
+        ++ctx->launch_count;
+      }
+      CU(cudaEventRecord(ctx->ev_main, ctx->s_main));
+      CU(cudaStreamWaitEvent(ctx->s_hash, ctx->ev_main, 0));
+      MsmState ms;
+      if ((rc = run_msm_sort(ctx, ctx->s_main, z, 4, nullptr, n, ms))) return rc;
       timer_begin(ctx, "hash", ctx->s_hash, &tb, &te);
       launch_hash((int)ctx->inst, nhb, ctx->s_hash, a);
       ++ctx->launch_count;
       CU(cudaGetLastError());
       timer_end(ctx, "hash", ctx->s_hash, tb, te);
+      CU(cudaEventRecord(ctx->ev_hash, ctx->s_hash));
+      CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_decoded, 0));
+      if ((rc = run_msm_finish(ctx, ctx->s_main, pts, badR, ms, Rw))) return rc;
+      CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_hash, 0));
     }
-    CU(cudaEventRecord(ctx->ev_hash, ctx->s_hash));
-    CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_decoded, 0));
-    if ((rc = run_msm_finish(ctx, ctx->s_main, pts, badR, ms, Rw))) return rc;
-    CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_hash, 0));
+    CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_points, 0));
+    timer_begin(ctx, "finalize", ctx->s_main, &tb, &te);
+    k_partial_out<<<1, kShardThreads, 0, ctx->s_main>>>(hpart, nhb, F ? nullptr : sb.s, weighted ? Rw : unitR, pbad,
+                                                        rec);
+    ++ctx->launch_count;
+    CU(cudaGetLastError());
+    timer_end(ctx, "finalize", ctx->s_main, tb, te);
+    return POSLO_OK;
+  };
+  if (replayable) {
+    const MsmPlan plan = msm_plan(ctx, n, 4);
+    const std::vector<uint64_t> sig = {n, batch->n2, batch->first_index, reinterpret_cast<uint64_t>(sb.msgs),
+                                       reinterpret_cast<uint64_t>(sb.offs), reinterpret_cast<uint64_t>(sb.s),
+                                       reinterpret_cast<uint64_t>(sb.R), sb.base_off, ds_nodes.size(),
+                                       (uint64_t)plan.c, (uint64_t)plan.seg_log2, ctx->inst, agg_mode,
+                                       batch->variant, batch->R_count};
+    rc = run_replayable(ctx, ctx->g_partial, sig, launch);
+  } else {
+    rc = launch();
   }
-  CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_points, 0));
-  cudaEvent_t tb, te;
-  timer_begin(ctx, "finalize", ctx->s_main, &tb, &te);
-  k_partial_out<<<1, kShardThreads, 0, ctx->s_main>>>(hpart, nhb, F ? nullptr : sb.s, weighted ? Rw : unitR, pbad,
-                                                      rec);
-  ++ctx->launch_count;
-  CU(cudaGetLastError());
-  timer_end(ctx, "finalize", ctx->s_main, tb, te);
-  uint32_t h[kShardWords];
+  if (rc != POSLO_OK) return rc;
+  uint32_t* h = reinterpret_cast<uint32_t*>(ctx->h_small);   // page-locked: no staging, one sync
   CU(cudaMemcpyAsync(h, rec, 4 * kShardWords, cudaMemcpyDeviceToHost, ctx->s_main));
   if ((rc = check_status(ctx))) return rc;
   memcpy(out->e, h, 32);
@@ -1525,7 +1565,16 @@ int poslo_combine_check(poslo_ctx* ctx, const uint8_t Y[32], const poslo_partial
   if ((rc = ensure_t(ctx, "combine_parts", sizeof(poslo_partial) * (size_t)n_parts, &d_parts))) return rc;
   if ((rc = ensure_t(ctx, "combine_total", sizeof(poslo_partial), &d_total))) return rc;
   if ((rc = ensure_t(ctx, "accept", 16, &d_acc))) return rc;
-  CU(cudaMemcpyAsync(d_parts, parts, sizeof(poslo_partial) * (size_t)n_parts, cudaMemcpyHostToDevice, ctx->s_main));
+  // the records go through the page-locked area when they fit (the copy is then asynchronous)
+  const size_t rec_bytes = sizeof(poslo_partial) * (size_t)n_parts;
+  const bool via_small = rec_bytes + sizeof(poslo_partial) + 16 <= kSmallHostBytes;
+  if (via_small) {
+    memcpy(ctx->h_small + sizeof(poslo_partial) + 16, parts, rec_bytes);
+    CU(cudaMemcpyAsync(d_parts, ctx->h_small + sizeof(poslo_partial) + 16, rec_bytes, cudaMemcpyHostToDevice,
+                       ctx->s_main));
+  } else {
+    CU(cudaMemcpyAsync(d_parts, parts, rec_bytes, cudaMemcpyHostToDevice, ctx->s_main));
+  }
   if (built) CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_table, 0));   // the table this call built
   cudaEvent_t tb, te;
   timer_begin(ctx, "finalize", ctx->s_main, &tb, &te);
@@ -1534,13 +1583,12 @@ int poslo_combine_check(poslo_ctx* ctx, const uint8_t Y[32], const poslo_partial
   ++ctx->launch_count;
   CU(cudaGetLastError());
   timer_end(ctx, "finalize", ctx->s_main, tb, te);
-  uint32_t h[kShardWords];
-  uint8_t h_acc = 0;
+  uint32_t* h = reinterpret_cast<uint32_t*>(ctx->h_small);   // total record, then the accept byte
   CU(cudaMemcpyAsync(h, d_total, 4 * kShardWords, cudaMemcpyDeviceToHost, ctx->s_main));
-  CU(cudaMemcpyAsync(&h_acc, d_acc, 1, cudaMemcpyDeviceToHost, ctx->s_main));
+  CU(cudaMemcpyAsync(ctx->h_small + sizeof(poslo_partial), d_acc, 1, cudaMemcpyDeviceToHost, ctx->s_main));
   if ((rc = check_status(ctx))) return rc;
   kforget.armed = false;   // the key decoded: its table is sound
-  *accept = h_acc;
+  *accept = ctx->h_small[sizeof(poslo_partial)];
   if (total) {
     memcpy(total->e, h, 32);
     memcpy(total->s, h + 8, 32);
@@ -1762,42 +1810,48 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
     timer_begin(ctx, "tree", ctx->s_main, &tb, &te);
     k_tree_leaves<<<(unsigned)((M / 2 + 127) / 128), 128, 0, ctx->s_main>>>(ta);
     ++ctx->launch_count;
-    std::vector<uint64_t> lvl_off(L + 1, 0);
-    lvl_off[1] = 0;
-    for (uint64_t l = 2; l <= L; ++l) {
-      lvl_off[l] = lvl_off[l - 1] + (M >> (l - 1));
+    for (uint64_t l = 2; l <= L; ++l) {   // level l from level l - 1 (node (l, k) at M - (M >> (l - 1)) + k)
       const uint64_t count = M >> l;
-      k_tree_level<<<(unsigned)((count + 127) / 128), 128, 0, ctx->s_main>>>(ta, lvl_off[l - 1], lvl_off[l], count);
+      k_tree_level<<<(unsigned)((count + 127) / 128), 128, 0, ctx->s_main>>>(ta, M - (M >> (l - 2)),
+                                                                             M - (M >> (l - 1)), count);
       ++ctx->launch_count;
     }
     CU(cudaGetLastError());
     timer_end(ctx, "tree", ctx->s_main, tb, te);
-    uint64_t *fa, *fb, *cnts;
-    if ((rc = ensure_t(ctx, "front_a", 8 * M, &fa))) return rc;
-    if ((rc = ensure_t(ctx, "front_b", 8 * M, &fb))) return rc;
-    if ((rc = ensure_t(ctx, "front_cnt", 16, &cnts))) return rc;
-    // frontier = {root}
-    const uint64_t init[2] = {0, 1};
-    CU(cudaMemcpyAsync(fa, init, 8, cudaMemcpyHostToDevice, ctx->s_main));
-    CU(cudaMemcpyAsync(cnts, init + 1, 8, cudaMemcpyHostToDevice, ctx->s_main));
+    // descent from the root (taken as failing: the weighted check of the batch failed), several
+    // levels per step while few nodes fail (k_bisect_step); state on the device, no round trip
+    uint64_t* fl;
+    uint64_t* cnts;
+    int* lvls;
+    if ((rc = ensure_t(ctx, "front_lists", 3 * 8 * M, &fl))) return rc;
+    if ((rc = ensure_t(ctx, "front_cnt", 3 * 8 + 2 * 4, &cnts))) return rc;
+    lvls = reinterpret_cast<int*>(cnts + 3);
+    BisectState bst{};
+    bst.fail[0] = fl;
+    bst.fail[1] = fl + M;
+    bst.fail[2] = fl + 2 * M;
+    bst.cnt = cnts;
+    bst.level = lvls;
+    struct {
+      uint64_t cnt[3];
+      int level[2];
+    } init = {{1, 0, 0}, {(int)L, (int)L}};
+    static_assert(sizeof(init) == 3 * 8 + 2 * 4, "descent state layout");
+    CU(cudaMemsetAsync(fl, 0, 8, ctx->s_main));   // the root's index, 0
+    CU(cudaMemcpyAsync(cnts, &init, sizeof(init), cudaMemcpyHostToDevice, ctx->s_main));
     // invalid starts as the malformed entries
     k_flags_or<<<grid_for(ctx, n, 256, 4), 256, 0, ctx->s_main>>>(badR, badS, nullptr, n, inv);
     ++ctx->launch_count;
-    const int bgrid = ctx->sm_count * 8;
+    // POSLO_BISECT_WAVES waves of resident blocks: a step checks at most as many nodes as the
+    // grid has warps
+    int bres = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bres, k_bisect_step, 128, 0) != cudaSuccess || bres < 1) bres = 1;
+    const int bgrid = ctx->sm_count * bres * POSLO_BISECT_WAVES;
     timer_begin(ctx, "bisect", ctx->s_main, &tb, &te);
-    uint64_t* cur = fa;
-    uint64_t* nxt = fb;
-    for (uint64_t l = L; l >= 1; --l) {
-      uint64_t* cur_cnt = cnts + ((L - l) & 1);
-      uint64_t* nxt_cnt = cnts + ((L - l + 1) & 1);
-      CU(cudaMemsetAsync(nxt_cnt, 0, 8, ctx->s_main));
-      k_bisect<<<bgrid, 128, 0, ctx->s_main>>>(ta, (int)l, lvl_off[l], cur, cur_cnt, nxt, nxt_cnt, tableY,
-                                               ctx->tableG);
+    for (int step = 0; step < (int)L; ++step) {
+      k_bisect_step<<<bgrid, 128, 0, ctx->s_main>>>(ta, bst, step, tableY, ctx->tableG, inv);
       ++ctx->launch_count;
-      std::swap(cur, nxt);
     }
-    k_bisect_leaves<<<bgrid, 128, 0, ctx->s_main>>>(ta, cur, cnts + (L & 1), tableY, ctx->tableG, inv);
-    ++ctx->launch_count;
     CU(cudaGetLastError());
     timer_end(ctx, "bisect", ctx->s_main, tb, te);
     // ---- confirmation: weighted check of every entry not flagged ----
@@ -1806,7 +1860,38 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
     if ((rc = ensure_t(ctx, "w_partial", (size_t)wblocks * kPartialWords * 8, &wpart))) return rc;
     k_weighted_sums<<<wblocks, kHashThreads, 0, ctx->s_main>>>(d_e, sb.s, z, inv, nullptr, n, wpart);
     ++ctx->launch_count;
-    if ((rc = run_msm(ctx, ctx->s_main, pts, z, 4, inv, n, Rw))) return rc;
+    // sum over the unflagged entries of [z_t]R_t = the whole batch's sum (Horner over the window
+    // sums the first weighted check left behind; undecodable points are not in it) minus the
+    // flagged entries' with decodable points (an MSM over the flagged entries alone)
+    {
+      timer_begin(ctx, "confirm", ctx->s_main, &tb, &te);
+      const MsmPlan pl1 = msm_plan(ctx, n, 4);
+      uint32_t *groups1, *Wc;
+      if ((rc = ensure_t(ctx, "msm_groups", 128 * (size_t)pl1.windows * (1 + pl1.jbits), &groups1))) return rc;
+      if ((rc = ensure_t(ctx, "confirm_pts", 4 * 96, &Wc))) return rc;
+      k_msm_final<<<1, 32, 0, ctx->s_main>>>(groups1, pl1, Wc);
+      ++ctx->launch_count;
+      uint64_t* fidx;
+      if ((rc = ensure_t(ctx, "confirm_idx", 8 * (n + 1), &fidx))) return rc;
+      if ((rc = run_compact(ctx, inv, n, 0, fidx, n, fidx + n))) return rc;
+      uint64_t nf = 0;
+      CU(cudaMemcpyAsync(&nf, fidx + n, 8, cudaMemcpyDeviceToHost, ctx->s_main));
+      CU(cudaStreamSynchronize(ctx->s_main));
+      if (nf) {
+        uint32_t *gp, *gz;
+        uint8_t* gs;
+        if ((rc = ensure_t(ctx, "confirm_gpts", 4 * kPtsWords * nf, &gp))) return rc;
+        if ((rc = ensure_t(ctx, "confirm_gz", 16 * nf, &gz))) return rc;
+        if ((rc = ensure_t(ctx, "confirm_gskip", nf, &gs))) return rc;
+        k_gather_flagged<<<(unsigned)((nf + 127) / 128), 128, 0, ctx->s_main>>>(pts, z, badR, fidx, nf, gp, gz, gs);
+        ++ctx->launch_count;
+        if ((rc = run_msm(ctx, ctx->s_main, gp, gz, 4, gs, nf, Wc + 32))) return rc;
+      }
+      k_point_diff<<<1, 32, 0, ctx->s_main>>>(Wc, nf ? Wc + 32 : nullptr, Rw);
+      ++ctx->launch_count;
+      CU(cudaGetLastError());
+      timer_end(ctx, "confirm", ctx->s_main, tb, te);
+    }
     if ((rc = run_finalize(ctx, wpart, wblocks, nullptr, 0, Rw, nullptr, tableY, d_acc, nullptr))) return rc;
     uint8_t confirmed = 0;
     CU(cudaMemcpyAsync(&confirmed, d_acc, 1, cudaMemcpyDeviceToHost, ctx->s_main));
@@ -2327,14 +2412,36 @@ int poslo_host::stage_requests(poslo_ctx* ctx, const ReqView* reqs, uint32_t nd,
   if ((rc = ensure_t(ctx, "sv_R", 32 * std::max<uint64_t>(N, 1), &Rv))) return rc;
   if ((rc = ensure_t(ctx, "sv_meta", 8 * meta.size(), &d_meta))) return rc;
   cudaStream_t st = ctx->s_main;
+  // requests in mapped page-locked memory: one gather kernel over a table of regions; the
+  // others: one copy per array
+  std::vector<GatherRegion> regions;
   for (uint32_t d = 0; d < nd; ++d) {
     const ReqView& r = reqs[d];
     if (r.n == 0) continue;
     const uint64_t lo = r.offs[0], len = r.offs[r.n] - lo;
+    if (r.d_msgs && r.d_offs && r.d_s && r.d_R) {
+      auto add = [&](const uint8_t* src, uint8_t* dst, uint64_t bytes) {
+        for (uint64_t o = 0; o < bytes; o += kGatherChunk)
+          regions.push_back(GatherRegion{src + o, dst + o, std::min<uint64_t>(kGatherChunk, bytes - o)});
+      };
+      add(r.d_msgs + lo, msgs + base[d], len);
+      add(reinterpret_cast<const uint8_t*>(r.d_offs), reinterpret_cast<uint8_t*>(raw + slot[d]), 8 * (r.n + 1));
+      add(r.d_s, sv + 32 * start[d], 32 * r.n);
+      add(r.d_R, Rv + 32 * start[d], 32 * r.n);
+      continue;
+    }
     if (len) CU(cudaMemcpyAsync(msgs + base[d], r.msgs + lo, len, cudaMemcpyHostToDevice, st));
     CU(cudaMemcpyAsync(raw + slot[d], r.offs, 8 * (r.n + 1), cudaMemcpyHostToDevice, st));
     CU(cudaMemcpyAsync(sv + 32 * start[d], r.s, 32 * r.n, cudaMemcpyHostToDevice, st));
     CU(cudaMemcpyAsync(Rv + 32 * start[d], r.R, 32 * r.n, cudaMemcpyHostToDevice, st));
+  }
+  if (!regions.empty()) {
+    GatherRegion* d_reg;
+    if ((rc = ensure_t(ctx, "sv_regions", sizeof(GatherRegion) * regions.size(), &d_reg))) return rc;
+    CU(cudaMemcpyAsync(d_reg, regions.data(), sizeof(GatherRegion) * regions.size(), cudaMemcpyHostToDevice, st));
+    const unsigned grid = (unsigned)std::min<size_t>(regions.size(), (size_t)ctx->sm_count * 8);
+    k_stage_gather<<<grid, 256, 0, st>>>(d_reg, (uint32_t)regions.size());
+    ++ctx->launch_count;
   }
   CU(cudaMemcpyAsync(d_meta, meta.data(), 8 * meta.size(), cudaMemcpyHostToDevice, st));
   CU(cudaMemsetAsync(offs, 0, 8, st));   // an empty batch still has offs[0] = 0

@@ -44,8 +44,17 @@ struct Req {
   std::chrono::steady_clock::time_point t_submit, t_done;
 };
 
+// One served batch on the service's clock (ns since poslo_serve_start).
+struct BatchRecord {
+  uint32_t worker = 0, requests = 0;
+  uint64_t entries = 0;
+  uint64_t t_take = 0, t_staged = 0, t_checked = 0, t_done = 0;
+};
+
 struct Server {
   poslo_ctx* owner = nullptr;
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  std::vector<BatchRecord> timeline;   // drained by poslo_serve_timeline (bounded)
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<Req*> pending;
@@ -72,7 +81,28 @@ namespace {
 // workspace of the multi-device path (decoded points, e, z, flags, MSM sort and segments).
 uint64_t request_charge(uint64_t n, uint64_t msg_bytes) { return msg_bytes + n * 640 + 4096; }
 
-void run_batch(Server* S, poslo_ctx* w, std::vector<Req*>& batch) {
+// The device address of page-locked host memory mapped into the device's address space, or
+// null (pageable or unknown memory, which is staged by copies instead).
+const void* mapped_address(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
+uint64_t since(const Server* S) {
+  return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now() - S->t0)
+      .count();
+}
+
+constexpr size_t kMaxTimeline = 1u << 20;   // records kept between two reads
+
+void run_batch(Server* S, poslo_ctx* w, uint32_t worker, std::vector<Req*>& batch) {
+  BatchRecord rec;
+  rec.worker = worker;
+  rec.t_take = since(S);
   const uint32_t nd = (uint32_t)batch.size();
   std::vector<uint8_t> Y(32 * (size_t)nd), ds;
   std::vector<uint64_t> start(nd + 1, 0), first(nd);
@@ -109,6 +139,9 @@ void run_batch(Server* S, poslo_ctx* w, std::vector<Req*>& batch) {
   mb.ds_off = ds_off.data();
   // each request's inputs go straight from its own buffers into the worker's device staging
   int rc = stage_requests(w, views.data(), nd, &mb);
+  rec.t_staged = since(S);
+  rec.requests = nd;
+  rec.entries = total;
   std::vector<uint8_t> acc(nd);
   std::vector<uint64_t> pairs(2 * std::max<uint64_t>(total, 1));
   uint64_t cnt = 0;
@@ -139,6 +172,7 @@ void run_batch(Server* S, poslo_ctx* w, std::vector<Req*>& batch) {
     S->cv_done.notify_all();
   };
   if (rc == POSLO_OK) rc = aver_multi(w, &mb, tabs.data(), acc.data(), pairs.data(), total, &cnt, &settled);
+  rec.t_checked = since(S);
   std::vector<int> rcs(nd, rc);
   std::vector<std::vector<uint64_t>> inv(nd);
   if (rc == POSLO_OK) {
@@ -187,9 +221,11 @@ void run_batch(Server* S, poslo_ctx* w, std::vector<Req*>& batch) {
   }
   S->batches += 1;
   S->batched_requests += nd;
+  rec.t_done = since(S);
+  if (S->timeline.size() < kMaxTimeline) S->timeline.push_back(rec);
 }
 
-void worker_loop(Server* S, poslo_ctx* w) {
+void worker_loop(Server* S, poslo_ctx* w, uint32_t worker) {
   cudaSetDevice(w->device);
   for (;;) {
     std::vector<Req*> batch;
@@ -207,7 +243,7 @@ void worker_loop(Server* S, poslo_ctx* w) {
         ent += r->n;
       }
     }
-    run_batch(S, w, batch);
+    run_batch(S, w, worker, batch);
     S->cv_done.notify_all();
   }
 }
@@ -261,7 +297,8 @@ int poslo_serve_start(poslo_ctx* ctx, uint32_t workers, uint32_t max_batch_devic
     }
     S->wctx.push_back(w);
   }
-  for (poslo_ctx* w : S->wctx) S->workers.emplace_back(poslo_host::worker_loop, S, w);
+  for (uint32_t k = 0; k < (uint32_t)S->wctx.size(); ++k)
+    S->workers.emplace_back(poslo_host::worker_loop, S, S->wctx[k], k);
   ctx->server = S;
   return POSLO_OK;
 }
@@ -329,6 +366,16 @@ int poslo_submit(poslo_ctx* ctx, const poslo_request* q, uint64_t* ticket) {
     if (q->n == 0) {
       r->offs.assign(1, 0);
       r->view.offs = r->offs.data();
+    } else {
+      // page-locked buffers the device can read are staged by a gather kernel
+      const void *dm = poslo_host::mapped_address(q->msgs + lo), *d_o = poslo_host::mapped_address(q->offs),
+                 *d_s = poslo_host::mapped_address(q->s), *d_R = poslo_host::mapped_address(q->R);
+      if (dm && d_o && d_s && d_R) {
+        r->view.d_msgs = static_cast<const uint8_t*>(dm) - lo;
+        r->view.d_offs = static_cast<const uint64_t*>(d_o);
+        r->view.d_s = static_cast<const uint8_t*>(d_s);
+        r->view.d_R = static_cast<const uint8_t*>(d_R);
+      }
     }
   } else {
     r->msgs.assign(q->msgs ? q->msgs + lo : nullptr, q->msgs ? q->msgs + hi : nullptr);
@@ -382,6 +429,26 @@ int poslo_serve_stats(poslo_ctx* ctx, uint64_t* batches, uint64_t* requests, uin
   if (batches) *batches = S->batches;
   if (requests) *requests = S->batched_requests;
   if (bytes_in_use) *bytes_in_use = S->used;
+  return POSLO_OK;
+}
+
+int poslo_serve_timeline(poslo_ctx* ctx, poslo_batch_record* out, uint64_t cap, uint64_t* n) {
+  if (!ctx || !ctx->server || !n || (cap && !out)) return POSLO_EINVAL;
+  Server* S = ctx->server;
+  std::lock_guard<std::mutex> lock(S->mu);
+  const uint64_t k = std::min<uint64_t>(cap, S->timeline.size());
+  for (uint64_t i = 0; i < k; ++i) {
+    const poslo_host::BatchRecord& r = S->timeline[i];
+    out[i].worker = r.worker;
+    out[i].requests = r.requests;
+    out[i].entries = r.entries;
+    out[i].t_take_ns = r.t_take;
+    out[i].t_staged_ns = r.t_staged;
+    out[i].t_checked_ns = r.t_checked;
+    out[i].t_done_ns = r.t_done;
+  }
+  *n = k;
+  S->timeline.erase(S->timeline.begin(), S->timeline.begin() + (ptrdiff_t)k);
   return POSLO_OK;
 }
 

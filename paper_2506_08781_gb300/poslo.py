@@ -33,7 +33,7 @@ EXPORTS = [
     "poslo_set_multi_window_limit", "poslo_set_key_cache", "poslo_key_cache_stats",
     "poslo_hash_entries_noalloc", "poslo_aver_multi", "poslo_distill_c", "poslo_sebver_c", "poslo_distill_stream",
     "poslo_serve_start", "poslo_serve_stop", "poslo_register_key", "poslo_submit", "poslo_poll",
-    "poslo_serve_stats", "poslo_aver_partial", "poslo_combine_check",
+    "poslo_serve_stats", "poslo_aver_partial", "poslo_combine_check", "poslo_serve_timeline",
 ]
 POSLO_PENDING = 1
 POSLO_EBUFSMALL = -5
@@ -69,6 +69,13 @@ class Partial(C.Structure):
         if len(b) != C.sizeof(cls):
             raise ValueError("a poslo_partial record is 216 bytes")
         return cls.from_buffer_copy(b)
+
+
+class BatchRecord(C.Structure):
+    """poslo_batch_record: one served batch on the service's clock (ns)."""
+    _fields_ = [("worker", C.c_uint32), ("requests", C.c_uint32), ("entries", C.c_uint64),
+                ("t_take_ns", C.c_uint64), ("t_staged_ns", C.c_uint64), ("t_checked_ns", C.c_uint64),
+                ("t_done_ns", C.c_uint64)]
 
 
 class Request(C.Structure):
@@ -144,6 +151,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "poslo_poll": ([vp, u64, u32, u8p, vp, u64, C.POINTER(u64), C.POINTER(u64)], C.c_int),
         "poslo_serve_stats": ([vp, C.POINTER(u64), C.POINTER(u64), C.POINTER(u64)], C.c_int),
         "poslo_aver_partial": ([vp, C.POINTER(Batch), u32, C.POINTER(Partial)], C.c_int),
+        "poslo_serve_timeline": ([vp, vp, u64, C.POINTER(u64)], C.c_int),
         "poslo_combine_check": ([vp, u8p, vp, u32, u8p, C.POINTER(Partial)], C.c_int),
     }
     for name in EXPORTS:
@@ -484,6 +492,13 @@ class Context:
         b, r, u = C.c_uint64(), C.c_uint64(), C.c_uint64()
         self._check(self.lib.poslo_serve_stats(self.h, C.byref(b), C.byref(r), C.byref(u)))
         return b.value, r.value, u.value
+
+    def serve_timeline(self, cap: int = 1 << 16) -> list:
+        """The service's per-batch records since the last read (oldest first), as dicts."""
+        out = (BatchRecord * max(cap, 1))()
+        n = C.c_uint64()
+        self._check(self.lib.poslo_serve_timeline(self.h, C.cast(out, C.c_void_p), cap, C.byref(n)))
+        return [{f: getattr(out[i], f) for f, _ in BatchRecord._fields_} for i in range(n.value)]
 
     def epoch_seeds(self, ds: bytes, first_epoch: int, n_epochs: int) -> np.ndarray:
         out = np.zeros(16 * max(n_epochs, 1), np.uint8)

@@ -156,3 +156,73 @@ def test_serving_malformed_request_fails_alone():
         else:
             assert (r[0], list(r[1])) == (not q["want"], q["want"])
     assert requests == 8 and in_use == 0
+
+
+def test_serving_timeline_accounts_for_every_batch():
+    """The per-batch records: one per batch run, every request counted once, the four times of
+    a batch in order, workers named by their index; reading them drains them."""
+    import __graft_entry__
+    __graft_entry__.build()
+    keys, reqs = _requests(12, 3, 20)
+    with poslo.Context(device=0, verifier_seed=synth.verifier_seed(12)) as ctx:
+        ctx.serve_start(workers=2, max_batch_devices=5, max_batch_entries=150)
+        kid = [ctx.register_key(Y) for _, _, Y in keys]
+        tickets = [_submit(ctx, kid, q) for q in reqs]
+        for t in tickets:
+            ctx.poll(t, wait_ms=60000)
+        batches, requests, _ = ctx.serve_stats()
+        recs = ctx.serve_timeline()
+        again = ctx.serve_timeline()
+        ctx.serve_stop()
+    assert len(recs) == batches and sum(r["requests"] for r in recs) == requests == len(reqs)
+    assert sum(r["entries"] for r in recs) == sum(q["msgs"].n for q in reqs)
+    for r in recs:
+        assert r["t_take_ns"] <= r["t_staged_ns"] <= r["t_checked_ns"] <= r["t_done_ns"]
+        assert r["worker"] in (0, 1) and 1 <= r["requests"] <= 5
+    assert again == []
+
+
+def test_serving_pinned_borrowed_requests_gathered():
+    """Borrowed requests in page-locked host memory are staged by the gather kernel that reads
+    them in place: messages at every alignment (16-byte vector copies and byte copies), offsets
+    absolute into one shared buffer; results equal the definition, mixed with copied requests."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    keys, reqs = _requests(13, 3, 24)
+    pads, chunks, pos = [], [], 0
+    for i, q in enumerate(reqs):
+        pad = i % 17
+        pads.append(pos + pad)
+        chunks.append(np.full(pad, 0xEE, np.uint8))
+        chunks.append(q["msgs"].data)
+        pos += pad + len(q["msgs"].data)
+    big = torch.from_numpy(np.concatenate(chunks + [np.zeros(16, np.uint8)])).pin_memory()
+    keep = []
+    with poslo.Context(device=0, verifier_seed=synth.verifier_seed(13)) as ctx:
+        ctx.serve_start(workers=2, max_batch_devices=8, max_batch_entries=300)
+        kid = [ctx.register_key(Y) for _, _, Y in keys]
+        tickets = []
+        for i, q in enumerate(reqs):
+            if i % 3 == 2:
+                tickets.append(_submit(ctx, kid, q))
+                continue
+            offs = torch.from_numpy((q["msgs"].offs.astype(np.uint64) + np.uint64(pads[i])).view(np.int64)).pin_memory()
+            s_t = torch.from_numpy(np.frombuffer(q["s"], np.uint8).copy()).pin_memory()
+            R_t = torch.from_numpy(np.frombuffer(q["R"], np.uint8).copy()).pin_memory()
+            keep.append((offs, s_t, R_t))
+            req = poslo.Request()
+            req.key_id, req.n2, req.first_index = kid[q["key"]], q["n2"], q["first"]
+            req.msgs, req.offs, req.n = big.data_ptr(), offs.data_ptr(), q["msgs"].n
+            req.s, req.R = s_t.data_ptr(), R_t.data_ptr()
+            dsb = (poslo.C.c_uint8 * len(q["ds"])).from_buffer_copy(q["ds"])
+            keep.append(dsb)
+            req.ds, req.ds_nodes = poslo.C.addressof(dsb), len(q["ds"]) // 24
+            req.flags = poslo.REQ_BORROW
+            t = poslo.C.c_uint64()
+            assert ctx.lib.poslo_submit(ctx.h, poslo.C.byref(req), poslo.C.byref(t)) == 0
+            tickets.append(t.value)
+        res = [ctx.poll(t, wait_ms=60000) for t in tickets]
+        ctx.serve_stop()
+    for q, r in zip(reqs, res):
+        assert (r[0], list(r[1])) == (not q["want"], q["want"])

@@ -180,3 +180,37 @@ def test_device_resident_shards(ctx):
         parts.append(ctx.aver_partial(bt, poslo.AGG_WEIGHTED))
     torch.cuda.synchronize()
     assert ctx.combine_check(Y, parts)[0] is True
+
+
+def test_record_of_a_replayed_call_follows_its_inputs(ctx):
+    """A device-resident shard of the same shape in a row is replayed from a CUDA graph: the
+    records still follow the inputs (a byte flipped between calls changes the record, restoring
+    it restores the record), in both modes."""
+    import torch
+    n = 96
+    sk, Y, msgs, s, R, ds = _log(46, n)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).copy()).cuda()
+    d_msgs = dev(msgs.data)
+    bt = ctx.make_batch(poslo.VARIANT_F, N2, Y, d_msgs, dev(msgs.offs.view(np.int64)),
+                        dev(np.frombuffer(b"".join(s), np.uint8)), dev(np.frombuffer(b"".join(R), np.uint8)),
+                        O.ds_serialize(ds))
+    def same(a, b):
+        # equal scalars and the same point (the projective coordinates of R~ depend on the
+        # order in which the device summed the points, not on the point)
+        return a[:64] == b[:64] and O.point_eq(_ext_to_point(a[64:192]), _ext_to_point(b[64:192]))
+
+    for mode in (poslo.AGG_UNIT, poslo.AGG_WEIGHTED):
+        c0 = ctx.graph_stats()
+        good = [ctx.aver_partial(bt, mode).to_bytes() for _ in range(3)]
+        assert same(good[0], good[1]) and same(good[0], good[2]) and ctx.combine_check(Y, [good[2]])[0] is True
+        off = int(msgs.offs[40])
+        d_msgs[off] ^= 0x11
+        torch.cuda.synchronize()
+        bad = ctx.aver_partial(bt, mode).to_bytes()
+        d_msgs[off] ^= 0x11
+        torch.cuda.synchronize()
+        again = ctx.aver_partial(bt, mode).to_bytes()
+        c1 = ctx.graph_stats()
+        assert bad[:32] != good[0][:32] and same(again, good[0])    # the flip changes e~ only
+        assert ctx.combine_check(Y, [bad])[0] is False
+        assert c1[1] > c0[1]                    # some of these calls were replays
