@@ -728,6 +728,8 @@ __global__ void __launch_bounds__(128, POSLO_BISECT_MINB) k_bisect_step(const Tr
 __global__ void k_gather_flagged(const uint32_t* pts, const uint32_t* z, const uint8_t* badR, const uint64_t* idx,
                                  uint64_t cnt, uint32_t* gp, uint32_t* gz, uint8_t* gs);
 __global__ void k_point_diff(const uint32_t* a, const uint32_t* b, uint32_t* out);
+__global__ void __launch_bounds__(256) k_ccd_points(const uint32_t* pts, const uint8_t* badR, const uint64_t* idx,
+                                                    uint64_t nf, const uint32_t* unit, uint8_t* enc_out);
 __global__ void __launch_bounds__(kHashThreads) k_weighted_sums(const uint8_t* e, const uint8_t* s, const uint32_t* z, const uint8_t* skip1,
                                 const uint8_t* skip2, uint64_t n, unsigned long long* partial);
 __global__ void __launch_bounds__(kPointThreads) k_pts_sum(const uint32_t* pts, const uint8_t* skip1, const uint8_t* skip2, uint64_t n,

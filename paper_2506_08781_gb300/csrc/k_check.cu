@@ -54,10 +54,15 @@ __global__ void __launch_bounds__(kHashThreads) k_sum_scalars(const uint8_t* s, 
 
 __global__ void k_reduce_scalars(const unsigned long long* partial, uint32_t nparts, uint8_t* out) {
   __shared__ unsigned long long sums[13];
-  if (threadIdx.x < 13) {
+  if (threadIdx.x < 13) sums[threadIdx.x] = 0;
+  __syncthreads();
+  // word w of every part, the parts split over blockDim.x / 13 threads per word
+  const uint32_t lanes = blockDim.x / 13;
+  if (threadIdx.x < lanes * 13) {
+    const uint32_t w = threadIdx.x % 13, lane = threadIdx.x / 13;
     unsigned long long v = 0;
-    for (uint32_t b = 0; b < nparts; ++b) v += partial[(size_t)b * 13 + threadIdx.x];
-    sums[threadIdx.x] = v;
+    for (uint32_t b = lane; b < nparts; b += lanes) v += partial[(size_t)b * 13 + w];
+    atomicAdd(&sums[w], v);
   }
   __syncthreads();
   if (threadIdx.x == 0) {

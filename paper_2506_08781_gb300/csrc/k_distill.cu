@@ -168,15 +168,15 @@ __device__ __forceinline__ bool group8_check(const ge& P, const sc& e, const sc&
     we = i == r ? e.v[i] : we;
     ws = i == r ? s.v[i] : ws;
   }
-  int8_t de[8], ds[8];
-  group8_digits(we, r, de);
-  group8_digits(ws, r, ds);
-  ge acc = table_pick(tY, 8 * r, de[0]);
-#pragma unroll
-  for (int i = 1; i < 8; ++i) acc = ge_add(acc, table_pick(tY, 8 * r + i, de[i]));
-#pragma unroll
-  for (int i = 0; i < 8; ++i) acc = ge_add(acc, table_pick(tG, 8 * r + i, ds[i]));
-#pragma unroll
+  int8_t dg[16];   // the 8 digits of e, then the 8 of s
+  group8_digits(we, r, dg);
+  group8_digits(ws, r, dg + 8);
+  // loops, not unrolled: one copy of the point addition in the code keeps the kernel inside
+  // the instruction cache (unrolled, the warps stalled mostly on instruction fetch)
+  ge acc = ge_identity();
+#pragma unroll 1
+  for (int i = 0; i < 16; ++i) acc = ge_add(acc, table_pick(i < 8 ? tY : tG, 8 * r + (i & 7), dg[i]));
+#pragma unroll 1
   for (int o = 4; o > 0; o >>= 1) {
     ge other;
     other.X = fe_shfl(acc.X, lane ^ o); other.Y = fe_shfl(acc.Y, lane ^ o);
@@ -261,6 +261,36 @@ __global__ void k_gather_flagged(const uint32_t* pts, const uint32_t* z, const u
   for (int i = 0; i < kPtsWords / 4; ++i) dst[i] = src[i];
   reinterpret_cast<uint4*>(gz)[t] = reinterpret_cast<const uint4*>(z)[k];
   gs[t] = badR ? badR[k] : 0;
+}
+
+// ccd^v's point: the batch's unit sum of its decodable R_t (unit, 32 words) minus the flagged
+// entries' decodable R_t (local indices idx[0 .. nf)), encoded to enc_out (32 bytes).  One
+// block: the flagged points are few next to the batch.
+__global__ void __launch_bounds__(256) k_ccd_points(const uint32_t* pts, const uint8_t* badR, const uint64_t* idx,
+                                                    uint64_t nf, const uint32_t* unit, uint8_t* enc_out) {
+  __shared__ uint32_t sp[256][32];
+  ge acc = ge_identity();
+  for (uint64_t i = threadIdx.x; i < nf; i += blockDim.x) {
+    const uint64_t t = idx[i];
+    if (badR && badR[t]) continue;
+    fe x, y, t2d;
+    pts_load(pts + (size_t)kPtsWords * t, x, y, t2d);
+    acc = ge_madd(acc, x, y, t2d);
+  }
+  ge_store(sp[threadIdx.x], acc);
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) ge_store(sp[threadIdx.x], ge_add(ge_load(sp[threadIdx.x]), ge_load(sp[threadIdx.x + h])));
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    uint32_t w[8];
+    ge_encode(ge_sub(ge_load(unit), ge_load(sp[0])), w);
+    for (int k = 0; k < 8; ++k) {
+      enc_out[4 * k] = (uint8_t)w[k]; enc_out[4 * k + 1] = (uint8_t)(w[k] >> 8);
+      enc_out[4 * k + 2] = (uint8_t)(w[k] >> 16); enc_out[4 * k + 3] = (uint8_t)(w[k] >> 24);
+    }
+  }
 }
 
 // out = a - b (b = nullptr: out = a), extended points of 32 words.

@@ -25,10 +25,15 @@ __global__ void __launch_bounds__(kShardThreads) k_partial_out(const unsigned lo
                                                               const uint32_t* point_bad, uint32_t* out) {
   __shared__ unsigned long long sums[kPartialWords];
   const int tid = threadIdx.x;
-  if (tid < kPartialWords) {
+  if (tid < kPartialWords) sums[tid] = 0;
+  __syncthreads();
+  // word w of every block's partial, the blocks split over kShardThreads / kPartialWords threads
+  constexpr int kLanesPerWord = kShardThreads / kPartialWords;
+  if (tid < kLanesPerWord * kPartialWords) {
+    const int w = tid % kPartialWords, lane = tid / kPartialWords;
     unsigned long long v = 0;
-    for (uint32_t b = 0; b < nhash; ++b) v += hash_partial[(size_t)b * kPartialWords + tid];
-    sums[tid] = v;
+    for (uint32_t b = lane; b < nhash; b += kLanesPerWord) v += hash_partial[(size_t)b * kPartialWords + w];
+    atomicAdd(&sums[w], v);
   }
   __syncthreads();
   if (tid == 0) {

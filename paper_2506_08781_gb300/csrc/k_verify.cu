@@ -432,11 +432,15 @@ __global__ void __launch_bounds__(kFinalThreads) k_finalize(const FinalArgs a) {
   if (tid < kPartialWords) sums[tid] = 0;
   if (tid == 0) { pbad = 0; bad_flag = 0; }
   __syncthreads();
-  // scalar partial sums
-  if (tid < kPartialWords) {
+  // scalar partial sums: word w of every block's partial, the blocks split over
+  // kFinalThreads / kPartialWords threads per word (a chain of dependent loads per word was the
+  // kernel's longest part)
+  constexpr int kLanesPerWord = kFinalThreads / kPartialWords;
+  if (tid < kLanesPerWord * kPartialWords) {
+    const int w = tid % kPartialWords, lane = tid / kPartialWords;
     unsigned long long v = 0;
-    for (uint32_t b = 0; b < a.nhash; ++b) v += a.hash_partial[(size_t)b * kPartialWords + tid];
-    sums[tid] = v;
+    for (uint32_t b = lane; b < a.nhash; b += kLanesPerWord) v += a.hash_partial[(size_t)b * kPartialWords + w];
+    atomicAdd(&sums[w], v);
   }
   // point partials
   ge acc = ge_identity();
@@ -511,10 +515,14 @@ __global__ void __launch_bounds__(128) k_final_prep(const PrepArgs a) {
   __shared__ uint32_t pts_[kPrepThreads][32];
   __shared__ uint32_t bad_flag;
   const int tid = threadIdx.x;
-  if (tid < kPartialWords) {
+  if (tid < kPartialWords) sums[tid] = 0;
+  __syncthreads();
+  constexpr int kLanesPerWord = kPrepThreads / kPartialWords;   // blocks split over lanes per word
+  if (tid < kLanesPerWord * kPartialWords) {
+    const int w = tid % kPartialWords, lane = tid / kPartialWords;
     unsigned long long v = 0;
-    for (uint32_t b = 0; b < a.nhash; ++b) v += a.hash_partial[(size_t)b * kPartialWords + tid];
-    sums[tid] = v;
+    for (uint32_t b = lane; b < a.nhash; b += kLanesPerWord) v += a.hash_partial[(size_t)b * kPartialWords + w];
+    atomicAdd(&sums[w], v);
   }
   __syncthreads();
   if (tid == 0) {

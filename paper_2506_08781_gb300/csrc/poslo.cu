@@ -820,7 +820,7 @@ int run_prep(poslo_ctx* ctx, const unsigned long long* hpart, uint32_t nhb, cons
     unsigned long long* sp;
     if ((rc = ensure_t(ctx, "ccd_spart_fast", (size_t)sblocks * 13 * 8, &sp))) return rc;
     k_sum_scalars<<<sblocks, kHashThreads, 0, ctx->s_table>>>(s_all, n, nullptr, sp);
-    k_reduce_scalars<<<1, 32, 0, ctx->s_table>>>(sp, sblocks, ccd_s);
+    k_reduce_scalars<<<1, 256, 0, ctx->s_table>>>(sp, sblocks, ccd_s);
     ctx->launch_count += 2;
   }
   CU(cudaGetLastError());
@@ -853,7 +853,7 @@ int run_prep_windows(poslo_ctx* ctx, const unsigned long long* hpart, uint32_t n
     unsigned long long* sp;
     if ((rc = ensure_t(ctx, "ccd_spart_fast", (size_t)sblocks * 13 * 8, &sp))) return rc;
     k_sum_scalars<<<sblocks, kHashThreads, 0, ctx->s_table>>>(s_all, n, nullptr, sp);
-    k_reduce_scalars<<<1, 32, 0, ctx->s_table>>>(sp, sblocks, ccd_s);
+    k_reduce_scalars<<<1, 256, 0, ctx->s_table>>>(sp, sblocks, ccd_s);
     ctx->launch_count += 2;
   }
   CU(cudaGetLastError());
@@ -1791,6 +1791,10 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
   const uint64_t capn = std::max<uint64_t>(std::min(cap, n), 1);
   if ((rc = ensure_t(ctx, "invalid_idx", 8 * capn + 8, &d_idx))) return rc;
   uint64_t* d_cnt = d_idx + capn;
+  uint64_t* fidx;   // local indices of the flagged entries (confirmation, ccd^v), count at fidx[n]
+  if ((rc = ensure_t(ctx, "confirm_idx", 8 * (n + 1), &fidx))) return rc;
+  uint64_t nf = 0;
+  bool confirmed = false;
   {
     // ---- localisation: segment-tree bisection over unit aggregates ----
     uint64_t M = 2, L = 1;
@@ -1871,10 +1875,7 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
       if ((rc = ensure_t(ctx, "confirm_pts", 4 * 96, &Wc))) return rc;
       k_msm_final<<<1, 32, 0, ctx->s_main>>>(groups1, pl1, Wc);
       ++ctx->launch_count;
-      uint64_t* fidx;
-      if ((rc = ensure_t(ctx, "confirm_idx", 8 * (n + 1), &fidx))) return rc;
       if ((rc = run_compact(ctx, inv, n, 0, fidx, n, fidx + n))) return rc;
-      uint64_t nf = 0;
       CU(cudaMemcpyAsync(&nf, fidx + n, 8, cudaMemcpyDeviceToHost, ctx->s_main));
       CU(cudaStreamSynchronize(ctx->s_main));
       if (nf) {
@@ -1893,9 +1894,10 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
       timer_end(ctx, "confirm", ctx->s_main, tb, te);
     }
     if ((rc = run_finalize(ctx, wpart, wblocks, nullptr, 0, Rw, nullptr, tableY, d_acc, nullptr))) return rc;
-    uint8_t confirmed = 0;
-    CU(cudaMemcpyAsync(&confirmed, d_acc, 1, cudaMemcpyDeviceToHost, ctx->s_main));
+    uint8_t conf = 0;
+    CU(cudaMemcpyAsync(&conf, d_acc, 1, cudaMemcpyDeviceToHost, ctx->s_main));
     if ((rc = check_status(ctx))) return rc;
+    confirmed = conf != 0;
     if (!confirmed) {
       // errors that cancel inside unit aggregates: settle every entry by its own check
       CheckArgs a{};
@@ -1913,17 +1915,20 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
       timer_end(ctx, "check", ctx->s_main, tb, te);
     }
   }
-  // ordered list of flagged entries and ccd^v over the others
-  const int pblocks = grid_for(ctx, n, kPointThreads, 8);
-  uint32_t* pp;
-  if ((rc = ensure_t(ctx, "ccd_ppart", (size_t)pblocks * kPointPartialWords * 4, &pp))) return rc;
+  // ordered list of flagged entries and ccd^v over the others; its point is the batch's unit
+  // sum (from the first stage) minus the flagged entries' points
   {
     if ((rc = run_compact(ctx, inv, n, batch->first_index, d_idx, std::min(cap, n), d_cnt))) return rc;
     k_sum_scalars<<<sblocks, kHashThreads, 0, ctx->s_main>>>(sb.s, n, inv, sp);
-    k_reduce_scalars<<<1, 32, 0, ctx->s_main>>>(sp, sblocks, d_ccd);
-    k_pts_sum<<<pblocks, kPointThreads, 0, ctx->s_main>>>(pts, inv, badR, n, pp);
-    k_sum_encode<<<1, kFinalThreads, 0, ctx->s_main>>>(pp, pblocks, nullptr, d_ccd + 32, nullptr);
-    ctx->launch_count += 4;
+    k_reduce_scalars<<<1, 256, 0, ctx->s_main>>>(sp, sblocks, d_ccd);
+    ctx->launch_count += 2;
+    if (!confirmed) {   // the per-entry checks changed the flags: list them again
+      if ((rc = run_compact(ctx, inv, n, 0, fidx, n, fidx + n))) return rc;
+      CU(cudaMemcpyAsync(&nf, fidx + n, 8, cudaMemcpyDeviceToHost, ctx->s_main));
+      CU(cudaStreamSynchronize(ctx->s_main));
+    }
+    k_ccd_points<<<1, 256, 0, ctx->s_main>>>(pts, badR, fidx, nf, unitR, d_ccd + 32);
+    ++ctx->launch_count;
     CU(cudaGetLastError());
   }
   uint64_t cnt = 0;
@@ -1969,7 +1974,7 @@ int poslo_agg(poslo_ctx* ctx, const uint8_t* scalars, const uint8_t* points, uin
   if ((rc = ensure_t(ctx, "agg_out", 64, &d_out))) return rc;
   if ((rc = ensure_t(ctx, "agg_bad", 16, &d_bad))) return rc;
   k_sum_scalars<<<sblocks, kHashThreads, 0, ctx->s_main>>>(static_cast<const uint8_t*>(dsc), n, nullptr, sp);
-  k_reduce_scalars<<<1, 32, 0, ctx->s_main>>>(sp, sblocks, d_out);
+  k_reduce_scalars<<<1, 256, 0, ctx->s_main>>>(sp, sblocks, d_out);
   CU(cudaStreamWaitEvent(ctx->s_main, ctx->ev_points, 0));
   k_sum_encode<<<1, kFinalThreads, 0, ctx->s_main>>>(ppart, npb, nullptr, d_out + 32, d_bad);
   ctx->launch_count += 3;
