@@ -740,6 +740,10 @@ void launch_epoch_seeds_multi(int inst, unsigned grid, unsigned block, cudaStrea
                               const uint32_t* ds_off, const uint64_t* seed_off, const uint64_t* e0, uint32_t n_dev,
                               uint32_t* seeds, uint32_t* status);
 constexpr uint64_t kGatherChunk = 1ull << 16;   // bytes of one chunk of the staging gather
+#ifndef POSLO_GATHER_MAX_REQUEST
+#define POSLO_GATHER_MAX_REQUEST (1ull << 20)
+#endif
+constexpr uint64_t kGatherMaxRequestBytes = POSLO_GATHER_MAX_REQUEST;   // larger requests: copy engines
 struct GatherRegion {
   const uint8_t* src;   // device-readable (mapped page-locked host memory)
   uint8_t* dst;         // device memory

@@ -2417,14 +2417,15 @@ int poslo_host::stage_requests(poslo_ctx* ctx, const ReqView* reqs, uint32_t nd,
   if ((rc = ensure_t(ctx, "sv_R", 32 * std::max<uint64_t>(N, 1), &Rv))) return rc;
   if ((rc = ensure_t(ctx, "sv_meta", 8 * meta.size(), &d_meta))) return rc;
   cudaStream_t st = ctx->s_main;
-  // requests in mapped page-locked memory: one gather kernel over a table of regions; the
-  // others: one copy per array
+  // small requests in mapped page-locked memory: one gather kernel over a table of regions
+  // (one launch instead of four copies each); large ones and all others: one copy per array,
+  // on the copy engines, which leave the SMs to the verification of other batches
   std::vector<GatherRegion> regions;
   for (uint32_t d = 0; d < nd; ++d) {
     const ReqView& r = reqs[d];
     if (r.n == 0) continue;
     const uint64_t lo = r.offs[0], len = r.offs[r.n] - lo;
-    if (r.d_msgs && r.d_offs && r.d_s && r.d_R) {
+    if (r.d_msgs && r.d_offs && r.d_s && r.d_R && len + 72 * r.n < kGatherMaxRequestBytes) {
       auto add = [&](const uint8_t* src, uint8_t* dst, uint64_t bytes) {
         for (uint64_t o = 0; o < bytes; o += kGatherChunk)
           regions.push_back(GatherRegion{src + o, dst + o, std::min<uint64_t>(kGatherChunk, bytes - o)});
