@@ -746,15 +746,28 @@ def bench_serving(ctx_factory, workers: int = SERVE_WORKERS, max_batch_entries: 
         recs = svc.serve_timeline(1 << 20)
         if not recs:
             return None
-        stage = sum(r["t_staged_ns"] - r["t_take_ns"] for r in recs) * 1e-9
-        check = sum(r["t_checked_ns"] - r["t_staged_ns"] for r in recs) * 1e-9
+        issue = sum(r["t_staged_ns"] - r["t_take_ns"] for r in recs) * 1e-9
+        # a worker waits for a batch's copies only once it has nothing else to do: after the
+        # batch's own issue, the end of its previous batch and the issue of its next one (the
+        # copies run while the previous batch is verified)
+        wait = 0.0
+        for w in {r["worker"] for r in recs}:
+            mine = sorted((r for r in recs if r["worker"] == w), key=lambda r: r["t_take_ns"])
+            for k, r in enumerate(mine):
+                busy_until = r["t_staged_ns"]
+                if k:
+                    busy_until = max(busy_until, mine[k - 1]["t_done_ns"])
+                if k + 1 < len(mine) and mine[k + 1]["t_take_ns"] < r["t_verify_ns"]:
+                    busy_until = max(busy_until, mine[k + 1]["t_staged_ns"])
+                wait += max(0, r["t_verify_ns"] - busy_until) * 1e-9
+        check = sum(r["t_checked_ns"] - r["t_verify_ns"] for r in recs) * 1e-9
         publish = sum(r["t_done_ns"] - r["t_checked_ns"] for r in recs) * 1e-9
-        busy = stage + check + publish
+        busy = issue + wait + check + publish
         return {"batches": len(recs), "requests_per_batch": float(np.mean([r["requests"] for r in recs])),
                 "entries_per_batch": float(np.mean([r["entries"] for r in recs])),
-                "worker_s_staging": stage, "worker_s_verifying": check, "worker_s_publishing": publish,
-                "worker_idle_frac": max(0.0, 1.0 - busy / (workers * wall)),
-                "staging_GB_per_s": sum(r["entries"] for r in recs) * 216e-9 / max(stage, 1e-9)}
+                "worker_s_issuing_copies": issue, "worker_s_waiting_for_copies": wait,
+                "worker_s_verifying": check, "worker_s_publishing": publish,
+                "worker_idle_frac": max(0.0, 1.0 - busy / (workers * wall))}
 
     svc.serve_timeline(1 << 20)      # drop the records of the warm-up
     # saturated (every request at t = 0): the service's peak

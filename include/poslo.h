@@ -295,9 +295,11 @@ int poslo_poll(poslo_ctx* ctx, uint64_t ticket, uint32_t wait_ms, uint8_t* accep
 /* Batches run, requests verified in them, budget bytes held by requests not yet polled. */
 int poslo_serve_stats(poslo_ctx* ctx, uint64_t* batches, uint64_t* requests, uint64_t* bytes_in_use);
 /* Per-batch timeline of the service (no counterpart in the paper), times in ns since
- * poslo_serve_start on the host's monotonic clock: the worker took the batch (t_take), its
- * requests' inputs were in device staging (t_staged), the multi-device verification returned
- * (t_checked), every result was published (t_done).  poslo_serve_timeline moves the oldest
+ * poslo_serve_start on the host's monotonic clock: the worker took the batch (t_take), the
+ * copies of its requests' inputs into device staging were issued (t_staged; they run while
+ * the worker's previous batch is verified), the inputs had landed and the worker began to
+ * verify it (t_verify), the multi-device verification returned (t_checked), every result was
+ * published (t_done).  poslo_serve_timeline moves the oldest
  * min(cap, held) records to out (in the order batches finished) and sets *n to that count; the
  * service holds at most 2^20 unread records (later batches are not recorded).  EINVAL without
  * a running service. */
@@ -305,7 +307,7 @@ typedef struct {
   uint32_t worker;          /* 0 .. workers - 1 */
   uint32_t requests;
   uint64_t entries;
-  uint64_t t_take_ns, t_staged_ns, t_checked_ns, t_done_ns;
+  uint64_t t_take_ns, t_staged_ns, t_verify_ns, t_checked_ns, t_done_ns;
 } poslo_batch_record;
 int poslo_serve_timeline(poslo_ctx* ctx, poslo_batch_record* out, uint64_t cap, uint64_t* n);
 

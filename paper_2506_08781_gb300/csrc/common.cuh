@@ -755,10 +755,22 @@ __global__ void k_rebase_offs(const uint64_t* raw, const uint64_t* slot, const u
 #ifndef POSLO_SEG_THREADS
 #define POSLO_SEG_THREADS 256
 #endif
-constexpr int kSegThreads = POSLO_SEG_THREADS;   // threads per device block of the segment sums
-__global__ void __launch_bounds__(kSegThreads) k_segment_sums(const uint8_t* e, const uint8_t* s, const uint32_t* z,
-                                                      const uint32_t* pts, const uint8_t* badR, const uint8_t* badS,
-                                                      const uint64_t* start, const uint64_t* order, SegSums out);
+constexpr int kSegThreads = POSLO_SEG_THREADS;   // threads per block of the segment sums
+// Entries per piece of the segment sums: a device's entries are cut into pieces of this size
+// (one block each), so a device of 65,536 entries no longer runs as one long block at the end.
+constexpr uint64_t kSegPiece = 2048;
+constexpr int kSegLimbWords = 4 * 13 + 1;          // a piece's partial: four 13-limb sums and its bad count
+// The pieces of a call: pieces[p] = device | (piece index within the device << 32), devices
+// largest first and a device's pieces consecutive; pfirst[d] = index of device d's first piece.
+constexpr int kSegScalars = 1, kSegPoints = 2;     // the two launches of the segment sums
+// k_segment_sums<kSegScalars> then k_segment_sums<kSegPoints>, one block per piece, on st.
+void launch_segment_sums(unsigned n_pieces, cudaStream_t st, const uint8_t* e, const uint8_t* s, const uint32_t* z,
+                         const uint32_t* pts, const uint8_t* badR, const uint8_t* badS, const uint64_t* start,
+                         const uint64_t* pieces, unsigned long long* piece_limbs, uint32_t* piece_R, SegSums out);
+// Devices of more than one piece: their pieces' limb sums, bad counts and points added up.
+__global__ void __launch_bounds__(kSegThreads) k_segment_combine(const uint64_t* start, const uint64_t* pfirst,
+                                                         const unsigned long long* piece_limbs,
+                                                         const uint32_t* piece_R, uint32_t n_dev, SegSums out);
 __global__ void __launch_bounds__(kFinalThreads) k_multi_check(const uint32_t* P1, const uint32_t* P1sub, const uint32_t* P2,
                                                                const uint32_t* Sw, const uint8_t* dev_flag,
                                                                uint32_t n_dev, const uint32_t* tableG,

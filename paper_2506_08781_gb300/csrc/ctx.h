@@ -22,6 +22,18 @@ struct DevBuf {
   size_t cap = 0;
 };
 
+// One staging set of a serving worker: the device buffers its next batch is copied into and
+// a page-locked area for the small tables that go up with it.  A staging thread fills a set
+// while the worker's own thread verifies from the other, so a set keeps its buffers, its
+// launch count and its error apart from the context's workspace map and fields.
+struct StageSet {
+  DevBuf msgs, raw, offs, s, R, meta, regions, status;
+  uint8_t* h = nullptr;   // page-locked: status word (16 bytes), offsets table, gather regions
+  size_t h_cap = 0;
+  uint64_t launches = 0;
+  std::string err;
+};
+
 struct KernelTimer {
   double total_ms = 0;
   uint64_t launches = 0;
@@ -78,6 +90,7 @@ struct poslo_ctx {
   uint32_t* status = nullptr;     // device status word
   uint32_t* h_status = nullptr;   // pinned mirror
   uint8_t* h_small = nullptr;     // pinned, kSmallHostBytes: small results and shard records
+  poslo_host::StageSet stage[2];  // serving staging sets (filled by a worker's staging thread)
   std::string err;
   bool profiling = false;
   uint64_t launch_count = 0;      // kernels launched by this context
@@ -129,8 +142,17 @@ struct ReqView {
   const uint8_t* d_s = nullptr;
   const uint8_t* d_R = nullptr;
 };
-// Copies the requests' inputs one by one into device staging buffers of ctx (the messages
-// back to back, offsets rebased on the device) and points mb's msgs, offs, s, R at them
-// (mb->on_device = 1).  The copies are issued on ctx's main stream.
-int stage_requests(poslo_ctx* ctx, const ReqView* reqs, uint32_t nd, poslo_multi_batch* mb);
+// Issues the copies of the requests' inputs into device staging set `set` (0 or 1) of ctx
+// (the messages back to back, offsets rebased on the device) and points mb's msgs, offs, s, R
+// at them (mb->on_device = 1).  Nothing waits: the copies and the gather run on ctx's copy
+// stream and end with ctx->ev_copy[set], so a worker stages its next batch while the current
+// one is verified on the main stream.  It touches only ctx->stage[set], s_copy and
+// ev_copy[set], so it may run on another thread than the one using the rest of ctx.  The
+// requests' host memory must stay valid, and the set unused, until stage_wait(ctx, set, rc)
+// has returned.
+int stage_requests(poslo_ctx* ctx, const ReqView* reqs, uint32_t nd, poslo_multi_batch* mb, int set);
+// On the context's own thread: waits for staging set `set` to land and returns the staging's
+// status (issue_rc from stage_requests, else EINVAL if a request's offsets fell below its
+// first), with its message in the context's error.
+int stage_wait(poslo_ctx* ctx, int set, int issue_rc);
 }  // namespace poslo_host

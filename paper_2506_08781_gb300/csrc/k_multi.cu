@@ -66,18 +66,80 @@ __global__ void k_rebase_offs(const uint64_t* raw, const uint64_t* slot, const u
   out[start[d] + k] = msg_base[d] + (v >= v0 ? v - v0 : 0);
 }
 
-// Per-device sums: weighted E_d = sum z e, S_d = sum z s (mod q), unit Eu_d, Su_d, the unit
-// point sum Ru_d and the count of malformed entries.  One block per device, taken in the
-// order `order` (largest devices first, so that no long block starts last).
-__global__ void __launch_bounds__(kSegThreads) k_segment_sums(const uint8_t* e, const uint8_t* s, const uint32_t* z,
-                                                              const uint32_t* pts, const uint8_t* badR,
-                                                              const uint8_t* badS, const uint64_t* start,
-                                                              const uint64_t* order, SegSums out) {
-  const uint32_t d = (uint32_t)order[blockIdx.x];
-  const uint64_t lo = start[d], hi = start[d + 1];
+namespace {
+
+__device__ __forceinline__ uint64_t seg_pieces(uint64_t n) { return n == 0 ? 1 : (n + kSegPiece - 1) / kSegPiece; }
+
+// The shared-memory tree over the block's points (one per thread of kThreads); the sum ends
+// in sp_[0].
+template <int kThreads = kSegThreads>
+__device__ __forceinline__ void seg_point_tree(uint32_t (*sp_)[32]) {
+  __syncthreads();
+  for (int h = kThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) ge_store(sp_[threadIdx.x], ge_add(ge_load(sp_[threadIdx.x]), ge_load(sp_[threadIdx.x + h])));
+    __syncthreads();
+  }
+}
+
+// Device d's results from its exact limb sums (four 13-limb sums, then the bad count) and
+// its point sum R (32 words): the scalars reduced mod q.  kPart selects what is written.
+template <int kPart>
+__device__ __forceinline__ void seg_write(const unsigned long long* tot, const uint32_t* R, uint32_t d, SegSums out) {
+  if (kPart & kSegScalars) {
+    if (threadIdx.x < 4) {
+      unsigned long long sums[13];
+      for (int k = 0; k < 13; ++k) sums[k] = tot[13 * threadIdx.x + k];
+      const sc r = limb_sums_to_scalar(sums);
+      uint32_t* dst = threadIdx.x == 0 ? out.Ew : threadIdx.x == 1 ? out.Sw : threadIdx.x == 2 ? out.Eu : out.Su;
+      for (int k = 0; k < 8; ++k) dst[8 * (size_t)d + k] = r.v[k];
+    }
+    if (threadIdx.x == 0) out.bad[d] = (uint32_t)tot[kSegLimbWords - 1];
+  }
+  if (kPart & kSegPoints) {
+    if (threadIdx.x < 32) out.Ru[32 * (size_t)d + threadIdx.x] = R[threadIdx.x];
+  }
+}
+
+}  // namespace
+
+// Per-device sums: weighted E_d = sum z e, S_d = sum z s (mod q), unit Eu_d, Su_d and the
+// count of malformed entries (kPart = kSegScalars), or the unit point sum Ru_d (kSegPoints):
+// two launches, each light enough for two blocks per SM.  One block per piece of at most
+// kSegPiece entries of one device: a device of one piece gets its results here, the others
+// leave exact partials (limb sums, which add without loss, and a point) for
+// k_segment_combine.
+template <int kPart, int kThreads>
+__global__ void __launch_bounds__(kThreads, 512 / kThreads) k_segment_sums(const uint8_t* e, const uint8_t* s, const uint32_t* z,
+                                                                 const uint32_t* pts, const uint8_t* badR,
+                                                                 const uint8_t* badS, const uint64_t* start,
+                                                                 const uint64_t* pieces,
+                                                                 unsigned long long* piece_limbs, uint32_t* piece_R,
+                                                                 SegSums out) {
+  const uint64_t pc = pieces[blockIdx.x];
+  const uint32_t d = (uint32_t)pc, piece = (uint32_t)(pc >> 32);
+  const uint64_t dlo = start[d], dhi = start[d + 1];
+  const uint64_t lo = dlo + (uint64_t)piece * kSegPiece, hi = min(lo + kSegPiece, dhi);
+  const bool whole = seg_pieces(dhi - dlo) == 1;   // block-uniform
+  if (kPart == kSegPoints) {
+    __shared__ uint32_t sp_[kThreads][32];
+    ge acc = ge_identity();
+    for (uint64_t t = lo + threadIdx.x; t < hi; t += blockDim.x) {
+      if (badR[t] || badS[t]) continue;
+      fe x, y, t2d;
+      pts_load(pts + (size_t)kPtsWords * t, x, y, t2d);
+      acc = ge_madd(acc, x, y, t2d);
+    }
+    ge_store(sp_[threadIdx.x], acc);
+    seg_point_tree<kThreads>(sp_);
+    if (!whole) {
+      if (threadIdx.x < 32) piece_R[32 * (size_t)blockIdx.x + threadIdx.x] = sp_[0][threadIdx.x];
+      return;
+    }
+    seg_write<kSegPoints>(nullptr, sp_[0], d, out);
+    return;
+  }
   acc13 Ew, Sw, Eu, Su;
   acc_zero(Ew); acc_zero(Sw); acc_zero(Eu); acc_zero(Su);
-  ge acc = ge_identity();
   uint32_t bad = 0;
   for (uint64_t t = lo + threadIdx.x; t < hi; t += blockDim.x) {
     if (badR[t] || badS[t]) {
@@ -98,14 +160,13 @@ __global__ void __launch_bounds__(kSegThreads) k_segment_sums(const uint8_t* e, 
     acc_add<12>(Sw, pr);
     acc_add<8>(Eu, ev);
     acc_add<8>(Su, sv);
-    fe x, y, t2d;
-    pts_load(pts + (size_t)kPtsWords * t, x, y, t2d);
-    acc = ge_madd(acc, x, y, t2d);
   }
-  // scalars: 4 x 13 limb sums, warp shuffles then shared memory
-  __shared__ unsigned long long red[kSegThreads / 32][4 * 13 + 1];
+  // 4 x 13 limb sums and the bad count: warp shuffles, then shared memory
+  __shared__ unsigned long long red[kThreads / 32][kSegLimbWords];
+  __shared__ unsigned long long tot[kSegLimbWords];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int k = 0; k < 4 * 13 + 1; ++k) {
+#pragma unroll
+  for (int k = 0; k < kSegLimbWords; ++k) {
     unsigned long long v;
     if (k < 13) v = Ew.v[k];
     else if (k < 26) v = Sw.v[k - 13];
@@ -115,31 +176,51 @@ __global__ void __launch_bounds__(kSegThreads) k_segment_sums(const uint8_t* e, 
     warp_sum_u64(v);
     if (lane == 0) red[warp][k] = v;
   }
-  // points: shared-memory tree
+  __syncthreads();
+  for (int k = threadIdx.x; k < kSegLimbWords; k += blockDim.x) {
+    unsigned long long v = 0;
+    for (int w = 0; w < kThreads / 32; ++w) v += red[w][k];
+    tot[k] = v;
+    if (!whole) piece_limbs[(size_t)blockIdx.x * kSegLimbWords + k] = v;
+  }
+  if (!whole) return;
+  __syncthreads();
+  seg_write<kSegScalars>(tot, nullptr, d, out);
+}
+
+void launch_segment_sums(unsigned n_pieces, cudaStream_t st, const uint8_t* e, const uint8_t* s, const uint32_t* z,
+                         const uint32_t* pts, const uint8_t* badR, const uint8_t* badS, const uint64_t* start,
+                         const uint64_t* pieces, unsigned long long* piece_limbs, uint32_t* piece_R, SegSums out) {
+  // the point sums in blocks of 128 threads (four per SM by registers), so that other blocks
+  // keep the SM busy through each block's tree
+  k_segment_sums<kSegScalars, kSegThreads><<<n_pieces, kSegThreads, 0, st>>>(e, s, z, pts, badR, badS, start, pieces,
+                                                                              piece_limbs, piece_R, out);
+  k_segment_sums<kSegPoints, 128><<<n_pieces, 128, 0, st>>>(e, s, z, pts, badR, badS, start, pieces, piece_limbs,
+                                                            piece_R, out);
+}
+
+// One block per device; devices of one piece have their results already.
+__global__ void __launch_bounds__(kSegThreads) k_segment_combine(const uint64_t* start, const uint64_t* pfirst,
+                                                                 const unsigned long long* piece_limbs,
+                                                                 const uint32_t* piece_R, uint32_t n_dev,
+                                                                 SegSums out) {
+  const uint32_t d = blockIdx.x;
+  if (d >= n_dev) return;
+  const uint64_t np = seg_pieces(start[d + 1] - start[d]);
+  if (np == 1) return;   // block-uniform
+  const uint64_t p0 = pfirst[d];
+  __shared__ unsigned long long tot[kSegLimbWords];
+  for (int k = threadIdx.x; k < kSegLimbWords; k += blockDim.x) {
+    unsigned long long v = 0;   // below 2^40 per piece: no overflow for any 32-bit entry count
+    for (uint64_t j = 0; j < np; ++j) v += piece_limbs[(p0 + j) * kSegLimbWords + k];
+    tot[k] = v;
+  }
+  ge acc = ge_identity();
+  for (uint64_t j = threadIdx.x; j < np; j += blockDim.x) acc = ge_add(acc, ge_load(piece_R + 32 * (p0 + j)));
   __shared__ uint32_t sp_[kSegThreads][32];
   ge_store(sp_[threadIdx.x], acc);
-  __syncthreads();
-  for (int h = kSegThreads / 2; h > 0; h >>= 1) {
-    if (threadIdx.x < h) ge_store(sp_[threadIdx.x], ge_add(ge_load(sp_[threadIdx.x]), ge_load(sp_[threadIdx.x + h])));
-    __syncthreads();
-  }
-  if (threadIdx.x < 4) {
-    unsigned long long sums[13];
-    for (int k = 0; k < 13; ++k) {
-      unsigned long long v = 0;
-      for (int w = 0; w < kSegThreads / 32; ++w) v += red[w][13 * threadIdx.x + k];
-      sums[k] = v;
-    }
-    const sc r = limb_sums_to_scalar(sums);
-    uint32_t* dst = threadIdx.x == 0 ? out.Ew : threadIdx.x == 1 ? out.Sw : threadIdx.x == 2 ? out.Eu : out.Su;
-    for (int k = 0; k < 8; ++k) dst[8 * (size_t)d + k] = r.v[k];
-  }
-  if (threadIdx.x < 32) out.Ru[32 * (size_t)d + threadIdx.x] = sp_[0][threadIdx.x];
-  if (threadIdx.x == 0) {
-    unsigned long long v = 0;
-    for (int w = 0; w < kSegThreads / 32; ++w) v += red[w][52];
-    out.bad[d] = (uint32_t)v;
-  }
+  seg_point_tree(sp_);
+  seg_write<kSegScalars | kSegPoints>(tot, sp_[0], d, out);
 }
 
 // Per-device, per-window weighted sums (the per-window form of the combined check, used for

@@ -971,6 +971,11 @@ void poslo_destroy(poslo_ctx* ctx) {
   if (ctx->tableG) cudaFree(ctx->tableG);
   if (ctx->status) cudaFree(ctx->status);
   if (ctx->h_status) cudaFreeHost(ctx->h_status);
+  for (poslo_host::StageSet& S : ctx->stage) {
+    for (poslo_host::DevBuf* b : {&S.msgs, &S.raw, &S.offs, &S.s, &S.R, &S.meta, &S.regions, &S.status})
+      if (b->p) cudaFree(b->p);
+    if (S.h) cudaFreeHost(S.h);
+  }
   if (ctx->ev_table) cudaEventDestroy(ctx->ev_table);
   if (ctx->ev_points) cudaEventDestroy(ctx->ev_points);
   if (ctx->ev_decoded) cudaEventDestroy(ctx->ev_decoded);
@@ -2392,7 +2397,61 @@ int poslo_host::build_key_table(poslo_ctx* ctx, const uint8_t Y[32], uint32_t* t
   return POSLO_OK;
 }
 
-int poslo_host::stage_requests(poslo_ctx* ctx, const ReqView* reqs, uint32_t nd, poslo_multi_batch* mb) {
+namespace {
+
+// Staging errors go to the set (another thread may be using the context meanwhile).
+int stage_fail(poslo_host::StageSet& S, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  S.err = buf;
+  return code;
+}
+
+#define SCU(call)                                                                                   \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess) return stage_fail(S, POSLO_EDEVICE, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+// Grows a staging buffer to at least `bytes` (by half again at least); the set's previous
+// copies have landed when this runs, and cudaFree waits for the device in any case.
+int stage_grow(poslo_host::StageSet& S, poslo_host::DevBuf& b, size_t bytes, void** out) {
+  bytes = std::max<size_t>(bytes, 16);
+  if (b.cap < bytes) {
+    size_t want = std::max(bytes, b.cap + b.cap / 2);
+    want = (want + 255) & ~size_t(255);
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    const cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return stage_fail(S, POSLO_ENOMEM, "staging buffer of %zu bytes: %s", want, cudaGetErrorString(e));
+    }
+    b.cap = want;
+  }
+  *out = b.p;
+  return POSLO_OK;
+}
+
+template <class T>
+int stage_grow_t(poslo_host::StageSet& S, poslo_host::DevBuf& b, size_t bytes, T** out) {
+  void* p;
+  const int rc = stage_grow(S, b, bytes, &p);
+  *out = static_cast<T*>(p);
+  return rc;
+}
+
+}  // namespace
+
+int poslo_host::stage_requests(poslo_ctx* ctx, const ReqView* reqs, uint32_t nd, poslo_multi_batch* mb, int set) {
+  if (set != 0 && set != 1) return POSLO_EINVAL;
+  StageSet& S = ctx->stage[set];
+  S.err.clear();
+  S.launches = 0;
   int rc;
   // slot: raw offsets of request d at [slot[d], slot[d+1]); start: its first entry in the
   // batch; base: its first message byte in the batch
@@ -2402,7 +2461,7 @@ int poslo_host::stage_requests(poslo_ctx* ctx, const ReqView* reqs, uint32_t nd,
   uint64_t* base = start + nd + 1;
   for (uint32_t d = 0; d < nd; ++d) {
     const ReqView& r = reqs[d];
-    if (r.n && r.offs[r.n] < r.offs[0]) return fail(ctx, POSLO_EINVAL, "request %u: offsets decrease", d);
+    if (r.n && r.offs[r.n] < r.offs[0]) return stage_fail(S, POSLO_EINVAL, "request %u: offsets decrease", d);
     slot[d + 1] = slot[d] + r.n + 1;
     start[d + 1] = start[d] + r.n;
     base[d + 1] = base[d] + (r.n ? r.offs[r.n] - r.offs[0] : 0);
@@ -2410,17 +2469,19 @@ int poslo_host::stage_requests(poslo_ctx* ctx, const ReqView* reqs, uint32_t nd,
   const uint64_t N = start[nd], M = base[nd];
   uint8_t *msgs, *sv, *Rv;
   uint64_t *raw, *offs, *d_meta;
-  if ((rc = ensure_t(ctx, "sv_msgs", std::max<uint64_t>(M, 16), &msgs))) return rc;
-  if ((rc = ensure_t(ctx, "sv_raw", 8 * std::max<uint64_t>(slot[nd], 1), &raw))) return rc;
-  if ((rc = ensure_t(ctx, "sv_offs", 8 * (N + 1), &offs))) return rc;
-  if ((rc = ensure_t(ctx, "sv_s", 32 * std::max<uint64_t>(N, 1), &sv))) return rc;
-  if ((rc = ensure_t(ctx, "sv_R", 32 * std::max<uint64_t>(N, 1), &Rv))) return rc;
-  if ((rc = ensure_t(ctx, "sv_meta", 8 * meta.size(), &d_meta))) return rc;
-  cudaStream_t st = ctx->s_main;
+  uint32_t* d_st;
+  if ((rc = stage_grow_t(S, S.msgs, M, &msgs))) return rc;
+  if ((rc = stage_grow_t(S, S.raw, 8 * slot[nd], &raw))) return rc;
+  if ((rc = stage_grow_t(S, S.offs, 8 * (N + 1), &offs))) return rc;
+  if ((rc = stage_grow_t(S, S.s, 32 * N, &sv))) return rc;
+  if ((rc = stage_grow_t(S, S.R, 32 * N, &Rv))) return rc;
+  if ((rc = stage_grow_t(S, S.meta, 8 * meta.size(), &d_meta))) return rc;
+  if ((rc = stage_grow_t(S, S.status, 4, &d_st))) return rc;
   // small requests in mapped page-locked memory: one gather kernel over a table of regions
   // (one launch instead of four copies each); large ones and all others: one copy per array,
   // on the copy engines, which leave the SMs to the verification of other batches
   std::vector<GatherRegion> regions;
+  std::vector<uint32_t> copied;
   for (uint32_t d = 0; d < nd; ++d) {
     const ReqView& r = reqs[d];
     if (r.n == 0) continue;
@@ -2434,37 +2495,83 @@ int poslo_host::stage_requests(poslo_ctx* ctx, const ReqView* reqs, uint32_t nd,
       add(reinterpret_cast<const uint8_t*>(r.d_offs), reinterpret_cast<uint8_t*>(raw + slot[d]), 8 * (r.n + 1));
       add(r.d_s, sv + 32 * start[d], 32 * r.n);
       add(r.d_R, Rv + 32 * start[d], 32 * r.n);
-      continue;
+    } else {
+      copied.push_back(d);
     }
-    if (len) CU(cudaMemcpyAsync(msgs + base[d], r.msgs + lo, len, cudaMemcpyHostToDevice, st));
-    CU(cudaMemcpyAsync(raw + slot[d], r.offs, 8 * (r.n + 1), cudaMemcpyHostToDevice, st));
-    CU(cudaMemcpyAsync(sv + 32 * start[d], r.s, 32 * r.n, cudaMemcpyHostToDevice, st));
-    CU(cudaMemcpyAsync(Rv + 32 * start[d], r.R, 32 * r.n, cudaMemcpyHostToDevice, st));
+  }
+  GatherRegion* d_reg = nullptr;
+  if (!regions.empty() && (rc = stage_grow_t(S, S.regions, sizeof(GatherRegion) * regions.size(), &d_reg)))
+    return rc;
+  // the status word and the two tables go up from page-locked memory: a copy from pageable
+  // memory would first wait for every copy already queued on the stream
+  const size_t meta_bytes = 8 * meta.size(), reg_bytes = sizeof(GatherRegion) * regions.size();
+  const size_t h_bytes = 16 + meta_bytes + reg_bytes;
+  if (S.h_cap < h_bytes) {
+    if (S.h) cudaFreeHost(S.h);
+    S.h = nullptr;
+    S.h_cap = 0;
+    const size_t want = std::max<size_t>(2 * h_bytes, 1 << 16);
+    if (cudaMallocHost(&S.h, want) != cudaSuccess) {
+      cudaGetLastError();
+      return stage_fail(S, POSLO_ENOMEM, "page-locked staging table of %zu bytes", want);
+    }
+    S.h_cap = want;
+  }
+  uint32_t* h_st = reinterpret_cast<uint32_t*>(S.h);
+  uint8_t* h_meta = S.h + 16;
+  uint8_t* h_reg = h_meta + meta_bytes;   // 8-byte aligned, as GatherRegion
+  *h_st = 0;
+  memcpy(h_meta, meta.data(), meta_bytes);
+  if (reg_bytes) memcpy(h_reg, regions.data(), reg_bytes);
+  // from here on only the stream's own errors end the staging early.  The copy stream, so
+  // that the staging overlaps the verification of the previous batch on s_main; the set's
+  // own status word, so that it neither reads nor clears that verification's.
+  cudaStream_t st = ctx->s_copy;
+  SCU(cudaMemsetAsync(d_st, 0, 4, st));
+  for (uint32_t d : copied) {
+    const ReqView& r = reqs[d];
+    const uint64_t lo = r.offs[0], len = r.offs[r.n] - lo;
+    if (len) SCU(cudaMemcpyAsync(msgs + base[d], r.msgs + lo, len, cudaMemcpyHostToDevice, st));
+    SCU(cudaMemcpyAsync(raw + slot[d], r.offs, 8 * (r.n + 1), cudaMemcpyHostToDevice, st));
+    SCU(cudaMemcpyAsync(sv + 32 * start[d], r.s, 32 * r.n, cudaMemcpyHostToDevice, st));
+    SCU(cudaMemcpyAsync(Rv + 32 * start[d], r.R, 32 * r.n, cudaMemcpyHostToDevice, st));
   }
   if (!regions.empty()) {
-    GatherRegion* d_reg;
-    if ((rc = ensure_t(ctx, "sv_regions", sizeof(GatherRegion) * regions.size(), &d_reg))) return rc;
-    CU(cudaMemcpyAsync(d_reg, regions.data(), sizeof(GatherRegion) * regions.size(), cudaMemcpyHostToDevice, st));
+    SCU(cudaMemcpyAsync(d_reg, h_reg, reg_bytes, cudaMemcpyHostToDevice, st));
     const unsigned grid = (unsigned)std::min<size_t>(regions.size(), (size_t)ctx->sm_count * 8);
     k_stage_gather<<<grid, 256, 0, st>>>(d_reg, (uint32_t)regions.size());
-    ++ctx->launch_count;
+    ++S.launches;
   }
-  CU(cudaMemcpyAsync(d_meta, meta.data(), 8 * meta.size(), cudaMemcpyHostToDevice, st));
-  CU(cudaMemsetAsync(offs, 0, 8, st));   // an empty batch still has offs[0] = 0
+  SCU(cudaMemcpyAsync(d_meta, h_meta, meta_bytes, cudaMemcpyHostToDevice, st));
+  SCU(cudaMemsetAsync(offs, 0, 8, st));   // an empty batch still has offs[0] = 0
   if (slot[nd]) {
     k_rebase_offs<<<(unsigned)((slot[nd] + 255) / 256), 256, 0, st>>>(raw, d_meta, d_meta + nd + 1,
                                                                        d_meta + 2 * ((size_t)nd + 1), nd, offs,
-                                                                       ctx->status);
-    ++ctx->launch_count;
+                                                                       d_st);
+    ++S.launches;
   }
-  CU(cudaGetLastError());
-  // the staging copies read host memory that the caller may release after this call returns
-  CU(cudaStreamSynchronize(st));
+  SCU(cudaMemcpyAsync(h_st, d_st, 4, cudaMemcpyDeviceToHost, st));
+  SCU(cudaGetLastError());
+  SCU(cudaEventRecord(ctx->ev_copy[set], st));
   mb->msgs = msgs;
   mb->offs = offs;
   mb->s = sv;
   mb->R = Rv;
   mb->on_device = 1;
+  return POSLO_OK;
+}
+
+#undef SCU
+
+int poslo_host::stage_wait(poslo_ctx* ctx, int set, int issue_rc) {
+  if (set != 0 && set != 1) return fail(ctx, POSLO_EINVAL, "staging set must be 0 or 1");
+  StageSet& S = ctx->stage[set];
+  ctx->launch_count += S.launches;
+  // what was issued has to land before the requests' memory may be released, error or not
+  CU(cudaEventSynchronize(ctx->ev_copy[set]));
+  if (issue_rc != POSLO_OK) return fail(ctx, issue_rc, "staging: %s", S.err.c_str());
+  if (*reinterpret_cast<const uint32_t*>(S.h) & kErrInput)
+    return fail(ctx, POSLO_EINVAL, "message offsets decrease (or precede msgs)");
   return POSLO_OK;
 }
 
@@ -2522,7 +2629,18 @@ int poslo_host::aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, const ui
       return mb->dev_start[a + 1] - mb->dev_start[a] > mb->dev_start[b + 1] - mb->dev_start[b];
     });
     meta.insert(meta.end(), order.begin(), order.end());
+    // pieces of the segment sums (devices largest first, a device's pieces together) | the
+    // first piece of every device
+    std::vector<uint64_t> pfirst(nd);
+    for (uint64_t d : order) {
+      const uint64_t n_d = mb->dev_start[d + 1] - mb->dev_start[d];
+      const uint64_t np = n_d == 0 ? 1 : (n_d + kSegPiece - 1) / kSegPiece;
+      pfirst[d] = meta.size() - (5 * (size_t)nd + 2);
+      for (uint64_t k = 0; k < np; ++k) meta.push_back(d | (k << 32));
+    }
+    meta.insert(meta.end(), pfirst.begin(), pfirst.end());
   }
+  const uint64_t n_pieces = meta.size() - (6 * (size_t)nd + 2);
   uint64_t* d_meta;
   uint32_t *d_n2, *d_dsoff;
   DsNode* d_nodes;
@@ -2580,6 +2698,8 @@ int poslo_host::aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, const ui
   const uint64_t* seg_seed_off = d_meta + 2 * nd + 1;
   const uint64_t* seg_e0 = d_meta + 3 * nd + 2;
   const uint64_t* seg_order = d_meta + 4 * nd + 2;
+  const uint64_t* seg_pieces = d_meta + 5 * nd + 2;
+  const uint64_t* seg_pfirst = seg_pieces + n_pieces;
   // ---- workspace of the first stage
   const uint64_t N1 = std::max<uint64_t>(N, 1);
   uint32_t *seeds, *pts, *z, *P1, *segbuf, *tmpart;
@@ -2591,6 +2711,10 @@ int poslo_host::aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, const ui
   if ((rc = ensure_t(ctx, "badS", N1, &badS))) return rc;
   if ((rc = ensure_t(ctx, "e_all", 32 * N1, &d_e))) return rc;
   if ((rc = ensure_t(ctx, "z", 16 * N1, &z))) return rc;
+  unsigned long long* piece_limbs;
+  uint32_t* piece_R;
+  if ((rc = ensure_t(ctx, "m_piece_limbs", 8 * kSegLimbWords * n_pieces, &piece_limbs))) return rc;
+  if ((rc = ensure_t(ctx, "m_piece_R", 4 * 32 * n_pieces, &piece_R))) return rc;
   if ((rc = ensure_t(ctx, "m_P", 384, &P1))) return rc;
   if ((rc = ensure_t(ctx, "accept", 16, &d_acc))) return rc;
   if ((rc = ensure_t(ctx, "m_devflag", nd, &dev_flag))) return rc;
@@ -2726,8 +2850,13 @@ int poslo_host::aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, const ui
     {
       cudaEvent_t tb, te;
       timer_begin(ctx, "segment_sums", ctx->s_main, &tb, &te);
-      k_segment_sums<<<nd, kSegThreads, 0, ctx->s_main>>>(d_e, sb.s, z, pts, badR, badS, seg_start, seg_order, ss);
-      ++ctx->launch_count;
+      launch_segment_sums((unsigned)n_pieces, ctx->s_main, d_e, sb.s, z, pts, badR, badS, seg_start, seg_pieces,
+                          piece_limbs, piece_R, ss);
+      ctx->launch_count += 2;
+      if (n_pieces > nd) {
+        k_segment_combine<<<nd, kSegThreads, 0, ctx->s_main>>>(seg_start, seg_pfirst, piece_limbs, piece_R, nd, ss);
+        ++ctx->launch_count;
+      }
       if (per_window) {
         k_segment_window_sums<<<nd * nw, kSegThreads, 0, ctx->s_main>>>(d_e, sb.s, z, badR, badS, seg_start,
                                                                         seg_order, nd, ms.pl, Ewd, Swd);

@@ -2,13 +2,15 @@
 // registered once and kept by the service.  Not in the paper (it verifies one signer's log
 // at a time); built on the multi-device path.
 //
-// Requests are copied at submission and admitted against a device-memory budget (EBUSY when
-// it would be exceeded).  W worker threads, each with its own internal context (streams and
-// workspace), take the oldest pending requests up to a batch size whenever they are free and
-// verify them as one multi-device batch; with two workers a batch is staged and hashed
-// while the previous one finishes on the GPU.  A request that arrives while the workers are
-// busy joins the next batch.  Each request's result (accept bit and invalid indices) is by
-// definition independent of the batch it was verified in.
+// Requests are copied at submission (or lent in page-locked memory) and admitted against a
+// device-memory budget (EBUSY when it would be exceeded).  W worker threads, each with its
+// own internal context (streams and workspace), take the oldest pending requests up to a
+// batch size and verify them as one multi-device batch.  While no worker is idle, a worker
+// also takes its next batch before verifying the current one and stages it into its second
+// set of device buffers on its copy stream, so the copies of one batch overlap the
+// verification of the previous one on the same worker.  A request that arrives while the
+// workers are busy joins the next batch.  Each request's result (accept bit and invalid
+// indices) is by definition independent of the batch it was verified in.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -18,6 +20,7 @@
 #include <cstring>
 #include <deque>
 #include <functional>
+#include <future>
 #include <memory>
 #include <mutex>
 #include <thread>
@@ -48,7 +51,7 @@ struct Req {
 struct BatchRecord {
   uint32_t worker = 0, requests = 0;
   uint64_t entries = 0;
-  uint64_t t_take = 0, t_staged = 0, t_checked = 0, t_done = 0;
+  uint64_t t_take = 0, t_staged = 0, t_verify = 0, t_checked = 0, t_done = 0;
 };
 
 struct Server {
@@ -73,6 +76,7 @@ struct Server {
   uint32_t max_dev = 4096;
   uint64_t max_entries = 1ull << 22;
   uint64_t batches = 0, batched_requests = 0;
+  uint32_t idle = 0;   // workers waiting for requests with no batch in hand
 };
 
 namespace {
@@ -99,49 +103,84 @@ uint64_t since(const Server* S) {
 
 constexpr size_t kMaxTimeline = 1u << 20;   // records kept between two reads
 
-void run_batch(Server* S, poslo_ctx* w, uint32_t worker, std::vector<Req*>& batch) {
+// A batch taken by a worker: its requests, the multi-device description of them and the
+// staging set its inputs are copied into.
+struct TakenBatch {
+  std::vector<Req*> batch;
   BatchRecord rec;
-  rec.worker = worker;
-  rec.t_take = since(S);
-  const uint32_t nd = (uint32_t)batch.size();
-  std::vector<uint8_t> Y(32 * (size_t)nd), ds;
-  std::vector<uint64_t> start(nd + 1, 0), first(nd);
-  std::vector<uint32_t> n2(nd), ds_off(nd + 1, 0);
-  std::vector<const uint32_t*> tabs(nd);
-  std::vector<ReqView> views(nd);
+  int set = 0, rc = POSLO_OK;
+  uint64_t total = 0;
+  std::vector<uint8_t> Y, ds;
+  std::vector<uint64_t> start, first;
+  std::vector<uint32_t> n2, ds_off;
+  std::vector<const uint32_t*> tabs;
+  std::vector<ReqView> views;
+  poslo_multi_batch mb{};
+};
+
+// Describes the batch and issues the copies of its inputs into staging set `set` (nothing
+// waits for them here).
+std::unique_ptr<TakenBatch> issue_staging(Server* S, poslo_ctx* w, uint32_t worker, std::vector<Req*>&& batch,
+                                          int set) {
+  cudaSetDevice(w->device);   // also on a staging thread
+  auto B = std::make_unique<TakenBatch>();
+  B->batch = std::move(batch);
+  B->set = set;
+  B->rec.worker = worker;
+  B->rec.t_take = since(S);
+  const uint32_t nd = (uint32_t)B->batch.size();
+  B->Y.resize(32 * (size_t)nd);
+  B->start.assign(nd + 1, 0);
+  B->first.resize(nd);
+  B->n2.resize(nd);
+  B->ds_off.assign(nd + 1, 0);
+  B->tabs.resize(nd);
+  B->views.resize(nd);
   {
     std::lock_guard<std::mutex> lock(S->mu);
     const size_t words = key_table_words();
     for (uint32_t d = 0; d < nd; ++d) {
-      const uint32_t k = batch[d]->key_id;
-      memcpy(Y.data() + 32 * (size_t)d, S->keys[k].data(), 32);
-      tabs[d] = S->table_blocks[k / Server::kKeysPerBlock] + (size_t)(k % Server::kKeysPerBlock) * words;
+      const uint32_t k = B->batch[d]->key_id;
+      memcpy(B->Y.data() + 32 * (size_t)d, S->keys[k].data(), 32);
+      B->tabs[d] = S->table_blocks[k / Server::kKeysPerBlock] + (size_t)(k % Server::kKeysPerBlock) * words;
     }
   }
-  uint64_t total = 0;
   for (uint32_t d = 0; d < nd; ++d) {
-    Req* r = batch[d];
-    views[d] = r->view;
-    total += r->n;
-    start[d + 1] = start[d] + r->n;
-    first[d] = r->first_index;
-    n2[d] = r->n2;
-    ds.insert(ds.end(), r->ds.begin(), r->ds.end());
-    ds_off[d + 1] = ds_off[d] + (uint32_t)(r->ds.size() / 24);
+    Req* r = B->batch[d];
+    B->views[d] = r->view;
+    B->total += r->n;
+    B->start[d + 1] = B->start[d] + r->n;
+    B->first[d] = r->first_index;
+    B->n2[d] = r->n2;
+    B->ds.insert(B->ds.end(), r->ds.begin(), r->ds.end());
+    B->ds_off[d + 1] = B->ds_off[d] + (uint32_t)(r->ds.size() / 24);
   }
-  poslo_multi_batch mb{};
+  poslo_multi_batch& mb = B->mb;
   mb.n_dev = nd;
-  mb.Y = Y.data();
-  mb.dev_start = start.data();
-  mb.first_index = first.data();
-  mb.n2 = n2.data();
-  mb.ds = ds.data();
-  mb.ds_off = ds_off.data();
+  mb.Y = B->Y.data();
+  mb.dev_start = B->start.data();
+  mb.first_index = B->first.data();
+  mb.n2 = B->n2.data();
+  mb.ds = B->ds.data();
+  mb.ds_off = B->ds_off.data();
   // each request's inputs go straight from its own buffers into the worker's device staging
-  int rc = stage_requests(w, views.data(), nd, &mb);
-  rec.t_staged = since(S);
-  rec.requests = nd;
-  rec.entries = total;
+  B->rc = stage_requests(w, B->views.data(), nd, &mb, set);
+  B->rec.t_staged = since(S);
+  B->rec.requests = nd;
+  B->rec.entries = B->total;
+  return B;
+}
+
+// Waits for the batch's inputs, verifies it and publishes every request's result.
+void run_batch(Server* S, poslo_ctx* w, TakenBatch& B) {
+  std::vector<Req*>& batch = B.batch;
+  BatchRecord& rec = B.rec;
+  const uint32_t nd = (uint32_t)batch.size();
+  const uint64_t total = B.total;
+  poslo_multi_batch& mb = B.mb;
+  // what was issued lands before anything else, even when issuing failed part way
+  int rc = stage_wait(w, B.set, B.rc);
+  rec.t_verify = since(S);
   std::vector<uint8_t> acc(nd);
   std::vector<uint64_t> pairs(2 * std::max<uint64_t>(total, 1));
   uint64_t cnt = 0;
@@ -171,7 +210,7 @@ void run_batch(Server* S, poslo_ctx* w, uint32_t worker, std::vector<Req*>& batc
     }
     S->cv_done.notify_all();
   };
-  if (rc == POSLO_OK) rc = aver_multi(w, &mb, tabs.data(), acc.data(), pairs.data(), total, &cnt, &settled);
+  if (rc == POSLO_OK) rc = aver_multi(w, &mb, B.tabs.data(), acc.data(), pairs.data(), total, &cnt, &settled);
   rec.t_checked = since(S);
   std::vector<int> rcs(nd, rc);
   std::vector<std::vector<uint64_t>> inv(nd);
@@ -186,7 +225,7 @@ void run_batch(Server* S, poslo_ctx* w, uint32_t worker, std::vector<Req*>& batc
       b.variant = POSLO_VARIANT_F;
       b.n2 = r->n2;
       static const uint8_t kNone[32] = {0};
-      b.Y = Y.data() + 32 * (size_t)d;
+      b.Y = B.Y.data() + 32 * (size_t)d;
       b.msgs = r->view.msgs ? r->view.msgs : kNone;
       b.offs = r->view.offs;
       b.n = r->n;
@@ -227,24 +266,52 @@ void run_batch(Server* S, poslo_ctx* w, uint32_t worker, std::vector<Req*>& batc
 
 void worker_loop(Server* S, poslo_ctx* w, uint32_t worker) {
   cudaSetDevice(w->device);
+  std::unique_ptr<TakenBatch> cur;   // staged, not yet verified
+  int set = 0;
   for (;;) {
     std::vector<Req*> batch;
     {
       std::unique_lock<std::mutex> lock(S->mu);
-      S->cv_work.wait(lock, [&] { return S->stop || !S->pending.empty(); });
-      if (S->stop && S->pending.empty()) return;
-      uint64_t ent = 0;
-      while (!S->pending.empty() && batch.size() < S->max_dev) {
-        Req* r = S->pending.front();
-        if (!batch.empty() && ent + r->n > S->max_entries) break;
-        S->pending.pop_front();
-        r->state = 1;
-        batch.push_back(r);
-        ent += r->n;
+      if (!cur) {
+        ++S->idle;
+        S->cv_work.wait(lock, [&] { return S->stop || !S->pending.empty(); });
+        --S->idle;
+        if (S->stop && S->pending.empty()) return;
+      }
+      // with a batch in hand, take the next one only while no worker is idle: an idle worker
+      // verifies it at once, this one only after its current batch
+      if (!cur || S->idle == 0) {
+        uint64_t ent = 0;
+        while (!S->pending.empty() && batch.size() < S->max_dev) {
+          Req* r = S->pending.front();
+          if (!batch.empty() && ent + r->n > S->max_entries) break;
+          S->pending.pop_front();
+          r->state = 1;
+          batch.push_back(r);
+          ent += r->n;
+        }
       }
     }
-    run_batch(S, w, worker, batch);
-    S->cv_done.notify_all();
+    // the next batch's copies are issued on a staging thread (the calls take milliseconds for
+    // hundreds of requests) and run while the current batch is verified on this one
+    std::unique_ptr<TakenBatch> next;
+    if (!batch.empty()) {
+      if (cur) {
+        auto issue = std::async(std::launch::async, issue_staging, S, w, worker, std::move(batch), set);
+        run_batch(S, w, *cur);
+        S->cv_done.notify_all();
+        cur.reset();
+        next = issue.get();
+      } else {
+        next = issue_staging(S, w, worker, std::move(batch), set);
+      }
+      set ^= 1;
+    }
+    if (cur) {
+      run_batch(S, w, *cur);
+      S->cv_done.notify_all();
+    }
+    cur = std::move(next);
   }
 }
 
@@ -295,6 +362,9 @@ int poslo_serve_start(poslo_ctx* ctx, uint32_t workers, uint32_t max_batch_devic
       delete S;
       return rc;
     }
+    // served batches rarely repeat a shape: no graph captures on the workers' contexts (which
+    // also keeps every capture away from the staging threads' allocations)
+    w->graphs = false;
     S->wctx.push_back(w);
   }
   for (uint32_t k = 0; k < (uint32_t)S->wctx.size(); ++k)
@@ -444,6 +514,7 @@ int poslo_serve_timeline(poslo_ctx* ctx, poslo_batch_record* out, uint64_t cap, 
     out[i].entries = r.entries;
     out[i].t_take_ns = r.t_take;
     out[i].t_staged_ns = r.t_staged;
+    out[i].t_verify_ns = r.t_verify;
     out[i].t_checked_ns = r.t_checked;
     out[i].t_done_ns = r.t_done;
   }

@@ -74,8 +74,8 @@ class Partial(C.Structure):
 class BatchRecord(C.Structure):
     """poslo_batch_record: one served batch on the service's clock (ns)."""
     _fields_ = [("worker", C.c_uint32), ("requests", C.c_uint32), ("entries", C.c_uint64),
-                ("t_take_ns", C.c_uint64), ("t_staged_ns", C.c_uint64), ("t_checked_ns", C.c_uint64),
-                ("t_done_ns", C.c_uint64)]
+                ("t_take_ns", C.c_uint64), ("t_staged_ns", C.c_uint64), ("t_verify_ns", C.c_uint64),
+                ("t_checked_ns", C.c_uint64), ("t_done_ns", C.c_uint64)]
 
 
 class Request(C.Structure):

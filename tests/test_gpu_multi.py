@@ -230,3 +230,43 @@ def test_multi_both_check_forms(limit):
             assert list(acc) == want_acc
             assert [tuple(int(x) for x in p) for p in pairs] == want_pairs
     assert want_acc.count(False) >= 2
+
+
+def test_multi_devices_across_segment_pieces(ctx):
+    """Devices of 0, 1, 2047, 2048, 2049, 4097 and 6500 entries: the per-device sums are taken
+    in pieces of 2,048 entries and combined, so devices at and around the piece size, with
+    tampered, non-canonical and undecodable entries in later pieces, must still give every
+    device's own Distill result (C++ oracle, itself pinned to the Python oracle)."""
+    from oracle import cpp_oracle as X
+    D, n2 = 16, 4
+    sizes = [2049, 0, 1, 2048, 6500, 2047, 4097]
+    parts, want_acc, want_pairs = [], [], []
+    for d, n in enumerate(sizes):
+        km = synth.key_material(900 + d, v=16)
+        msgs = synth.messages(900 + d, n, 1, 60)
+        sub = synth.bpv_subsets(900 + d, n, v=16, k=4)
+        s, R = X.sign_f(km.y, km.root, D, n2, km.bpv_r, sub, msgs.data, msgs.offs, 0)
+        s, R = bytearray(s.tobytes()[:32 * n]), bytearray(R.tobytes()[:32 * n])
+        if n == 2049:      # non-canonical s in the second piece
+            v = int.from_bytes(bytes(s[32 * 2048:32 * 2049]), "little") + O.Q
+            s[32 * 2048:32 * 2049] = v.to_bytes(32, "little")
+        if n == 6500:      # flips in the third and fourth pieces, an undecodable R in the first
+            msgs = synth.apply_tamper(msgs, synth.Tamper(np.array([4500, 6499]), np.zeros(2, np.int64),
+                                                         np.array([0x21, 0x80], np.uint8)))
+            R[32 * 10:32 * 11] = (O.P + 1).to_bytes(32, "little")
+        if n == 4097:      # the entry alone in the last piece
+            msgs = synth.apply_tamper(msgs, synth.Tamper(np.array([4096]), np.zeros(1, np.int64),
+                                                         np.array([0x01], np.uint8)))
+        Y = X.base_mult(int.from_bytes(km.y, "little"))
+        ds = O.ds_serialize(O.ds_root(km.root, D))
+        inv, _, _ = X.distill_f(Y, msgs.data, msgs.offs, 0, n2, bytes(s), bytes(R), ds)
+        want_acc.append(not inv)
+        want_pairs += [(d, int(t)) for t in inv]
+        parts.append((Y, msgs, bytes(s), bytes(R), ds))
+    cat = synth.pack([m for p in parts for m in p[1].as_list()])
+    acc, pairs = ctx.aver_multi([p[0] for p in parts], sizes, [0] * len(sizes), [n2] * len(sizes),
+                                [p[4] for p in parts], cat.data, cat.offs, b"".join(p[2] for p in parts),
+                                b"".join(p[3] for p in parts))
+    assert list(acc) == want_acc and [tuple(int(x) for x in p) for p in pairs] == want_pairs
+    assert want_acc == [False, True, True, True, False, True, False]
+    assert (4, 10) in want_pairs and (4, 4500) in want_pairs and (6, 4096) in want_pairs

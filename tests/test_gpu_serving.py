@@ -159,7 +159,7 @@ def test_serving_malformed_request_fails_alone():
 
 
 def test_serving_timeline_accounts_for_every_batch():
-    """The per-batch records: one per batch run, every request counted once, the four times of
+    """The per-batch records: one per batch run, every request counted once, the five times of
     a batch in order, workers named by their index; reading them drains them."""
     import __graft_entry__
     __graft_entry__.build()
@@ -177,9 +177,30 @@ def test_serving_timeline_accounts_for_every_batch():
     assert len(recs) == batches and sum(r["requests"] for r in recs) == requests == len(reqs)
     assert sum(r["entries"] for r in recs) == sum(q["msgs"].n for q in reqs)
     for r in recs:
-        assert r["t_take_ns"] <= r["t_staged_ns"] <= r["t_checked_ns"] <= r["t_done_ns"]
+        assert r["t_take_ns"] <= r["t_staged_ns"] <= r["t_verify_ns"] <= r["t_checked_ns"] <= r["t_done_ns"]
         assert r["worker"] in (0, 1) and 1 <= r["requests"] <= 5
     assert again == []
+
+
+def test_serving_stages_next_batch_while_verifying():
+    """One busy worker takes its next batch before verifying the current one and issues that
+    batch's copies into its other staging set from a staging thread: consecutive batches
+    overlap on the worker's timeline, and every result still equals the definition (tampered
+    requests included)."""
+    import __graft_entry__
+    __graft_entry__.build()
+    keys, reqs = _requests(13, 3, 16)
+    with poslo.Context(device=0, verifier_seed=synth.verifier_seed(13)) as ctx:
+        ctx.serve_start(workers=1, max_batch_devices=2, max_batch_entries=1 << 20)
+        kid = [ctx.register_key(Y) for _, _, Y in keys]
+        tickets = [_submit(ctx, kid, q) for q in reqs]
+        got = [ctx.poll(t, wait_ms=60000) for t in tickets]
+        recs = sorted(ctx.serve_timeline(), key=lambda r: r["t_take_ns"])
+        ctx.serve_stop()
+    for q, (acc, inv) in zip(reqs, got):
+        assert (acc, list(inv)) == (not q["want"], q["want"])
+    overlapped = sum(1 for a, b in zip(recs, recs[1:]) if b["t_take_ns"] < a["t_checked_ns"])
+    assert len(recs) >= 8 and overlapped >= 1
 
 
 def test_serving_pinned_borrowed_requests_gathered():
