@@ -612,7 +612,7 @@ SERVE_REQUESTS = 1500
 SERVE_LO, SERVE_HI = 1, 65536
 SERVE_TAMPER_FRAC = 0.01
 SERVE_BUDGET = 64 << 30
-SERVE_WORKERS = 3
+SERVE_WORKERS = 2                      # each stages its next batch while verifying the current one
 SERVE_MAX_BATCH = 1 << 22              # entries per served batch at most
 SERVE_PER_LEVEL = 20000                # requests per load level, drawn from the SERVE_REQUESTS payloads
 
@@ -762,12 +762,22 @@ def bench_serving(ctx_factory, workers: int = SERVE_WORKERS, max_batch_entries: 
                 wait += max(0, r["t_verify_ns"] - busy_until) * 1e-9
         check = sum(r["t_checked_ns"] - r["t_verify_ns"] for r in recs) * 1e-9
         publish = sum(r["t_done_ns"] - r["t_checked_ns"] for r in recs) * 1e-9
-        busy = issue + wait + check + publish
+        busy = wait + check + publish
+        # steady state: the rate between the times 10 % and 90 % of the entries were done (the
+        # ramp while the first requests arrive and the drain of the last batches left out)
+        done = sorted(recs, key=lambda r: r["t_done_ns"])
+        cum = np.cumsum([r["entries"] for r in done])
+        t10 = done[int(np.searchsorted(cum, 0.1 * cum[-1]))]["t_done_ns"]
+        k90 = int(np.searchsorted(cum, 0.9 * cum[-1]))
+        t90 = done[k90]["t_done_ns"]
+        e10 = cum[int(np.searchsorted(cum, 0.1 * cum[-1]))]
+        steady = (cum[k90] - e10) / ((t90 - t10) * 1e-9) if t90 > t10 else None
         return {"batches": len(recs), "requests_per_batch": float(np.mean([r["requests"] for r in recs])),
                 "entries_per_batch": float(np.mean([r["entries"] for r in recs])),
-                "worker_s_issuing_copies": issue, "worker_s_waiting_for_copies": wait,
+                "staging_s_issuing_copies": issue, "worker_s_waiting_for_copies": wait,
                 "worker_s_verifying": check, "worker_s_publishing": publish,
-                "worker_idle_frac": max(0.0, 1.0 - busy / (workers * wall))}
+                "worker_idle_frac": max(0.0, 1.0 - busy / (workers * wall)),
+                "steady_entries_per_s": steady}
 
     svc.serve_timeline(1 << 20)      # drop the records of the warm-up
     # saturated (every request at t = 0): the service's peak
@@ -794,7 +804,9 @@ def bench_serving(ctx_factory, workers: int = SERVE_WORKERS, max_batch_entries: 
                         f"entries drawn uniformly; |m|~U[32,256], 1 % of payloads tampered, 64 GB budget, {workers} workers, "
                         f"batches of at most {max_batch_entries} entries, request data lent from pinned host "
                         "memory (POSLO_REQ_BORROW)",
-            "peak_entries_per_s": peak, "peak_timeline": sat_timeline, "levels": levels, "batches": batches,
+            "peak_entries_per_s": peak,
+            "steady_entries_per_s": sat_timeline["steady_entries_per_s"] if sat_timeline else None,
+            "peak_timeline": sat_timeline, "levels": levels, "batches": batches,
             "requests_served": nreq,
             "setup_s": setup_s}
     if not plain_path:

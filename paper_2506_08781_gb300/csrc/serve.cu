@@ -77,6 +77,7 @@ struct Server {
   uint64_t max_entries = 1ull << 22;
   uint64_t batches = 0, batched_requests = 0;
   uint32_t idle = 0;   // workers waiting for requests with no batch in hand
+  uint64_t pending_entries = 0;   // entries of the pending requests
 };
 
 namespace {
@@ -102,6 +103,7 @@ uint64_t since(const Server* S) {
 }
 
 constexpr size_t kMaxTimeline = 1u << 20;   // records kept between two reads
+constexpr uint64_t kMinShare = 1u << 16;     // entries: below this a batch is not split further
 
 // A batch taken by a worker: its requests, the multi-device description of them and the
 // staging set its inputs are copied into.
@@ -281,11 +283,17 @@ void worker_loop(Server* S, poslo_ctx* w, uint32_t worker) {
       // with a batch in hand, take the next one only while no worker is idle: an idle worker
       // verifies it at once, this one only after its current batch
       if (!cur || S->idle == 0) {
+        // when fewer entries wait than the workers' next batches hold, an even share each, so
+        // that the last batches of a burst end together rather than one after another
+        const uint64_t W = S->wctx.size();
+        uint64_t cap = S->max_entries;
+        if (S->pending_entries < W * cap) cap = std::max<uint64_t>((S->pending_entries + W - 1) / W, kMinShare);
         uint64_t ent = 0;
         while (!S->pending.empty() && batch.size() < S->max_dev) {
           Req* r = S->pending.front();
-          if (!batch.empty() && ent + r->n > S->max_entries) break;
+          if (!batch.empty() && ent + r->n > cap) break;
           S->pending.pop_front();
+          S->pending_entries -= r->n;
           r->state = 1;
           batch.push_back(r);
           ent += r->n;
@@ -461,6 +469,7 @@ int poslo_submit(poslo_ctx* ctx, const poslo_request* q, uint64_t* ticket) {
     r->ticket = S->next_ticket++;
     *ticket = r->ticket;
     S->pending.push_back(r.get());
+    S->pending_entries += r->n;
     S->reqs.emplace(r->ticket, std::move(r));
   }
   S->cv_work.notify_one();
