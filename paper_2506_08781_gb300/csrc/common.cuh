@@ -330,6 +330,23 @@ __device__ __forceinline__ sc limb_sums_to_scalar(const unsigned long long* sums
 //                  [e]Y + [s]G taken from the two fixed-window tables (128 additions)
 
 
+//   k_entry_check_quad  the same check, one quad of lanes per entry (quad-cooperative table
+//                  additions), on the decoded points and malformed flags of the first stage:
+//                  the direct localisation of small batches, where the latency of one entry is
+//                  the latency of the launch
+struct DirectCheckArgs {
+  const uint8_t* e;          // n*32 (from k_hash)
+  const uint8_t* s;          // n*32
+  const uint32_t* pts;       // n*kPtsWords decoded R_t (from k_points)
+  const uint8_t* badR;       // n: R_t does not decode
+  const uint8_t* badS;       // n: s_t not canonical
+  uint64_t n;
+  const uint32_t* tableY;
+  const uint32_t* tableG;
+  uint8_t* invalid;          // n bytes: 1 = entry fails its own check
+};
+__global__ void __launch_bounds__(128) k_entry_check_quad(const DirectCheckArgs a);
+
 __device__ __forceinline__ ge double_scalar_tables(const uint32_t e[8], const uint32_t s[8],
                                                    const uint32_t* tableY, const uint32_t* tableG) {
   int8_t de[64], ds_[64];

@@ -24,6 +24,33 @@ __global__ void __launch_bounds__(128) k_entry_check(const CheckArgs a) {
   }
 }
 
+// One quad of lanes per entry; every lane runs every quad operation (full-mask shuffles), so
+// surplus quads repeat the last entry and do not write.
+__global__ void __launch_bounds__(128) k_entry_check_quad(const DirectCheckArgs a) {
+  const uint64_t quad = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 2;
+  if (a.n == 0) return;   // grid-uniform
+  const uint64_t t = quad < a.n ? quad : a.n - 1;
+  const uint4* ep = reinterpret_cast<const uint4*>(a.e + 32 * t);
+  const uint4* sp = reinterpret_cast<const uint4*>(a.s + 32 * t);
+  const uint4 e0 = ep[0], e1 = ep[1], s0 = __ldg(sp), s1 = __ldg(sp + 1);
+  const uint32_t e[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
+  const uint32_t s[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+  ge acc = ge_identity();
+  int ce = 0, cs = 0;
+  for (int w = 0; w < kTableWindows; ++w) {
+    acc = ge_add_quad(acc, table_pick(a.tableY, w, sc_digit4(e, w, ce)));
+    acc = ge_add_quad(acc, table_pick(a.tableG, w, sc_digit4(s, w, cs)));
+  }
+  ge R;
+  fe t2d;
+  pts_load(a.pts + (size_t)kPtsWords * t, R.X, R.Y, t2d);
+  R.Z = fe_one();
+  R.T = fe_mul(R.X, R.Y);
+  const ge d = ge_sub(R, acc);
+  const bool ok = !a.badR[t] && !a.badS[t] && ge_is_identity(ge_dbl_quad(ge_dbl_quad(ge_dbl_quad(d))));
+  if ((threadIdx.x & 3) == 0 && quad < a.n) a.invalid[t] = ok ? 0 : 1;
+}
+
 __global__ void __launch_bounds__(kHashThreads) k_sum_scalars(const uint8_t* s, uint64_t n, const uint8_t* skip,
                                                              unsigned long long* partial) {
   acc13 acc;

@@ -62,27 +62,41 @@ def _shift(s, t, d):
     s[32 * t:32 * t + 32] = v.to_bytes(32, "little")
 
 
-@pytest.mark.parametrize("n,count", [(700, 1), (700, 60), (1 << 15, 5), (1 << 15, 300), (1 << 15, 3000)])
+@pytest.mark.parametrize("n,count", [(16385, 1), (20000, 60), (1 << 15, 5), (1 << 15, 300), (1 << 15, 3000)])
 def test_tampered_entries_confirmed_without_fallback(ctx, n, count):
-    """Sparse to dense one-byte flips (the descent jumps several levels while few nodes fail,
-    one level at a time when many do); the confirmation by subtraction accepts at once."""
+    """Sparse to dense one-byte flips above the direct-check size (the descent jumps several
+    levels while few nodes fail, one level at a time when many do); the confirmation by
+    subtraction accepts at once."""
     Y, msgs, s, R, ds = _log(60 + count, n)
     plan = synth.tamper_plan(count, msgs, count)
     bad = synth.apply_tamper(msgs, plan)
-    want, fallback = _run(ctx, Y, bad, s, R, ds, python_too=n <= 700)
+    want, fallback = _run(ctx, Y, bad, s, R, ds)
     assert want == [int(t) for t in plan.idx] and fallback == 0
+    assert ctx.kernel_time("bisect")[1] >= 1 and ctx.kernel_time("direct")[1] == 0
+
+
+@pytest.mark.parametrize("n,count", [(1, 1), (700, 1), (700, 60), (4096, 400), (16384, 30)])
+def test_small_batches_checked_entry_by_entry(ctx, n, count):
+    """Up to 16,384 entries Distill localises by every entry's own check in one launch (no tree,
+    no descent, no confirmation): the list and ccd^v are the oracle's."""
+    Y, msgs, s, R, ds = _log(80 + count, n)
+    plan = synth.tamper_plan(count, msgs, count)
+    bad = synth.apply_tamper(msgs, plan)
+    want, fallback = _run(ctx, Y, bad, s, R, ds, python_too=n <= 700)
+    assert want == sorted(int(t) for t in plan.idx) and fallback == 0
+    assert ctx.kernel_time("direct")[1] == 1 and ctx.kernel_time("bisect")[1] == 0
 
 
 def test_malformed_and_tampered_confirmed_without_fallback(ctx):
     """Undecodable R_t and non-canonical s_t are flagged before the descent; the subtraction
     leaves out the undecodable points (never in the batch's sum) and takes out the others."""
-    n = 300
+    n = 20000
     Y, msgs, s, R, ds = _log(71, n)
     s[32 * 10:32 * 11] = (int.from_bytes(bytes(s[32 * 10:32 * 11]), "little") + O.Q).to_bytes(32, "little")
     R[32 * 200:32 * 201] = (O.P + 1).to_bytes(32, "little")
     bad = synth.apply_tamper(msgs, synth.tamper_plan(71, msgs, 3))
-    want, fallback = _run(ctx, Y, bad, s, R, ds, python_too=True)
-    assert 10 in want and 200 in want and fallback == 0
+    want, fallback = _run(ctx, Y, bad, s, R, ds)
+    assert 10 in want and 200 in want and fallback == 0 and ctx.kernel_time("bisect")[1] >= 1
 
 
 def test_cancelling_pair_in_one_leaf_pair_needs_the_fallback(ctx):
@@ -100,7 +114,7 @@ def test_cancelling_pair_in_one_leaf_pair_needs_the_fallback(ctx):
 def test_cancelling_pair_far_apart_found_by_the_descent(ctx):
     """s_3 + d and s_5000 - d sit in different subtrees: the nodes holding one of them fail, so
     the descent flags both and the confirmation accepts the rest."""
-    n = 1 << 13
+    n = 1 << 15
     Y, msgs, s, R, ds = _log(73, n)
     _shift(s, 3, 777)
     _shift(s, 5000, -777)

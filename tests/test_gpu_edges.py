@@ -314,3 +314,34 @@ def test_served_request_edges():
                 assert acc is (not want) and list(idx) == want
         finally:
             c.serve_stop()
+
+
+def test_all_edges_through_the_descent(ctx):
+    """The same edges spread over a batch above the direct-check size (16,384 entries), so that
+    Distill localises them by the descent over the segment tree and the confirmation, not by
+    every entry's own check; signed and checked by the C++ oracle (pinned to the Python one)."""
+    import types
+    from oracle import cpp_oracle as X
+    n, first, depth = 16400, 8, 13         # 2^13 epochs of N2 = 4 entries hold the batch
+    km = synth.key_material(75, v=16)
+    msgs = synth.messages(75, n, 1, 70)
+    sub = synth.bpv_subsets(75, n, first_index=first, v=16, k=4)
+    sa, Ra = X.sign_f(km.y, km.root, depth, N2, km.bpv_r, sub, msgs.data, msgs.offs, first)
+    sb, Rb = sa.tobytes(), Ra.tobytes()
+    s = [sb[32 * t:32 * t + 32] for t in range(n)]
+    R = [Rb[32 * t:32 * t + 32] for t in range(n)]
+    sk = types.SimpleNamespace(y=int.from_bytes(km.y, "little"))
+    Y = X.base_mult(sk.y)
+    ds = O.ds_root(km.root, depth)
+    names = list(EDGES)
+    s, R, bad = _apply(sk, Y, msgs, s, R, ds, {100 + 941 * k: names[k] for k in range(len(names))}, first=first)
+    want, ws, wR = X.distill_f(Y, msgs.data, msgs.offs, first, N2, b"".join(s), b"".join(R), O.ds_serialize(ds))
+    assert want == bad and len(want) == len(INVALID)
+    b = _gpu_batch(ctx, Y, msgs, s, R, ds, first=first)
+    assert ctx.aver(b, poslo.AGG_UNIT) is False and ctx.aver(b, poslo.AGG_WEIGHTED) is False
+    ctx.set_profiling(True)
+    ctx.reset_kernel_times()
+    idx, cs, cR = ctx.distill(b)
+    ctx.set_profiling(False)
+    assert ctx.kernel_time("bisect")[1] >= 1 and ctx.kernel_time("direct")[1] == 0
+    assert list(idx) == want and cs == ws and cR == wR
