@@ -330,10 +330,10 @@ __device__ __forceinline__ sc limb_sums_to_scalar(const unsigned long long* sums
 //                  [e]Y + [s]G taken from the two fixed-window tables (128 additions)
 
 
-//   k_entry_check_quad  the same check, one quad of lanes per entry (quad-cooperative table
-//                  additions), on the decoded points and malformed flags of the first stage:
-//                  the direct localisation of small batches, where the latency of one entry is
-//                  the latency of the launch
+//   k_entry_check_group  the same check, eight lanes per entry (two quads summing the Y and
+//                  the G terms side by side with quad-cooperative additions), on the decoded
+//                  points and malformed flags of the first stage: the direct localisation of
+//                  small batches, where the latency of one entry is the latency of the launch
 struct DirectCheckArgs {
   const uint8_t* e;          // n*32 (from k_hash)
   const uint8_t* s;          // n*32
@@ -345,7 +345,7 @@ struct DirectCheckArgs {
   const uint32_t* tableG;
   uint8_t* invalid;          // n bytes: 1 = entry fails its own check
 };
-__global__ void __launch_bounds__(128) k_entry_check_quad(const DirectCheckArgs a);
+__global__ void __launch_bounds__(128) k_entry_check_group(const DirectCheckArgs a);
 
 __device__ __forceinline__ ge double_scalar_tables(const uint32_t e[8], const uint32_t s[8],
                                                    const uint32_t* tableY, const uint32_t* tableG) {
@@ -746,7 +746,7 @@ __global__ void k_gather_flagged(const uint32_t* pts, const uint32_t* z, const u
                                  uint64_t cnt, uint32_t* gp, uint32_t* gz, uint8_t* gs);
 __global__ void k_point_diff(const uint32_t* a, const uint32_t* b, uint32_t* out);
 __global__ void __launch_bounds__(256) k_ccd_points(const uint32_t* pts, const uint8_t* badR, const uint64_t* idx,
-                                                    uint64_t nf, const uint32_t* unit, uint8_t* enc_out);
+                                                    const uint64_t* nf_dev, const uint32_t* unit, uint8_t* enc_out);
 __global__ void __launch_bounds__(kHashThreads) k_weighted_sums(const uint8_t* e, const uint8_t* s, const uint32_t* z, const uint8_t* skip1,
                                 const uint8_t* skip2, uint64_t n, unsigned long long* partial);
 __global__ void __launch_bounds__(kPointThreads) k_pts_sum(const uint32_t* pts, const uint8_t* skip1, const uint8_t* skip2, uint64_t n,

@@ -24,23 +24,37 @@ __global__ void __launch_bounds__(128) k_entry_check(const CheckArgs a) {
   }
 }
 
-// One quad of lanes per entry; every lane runs every quad operation (full-mask shuffles), so
-// surplus quads repeat the last entry and do not write.
-__global__ void __launch_bounds__(128) k_entry_check_quad(const DirectCheckArgs a) {
-  const uint64_t quad = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 2;
+// Eight lanes per entry: the first quad sums the 64 terms of [e]Y from Y's window table, the
+// second the 64 of [s]G from G's, each fetching the next window's entry during the current
+// addition; the two sums meet by shuffles.  Every lane runs every quad operation (full-mask
+// shuffles), so surplus groups repeat the last entry and do not write.
+__global__ void __launch_bounds__(128) k_entry_check_group(const DirectCheckArgs a) {
+  const uint64_t grp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
   if (a.n == 0) return;   // grid-uniform
-  const uint64_t t = quad < a.n ? quad : a.n - 1;
-  const uint4* ep = reinterpret_cast<const uint4*>(a.e + 32 * t);
-  const uint4* sp = reinterpret_cast<const uint4*>(a.s + 32 * t);
-  const uint4 e0 = ep[0], e1 = ep[1], s0 = __ldg(sp), s1 = __ldg(sp + 1);
-  const uint32_t e[8] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z, e1.w};
-  const uint32_t s[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+  const uint64_t t = grp < a.n ? grp : a.n - 1;
+  const bool g_half = (threadIdx.x & 4) != 0;
+  const uint4* kp = reinterpret_cast<const uint4*>((g_half ? a.s : a.e) + 32 * t);
+  const uint4 k0 = __ldg(kp), k1 = __ldg(kp + 1);
+  const uint32_t k[8] = {k0.x, k0.y, k0.z, k0.w, k1.x, k1.y, k1.z, k1.w};
+  const uint32_t* tab = g_half ? a.tableG : a.tableY;
   ge acc = ge_identity();
-  int ce = 0, cs = 0;
+  int carry = 0;
+  ge next = table_pick(tab, 0, sc_digit4(k, 0, carry));
   for (int w = 0; w < kTableWindows; ++w) {
-    acc = ge_add_quad(acc, table_pick(a.tableY, w, sc_digit4(e, w, ce)));
-    acc = ge_add_quad(acc, table_pick(a.tableG, w, sc_digit4(s, w, cs)));
+    const ge cur = next;
+    if (w + 1 < kTableWindows) next = table_pick(tab, w + 1, sc_digit4(k, w + 1, carry));
+    acc = ge_add_quad(acc, cur);
   }
+  // both quads: [e]Y + [s]G
+  ge other;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    other.X.v[i] = __shfl_xor_sync(0xffffffffu, acc.X.v[i], 4);
+    other.Y.v[i] = __shfl_xor_sync(0xffffffffu, acc.Y.v[i], 4);
+    other.Z.v[i] = __shfl_xor_sync(0xffffffffu, acc.Z.v[i], 4);
+    other.T.v[i] = __shfl_xor_sync(0xffffffffu, acc.T.v[i], 4);
+  }
+  acc = ge_add_quad(acc, other);
   ge R;
   fe t2d;
   pts_load(a.pts + (size_t)kPtsWords * t, R.X, R.Y, t2d);
@@ -48,7 +62,7 @@ __global__ void __launch_bounds__(128) k_entry_check_quad(const DirectCheckArgs 
   R.T = fe_mul(R.X, R.Y);
   const ge d = ge_sub(R, acc);
   const bool ok = !a.badR[t] && !a.badS[t] && ge_is_identity(ge_dbl_quad(ge_dbl_quad(ge_dbl_quad(d))));
-  if ((threadIdx.x & 3) == 0 && quad < a.n) a.invalid[t] = ok ? 0 : 1;
+  if ((threadIdx.x & 7) == 0 && grp < a.n) a.invalid[t] = ok ? 0 : 1;
 }
 
 __global__ void __launch_bounds__(kHashThreads) k_sum_scalars(const uint8_t* s, uint64_t n, const uint8_t* skip,

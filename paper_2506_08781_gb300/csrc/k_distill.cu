@@ -264,12 +264,14 @@ __global__ void k_gather_flagged(const uint32_t* pts, const uint32_t* z, const u
 }
 
 // ccd^v's point: the batch's unit sum of its decodable R_t (unit, 32 words) minus the flagged
-// entries' decodable R_t (local indices idx[0 .. nf)), encoded to enc_out (32 bytes).  One
-// block: the flagged points are few next to the batch.
+// entries' decodable R_t (local indices idx[0 .. *nf_dev), the count left in device memory by
+// the compaction), encoded to enc_out (32 bytes).  One block: the flagged points are few next
+// to the batch.
 __global__ void __launch_bounds__(256) k_ccd_points(const uint32_t* pts, const uint8_t* badR, const uint64_t* idx,
-                                                    uint64_t nf, const uint32_t* unit, uint8_t* enc_out) {
+                                                    const uint64_t* nf_dev, const uint32_t* unit, uint8_t* enc_out) {
   __shared__ uint32_t sp[256][32];
   ge acc = ge_identity();
+  const uint64_t nf = *nf_dev;
   for (uint64_t i = threadIdx.x; i < nf; i += blockDim.x) {
     const uint64_t t = idx[i];
     if (badR && badR[t]) continue;

@@ -324,9 +324,9 @@ int validate_batch(poslo_ctx* ctx, const poslo_batch* b) {
 // localisation; longer logs go through poslo_distill_stream in chunks.
 constexpr uint64_t kMaxCallEntries = (1ull << 32) - 1;
 // Distill batches up to this many entries are localised by every entry's own check (one
-// quad-cooperative launch) rather than by the descent over the segment tree: measured on
-// GB300, 0.28 ms of checking at 4,096 entries and 0.60 ms at 16,384 against 1.0 ms of tree,
-// descent and confirmation; the two meet near 32,768.
+// launch, eight lanes per entry) rather than by the descent over the segment tree: measured
+// on GB300, 0.18 ms of checking at 4,096 entries and 0.56 ms at 16,384 against 1.0 ms of
+// tree, descent and confirmation; the two meet near 32,768.
 constexpr uint64_t kDirectCheckMax = 16384;
 
 // Host inputs are copied R_t first: ev_staged marks their arrival, so the decoding (the
@@ -1821,7 +1821,7 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
     a.invalid = inv;
     cudaEvent_t tb, te;
     timer_begin(ctx, "direct", ctx->s_main, &tb, &te);
-    k_entry_check_quad<<<(unsigned)((4 * n + 127) / 128), 128, 0, ctx->s_main>>>(a);
+    k_entry_check_group<<<(unsigned)((8 * n + 127) / 128), 128, 0, ctx->s_main>>>(a);
     ++ctx->launch_count;
     CU(cudaGetLastError());
     timer_end(ctx, "direct", ctx->s_main, tb, te);
@@ -1952,12 +1952,10 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
     k_sum_scalars<<<sblocks, kHashThreads, 0, ctx->s_main>>>(sb.s, n, inv, sp);
     k_reduce_scalars<<<1, 256, 0, ctx->s_main>>>(sp, sblocks, d_ccd);
     ctx->launch_count += 2;
-    if (!confirmed) {   // the per-entry checks changed the flags: list them again
-      if ((rc = run_compact(ctx, inv, n, 0, fidx, n, fidx + n))) return rc;
-      CU(cudaMemcpyAsync(&nf, fidx + n, 8, cudaMemcpyDeviceToHost, ctx->s_main));
-      CU(cudaStreamSynchronize(ctx->s_main));
-    }
-    k_ccd_points<<<1, 256, 0, ctx->s_main>>>(pts, badR, fidx, nf, unitR, d_ccd + 32);
+    // the per-entry checks set the flags (direct localisation, or the fallback after a failed
+    // confirmation): list them again; the count stays on the device for k_ccd_points
+    if (!confirmed && (rc = run_compact(ctx, inv, n, 0, fidx, n, fidx + n))) return rc;
+    k_ccd_points<<<1, 256, 0, ctx->s_main>>>(pts, badR, fidx, fidx + n, unitR, d_ccd + 32);
     ++ctx->launch_count;
     CU(cudaGetLastError());
   }
