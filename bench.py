@@ -239,7 +239,38 @@ def make_multi_workload(ctx, n_dev=MULTI_DEVICES, lo=MULTI_LO, hi=MULTI_HI, seed
                 R=np.concatenate(Rs), ds=dss, pairs=sorted(pairs), total=total)
 
 
-def bench_multi(ctx, steps: int, warmup: int) -> dict:
+MULTI_ORACLE_EVERY = 64                # the C++ oracle verifies every 64th device of the workload
+
+
+def multi_oracle_subsample(w, every: int = MULTI_ORACLE_EVERY) -> dict:
+    """The C++ oracle's per-device Distill (the definition) on every `every`-th device of the
+    4,096-device workload, entries split over all host cores; its lists are checked against
+    the tamper plan's pairs of those devices."""
+    from oracle import cpp_oracle as X
+    cores = host_cores()
+    sizes = w["sizes"]
+    start = np.zeros(len(sizes) + 1, np.int64)
+    start[1:] = np.cumsum(sizes)
+    devices = list(range(0, len(sizes), every))
+    n, found = 0, []
+    t0 = time.perf_counter()
+    for d in devices:
+        lo, hi = int(start[d]), int(start[d + 1])
+        inv, _, _ = X.distill_f(w["Y"][d], w["msgs"].data, w["msgs"].offs[lo:hi + 1], 0, MULTI_N2,
+                                w["s"][32 * lo:32 * hi], w["R"][32 * lo:32 * hi], w["ds"][d], cores)
+        found += [(d, int(t)) for t in inv]
+        n += hi - lo
+    sec = time.perf_counter() - t0
+    assert found == [p for p in w["pairs"] if p[0] % every == 0], "the C++ oracle's lists differ from the plan"
+    rate = n / sec
+    return {"value": rate, "unit": "entries/s", "cores": cores, "kind": "oracle",
+            "implementation": "C++ oracle (oracle/poslo_oracle.cpp)",
+            "sample": f"every {every}th device ({len(devices)} devices, {n} of the {w['total']} entries) verified "
+                      f"by the C++ oracle's per-device Distill on {cores} std::thread workers in {sec:.1f} s; "
+                      f"the whole workload at this rate: {w['total'] / rate / 60:.0f} min"}
+
+
+def bench_multi(ctx, steps: int, warmup: int, cpu: bool = False) -> dict:
     import torch
     from paper_2506_08781_gb300 import poslo
     t0 = time.perf_counter()
@@ -283,7 +314,7 @@ def bench_multi(ctx, steps: int, warmup: int) -> dict:
                         f"|m|~U[32,256], {len(w['pairs'])} devices with one flipped byte",
             "value": w["total"] / (ms * 1e-3), "unit": "entries/s", "ms_per_step": ms, "steps": steps,
             "invalid_found": len(got), "setup_s": setup_s, "msm_window": msm_window, "msm_range_log2": msm_range,
-            "stages": stages}
+            "stages": stages, "cpu_baseline": multi_oracle_subsample(w) if cpu else None}
 
 
 # ------------------------------------------------------------------------------ Distill with tampered entries
@@ -1047,7 +1078,7 @@ def run_ours(args):
     multi = None
     replay = None
     if not args.no_multi and world == 1:
-        multi = bench_multi(ctx, steps=max(2, args.steps // 5), warmup=2)
+        multi = bench_multi(ctx, steps=max(2, args.steps // 5), warmup=2, cpu=not args.no_cpu_baseline)
         replay = bench_graph_replay(ctx)
     serving = None
     if not args.no_serving and world == 1:
