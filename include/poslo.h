@@ -52,7 +52,9 @@ typedef enum {
   POSLO_EINVAL = -1,    /* malformed argument: sizes, bad public key, seed not disclosed (SRet bottom) */
   POSLO_ENOMEM = -2,    /* device memory could not be allocated or the context budget is exceeded */
   POSLO_EDEVICE = -3,   /* CUDA error (no device, launch failure) */
-  POSLO_ETIMEOUT = -4,  /* a bounded device-side wait expired */
+  POSLO_ETIMEOUT = -4,  /* a bounded device-side wait expired.  Reserved: no kernel of this
+                           library waits on a flag or on another block (every step is its own
+                           launch, ordered by streams and events), so no call returns it */
   POSLO_EBUFSMALL = -5, /* an output buffer is too small; the needed count is still reported */
   POSLO_EBUSY = -6,     /* serving: admission refused by the memory budget */
   POSLO_ENOTFOUND = -7, /* serving: unknown key id or ticket */
