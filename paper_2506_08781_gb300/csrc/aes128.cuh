@@ -89,37 +89,67 @@ __device__ __forceinline__ uint32_t aes_sub4(const AesCtx& c, uint32_t a, uint32
          (c.T<0>(d) & 0x00ff0000u) >> 16;
 }
 
+// State of one FIPS-197 Cipher (Nk = 4, Nr = 10) between rounds: the round key k and the
+// state s, both as four big-endian column words.
+struct AesState {
+  uint32_t k0, k1, k2, k3, s0, s1, s2, s3;
+};
+
+__device__ __forceinline__ AesState aes_begin(const uint32_t key[4], const uint32_t in[4]) {
+  return AesState{key[0], key[1], key[2], key[3], in[0] ^ key[0], in[1] ^ key[1], in[2] ^ key[2], in[3] ^ key[3]};
+}
+
+// Round r (1..10) with round constant rcon = x^(r-1).
+__device__ __forceinline__ void aes_round(const AesCtx& c, AesState& a, int r, uint32_t rcon) {
+  // round key r from round key r-1: SubWord(RotWord(w3)) ^ Rcon into w0, then the chain
+  // (RotWord moves byte 2 of w3 to the top, so SubWord(RotWord(w3)) = S(w3 bytes 2,1,0,3))
+  const uint32_t sub = aes_sub4(c, a.k3 << 8, a.k3 << 8, a.k3 << 8, a.k3 >> 24);
+  a.k0 ^= sub ^ (rcon << 24);
+  a.k1 ^= a.k0;
+  a.k2 ^= a.k1;
+  a.k3 ^= a.k2;
+  uint32_t t0, t1, t2, t3;
+  if (r < 10) {
+    t0 = c.T<3>(a.s0) ^ ror32(c.T<2>(a.s1), 8) ^ ror32(c.T<1>(a.s2), 16) ^ ror32(c.T<0>(a.s3), 24) ^ a.k0;
+    t1 = c.T<3>(a.s1) ^ ror32(c.T<2>(a.s2), 8) ^ ror32(c.T<1>(a.s3), 16) ^ ror32(c.T<0>(a.s0), 24) ^ a.k1;
+    t2 = c.T<3>(a.s2) ^ ror32(c.T<2>(a.s3), 8) ^ ror32(c.T<1>(a.s0), 16) ^ ror32(c.T<0>(a.s1), 24) ^ a.k2;
+    t3 = c.T<3>(a.s3) ^ ror32(c.T<2>(a.s0), 8) ^ ror32(c.T<1>(a.s1), 16) ^ ror32(c.T<0>(a.s2), 24) ^ a.k3;
+  } else {   // last round: no MixColumns
+    t0 = aes_sub4(c, a.s0, a.s1, a.s2, a.s3) ^ a.k0;
+    t1 = aes_sub4(c, a.s1, a.s2, a.s3, a.s0) ^ a.k1;
+    t2 = aes_sub4(c, a.s2, a.s3, a.s0, a.s1) ^ a.k2;
+    t3 = aes_sub4(c, a.s3, a.s0, a.s1, a.s2) ^ a.k3;
+  }
+  a.s0 = t0; a.s1 = t1; a.s2 = t2; a.s3 = t3;
+}
+
 // E_key(in): FIPS-197 Cipher with Nk = 4, Nr = 10.
 __device__ __forceinline__ void aes128_encrypt(const AesCtx& c, const uint32_t key[4], const uint32_t in[4],
                                                uint32_t out[4]) {
-  uint32_t k0 = key[0], k1 = key[1], k2 = key[2], k3 = key[3];
-  uint32_t s0 = in[0] ^ k0, s1 = in[1] ^ k1, s2 = in[2] ^ k2, s3 = in[3] ^ k3;
+  AesState a = aes_begin(key, in);
   uint32_t rcon = 0x01u;
 #pragma unroll 1
   for (int r = 1; r <= 10; ++r) {
-    // round key r from round key r-1: SubWord(RotWord(w3)) ^ Rcon into w0, then the chain
-    // (RotWord moves byte 2 of w3 to the top, so SubWord(RotWord(w3)) = S(w3 bytes 2,1,0,3))
-    const uint32_t sub = aes_sub4(c, k3 << 8, k3 << 8, k3 << 8, k3 >> 24);
-    k0 ^= sub ^ (rcon << 24);
-    k1 ^= k0;
-    k2 ^= k1;
-    k3 ^= k2;
+    aes_round(c, a, r, rcon);
     rcon = gf8_xtime(rcon);
-    uint32_t t0, t1, t2, t3;
-    if (r < 10) {
-      t0 = c.T<3>(s0) ^ ror32(c.T<2>(s1), 8) ^ ror32(c.T<1>(s2), 16) ^ ror32(c.T<0>(s3), 24) ^ k0;
-      t1 = c.T<3>(s1) ^ ror32(c.T<2>(s2), 8) ^ ror32(c.T<1>(s3), 16) ^ ror32(c.T<0>(s0), 24) ^ k1;
-      t2 = c.T<3>(s2) ^ ror32(c.T<2>(s3), 8) ^ ror32(c.T<1>(s0), 16) ^ ror32(c.T<0>(s1), 24) ^ k2;
-      t3 = c.T<3>(s3) ^ ror32(c.T<2>(s0), 8) ^ ror32(c.T<1>(s1), 16) ^ ror32(c.T<0>(s2), 24) ^ k3;
-    } else {   // last round: no MixColumns
-      t0 = aes_sub4(c, s0, s1, s2, s3) ^ k0;
-      t1 = aes_sub4(c, s1, s2, s3, s0) ^ k1;
-      t2 = aes_sub4(c, s2, s3, s0, s1) ^ k2;
-      t3 = aes_sub4(c, s3, s0, s1, s2) ^ k3;
-    }
-    s0 = t0; s1 = t1; s2 = t2; s3 = t3;
   }
-  out[0] = s0; out[1] = s1; out[2] = s2; out[3] = s3;
+  out[0] = a.s0; out[1] = a.s1; out[2] = a.s2; out[3] = a.s3;
+}
+
+// E_keyA(in) and E_keyB(in) with their rounds interleaved: two independent chains in one
+// loop, so each one's table reads and XORs fill the other's dependency gaps.
+__device__ __forceinline__ void aes128_encrypt2(const AesCtx& c, const uint32_t keyA[4], const uint32_t keyB[4],
+                                                const uint32_t in[4], uint32_t outA[4], uint32_t outB[4]) {
+  AesState a = aes_begin(keyA, in), b = aes_begin(keyB, in);
+  uint32_t rcon = 0x01u;
+#pragma unroll 1
+  for (int r = 1; r <= 10; ++r) {
+    aes_round(c, a, r, rcon);
+    aes_round(c, b, r, rcon);
+    rcon = gf8_xtime(rcon);
+  }
+  outA[0] = a.s0; outA[1] = a.s1; outA[2] = a.s2; outA[3] = a.s3;
+  outB[0] = b.s0; outB[1] = b.s1; outB[2] = b.s2; outB[3] = b.s3;
 }
 
 // Initial values (the MDC-2 constants 0x52.. and 0x25.. widened to 16 bytes): MMO and the
@@ -158,8 +188,7 @@ __device__ __forceinline__ void prf_entry_aes(const AesCtx& c, const uint32_t x0
 // halves (words 2 and 3).
 __device__ __forceinline__ void mdc2_step(const AesCtx& c, uint32_t h[4], uint32_t g[4], const uint32_t m[4]) {
   uint32_t a[4], b[4];
-  aes128_encrypt(c, h, m, a);
-  aes128_encrypt(c, g, m, b);
+  aes128_encrypt2(c, h, g, m, a, b);
 #pragma unroll
   for (int i = 0; i < 4; ++i) { a[i] ^= m[i]; b[i] ^= m[i]; }
   h[0] = a[0]; h[1] = a[1]; h[2] = b[2]; h[3] = b[3];
