@@ -13,6 +13,7 @@
 // first_index (2), n (2), malformed (1), agg_mode (1); the kernels read and write e~, s~, R~
 // (words 0..47) and malformed (word kShardBadWord = 52); the host fills in the rest.
 #include "common.cuh"
+#include "compact.cuh"
 
 namespace poslo {
 
@@ -83,77 +84,110 @@ __global__ void __launch_bounds__(kShardThreads) k_combine_check(const uint32_t*
   __shared__ uint32_t sR[32];
   __shared__ uint32_t well_formed;
   const int tid = threadIdx.x;
+  // a single call's worth of arithmetic from compact (out-of-line) field and point
+  // operations: the kernel's code is fetched cold on every launch.  Thread 0 sums the
+  // records, thread 32 (another warp, so the two run side by side) checks them.
+  __shared__ uint32_t valid_records;
+  if (tid == 32) {
+    bool ok = true;
+#pragma unroll 1
+    for (uint32_t i = 0; i < nparts; ++i) {
+      const uint32_t* p = parts + (size_t)i * kShardWords;
+      if (!sc_is_canonical(p) || !sc_is_canonical(p + 8)) ok = false;
+      // coordinates below p, Z != 0, XY = ZT and -X^2 + Y^2 = Z^2 + d T^2 (the extended curve)
+      fe c[4];
+      bool canon = true;
+#pragma unroll 1
+      for (int q = 0; q < 4; ++q) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) c[q].v[k] = p[16 + 8 * q + k];
+        const fe r = compact::canon(c[q]);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) canon &= r.v[k] == c[q].v[k];
+      }
+      const fe XX = compact::sq(c[0]), YY = compact::sq(c[1]), ZZ = compact::sq(c[2]), TT = compact::sq(c[3]);
+      const bool on = !fe_is_zero(c[2]) && fe_eq(compact::mul(c[0], c[1]), compact::mul(c[2], c[3])) &&
+                      fe_eq(fe_sub(YY, XX), fe_add(ZZ, compact::mul(fe_d(), TT)));
+      if (!canon || !on) ok = false;
+    }
+    valid_records = ok ? 1u : 0u;
+  }
+  __shared__ unsigned long long bad_sum;
   if (tid == 0) {
     sc e, s;
 #pragma unroll
     for (int k = 0; k < 8; ++k) e.v[k] = s.v[k] = 0;
     ge R = ge_identity();
     unsigned long long bad = 0;
-    bool ok = true;
+#pragma unroll 1
     for (uint32_t i = 0; i < nparts; ++i) {
       const uint32_t* p = parts + (size_t)i * kShardWords;
       sc ei, si;
+      ge Pi;
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         ei.v[k] = p[k];
         si.v[k] = p[8 + k];
-      }
-      if (!sc_is_canonical(ei.v) || !sc_is_canonical(si.v)) ok = false;
-      ge Pi;
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
         Pi.X.v[k] = p[16 + k];
         Pi.Y.v[k] = p[24 + k];
         Pi.Z.v[k] = p[32 + k];
         Pi.T.v[k] = p[40 + k];
       }
-      // coordinates below p, Z != 0, XY = ZT and -X^2 + Y^2 = Z^2 + d T^2 (the extended curve)
-      const fe X = Pi.X, Y = Pi.Y, Z = Pi.Z, T = Pi.T;
-      bool canon = true;
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        canon &= fe_canon(X).v[k] == X.v[k] && fe_canon(Y).v[k] == Y.v[k] && fe_canon(Z).v[k] == Z.v[k] &&
-                 fe_canon(T).v[k] == T.v[k];
-      }
-      const fe XX = fe_sq(X), YY = fe_sq(Y), ZZ = fe_sq(Z), TT = fe_sq(T);
-      const bool on = !fe_is_zero(Z) && fe_eq(fe_mul(X, Y), fe_mul(Z, T)) &&
-                      fe_eq(fe_sub(YY, XX), fe_add(ZZ, fe_mul(fe_d(), TT)));
-      if (!canon || !on) ok = false;
       e = sc_add(e, ei);
       s = sc_add(s, si);
-      R = ge_add(R, Pi);
+      R = i == 0 ? Pi : compact::add(R, Pi);
       bad += p[kShardBadWord];
     }
     recode4(e.v, dig_e);
     recode4(s.v, dig_s);
     ge_store(sR, R);
-    well_formed = (ok && bad == 0) ? 1u : 0u;
+    bad_sum = bad;
     if (total) {
-      const fe X = fe_canon(R.X), Y = fe_canon(R.Y), Z = fe_canon(R.Z), T = fe_canon(R.T);
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         total[k] = e.v[k];
         total[8 + k] = s.v[k];
-        total[16 + k] = X.v[k];
-        total[24 + k] = Y.v[k];
-        total[32 + k] = Z.v[k];
-        total[40 + k] = T.v[k];
       }
       total[kShardBadWord] = bad > 0xffffffffull ? 0xffffffffu : (uint32_t)bad;
     }
   }
   __syncthreads();
+  if (tid < 4 && total) {   // R~ in canonical coordinates, one coordinate per thread
+    fe c;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) c.v[k] = sR[8 * tid + k];
+    const fe r = compact::canon(c);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) total[16 + 8 * tid + k] = r.v[k];
+  }
+  if (tid == 0) well_formed = (valid_records && bad_sum == 0) ? 1u : 0u;
+  __syncthreads();
   const ge term = tid < 64 ? table_pick(tableY, tid, dig_e[tid]) : table_pick(tableG, tid - 64, dig_s[tid - 64]);
   ge_store(pts_[tid], term);
   __syncthreads();
-  for (int h = kShardThreads / 2; h > 0; h >>= 1) {
-    if (tid < h) ge_store(pts_[tid], ge_add(ge_load(pts_[tid]), ge_load(pts_[tid + h])));
+  // e~Y + s~G: quad q adds terms 4q .. 4q + 3, then a tree over the 32 quads' sums; every
+  // lane takes part in every quad operation (full-mask shuffles), surplus quads' sums unused
+  constexpr int kQuads = kShardThreads / 4;
+  __shared__ uint32_t qs_[kQuads][32];
+  const int quad = tid >> 2;
+  ge acc = ge_identity();
+#pragma unroll 1
+  for (int k = 0; k < 4; ++k) acc = ge_add_quad(acc, ge_load(pts_[4 * quad + k]));
+  if ((tid & 3) == 0) ge_store(qs_[quad], acc);
+  __syncthreads();
+#pragma unroll 1
+  for (int h = kQuads / 2; h > 0; h >>= 1) {
+    const ge sum = ge_add_quad(ge_load(qs_[quad]), ge_load(qs_[(quad + h) % kQuads]));
+    __syncthreads();
+    if ((tid & 3) == 0 && quad < h) ge_store(qs_[quad], sum);
     __syncthreads();
   }
-  if (tid == 0) {
-    const ge diff = ge_sub(ge_load(sR), ge_load(pts_[0]));
-    const bool ok = ge_is_identity(ge_mul_cofactor(diff)) && well_formed && (*status & kErrKey) == 0;
-    accept[0] = ok ? 1 : 0;
+  // [8](R~ - e~Y - s~G) by the first warp's quads (all of them compute it)
+  if (tid < 32) {
+    ge d = ge_add_quad(ge_load(sR), ge_neg(ge_load(qs_[0])));
+#pragma unroll 1
+    for (int i = 0; i < 3; ++i) d = ge_dbl_quad(d);
+    if (tid == 0) accept[0] = (ge_is_identity(d) && well_formed && (*status & kErrKey) == 0) ? 1 : 0;
   }
 }
 
