@@ -49,6 +49,38 @@ static __device__ __noinline__ ge dbl(const ge& p) {
 
 static __device__ __forceinline__ ge sub(const ge& p, const ge& q) { return add(p, ge_neg(q)); }
 
+static __device__ __noinline__ fe sqn(fe a, int n) {
+#pragma unroll 1
+  for (int i = 0; i < n; ++i) a = sq(a);
+  return a;
+}
+
+// z^(p-2), Fermat's inverse (0 -> 0), by the addition chain of fe_inv.
+static __device__ __noinline__ fe inv(const fe& z) {
+  const fe z2 = sq(z);
+  const fe z9 = mul(sqn(z2, 2), z);
+  const fe z11 = mul(z9, z2);
+  const fe z_5 = mul(sq(z11), z9);                 // 2^5 - 1
+  const fe z_10 = mul(sqn(z_5, 5), z_5);           // 2^10 - 1
+  const fe z_20 = mul(sqn(z_10, 10), z_10);        // 2^20 - 1
+  const fe z_40 = mul(sqn(z_20, 20), z_20);        // 2^40 - 1
+  const fe z_50 = mul(sqn(z_40, 10), z_10);        // 2^50 - 1
+  const fe z_100 = mul(sqn(z_50, 50), z_50);       // 2^100 - 1
+  const fe z_200 = mul(sqn(z_100, 100), z_100);    // 2^200 - 1
+  const fe z_250 = mul(sqn(z_200, 50), z_50);      // 2^250 - 1
+  return mul(sqn(z_250, 5), z11);
+}
+
+// The compressed encoding (y with the parity of x in bit 255), as ge_encode.
+static __device__ __noinline__ void encode(const ge& p, uint32_t b[8]) {
+  const fe zi = inv(p.Z);
+  const fe x = canon(mul(p.X, zi));
+  const fe y = canon(mul(p.Y, zi));
+#pragma unroll
+  for (int i = 0; i < 8; ++i) b[i] = y.v[i];
+  b[7] |= (x.v[0] & 1u) << 31;
+}
+
 static __device__ __forceinline__ ge mul_cofactor(ge p) {
 #pragma unroll 1
   for (int i = 0; i < 3; ++i) p = dbl(p);

@@ -8,6 +8,7 @@
 // entries whose errors cancel, so the host confirms the rest of the batch with the weighted
 // check afterwards and falls back to per-entry checks of everything when that fails.
 #include "common.cuh"
+#include "compact.cuh"
 
 namespace poslo {
 
@@ -281,13 +282,15 @@ __global__ void __launch_bounds__(256) k_ccd_points(const uint32_t* pts, const u
   }
   ge_store(sp[threadIdx.x], acc);
   __syncthreads();
+  // once per call: compact (out-of-line) point operations, the code being fetched cold
+#pragma unroll 1
   for (int h = 128; h > 0; h >>= 1) {
-    if (threadIdx.x < h) ge_store(sp[threadIdx.x], ge_add(ge_load(sp[threadIdx.x]), ge_load(sp[threadIdx.x + h])));
+    if (threadIdx.x < h) ge_store(sp[threadIdx.x], compact::add(ge_load(sp[threadIdx.x]), ge_load(sp[threadIdx.x + h])));
     __syncthreads();
   }
   if (threadIdx.x == 0) {
     uint32_t w[8];
-    ge_encode(ge_sub(ge_load(unit), ge_load(sp[0])), w);
+    compact::encode(compact::sub(ge_load(unit), ge_load(sp[0])), w);
     for (int k = 0; k < 8; ++k) {
       enc_out[4 * k] = (uint8_t)w[k]; enc_out[4 * k + 1] = (uint8_t)(w[k] >> 8);
       enc_out[4 * k + 2] = (uint8_t)(w[k] >> 16); enc_out[4 * k + 3] = (uint8_t)(w[k] >> 24);

@@ -1,6 +1,7 @@
 // Verification kernels: epoch seeds, hashing and scalar aggregation, point decoding and sums,
 // window tables and the final cofactored check.
 #include "common.cuh"
+#include "compact.cuh"
 
 namespace poslo {
 
@@ -421,6 +422,8 @@ __global__ void __launch_bounds__(128) k_table_fill(uint32_t n, uint32_t* __rest
   }
 }
 
+// Runs once per call: its point operations are the compact (out-of-line) ones, its code being
+// fetched cold on every launch.
 __global__ void __launch_bounds__(kFinalThreads) k_finalize(const FinalArgs a) {
   __shared__ unsigned long long sums[kPartialWords];
   __shared__ uint32_t pts[kFinalThreads][32];
@@ -446,14 +449,14 @@ __global__ void __launch_bounds__(kFinalThreads) k_finalize(const FinalArgs a) {
   ge acc = ge_identity();
   uint32_t bad = 0;
   for (uint32_t b = tid; b < a.npoint; b += kFinalThreads) {
-    acc = ge_add(acc, ge_load(a.point_partial + (size_t)b * kPointPartialWords));
+    acc = compact::add(acc, ge_load(a.point_partial + (size_t)b * kPointPartialWords));
     bad += a.point_partial[(size_t)b * kPointPartialWords + 32];
   }
   ge_store(pts[tid], acc);
   atomicAdd(&pbad, bad);
   __syncthreads();
   for (int h = kFinalThreads / 2; h > 0; h >>= 1) {
-    if (tid < h) ge_store(pts[tid], ge_add(ge_load(pts[tid]), ge_load(pts[tid + h])));
+    if (tid < h) ge_store(pts[tid], compact::add(ge_load(pts[tid]), ge_load(pts[tid + h])));
     __syncthreads();
   }
   if (tid == 0) {
@@ -482,18 +485,18 @@ __global__ void __launch_bounds__(kFinalThreads) k_finalize(const FinalArgs a) {
   // window terms: thread w adds dig_e[w] 16^w Y + dig_s[w] 16^w G
   ge term = ge_identity();
   if (tid < kTableWindows) {
-    term = ge_add(table_pick(a.tableY, tid, dig_e[tid]), table_pick(a.tableG, tid, dig_s[tid]));
+    term = compact::add(table_pick(a.tableY, tid, dig_e[tid]), table_pick(a.tableG, tid, dig_s[tid]));
   }
   ge_store(pts[tid], term);
   __syncthreads();
   for (int h = kTableWindows / 2; h > 0; h >>= 1) {
-    if (tid < h) ge_store(pts[tid], ge_add(ge_load(pts[tid]), ge_load(pts[tid + h])));
+    if (tid < h) ge_store(pts[tid], compact::add(ge_load(pts[tid]), ge_load(pts[tid + h])));
     __syncthreads();
   }
   if (tid == 0) {
     const ge eYsG = ge_load(pts[0]);
-    const ge diff = ge_sub(R, eYsG);
-    const bool ok = ge_is_identity(ge_mul_cofactor(diff)) && !bad_flag;
+    const ge diff = compact::sub(R, eYsG);
+    const bool ok = ge_is_identity(compact::mul_cofactor(diff)) && !bad_flag;
     const bool key_bad = (*a.status & kErrKey) != 0;
     a.accept[0] = (ok && !key_bad) ? 1 : 0;
     if (a.out_words) {
@@ -547,7 +550,7 @@ __global__ void __launch_bounds__(128) k_final_prep(const PrepArgs a) {
   ge_store(pts_[tid], term);
   __syncthreads();
   for (int h = kPrepThreads / 2; h > 0; h >>= 1) {
-    if (tid < h) ge_store(pts_[tid], ge_add(ge_load(pts_[tid]), ge_load(pts_[tid + h])));
+    if (tid < h) ge_store(pts_[tid], compact::add(ge_load(pts_[tid]), ge_load(pts_[tid + h])));
     __syncthreads();
   }
   if (tid < 32) a.prep[tid] = pts_[0][tid];
@@ -622,7 +625,7 @@ __global__ void __launch_bounds__(kWindowThreads) k_window_prep(const unsigned l
   ge_store(pts_[tid], term);
   __syncthreads();
   for (int h = kWindowThreads / 2; h > 0; h >>= 1) {
-    if (tid < h) ge_store(pts_[tid], ge_add(ge_load(pts_[tid]), ge_load(pts_[tid + h])));
+    if (tid < h) ge_store(pts_[tid], compact::add(ge_load(pts_[tid]), ge_load(pts_[tid + h])));
     __syncthreads();
   }
   if (tid < 32) Pw[32 * w + tid] = pts_[0][tid];
@@ -631,8 +634,8 @@ __global__ void __launch_bounds__(kWindowThreads) k_window_prep(const unsigned l
 __global__ void k_final_check(const uint32_t* prep, const uint32_t* R, const uint32_t* point_bad,
                               const uint32_t* status, uint8_t* accept) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const ge diff = ge_sub(ge_load(R), ge_load(prep));
-  const bool ok = ge_is_identity(ge_mul_cofactor(diff)) && prep[32] == 0 && !(point_bad && *point_bad) &&
+  const ge diff = compact::sub(ge_load(R), ge_load(prep));
+  const bool ok = ge_is_identity(compact::mul_cofactor(diff)) && prep[32] == 0 && !(point_bad && *point_bad) &&
                   (*status & kErrKey) == 0;
   accept[0] = ok ? 1 : 0;
 }
