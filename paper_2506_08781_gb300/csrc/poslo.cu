@@ -2590,9 +2590,14 @@ int poslo_host::stage_wait(poslo_ctx* ctx, int set, int issue_rc) {
   if (set != 0 && set != 1) return fail(ctx, POSLO_EINVAL, "staging set must be 0 or 1");
   StageSet& S = ctx->stage[set];
   ctx->launch_count += S.launches;
-  // what was issued has to land before the requests' memory may be released, error or not
+  // what was issued has to land before the requests' memory may be released, error or not:
+  // a staging that stopped part way recorded no event, so the whole copy stream is drained
+  if (issue_rc != POSLO_OK) {
+    cudaStreamSynchronize(ctx->s_copy);
+    cudaGetLastError();
+    return fail(ctx, issue_rc, "staging: %s", S.err.c_str());
+  }
   CU(cudaEventSynchronize(ctx->ev_copy[set]));
-  if (issue_rc != POSLO_OK) return fail(ctx, issue_rc, "staging: %s", S.err.c_str());
   if (*reinterpret_cast<const uint32_t*>(S.h) & kErrInput)
     return fail(ctx, POSLO_EINVAL, "message offsets decrease (or precede msgs)");
   return POSLO_OK;

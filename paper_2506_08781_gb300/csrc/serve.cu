@@ -23,6 +23,7 @@
 #include <future>
 #include <memory>
 #include <mutex>
+#include <system_error>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -305,7 +306,13 @@ void worker_loop(Server* S, poslo_ctx* w, uint32_t worker) {
     std::unique_ptr<TakenBatch> next;
     if (!batch.empty()) {
       if (cur) {
-        auto issue = std::async(std::launch::async, issue_staging, S, w, worker, std::move(batch), set);
+        std::future<std::unique_ptr<TakenBatch>> issue;
+        try {
+          // a copy of the list: a launch that fails may already have taken its arguments
+          issue = std::async(std::launch::async, issue_staging, S, w, worker, std::vector<Req*>(batch), set);
+        } catch (const std::system_error&) {   // no thread to be had: issue it here
+          issue = std::async(std::launch::deferred, issue_staging, S, w, worker, std::move(batch), set);
+        }
         run_batch(S, w, *cur);
         S->cv_done.notify_all();
         cur.reset();
