@@ -87,5 +87,26 @@ static __device__ __forceinline__ ge mul_cofactor(ge p) {
   return p;
 }
 
+// The sum of the 128 points terms[0..127] (32 words each, in shared memory) by a block of
+// 128 threads: quad q adds terms 4q .. 4q + 3 (quad-cooperative additions), then a tree over
+// the 32 quads' sums in qs; the sum ends in qs[0].  Every thread calls it (full-mask
+// shuffles, barriers inside); the caller has stored the terms and synchronised.
+__device__ __forceinline__ void quad_sum128(uint32_t (*terms)[32], uint32_t (*qs)[32]) {
+  constexpr int kQuads = 32;
+  const int tid = threadIdx.x, quad = tid >> 2;
+  ge acc = ge_identity();
+#pragma unroll 1
+  for (int k = 0; k < 4; ++k) acc = ge_add_quad(acc, ge_load(terms[4 * quad + k]));
+  if ((tid & 3) == 0) ge_store(qs[quad], acc);
+  __syncthreads();
+#pragma unroll 1
+  for (int h = kQuads / 2; h > 0; h >>= 1) {
+    const ge sum = ge_add_quad(ge_load(qs[quad]), ge_load(qs[(quad + h) % kQuads]));
+    __syncthreads();
+    if ((tid & 3) == 0 && quad < h) ge_store(qs[quad], sum);
+    __syncthreads();
+  }
+}
+
 }  // namespace compact
 }  // namespace poslo

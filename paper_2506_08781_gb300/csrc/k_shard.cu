@@ -165,23 +165,10 @@ __global__ void __launch_bounds__(kShardThreads) k_combine_check(const uint32_t*
   const ge term = tid < 64 ? table_pick(tableY, tid, dig_e[tid]) : table_pick(tableG, tid - 64, dig_s[tid - 64]);
   ge_store(pts_[tid], term);
   __syncthreads();
-  // e~Y + s~G: quad q adds terms 4q .. 4q + 3, then a tree over the 32 quads' sums; every
-  // lane takes part in every quad operation (full-mask shuffles), surplus quads' sums unused
-  constexpr int kQuads = kShardThreads / 4;
-  __shared__ uint32_t qs_[kQuads][32];
-  const int quad = tid >> 2;
-  ge acc = ge_identity();
-#pragma unroll 1
-  for (int k = 0; k < 4; ++k) acc = ge_add_quad(acc, ge_load(pts_[4 * quad + k]));
-  if ((tid & 3) == 0) ge_store(qs_[quad], acc);
-  __syncthreads();
-#pragma unroll 1
-  for (int h = kQuads / 2; h > 0; h >>= 1) {
-    const ge sum = ge_add_quad(ge_load(qs_[quad]), ge_load(qs_[(quad + h) % kQuads]));
-    __syncthreads();
-    if ((tid & 3) == 0 && quad < h) ge_store(qs_[quad], sum);
-    __syncthreads();
-  }
+  // e~Y + s~G: the 128 terms summed by quads
+  static_assert(kShardThreads == 128, "one term per thread");
+  __shared__ uint32_t qs_[32][32];
+  compact::quad_sum128(pts_, qs_);
   // [8](R~ - e~Y - s~G) by the first warp's quads (all of them compute it)
   if (tid < 32) {
     ge d = ge_add_quad(ge_load(sR), ge_neg(ge_load(qs_[0])));

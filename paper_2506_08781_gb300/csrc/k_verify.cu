@@ -549,11 +549,9 @@ __global__ void __launch_bounds__(128) k_final_prep(const PrepArgs a) {
   const ge term = tid < 64 ? table_pick(a.tableY, tid, dig_e[tid]) : table_pick(a.tableG, tid - 64, dig_s[tid - 64]);
   ge_store(pts_[tid], term);
   __syncthreads();
-  for (int h = kPrepThreads / 2; h > 0; h >>= 1) {
-    if (tid < h) ge_store(pts_[tid], compact::add(ge_load(pts_[tid]), ge_load(pts_[tid + h])));
-    __syncthreads();
-  }
-  if (tid < 32) a.prep[tid] = pts_[0][tid];
+  __shared__ uint32_t qs_[32][32];
+  compact::quad_sum128(pts_, qs_);
+  if (tid < 32) a.prep[tid] = qs_[0][tid];
   if (tid == 0) a.prep[32] = bad_flag;
 }
 
@@ -624,20 +622,20 @@ __global__ void __launch_bounds__(kWindowThreads) k_window_prep(const unsigned l
   const ge term = tid < 64 ? table_pick(tableY, tid, dig_e[tid]) : table_pick(tableG, tid - 64, dig_s[tid - 64]);
   ge_store(pts_[tid], term);
   __syncthreads();
-  for (int h = kWindowThreads / 2; h > 0; h >>= 1) {
-    if (tid < h) ge_store(pts_[tid], compact::add(ge_load(pts_[tid]), ge_load(pts_[tid + h])));
-    __syncthreads();
-  }
-  if (tid < 32) Pw[32 * w + tid] = pts_[0][tid];
+  __shared__ uint32_t qs_[32][32];
+  compact::quad_sum128(pts_, qs_);
+  if (tid < 32) Pw[32 * w + tid] = qs_[0][tid];
 }
 
+// One warp (quad operations: every lane takes part).
 __global__ void k_final_check(const uint32_t* prep, const uint32_t* R, const uint32_t* point_bad,
                               const uint32_t* status, uint8_t* accept) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const ge diff = compact::sub(ge_load(R), ge_load(prep));
-  const bool ok = ge_is_identity(compact::mul_cofactor(diff)) && prep[32] == 0 && !(point_bad && *point_bad) &&
-                  (*status & kErrKey) == 0;
-  accept[0] = ok ? 1 : 0;
+  if (blockIdx.x != 0) return;
+  ge d = ge_add_quad(ge_load(R), ge_neg(ge_load(prep)));
+#pragma unroll 1
+  for (int i = 0; i < 3; ++i) d = ge_dbl_quad(d);
+  const bool ok = ge_is_identity(d) && prep[32] == 0 && !(point_bad && *point_bad) && (*status & kErrKey) == 0;
+  if (threadIdx.x == 0) accept[0] = ok ? 1 : 0;
 }
 
 // Host launchers (kernel templates are launched from the translation unit that defines them).
