@@ -347,6 +347,7 @@ struct DirectCheckArgs {
 };
 __global__ void __launch_bounds__(128) k_entry_check_group(const DirectCheckArgs a);
 
+
 __device__ __forceinline__ ge double_scalar_tables(const uint32_t e[8], const uint32_t s[8],
                                                    const uint32_t* tableY, const uint32_t* tableG) {
   int8_t de[64], ds_[64];
@@ -613,6 +614,44 @@ __device__ __forceinline__ void pts_load(const uint32_t* src, fe& x, fe& y, fe& 
   t2d = fe_const(v[4].x, v[4].y, v[4].z, v[4].w, v[5].x, v[5].y, v[5].z, v[5].w);
 }
 
+// [8](R_t - e_t Y - s_t G) = O for entry t by the eight lanes of a group (lanes 8g .. 8g+7 of
+// the warp): the first quad sums the 64 terms of [e]Y from Y's window table, the second the
+// 64 of [s]G from G's, each fetching the next window's entry during the current addition;
+// the two sums meet by shuffles and every lane returns the verdict.  Every lane of the warp
+// must call it (full-mask shuffles).
+__device__ __forceinline__ bool entry_check8(const uint8_t* e32, const uint8_t* s32, const uint32_t* pts_t,
+                                             bool malformed, const uint32_t* tableY, const uint32_t* tableG) {
+  const bool g_half = (threadIdx.x & 4) != 0;
+  const uint4* kp = reinterpret_cast<const uint4*>(g_half ? s32 : e32);
+  const uint4 k0 = __ldg(kp), k1 = __ldg(kp + 1);
+  const uint32_t k[8] = {k0.x, k0.y, k0.z, k0.w, k1.x, k1.y, k1.z, k1.w};
+  const uint32_t* tab = g_half ? tableG : tableY;
+  ge acc = ge_identity();
+  int carry = 0;
+  ge next = table_pick(tab, 0, sc_digit4(k, 0, carry));
+  for (int w = 0; w < kTableWindows; ++w) {
+    const ge cur = next;
+    if (w + 1 < kTableWindows) next = table_pick(tab, w + 1, sc_digit4(k, w + 1, carry));
+    acc = ge_add_quad(acc, cur);
+  }
+  ge other;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    other.X.v[i] = __shfl_xor_sync(0xffffffffu, acc.X.v[i], 4);
+    other.Y.v[i] = __shfl_xor_sync(0xffffffffu, acc.Y.v[i], 4);
+    other.Z.v[i] = __shfl_xor_sync(0xffffffffu, acc.Z.v[i], 4);
+    other.T.v[i] = __shfl_xor_sync(0xffffffffu, acc.T.v[i], 4);
+  }
+  acc = ge_add_quad(acc, other);
+  ge R;
+  fe t2d;
+  pts_load(pts_t, R.X, R.Y, t2d);
+  R.Z = fe_one();
+  R.T = fe_mul(R.X, R.Y);
+  const ge d = ge_sub(R, acc);
+  return !malformed && ge_is_identity(ge_dbl_quad(ge_dbl_quad(ge_dbl_quad(d))));
+}
+
 // ---- Distill segment tree (k_distill.cu) ----
 struct TreeArgs {
   const uint32_t* pts;       // n*kPtsWords decoded points
@@ -824,6 +863,10 @@ struct MultiCheckArgs {
   uint8_t* inv;               // out: 1 = entry invalid (written for the flagged devices' entries)
 };
 __global__ void __launch_bounds__(128) k_multi_entry_check(const MultiCheckArgs a);
+// The same checks with eight lanes per entry (as k_entry_check_group): for few flagged
+// entries, where one entry's latency is the launch's.
+__global__ void __launch_bounds__(128) k_multi_entry_check_group(const MultiCheckArgs a);
+constexpr uint64_t kMultiGroupCheckMax = 16384;   // flagged entries up to which the group form runs
 __global__ void k_segment_any(const uint8_t* inv, const uint64_t* seg_start, const uint32_t* fl, uint8_t* out);
 // ---- POSLO-C distillation and SeBVer (k_ccd.cu) ----
 constexpr int kCcdThreads = 128;

@@ -24,44 +24,13 @@ __global__ void __launch_bounds__(128) k_entry_check(const CheckArgs a) {
   }
 }
 
-// Eight lanes per entry: the first quad sums the 64 terms of [e]Y from Y's window table, the
-// second the 64 of [s]G from G's, each fetching the next window's entry during the current
-// addition; the two sums meet by shuffles.  Every lane runs every quad operation (full-mask
-// shuffles), so surplus groups repeat the last entry and do not write.
+// Eight lanes per entry (entry_check8); surplus groups repeat the last entry and do not write.
 __global__ void __launch_bounds__(128) k_entry_check_group(const DirectCheckArgs a) {
   const uint64_t grp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
   if (a.n == 0) return;   // grid-uniform
   const uint64_t t = grp < a.n ? grp : a.n - 1;
-  const bool g_half = (threadIdx.x & 4) != 0;
-  const uint4* kp = reinterpret_cast<const uint4*>((g_half ? a.s : a.e) + 32 * t);
-  const uint4 k0 = __ldg(kp), k1 = __ldg(kp + 1);
-  const uint32_t k[8] = {k0.x, k0.y, k0.z, k0.w, k1.x, k1.y, k1.z, k1.w};
-  const uint32_t* tab = g_half ? a.tableG : a.tableY;
-  ge acc = ge_identity();
-  int carry = 0;
-  ge next = table_pick(tab, 0, sc_digit4(k, 0, carry));
-  for (int w = 0; w < kTableWindows; ++w) {
-    const ge cur = next;
-    if (w + 1 < kTableWindows) next = table_pick(tab, w + 1, sc_digit4(k, w + 1, carry));
-    acc = ge_add_quad(acc, cur);
-  }
-  // both quads: [e]Y + [s]G
-  ge other;
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    other.X.v[i] = __shfl_xor_sync(0xffffffffu, acc.X.v[i], 4);
-    other.Y.v[i] = __shfl_xor_sync(0xffffffffu, acc.Y.v[i], 4);
-    other.Z.v[i] = __shfl_xor_sync(0xffffffffu, acc.Z.v[i], 4);
-    other.T.v[i] = __shfl_xor_sync(0xffffffffu, acc.T.v[i], 4);
-  }
-  acc = ge_add_quad(acc, other);
-  ge R;
-  fe t2d;
-  pts_load(a.pts + (size_t)kPtsWords * t, R.X, R.Y, t2d);
-  R.Z = fe_one();
-  R.T = fe_mul(R.X, R.Y);
-  const ge d = ge_sub(R, acc);
-  const bool ok = !a.badR[t] && !a.badS[t] && ge_is_identity(ge_dbl_quad(ge_dbl_quad(ge_dbl_quad(d))));
+  const bool ok = entry_check8(a.e + 32 * t, a.s + 32 * t, a.pts + (size_t)kPtsWords * t, a.badR[t] || a.badS[t],
+                               a.tableY, a.tableG);
   if ((threadIdx.x & 7) == 0 && grp < a.n) a.invalid[t] = ok ? 0 : 1;
 }
 

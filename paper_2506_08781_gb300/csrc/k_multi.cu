@@ -506,6 +506,24 @@ __global__ void __launch_bounds__(128) k_multi_entry_check(const MultiCheckArgs 
   }
 }
 
+// k_multi_entry_check with eight lanes per entry; surplus groups repeat the last entry and
+// do not write.
+__global__ void __launch_bounds__(128) k_multi_entry_check_group(const MultiCheckArgs a) {
+  const uint64_t total = a.fstart[a.nfl];
+  if (total == 0) return;   // grid-uniform
+  const uint64_t grp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+  const uint64_t t = grp < total ? grp : total - 1;
+  uint32_t lo = 0, hi = a.nfl;   // fstart[lo] <= t < fstart[hi]
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (a.fstart[mid] <= t) lo = mid; else hi = mid;
+  }
+  const uint64_t g = a.seg_start[a.fl[lo]] + (t - a.fstart[lo]);
+  const bool ok = entry_check8(a.e + 32 * g, a.s + 32 * g, a.pts + (size_t)kPtsWords * g, a.badR[g] || a.badS[g],
+                               a.tabs[a.fl[lo]], a.tableG);
+  if ((threadIdx.x & 7) == 0 && grp < total) a.inv[g] = ok ? 0 : 1;
+}
+
 // Per flagged device k: 1 if any of its entries is flagged in inv.
 __global__ void k_segment_any(const uint8_t* inv, const uint64_t* seg_start, const uint32_t* fl, uint8_t* out) {
   const uint32_t d = fl[blockIdx.x];

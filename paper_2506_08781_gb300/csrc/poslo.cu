@@ -3009,7 +3009,10 @@ int poslo_host::aver_multi(poslo_ctx* ctx, const poslo_multi_batch* mb, const ui
     ca.tabs = d_tabs;
     ca.tableG = ctx->tableG;
     ca.inv = inv;
-    if (fst[nfl]) k_multi_entry_check<<<grid_for(ctx, fst[nfl], 128, 8), 128, 0, ctx->s_main>>>(ca);
+    if (fst[nfl] && fst[nfl] <= kMultiGroupCheckMax)
+      k_multi_entry_check_group<<<(unsigned)((8 * fst[nfl] + 127) / 128), 128, 0, ctx->s_main>>>(ca);
+    else if (fst[nfl])
+      k_multi_entry_check<<<grid_for(ctx, fst[nfl], 128, 8), 128, 0, ctx->s_main>>>(ca);
     k_segment_any<<<nfl, 256, 0, ctx->s_main>>>(inv, seg_start, d_fl, d_any);
     ctx->launch_count += 2;
     CU(cudaGetLastError());
