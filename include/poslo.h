@@ -254,12 +254,16 @@ int poslo_combine_check(poslo_ctx* ctx, const uint8_t Y[32], const poslo_partial
  * on the same device.  Requests are copied at submission (unless flagged POSLO_REQ_BORROW)
  * and admitted against the context's mem_budget (POSLO_EBUSY when the device memory they
  * would need does not fit; 0 = no limit).  A worker copies each request of a batch straight
- * from its buffers into device staging (no host concatenation); pinned request buffers make
- * these copies asynchronous DMA.
+ * from its buffers into device staging (no host concatenation): lent page-locked requests
+ * below 1 MiB are read in place by one gather kernel, larger ones and copied requests by one
+ * DMA copy per array (asynchronous when the buffers are page-locked).
  * A free worker takes the oldest pending requests, up to max_batch_devices requests and
  * max_batch_entries entries, and verifies them as one multi-device batch; requests arriving
- * meanwhile join the next batch.  Each result is what poslo_distill gives for that request
- * alone.  All serving calls on one context may be made from any host thread. */
+ * meanwhile join the next batch.  While no worker is idle, a worker also takes its next batch
+ * before verifying the current one and stages it in the background (a second set of device
+ * buffers), and when fewer entries wait than the workers' next batches would hold, each takes
+ * an even share.  Each result is what poslo_distill gives for that request alone.  All
+ * serving calls on one context may be made from any host thread. */
 typedef struct {
   uint32_t key_id;        /* from poslo_register_key */
   uint32_t n2;
