@@ -549,6 +549,7 @@ __global__ void __launch_bounds__(128) k_final_prep(const PrepArgs a) {
   const ge term = tid < 64 ? table_pick(a.tableY, tid, dig_e[tid]) : table_pick(a.tableG, tid - 64, dig_s[tid - 64]);
   ge_store(pts_[tid], term);
   __syncthreads();
+  static_assert(kPrepThreads == 128 && kWindowThreads == 128, "quad_sum128 takes one term per thread of 128");
   __shared__ uint32_t qs_[32][32];
   compact::quad_sum128(pts_, qs_);
   if (tid < 32) a.prep[tid] = qs_[0][tid];
@@ -622,6 +623,7 @@ __global__ void __launch_bounds__(kWindowThreads) k_window_prep(const unsigned l
   const ge term = tid < 64 ? table_pick(tableY, tid, dig_e[tid]) : table_pick(tableG, tid - 64, dig_s[tid - 64]);
   ge_store(pts_[tid], term);
   __syncthreads();
+  static_assert(kPrepThreads == 128 && kWindowThreads == 128, "quad_sum128 takes one term per thread of 128");
   __shared__ uint32_t qs_[32][32];
   compact::quad_sum128(pts_, qs_);
   if (tid < 32) Pw[32 * w + tid] = qs_[0][tid];
