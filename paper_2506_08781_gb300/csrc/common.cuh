@@ -378,10 +378,6 @@ struct CheckArgs {
 // Reduce scalar partials (13 u64 limb sums per block) to one canonical scalar.
 
 
-// Ordered compaction of flagged entries: one block walks the flags in chunks of its size,
-// each chunk scanned with warp ballots, and writes first_index + t for every flag in
-// ascending order (up to cap; the total count goes to *count).
-constexpr int kCompactThreads = 1024;
 
 
 // Sum point partials (one block) and encode the result.
@@ -714,8 +710,6 @@ __global__ void __launch_bounds__(128) k_entry_check(const CheckArgs a);
 __global__ void __launch_bounds__(kHashThreads) k_sum_scalars(const uint8_t* s, uint64_t n, const uint8_t* skip,
                                                              unsigned long long* partial);
 __global__ void k_reduce_scalars(const unsigned long long* partial, uint32_t nparts, uint8_t* out);
-__global__ void __launch_bounds__(kCompactThreads) k_compact(const uint8_t* flags, uint64_t n, uint64_t first_index,
-                                                             uint64_t* out, uint64_t cap, uint64_t* count);
 __global__ void k_sum_encode(const uint32_t* partial, uint32_t nparts, uint32_t* point_out, uint8_t* enc_out,
                              uint32_t* bad_out);
 __global__ void k_keygen_y(const uint8_t* y, const uint32_t* tableG, uint8_t* Y_out);
@@ -788,8 +782,6 @@ __global__ void __launch_bounds__(256) k_ccd_points(const uint32_t* pts, const u
                                                     const uint64_t* nf_dev, const uint32_t* unit, uint8_t* enc_out);
 __global__ void __launch_bounds__(kHashThreads) k_weighted_sums(const uint8_t* e, const uint8_t* s, const uint32_t* z, const uint8_t* skip1,
                                 const uint8_t* skip2, uint64_t n, unsigned long long* partial);
-__global__ void __launch_bounds__(kPointThreads) k_pts_sum(const uint32_t* pts, const uint8_t* skip1, const uint8_t* skip2, uint64_t n,
-                          uint32_t* partial);
 __global__ void k_flags_or(const uint8_t* a, const uint8_t* b, const uint8_t* c, uint64_t n, uint8_t* out);
 __global__ void k_encode_ext(const uint32_t* point, uint8_t* out);
 void launch_epoch_seeds_multi(int inst, unsigned grid, unsigned block, cudaStream_t st, const DsNode* ds_all,

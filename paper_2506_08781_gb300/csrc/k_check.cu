@@ -84,34 +84,6 @@ __global__ void k_reduce_scalars(const unsigned long long* partial, uint32_t npa
   }
 }
 
-__global__ void __launch_bounds__(kCompactThreads) k_compact(const uint8_t* flags, uint64_t n, uint64_t first_index,
-                                                             uint64_t* out, uint64_t cap, uint64_t* count) {
-  __shared__ uint32_t warp_tot[kCompactThreads / 32];
-  __shared__ uint64_t base;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) base = 0;
-  __syncthreads();
-  for (uint64_t c0 = 0; c0 < n; c0 += kCompactThreads) {
-    const uint64_t t = c0 + threadIdx.x;
-    const bool f = t < n && flags[t] != 0;
-    const uint32_t m = __ballot_sync(0xffffffffu, f);
-    if (lane == 0) warp_tot[warp] = __popc(m);
-    __syncthreads();
-    uint64_t off = base;
-    for (int w = 0; w < warp; ++w) off += warp_tot[w];
-    off += __popc(m & ((1u << lane) - 1u));
-    if (f && off < cap) out[off] = first_index + t;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      uint64_t tot = 0;
-      for (int w = 0; w < kCompactThreads / 32; ++w) tot += warp_tot[w];
-      base += tot;
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *count = base;
-}
-
 __global__ void k_sum_encode(const uint32_t* partial, uint32_t nparts, uint32_t* point_out, uint8_t* enc_out,
                              uint32_t* bad_out) {
   __shared__ uint32_t sp[kFinalThreads][32];

@@ -340,28 +340,6 @@ __global__ void __launch_bounds__(kHashThreads) k_weighted_sums(const uint8_t* e
   }
 }
 
-// Unit sum of the stored points not flagged (partials in the k_points layout).
-__global__ void __launch_bounds__(kPointThreads) k_pts_sum(const uint32_t* pts, const uint8_t* skip1,
-                                                          const uint8_t* skip2, uint64_t n, uint32_t* partial) {
-  ge acc = ge_identity();
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
-    if (flagged(skip1, skip2, t)) continue;
-    fe x, y, t2d;
-    pts_load(pts + (size_t)kPtsWords * t, x, y, t2d);
-    acc = ge_madd(acc, x, y, t2d);
-  }
-  __shared__ uint32_t sp[kPointThreads][32];
-  ge_store(sp[threadIdx.x], acc);
-  __syncthreads();
-  for (int h = kPointThreads / 2; h > 0; h >>= 1) {
-    if (threadIdx.x < h) ge_store(sp[threadIdx.x], ge_add(ge_load(sp[threadIdx.x]), ge_load(sp[threadIdx.x + h])));
-    __syncthreads();
-  }
-  if (threadIdx.x < 32) partial[(uint64_t)blockIdx.x * kPointPartialWords + threadIdx.x] = sp[0][threadIdx.x];
-  if (threadIdx.x == 0) partial[(uint64_t)blockIdx.x * kPointPartialWords + 32] = 0;
-}
-
 // out[t] = a[t] | b[t] | c[t] (NULL arrays count as zero).
 __global__ void k_flags_or(const uint8_t* a, const uint8_t* b, const uint8_t* c, uint64_t n, uint8_t* out) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
