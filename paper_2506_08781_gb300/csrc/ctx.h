@@ -91,6 +91,8 @@ struct poslo_ctx {
   uint32_t* h_status = nullptr;   // pinned mirror
   uint8_t* h_small = nullptr;     // pinned, kSmallHostBytes: small results and shard records
   poslo_host::StageSet stage[2];  // serving staging sets (filled by a worker's staging thread)
+  uint8_t* h_pack = nullptr;      // page-locked packing of small host batches
+  size_t h_pack_cap = 0;
   std::string err;
   bool profiling = false;
   uint64_t launch_count = 0;      // kernels launched by this context

@@ -292,7 +292,15 @@ struct Staged {
   uint64_t base_off = 0;
   const uint8_t* s = nullptr;
   const uint8_t* R = nullptr;
+  bool packed = false;   // a host batch that went up as one copy before any launch
 };
+
+// Host batches up to this many bytes (R_t, offsets, messages, s_t) are packed into page-locked
+// memory and go up as one copy: fewer, asynchronous copies, and every input is on the device
+// before the first launch, so the launch sequence can be replayed from a CUDA graph as for
+// device-resident batches.  Larger host batches are copied array by array, R_t first, so that
+// the decoding starts while the messages are still in flight.
+constexpr size_t kPackMaxBytes = 8u << 20;
 
 bool device_aligned(const void* offs, const void* s, const void* R) {
   return !(reinterpret_cast<uintptr_t>(offs) & 7) && !(reinterpret_cast<uintptr_t>(s) & 15) &&
@@ -337,6 +345,43 @@ int stage_batch(poslo_ctx* ctx, const poslo_batch* b, Staged& sb, size_t s_bytes
   const void* p;
   const size_t s_bytes = s_bytes_override ? s_bytes_override : (b->variant == POSLO_VARIANT_F ? 32 * b->n : 32);
   const size_t R_bytes = 32 * (b->variant == POSLO_VARIANT_F ? b->n : b->R_count);
+  if (!dev && b->n) {
+    const uint64_t lo = b->offs[0], hi = b->offs[b->n];
+    if (hi < lo) return fail(ctx, POSLO_EINVAL, "offsets decrease");
+    const size_t offs_bytes = 8 * (b->n + 1), msg_bytes = hi - lo;
+    auto up16 = [](size_t x) { return (x + 15) & ~size_t(15); };
+    const size_t oR = 0, oO = up16(R_bytes), oM = oO + up16(offs_bytes), oS = oM + up16(msg_bytes);
+    const size_t total = oS + up16(s_bytes);
+    if (total <= kPackMaxBytes) {
+      if (ctx->h_pack_cap < total) {
+        if (ctx->h_pack) cudaFreeHost(ctx->h_pack);
+        ctx->h_pack = nullptr;
+        ctx->h_pack_cap = 0;
+        const size_t want = std::max<size_t>(total, 1 << 20);
+        if (cudaMallocHost(&ctx->h_pack, want) != cudaSuccess) {
+          cudaGetLastError();
+          return fail(ctx, POSLO_ENOMEM, "page-locked staging of %zu bytes", want);
+        }
+        ctx->h_pack_cap = want;
+      }
+      uint8_t* d;
+      if ((rc = ensure_t(ctx, "packed_in", total, &d))) return rc;
+      // the previous call's copy out of h_pack has completed: every call ends synchronised
+      memcpy(ctx->h_pack + oR, b->R, R_bytes);
+      memcpy(ctx->h_pack + oO, b->offs, offs_bytes);
+      if (msg_bytes) memcpy(ctx->h_pack + oM, b->msgs + lo, msg_bytes);
+      memcpy(ctx->h_pack + oS, b->s, s_bytes);
+      CU(cudaMemcpyAsync(d, ctx->h_pack, total, cudaMemcpyHostToDevice, ctx->s_main));
+      CU(cudaEventRecord(ctx->ev_staged, ctx->s_main));
+      sb.R = d + oR;
+      sb.offs = reinterpret_cast<const uint64_t*>(d + oO);
+      sb.msgs = d + oM;
+      sb.base_off = lo;
+      sb.s = d + oS;
+      sb.packed = true;
+      return POSLO_OK;
+    }
+  }
   if ((rc = stage(ctx, "R_in", b->R, R_bytes, dev, ctx->s_main, &p))) return rc;
   sb.R = static_cast<const uint8_t*>(p);
   CU(cudaEventRecord(ctx->ev_staged, ctx->s_main));
@@ -976,6 +1021,7 @@ void poslo_destroy(poslo_ctx* ctx) {
   if (ctx->tableG) cudaFree(ctx->tableG);
   if (ctx->status) cudaFree(ctx->status);
   if (ctx->h_status) cudaFreeHost(ctx->h_status);
+  if (ctx->h_pack) cudaFreeHost(ctx->h_pack);
   for (poslo_host::StageSet& S : ctx->stage) {
     for (poslo_host::DevBuf* b : {&S.msgs, &S.raw, &S.offs, &S.s, &S.R, &S.meta, &S.regions, &S.status})
       if (b->p) cudaFree(b->p);
@@ -1445,7 +1491,7 @@ int poslo_aver_partial(poslo_ctx* ctx, const poslo_batch* batch, uint32_t agg_mo
   const uint32_t nhb = (uint32_t)grid_for(ctx, n, kHashThreads, 8);
   unsigned long long* hpart;
   if ((rc = ensure_t(ctx, "hash_partial", (size_t)nhb * kPartialWords * 8, &hpart))) return rc;
-  const bool replayable = batch->on_device != 0;
+  const bool replayable = batch->on_device != 0 || sb.packed;
   ZPre zp;
   make_zpre(ctx->vseed, zp.w);
   HashArgs a{};
@@ -1680,7 +1726,7 @@ int poslo_distill(poslo_ctx* ctx, const poslo_batch* batch, uint64_t* invalid_id
   uint32_t* Pw_bad = Pw + 32 * kMsmMaxWindows;
   // ---- up to the weighted check of the whole batch; a device-resident batch of the previous
   // call's shape replays it from a CUDA graph
-  const bool replayable = batch->on_device != 0;
+  const bool replayable = batch->on_device != 0 || sb.packed;
   auto stage1 = [&]() -> int {
     int rc;
     // window table of Y (table stream), unless cached
