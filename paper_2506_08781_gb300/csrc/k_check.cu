@@ -1,5 +1,6 @@
 // Per-entry checks, the reference multi-scalar multiplication, masked sums and ordered compaction used by Distill.
 #include "common.cuh"
+#include "compact.cuh"
 
 namespace poslo {
 
@@ -91,17 +92,20 @@ __global__ void k_sum_encode(const uint32_t* partial, uint32_t nparts, uint32_t*
   const int tid = threadIdx.x;
   if (tid == 0) sbad = 0;
   __syncthreads();
+  // once per call: compact (out-of-line) point operations, the code being fetched cold
   ge acc = ge_identity();
   uint32_t bad = 0;
+#pragma unroll 1
   for (uint32_t b = tid; b < nparts; b += kFinalThreads) {
-    acc = ge_add(acc, ge_load(partial + (size_t)b * kPointPartialWords));
+    acc = compact::add(acc, ge_load(partial + (size_t)b * kPointPartialWords));
     bad += partial[(size_t)b * kPointPartialWords + 32];
   }
   ge_store(sp[tid], acc);
   atomicAdd(&sbad, bad);
   __syncthreads();
+#pragma unroll 1
   for (int h = kFinalThreads / 2; h > 0; h >>= 1) {
-    if (tid < h) ge_store(sp[tid], ge_add(ge_load(sp[tid]), ge_load(sp[tid + h])));
+    if (tid < h) ge_store(sp[tid], compact::add(ge_load(sp[tid]), ge_load(sp[tid + h])));
     __syncthreads();
   }
   if (tid == 0) {
@@ -109,7 +113,7 @@ __global__ void k_sum_encode(const uint32_t* partial, uint32_t nparts, uint32_t*
     if (point_out) ge_store(point_out, r);
     if (enc_out) {
       uint32_t w[8];
-      ge_encode(r, w);
+      compact::encode(r, w);
       for (int k = 0; k < 8; ++k) {
         enc_out[4 * k] = (uint8_t)w[k]; enc_out[4 * k + 1] = (uint8_t)(w[k] >> 8);
         enc_out[4 * k + 2] = (uint8_t)(w[k] >> 16); enc_out[4 * k + 3] = (uint8_t)(w[k] >> 24);
@@ -123,7 +127,7 @@ __global__ void k_sum_encode(const uint32_t* partial, uint32_t nparts, uint32_t*
 __global__ void k_encode_ext(const uint32_t* point, uint8_t* out) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   uint32_t w[8];
-  ge_encode(ge_load(point), w);
+  compact::encode(ge_load(point), w);
   for (int k = 0; k < 8; ++k) {
     out[4 * k] = (uint8_t)w[k]; out[4 * k + 1] = (uint8_t)(w[k] >> 8);
     out[4 * k + 2] = (uint8_t)(w[k] >> 16); out[4 * k + 3] = (uint8_t)(w[k] >> 24);
