@@ -299,8 +299,9 @@ struct Staged {
 // memory and go up as one copy: fewer, asynchronous copies, and every input is on the device
 // before the first launch, so the launch sequence can be replayed from a CUDA graph as for
 // device-resident batches.  Larger host batches are copied array by array, R_t first, so that
-// the decoding starts while the messages are still in flight.
-constexpr size_t kPackMaxBytes = 8u << 20;
+// the decoding starts while the messages are still in flight (and page-locked callers' arrays
+// go by DMA without a host copy).
+constexpr size_t kPackMaxBytes = 1u << 20;
 
 bool device_aligned(const void* offs, const void* s, const void* R) {
   return !(reinterpret_cast<uintptr_t>(offs) & 7) && !(reinterpret_cast<uintptr_t>(s) & 15) &&
