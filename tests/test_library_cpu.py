@@ -121,3 +121,37 @@ def test_product_path_never_imports_the_oracle():
             "print(any(m == 'oracle' or m.startswith('oracle.') for m in sys.modules))")
     r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and r.stdout.strip() == "False", r.stderr
+
+
+def test_binding_structures_match_the_header(tmp_path):
+    """Every C structure of include/poslo.h and its ctypes mirror in the binding agree in size
+    and in the offset of every field (compiled by the host C compiler; no GPU needed)."""
+    import ctypes as C
+    import shutil
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    pairs = {"poslo_params": poslo.Params, "poslo_batch": poslo.Batch, "poslo_multi_batch": poslo.MultiBatch,
+             "poslo_partial": poslo.Partial, "poslo_request": poslo.Request, "poslo_batch_record": poslo.BatchRecord,
+             "poslo_ccd_c": poslo.CcdC}
+    lines = []
+    for cname, py in pairs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "poslo.h"\nint main(void) {\n' +
+                   "\n".join(lines) + "\n  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True,
+                   capture_output=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {}
+    for ln in out:
+        if ln:
+            parts = ln.split()
+            got[tuple(parts[:-1])] = int(parts[-1])
+    for cname, py in pairs.items():
+        assert got[(cname, "size")] == C.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
