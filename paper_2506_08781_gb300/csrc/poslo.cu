@@ -2273,8 +2273,10 @@ void store_le_words(const uint32_t* w, uint8_t* out) {
 // Shared part of C.Distill and SeBVer: checks the batch (whole epochs, per-epoch s~_i and
 // R~_i), stages it, starts the key table, and leaves the per-epoch sums e~_i (n1 x 32 bytes,
 // limbs little-endian) in *esum.
+// The key's window table comes from the key cache; a table this call builds into a new cache
+// slot is forgotten again (kforget) unless the caller disarms it once the key has decoded.
 int ccd_common(poslo_ctx* ctx, const poslo_batch* batch, uint32_t n_umbrella, Staged& sb, uint64_t& n1,
-               uint32_t** tableY, uint8_t** esum) {
+               uint32_t** tableY, uint8_t** esum, std::vector<uint32_t>& kmiss, KeyForget& kforget) {
   int rc;
   if ((rc = validate_batch(ctx, batch))) return rc;
   if (batch->variant != POSLO_VARIANT_C) return fail(ctx, POSLO_EINVAL, "distillation with ccd is POSLO-C");
@@ -2285,7 +2287,16 @@ int ccd_common(poslo_ctx* ctx, const poslo_batch* batch, uint32_t n_umbrella, St
                                                       (unsigned long long)n1);
   if ((rc = reset_status(ctx))) return rc;
   if ((rc = stage_batch(ctx, batch, sb, 32 * n1))) return rc;
-  if ((rc = run_ytable(ctx, batch->Y, tableY))) return rc;
+  std::vector<const uint32_t*> ktab;
+  std::vector<uint32_t*> kdst;
+  const bool kcached = key_cache_lookup(ctx, batch->Y, 1, ktab, kmiss, kdst);
+  kforget.armed = kcached && !kmiss.empty();
+  if (kcached && kmiss.empty()) {
+    *tableY = const_cast<uint32_t*>(ktab[0]);
+    CU(cudaEventRecord(ctx->ev_table, ctx->s_main));   // nothing to wait for
+  } else if ((rc = run_ytable(ctx, batch->Y, tableY, kcached ? kdst[0] : nullptr))) {
+    return rc;
+  }
   uint8_t* d_e;
   if ((rc = ensure_t(ctx, "e_all", 32 * batch->n, &d_e))) return rc;
   if ((rc = ensure_t(ctx, "ccd_esum", 32 * n1, esum))) return rc;
@@ -2312,7 +2323,9 @@ int poslo_distill_c(poslo_ctx* ctx, const poslo_batch* batch, uint32_t n_umbrell
   uint64_t n1 = 0;
   uint32_t* tableY;
   uint8_t* esum;
-  if ((rc = ccd_common(ctx, batch, n_umbrella, sb, n1, &tableY, &esum))) return rc;
+  std::vector<uint32_t> kmiss;
+  KeyForget kforget{ctx, batch ? batch->Y : nullptr, &kmiss, false};
+  if ((rc = ccd_common(ctx, batch, n_umbrella, sb, n1, &tableY, &esum, kmiss, kforget))) return rc;
   const uint64_t g = n1 / n_umbrella;
   uint32_t *pts, *ppart, npb, *words;
   uint8_t *badR, *ok, *inv, *encs;
@@ -2349,6 +2362,7 @@ int poslo_distill_c(poslo_ctx* ctx, const poslo_batch* batch, uint32_t n_umbrell
   CU(cudaMemcpyAsync(he.data(), encs, he.size(), cudaMemcpyDeviceToHost, ctx->s_main));
   CU(cudaMemcpyAsync(&cnt, d_cnt, 8, cudaMemcpyDeviceToHost, ctx->s_main));
   if ((rc = check_status(ctx))) return rc;
+  kforget.armed = false;   // the key decoded: its table is sound
   store_le_words(hw.data(), ccd->s_v);
   memcpy(ccd->R_v, he.data(), 32);
   for (uint32_t l = 0; l < n_umbrella; ++l) {
@@ -2374,7 +2388,9 @@ int poslo_sebver_c(poslo_ctx* ctx, const poslo_batch* batch, uint32_t n_umbrella
   uint64_t n1 = 0;
   uint32_t* tableY;
   uint8_t* esum;
-  if ((rc = ccd_common(ctx, batch, n_umbrella, sb, n1, &tableY, &esum))) return rc;
+  std::vector<uint32_t> kmiss;
+  KeyForget kforget{ctx, batch ? batch->Y : nullptr, &kmiss, false};
+  if ((rc = ccd_common(ctx, batch, n_umbrella, sb, n1, &tableY, &esum, kmiss, kforget))) return rc;
   const uint64_t g = n1 / n_umbrella;
   const uint64_t first_epoch = batch->first_index / batch->n2;
   // the epochs of ccd^i, as positions in the batch
@@ -2388,7 +2404,11 @@ int poslo_sebver_c(poslo_ctx* ctx, const poslo_batch* batch, uint32_t n_umbrella
     mask[pos[k]] = 1;
   }
   const uint64_t nchk = mode == POSLO_SEBVER_V ? 1 : (mode == POSLO_SEBVER_U ? n_umbrella : ccd->n_invalid);
-  if (nchk == 0) return check_status(ctx);
+  if (nchk == 0) {
+    if ((rc = check_status(ctx))) return rc;
+    kforget.armed = false;   // the key decoded: its table is sound
+    return POSLO_OK;
+  }
   uint8_t *d_mask, *s_chk, *R_chk, *bad, *d_bits;
   uint32_t *e_chk, *pts, *ppart, npb;
   uint64_t* d_pos;
@@ -2435,7 +2455,9 @@ int poslo_sebver_c(poslo_ctx* ctx, const poslo_batch* batch, uint32_t n_umbrella
   ++ctx->launch_count;
   CU(cudaGetLastError());
   CU(cudaMemcpyAsync(bits, d_bits, nchk, cudaMemcpyDeviceToHost, ctx->s_main));
-  return check_status(ctx);
+  if ((rc = check_status(ctx))) return rc;
+  kforget.armed = false;   // the key decoded: its table is sound
+  return POSLO_OK;
 }
 
 }  // extern "C"

@@ -122,3 +122,29 @@ def test_distill_c_every_epoch_invalid(env):
         _flip(ms, i, 0)
     valid, ccd = _run(ctx, Y, ms, 4, s_ep, R, O.ds_root(km.root, 2), 2)
     assert valid == [False] * 4 and ccd["s_v"] == bytes(32) and ccd["R_v"] == O.encode_point(O.IDENTITY)
+
+
+def test_distill_c_and_sebver_use_the_key_cache(env):
+    """POSLO-C Distill builds the key's window table into the context's key cache and the
+    SeBVer calls that follow reuse it (results equal the oracle's all along); a key that does
+    not decode is refused (EINVAL) and not kept, so the next call misses again."""
+    ctx, _ = env
+    km, Y, R, ms, s_ep = _epochs(66, 2, 4, 4)
+    _flip(ms, 1, 2)
+    ds_l = O.ds_root(km.root, 2)
+    h0, m0 = ctx.key_cache_stats()
+    _run(ctx, Y, ms, 4, s_ep, R, ds_l, 2)           # distill_c misses, SeBVer V, U and I hit
+    h1, m1 = ctx.key_cache_stats()
+    assert (h1 - h0, m1 - m0) == (3, 1)
+    y = 2
+    while O.decode_point(y.to_bytes(32, "little")) is not None:
+        y += 1
+    flat = synth.pack([m for mk in ms for m in mk])
+    b = ctx.make_batch(poslo.VARIANT_C, 4, y.to_bytes(32, "little"), flat.data, flat.offs, b"".join(s_ep),
+                       b"".join(R), O.ds_serialize(ds_l))
+    for _ in range(2):
+        with pytest.raises(poslo.PosloError) as e:
+            ctx.distill_c(b, 2)
+        assert e.value.code == -1
+    h2, m2 = ctx.key_cache_stats()
+    assert (h2 - h1, m2 - m1) == (0, 2)
