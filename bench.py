@@ -448,8 +448,8 @@ def bench_small_latency(device: int, calls: int = SMALL_CALLS) -> dict:
     ds = struct.pack("<II", SMALL_D, 0) + km.root
     Yc, epoch_R = ctx.keygen_c(km.y, km.r, SMALL_D, N2)
     s_ep = ctx.sign_c(km.y, km.r, km.root, SMALL_D, N2, msgs.data, msgs.offs, 0, 1 << SMALL_D).reshape(-1, 32)
-    # C.Agg of the four epochs' signatures (test-data side, outside the timed calls)
-    s_agg = (sum(int.from_bytes(bytes(r), "little") for r in s_ep) % Q_ORDER).to_bytes(32, "little")
+    # C.Agg of the epochs' signatures (test-data side, outside the timed calls)
+    s_agg, _ = ctx.agg(s_ep.tobytes(), np.asarray(epoch_R, np.uint8).tobytes())
     Yf, bpv_R = ctx.keygen_f(km.y, km.bpv_r)
     sub = synth.bpv_subsets(SEED + 11, SMALL_N, v=64, k=4)
     s_f, R_f = ctx.sign_f(km.y, km.root, SMALL_D, N2, km.bpv_r, bpv_R, sub, msgs.data, msgs.offs)
@@ -523,7 +523,6 @@ def bench_stream(device: int) -> dict:
 
 # ------------------------------------------------------------------------------ POSLO-C, hash-bound
 
-Q_ORDER = 2 ** 252 + 27742317777372353535851937790883648493   # order of the group (edwards25519)
 # Thread instructions per AES-128 of the table cipher with its on-the-fly key schedule, counted
 # from the algorithm (not the compiled code): each of the 16 round lookups and 4 key-schedule
 # S-box lookups is a byte extract, an address computation and a shared-memory read (3); a full
@@ -591,8 +590,8 @@ def bench_hash_bound(device: int, steps: int, warmup: int) -> dict:
             ctx = poslo.Context(device=device, instantiation=inst)
             Y, epoch_R = ctx.keygen_c(km.y, km.r, D, N2)
             s_ep = ctx.sign_c(km.y, km.r, km.root, D, N2, msgs.data, msgs.offs, 0, 1 << D).reshape(-1, 32)
-            s_agg = sum(int.from_bytes(bytes(r), "little") for r in s_ep) % Q_ORDER
-            d_s = torch.from_numpy(np.frombuffer(s_agg.to_bytes(32, "little"), np.uint8).copy()).cuda()
+            s_agg, _ = ctx.agg(s_ep.tobytes(), np.asarray(epoch_R, np.uint8).tobytes())   # C.Agg, test data
+            d_s = torch.from_numpy(np.frombuffer(s_agg, np.uint8).copy()).cuda()
             d_R = torch.from_numpy(np.asarray(epoch_R, np.uint8).copy()).cuda()
             ds = struct.pack("<II", D, 0) + km.root
             torch.cuda.synchronize()
