@@ -742,6 +742,8 @@ __global__ void __launch_bounds__(kCombineBigThreads) k_msm_combine_big(const ui
                                                                         const uint32_t* big_count);
 __global__ void __launch_bounds__(128) k_msm_chunk(const uint32_t* buckets, MsmPlan pl, uint32_t* L, uint32_t* T);
 __global__ void __launch_bounds__(512) k_msm_groups(const uint32_t* L, const uint32_t* T, MsmPlan pl, uint32_t* groups);
+constexpr int kMsmDirectMaxC = 8;   // windows up to this width skip the chunk and group sums (512 threads)
+__global__ void __launch_bounds__(512) k_msm_direct_groups(const uint32_t* buckets, MsmPlan pl, uint32_t* groups);
 __global__ void __launch_bounds__(32) k_msm_final(const uint32_t* groups, MsmPlan pl, uint32_t* out);
 __global__ void __launch_bounds__(32) k_msm_windows(const uint32_t* groups, MsmPlan pl, uint32_t* W);
 __global__ void __launch_bounds__(32) k_msm_window_check(const uint32_t* groups, MsmPlan pl, const uint32_t* Pw,

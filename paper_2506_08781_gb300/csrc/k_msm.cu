@@ -249,6 +249,49 @@ __global__ void __launch_bounds__(128) k_msm_chunk(const uint32_t* buckets, MsmP
   }
 }
 
+// Narrow windows (c <= 8, the plans of batches of a few thousand entries): the window sum
+// W_w = sum_d d B_d directly, one block per window and one quad per bucket d = 1 .. 2^(c-1):
+// d B_d by double-and-add over c bits (the same c steps for every quad, the addition taken or
+// not by a select: quad operations need every lane of the warp), then a tree over the
+// buckets.  W_w goes to group 0 of window w and O to its other groups, which the window
+// kernels read as G_0 + 16 sum_k 2^k G_{1+k} = W_w.  It replaces the running sums over chunks
+// and the group sums, whose chains of dependent additions set the latency at these sizes.
+__global__ void __launch_bounds__(512) k_msm_direct_groups(const uint32_t* buckets, MsmPlan pl, uint32_t* groups) {
+  extern __shared__ uint32_t sp[];   // one point (32 words) per quad
+  const int w = blockIdx.x;
+  const int quad = threadIdx.x >> 2, nq = blockDim.x >> 2;   // nq = 2^(c-1)
+  const uint32_t d = (uint32_t)quad + 1;
+  const ge B = ge_load(buckets + 32 * ((size_t)w * pl.nb + d));
+  ge acc = ge_identity();
+#pragma unroll 1
+  for (int bit = pl.c - 1; bit >= 0; --bit) {
+    acc = ge_dbl_quad(acc);
+    const ge sum = ge_add_quad(acc, B);
+    acc = ge_select(acc, sum, ((d >> bit) & 1u) != 0);
+  }
+  if ((threadIdx.x & 3) == 0) ge_store(sp + 32 * quad, acc);
+  __syncthreads();
+#pragma unroll 1
+  for (int h = nq / 2; h > 0; h >>= 1) {
+    const ge sum = ge_add_quad(ge_load(sp + 32 * quad), ge_load(sp + 32 * ((quad + h) % nq)));
+    __syncthreads();
+    if ((threadIdx.x & 3) == 0 && quad < h) ge_store(sp + 32 * quad, sum);
+    __syncthreads();
+  }
+  const int ng = 1 + pl.jbits;
+  uint32_t* G = groups + 32 * (size_t)w * ng;
+  for (int i = threadIdx.x; i < 32 * ng; i += blockDim.x) {
+    const int g = i >> 5, k = i & 31;
+    uint32_t v;
+    if (g == 0) {
+      v = sp[k];
+    } else {   // the identity (0 : 1 : 1 : 0), word k of the extended point
+      v = (k == 8 || k == 16) ? 1u : 0u;
+    }
+    G[i] = v;
+  }
+}
+
 // Group sums per window: group 0 = sum_j L_j; group 1+k = sum of T_j over chunks j whose
 // bit k is set.  One block of 256 quads per (window, group); every quad takes part in every
 // addition of the tree (quad operations need all lanes), only the surviving half keeps it.

@@ -763,9 +763,14 @@ int run_msm_finish(poslo_ctx* ctx, cudaStream_t st, const uint32_t* pts, const u
   timer_end(ctx, "msm_bucket", st, sb_, se_);
   timer_begin(ctx, "msm_reduce", st, &sb_, &se_);
   const size_t nch = (size_t)pl.windows * pl.nchunks;
-  k_msm_chunk<<<(unsigned)((4 * nch + 127) / 128), 128, 0, st>>>(buckets, pl, L, T);
-  k_msm_groups<<<pl.windows * (1 + pl.jbits), 512, 0, st>>>(L, T, pl, groups);
-  ctx->launch_count += 2;
+  if (pl.c <= kMsmDirectMaxC) {   // narrow windows: W_w = sum_d d B_d directly (into group 0)
+    const unsigned threads = 4u << (pl.c - 1);
+    k_msm_direct_groups<<<pl.windows, threads, (size_t)32 * 4 * (threads / 4), st>>>(buckets, pl, groups);
+  } else {
+    k_msm_chunk<<<(unsigned)((4 * nch + 127) / 128), 128, 0, st>>>(buckets, pl, L, T);
+    k_msm_groups<<<pl.windows * (1 + pl.jbits), 512, 0, st>>>(L, T, pl, groups);
+  }
+  ctx->launch_count += pl.c <= kMsmDirectMaxC ? 1 : 2;
   timer_end(ctx, "msm_reduce", st, sb_, se_);
   if (groups_out) {   // the caller checks window by window (k_msm_window_check)
     *groups_out = groups;
